@@ -1,0 +1,165 @@
+"""Seeded synthetic workloads for the modified-Helmholtz heat solver.
+
+This module is shared by the CPU oracle, the tests and the benchmark.  It only
+*generates inputs*: boundary-node coordinates of the domains, forcing
+functions, manufactured solutions and their data.  It holds none of the
+method's arithmetic (no kernels, no quadrature, no derivatives, no trees).
+
+Domains follow the paper's setting (Section 2, a bounded multiply connected
+domain Omega with outer boundary Gamma_0 and holes Gamma_1..Gamma_m, each curve
+parametrised on [0, 2*pi) and sampled at N equispaced parameter values,
+Section 3.2).  Orientation convention used throughout the library: the outer
+curve runs counter-clockwise, holes run clockwise, so that the right-hand
+normal (y2', -y1')/|y'| points out of Omega.
+
+Workloads (sizes in the docstrings of each generator):
+  * ``disk_with_hole``   : unit disk minus a circle of radius 0.3 at (0.2, 0),
+                            128 nodes per curve, uniform level-4 tree, 4x4
+                            Gauss-Legendre nodes per leaf, dt = alpha^2 = 1e-2,
+                            manufactured solution u = exp(-t) sin(pi x) cos(pi y).
+  * ``starfish_domain``  : unit disk minus 5 five-armed starfish holes
+                            r(t) = 0.12 (1 + 0.3 cos 5t), centres drawn with a
+                            seed so that curves keep a gap >= 0.05, 1024 nodes
+                            per curve; forcing = sum of 20 Gaussians (widths
+                            0.02-0.1); adaptive tree to level 8 with 8x8 nodes
+                            per leaf; dt = alpha^2 = 1e-3.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+TWO_PI = 2.0 * math.pi
+
+
+def curve_params(n: int) -> np.ndarray:
+    """Equispaced parameter values t_n = 2 pi n / N, n = 0..N-1 (Section 3.2)."""
+    return TWO_PI * np.arange(n, dtype=np.float64) / n
+
+
+def circle_nodes(center, radius: float, n: int, clockwise: bool) -> np.ndarray:
+    """Nodes of a circle, shape (n, 2)."""
+    t = curve_params(n)
+    s = -1.0 if clockwise else 1.0
+    return np.stack([center[0] + radius * np.cos(t), center[1] + s * radius * np.sin(t)], axis=1)
+
+
+def starfish_nodes(center, r0: float, eps: float, arms: int, n: int, clockwise: bool,
+                   phase: float = 0.0) -> np.ndarray:
+    """Nodes of r(t) = r0 (1 + eps cos(arms (t - phase))), shape (n, 2)."""
+    t = curve_params(n)
+    r = r0 * (1.0 + eps * np.cos(arms * (t - phase)))
+    s = -1.0 if clockwise else 1.0
+    return np.stack([center[0] + r * np.cos(t), center[1] + s * r * np.sin(t)], axis=1)
+
+
+@dataclass
+class GaussianForcing:
+    """F(x) = sum_i A_i exp(-|x - c_i|^2 / (2 s_i^2)), time independent."""
+    amp: np.ndarray
+    width: np.ndarray
+    center: np.ndarray  # (n, 2)
+
+    def __call__(self, xy: np.ndarray) -> np.ndarray:
+        xy = np.asarray(xy, dtype=np.float64)
+        out = np.zeros(xy.shape[0])
+        for a, s, c in zip(self.amp, self.width, self.center):
+            d2 = (xy[:, 0] - c[0]) ** 2 + (xy[:, 1] - c[1]) ** 2
+            out += a * np.exp(-d2 / (2.0 * s * s))
+        return out
+
+
+def gaussian_forcing(seed: int = 3, n: int = 20) -> GaussianForcing:
+    """20 Gaussians, amplitudes U[-1,1], widths U[0.02,0.1], centres uniform in the unit disk."""
+    rng = np.random.default_rng(seed)
+    amp = rng.uniform(-1.0, 1.0, n)
+    width = rng.uniform(0.02, 0.1, n)
+    rad = np.sqrt(rng.uniform(0.0, 1.0, n))
+    ang = rng.uniform(0.0, TWO_PI, n)
+    center = np.stack([rad * np.cos(ang), rad * np.sin(ang)], axis=1)
+    return GaussianForcing(amp, width, center)
+
+
+class Manufactured:
+    """u = exp(-t) sin(pi x) cos(pi y);  u_t - Lap u = F = (2 pi^2 - 1) u;  f = u on Gamma."""
+
+    @staticmethod
+    def u(t: float, xy: np.ndarray) -> np.ndarray:
+        xy = np.asarray(xy, dtype=np.float64)
+        return math.exp(-t) * np.sin(math.pi * xy[:, 0]) * np.cos(math.pi * xy[:, 1])
+
+    @staticmethod
+    def F(t: float, xy: np.ndarray) -> np.ndarray:
+        return (2.0 * math.pi ** 2 - 1.0) * Manufactured.u(t, xy)
+
+
+@dataclass
+class Workload:
+    name: str
+    curves: list                      # list of (N_k, 2) float64 arrays, curve 0 = outer
+    box: tuple                        # (xmin, ymin, width) of the square D
+    q: int                            # Gauss-Legendre nodes per leaf side
+    min_level: int
+    max_level: int
+    refine_tol: float                 # absolute interpolation-error tolerance on F (inf = uniform)
+    dt: float
+    alpha: float                      # screening length, alpha^2 = dt for IMEX Euler
+    steps: int
+    p: int                            # multipole order
+    forcing: object = None            # callable F(xy) (time independent) or None
+    manufactured: bool = False
+    ext_const: list = field(default_factory=list)  # exterior constants C_k per curve
+
+    @property
+    def n_gamma(self) -> int:
+        return int(sum(c.shape[0] for c in self.curves))
+
+
+def disk_with_hole(n_per_curve: int = 128, level: int = 4, q: int = 4, dt: float = 1e-2,
+                   steps: int = 10, p: int = 20) -> Workload:
+    """Unit disk minus the circle r = 0.3 centred at (0.2, 0): N_Gamma = 2 x 128, uniform
+    level-4 tree on [-1,1]^2 with 4x4 nodes per leaf (N_D = 4096), dt = alpha^2 = 1e-2."""
+    outer = circle_nodes((0.0, 0.0), 1.0, n_per_curve, clockwise=False)
+    hole = circle_nodes((0.2, 0.0), 0.3, n_per_curve, clockwise=True)
+    return Workload("disk_with_hole", [outer, hole], (-1.0, -1.0, 2.0), q, level, level,
+                    math.inf, dt, math.sqrt(dt), steps, p, None, True, [0.0, 0.0])
+
+
+def starfish_centres(seed: int = 2, n_holes: int = 5, r_max: float = 0.12 * 1.3,
+                     gap: float = 0.05, outer_radius: float = 1.0):
+    """Rejection-sample hole centres so that the bounding circles of the holes keep a gap
+    >= `gap` from each other and from the outer circle (hence so do the curves)."""
+    rng = np.random.default_rng(seed)
+    centres = []
+    lim = outer_radius - r_max - gap
+    while len(centres) < n_holes:
+        c = rng.uniform(-lim, lim, 2)
+        if np.hypot(c[0], c[1]) > lim:
+            continue
+        if all(np.hypot(c[0] - d[0], c[1] - d[1]) >= 2 * r_max + gap for d in centres):
+            centres.append(c)
+    return np.array(centres)
+
+
+# Absolute refinement tolerance for the starfish workload's Gaussian forcing: with 8x8 nodes
+# per leaf, min level 4 and max level 8 it gives an adaptive tree of 4027 leaves
+# (257,728 volume nodes, leaves on levels 4..8); the closest refinement decision is
+# 4e-4 (relative) away from the tolerance, so trees built in any FP64 arithmetic agree.
+STARFISH_REFINE_TOL = 3.0e-10
+
+
+def starfish_domain(n_per_curve: int = 1024, n_holes: int = 5, seed: int = 2, q: int = 8,
+                    min_level: int = 4, max_level: int = 8, refine_tol: float = STARFISH_REFINE_TOL,
+                    dt: float = 1e-3, steps: int = 100, p: int = 20,
+                    forcing_seed: int = 3) -> Workload:
+    """Radius-1 disk minus 5 starfish holes r(t) = 0.12 (1 + 0.3 cos 5t) (clockwise), 1024
+    nodes per curve (N_Gamma = 6144); Gaussian-sum forcing; adaptive tree (8x8 per leaf);
+    dt = alpha^2 = 1e-3; f = 0 on every curve; exterior constants C_k = 0."""
+    outer = circle_nodes((0.0, 0.0), 1.0, n_per_curve, clockwise=False)
+    cs = starfish_centres(seed, n_holes)
+    holes = [starfish_nodes(c, 0.12, 0.3, 5, n_per_curve, clockwise=True) for c in cs]
+    return Workload("starfish_domain", [outer] + holes, (-1.0, -1.0, 2.0), q, min_level,
+                    max_level, refine_tol, dt, math.sqrt(dt), steps, p,
+                    gaussian_forcing(forcing_seed), False, [0.0] * (n_holes + 1))

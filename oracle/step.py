@@ -1,0 +1,76 @@
+"""One IMEX (backward) Euler step of the heat equation (Section 2):
+    u^{N+1} - alpha^2 Lap u^{N+1} = B = u^N + dt F^N  in Omega,  alpha^2 = dt,
+    u^{N+1} = f(t_{N+1}) on Gamma,
+solved as U = U^p + U^h (Section 2):
+  1. B~ = u^N + dt F^N at volume nodes in Omega; outside Omega the extension
+     (Section 3.1): the constant C_k of the curve whose exterior holds the node
+     plus dt F^N ("const"), or caller-supplied values ("array");
+  2. U~^p = volume potential of B~ at the volume nodes (oracle.volume);
+  3. U^p on Gamma by leaf interpolation (Section 3.1);
+  4. g = f - U^p on Gamma; solve A sigma = -2 alpha^2 g (oracle.bie);
+  5. U^h at volume nodes in Omega (oracle.bie.dlp_eval);
+  6. u^{N+1} = U~^p + U^h in Omega; outside Omega u^{N+1} = C_k ("const") or
+     U~^p ("array").
+The volume operator is passed in as a callable so that uniform trees can use
+the dense cached operator and adaptive trees the direct sum.
+"""
+import numpy as np
+
+from . import bie
+
+
+class Problem:
+    def __init__(self, curves, tree, alpha, dt, info, bnd_leaf, A, ext_mode="const",
+                 ext_const=None, volume_op=None, gmres_tol=1e-10, use_lu=False):
+        self.curves = curves
+        self.tree = tree
+        self.alpha = alpha
+        self.dt = dt
+        self.info = info                       # geometry.classify(curves, tree.nodes())
+        self.bnd_leaf = bnd_leaf               # leaf index of every boundary node
+        self.A = A                             # dense Nystrom matrix
+        self.ext_mode = ext_mode
+        self.ext_const = ext_const
+        self.volume_op = volume_op             # callable B~ (N_D,) -> U~^p (N_D,)
+        self.gmres_tol = gmres_tol
+        self.use_lu = use_lu
+        self.nodes = tree.nodes()
+        self.bnodes = np.concatenate([c.nodes for c in curves])
+        self.inside = info.region == -1
+
+
+def heat_step(pb: Problem, u, F, f_next, b_ext=None, sigma0=None):
+    """Returns (u_next, sigma, gmres_iterations)."""
+    region = pb.info.region
+    B = u + pb.dt * F
+    out = ~pb.inside
+    if pb.ext_mode == "const":
+        B[out] = np.asarray(pb.ext_const)[region[out]] + pb.dt * F[out]
+    else:
+        B[out] = b_ext[out]
+    Up = pb.volume_op(B)
+    from . import volume
+    Ug = volume.interpolate(pb.tree.leaf_array(), Up, pb.tree.q, pb.bnodes, pb.bnd_leaf)
+    g = f_next - Ug
+    rhs = -2.0 * pb.alpha ** 2 * g
+    if pb.use_lu:
+        sigma = np.linalg.solve(pb.A, rhs)
+        its = 0
+    else:
+        sigma, its, _ = bie.gmres(pb.A, rhs, sigma0, pb.gmres_tol)
+    u_next = Up.copy()
+    idx = np.nonzero(pb.inside)[0]
+    sub_info = _subset(pb.info, idx)
+    u_next[idx] += bie.dlp_eval(pb.curves, sigma, pb.alpha, pb.nodes[idx], sub_info, pb.A @ sigma)
+    if pb.ext_mode == "const":
+        u_next[out] = np.asarray(pb.ext_const)[region[out]]
+    return u_next, sigma, its
+
+
+def _subset(info, idx):
+    class _S:
+        pass
+    s = _S()
+    s.region = info.region[idx]
+    s.proj = [info.proj[i] for i in idx]
+    return s
