@@ -1,0 +1,195 @@
+/*
+ * mh.h -- C ABI of libmh, a GB300 (sm_103a) implementation of the per-time-step
+ * modified-Helmholtz solve of Kropinski & Quaife, "Fast integral equation methods
+ * for the heat equation and the modified Helmholtz equation in two dimensions".
+ *
+ * The heat equation u_t - Lap u = F is discretised in time first (Section 2):
+ * each IMEX Euler step solves u - alpha^2 Lap u = B, alpha^2 = dt,
+ * B = u^N + dt F^N, with u = f on Gamma.  The solution is U = U^p + U^h:
+ *   U^p  volume potential of the extended B over the leaves of a quadtree
+ *        (Section 3.1, eq. volume_potential),   kernel G = K0(r/alpha)/(2 pi alpha^2);
+ *   U^h  double-layer potential (Section 2) whose density solves the second-kind
+ *        integral equation (Section 2, eq. dirichlet:inteqn), discretised by the
+ *        Alpert-corrected trapezoid rule (Section 3.2, eq. discrete_sys) and solved
+ *        by GMRES (Section 3.2).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an mh_status; mh_last_error(ctx) gives a message.
+ *     No call aborts, traps or exits the process.
+ *   - "_dev" pointers are device pointers on the context's device, "_host"
+ *     pointers are host pointers.  All array arguments are owned by the caller
+ *     and are only read or written during the call (asynchronously on the
+ *     context's stream for device arrays; host arrays are done when the call
+ *     returns).  Opaque objects (mh_ctx, mh_boundary, mh_tree, mh_problem)
+ *     own their device memory and free it in the matching *_destroy.
+ *   - Doubles are IEEE binary64.  Point arrays are interleaved (x, y) pairs.
+ *   - Boundary curves: curve 0 is the outer boundary Gamma_0 (counter-clockwise),
+ *     curves 1.. are holes (clockwise); curve k is sampled at N_k (even) equispaced
+ *     parameter values t_n = 2 pi n / N_k (Section 3.2).  The right-hand normal
+ *     (y2', -y1')/|y'| is then the outward normal of Omega.
+ *   - Volume nodes: each leaf carries q x q Gauss-Legendre nodes, node j = iy*q + ix,
+ *     leaves in Morton order of their lower-left corner (leaf-major node arrays).
+ */
+#ifndef MH_H
+#define MH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MH_OK = 0,
+    MH_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported option */
+    MH_ERR_GEOMETRY = 2,      /* wrong curve orientation, odd node count, points off the tree */
+    MH_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has the CUDA error string) */
+    MH_ERR_OOM = 4,           /* device allocation failed */
+    MH_ERR_NOT_CONVERGED = 5, /* GMRES hit max_iter before the tolerance */
+    MH_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+    MH_ERR_NUMERIC = 7,       /* non-finite value detected */
+    MH_ERR_CALLBACK = 8       /* the user field callback returned non-zero */
+} mh_status;
+
+typedef enum {
+    MH_PREC_FP64 = 0,   /* every step in binary64 */
+    MH_PREC_MIXED = 1   /* binary32 inner products/contractions, binary64 Krylov
+                           orthogonalisation, residuals and refinement */
+} mh_precision;
+
+typedef struct mh_ctx mh_ctx;
+typedef struct mh_boundary mh_boundary;
+typedef struct mh_tree mh_tree;
+typedef struct mh_problem mh_problem;
+
+typedef struct {
+    int iterations;        /* total Krylov iterations (all refinement sweeps) */
+    int refinements;       /* FP64 refinement sweeps (mixed precision), else 0 */
+    double rel_residual;   /* final ||b - A x|| / ||b|| computed in binary64 */
+    int converged;         /* 1 if rel_residual <= tol */
+} mh_gmres_info;
+
+typedef struct {
+    int gmres_iterations;
+    double gmres_rel_residual;
+} mh_step_info;
+
+/* Field callback used by mh_tree_build: evaluate the user's F at n points
+ * xy_host[2n] (host memory) into out_host[n]; return 0 on success. */
+typedef int (*mh_field_fn)(const double* xy_host, int64_t n, double* out_host, void* user);
+
+/* ---- context --------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`, issuing all work on `stream`
+ * (a cudaStream_t, NULL = the legacy default stream). */
+mh_status mh_create(int device, void* stream, mh_ctx** out);
+mh_status mh_destroy(mh_ctx* ctx);
+/* Message describing the last error on ctx (valid until the next call on ctx). */
+const char* mh_last_error(const mh_ctx* ctx);
+/* Number of kernels this context has launched so far (for launch accounting). */
+int64_t mh_kernel_launches(const mh_ctx* ctx);
+
+/* ---- boundary (Section 3.2) -------------------------------------------------------- */
+
+/* Build the boundary from node coordinates xy_host[2 N_Gamma] (curves concatenated,
+ * n_nodes_host[k] = N_k, each even and >= 2*alpert_order + 2).  y', y'' at the nodes
+ * are computed pseudospectrally (Section 3.2).  alpert_order in 1..10 selects the
+ * l-point log-singular correction (window a = l); 0 selects the plain trapezoid rule
+ * with the diagonal limit -kappa/2 of d/dnu K0 (Section 2).
+ * Errors: MH_ERR_GEOMETRY if the outer curve is not counter-clockwise or a hole is
+ * not clockwise, MH_ERR_INVALID_ARG for bad sizes. */
+mh_status mh_boundary_create(mh_ctx* ctx, int n_curves, const int32_t* n_nodes_host,
+                             const double* xy_host, int alpert_order, mh_boundary** out);
+mh_status mh_boundary_destroy(mh_boundary* bnd);
+mh_status mh_boundary_size(const mh_boundary* bnd, int64_t* n_gamma);
+/* Per node: x, y, x', y', x'', y'', |y'|, K(x,x) diagonal limit (8 doubles per node). */
+mh_status mh_boundary_geometry(mh_ctx* ctx, const mh_boundary* bnd, double* out_host);
+
+/* ---- quadtree (Section 3.1) --------------------------------------------------------- */
+
+/* Build the quadtree on D = [box[0], box[0]+box[2]] x [box[1], box[1]+box[2]] on the
+ * device: leaves are split level by level while level < min_level or, if refine_fn is
+ * not NULL, while max over the four children's nodes of |F - P_b F| > refine_tol
+ * (P_b F = q x q tensor interpolant of F on the box's own nodes, Section 3.1); then
+ * the tree is 2:1 balanced (touching leaves differ by at most one level) and the
+ * U, V, W, X interaction lists are formed.  q in 2..16, 0 <= min_level <= max_level <= 10. */
+mh_status mh_tree_build(mh_ctx* ctx, const double* box3_host, int q, int min_level, int max_level,
+                        mh_field_fn refine_fn, void* user, double refine_tol, mh_tree** out);
+mh_status mh_tree_destroy(mh_tree* tree);
+mh_status mh_tree_size(const mh_tree* tree, int64_t* n_leaves, int64_t* n_boxes, int64_t* n_nodes);
+/* Leaves (level, ix, iy) in node order, 3 int32 each. */
+mh_status mh_tree_leaves(mh_ctx* ctx, const mh_tree* tree, int32_t* out_host);
+/* All boxes (level, ix, iy) ordered by level then Morton key, 3 int32 each. */
+mh_status mh_tree_boxes(mh_ctx* ctx, const mh_tree* tree, int32_t* out_host);
+/* Volume node coordinates, 2 doubles per node, into device memory. */
+mh_status mh_tree_nodes(mh_ctx* ctx, const mh_tree* tree, double* out_dev);
+/* Interaction list `which` (0 = U, 1 = V, 2 = W, 3 = X) in CSR form over all boxes
+ * (box ids as in mh_tree_boxes): offsets_host[n_boxes + 1]; items_host may be NULL to
+ * query offsets only.  Item lists are sorted by box id. */
+mh_status mh_tree_list(mh_ctx* ctx, const mh_tree* tree, int which, int32_t* offsets_host,
+                       int32_t* items_host);
+
+/* ---- volume potential (Section 3.1) ------------------------------------------------ */
+
+/* up_dev[i] = sum over leaves of int_leaf G(x_i - y) P(y) dA at every volume node x_i,
+ * P = the leaf's q x q interpolant of b_dev (eq. volume_potential with the leaf
+ * polynomial of Section 3.1), evaluated by near-field tables on adjacent leaves and a
+ * multipole method of order p (K_n multipoles, I_n locals) for the rest.
+ * b_dev, up_dev: n_nodes doubles (device).  p in 1..40. */
+mh_status mh_volume_potential(mh_ctx* ctx, mh_tree* tree, double alpha, int p, const double* b_dev,
+                              double* up_dev, mh_precision prec);
+
+/* ---- double layer and BIE (Section 2 and 3.2) --------------------------------------- */
+
+/* targets_dev == NULL: out_dev = A sigma, the discretised operator of
+ *   eq. discrete_sys (sigma + (1/pi) Q[K sigma], K(y,x) = (1/alpha) K1(|y-x|/alpha)
+ *   (y-x).n_y/|y-x|), n_targets ignored, out has N_Gamma entries.
+ * targets_dev != NULL: out_dev[i] = U^h(x_i) = (1/(2 pi alpha^2)) int d/dnu_y K0 sigma ds
+ *   at n_targets points (2 doubles each) assumed inside Omega, with the near-boundary
+ *   rule: 16x upsampled density for targets within 5 h_s of a curve, interpolation
+ *   along the normal within h_s/4. */
+mh_status mh_double_layer_apply(mh_ctx* ctx, mh_boundary* bnd, double alpha, const double* sigma_dev,
+                                const double* targets_dev, int64_t n_targets, double* out_dev,
+                                mh_precision prec);
+
+/* Solve A sigma = rhs (eq. discrete_sys) by unrestarted GMRES (Section 3.2), stopping
+ * when ||rhs - A sigma|| <= tol ||rhs|| (the paper uses tol = 1e-10, Section 4).
+ * sigma_dev: in = initial guess, out = solution.  MH_PREC_MIXED runs binary32-operator
+ * GMRES inside binary64 iterative refinement.  Returns MH_ERR_NOT_CONVERGED (with
+ * sigma holding the best iterate) if max_iter iterations do not reach tol. */
+mh_status mh_gmres_solve(mh_ctx* ctx, mh_boundary* bnd, double alpha, const double* rhs_dev,
+                         double* sigma_dev, double tol, int max_iter, mh_precision prec,
+                         mh_gmres_info* info);
+
+/* ---- heat step (Section 2) ---------------------------------------------------------- */
+
+typedef enum { MH_EXT_CONST = 0, MH_EXT_ARRAY = 1 } mh_ext_mode;
+
+/* Bind a tree and a boundary into a time-stepping problem with step dt (alpha^2 = dt,
+ * IMEX Euler) and multipole order p.  Volume nodes are classified (inside Omega or on
+ * the exterior side of curve k) and the boundary nodes located in the leaves.
+ * Exterior extension of B (Section 3.1): MH_EXT_CONST uses ext_const_host[k] + dt F
+ * outside curve k (the paper's constant extension); MH_EXT_ARRAY takes the exterior
+ * values from heat_step's b_ext_dev. */
+mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* bnd, double dt, int p,
+                            int ext_mode, const double* ext_const_host, mh_problem** out);
+mh_status mh_problem_destroy(mh_problem* prob);
+/* Region of every volume node: -1 inside Omega, k on the exterior side of curve k. */
+mh_status mh_problem_regions(mh_ctx* ctx, const mh_problem* prob, int32_t* region_host);
+
+/* One IMEX Euler step u^N -> u^{N+1} (Section 2):
+ *   B = u + dt F (inside), extension outside; U^p = volume potential of B;
+ *   g = f_next - U^p on Gamma (leaf interpolation, Section 3.1); solve
+ *   A sigma = -2 alpha^2 g (GMRES, tolerance gmres_tol); u_next = U^p + U^h inside
+ *   Omega, = ext_const (CONST) or U^p (ARRAY) outside.
+ * u_dev, F_dev, b_ext_dev, u_next_dev: n_nodes doubles; f_next_dev, sigma_dev: N_Gamma
+ * doubles (sigma: in = warm start, out = density).  u_dev and u_next_dev may alias. */
+mh_status heat_step(mh_ctx* ctx, mh_problem* prob, const double* u_dev, const double* F_dev,
+                    const double* f_next_dev, const double* b_ext_dev, double* u_next_dev,
+                    double* sigma_dev, double gmres_tol, mh_precision prec, mh_step_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MH_H */

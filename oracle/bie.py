@@ -52,11 +52,13 @@ def kernel(yx, ny, alpha, x):
     return k1(r / alpha) / alpha * (d[..., 0] * ny[..., 0] + d[..., 1] * ny[..., 1]) / r
 
 
-def nystrom_matrix(curves, alpha: float, alpert_order=_alpert.DEFAULT_ORDER) -> np.ndarray:
-    """Dense N_Gamma x N_Gamma matrix of the operator A (eq. discrete_sys)."""
+def nystrom_matrix(curves, alpha: float, alpert_order=_alpert.DEFAULT_ORDER, rows=None) -> np.ndarray:
+    """Dense N_Gamma x N_Gamma matrix of the operator A (eq. discrete_sys), or only the
+    listed global row indices (array of shape (len(rows), N_Gamma))."""
     offs = np.cumsum([0] + [c.n for c in curves])
     ntot = int(offs[-1])
-    A = np.zeros((ntot, ntot))
+    wanted = None if rows is None else {int(r): i for i, r in enumerate(rows)}
+    A = np.zeros((ntot if rows is None else len(rows), ntot))
     allnodes = np.concatenate([c.nodes for c in curves])
     allnorm = np.concatenate([c.normal for c in curves])
     allw = np.concatenate([c.speed * c.h for c in curves])
@@ -65,6 +67,8 @@ def nystrom_matrix(curves, alpha: float, alpert_order=_alpert.DEFAULT_ORDER) -> 
     for k, c in enumerate(curves):
         for jj in range(c.n):
             j = offs[k] + jj
+            if wanted is not None and j not in wanted:
+                continue
             x = c.nodes[jj]
             d = allnodes - x
             r = np.hypot(d[:, 0], d[:, 1])
@@ -86,8 +90,9 @@ def nystrom_matrix(curves, alpha: float, alpert_order=_alpert.DEFAULT_ORDER) -> 
                 coef = np.concatenate([wm, wm]) * c.h * sp * kv            # (2l,)
                 interp = trig_kernel(tt[:, None] - c.t[None, :], c.n)     # (2l, N)
                 row[offs[k]:offs[k + 1]] += coef @ interp
-            A[j] = row / math.pi
-            A[j, j] += 1.0
+            r_out = j if wanted is None else wanted[j]
+            A[r_out] = row / math.pi
+            A[r_out, j] += 1.0
     return A
 
 

@@ -1,0 +1,257 @@
+"""Python binding of libmh (include/mh.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module passes device
+pointers of torch tensors (torch is used for device memory and streams), sizes
+and host arrays through ctypes, and raises MHError on a non-zero status.
+There is no fallback: if libmh.so is missing the import fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libmh.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with `python -m paper_1007_5335_gb300.build`")
+
+_lib = ctypes.CDLL(_LIB_PATH)
+
+MH_PREC_FP64 = 0
+MH_PREC_MIXED = 1
+MH_EXT_CONST = 0
+MH_EXT_ARRAY = 1
+STATUS = {0: "MH_OK", 1: "MH_ERR_INVALID_ARG", 2: "MH_ERR_GEOMETRY", 3: "MH_ERR_CUDA", 4: "MH_ERR_OOM",
+          5: "MH_ERR_NOT_CONVERGED", 6: "MH_ERR_TIMEOUT", 7: "MH_ERR_NUMERIC", 8: "MH_ERR_CALLBACK"}
+LISTS = {"U": 0, "V": 1, "W": 2, "X": 3}
+
+_p = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_d = ctypes.c_double
+
+
+class GmresInfo(ctypes.Structure):
+    _fields_ = [("iterations", _i), ("refinements", _i), ("rel_residual", _d), ("converged", _i)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("gmres_iterations", _i), ("gmres_rel_residual", _d)]
+
+
+FIELD_FN = ctypes.CFUNCTYPE(_i, ctypes.POINTER(_d), _i64, ctypes.POINTER(_d), _p)
+
+_SIGS = {
+    "mh_create": [_i, _p, ctypes.POINTER(_p)],
+    "mh_destroy": [_p],
+    "mh_kernel_launches": [_p],
+    "mh_boundary_create": [_p, _i, _p, _p, _i, ctypes.POINTER(_p)],
+    "mh_boundary_destroy": [_p],
+    "mh_boundary_size": [_p, ctypes.POINTER(_i64)],
+    "mh_boundary_geometry": [_p, _p, _p],
+    "mh_tree_build": [_p, _p, _i, _i, _i, FIELD_FN, _p, _d, ctypes.POINTER(_p)],
+    "mh_tree_destroy": [_p],
+    "mh_tree_size": [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
+    "mh_tree_leaves": [_p, _p, _p],
+    "mh_tree_boxes": [_p, _p, _p],
+    "mh_tree_nodes": [_p, _p, _p],
+    "mh_tree_list": [_p, _p, _i, _p, _p],
+    "mh_volume_potential": [_p, _p, _d, _i, _p, _p, _i],
+    "mh_double_layer_apply": [_p, _p, _d, _p, _p, _i64, _p, _i],
+    "mh_gmres_solve": [_p, _p, _d, _p, _p, _d, _i, _i, ctypes.POINTER(GmresInfo)],
+    "mh_problem_create": [_p, _p, _p, _d, _i, _i, _p, ctypes.POINTER(_p)],
+    "mh_problem_destroy": [_p],
+    "mh_problem_regions": [_p, _p, _p],
+    "heat_step": [_p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int64 if _name == "mh_kernel_launches" else _i
+_lib.mh_last_error.argtypes = [_p]
+_lib.mh_last_error.restype = ctypes.c_char_p
+
+
+class MHError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    """Device pointer of a contiguous CUDA float64 tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype.itemsize != 8 or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor of 8-byte elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """mh_create / mh_destroy.  All work is issued on torch's current stream."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.device = device
+        stream = torch.cuda.current_stream(device).cuda_stream
+        h = _p()
+        st = _lib.mh_create(device, _p(stream), ctypes.byref(h))
+        if st:
+            raise MHError(st, "mh_create failed")
+        self.h = h
+
+    def check(self, st):
+        if st:
+            raise MHError(st, _lib.mh_last_error(self.h).decode())
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.mh_kernel_launches(self.h))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.mh_destroy(self.h)
+            self.h = None
+
+
+class Boundary:
+    """mh_boundary_create: curves = list of (N_k, 2) arrays (outer CCW first, holes CW)."""
+
+    def __init__(self, ctx: Context, curves, alpert_order: int = 8):
+        self.ctx = ctx
+        nn = np.array([c.shape[0] for c in curves], dtype=np.int32)
+        xy = np.ascontiguousarray(np.concatenate(curves), dtype=np.float64)
+        h = _p()
+        ctx.check(_lib.mh_boundary_create(ctx.h, len(curves), nn.ctypes.data_as(_p), xy.ctypes.data_as(_p),
+                                          alpert_order, ctypes.byref(h)))
+        self.h = h
+        self.n = int(xy.shape[0])
+        self.n_curves = len(curves)
+
+    def geometry(self) -> np.ndarray:
+        out = np.zeros((self.n, 8))
+        self.ctx.check(_lib.mh_boundary_geometry(self.ctx.h, self.h, out.ctypes.data_as(_p)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.mh_boundary_destroy(self.h)
+            self.h = None
+
+
+class Tree:
+    """mh_tree_build.  refine_fn(xy: (n,2) ndarray) -> (n,) ndarray evaluates F on the host."""
+
+    def __init__(self, ctx: Context, box, q: int, min_level: int, max_level: int, refine_fn=None,
+                 refine_tol: float = float("inf")):
+        self.ctx = ctx
+        self._err = None
+
+        def cb(xy_p, n, out_p, user):
+            try:
+                xy = np.ctypeslib.as_array(xy_p, shape=(n, 2))
+                out = np.ctypeslib.as_array(out_p, shape=(n,))
+                out[:] = refine_fn(xy)
+                return 0
+            except Exception as e:  # reported through the status
+                self._err = e
+                return 1
+
+        self._cb = FIELD_FN(cb) if refine_fn is not None else FIELD_FN()
+        box = np.ascontiguousarray(box, dtype=np.float64)
+        h = _p()
+        ctx.check(_lib.mh_tree_build(ctx.h, box.ctypes.data_as(_p), q, min_level, max_level, self._cb, None,
+                                     float(refine_tol), ctypes.byref(h)))
+        self.h = h
+        nl, nb, nn = _i64(), _i64(), _i64()
+        _lib.mh_tree_size(h, ctypes.byref(nl), ctypes.byref(nb), ctypes.byref(nn))
+        self.n_leaves, self.n_boxes, self.n_nodes = nl.value, nb.value, nn.value
+        self.q = q
+
+    def leaves(self) -> np.ndarray:
+        out = np.zeros((self.n_leaves, 3), dtype=np.int32)
+        self.ctx.check(_lib.mh_tree_leaves(self.ctx.h, self.h, out.ctypes.data_as(_p)))
+        return out
+
+    def boxes(self) -> np.ndarray:
+        out = np.zeros((self.n_boxes, 3), dtype=np.int32)
+        self.ctx.check(_lib.mh_tree_boxes(self.ctx.h, self.h, out.ctypes.data_as(_p)))
+        return out
+
+    def nodes(self):
+        import torch
+        out = torch.empty((self.n_nodes, 2), dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        self.ctx.check(_lib.mh_tree_nodes(self.ctx.h, self.h, _ptr(out)))
+        return out
+
+    def list(self, which: str):
+        offs = np.zeros(self.n_boxes + 1, dtype=np.int32)
+        self.ctx.check(_lib.mh_tree_list(self.ctx.h, self.h, LISTS[which], offs.ctypes.data_as(_p), None))
+        items = np.zeros(max(int(offs[-1]), 1), dtype=np.int32)
+        self.ctx.check(_lib.mh_tree_list(self.ctx.h, self.h, LISTS[which], offs.ctypes.data_as(_p),
+                                         items.ctypes.data_as(_p)))
+        return offs, items[:offs[-1]]
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.mh_tree_destroy(self.h)
+            self.h = None
+
+
+def mh_volume_potential(ctx: Context, tree: Tree, alpha: float, p: int, b, out, prec: int = MH_PREC_FP64):
+    ctx.check(_lib.mh_volume_potential(ctx.h, tree.h, float(alpha), int(p), _ptr(b), _ptr(out), int(prec)))
+    return out
+
+
+def mh_double_layer_apply(ctx: Context, bnd: Boundary, alpha: float, sigma, out, targets=None,
+                          prec: int = MH_PREC_FP64):
+    n_t = 0 if targets is None else int(targets.shape[0])
+    ctx.check(_lib.mh_double_layer_apply(ctx.h, bnd.h, float(alpha), _ptr(sigma), _ptr(targets), n_t, _ptr(out),
+                                         int(prec)))
+    return out
+
+
+def mh_gmres_solve(ctx: Context, bnd: Boundary, alpha: float, rhs, sigma, tol: float = 1e-10,
+                   max_iter: int = 100, prec: int = MH_PREC_FP64) -> GmresInfo:
+    info = GmresInfo()
+    ctx.check(_lib.mh_gmres_solve(ctx.h, bnd.h, float(alpha), _ptr(rhs), _ptr(sigma), float(tol), int(max_iter),
+                                  int(prec), ctypes.byref(info)))
+    return info
+
+
+class Problem:
+    """mh_problem_create: tree + boundary + dt (alpha^2 = dt) + multipole order p."""
+
+    def __init__(self, ctx: Context, tree: Tree, bnd: Boundary, dt: float, p: int, ext_mode: int = MH_EXT_CONST,
+                 ext_const=None):
+        self.ctx, self.tree, self.bnd = ctx, tree, bnd
+        ec = np.ascontiguousarray(ext_const if ext_const is not None else np.zeros(bnd.n_curves), dtype=np.float64)
+        h = _p()
+        ctx.check(_lib.mh_problem_create(ctx.h, tree.h, bnd.h, float(dt), int(p), int(ext_mode),
+                                         ec.ctypes.data_as(_p), ctypes.byref(h)))
+        self.h = h
+        self.dt = dt
+        self.alpha = float(np.sqrt(dt))
+
+    def regions(self) -> np.ndarray:
+        out = np.zeros(self.tree.n_nodes, dtype=np.int32)
+        self.ctx.check(_lib.mh_problem_regions(self.ctx.h, self.h, out.ctypes.data_as(_p)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.mh_problem_destroy(self.h)
+            self.h = None
+
+
+def heat_step(ctx: Context, prob: Problem, u, F, f_next, u_next, sigma, b_ext=None, gmres_tol: float = 1e-10,
+              prec: int = MH_PREC_FP64) -> StepInfo:
+    info = StepInfo()
+    ctx.check(_lib.heat_step(ctx.h, prob.h, _ptr(u), _ptr(F), _ptr(f_next), _ptr(b_ext), _ptr(u_next), _ptr(sigma),
+                             float(gmres_tol), int(prec), ctypes.byref(info)))
+    return info
+
+
+def library_path() -> str:
+    return _LIB_PATH

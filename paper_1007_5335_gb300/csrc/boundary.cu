@@ -1,0 +1,1119 @@
+// Boundary part of the method: geometry (Section 3.2, pseudospectral normals), the
+// Nystrom operator of eq. discrete_sys with the Alpert log-singular correction and
+// Fourier interpolation (Section 3.2), its application, GMRES (Section 3.2), and the
+// off-surface double-layer potential U^h (Section 2) with the near-boundary rules.
+#include <algorithm>
+#include <cmath>
+
+#include "alpert_rule.h"
+#include "bessel.cuh"
+#include "mh_internal.cuh"
+
+namespace {
+
+constexpr int UPSAMPLE = 16;        // fine grid for targets within 5 h_s of a curve
+constexpr double NEAR_NODE = 6.0;   // project on the curve when the nearest node is within 6 h*
+constexpr double NEAR_FINE = 5.0;   // d < 5 h_s: upsampled rule
+constexpr double NEAR_LINE = 0.25;  // d < h_s/4: interpolation along the normal
+
+struct AlpertRule {
+    int l, a;
+    double x[MH_ALPERT_LMAX], w[MH_ALPERT_LMAX];
+};
+
+// Modes m = 0..N/2 of curve k start at coef index off[k]/2 + k (4 doubles per mode).
+__device__ __forceinline__ int64_t coef_base(const int32_t* off, int k) { return (int64_t)off[k] / 2 + k; }
+
+// Warp sum; the result is broadcast from lane 0 so that every lane holds the same bits
+// (butterfly sums can differ in the last bit between lanes, and callers branch on them).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// Fourier coefficients c_m = (1/N) sum_n y_n e^{-2 pi i m n / N}, m = 0..N/2, of the
+// node coordinates (x and y), exact twiddles through the integer m n mod N.
+__global__ void k_fourier_xy(const double* __restrict__ xy, const int32_t* __restrict__ nn,
+                             const int32_t* __restrict__ off, int ncurves, int64_t total, double* coef) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int k = 0;
+    while (k + 1 < ncurves && g >= coef_base(off, k + 1)) ++k;
+    const int N = nn[k];
+    const int m = (int)(g - coef_base(off, k));
+    const double* p = xy + 2 * (int64_t)off[k];
+    double xr = 0, xi = 0, yr = 0, yi = 0;
+    for (int n = 0; n < N; ++n) {
+        int r = (int)(((int64_t)m * n) % N);
+        double s, c;
+        sincospi(2.0 * r / N, &s, &c);
+        xr += p[2 * n] * c;
+        xi -= p[2 * n] * s;
+        yr += p[2 * n + 1] * c;
+        yi -= p[2 * n + 1] * s;
+    }
+    double inv = 1.0 / N;
+    coef[4 * g + 0] = xr * inv;
+    coef[4 * g + 1] = xi * inv;
+    coef[4 * g + 2] = yr * inv;
+    coef[4 * g + 3] = yi * inv;
+}
+
+// Contribution of mode m of one coordinate (re, im) at angle with (s, c) = sin, cos(m t).
+// Accumulates value, first and second t-derivative of the trigonometric interpolant
+//   p(t) = c_0 + sum_{0<m<N/2} 2 Re(c_m e^{imt}) + c_{N/2} cos(N t / 2).
+__device__ __forceinline__ void mode_acc(int m, int N, double re, double im, double s, double c, double& v,
+                                         double& d1, double& d2) {
+    if (m == 0) {
+        v += re;
+    } else if (2 * m == N) {
+        double h = 0.5 * N;
+        v += re * c;
+        d1 -= h * re * s;
+        d2 -= h * h * re * c;
+    } else {
+        double a = 2.0 * (re * c - im * s);
+        v += a;
+        d1 += 2.0 * m * (-re * s - im * c);
+        d2 -= (double)m * m * a;
+    }
+}
+
+// Position and first two derivatives at the nodes (exact twiddles), plus |y'| and the
+// diagonal limit K(x,x) = -(y''.n)/(2|y'|^2) (Section 2).
+__global__ void k_node_geometry(const double* __restrict__ coef, const int32_t* __restrict__ nn,
+                                const int32_t* __restrict__ off, const int32_t* __restrict__ curve_of,
+                                int64_t n, double* geo) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int k = curve_of[j];
+    const int N = nn[k];
+    const int i = (int)(j - off[k]);
+    const double* c = coef + 4 * coef_base(off, k);
+    double x = 0, dx = 0, ddx = 0, y = 0, dy = 0, ddy = 0;
+    for (int m = 0; m <= N / 2; ++m) {
+        int r = (int)(((int64_t)m * i) % N);
+        double s, co;
+        sincospi(2.0 * r / N, &s, &co);
+        mode_acc(m, N, c[4 * m], c[4 * m + 1], s, co, x, dx, ddx);
+        mode_acc(m, N, c[4 * m + 2], c[4 * m + 3], s, co, y, dy, ddy);
+    }
+    double sp = sqrt(dx * dx + dy * dy);
+    double nx = dy / sp, ny = -dx / sp;
+    double* g = geo + 8 * j;
+    g[0] = x;
+    g[1] = y;
+    g[2] = dx;
+    g[3] = dy;
+    g[4] = ddx;
+    g[5] = ddy;
+    g[6] = sp;
+    g[7] = -(ddx * nx + ddy * ny) / (2.0 * sp * sp);
+}
+
+// Geometry on the 16x fine grid t_f = 2 pi f / (16 N): x, y, nx, ny, |y'|, h_f.
+__global__ void k_fine_geometry(const double* __restrict__ coef, const int32_t* __restrict__ nn,
+                                const int32_t* __restrict__ off, const int64_t* __restrict__ foff, int ncurves,
+                                int64_t nfine, double* fg) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= nfine) return;
+    int k = 0;
+    while (k + 1 < ncurves && g >= foff[k + 1]) ++k;
+    const int N = nn[k];
+    const int NF = UPSAMPLE * N;
+    const int f = (int)(g - foff[k]);
+    const double* c = coef + 4 * coef_base(off, k);
+    double x = 0, dx = 0, ddx = 0, y = 0, dy = 0, ddy = 0;
+    for (int m = 0; m <= N / 2; ++m) {
+        int r = (int)(((int64_t)m * f) % NF);
+        double s, co;
+        sincospi(2.0 * r / NF, &s, &co);
+        mode_acc(m, N, c[4 * m], c[4 * m + 1], s, co, x, dx, ddx);
+        mode_acc(m, N, c[4 * m + 2], c[4 * m + 3], s, co, y, dy, ddy);
+    }
+    double sp = sqrt(dx * dx + dy * dy);
+    double* o = fg + 6 * g;
+    o[0] = x;
+    o[1] = y;
+    o[2] = dy / sp;
+    o[3] = -dx / sp;
+    o[4] = sp;
+    o[5] = 2.0 * MH_PI / NF;
+}
+
+// Warp-cooperative evaluation of a curve (position, y', y'') at an arbitrary parameter t.
+__device__ void curve_eval_warp(const double* c, int N, double t, double out[6]) {
+    const int lane = threadIdx.x & 31;
+    double x = 0, dx = 0, ddx = 0, y = 0, dy = 0, ddy = 0;
+    for (int m = lane; m <= N / 2; m += 32) {
+        double s, co;
+        sincos(m * t, &s, &co);
+        mode_acc(m, N, c[4 * m], c[4 * m + 1], s, co, x, dx, ddx);
+        mode_acc(m, N, c[4 * m + 2], c[4 * m + 3], s, co, y, dy, ddy);
+    }
+    out[0] = warp_sum(x);
+    out[1] = warp_sum(y);
+    out[2] = warp_sum(dx);
+    out[3] = warp_sum(dy);
+    out[4] = warp_sum(ddx);
+    out[5] = warp_sum(ddy);
+}
+
+// K(y, x) = (1/alpha) K1(|y-x|/alpha) (y-x).n_y / |y-x|  (Section 3.2)
+__device__ __forceinline__ double dl_kernel(double yx, double yy, double nx, double ny, double xx, double xy,
+                                            double inv_alpha) {
+    double dx = yx - xx, dy = yy - xy;
+    double r = sqrt(dx * dx + dy * dy);
+    return mh_k1(r * inv_alpha) * inv_alpha * (dx * nx + dy * ny) / r;
+}
+
+// Trapezoid part of eq. discrete_sys (all curves), the own-curve Alpert window left
+// empty (or, with l = 0, the diagonal limit), identity on the diagonal.
+__global__ void k_assemble_trap(const double* __restrict__ geo, const int32_t* __restrict__ curve_of,
+                                const int32_t* __restrict__ nn, const int32_t* __restrict__ off, int64_t n,
+                                double inv_alpha, int a, double* A) {
+    int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (col >= n) return;
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        const double* gj = geo + 8 * j;
+        const double* gc = geo + 8 * col;
+        const int kj = curve_of[j], kc = curve_of[col];
+        const double h = 2.0 * MH_PI / nn[kc];
+        double v;
+        bool win = false;
+        if (kj == kc) {
+            int N = nn[kj];
+            int d = (int)((col - j) % N);
+            if (d < 0) d += N;
+            int circ = d < N - d ? d : N - d;
+            win = a > 0 ? circ < a : circ == 0;
+        }
+        if (win) {
+            v = (a == 0) ? gj[7] * gj[6] * h : 0.0;
+        } else {
+            double sp = gc[6];
+            v = dl_kernel(gc[0], gc[1], gc[3] / sp, -gc[2] / sp, gj[0], gj[1], inv_alpha) * sp * h;
+        }
+        A[j * n + col] = v * (1.0 / MH_PI) + (col == j ? 1.0 : 0.0);
+    }
+}
+
+// Alpert correction rows: 2l off-grid nodes t_j +- x_m h per row with geometry from the
+// trigonometric interpolant, spread onto the own curve's nodes through the periodic
+// interpolation kernel D_N(tau) = sin(N tau/2) cot(tau/2) / N (Section 3.2).
+__global__ void k_assemble_alpert(const double* __restrict__ geo, const double* __restrict__ coef,
+                                  const int32_t* __restrict__ curve_of, const int32_t* __restrict__ nn,
+                                  const int32_t* __restrict__ off, int64_t n, double inv_alpha, AlpertRule R,
+                                  double* A) {
+    __shared__ double cp[2 * MH_ALPERT_LMAX], sp_s[2 * MH_ALPERT_LMAX], sh[2 * MH_ALPERT_LMAX];
+    const int64_t j = blockIdx.x;
+    const int k = curve_of[j];
+    const int N = nn[k];
+    const int o = off[k];
+    const int jj = (int)(j - o);
+    const double h = 2.0 * MH_PI / N;
+    const double* c = coef + 4 * coef_base(off, k);
+    const double* gj = geo + 8 * j;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int p = warp; p < 2 * R.l; p += nw) {
+        const int m = p % R.l;
+        const double s = p < R.l ? 1.0 : -1.0;
+        double t = (jj + s * R.x[m]) * h;
+        double v[6];
+        curve_eval_warp(c, N, t, v);
+        if ((threadIdx.x & 31) == 0) {
+            double spd = sqrt(v[2] * v[2] + v[3] * v[3]);
+            double K = dl_kernel(v[0], v[1], v[3] / spd, -v[2] / spd, gj[0], gj[1], inv_alpha);
+            cp[p] = (1.0 / MH_PI) * h * R.w[m] * spd * K;
+            sp_s[p] = s * sinpi(R.x[m]) / N;
+            sh[p] = s * R.x[m];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double sgn = ((jj - i) & 1) ? -1.0 : 1.0;
+        double acc = 0.0;
+        for (int p = 0; p < 2 * R.l; ++p) {
+            double v = (jj - i + sh[p]) / N;
+            acc += cp[p] * sp_s[p] * cospi(v) / sinpi(v);
+        }
+        A[j * n + o + i] += sgn * acc;
+    }
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// y = A x, one warp per row, 16-byte loads (N_Gamma is even, so rows stay aligned).
+__global__ void k_gemv64(const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ y,
+                         int64_t n) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < n; row += nwarps) {
+        const double2* a = reinterpret_cast<const double2*>(A + row * n);
+        const double2* xv = reinterpret_cast<const double2*>(x);
+        double acc = 0.0;
+        for (int64_t c = lane; c < n / 2; c += 32) {
+            double2 av = __ldcs(a + c);
+            double2 xx = __ldg(xv + c);
+            acc = fma(av.x, xx.x, acc);
+            acc = fma(av.y, xx.y, acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) y[row] = acc;
+    }
+}
+
+__global__ void k_gemv32(const float* __restrict__ A, const double* __restrict__ x, double* __restrict__ y,
+                         int64_t n) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < n; row += nwarps) {
+        const float2* a = reinterpret_cast<const float2*>(A + row * n);
+        const double2* xv = reinterpret_cast<const double2*>(x);
+        float acc = 0.f;
+        for (int64_t c = lane; c < n / 2; c += 32) {
+            float2 av = __ldcs(a + c);
+            double2 xx = __ldg(xv + c);
+            acc = fmaf(av.x, (float)xx.x, acc);
+            acc = fmaf(av.y, (float)xx.y, acc);
+        }
+        double d = warp_sum((double)acc);
+        if (lane == 0) y[row] = d;
+    }
+}
+
+// ---------------- GMRES helpers (binary64 Arnoldi) ----------------
+
+template <int BS>
+__device__ double block_sum(double v) {
+    __shared__ double red[BS / 32];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < BS / 32 ? red[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+    }
+    __syncthreads();
+    return t;
+}
+
+// h[i] = V_i . w for i <= k (one block per i)
+__global__ void k_multidot(const double* __restrict__ V, const double* __restrict__ w, int64_t n, double* h) {
+    const int i = blockIdx.x;
+    const double* v = V + (int64_t)i * n;
+    double acc = 0.0;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc = fma(v[e], w[e], acc);
+    acc = block_sum<256>(acc);
+    if (threadIdx.x == 0) h[i] = acc;
+}
+
+// w -= sum_{i<=k} h[i] V_i ; hacc[i] += h[i]
+__global__ void k_multiaxpy(const double* __restrict__ V, const double* __restrict__ h, int k1, int64_t n,
+                            double* w) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = w[e];
+        for (int i = 0; i < k1; ++i) acc = fma(-h[i], V[(int64_t)i * n + e], acc);
+        w[e] = acc;
+    }
+}
+
+__global__ void k_norm(const double* __restrict__ w, int64_t n, double* out) {
+    double acc = 0.0;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc = fma(w[e], w[e], acc);
+    acc = block_sum<1024>(acc);
+    if (threadIdx.x == 0) *out = sqrt(acc);
+}
+
+// Hcol[i] = h1[i] + h2[i] (i <= k), Hcol[k+1] = ||w||, v_{k+1} = w / ||w||
+__global__ void k_finish_column(const double* __restrict__ h1, const double* __restrict__ h2,
+                                const double* __restrict__ nrm, int k, double* Hcol, const double* __restrict__ w,
+                                double* vnext, int64_t n) {
+    const double s = *nrm;
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e0 <= k) Hcol[e0] = h1[e0] + h2[e0];
+    if (e0 == k + 1) Hcol[k + 1] = s;
+    for (int64_t e = e0; e < n; e += (int64_t)gridDim.x * blockDim.x) vnext[e] = w[e] * inv;
+}
+
+// Apply the previous Givens rotations to column k of H, form rotation k, update g.
+// small[0] = |g_{k+1}| (residual estimate).
+__global__ void k_givens(double* H, int ldh, int k, double* cs, double* sn, double* g, double* small) {
+    double* col = H + (int64_t)k * ldh;
+    for (int i = 0; i < k; ++i) {
+        double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    double a = col[k], b = col[k + 1];
+    double den = hypot(a, b);
+    double c = den > 0 ? a / den : 1.0, s = den > 0 ? b / den : 0.0;
+    cs[k] = c;
+    sn[k] = s;
+    col[k] = den;
+    col[k + 1] = 0.0;
+    g[k + 1] = -s * g[k];
+    g[k] = c * g[k];
+    small[0] = fabs(g[k + 1]);
+}
+
+// Solve R y = g (k x k upper triangular, column-major with leading dimension ldh).
+__global__ void k_backsolve(const double* H, int ldh, int k, const double* g, double* y) {
+    for (int i = k - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int j = i + 1; j < k; ++j) acc -= H[(int64_t)j * ldh + i] * y[j];
+        y[i] = acc / H[(int64_t)i * ldh + i];
+    }
+}
+
+// x += sum_i y_i V_i
+__global__ void k_update_x(const double* __restrict__ V, const double* __restrict__ y, int k, int64_t n,
+                           double* x) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = x[e];
+        for (int i = 0; i < k; ++i) acc = fma(y[i], V[(int64_t)i * n + e], acc);
+        x[e] = acc;
+    }
+}
+
+// r = b - r (in place on r), v0 = r / ||r|| later
+__global__ void k_sub_from(const double* __restrict__ b, double* r, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        r[e] = b[e] - r[e];
+}
+
+__global__ void k_scale_into(const double* __restrict__ r, const double* __restrict__ nrm, double* v, double* g,
+                             int64_t n) {
+    const double s = *nrm;
+    const double inv = s > 0 ? 1.0 / s : 0.0;
+    int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e0 == 0) g[0] = s;
+    for (int64_t e = e0; e < n; e += (int64_t)gridDim.x * blockDim.x) v[e] = r[e] * inv;
+}
+
+__global__ void k_axpy(double a, const double* __restrict__ x, double* y, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = fma(a, x[e], y[e]);
+}
+
+// ---------------- classification of off-surface targets ----------------
+
+// One warp per target.  For every curve: nearest node (smallest index on ties); if it is
+// closer than 6 h*, Newton projection on the trigonometric interpolant giving the foot
+// t*, distance d and side; otherwise the side from the trapezoid Laplace double layer of
+// unit density (1 inside the outer curve, -1 inside a hole).
+__global__ void k_classify(const double* __restrict__ pts, int64_t npts, const double* __restrict__ geo,
+                           const double* __restrict__ coef, const int32_t* __restrict__ nn,
+                           const int32_t* __restrict__ off, int ncurves, int32_t* region, uint32_t* fine,
+                           int32_t* line_curve, double* line_data) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= npts) return;
+    const double px = pts[2 * t], py = pts[2 * t + 1];
+    int reg = -1;
+    uint32_t mask = 0;
+    int lc = -1;
+    double ld[4] = {0, 0, 0, 0};
+    double lbest = 1e300;
+    for (int k = 0; k < ncurves; ++k) {
+        const int N = nn[k];
+        const int o = off[k];
+        const double h = 2.0 * MH_PI / N;
+        double best = 1e300;
+        int bi = 0x7fffffff;
+        for (int i = lane; i < N; i += 32) {
+            const double* g = geo + 8 * (int64_t)(o + i);
+            double dx = g[0] - px, dy = g[1] - py;
+            double d2 = dx * dx + dy * dy;
+            if (d2 < best || (d2 == best && i < bi)) {
+                best = d2;
+                bi = i;
+            }
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            double ob = __shfl_xor_sync(0xffffffffu, best, s);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, s);
+            if (ob < best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        const double hstar = geo[8 * (int64_t)(o + bi) + 6] * h;
+        bool outside;
+        if (sqrt(best) < NEAR_NODE * hstar) {
+            const double* c = coef + 4 * coef_base(off, k);
+            double tt = bi * h;
+            double v[6];
+            for (int it = 0; it < 30; ++it) {
+                curve_eval_warp(c, N, tt, v);
+                double rx = v[0] - px, ry = v[1] - py;
+                double gr = rx * v[2] + ry * v[3];
+                double hs = v[2] * v[2] + v[3] * v[3] + rx * v[4] + ry * v[5];
+                if (hs <= 0) hs = v[2] * v[2] + v[3] * v[3];
+                double dt = gr / hs;
+                tt -= dt;
+                if (fabs(dt) < 1e-15) break;
+            }
+            tt = fmod(tt, 2.0 * MH_PI);
+            if (tt < 0) tt += 2.0 * MH_PI;
+            curve_eval_warp(c, N, tt, v);
+            double spd = sqrt(v[2] * v[2] + v[3] * v[3]);
+            double nx = v[3] / spd, ny = -v[2] / spd;
+            double rx = px - v[0], ry = py - v[1];
+            double d = sqrt(rx * rx + ry * ry);
+            double side = rx * nx + ry * ny;
+            double hs = spd * h;
+            outside = side >= 0.0;
+            if (d < NEAR_FINE * hs) mask |= 1u << k;
+            if (d < NEAR_LINE * hs && d < lbest) {
+                lbest = d;
+                lc = k;
+                ld[0] = tt;
+                ld[1] = d;
+                ld[2] = hs;
+            }
+        } else {
+            double acc = 0.0;
+            for (int i = lane; i < N; i += 32) {
+                const double* g = geo + 8 * (int64_t)(o + i);
+                double dx = g[0] - px, dy = g[1] - py;
+                double sp = g[6];
+                acc += (dx * g[3] / sp - dy * g[2] / sp) / (dx * dx + dy * dy) * sp * h;
+            }
+            acc = warp_sum(acc) / (2.0 * MH_PI);
+            outside = (k == 0) ? (acc < 0.5) : (acc < -0.5);
+        }
+        if (outside && reg == -1) reg = k;
+    }
+    if (lane == 0) {
+        region[t] = reg;
+        fine[t] = mask;
+        line_curve[t] = lc;
+        for (int i = 0; i < 4; ++i) line_data[4 * t + i] = ld[i];
+    }
+}
+
+// Foot point and inward normal of each line target, then the 4 auxiliary points
+// y* - m (h_s/4) n*, m = 1..4.
+__global__ void k_line_aux(const int32_t* __restrict__ line_tgt, const int32_t* __restrict__ line_curve,
+                           const double* __restrict__ line_data, int64_t nline, const double* __restrict__ coef,
+                           const int32_t* __restrict__ nn, const int32_t* __restrict__ off, int64_t n_user,
+                           double* ext_xy) {
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= nline) return;
+    const int k = line_curve[t];
+    double v[6];
+    curve_eval_warp(coef + 4 * coef_base(off, k), nn[k], line_data[4 * t], v);
+    if ((threadIdx.x & 31) == 0) {
+        double spd = sqrt(v[2] * v[2] + v[3] * v[3]);
+        double nx = v[3] / spd, ny = -v[2] / spd;
+        double hs = line_data[4 * t + 2];
+        for (int m = 1; m <= 4; ++m) {
+            double dm = m * NEAR_LINE * hs;
+            int64_t e = n_user + 4 * t + (m - 1);
+            ext_xy[2 * e] = v[0] - dm * nx;
+            ext_xy[2 * e + 1] = v[1] - dm * ny;
+        }
+    }
+}
+
+// ---------------- off-surface evaluation ----------------
+
+// Fourier coefficients of a scalar density per curve: 2 doubles per mode.
+__global__ void k_fourier_scalar(const double* __restrict__ v, const int32_t* __restrict__ nn,
+                                 const int32_t* __restrict__ off, int ncurves, int64_t total, double* coef) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int k = 0;
+    while (k + 1 < ncurves && g >= coef_base(off, k + 1)) ++k;
+    const int N = nn[k];
+    const int m = (int)(g - coef_base(off, k));
+    const double* p = v + off[k];
+    double re = 0, im = 0;
+    for (int n = 0; n < N; ++n) {
+        int r = (int)(((int64_t)m * n) % N);
+        double s, c;
+        sincospi(2.0 * r / N, &s, &c);
+        re += p[n] * c;
+        im -= p[n] * s;
+    }
+    coef[2 * g] = re / N;
+    coef[2 * g + 1] = im / N;
+}
+
+// Density on the fine grid times |y'| h_f (quadrature weight folded in).
+__global__ void k_fine_density(const double* __restrict__ sc, const double* __restrict__ fg,
+                               const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
+                               const int64_t* __restrict__ foff, int ncurves, int64_t nfine, double* wf) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= nfine) return;
+    int k = 0;
+    while (k + 1 < ncurves && g >= foff[k + 1]) ++k;
+    const int N = nn[k];
+    const int NF = UPSAMPLE * N;
+    const int f = (int)(g - foff[k]);
+    const double* c = sc + 2 * coef_base(off, k);
+    double v = 0, d1 = 0, d2 = 0;
+    for (int m = 0; m <= N / 2; ++m) {
+        int r = (int)(((int64_t)m * f) % NF);
+        double s, co;
+        sincospi(2.0 * r / NF, &s, &co);
+        mode_acc(m, N, c[2 * m], c[2 * m + 1], s, co, v, d1, d2);
+    }
+    wf[g] = v * fg[6 * g + 4] * fg[6 * g + 5];
+}
+
+// Coarse trapezoid sum over all curves not flagged fine for the target:
+//   out[t] = -(1/(2 pi alpha^2)) sum_n K(y_n, x_t) sigma_n |y'_n| h
+// Sources are staged through shared memory in tiles of the block size.
+template <int BS>
+__global__ void k_dlp_coarse(const double* __restrict__ xy, const uint32_t* __restrict__ fine, int64_t nt,
+                             const double* __restrict__ geo, const double* __restrict__ sigma,
+                             const int32_t* __restrict__ curve_of, const int32_t* __restrict__ nn, int64_t ns,
+                             double inv_alpha, double pref, double* out) {
+    __shared__ double sx[BS], sy[BS], snx[BS], sny[BS], sw[BS];
+    __shared__ int sk[BS];
+    const int64_t t = blockIdx.x * (int64_t)BS + threadIdx.x;
+    const bool active = t < nt;
+    const double px = active ? xy[2 * t] : 0.0, py = active ? xy[2 * t + 1] : 0.0;
+    const uint32_t mask = active ? fine[t] : 0xffffffffu;
+    double acc = 0.0;
+    for (int64_t s0 = 0; s0 < ns; s0 += BS) {
+        int64_t s = s0 + threadIdx.x;
+        if (s < ns) {
+            const double* g = geo + 8 * s;
+            int k = curve_of[s];
+            double sp = g[6];
+            sx[threadIdx.x] = g[0];
+            sy[threadIdx.x] = g[1];
+            snx[threadIdx.x] = g[3] / sp;
+            sny[threadIdx.x] = -g[2] / sp;
+            sw[threadIdx.x] = sigma[s] * sp * (2.0 * MH_PI / nn[k]);
+            sk[threadIdx.x] = k;
+        }
+        __syncthreads();
+        const int cnt = (ns - s0) < BS ? (int)(ns - s0) : BS;
+        if (active) {
+            for (int i = 0; i < cnt; ++i) {
+                if (mask & (1u << sk[i])) continue;
+                acc += dl_kernel(sx[i], sy[i], snx[i], sny[i], px, py, inv_alpha) * sw[i];
+            }
+        }
+        __syncthreads();
+    }
+    if (active) out[t] = pref * acc;
+}
+
+// Upsampled rule for (target, curve) pairs: one warp per pair.
+__global__ void k_dlp_fine(const double* __restrict__ xy, const int32_t* __restrict__ ptgt,
+                           const int32_t* __restrict__ pcurve, int64_t npairs, const double* __restrict__ fg,
+                           const double* __restrict__ wf, const int64_t* __restrict__ foff, double inv_alpha,
+                           double pref, double* out) {
+    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (p >= npairs) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ptgt[p];
+    const int k = pcurve[p];
+    const double px = xy[2 * t], py = xy[2 * t + 1];
+    double acc = 0.0;
+    for (int64_t f = foff[k] + lane; f < foff[k + 1]; f += 32) {
+        const double* g = fg + 6 * f;
+        acc += dl_kernel(g[0], g[1], g[2], g[3], px, py, inv_alpha) * wf[f];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) atomicAdd(out + t, pref * acc);
+}
+
+// Normal-line rule: degree-4 interpolation in the distance through the interior limit
+// v0 = -(A sigma)(t*) / (2 alpha^2) (trigonometric interpolation of the on-surface
+// values) and the values at the 4 auxiliary points.
+__global__ void k_dlp_line(const int32_t* __restrict__ line_tgt, const int32_t* __restrict__ line_curve,
+                           const double* __restrict__ line_data, int64_t nline, const double* __restrict__ asig,
+                           const int32_t* __restrict__ nn, const int32_t* __restrict__ off, int64_t n_user,
+                           double alpha, double* out) {
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= nline) return;
+    const int lane = threadIdx.x & 31;
+    const int k = line_curve[t];
+    const int N = nn[k];
+    const double ts = line_data[4 * t];
+    const double* a = asig + off[k];
+    double acc = 0.0;
+    for (int i = lane; i < N; i += 32) {
+        double tau = ts - 2.0 * MH_PI * i / N;
+        double sh = sin(0.5 * tau);
+        double dk = fabs(sh) < 1e-300 ? 1.0 : sin(0.5 * N * tau) * cos(0.5 * tau) / sh / N;
+        acc += dk * a[i];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        double vals[5], dist[5];
+        vals[0] = -acc / (2.0 * alpha * alpha);
+        dist[0] = 0.0;
+        double hs = line_data[4 * t + 2];
+        for (int m = 1; m <= 4; ++m) {
+            dist[m] = m * NEAR_LINE * hs;
+            vals[m] = out[n_user + 4 * t + (m - 1)];
+        }
+        double d = line_data[4 * t + 1];
+        double r = 0.0;
+        for (int i = 0; i < 5; ++i) {
+            double w = 1.0;
+            for (int j = 0; j < 5; ++j)
+                if (j != i) w *= (d - dist[j]) / (dist[i] - dist[j]);
+            r += w * vals[i];
+        }
+        out[line_tgt[t]] = r;
+    }
+}
+
+}  // namespace
+
+// ============================ host side ============================
+
+static mh_status upload_alpert(int l, AlpertRule* R) {
+    R->l = l;
+    R->a = l;
+    for (int m = 0; m < MH_ALPERT_LMAX; ++m) {
+        R->x[m] = m < l ? mh_alpert_nodes[l][m] : 0.0;
+        R->w[m] = m < l ? mh_alpert_weights[l][m] : 0.0;
+    }
+    return MH_OK;
+}
+
+extern "C" mh_status mh_boundary_create(mh_ctx* ctx, int n_curves, const int32_t* n_nodes_host,
+                                        const double* xy_host, int alpert_order, mh_boundary** out) {
+    if (!ctx || !out || !n_nodes_host || !xy_host) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (n_curves < 1 || n_curves > 32) return mh_fail(ctx, MH_ERR_INVALID_ARG, "n_curves must be in 1..32");
+    if (alpert_order < 0 || alpert_order > MH_ALPERT_LMAX)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "alpert_order must be in 0..%d", MH_ALPERT_LMAX);
+    auto* b = new mh_boundary();
+    b->n_curves = n_curves;
+    b->alpert_order = alpert_order;
+    int64_t tot = 0;
+    for (int k = 0; k < n_curves; ++k) {
+        int N = n_nodes_host[k];
+        if (N < 2 * alpert_order + 4 || N % 2) {
+            delete b;
+            return mh_fail(ctx, MH_ERR_INVALID_ARG, "curve %d: N=%d must be even and >= 2*alpert_order+4", k, N);
+        }
+        b->n_nodes.push_back(N);
+        b->offset.push_back((int32_t)tot);
+        tot += N;
+    }
+    b->offset.push_back((int32_t)tot);
+    b->n = tot;
+    std::vector<int32_t> curve_of(tot);
+    for (int k = 0; k < n_curves; ++k)
+        for (int i = b->offset[k]; i < b->offset[k + 1]; ++i) curve_of[i] = k;
+    cudaStream_t st = ctx->stream;
+    auto fail = [&](mh_status s) {
+        delete b;
+        return s;
+    };
+#define BCHK(call)                                                                                     \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return fail(mh_fail(ctx, MH_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_))); \
+    } while (0)
+    BCHK(b->d_nn.alloc(n_curves));
+    BCHK(b->d_off.alloc(n_curves + 1));
+    BCHK(b->d_curve_of.alloc(tot));
+    BCHK(b->xy.alloc(2 * tot));
+    BCHK(b->geo.alloc(8 * tot));
+    const int64_t nmodes = tot / 2 + n_curves;
+    BCHK(b->coef.alloc(4 * nmodes));
+    BCHK(cudaMemcpyAsync(b->d_nn.p, b->n_nodes.data(), n_curves * 4, cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemcpyAsync(b->d_off.p, b->offset.data(), (n_curves + 1) * 4, cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemcpyAsync(b->d_curve_of.p, curve_of.data(), tot * 4, cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemcpyAsync(b->xy.p, xy_host, 2 * tot * 8, cudaMemcpyHostToDevice, st));
+    k_fourier_xy<<<mh_grid(nmodes, 128), 128, 0, st>>>(b->xy.p, b->d_nn.p, b->d_off.p, n_curves, nmodes, b->coef.p);
+    ctx->launches++;
+    k_node_geometry<<<mh_grid(tot, 128), 128, 0, st>>>(b->coef.p, b->d_nn.p, b->d_off.p, b->d_curve_of.p, tot,
+                                                         b->geo.p);
+    ctx->launches++;
+    // fine grid
+    b->fine_off.resize(n_curves + 1);
+    b->fine_off[0] = 0;
+    for (int k = 0; k < n_curves; ++k) b->fine_off[k + 1] = b->fine_off[k] + (int64_t)UPSAMPLE * b->n_nodes[k];
+    b->n_fine = b->fine_off[n_curves];
+    BCHK(b->d_fine_off.alloc(n_curves + 1));
+    BCHK(b->fine_geo.alloc(6 * b->n_fine));
+    BCHK(cudaMemcpyAsync(b->d_fine_off.p, b->fine_off.data(), (n_curves + 1) * 8, cudaMemcpyHostToDevice, st));
+    k_fine_geometry<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(b->coef.p, b->d_nn.p, b->d_off.p, b->d_fine_off.p,
+                                                               n_curves, b->n_fine, b->fine_geo.p);
+    ctx->launches++;
+    BCHK(cudaGetLastError());
+    // orientation: signed area (1/2) sum (x y' - y x') h per curve
+    std::vector<double> geo(8 * tot);
+    BCHK(cudaMemcpyAsync(geo.data(), b->geo.p, 8 * tot * 8, cudaMemcpyDeviceToHost, st));
+    BCHK(cudaStreamSynchronize(st));
+    for (int k = 0; k < n_curves; ++k) {
+        double area = 0.0, h = 2.0 * MH_PI / b->n_nodes[k];
+        for (int i = b->offset[k]; i < b->offset[k + 1]; ++i)
+            area += 0.5 * h * (geo[8 * i] * geo[8 * i + 3] - geo[8 * i + 1] * geo[8 * i + 2]);
+        if ((k == 0 && area <= 0) || (k > 0 && area >= 0))
+            return fail(mh_fail(ctx, MH_ERR_GEOMETRY,
+                                "curve %d has the wrong orientation (outer curve must be counter-clockwise, "
+                                "holes clockwise)", k));
+    }
+#undef BCHK
+    *out = b;
+    return MH_OK;
+}
+
+extern "C" mh_status mh_boundary_destroy(mh_boundary* b) {
+    delete b;
+    return MH_OK;
+}
+
+extern "C" mh_status mh_boundary_size(const mh_boundary* b, int64_t* n) {
+    if (!b || !n) return MH_ERR_INVALID_ARG;
+    *n = b->n;
+    return MH_OK;
+}
+
+extern "C" mh_status mh_boundary_geometry(mh_ctx* ctx, const mh_boundary* b, double* out_host) {
+    if (!ctx || !b || !out_host) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    MH_CUDA(ctx, cudaMemcpyAsync(out_host, b->geo.p, 8 * b->n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return MH_OK;
+}
+
+mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha) {
+    if (b->op.alpha == alpha && b->op.A64.p) return MH_OK;
+    const int64_t n = b->n;
+    MH_ALLOC(ctx, b->op.A64, n * n);
+    b->op.A32.release();
+    b->op.alpha = -1.0;
+    cudaStream_t st = ctx->stream;
+    dim3 grid((unsigned)mh_grid(n, 256), (unsigned)std::min<int64_t>(n, 65535));
+    k_assemble_trap<<<grid, 256, 0, st>>>(b->geo.p, b->d_curve_of.p, b->d_nn.p, b->d_off.p, n, 1.0 / alpha,
+                                          b->alpert_order, b->op.A64.p);
+    MH_LAUNCHED(ctx);
+    if (b->alpert_order > 0) {
+        AlpertRule R;
+        upload_alpert(b->alpert_order, &R);
+        k_assemble_alpert<<<(unsigned)n, 128, 0, st>>>(b->geo.p, b->coef.p, b->d_curve_of.p, b->d_nn.p, b->d_off.p, n,
+                                                       1.0 / alpha, R, b->op.A64.p);
+        MH_LAUNCHED(ctx);
+    }
+    b->op.alpha = alpha;
+    return MH_OK;
+}
+
+static mh_status ensure_fp32(mh_ctx* ctx, mh_boundary* b) {
+    if (b->op.A32.p) return MH_OK;
+    const int64_t nn = b->n * b->n;
+    MH_ALLOC(ctx, b->op.A32, nn);
+    k_to_float<<<152 * 8, 256, 0, ctx->stream>>>(b->op.A64.p, b->op.A32.p, nn);
+    MH_LAUNCHED(ctx);
+    return MH_OK;
+}
+
+static int gemv_blocks(int64_t n) {
+    int64_t need = (n + 7) / 8;            // 8 warps per block
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, 152 * 16));
+}
+
+mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec) {
+    if (prec == MH_PREC_MIXED) {
+        MH_TRY(ensure_fp32(ctx, b));
+        k_gemv32<<<gemv_blocks(b->n), 256, 0, ctx->stream>>>(b->op.A32.p, x, y, b->n);
+    } else {
+        k_gemv64<<<gemv_blocks(b->n), 256, 0, ctx->stream>>>(b->op.A64.p, x, y, b->n);
+    }
+    MH_LAUNCHED(ctx);
+    return MH_OK;
+}
+
+struct gmres_ws {
+    dbuf<double> V, H, cs, sn, g, y, h1, h2, small, w;
+    int m = 0;
+    int64_t n = 0;
+};
+
+static mh_status vec_norm(mh_ctx* ctx, const double* v, int64_t n, double* dev_out, double* host_out) {
+    k_norm<<<1, 1024, 0, ctx->stream>>>(v, n, dev_out);
+    MH_LAUNCHED(ctx);
+    MH_CUDA(ctx, cudaMemcpyAsync(host_out, dev_out, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return MH_OK;
+}
+
+// Unrestarted GMRES on A (precision prec) for A x = b; x holds the initial guess.
+// Returns iterations used and the Givens residual estimate (absolute).
+static mh_status gmres_core(mh_ctx* ctx, mh_boundary* bd, gmres_ws& ws, const double* b, double* x, double abs_tol,
+                            int max_iter, mh_precision prec, int* iters, double* resid) {
+    const int64_t n = bd->n;
+    cudaStream_t st = ctx->stream;
+    const int ew = mh_grid(n, 256) < 152 * 4 ? mh_grid(n, 256) : 152 * 4;
+    const int ldh = max_iter + 1;
+    // r = b - A x
+    MH_TRY(bie_apply(ctx, bd, x, ws.w.p, prec));
+    k_sub_from<<<ew, 256, 0, st>>>(b, ws.w.p, n);
+    MH_LAUNCHED(ctx);
+    double beta;
+    MH_TRY(vec_norm(ctx, ws.w.p, n, ws.small.p + 1, &beta));
+    *iters = 0;
+    *resid = beta;
+    if (beta <= abs_tol) return MH_OK;
+    k_scale_into<<<ew, 256, 0, st>>>(ws.w.p, ws.small.p + 1, ws.V.p, ws.g.p, n);
+    MH_LAUNCHED(ctx);
+    int k = 0;
+    double res = beta;
+    for (; k < max_iter; ++k) {
+        double* vk = ws.V.p + (int64_t)k * n;
+        MH_TRY(bie_apply(ctx, bd, vk, ws.w.p, prec));
+        // classical Gram-Schmidt, twice
+        k_multidot<<<k + 1, 256, 0, st>>>(ws.V.p, ws.w.p, n, ws.h1.p);
+        MH_LAUNCHED(ctx);
+        k_multiaxpy<<<ew, 256, 0, st>>>(ws.V.p, ws.h1.p, k + 1, n, ws.w.p);
+        MH_LAUNCHED(ctx);
+        k_multidot<<<k + 1, 256, 0, st>>>(ws.V.p, ws.w.p, n, ws.h2.p);
+        MH_LAUNCHED(ctx);
+        k_multiaxpy<<<ew, 256, 0, st>>>(ws.V.p, ws.h2.p, k + 1, n, ws.w.p);
+        MH_LAUNCHED(ctx);
+        k_norm<<<1, 1024, 0, st>>>(ws.w.p, n, ws.small.p + 1);
+        MH_LAUNCHED(ctx);
+        k_finish_column<<<ew, 256, 0, st>>>(ws.h1.p, ws.h2.p, ws.small.p + 1, k, ws.H.p + (int64_t)k * ldh, ws.w.p,
+                                            ws.V.p + (int64_t)(k + 1) * n, n);
+        MH_LAUNCHED(ctx);
+        k_givens<<<1, 1, 0, st>>>(ws.H.p, ldh, k, ws.cs.p, ws.sn.p, ws.g.p, ws.small.p);
+        MH_LAUNCHED(ctx);
+        MH_CUDA(ctx, cudaMemcpyAsync(&res, ws.small.p, 8, cudaMemcpyDeviceToHost, st));
+        MH_CUDA(ctx, cudaStreamSynchronize(st));
+        if (!std::isfinite(res)) return mh_fail(ctx, MH_ERR_NUMERIC, "GMRES residual is not finite");
+        if (res <= abs_tol) {
+            ++k;
+            break;
+        }
+    }
+    k_backsolve<<<1, 1, 0, st>>>(ws.H.p, ldh, k, ws.g.p, ws.y.p);
+    MH_LAUNCHED(ctx);
+    k_update_x<<<ew, 256, 0, st>>>(ws.V.p, ws.y.p, k, n, x);
+    MH_LAUNCHED(ctx);
+    *iters = k;
+    *resid = res;
+    return MH_OK;
+}
+
+mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, double tol, int max_iter,
+                    mh_precision prec, mh_gmres_info* info) {
+    const int64_t n = bd->n;
+    if (max_iter < 1 || max_iter > 1000) return mh_fail(ctx, MH_ERR_INVALID_ARG, "max_iter must be in 1..1000");
+    gmres_ws ws;
+    const int ldh = max_iter + 1;
+    MH_ALLOC(ctx, ws.V, (int64_t)(max_iter + 1) * n);
+    MH_ALLOC(ctx, ws.H, (int64_t)ldh * max_iter);
+    MH_ALLOC(ctx, ws.cs, max_iter + 1);
+    MH_ALLOC(ctx, ws.sn, max_iter + 1);
+    MH_ALLOC(ctx, ws.g, max_iter + 2);
+    MH_ALLOC(ctx, ws.y, max_iter + 1);
+    MH_ALLOC(ctx, ws.h1, max_iter + 2);
+    MH_ALLOC(ctx, ws.h2, max_iter + 2);
+    MH_ALLOC(ctx, ws.small, 4);
+    MH_ALLOC(ctx, ws.w, n);
+    MH_CUDA(ctx, cudaMemsetAsync(ws.g.p, 0, (max_iter + 2) * 8, ctx->stream));
+    double bnorm;
+    MH_TRY(vec_norm(ctx, b, n, ws.small.p + 2, &bnorm));
+    mh_gmres_info inf{0, 0, 0.0, 0};
+    if (bnorm == 0.0) {
+        MH_CUDA(ctx, cudaMemsetAsync(x, 0, n * 8, ctx->stream));
+        inf.converged = 1;
+        if (info) *info = inf;
+        return MH_OK;
+    }
+    if (prec == MH_PREC_FP64) {
+        int it;
+        double res;
+        MH_TRY(gmres_core(ctx, bd, ws, b, x, tol * bnorm, max_iter, MH_PREC_FP64, &it, &res));
+        inf.iterations = it;
+    } else {
+        // binary64 iterative refinement around binary32-operator GMRES
+        dbuf<double> r, dx;
+        MH_ALLOC(ctx, r, n);
+        MH_ALLOC(ctx, dx, n);
+        int total = 0;
+        for (int sweep = 0; sweep < 12 && total < max_iter; ++sweep) {
+            MH_TRY(bie_apply(ctx, bd, x, r.p, MH_PREC_FP64));
+            k_sub_from<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(b, r.p, n);
+            MH_LAUNCHED(ctx);
+            double rn;
+            MH_TRY(vec_norm(ctx, r.p, n, ws.small.p + 2, &rn));
+            if (rn <= tol * bnorm) break;
+            MH_CUDA(ctx, cudaMemsetAsync(dx.p, 0, n * 8, ctx->stream));
+            MH_CUDA(ctx, cudaMemsetAsync(ws.g.p, 0, (max_iter + 2) * 8, ctx->stream));
+            int it;
+            double res;
+            MH_TRY(gmres_core(ctx, bd, ws, r.p, dx.p, std::max(tol * bnorm, 1e-5 * rn), max_iter - total,
+                              MH_PREC_MIXED, &it, &res));
+            total += it;
+            inf.refinements++;
+            k_axpy<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(1.0, dx.p, x, n);
+            MH_LAUNCHED(ctx);
+        }
+        inf.iterations = total;
+    }
+    // true residual in binary64
+    MH_TRY(bie_apply(ctx, bd, x, ws.w.p, MH_PREC_FP64));
+    k_sub_from<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(b, ws.w.p, n);
+    MH_LAUNCHED(ctx);
+    double rn;
+    MH_TRY(vec_norm(ctx, ws.w.p, n, ws.small.p + 2, &rn));
+    inf.rel_residual = rn / bnorm;
+    inf.converged = inf.rel_residual <= tol;
+    if (info) *info = inf;
+    if (!inf.converged)
+        return mh_fail(ctx, MH_ERR_NOT_CONVERGED, "GMRES stopped after %d iterations at relative residual %.3e",
+                       inf.iterations, inf.rel_residual);
+    return MH_OK;
+}
+
+mh_status dlp_classify(mh_ctx* ctx, mh_boundary* b, const double* xy_dev, int64_t n, dlp_targets* tg) {
+    cudaStream_t st = ctx->stream;
+    tg->n = n;
+    dbuf<uint32_t> fine0;
+    dbuf<int32_t> lcurve;
+    dbuf<double> ldata;
+    MH_ALLOC(ctx, tg->region, n);
+    MH_ALLOC(ctx, fine0, n);
+    MH_ALLOC(ctx, lcurve, n);
+    MH_ALLOC(ctx, ldata, 4 * n);
+    if (n > 0) {
+        k_classify<<<mh_grid(n * 32, 256), 256, 0, st>>>(xy_dev, n, b->geo.p, b->coef.p, b->d_nn.p, b->d_off.p,
+                                                         b->n_curves, tg->region.p, fine0.p, lcurve.p, ldata.p);
+        MH_LAUNCHED(ctx);
+    }
+    // host-side compaction of the (few) line targets and fine pairs
+    std::vector<uint32_t> fm(n);
+    std::vector<int32_t> lc(n), reg(n);
+    std::vector<double> ld(4 * n);
+    MH_CUDA(ctx, cudaMemcpyAsync(fm.data(), fine0.p, n * 4, cudaMemcpyDeviceToHost, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(lc.data(), lcurve.p, n * 4, cudaMemcpyDeviceToHost, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(ld.data(), ldata.p, 4 * n * 8, cudaMemcpyDeviceToHost, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(reg.data(), tg->region.p, n * 4, cudaMemcpyDeviceToHost, st));
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
+    std::vector<int32_t> ltgt, lcur;
+    std::vector<double> ldat;
+    for (int64_t i = 0; i < n; ++i)
+        if (lc[i] >= 0 && reg[i] == -1) {
+            ltgt.push_back((int32_t)i);
+            lcur.push_back(lc[i]);
+            for (int j = 0; j < 4; ++j) ldat.push_back(ld[4 * i + j]);
+        }
+    tg->n_line = (int64_t)ltgt.size();
+    tg->n_ext = n + 4 * tg->n_line;
+    std::vector<uint32_t> fext(tg->n_ext);
+    for (int64_t i = 0; i < n; ++i) fext[i] = fm[i];
+    for (int64_t t = 0; t < tg->n_line; ++t)
+        for (int m = 0; m < 4; ++m) fext[n + 4 * t + m] = fm[ltgt[t]] | (1u << lcur[t]);
+    std::vector<int32_t> pt, pc;
+    for (int64_t i = 0; i < tg->n_ext; ++i)
+        for (int k = 0; k < b->n_curves; ++k)
+            if (fext[i] & (1u << k)) {
+                pt.push_back((int32_t)i);
+                pc.push_back(k);
+            }
+    tg->n_pairs = (int64_t)pt.size();
+    MH_ALLOC(ctx, tg->xy, 2 * tg->n_ext);
+    MH_ALLOC(ctx, tg->fine, tg->n_ext);
+    MH_ALLOC(ctx, tg->line_tgt, tg->n_line);
+    MH_ALLOC(ctx, tg->line_curve, tg->n_line);
+    MH_ALLOC(ctx, tg->line_data, 4 * tg->n_line);
+    MH_ALLOC(ctx, tg->pair_tgt, tg->n_pairs);
+    MH_ALLOC(ctx, tg->pair_curve, tg->n_pairs);
+    if (n > 0) MH_CUDA(ctx, cudaMemcpyAsync(tg->xy.p, xy_dev, 2 * n * 8, cudaMemcpyDeviceToDevice, st));
+    if (tg->n_ext) MH_CUDA(ctx, cudaMemcpyAsync(tg->fine.p, fext.data(), tg->n_ext * 4, cudaMemcpyHostToDevice, st));
+    if (tg->n_line) {
+        MH_CUDA(ctx, cudaMemcpyAsync(tg->line_tgt.p, ltgt.data(), tg->n_line * 4, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(tg->line_curve.p, lcur.data(), tg->n_line * 4, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(tg->line_data.p, ldat.data(), 4 * tg->n_line * 8, cudaMemcpyHostToDevice, st));
+        k_line_aux<<<mh_grid(tg->n_line * 32, 256), 256, 0, st>>>(tg->line_tgt.p, tg->line_curve.p, tg->line_data.p,
+                                                                  tg->n_line, b->coef.p, b->d_nn.p, b->d_off.p, n,
+                                                                  tg->xy.p);
+        MH_LAUNCHED(ctx);
+    }
+    if (tg->n_pairs) {
+        MH_CUDA(ctx, cudaMemcpyAsync(tg->pair_tgt.p, pt.data(), tg->n_pairs * 4, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(tg->pair_curve.p, pc.data(), tg->n_pairs * 4, cudaMemcpyHostToDevice, st));
+    }
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
+    return MH_OK;
+}
+
+mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, const dlp_targets* tg, const double* sigma,
+                       double* out, mh_precision prec) {
+    (void)prec;
+    cudaStream_t st = ctx->stream;
+    MH_TRY(bie_assemble(ctx, b, alpha));
+    const double pref = -1.0 / (2.0 * MH_PI * alpha * alpha);
+    dbuf<double> ext, sc, wf, asig;
+    MH_ALLOC(ctx, ext, tg->n_ext);
+    if (tg->n_ext) {
+        k_dlp_coarse<128><<<mh_grid(tg->n_ext, 128), 128, 0, st>>>(tg->xy.p, tg->fine.p, tg->n_ext, b->geo.p, sigma,
+                                                                   b->d_curve_of.p, b->d_nn.p, b->n, 1.0 / alpha,
+                                                                   pref, ext.p);
+        MH_LAUNCHED(ctx);
+    }
+    if (tg->n_pairs) {
+        const int64_t nmodes = b->n / 2 + b->n_curves;
+        MH_ALLOC(ctx, sc, 2 * nmodes);
+        MH_ALLOC(ctx, wf, b->n_fine);
+        k_fourier_scalar<<<mh_grid(nmodes, 128), 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->n_curves, nmodes,
+                                                               sc.p);
+        MH_LAUNCHED(ctx);
+        k_fine_density<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(sc.p, b->fine_geo.p, b->d_nn.p, b->d_off.p,
+                                                                 b->d_fine_off.p, b->n_curves, b->n_fine, wf.p);
+        MH_LAUNCHED(ctx);
+        k_dlp_fine<<<mh_grid(tg->n_pairs * 32, 256), 256, 0, st>>>(tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p,
+                                                                   tg->n_pairs, b->fine_geo.p, wf.p, b->d_fine_off.p,
+                                                                   1.0 / alpha, pref, ext.p);
+        MH_LAUNCHED(ctx);
+    }
+    if (tg->n_line) {
+        MH_ALLOC(ctx, asig, b->n);
+        MH_TRY(bie_apply(ctx, b, sigma, asig.p, MH_PREC_FP64));
+        k_dlp_line<<<mh_grid(tg->n_line * 32, 256), 256, 0, st>>>(tg->line_tgt.p, tg->line_curve.p, tg->line_data.p,
+                                                                  tg->n_line, asig.p, b->d_nn.p, b->d_off.p, tg->n,
+                                                                  alpha, ext.p);
+        MH_LAUNCHED(ctx);
+    }
+    if (tg->n) MH_CUDA(ctx, cudaMemcpyAsync(out, ext.p, tg->n * 8, cudaMemcpyDeviceToDevice, st));
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
+    return MH_OK;
+}
+
+extern "C" mh_status mh_double_layer_apply(mh_ctx* ctx, mh_boundary* b, double alpha, const double* sigma_dev,
+                                           const double* targets_dev, int64_t n_targets, double* out_dev,
+                                           mh_precision prec) {
+    if (!ctx || !b || !sigma_dev || !out_dev) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    if (!(alpha > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "alpha must be positive");
+    MH_TRY(bie_assemble(ctx, b, alpha));
+    if (!targets_dev) {
+        MH_TRY(bie_apply(ctx, b, sigma_dev, out_dev, prec));
+        MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        return MH_OK;
+    }
+    if (n_targets < 0) return mh_fail(ctx, MH_ERR_INVALID_ARG, "n_targets < 0");
+    dlp_targets tg;
+    MH_TRY(dlp_classify(ctx, b, targets_dev, n_targets, &tg));
+    return dlp_evaluate(ctx, b, alpha, &tg, sigma_dev, out_dev, prec);
+}
+
+extern "C" mh_status mh_gmres_solve(mh_ctx* ctx, mh_boundary* b, double alpha, const double* rhs_dev,
+                                    double* sigma_dev, double tol, int max_iter, mh_precision prec,
+                                    mh_gmres_info* info) {
+    if (!ctx || !b || !rhs_dev || !sigma_dev) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    if (!(alpha > 0) || !(tol > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "alpha and tol must be positive");
+    MH_TRY(bie_assemble(ctx, b, alpha));
+    return gmres_run(ctx, b, rhs_dev, sigma_dev, tol, max_iter, prec, info);
+}

@@ -1,0 +1,176 @@
+// Internal declarations shared by the libmh translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/mh.h"
+
+#define MH_PI 3.14159265358979323846
+
+struct mh_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int64_t launches = 0;
+};
+
+// Records a message on ctx and returns the status.
+mh_status mh_fail(mh_ctx* ctx, mh_status st, const char* fmt, ...);
+
+#define MH_CUDA(ctx, call)                                                                      \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return mh_fail((ctx), e_ == cudaErrorMemoryAllocation ? MH_ERR_OOM : MH_ERR_CUDA,  \
+                           "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,    \
+                           __LINE__);                                                           \
+    } while (0)
+
+#define MH_LAUNCHED(ctx)                                                                        \
+    do {                                                                                        \
+        (ctx)->launches++;                                                                      \
+        cudaError_t e_ = cudaGetLastError();                                                    \
+        if (e_ != cudaSuccess)                                                                  \
+            return mh_fail((ctx), MH_ERR_CUDA, "kernel launch failed: %s (%s:%d)",              \
+                           cudaGetErrorString(e_), __FILE__, __LINE__);                         \
+    } while (0)
+
+#define MH_TRY(expr)                                                                            \
+    do {                                                                                        \
+        mh_status s_ = (expr);                                                                  \
+        if (s_ != MH_OK) return s_;                                                             \
+    } while (0)
+
+// Device buffer with RAII free.
+template <class T>
+struct dbuf {
+    T* p = nullptr;
+    size_t n = 0;
+    dbuf() = default;
+    dbuf(const dbuf&) = delete;
+    dbuf& operator=(const dbuf&) = delete;
+    ~dbuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t alloc(size_t count) {
+        release();
+        n = count;
+        if (count == 0) return cudaSuccess;
+        return cudaMalloc((void**)&p, count * sizeof(T));
+    }
+};
+
+#define MH_ALLOC(ctx, buf, count) MH_CUDA(ctx, (buf).alloc(count))
+
+// Assembled boundary operator for one alpha (eq. discrete_sys), row-major N x N.
+struct bie_operator {
+    double alpha = -1.0;
+    dbuf<double> A64;
+    dbuf<float> A32;
+};
+
+struct mh_boundary {
+    int n_curves = 0;
+    int64_t n = 0;                       // N_Gamma
+    int alpert_order = 0;                // l (window a = l), 0 = plain trapezoid
+    std::vector<int32_t> n_nodes, offset; // per curve (host)
+    dbuf<int32_t> d_nn, d_off;           // per curve (device)
+    dbuf<int32_t> d_curve_of;            // curve index of every node
+    dbuf<double> xy;                     // [n][2]
+    dbuf<double> geo;                    // [n][8]: x y x' y' x'' y'' |y'| kdiag
+    dbuf<double> coef;                   // per curve Fourier coefficients: [off*2 ...] see boundary.cu
+    // fine (16x) grid per curve: positions, normals, speed*h_fine
+    int64_t n_fine = 0;
+    std::vector<int64_t> fine_off;
+    dbuf<int64_t> d_fine_off;
+    dbuf<double> fine_geo;               // [n_fine][5]: x y nx ny |y'| h_f
+    bie_operator op;
+};
+
+// Classified target set for off-surface evaluation.
+struct dlp_targets {
+    int64_t n = 0;          // user targets
+    int64_t n_ext = 0;      // user targets + auxiliary points of the normal-line rule
+    dbuf<double> xy;        // [n_ext][2]
+    dbuf<uint32_t> fine;    // [n_ext] bit k: use the upsampled rule on curve k
+    dbuf<int32_t> region;   // [n] -1 inside Omega, k exterior side of curve k
+    // normal-line rule: per line target
+    int64_t n_line = 0;
+    dbuf<int32_t> line_tgt;     // target index
+    dbuf<int32_t> line_curve;   // curve
+    dbuf<double> line_data;     // [n_line][4]: t*, d, h_s, unused
+    // fine pairs (ext target, curve)
+    int64_t n_pairs = 0;
+    dbuf<int32_t> pair_tgt, pair_curve;
+};
+
+struct mh_tree {
+    double box[3];
+    int q = 0, min_level = 0, max_level = 0;
+    int64_t n_leaves = 0, n_boxes = 0, n_nodes = 0;
+    std::vector<int32_t> lvl_start;      // box id range per level (host), size max_level+2
+    dbuf<int32_t> boxes;                 // [n_boxes][3] level ix iy, level then Morton order
+    dbuf<int32_t> leaf_box;              // [n_leaves] box id of each leaf (node order)
+    dbuf<int32_t> box_leaf;              // [n_boxes] leaf index or -1
+    dbuf<int32_t> box_parent;            // [n_boxes]
+    dbuf<int32_t> box_child;             // [n_boxes][4] or -1
+    dbuf<int32_t> status;                // dense per-level status map (Morton indexed), box id or -1
+    std::vector<int64_t> status_off;     // per level offset into status
+    dbuf<double> nodes;                  // [n_nodes][2]
+    dbuf<int32_t> list_off[4], list_item[4];   // U V W X in CSR over boxes
+    std::vector<int64_t> list_len;       // total items per list
+    void* vol = nullptr;                 // volume operator data (volume.cu)
+};
+
+struct mh_problem {
+    mh_tree* tree = nullptr;
+    mh_boundary* bnd = nullptr;
+    double dt = 0, alpha = 0;
+    int p = 0;
+    int ext_mode = 0;
+    std::vector<double> ext_const;
+    dbuf<double> d_ext_const;
+    dlp_targets tg;                      // volume nodes inside Omega (classification of all nodes)
+    dbuf<int32_t> region;                // [n_nodes]
+    dbuf<int32_t> inside_idx;            // indices of nodes inside Omega
+    int64_t n_inside = 0;
+    dbuf<int32_t> bnd_leaf;              // leaf of every boundary node
+    dbuf<double> B, Up, Ug, rhs, Uh;     // work arrays
+};
+
+// ---- boundary.cu ----
+mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha);
+mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec);
+mh_status dlp_classify(mh_ctx* ctx, mh_boundary* b, const double* xy_dev, int64_t n, dlp_targets* tg);
+mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, const dlp_targets* tg,
+                       const double* sigma, double* out, mh_precision prec);
+mh_status gmres_run(mh_ctx* ctx, mh_boundary* b, const double* rhs, double* x, double tol, int max_iter,
+                    mh_precision prec, mh_gmres_info* info);
+
+// ---- tree.cu ----
+void mh_gauss_legendre(int n, double* x, double* w);
+const double* tree_gl_nodes(const mh_tree* t);
+
+// ---- volume.cu ----
+mh_status volume_apply(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* b, double* up,
+                       mh_precision prec);
+void volume_free(mh_tree* t);
+mh_status tree_locate(mh_ctx* ctx, const mh_tree* t, const double* xy_dev, int64_t n, int32_t* leaf_out);
+mh_status tree_interpolate(mh_ctx* ctx, const mh_tree* t, const double* vals, const double* xy_dev,
+                           const int32_t* leaf, int64_t n, double* out);
+
+inline int mh_grid(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 2147483647LL) g = 2147483647LL;
+    return (int)g;
+}
