@@ -835,12 +835,6 @@ mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_
     return MH_OK;
 }
 
-struct gmres_ws {
-    dbuf<double> V, H, cs, sn, g, y, h1, h2, small, w;
-    int m = 0;
-    int64_t n = 0;
-};
-
 static mh_status vec_norm(mh_ctx* ctx, const double* v, int64_t n, double* dev_out, double* host_out) {
     k_norm<<<1, 1024, 0, ctx->stream>>>(v, n, dev_out);
     MH_LAUNCHED(ctx);
@@ -910,18 +904,24 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
                     mh_precision prec, mh_gmres_info* info) {
     const int64_t n = bd->n;
     if (max_iter < 1 || max_iter > 1000) return mh_fail(ctx, MH_ERR_INVALID_ARG, "max_iter must be in 1..1000");
-    gmres_ws ws;
-    const int ldh = max_iter + 1;
-    MH_ALLOC(ctx, ws.V, (int64_t)(max_iter + 1) * n);
-    MH_ALLOC(ctx, ws.H, (int64_t)ldh * max_iter);
-    MH_ALLOC(ctx, ws.cs, max_iter + 1);
-    MH_ALLOC(ctx, ws.sn, max_iter + 1);
-    MH_ALLOC(ctx, ws.g, max_iter + 2);
-    MH_ALLOC(ctx, ws.y, max_iter + 1);
-    MH_ALLOC(ctx, ws.h1, max_iter + 2);
-    MH_ALLOC(ctx, ws.h2, max_iter + 2);
-    MH_ALLOC(ctx, ws.small, 4);
-    MH_ALLOC(ctx, ws.w, n);
+    gmres_ws& ws = bd->ws;
+    if (ws.m < max_iter || ws.n != n) {
+        const int ldh = max_iter + 1;
+        MH_ALLOC(ctx, ws.V, (int64_t)(max_iter + 1) * n);
+        MH_ALLOC(ctx, ws.H, (int64_t)ldh * max_iter);
+        MH_ALLOC(ctx, ws.cs, max_iter + 1);
+        MH_ALLOC(ctx, ws.sn, max_iter + 1);
+        MH_ALLOC(ctx, ws.g, max_iter + 2);
+        MH_ALLOC(ctx, ws.y, max_iter + 1);
+        MH_ALLOC(ctx, ws.h1, max_iter + 2);
+        MH_ALLOC(ctx, ws.h2, max_iter + 2);
+        MH_ALLOC(ctx, ws.small, 4);
+        MH_ALLOC(ctx, ws.w, n);
+        MH_ALLOC(ctx, ws.r, n);
+        MH_ALLOC(ctx, ws.dx, n);
+        ws.m = max_iter;
+        ws.n = n;
+    }
     MH_CUDA(ctx, cudaMemsetAsync(ws.g.p, 0, (max_iter + 2) * 8, ctx->stream));
     double bnorm;
     MH_TRY(vec_norm(ctx, b, n, ws.small.p + 2, &bnorm));
@@ -939,9 +939,8 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
         inf.iterations = it;
     } else {
         // binary64 iterative refinement around binary32-operator GMRES
-        dbuf<double> r, dx;
-        MH_ALLOC(ctx, r, n);
-        MH_ALLOC(ctx, dx, n);
+        dbuf<double>& r = ws.r;
+        dbuf<double>& dx = ws.dx;
         int total = 0;
         for (int sweep = 0; sweep < 12 && total < max_iter; ++sweep) {
             MH_TRY(bie_apply(ctx, bd, x, r.p, MH_PREC_FP64));
@@ -1046,18 +1045,24 @@ mh_status dlp_classify(mh_ctx* ctx, mh_boundary* b, const double* xy_dev, int64_
         MH_CUDA(ctx, cudaMemcpyAsync(tg->pair_tgt.p, pt.data(), tg->n_pairs * 4, cudaMemcpyHostToDevice, st));
         MH_CUDA(ctx, cudaMemcpyAsync(tg->pair_curve.p, pc.data(), tg->n_pairs * 4, cudaMemcpyHostToDevice, st));
     }
+    MH_ALLOC(ctx, tg->ext, std::max<int64_t>(tg->n_ext, 1));
+    MH_ALLOC(ctx, tg->sc, 2 * (b->n / 2 + b->n_curves));
+    MH_ALLOC(ctx, tg->wf, b->n_fine);
+    MH_ALLOC(ctx, tg->asig, b->n);
     MH_CUDA(ctx, cudaStreamSynchronize(st));
     return MH_OK;
 }
 
-mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, const dlp_targets* tg, const double* sigma,
+mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* tg, const double* sigma,
                        double* out, mh_precision prec) {
     (void)prec;
     cudaStream_t st = ctx->stream;
     MH_TRY(bie_assemble(ctx, b, alpha));
     const double pref = -1.0 / (2.0 * MH_PI * alpha * alpha);
-    dbuf<double> ext, sc, wf, asig;
-    MH_ALLOC(ctx, ext, tg->n_ext);
+    dbuf<double>& ext = tg->ext;
+    dbuf<double>& sc = tg->sc;
+    dbuf<double>& wf = tg->wf;
+    dbuf<double>& asig = tg->asig;
     if (tg->n_ext) {
         k_dlp_coarse<128><<<mh_grid(tg->n_ext, 128), 128, 0, st>>>(tg->xy.p, tg->fine.p, tg->n_ext, b->geo.p, sigma,
                                                                    b->d_curve_of.p, b->d_nn.p, b->n, 1.0 / alpha,
@@ -1066,8 +1071,6 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, const dlp_targ
     }
     if (tg->n_pairs) {
         const int64_t nmodes = b->n / 2 + b->n_curves;
-        MH_ALLOC(ctx, sc, 2 * nmodes);
-        MH_ALLOC(ctx, wf, b->n_fine);
         k_fourier_scalar<<<mh_grid(nmodes, 128), 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->n_curves, nmodes,
                                                                sc.p);
         MH_LAUNCHED(ctx);
@@ -1080,7 +1083,6 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, const dlp_targ
         MH_LAUNCHED(ctx);
     }
     if (tg->n_line) {
-        MH_ALLOC(ctx, asig, b->n);
         MH_TRY(bie_apply(ctx, b, sigma, asig.p, MH_PREC_FP64));
         k_dlp_line<<<mh_grid(tg->n_line * 32, 256), 256, 0, st>>>(tg->line_tgt.p, tg->line_curve.p, tg->line_data.p,
                                                                   tg->n_line, asig.p, b->d_nn.p, b->d_off.p, tg->n,
@@ -1088,7 +1090,6 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, const dlp_targ
         MH_LAUNCHED(ctx);
     }
     if (tg->n) MH_CUDA(ctx, cudaMemcpyAsync(out, ext.p, tg->n * 8, cudaMemcpyDeviceToDevice, st));
-    MH_CUDA(ctx, cudaStreamSynchronize(st));
     return MH_OK;
 }
 
@@ -1106,7 +1107,9 @@ extern "C" mh_status mh_double_layer_apply(mh_ctx* ctx, mh_boundary* b, double a
     if (n_targets < 0) return mh_fail(ctx, MH_ERR_INVALID_ARG, "n_targets < 0");
     dlp_targets tg;
     MH_TRY(dlp_classify(ctx, b, targets_dev, n_targets, &tg));
-    return dlp_evaluate(ctx, b, alpha, &tg, sigma_dev, out_dev, prec);
+    MH_TRY(dlp_evaluate(ctx, b, alpha, &tg, sigma_dev, out_dev, prec));
+    MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return MH_OK;
 }
 
 extern "C" mh_status mh_gmres_solve(mh_ctx* ctx, mh_boundary* b, double alpha, const double* rhs_dev,

@@ -71,6 +71,13 @@ struct dbuf {
 
 #define MH_ALLOC(ctx, buf, count) MH_CUDA(ctx, (buf).alloc(count))
 
+// GMRES workspace (kept by the boundary so that repeated solves allocate nothing).
+struct gmres_ws {
+    dbuf<double> V, H, cs, sn, g, y, h1, h2, small, w, r, dx;
+    int m = 0;
+    int64_t n = 0;
+};
+
 // Assembled boundary operator for one alpha (eq. discrete_sys), row-major N x N.
 struct bie_operator {
     double alpha = -1.0;
@@ -94,6 +101,7 @@ struct mh_boundary {
     dbuf<int64_t> d_fine_off;
     dbuf<double> fine_geo;               // [n_fine][5]: x y nx ny |y'| h_f
     bie_operator op;
+    gmres_ws ws;
 };
 
 // Classified target set for off-surface evaluation.
@@ -111,6 +119,8 @@ struct dlp_targets {
     // fine pairs (ext target, curve)
     int64_t n_pairs = 0;
     dbuf<int32_t> pair_tgt, pair_curve;
+    // evaluation workspaces (allocated once by dlp_classify)
+    dbuf<double> ext, sc, wf, asig;
 };
 
 struct mh_tree {
@@ -151,7 +161,7 @@ struct mh_problem {
 mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha);
 mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec);
 mh_status dlp_classify(mh_ctx* ctx, mh_boundary* b, const double* xy_dev, int64_t n, dlp_targets* tg);
-mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, const dlp_targets* tg,
+mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* tg,
                        const double* sigma, double* out, mh_precision prec);
 mh_status gmres_run(mh_ctx* ctx, mh_boundary* b, const double* rhs, double* x, double tol, int max_iter,
                     mh_precision prec, mh_gmres_info* info);

@@ -1,0 +1,179 @@
+// IMEX (backward) Euler heat step (Section 2): u^{N+1} - alpha^2 Lap u^{N+1} = u^N + dt F^N,
+// alpha^2 = dt, solved as U = U^p + U^h.  The per-step work is
+//   form B~ (extension outside Omega, Section 3.1) -> volume potential -> leaf
+//   interpolation onto Gamma (Section 3.1) -> rhs = -2 alpha^2 (f - U^p) -> GMRES ->
+//   double layer at the nodes in Omega -> combine,
+// all on the context's stream.  Classification of the volume nodes, the leaf of every
+// boundary node, the boundary operator and the multipole operators are built once by
+// mh_problem_create.
+#include <algorithm>
+#include <cmath>
+#include <memory>
+
+#include "mh_internal.cuh"
+
+namespace {
+
+__global__ void k_form_B(const double* __restrict__ u, const double* __restrict__ F,
+                         const int32_t* __restrict__ region, const double* __restrict__ ext_const,
+                         const double* __restrict__ b_ext, int ext_mode, double dt, int64_t n, double* B) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = region[i];
+    double v;
+    if (r < 0)
+        v = u[i] + dt * F[i];
+    else
+        v = ext_mode == MH_EXT_CONST ? ext_const[r] + dt * F[i] : b_ext[i];
+    B[i] = v;
+}
+
+__global__ void k_rhs(const double* __restrict__ f, const double* __restrict__ ug, double c, int64_t n, double* rhs) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) rhs[i] = c * (f[i] - ug[i]);
+}
+
+__global__ void k_combine(const double* __restrict__ up, const double* __restrict__ uh,
+                          const int32_t* __restrict__ region, const int32_t* __restrict__ slot,
+                          const double* __restrict__ ext_const, int ext_mode, int64_t n, double* out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = region[i];
+    if (r < 0)
+        out[i] = up[i] + uh[slot[i]];
+    else
+        out[i] = ext_mode == MH_EXT_CONST ? ext_const[r] : up[i];
+}
+
+__global__ void k_gather_xy(const double* __restrict__ xy, const int32_t* __restrict__ idx, int64_t n, double* out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[2 * i] = xy[2 * idx[i]];
+    out[2 * i + 1] = xy[2 * idx[i] + 1];
+}
+
+}  // namespace
+
+struct ProblemImpl : mh_problem {
+    dbuf<int32_t> slot;       // position of an inside node in the inside list, else -1
+};
+
+extern "C" mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* bnd, double dt, int p, int ext_mode,
+                                       const double* ext_const_host, mh_problem** out) {
+    if (!ctx || !tree || !bnd || !out) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (!(dt > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "dt must be positive");
+    if (p < 1 || p > 40) return mh_fail(ctx, MH_ERR_INVALID_ARG, "p must be in 1..40");
+    if (ext_mode != MH_EXT_CONST && ext_mode != MH_EXT_ARRAY) return mh_fail(ctx, MH_ERR_INVALID_ARG, "bad ext_mode");
+    if (ext_mode == MH_EXT_CONST && !ext_const_host)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "MH_EXT_CONST needs ext_const_host");
+    cudaStream_t st = ctx->stream;
+    std::unique_ptr<ProblemImpl> P(new ProblemImpl());
+    P->tree = tree;
+    P->bnd = bnd;
+    P->dt = dt;
+    P->alpha = std::sqrt(dt);
+    P->p = p;
+    P->ext_mode = ext_mode;
+    const int nc = bnd->n_curves;
+    P->ext_const.assign(nc, 0.0);
+    if (ext_const_host) P->ext_const.assign(ext_const_host, ext_const_host + nc);
+    MH_ALLOC(ctx, P->d_ext_const, nc);
+    MH_CUDA(ctx, cudaMemcpyAsync(P->d_ext_const.p, P->ext_const.data(), nc * 8, cudaMemcpyHostToDevice, st));
+    const int64_t n = tree->n_nodes;
+    // classify every node, then re-classify the inside ones as the evaluation target set
+    {
+        dlp_targets all;
+        MH_TRY(dlp_classify(ctx, bnd, tree->nodes.p, n, &all));
+        MH_ALLOC(ctx, P->region, n);
+        MH_CUDA(ctx, cudaMemcpyAsync(P->region.p, all.region.p, n * 4, cudaMemcpyDeviceToDevice, st));
+        std::vector<int32_t> reg(n), slot(n, -1), idx;
+        MH_CUDA(ctx, cudaMemcpyAsync(reg.data(), all.region.p, n * 4, cudaMemcpyDeviceToHost, st));
+        MH_CUDA(ctx, cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < n; ++i)
+            if (reg[i] < 0) {
+                slot[i] = (int32_t)idx.size();
+                idx.push_back((int32_t)i);
+            }
+        P->n_inside = (int64_t)idx.size();
+        MH_ALLOC(ctx, P->inside_idx, std::max<int64_t>(P->n_inside, 1));
+        MH_ALLOC(ctx, P->slot, n);
+        MH_CUDA(ctx, cudaMemcpyAsync(P->slot.p, slot.data(), n * 4, cudaMemcpyHostToDevice, st));
+        dbuf<double> xin;
+        MH_ALLOC(ctx, xin, std::max<int64_t>(2 * P->n_inside, 2));
+        if (P->n_inside) {
+            MH_CUDA(ctx, cudaMemcpyAsync(P->inside_idx.p, idx.data(), P->n_inside * 4, cudaMemcpyHostToDevice, st));
+            k_gather_xy<<<mh_grid(P->n_inside, 256), 256, 0, st>>>(tree->nodes.p, P->inside_idx.p, P->n_inside, xin.p);
+            MH_LAUNCHED(ctx);
+        }
+        MH_TRY(dlp_classify(ctx, bnd, xin.p, P->n_inside, &P->tg));
+    }
+    // leaf of every boundary node
+    MH_ALLOC(ctx, P->bnd_leaf, bnd->n);
+    MH_TRY(tree_locate(ctx, tree, bnd->xy.p, bnd->n, P->bnd_leaf.p));
+    {
+        std::vector<int32_t> bl(bnd->n);
+        MH_CUDA(ctx, cudaMemcpyAsync(bl.data(), P->bnd_leaf.p, bnd->n * 4, cudaMemcpyDeviceToHost, st));
+        MH_CUDA(ctx, cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < bnd->n; ++i)
+            if (bl[i] < 0) return mh_fail(ctx, MH_ERR_GEOMETRY, "boundary node %lld lies outside the tree", (long long)i);
+    }
+    MH_ALLOC(ctx, P->B, n);
+    MH_ALLOC(ctx, P->Up, n);
+    MH_ALLOC(ctx, P->Ug, bnd->n);
+    MH_ALLOC(ctx, P->rhs, bnd->n);
+    MH_ALLOC(ctx, P->Uh, std::max<int64_t>(P->n_inside, 1));
+    // operators: boundary (alpha) and volume (alpha, p) -- built once here
+    MH_TRY(bie_assemble(ctx, bnd, P->alpha));
+    MH_CUDA(ctx, cudaMemsetAsync(P->B.p, 0, n * 8, st));
+    MH_TRY(volume_apply(ctx, tree, P->alpha, p, P->B.p, P->Up.p, MH_PREC_FP64));
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
+    *out = P.release();
+    return MH_OK;
+}
+
+extern "C" mh_status mh_problem_destroy(mh_problem* p) {
+    delete static_cast<ProblemImpl*>(p);
+    return MH_OK;
+}
+
+extern "C" mh_status mh_problem_regions(mh_ctx* ctx, const mh_problem* p, int32_t* region_host) {
+    if (!ctx || !p || !region_host) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    MH_CUDA(ctx, cudaMemcpyAsync(region_host, p->region.p, p->tree->n_nodes * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return MH_OK;
+}
+
+extern "C" mh_status heat_step(mh_ctx* ctx, mh_problem* prob, const double* u_dev, const double* F_dev,
+                               const double* f_next_dev, const double* b_ext_dev, double* u_next_dev,
+                               double* sigma_dev, double gmres_tol, mh_precision prec, mh_step_info* info) {
+    if (!ctx || !prob || !u_dev || !F_dev || !f_next_dev || !u_next_dev || !sigma_dev)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    ProblemImpl* P = static_cast<ProblemImpl*>(prob);
+    if (P->ext_mode == MH_EXT_ARRAY && !b_ext_dev)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "MH_EXT_ARRAY needs b_ext_dev");
+    if (!(gmres_tol > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "gmres_tol must be positive");
+    cudaStream_t st = ctx->stream;
+    mh_tree* t = P->tree;
+    mh_boundary* b = P->bnd;
+    const int64_t n = t->n_nodes, ng = b->n;
+    k_form_B<<<mh_grid(n, 256), 256, 0, st>>>(u_dev, F_dev, P->region.p, P->d_ext_const.p, b_ext_dev, P->ext_mode,
+                                              P->dt, n, P->B.p);
+    MH_LAUNCHED(ctx);
+    MH_TRY(volume_apply(ctx, t, P->alpha, P->p, P->B.p, P->Up.p, prec));
+    MH_TRY(tree_interpolate(ctx, t, P->Up.p, b->xy.p, P->bnd_leaf.p, ng, P->Ug.p));
+    k_rhs<<<mh_grid(ng, 256), 256, 0, st>>>(f_next_dev, P->Ug.p, -2.0 * P->dt, ng, P->rhs.p);
+    MH_LAUNCHED(ctx);
+    mh_gmres_info gi{};
+    mh_status s = gmres_run(ctx, b, P->rhs.p, sigma_dev, gmres_tol, 100, prec, &gi);
+    if (info) {
+        info->gmres_iterations = gi.iterations;
+        info->gmres_rel_residual = gi.rel_residual;
+    }
+    if (s != MH_OK) return s;
+    MH_TRY(dlp_evaluate(ctx, b, P->alpha, &P->tg, sigma_dev, P->Uh.p, prec));
+    k_combine<<<mh_grid(n, 256), 256, 0, st>>>(P->Up.p, P->Uh.p, P->region.p, P->slot.p, P->d_ext_const.p,
+                                               P->ext_mode, n, u_next_dev);
+    MH_LAUNCHED(ctx);
+    return MH_OK;
+}

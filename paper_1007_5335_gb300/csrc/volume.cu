@@ -1,0 +1,817 @@
+// Volume potential (Section 3.1, eq. volume_potential): U(x) = sum over leaves of
+// int_leaf G(x - y) P(y) dA with G = K0(r/alpha)/(2 pi alpha^2) and P the leaf's q x q
+// interpolant of B.  Evaluated by an adaptive multipole method on the device quadtree:
+//
+//   near  (U list): precomputed per-(level, configuration) q^2 x q^2 tables of the exact
+//                   integrals of G times the source leaf's Lagrange basis (device kernel,
+//                   graded tensor Gauss-Legendre rule);
+//   P2M / M2M       K_n multipoles   M_n = int P(y) I_n(k rho) e^{-i n phi} dA / (2 pi alpha^2)
+//   M2L (V list)    K_n -> I_n locals through Graf's addition theorem,
+//   P2L (X list), M2P (W list), L2L, L2P,
+// with k = 1/alpha, n = -p..p.  Expansions are scaled by I_n(k s_l) (s_l = box radius of
+// level l) so that every coefficient and operator entry is O(1), and stored in a real
+// form of length 2p+1 ([a_0, a_1, b_1, ..., a_p, b_p], M_{-n} = conj(M_n) for a real B).
+//
+// Every pass is a batch of small dense contractions "y_dst += T_op x_src" with the
+// operator T_op chosen by (level, relative configuration).  Tasks are sorted by operator;
+// a block stages one operator and up to 32 source vectors in shared memory and writes
+// its products to a task-indexed buffer, and a segmented reduction sums the products of
+// each destination in a fixed order (deterministic, no atomics).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <complex>
+#include <map>
+#include <memory>
+#include <tuple>
+
+#include "bessel.cuh"
+#include "mh_internal.cuh"
+
+namespace {
+
+constexpr int CHUNK = 32;   // tasks per block in the contraction kernel
+constexpr int NGLN = 16;    // Gauss-Legendre points per panel in the near-table rule
+constexpr int NGLQ = 32;    // Gauss-Legendre points per axis for the smooth P2M/P2L integrals
+
+// ---------------- host Bessel functions (operator construction) ----------------
+
+double h_k0(double z) {
+    if (z <= 2.0) {
+        const double y = 0.25 * z * z;
+        double si = mh_ser_i0_h[MH_BESSEL_NSER - 1], sh = mh_ser_k0h_h[MH_BESSEL_NSER - 1];
+        for (int k = MH_BESSEL_NSER - 2; k >= 0; --k) {
+            si = si * y + mh_ser_i0_h[k];
+            sh = sh * y + mh_ser_k0h_h[k];
+        }
+        return sh - (std::log(0.5 * z) + MH_EULER_GAMMA) * si;
+    }
+    double x = 4.0 / z - 1.0, b1 = 0, b2 = 0;
+    for (int k = MH_CHEB_K0_N64 - 1; k >= 1; --k) {
+        double t = 2 * x * b1 - b2 + mh_cheb_k0_h[k];
+        b2 = b1;
+        b1 = t;
+    }
+    return std::exp(-z) / std::sqrt(z) * (x * b1 - b2 + mh_cheb_k0_h[0]);
+}
+
+double h_k1(double z) {
+    if (z <= 2.0) {
+        const double y = 0.25 * z * z;
+        double si = mh_ser_i1_h[MH_BESSEL_NSER - 1], sp = mh_ser_k1p_h[MH_BESSEL_NSER - 1];
+        for (int k = MH_BESSEL_NSER - 2; k >= 0; --k) {
+            si = si * y + mh_ser_i1_h[k];
+            sp = sp * y + mh_ser_k1p_h[k];
+        }
+        return 1.0 / z + std::log(0.5 * z) * (0.5 * z) * si - 0.25 * z * sp;
+    }
+    double x = 4.0 / z - 1.0, b1 = 0, b2 = 0;
+    for (int k = MH_CHEB_K1_N64 - 1; k >= 1; --k) {
+        double t = 2 * x * b1 - b2 + mh_cheb_k1_h[k];
+        b2 = b1;
+        b1 = t;
+    }
+    return std::exp(-z) / std::sqrt(z) * (x * b1 - b2 + mh_cheb_k1_h[0]);
+}
+
+// K_0..K_nmax(z) by the (stable) forward recurrence K_{n+1} = K_{n-1} + (2n/z) K_n.
+void h_kn_all(double z, int nmax, double* K) {
+    K[0] = h_k0(z);
+    if (nmax >= 1) K[1] = h_k1(z);
+    for (int n = 1; n < nmax; ++n) K[n + 1] = K[n - 1] + (2.0 * n / z) * K[n];
+}
+
+// I_n(z) = sum_k (z/2)^{n+2k} / (k! (n+k)!)  (all terms positive).
+double h_in(int n, double z) {
+    if (n < 0) n = -n;
+    if (z == 0.0) return n == 0 ? 1.0 : 0.0;
+    const double h = 0.5 * z;
+    double t = 1.0;
+    for (int i = 1; i <= n; ++i) t *= h / i;
+    double s = t, y = h * h;
+    for (int k = 1; k < 2000; ++k) {
+        t *= y / ((double)k * (n + k));
+        s += t;
+        if (t < 1e-17 * s) break;
+    }
+    return s;
+}
+
+// Complex operator T(m, n), m = 0..p, n = -p..p, on conjugate-symmetric vectors -> real
+// (2p+1) x (2p+1) matrix acting on [a_0, a_1, b_1, ..., a_p, b_p].
+template <class F>
+void real_form(int p, F T, double* out /* row-major (2p+1)^2 */) {
+    const int P = 2 * p + 1;
+    std::fill(out, out + P * P, 0.0);
+    for (int m = 0; m <= p; ++m)
+        for (int n = 0; n <= p; ++n) {
+            const std::complex<double> t = T(m, n);
+            const std::complex<double> tc = n > 0 ? T(m, -n) : std::complex<double>(0.0, 0.0);
+            const int ra = m == 0 ? 0 : 2 * m - 1, rb = 2 * m;
+            const int ca = n == 0 ? 0 : 2 * n - 1, cb = 2 * n;
+            // y_m += t x_n + tc conj(x_n),  x_n = a + i b
+            out[ra * P + ca] += (t + tc).real();
+            if (m > 0) out[rb * P + ca] += (t + tc).imag();
+            if (n > 0) {
+                out[ra * P + cb] += (tc - t).imag();
+                if (m > 0) out[rb * P + cb] += (t - tc).real();
+            }
+        }
+}
+
+// ---------------- device kernels ----------------
+
+struct NearCfg {
+    double sx, sy, sw;   // source box centre relative to the target box centre, source width
+    double tw;           // target box width
+};
+
+// Panels on [lo, hi] graded geometrically (ratio 4) toward c from the panel size delta;
+// when c lies inside, both sides are graded toward it.
+__device__ int grade_side(double a, double b, bool toward_a, double delta, double* pa, double* pb, int n) {
+    const double L = b - a;
+    double prev = 0.0, d = delta;
+    while (d < L && n < 60) {
+        if (toward_a) {
+            pa[n] = a + prev;
+            pb[n] = a + d;
+        } else {
+            pa[n] = b - d;
+            pb[n] = b - prev;
+        }
+        ++n;
+        prev = d;
+        d *= 4.0;
+    }
+    if (toward_a) {
+        pa[n] = a + prev;
+        pb[n] = b;
+    } else {
+        pa[n] = a;
+        pb[n] = b - prev;
+    }
+    return n + 1;
+}
+
+__device__ int make_panels(double lo, double hi, double c, double delta, double* pa, double* pb) {
+    if (c > lo && c < hi) {
+        int n = grade_side(lo, c, false, delta, pa, pb, 0);
+        return grade_side(c, hi, true, delta, pa, pb, n);
+    }
+    return grade_side(lo, hi, c <= lo, delta, pa, pb, 0);
+}
+
+// One block per (configuration, target node i): row i of the q^2 x q^2 near table,
+//   T[i][j] = int_source G(x_i - y) L_j(y) dA,
+// by a tensor Gauss-Legendre rule on panels graded toward the target point.
+__global__ void k_near_tables(const NearCfg* __restrict__ cfg, int q, const double* __restrict__ xi,
+                              const double* __restrict__ gx, const double* __restrict__ gw, double inv_alpha,
+                              double pref, double* out) {
+    __shared__ double pxa[64], pxb[64], pya[64], pyb[64];
+    __shared__ int npx, npy;
+    __shared__ double sG[NGLN][NGLN + 1], sLx[16][NGLN], sLy[16][NGLN], sT[NGLN][17];
+    const int qq = q * q;
+    const int c = blockIdx.x / qq, i = blockIdx.x % qq;
+    const NearCfg C = cfg[c];
+    const double tx = 0.5 * C.tw * xi[i % q], ty = 0.5 * C.tw * xi[i / q];
+    const double x0 = C.sx - 0.5 * C.sw, x1 = C.sx + 0.5 * C.sw, y0 = C.sy - 0.5 * C.sw, y1 = C.sy + 0.5 * C.sw;
+    if (threadIdx.x == 0) {
+        const double dx = fmax(fmax(x0 - tx, tx - x1), 0.0), dy = fmax(fmax(y0 - ty, ty - y1), 0.0);
+        const double d = sqrt(dx * dx + dy * dy);
+        const double delta = d > 0.0 ? 0.5 * d : C.sw * 3.7252902984619141e-09;   // 4^-14
+        npx = make_panels(x0, x1, tx, delta, pxa, pxb);
+        npy = make_panels(y0, y1, ty, delta, pya, pyb);
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    double acc = 0.0;
+    for (int ix = 0; ix < npx; ++ix)
+        for (int iy = 0; iy < npy; ++iy) {
+            const double hx = 0.5 * (pxb[ix] - pxa[ix]), mx = 0.5 * (pxb[ix] + pxa[ix]);
+            const double hy = 0.5 * (pyb[iy] - pya[iy]), my = 0.5 * (pyb[iy] + pya[iy]);
+            {
+                const int u = t % NGLN, v = t / NGLN;
+                const double X = mx + hx * gx[u], Y = my + hy * gx[v];
+                const double r = sqrt((X - tx) * (X - tx) + (Y - ty) * (Y - ty));
+                sG[v][u] = pref * mh_k0(r * inv_alpha) * hx * hy * gw[u] * gw[v];
+            }
+            if (t < q * NGLN) {
+                const int a = t / NGLN, u = t % NGLN;
+                const double sx = (mx + hx * gx[u] - C.sx) * (2.0 / C.sw);
+                const double sy = (my + hy * gx[u] - C.sy) * (2.0 / C.sw);
+                double lx = 1.0, ly = 1.0;
+                for (int m = 0; m < q; ++m)
+                    if (m != a) {
+                        lx *= (sx - xi[m]) / (xi[a] - xi[m]);
+                        ly *= (sy - xi[m]) / (xi[a] - xi[m]);
+                    }
+                sLx[a][u] = lx;
+                sLy[a][u] = ly;
+            }
+            __syncthreads();
+            if (t < NGLN * q) {
+                const int v = t / q, a = t % q;
+                double s = 0.0;
+                for (int u = 0; u < NGLN; ++u) s += sG[v][u] * sLx[a][u];
+                sT[v][a] = s;
+            }
+            __syncthreads();
+            if (t < qq) {
+                const int b = t / q, a = t % q;
+                double s = 0.0;
+                for (int v = 0; v < NGLN; ++v) s += sLy[b][v] * sT[v][a];
+                acc += s;
+            }
+            __syncthreads();
+        }
+    if (t < qq) out[((int64_t)c * qq + i) * qq + t] = acc;
+}
+
+// Batched contraction: each block applies one operator (R x C, row-major) to up to CHUNK
+// source vectors gathered from `vec` and writes the products to temp[task][R].
+template <typename TOP>
+__global__ void k_apply(const TOP* __restrict__ ops, const int64_t* __restrict__ op_off,
+                        const int32_t* __restrict__ op_C, const int32_t* __restrict__ chunk_op,
+                        const int32_t* __restrict__ chunk_t0, const int64_t* __restrict__ task_src,
+                        const double* __restrict__ vec, int R, double* __restrict__ temp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TOP* sA = reinterpret_cast<TOP*>(smem_raw);
+    const int ch = blockIdx.x;
+    const int op = chunk_op[ch];
+    const int t0 = chunk_t0[ch];
+    const int nt = chunk_t0[ch + 1] - t0;   // chunks never straddle two operators
+    const int C = op_C[op];
+    const int lda = C + 1;
+    TOP* sX = sA + R * lda;
+    const TOP* A = ops + op_off[op];
+    for (int e = threadIdx.x; e < R * C; e += blockDim.x) sA[(e / C) * lda + (e % C)] = A[e];
+    for (int e = threadIdx.x; e < nt * C; e += blockDim.x) {
+        const int tt = e / C, cc = e % C;
+        sX[tt * lda + cc] = (TOP)vec[task_src[t0 + tt] + cc];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < nt * R; o += blockDim.x) {
+        const int tt = o / R, r = o % R;
+        const TOP* a = sA + r * lda;
+        const TOP* x = sX + tt * lda;
+        TOP acc = 0;
+        for (int cc = 0; cc < C; ++cc) acc += a[cc] * x[cc];
+        temp[(int64_t)(t0 + tt) * R + r] = (double)acc;
+    }
+}
+
+// Per destination (one warp each): vec[dst + r] = (acc ? vec : 0) + sum of its products.
+__global__ void k_reduce(const double* __restrict__ temp, int R, const int64_t* __restrict__ dst_off,
+                         const int32_t* __restrict__ dst_ptr, const int32_t* __restrict__ dst_task, int64_t n_dst,
+                         int accumulate, double* vec) {
+    const int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (d >= n_dst) return;
+    const int j0 = dst_ptr[d], j1 = dst_ptr[d + 1];
+    double* y = vec + dst_off[d];
+    for (int r = lane; r < R; r += 32) {
+        double s = accumulate ? y[r] : 0.0;
+        for (int j = j0; j < j1; ++j) s += temp[(int64_t)dst_task[j] * R + r];
+        y[r] = s;
+    }
+}
+
+// ---------------- host structures ----------------
+
+struct Task {
+    int op;
+    int64_t src, dst;
+};
+
+struct Phase {
+    int R = 0;
+    bool accumulate = false;
+    int64_t n_tasks = 0, n_dst = 0, n_chunks = 0;
+    int smem = 0;
+    dbuf<int32_t> chunk_op, chunk_t0, dst_ptr, dst_task;
+    dbuf<int64_t> task_src, dst_off;
+};
+
+struct OpPool {
+    std::vector<double> data;
+    std::vector<int64_t> off;
+    std::vector<int32_t> R, C;
+    int add(int r, int c, const double* v) {
+        off.push_back((int64_t)data.size());
+        R.push_back(r);
+        C.push_back(c);
+        data.insert(data.end(), v, v + (size_t)r * c);
+        return (int)off.size() - 1;
+    }
+};
+
+struct VolData {
+    double alpha = -1;
+    int p = -1;
+    int P = 0, qq = 0;
+    int64_t B_off = 0, U_off = 0, M_off = 0, L_off = 0, vec_len = 0;
+    dbuf<double> ops64, vec, temp;
+    dbuf<float> ops32;
+    dbuf<int64_t> d_op_off;
+    dbuf<int32_t> d_op_C;
+    std::vector<int> op_C;
+    std::unique_ptr<Phase> p2m, m2l, out;
+    std::vector<std::unique_ptr<Phase>> m2m, l2l;   // by level
+    int64_t temp_len = 0;
+    int64_t n_near_tables = 0;
+};
+
+mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumulate, const std::vector<int>& op_C,
+                      Phase* ph, int64_t* temp_need) {
+    ph->R = R;
+    ph->accumulate = accumulate;
+    ph->n_tasks = (int64_t)tasks.size();
+    // sort by operator (stable: keeps the generation order inside an operator)
+    std::vector<int64_t> order(tasks.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int64_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return tasks[a].op < tasks[b].op; });
+    std::vector<int64_t> src(tasks.size());
+    std::vector<int32_t> cop, ct0;
+    int maxC = 1;
+    for (size_t s = 0; s < order.size(); ++s) {
+        const Task& t = tasks[order[s]];
+        src[s] = t.src;
+        if (s == 0 || tasks[order[s - 1]].op != t.op || (int64_t)(s - ct0.back()) >= CHUNK) {
+            cop.push_back(t.op);
+            ct0.push_back((int32_t)s);
+        }
+        maxC = std::max(maxC, op_C[t.op]);
+    }
+    ph->n_chunks = (int64_t)cop.size();
+    ct0.push_back((int32_t)order.size());   // end of the last chunk
+    // destinations: tasks grouped by destination in generation order
+    std::vector<int64_t> rank(tasks.size());
+    for (size_t s = 0; s < order.size(); ++s) rank[order[s]] = (int64_t)s;
+    std::map<int64_t, std::vector<int32_t>> bydst;
+    for (size_t i = 0; i < tasks.size(); ++i) bydst[tasks[i].dst].push_back((int32_t)rank[i]);
+    std::vector<int64_t> doff;
+    std::vector<int32_t> dptr{0}, dtask;
+    for (auto& kv : bydst) {
+        doff.push_back(kv.first);
+        dtask.insert(dtask.end(), kv.second.begin(), kv.second.end());
+        dptr.push_back((int32_t)dtask.size());
+    }
+    ph->n_dst = (int64_t)doff.size();
+    ph->smem = (int)((R + CHUNK) * (maxC + 1) * sizeof(double));
+    cudaStream_t st = ctx->stream;
+    auto up32 = [&](dbuf<int32_t>& b, const std::vector<int32_t>& v) -> mh_status {
+        MH_ALLOC(ctx, b, std::max<size_t>(v.size(), 1));
+        if (!v.empty()) MH_CUDA(ctx, cudaMemcpyAsync(b.p, v.data(), v.size() * 4, cudaMemcpyHostToDevice, st));
+        return MH_OK;
+    };
+    auto up64 = [&](dbuf<int64_t>& b, const std::vector<int64_t>& v) -> mh_status {
+        MH_ALLOC(ctx, b, std::max<size_t>(v.size(), 1));
+        if (!v.empty()) MH_CUDA(ctx, cudaMemcpyAsync(b.p, v.data(), v.size() * 8, cudaMemcpyHostToDevice, st));
+        return MH_OK;
+    };
+    MH_TRY(up32(ph->chunk_op, cop));
+    MH_TRY(up32(ph->chunk_t0, ct0));
+    MH_TRY(up32(ph->dst_ptr, dptr));
+    MH_TRY(up32(ph->dst_task, dtask));
+    MH_TRY(up64(ph->task_src, src));
+    MH_TRY(up64(ph->dst_off, doff));
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
+    *temp_need = std::max<int64_t>(*temp_need, ph->n_tasks * R);
+    return MH_OK;
+}
+
+template <typename TOP>
+mh_status run_phase(mh_ctx* ctx, VolData* V, const TOP* ops, const Phase* ph) {
+    if (ph->n_tasks == 0) return MH_OK;
+    const int smem = (int)(ph->smem / sizeof(double) * sizeof(TOP));
+    k_apply<TOP><<<(unsigned)ph->n_chunks, 256, smem, ctx->stream>>>(ops, V->d_op_off.p, V->d_op_C.p, ph->chunk_op.p,
+                                                                     ph->chunk_t0.p, ph->task_src.p, V->vec.p, ph->R,
+                                                                     V->temp.p);
+    MH_LAUNCHED(ctx);
+    k_reduce<<<mh_grid(ph->n_dst * 32, 256), 256, 0, ctx->stream>>>(V->temp.p, ph->R, ph->dst_off.p, ph->dst_ptr.p,
+                                                                    ph->dst_task.p, ph->n_dst, ph->accumulate,
+                                                                    V->vec.p);
+    MH_LAUNCHED(ctx);
+    return MH_OK;
+}
+
+struct HostTree {
+    std::vector<int32_t> boxes, box_leaf, leaf_box;
+    std::vector<int32_t> off[4], item[4];
+};
+
+mh_status fetch_tree(mh_ctx* ctx, const mh_tree* t, HostTree* h) {
+    cudaStream_t st = ctx->stream;
+    h->boxes.resize(3 * t->n_boxes);
+    h->box_leaf.resize(t->n_boxes);
+    h->leaf_box.resize(t->n_leaves);
+    MH_CUDA(ctx, cudaMemcpyAsync(h->boxes.data(), t->boxes.p, 3 * t->n_boxes * 4, cudaMemcpyDeviceToHost, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(h->box_leaf.data(), t->box_leaf.p, t->n_boxes * 4, cudaMemcpyDeviceToHost, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(h->leaf_box.data(), t->leaf_box.p, t->n_leaves * 4, cudaMemcpyDeviceToHost, st));
+    for (int w = 0; w < 4; ++w) {
+        h->off[w].resize(t->n_boxes + 1);
+        h->item[w].resize(std::max<int64_t>(t->list_len[w], 1));
+        MH_CUDA(ctx, cudaMemcpyAsync(h->off[w].data(), t->list_off[w].p, (t->n_boxes + 1) * 4, cudaMemcpyDeviceToHost,
+                                     st));
+        if (t->list_len[w])
+            MH_CUDA(ctx, cudaMemcpyAsync(h->item[w].data(), t->list_item[w].p, t->list_len[w] * 4,
+                                         cudaMemcpyDeviceToHost, st));
+    }
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
+    return MH_OK;
+}
+
+// Build every operator and pass of the multipole method for (tree, alpha, p).
+mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V) {
+    const int q = t->q, qq = q * q, P = 2 * p + 1, L = t->max_level;
+    const double k = 1.0 / alpha, pref = 1.0 / (2.0 * MH_PI * alpha * alpha);
+    const double x0 = t->box[0], y0 = t->box[1], W = t->box[2];
+    V->alpha = alpha;
+    V->p = p;
+    V->P = P;
+    V->qq = qq;
+    HostTree h;
+    MH_TRY(fetch_tree(ctx, t, &h));
+    const int64_t nb = t->n_boxes, nl = t->n_leaves;
+    V->B_off = 0;
+    V->U_off = nl * qq;
+    V->M_off = 2 * nl * qq;
+    V->L_off = V->M_off + nb * P;
+    V->vec_len = V->L_off + nb * P;
+    auto lev = [&](int b) { return h.boxes[3 * b]; };
+    auto bx = [&](int b) { return h.boxes[3 * b + 1]; };
+    auto by = [&](int b) { return h.boxes[3 * b + 2]; };
+    auto width = [&](int l) { return W / (double)(1 << l); };
+    // level scales: s_l = box radius, I_n(k s_l) for n = 0..p
+    std::vector<std::vector<double>> Is(L + 1, std::vector<double>(p + 1));
+    for (int l = 0; l <= L; ++l)
+        for (int n = 0; n <= p; ++n) {
+            Is[l][n] = h_in(n, k * width(l) * 0.70710678118654752);
+            if (!(Is[l][n] > 1e-300) || !std::isfinite(Is[l][n]))
+                return mh_fail(ctx, MH_ERR_NUMERIC, "expansion scale I_%d(%g) out of range at level %d", n,
+                               k * width(l) * 0.707, l);
+        }
+    std::vector<double> glx(NGLQ), glw(NGLQ), qx(q), qw(q), g16x(NGLN), g16w(NGLN);
+    mh_gauss_legendre(NGLQ, glx.data(), glw.data());
+    mh_gauss_legendre(q, qx.data(), qw.data());
+    mh_gauss_legendre(NGLN, g16x.data(), g16w.data());
+    // Lagrange basis of the leaf nodes at the 32-point rule: LG[a * NGLQ + u] = l_a(glx[u])
+    std::vector<double> LG((size_t)q * NGLQ);
+    for (int a = 0; a < q; ++a)
+        for (int u = 0; u < NGLQ; ++u) {
+            double v = 1.0;
+            for (int m = 0; m < q; ++m)
+                if (m != a) v *= (glx[u] - qx[m]) / (qx[a] - qx[m]);
+            LG[a * NGLQ + u] = v;
+        }
+    auto lag = [&](int a, int u) { return LG[a * NGLQ + u]; };
+    OpPool pool;
+    std::vector<double> buf;
+    // ---- P2M and L2P per level ----
+    std::vector<int> op_p2m(L + 1, -1), op_l2p(L + 1, -1);
+    for (int l = 2; l <= L; ++l) {
+        const double w = width(l);
+        buf.assign((size_t)P * qq, 0.0);
+        for (int v = 0; v < NGLQ; ++v)
+            for (int u = 0; u < NGLQ; ++u) {
+                const double X = 0.5 * w * glx[u], Y = 0.5 * w * glx[v];
+                const double wt = 0.25 * w * w * glw[u] * glw[v] * pref;
+                const double rho = std::hypot(X, Y), ph = std::atan2(Y, X);
+                for (int n = 0; n <= p; ++n) {
+                    const double f = h_in(n, k * rho) / Is[l][n] * wt;
+                    const double cr = f * std::cos(n * ph), ci = -f * std::sin(n * ph);
+                    for (int j = 0; j < qq; ++j) {
+                        const double lj = lag(j % q, u) * lag(j / q, v);
+                        if (n == 0)
+                            buf[j] += cr * lj;
+                        else {
+                            buf[(2 * n - 1) * qq + j] += cr * lj;
+                            buf[(2 * n) * qq + j] += ci * lj;
+                        }
+                    }
+                }
+            }
+        op_p2m[l] = pool.add(P, qq, buf.data());
+        buf.assign((size_t)qq * P, 0.0);
+        for (int i = 0; i < qq; ++i) {
+            const double X = 0.5 * w * qx[i % q], Y = 0.5 * w * qx[i / q];
+            const double r = std::hypot(X, Y), th = std::atan2(Y, X);
+            for (int n = 0; n <= p; ++n) {
+                const double b = h_in(n, k * r) / Is[l][n];
+                if (n == 0)
+                    buf[i * P] = b;
+                else {
+                    buf[i * P + 2 * n - 1] = 2 * b * std::cos(n * th);
+                    buf[i * P + 2 * n] = -2 * b * std::sin(n * th);
+                }
+            }
+        }
+        op_l2p[l] = pool.add(qq, P, buf.data());
+    }
+    // ---- M2M and L2L (child c at level l+1, parent at l) ----
+    std::vector<std::array<int, 4>> op_m2m(L + 1), op_l2l(L + 1);
+    for (int l = 2; l < L; ++l)
+        for (int c = 0; c < 4; ++c) {
+            const double h2 = 0.25 * width(l);
+            const std::complex<double> d((c & 1) ? h2 : -h2, (c & 2) ? h2 : -h2);
+            const double dr = std::abs(d), da = std::arg(d);
+            std::vector<double> Id(2 * p + 1);
+            for (int j = 0; j <= 2 * p; ++j) Id[j] = h_in(j, k * dr);
+            buf.assign((size_t)P * P, 0.0);
+            real_form(p,
+                      [&](int m, int n) {
+                          const int j = m - n;
+                          return Is[l + 1][std::abs(n)] * Id[std::abs(j)] * std::polar(1.0, -j * da) / Is[l][m];
+                      },
+                      buf.data());
+            op_m2m[l][c] = pool.add(P, P, buf.data());
+            real_form(p,
+                      [&](int m, int n) {
+                          const int j = n - m;
+                          return Is[l + 1][m] * Id[std::abs(j)] * std::polar(1.0, j * da) / Is[l][std::abs(n)];
+                      },
+                      buf.data());
+            op_l2l[l][c] = pool.add(P, P, buf.data());
+        }
+    // ---- configuration-keyed operators discovered from the lists ----
+    std::map<std::tuple<int, int, int, int>, int> near_key, m2l_key, m2p_key, p2l_key;
+    std::vector<NearCfg> near_cfg;
+    std::vector<int> near_level;
+    std::vector<Task> t_out, t_m2l, t_p2m;
+    std::vector<std::vector<Task>> t_m2m(L + 1), t_l2l(L + 1);
+    // relative centre offset (source minus target) from integer coordinates
+    auto rel = [&](int tb, int sb) {
+        const int lt = lev(tb), ls = lev(sb), f = std::max(lt, ls);
+        const double wf = width(f);
+        const double dx = ((2.0 * bx(sb) + 1) * (1 << (f - ls)) - (2.0 * bx(tb) + 1) * (1 << (f - lt))) * 0.5 * wf;
+        const double dy = ((2.0 * by(sb) + 1) * (1 << (f - ls)) - (2.0 * by(tb) + 1) * (1 << (f - lt))) * 0.5 * wf;
+        return std::complex<double>(dx, dy);
+    };
+    std::vector<double> Kb(2 * p + 2);
+    for (int64_t b = 0; b < nb; ++b) {
+        const int l = lev((int)b);
+        const int leaf = h.box_leaf[b];
+        // U list -> near tables
+        if (leaf >= 0) {
+            for (int j = h.off[0][b]; j < h.off[0][b + 1]; ++j) {
+                const int c = h.item[0][j];
+                const int lc = lev(c), f = std::max(l, lc);
+                const int ox = bx(c) * (1 << (f - lc)) - bx((int)b) * (1 << (f - l));
+                const int oy = by(c) * (1 << (f - lc)) - by((int)b) * (1 << (f - l));
+                auto key = std::make_tuple(l, lc - l, ox, oy);
+                auto it = near_key.find(key);
+                int id;
+                if (it == near_key.end()) {
+                    id = (int)near_cfg.size();
+                    near_key[key] = id;
+                    const std::complex<double> r = rel((int)b, c);
+                    near_cfg.push_back(NearCfg{r.real(), r.imag(), width(lc), width(l)});
+                    near_level.push_back(l);
+                } else {
+                    id = it->second;
+                }
+                t_out.push_back(Task{-1 - id, V->B_off + (int64_t)h.box_leaf[c] * qq, V->U_off + (int64_t)leaf * qq});
+            }
+            if (l >= 2) t_out.push_back(Task{op_l2p[l], V->L_off + b * P, V->U_off + (int64_t)leaf * qq});
+            // W list -> M2P
+            for (int j = h.off[2][b]; j < h.off[2][b + 1]; ++j) {
+                const int c = h.item[2][j];
+                auto key = std::make_tuple(l, bx(c) - 2 * bx((int)b), by(c) - 2 * by((int)b), 0);
+                auto it = m2p_key.find(key);
+                int id;
+                if (it == m2p_key.end()) {
+                    const std::complex<double> r = rel((int)b, c);   // source centre - target centre
+                    const double w = width(l);
+                    buf.assign((size_t)qq * P, 0.0);
+                    for (int i = 0; i < qq; ++i) {
+                        const std::complex<double> z =
+                            std::complex<double>(0.5 * w * qx[i % q], 0.5 * w * qx[i / q]) - r;
+                        const double rr = std::abs(z), th = std::arg(z);
+                        h_kn_all(k * rr, p, Kb.data());
+                        for (int n = 0; n <= p; ++n) {
+                            const double v = Is[l + 1][n] * Kb[n];
+                            if (n == 0)
+                                buf[i * P] = v;
+                            else {
+                                buf[i * P + 2 * n - 1] = 2 * v * std::cos(n * th);
+                                buf[i * P + 2 * n] = -2 * v * std::sin(n * th);
+                            }
+                        }
+                    }
+                    id = pool.add(qq, P, buf.data());
+                    m2p_key[key] = id;
+                } else {
+                    id = it->second;
+                }
+                t_out.push_back(Task{id, V->M_off + (int64_t)c * P, V->U_off + (int64_t)leaf * qq});
+            }
+            if (l >= 2) t_p2m.push_back(Task{op_p2m[l], V->B_off + (int64_t)leaf * qq, V->M_off + b * P});
+        }
+        if (l < 2) continue;
+        // V list -> M2L
+        for (int j = h.off[1][b]; j < h.off[1][b + 1]; ++j) {
+            const int s = h.item[1][j];
+            auto key = std::make_tuple(l, bx(s) - bx((int)b), by(s) - by((int)b), 0);
+            auto it = m2l_key.find(key);
+            int id;
+            if (it == m2l_key.end()) {
+                const std::complex<double> D = -rel((int)b, s);   // target centre - source centre
+                const double R = std::abs(D), Ph = std::arg(D);
+                h_kn_all(k * R, 2 * p, Kb.data());
+                buf.assign((size_t)P * P, 0.0);
+                real_form(p,
+                          [&](int m, int n) {
+                              const int jj = n - m;
+                              const double sg = (m & 1) ? -1.0 : 1.0;
+                              return Is[l][m] * sg * Kb[std::abs(jj)] * std::polar(1.0, jj * Ph) * Is[l][std::abs(n)];
+                          },
+                          buf.data());
+                id = pool.add(P, P, buf.data());
+                m2l_key[key] = id;
+            } else {
+                id = it->second;
+            }
+            t_m2l.push_back(Task{id, V->M_off + (int64_t)s * P, V->L_off + b * P});
+        }
+        // X list -> P2L
+        for (int j = h.off[3][b]; j < h.off[3][b + 1]; ++j) {
+            const int c = h.item[3][j];
+            auto key = std::make_tuple(l, 2 * bx(c) - bx((int)b), 2 * by(c) - by((int)b), 0);
+            auto it = p2l_key.find(key);
+            int id;
+            if (it == p2l_key.end()) {
+                const std::complex<double> r = rel((int)b, c);   // source centre - target centre
+                const double wc = width(l - 1);
+                buf.assign((size_t)P * qq, 0.0);
+                for (int v = 0; v < NGLQ; ++v)
+                    for (int u = 0; u < NGLQ; ++u) {
+                        const std::complex<double> uu =
+                            r + std::complex<double>(0.5 * wc * glx[u], 0.5 * wc * glx[v]);
+                        const double wt = 0.25 * wc * wc * glw[u] * glw[v] * pref;
+                        const double ru = std::abs(uu), au = std::arg(uu);
+                        h_kn_all(k * ru, p, Kb.data());
+                        for (int m = 0; m <= p; ++m) {
+                            const double f = Is[l][m] * Kb[m] * wt;
+                            const double cr = f * std::cos(m * au), ci = -f * std::sin(m * au);
+                            for (int jj = 0; jj < qq; ++jj) {
+                                const double lj = lag(jj % q, u) * lag(jj / q, v);
+                                if (m == 0)
+                                    buf[jj] += cr * lj;
+                                else {
+                                    buf[(2 * m - 1) * qq + jj] += cr * lj;
+                                    buf[(2 * m) * qq + jj] += ci * lj;
+                                }
+                            }
+                        }
+                    }
+                id = pool.add(P, qq, buf.data());
+                p2l_key[key] = id;
+            } else {
+                id = it->second;
+            }
+            t_m2l.push_back(Task{id, V->B_off + (int64_t)h.box_leaf[c] * qq, V->L_off + b * P});
+        }
+    }
+    // M2M / L2L tasks from the parent-child structure (children of internal boxes, level >= 2)
+    {
+        std::vector<int32_t> child(4 * nb);
+        MH_CUDA(ctx, cudaMemcpyAsync(child.data(), t->box_child.p, 4 * nb * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int64_t b = 0; b < nb; ++b) {
+            const int l = lev((int)b);
+            if (h.box_leaf[b] >= 0 || l < 2 || l >= L) continue;
+            for (int c = 0; c < 4; ++c) {
+                const int ch = child[4 * b + c];
+                if (ch < 0) continue;
+                t_m2m[l].push_back(Task{op_m2m[l][c], V->M_off + (int64_t)ch * P, V->M_off + b * P});
+                t_l2l[l].push_back(Task{op_l2l[l][c], V->L_off + b * P, V->L_off + (int64_t)ch * P});
+            }
+        }
+    }
+    // near tables on the device, appended to the pool
+    const int nnear = (int)near_cfg.size();
+    V->n_near_tables = nnear;
+    const int64_t near_base = (int64_t)pool.data.size();
+    const int first_near_op = (int)pool.off.size();
+    for (int i = 0; i < nnear; ++i) {
+        pool.off.push_back(near_base + (int64_t)i * qq * qq);
+        pool.R.push_back(qq);
+        pool.C.push_back(qq);
+    }
+    for (auto& tk : t_out)
+        if (tk.op < 0) tk.op = first_near_op + (-1 - tk.op);
+    const int64_t total = near_base + (int64_t)nnear * qq * qq;
+    MH_ALLOC(ctx, V->ops64, total);
+    cudaStream_t st = ctx->stream;
+    if (near_base) MH_CUDA(ctx, cudaMemcpyAsync(V->ops64.p, pool.data.data(), near_base * 8, cudaMemcpyHostToDevice, st));
+    if (nnear) {
+        dbuf<NearCfg> dcfg;
+        dbuf<double> dxi, dgx, dgw;
+        MH_ALLOC(ctx, dcfg, nnear);
+        MH_ALLOC(ctx, dxi, q);
+        MH_ALLOC(ctx, dgx, NGLN);
+        MH_ALLOC(ctx, dgw, NGLN);
+        MH_CUDA(ctx, cudaMemcpyAsync(dcfg.p, near_cfg.data(), nnear * sizeof(NearCfg), cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(dxi.p, qx.data(), q * 8, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(dgx.p, g16x.data(), NGLN * 8, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(dgw.p, g16w.data(), NGLN * 8, cudaMemcpyHostToDevice, st));
+        k_near_tables<<<(unsigned)(nnear * qq), 256, 0, st>>>(dcfg.p, q, dxi.p, dgx.p, dgw.p, k, pref,
+                                                              V->ops64.p + near_base);
+        MH_LAUNCHED(ctx);
+        MH_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    MH_ALLOC(ctx, V->ops32, total);
+    {
+        // binary32 copy of every operator (mixed precision)
+        std::vector<double> all(total);
+        MH_CUDA(ctx, cudaMemcpyAsync(all.data(), V->ops64.p, total * 8, cudaMemcpyDeviceToHost, st));
+        MH_CUDA(ctx, cudaStreamSynchronize(st));
+        std::vector<float> f(all.begin(), all.end());
+        MH_CUDA(ctx, cudaMemcpyAsync(V->ops32.p, f.data(), total * 4, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    V->op_C.assign(pool.C.begin(), pool.C.end());
+    MH_ALLOC(ctx, V->d_op_off, pool.off.size());
+    MH_ALLOC(ctx, V->d_op_C, pool.C.size());
+    MH_CUDA(ctx, cudaMemcpyAsync(V->d_op_off.p, pool.off.data(), pool.off.size() * 8, cudaMemcpyHostToDevice, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(V->d_op_C.p, pool.C.data(), pool.C.size() * 4, cudaMemcpyHostToDevice, st));
+    // phases
+    int64_t need = 1;
+    V->p2m.reset(new Phase());
+    MH_TRY(build_phase(ctx, t_p2m, P, false, V->op_C, V->p2m.get(), &need));
+    V->m2m.clear();
+    V->l2l.clear();
+    V->m2m.resize(L + 1);
+    V->l2l.resize(L + 1);
+    for (int l = 0; l <= L; ++l) {
+        V->m2m[l].reset(new Phase());
+        V->l2l[l].reset(new Phase());
+        MH_TRY(build_phase(ctx, t_m2m[l], P, false, V->op_C, V->m2m[l].get(), &need));
+        MH_TRY(build_phase(ctx, t_l2l[l], P, true, V->op_C, V->l2l[l].get(), &need));
+    }
+    V->m2l.reset(new Phase());
+    MH_TRY(build_phase(ctx, t_m2l, P, false, V->op_C, V->m2l.get(), &need));
+    V->out.reset(new Phase());
+    MH_TRY(build_phase(ctx, t_out, qq, false, V->op_C, V->out.get(), &need));
+    MH_ALLOC(ctx, V->vec, V->vec_len);
+    MH_ALLOC(ctx, V->temp, need);
+    V->temp_len = need;
+    MH_CUDA(ctx, cudaMemsetAsync(V->vec.p, 0, V->vec_len * 8, st));
+    // shared-memory opt-in for the contraction kernel
+    int maxs = 0;
+    for (auto* ph : {V->p2m.get(), V->m2l.get(), V->out.get()}) maxs = std::max(maxs, ph->smem);
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    return MH_OK;
+}
+
+}  // namespace
+
+void volume_free(mh_tree* t) {
+    delete static_cast<VolData*>(t->vol);
+    t->vol = nullptr;
+}
+
+template <typename TOP>
+static mh_status volume_run(mh_ctx* ctx, mh_tree* t, VolData* V, const TOP* ops) {
+    MH_TRY(run_phase(ctx, V, ops, V->p2m.get()));
+    for (int l = t->max_level - 1; l >= 2; --l) MH_TRY(run_phase(ctx, V, ops, V->m2m[l].get()));
+    MH_TRY(run_phase(ctx, V, ops, V->m2l.get()));
+    for (int l = 2; l < t->max_level; ++l) MH_TRY(run_phase(ctx, V, ops, V->l2l[l].get()));
+    MH_TRY(run_phase(ctx, V, ops, V->out.get()));
+    return MH_OK;
+}
+
+mh_status volume_apply(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* b, double* up,
+                       mh_precision prec) {
+    VolData* V = static_cast<VolData*>(t->vol);
+    if (!V || V->alpha != alpha || V->p != p) {
+        delete V;
+        V = new VolData();
+        t->vol = V;
+        mh_status s = volume_setup(ctx, t, alpha, p, V);
+        if (s != MH_OK) {
+            delete V;
+            t->vol = nullptr;
+            return s;
+        }
+    }
+    const int64_t nn = t->n_nodes;
+    MH_CUDA(ctx, cudaMemcpyAsync(V->vec.p + V->B_off, b, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (prec == MH_PREC_MIXED)
+        MH_TRY(volume_run<float>(ctx, t, V, V->ops32.p));
+    else
+        MH_TRY(volume_run<double>(ctx, t, V, V->ops64.p));
+    MH_CUDA(ctx, cudaMemcpyAsync(up, V->vec.p + V->U_off, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    return MH_OK;
+}
+
+extern "C" mh_status mh_volume_potential(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* b_dev,
+                                         double* up_dev, mh_precision prec) {
+    if (!ctx || !t || !b_dev || !up_dev) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    if (!(alpha > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "alpha must be positive");
+    if (p < 1 || p > 40) return mh_fail(ctx, MH_ERR_INVALID_ARG, "p must be in 1..40");
+    MH_TRY(volume_apply(ctx, t, alpha, p, b_dev, up_dev, prec));
+    MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return MH_OK;
+}

@@ -1,0 +1,79 @@
+"""GPU parity of heat_step (Section 2, IMEX Euler) against the oracle's step on the
+disk-with-hole workload (uniform level-4 tree, q = 4, dt = alpha^2 = 1e-2, N_Gamma = 256,
+N_D = 4096) with the manufactured solution: node classification must agree exactly,
+u after three steps to relative L2 <= 1e-10 in FP64 (GMRES tolerance 1e-12 on both
+sides) and <= 1e-6 in mixed precision."""
+import numpy as np
+import pytest
+
+import mh_workloads as W
+from oracle import bie, geometry as G, step as S, tree as T, volume as V
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mh():
+    import paper_1007_5335_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(mh):
+    return mh.Context(0)
+
+
+@pytest.fixture(scope="module")
+def oracle_c1():
+    wl = W.disk_with_hole()
+    curves = G.make_curves(wl.curves)
+    tr = T.build(wl.box, wl.q, wl.min_level, wl.max_level)
+    nodes = tr.nodes()
+    info = G.classify(curves, nodes)
+    bn = np.concatenate([c.nodes for c in curves])
+    bleaf = [tr.locate(p) for p in bn]
+    M = V.uniform_operator(wl.min_level, wl.box, wl.q, wl.alpha, order=[(b[1], b[2]) for b in tr.leaves])
+    A = bie.nystrom_matrix(curves, wl.alpha)
+    pb = S.Problem(curves, tr, wl.alpha, wl.dt, info, bleaf, A, ext_mode="array", volume_op=lambda b: M @ b,
+                   gmres_tol=1e-12, use_lu=True)
+    return wl, pb, nodes, bn
+
+
+def _run_oracle(wl, pb, nodes, bn, steps):
+    mf = W.Manufactured
+    u = mf.u(0.0, nodes)
+    t = 0.0
+    for _ in range(steps):
+        b_ext = mf.u(t, nodes) + wl.dt * mf.F(t, nodes)
+        u, sigma, _ = S.heat_step(pb, u, mf.F(t, nodes), mf.u(t + wl.dt, bn), b_ext=b_ext)
+        t += wl.dt
+    return u
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6)])
+def test_heat_step_matches_oracle(mh, ctx, oracle_c1, prec, tol):
+    wl, pb, nodes, bn = oracle_c1
+    gt = mh.Tree(ctx, wl.box, wl.q, wl.min_level, wl.max_level)
+    bnd = mh.Boundary(ctx, wl.curves, alpert_order=8)
+    prob = mh.Problem(ctx, gt, bnd, wl.dt, wl.p, ext_mode=mh.MH_EXT_ARRAY)
+    assert np.array_equal(prob.regions(), pb.info.region)
+    mf = W.Manufactured
+    dev = lambda a: torch.tensor(a, device="cuda")
+    u = dev(mf.u(0.0, nodes))
+    un = torch.empty_like(u)
+    sigma = torch.zeros(bnd.n, dtype=torch.float64, device="cuda")
+    t = 0.0
+    steps = 3
+    for _ in range(steps):
+        b_ext = dev(mf.u(t, nodes) + wl.dt * mf.F(t, nodes))
+        info = mh.heat_step(ctx, prob, u, dev(mf.F(t, nodes)), dev(mf.u(t + wl.dt, bn)), un, sigma, b_ext=b_ext,
+                            gmres_tol=1e-12, prec=prec)
+        u, un = un, u
+        t += wl.dt
+    ref = _run_oracle(wl, pb, nodes, bn, steps)
+    got = u.cpu().numpy()
+    inside = pb.inside
+    e = float(np.linalg.norm(got[inside] - ref[inside]) / np.linalg.norm(ref[inside]))
+    print(f"heat_step prec={prec}: rel L2 {e:.2e}, gmres its {info.gmres_iterations}")
+    assert e < tol
