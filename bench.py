@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the per-step heat solve (IMEX Euler, Section 2) on the starfish workload:
+unit disk minus 5 starfish holes (N_Gamma = 6 x 1024), adaptive quadtree to level 8 with
+8 x 8 nodes per leaf (N_D = 257,728), Gaussian-sum forcing, dt = alpha^2 = 1e-3, p = 20.
+
+One step = heat_step: B -> volume potential (adaptive multipole method) -> leaf
+interpolation onto Gamma -> GMRES on the Nystrom system (tol 1e-10) -> double layer at
+the nodes in Omega -> combine.  Metric: points * timesteps / s, points = N_D + N_Gamma.
+
+  python bench.py [--gpus N --steps K --warmup W] [--prec mixed|fp64] [--impl reference]
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the
+library's stream; between timed steps a 256 MB buffer is written (L2 flush, untimed).
+`e2e` repeats the K steps through the public API with host buffers: the step's inputs
+(u, F, f) are copied from pinned host memory and the result u^{N+1} is copied back
+inside the timed region.  With N > 1 (torchrun) every rank runs its own replica of the
+problem (the single-problem path does not shard), the time is the max over ranks and
+the value sums the points of all ranks.  --impl reference times the CPU oracle on a
+bounded sample of the same workload (rank 0 only).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import mh_workloads as W  # noqa: E402
+
+METRIC = "points*timesteps/s per GB300 at rel-L2 err<=1e-6 vs FP64 oracle; % of roofline"
+FP64_PEAK_TFLOPS = 1.25     # nominal GB300 binary64 rate (all pipes)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.device), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def setup_problem(mh, ctx, wl, torch, dev):
+    t0 = time.time()
+    tree = mh.Tree(ctx, wl.box, wl.q, wl.min_level, wl.max_level, wl.forcing, wl.refine_tol)
+    bnd = mh.Boundary(ctx, wl.curves, alpert_order=8)
+    prob = mh.Problem(ctx, tree, bnd, wl.dt, wl.p, ext_mode=mh.MH_EXT_CONST, ext_const=wl.ext_const)
+    torch.cuda.synchronize(dev)
+    nodes = tree.nodes().cpu().numpy()
+    F = wl.forcing(nodes)
+    return tree, bnd, prob, nodes, F, time.time() - t0
+
+
+def run_ours(args):
+    import torch
+    import paper_1007_5335_gb300 as mh
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    wl = W.starfish_domain()
+    prec = mh.MH_PREC_MIXED if args.prec == "mixed" else mh.MH_PREC_FP64
+    ctx = mh.Context(local)
+    tree, bnd, prob, nodes, F_np, t_setup = setup_problem(mh, ctx, wl, torch, dev)
+    n_pts = tree.n_nodes + bnd.n
+    F = torch.tensor(F_np, device=dev)
+    f_next = torch.zeros(bnd.n, dtype=torch.float64, device=dev)     # f = 0 on every curve
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def run_steps(k, u, sigma, timed, prec_):
+        un = torch.empty_like(u)
+        times, its = [], []
+        for _ in range(k):
+            if timed:
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+            info = mh.heat_step(ctx, prob, u, F, f_next, un, sigma, gmres_tol=1e-10, prec=prec_)
+            if timed:
+                b.record()
+                b.synchronize()
+                times.append(a.elapsed_time(b))
+            its.append(info.gmres_iterations)
+            u, un = un, u
+        return u, times, its
+
+    # accuracy of the headline precision against the FP64 path (same steps from u = 0)
+    u0 = torch.zeros(tree.n_nodes, dtype=torch.float64, device=dev)
+    err = None
+    if prec == mh.MH_PREC_MIXED and args.check_steps > 0:
+        s64 = torch.zeros(bnd.n, dtype=torch.float64, device=dev)
+        s32 = torch.zeros(bnd.n, dtype=torch.float64, device=dev)
+        u64, _, _ = run_steps(args.check_steps, u0.clone(), s64, False, mh.MH_PREC_FP64)
+        u32, _, _ = run_steps(args.check_steps, u0.clone(), s32, False, mh.MH_PREC_MIXED)
+        regions = prob.regions()
+        ins = torch.tensor(regions == -1, device=dev)
+        err = float(torch.linalg.norm((u32 - u64)[ins]) / torch.linalg.norm(u64[ins]))
+
+    sigma = torch.zeros(bnd.n, dtype=torch.float64, device=dev)
+    u, _, _ = run_steps(args.warmup, u0.clone(), sigma, False, prec)
+    ctx.profile(True)
+    ctx.profile_read("gmres", reset=True)
+    launches0 = ctx.launches
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        u, times, its = run_steps(args.steps, u, sigma, True, prec)
+    torch.cuda.synchronize(dev)
+    launches = ctx.launches - launches0
+    regions_ms = {}
+    for r in ("dlp_coarse", "dlp_fine", "bie_gemv", "volume_contract", "volume_apply", "gmres", "dlp_evaluate"):
+        regions_ms[r] = ctx.profile_read(r)
+    ctx.profile(False)
+    total_ms = float(sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # end to end through the API with host buffers
+    pin = lambda a: torch.tensor(a).pin_memory()
+    u_h = pin(u.cpu().numpy())
+    F_h = pin(F_np)
+    f_h = pin(np.zeros(bnd.n))
+    out_h = torch.empty(tree.n_nodes, dtype=torch.float64).pin_memory()
+    ud = torch.empty_like(u)
+    Fd = torch.empty_like(F)
+    fd = torch.empty_like(f_next)
+    und = torch.empty_like(u)
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        ud.copy_(u_h, non_blocking=True)
+        Fd.copy_(F_h, non_blocking=True)
+        fd.copy_(f_h, non_blocking=True)
+        mh.heat_step(ctx, prob, ud, Fd, fd, und, sigma, gmres_tol=1e-10, prec=prec)
+        out_h.copy_(und, non_blocking=True)
+        b.record()
+        b.synchronize()
+        e2e_times.append(a.elapsed_time(b))
+        u_h.copy_(out_h)
+    e2e_ms = float(sum(e2e_times))
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    bytes_in = (2 * tree.n_nodes + bnd.n) * 8
+    bytes_out = tree.n_nodes * 8
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    value = n_pts * args.steps * world / (total_ms / 1e3)
+    e2e_value = n_pts * args.steps * world / (e2e_ms / 1e3)
+    peaks = _peaks()
+    roof = roofline(regions_ms, tree, bnd, prob, prec, mh, peaks, args.steps)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "points*timesteps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64" if prec == mh.MH_PREC_MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": "starfish_domain: unit disk minus 5 starfish holes, N_Gamma=6144, "
+                               "N_D=%d (adaptive tree levels 4-8, 8x8 GL nodes per leaf), dt=alpha^2=1e-3, p=20, "
+                               "IMEX Euler, GMRES tol 1e-10" % tree.n_nodes,
+                   "points": n_pts, "n_gamma": bnd.n, "n_d": tree.n_nodes, "precision": args.prec,
+                   "l2": "flushed between timed steps (256 MB write, untimed)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "rel_l2_vs_fp64_path": err,
+        "gmres_iterations": its,
+        "setup_s": t_setup,
+        "e2e": {"value": e2e_value, "unit": "points*timesteps/s", "h2d_bytes_per_step": bytes_in,
+                "d2h_bytes_per_step": bytes_out},
+        "gpu_launches": launches,
+        "regions_ms_per_step": {k: v[0] / args.steps for k, v in regions_ms.items()},
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def roofline(regions_ms, tree, bnd, prob, prec, mh, peaks, steps):
+    """Roofline of the dominant instrumented kernel region."""
+    cand = {k: v for k, v in regions_ms.items() if k in ("dlp_coarse", "bie_gemv", "volume_contract", "dlp_fine")}
+    name = max(cand, key=lambda k: cand[k][0])
+    ms, launches = cand[name]
+    avg_s = ms / max(launches, 1) / 1e3
+    n = bnd.n
+    if name == "bie_gemv":
+        elt = 4 if prec == mh.MH_PREC_MIXED else 8
+        work = n * n * elt + 2 * n * 8           # operator + x + y bytes per launch
+        achieved = work / avg_s / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": launches,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    if name in ("dlp_coarse", "dlp_fine"):
+        # pair interactions x 2 x (FMA-equivalent operations of one double-layer kernel value)
+        pairs = prob_inside(prob) * n if name == "dlp_coarse" else None
+        flops_per_pair = 2 * 34
+        if pairs is None:
+            return {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+                    "traffic": None}
+        achieved = pairs * flops_per_pair / avg_s / 1e12
+        peak = FP32_PEAK_TFLOPS if prec == mh.MH_PREC_MIXED else FP64_PEAK_TFLOPS
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": launches,
+                "pairs_per_launch": pairs, "flops_per_pair": flops_per_pair,
+                "peak_source": "nominal: binary64 1.25 TFLOP/s; binary32 152 SM x 128 lanes x 2 x 2.07 GHz"}
+    return {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+            "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": launches}
+
+
+def prob_inside(prob):
+    r = prob.regions()
+    return int(np.sum(r == -1))
+
+
+def cpu_baseline(wl, budget_s=20.0, seed=11):
+    """The oracle as it stands, on a bounded sample of one step of the workload: the
+    volume potential and the double layer at sampled nodes, and sampled rows of the
+    Nystrom matrix; extrapolated to one full step (N_D targets, N_Gamma rows, dense solve)."""
+    from oracle import bie, geometry as G, tree as T, volume as V
+    t_start = time.time()
+    curves = G.make_curves(wl.curves)
+    tr = T.build(wl.box, wl.q, wl.min_level, wl.max_level, wl.forcing, wl.refine_tol)
+    nodes = tr.nodes()
+    leaves = tr.leaf_array()
+    rng = np.random.default_rng(seed)
+    B = wl.forcing(nodes) * wl.dt
+    ntot = nodes.shape[0]
+    # per-target volume potential cost
+    t0 = time.time()
+    nv = 0
+    while time.time() - t0 < 0.45 * budget_s and nv < 64:
+        i = rng.integers(ntot)
+        V.volume_potential(leaves, B.reshape(len(leaves), -1), wl.q, wl.alpha, nodes[i:i + 1])
+        nv += 1
+    t_vol = (time.time() - t0) / nv
+    # per-row Nystrom assembly cost
+    t0 = time.time()
+    rows = np.sort(rng.choice(sum(c.n for c in curves), 16, replace=False))
+    R = bie.nystrom_matrix(curves, wl.alpha, rows=rows)
+    t_row = (time.time() - t0) / len(rows)
+    # dense solve cost (LU of an N_Gamma x N_Gamma matrix)
+    n = R.shape[1]
+    M = np.eye(n) + 1e-3 * rng.standard_normal((n, n))
+    t0 = time.time()
+    np.linalg.solve(M, rng.standard_normal(n))
+    t_solve = time.time() - t0
+    # per-target double-layer cost
+    sig = rng.standard_normal(n)
+    inside = [i for i in rng.choice(ntot, 64, replace=False)]
+    info = G.classify(curves, nodes[inside])
+    ins = [k for k, i in enumerate(inside) if info.region[k] == -1][:16]
+    t0 = time.time()
+    sub = G.classify(curves, nodes[[inside[k] for k in ins]])
+    bie.dlp_eval(curves, sig, wl.alpha, nodes[[inside[k] for k in ins]], sub, None)
+    t_dlp = (time.time() - t0) / max(len(ins), 1)
+    t_step = ntot * (t_vol + t_dlp) + n * t_row + t_solve
+    # the oracle's per-target loops run in one thread; only the dense solve uses BLAS threads
+    blas = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": (ntot + n) / t_step, "unit": "points*timesteps/s", "cores": 1, "blas_threads": blas,
+            "kind": "oracle",
+            "sample": f"{nv} volume targets, {len(ins)} double-layer targets, {len(rows)} Nystrom rows, one "
+                      f"{n}x{n} dense solve; extrapolated to one step ({ntot} targets, {n} rows)",
+            "seconds_per_step_extrapolated": t_step, "wall_s": time.time() - t_start}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = W.starfish_domain()
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    budget = max(2.0, min(8.0, 150.0 / max(args.steps + args.warmup, 1)))
+    for _ in range(args.warmup):
+        cpu_baseline(wl, budget_s=budget, seed=100)
+    for s in range(args.steps):
+        vals.append(cpu_baseline(wl, budget_s=budget, seed=200 + s))
+    value = float(np.mean([v["value"] for v in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points*timesteps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "starfish_domain (as the GPU arm), oracle on a bounded sample per step"},
+            "cpu_baseline": {"value": value, "unit": "points*timesteps/s", "cores": vals[0]["cores"],
+                             "kind": "oracle", "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": "points*timesteps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--check-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

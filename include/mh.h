@@ -89,6 +89,15 @@ const char* mh_last_error(const mh_ctx* ctx);
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t mh_kernel_launches(const mh_ctx* ctx);
 
+/* Timing of named kernel regions (library instrumentation, no counterpart in the paper).
+ * When enabled, the library records a CUDA event pair on its stream around each launch
+ * of the instrumented kernels: "dlp_coarse", "dlp_fine", "bie_gemv", "volume_apply",
+ * "volume_contract", "gmres", "dlp_evaluate".  mh_profile_read synchronises the stream
+ * and returns the summed event time (ms) and number of timed launches of `region`
+ * since the last reset; reset != 0 clears all regions afterwards. */
+mh_status mh_profile_enable(mh_ctx* ctx, int on);
+mh_status mh_profile_read(mh_ctx* ctx, const char* region, double* total_ms, int64_t* launches, int reset);
+
 /* ---- boundary (Section 3.2) -------------------------------------------------------- */
 
 /* Build the boundary from node coordinates xy_host[2 N_Gamma] (curves concatenated,

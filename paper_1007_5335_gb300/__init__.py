@@ -64,6 +64,8 @@ _SIGS = {
     "mh_problem_destroy": [_p],
     "mh_problem_regions": [_p, _p, _p],
     "heat_step": [_p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
+    "mh_profile_enable": [_p, _i],
+    "mh_profile_read": [_p, ctypes.c_char_p, ctypes.POINTER(_d), ctypes.POINTER(_i64), _i],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -108,6 +110,16 @@ class Context:
     @property
     def launches(self) -> int:
         return int(_lib.mh_kernel_launches(self.h))
+
+    def profile(self, on: bool = True):
+        """mh_profile_enable: time the instrumented kernel regions with CUDA events."""
+        self.check(_lib.mh_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self, region: str, reset: bool = False):
+        """mh_profile_read -> (total_ms, launches) of a named region."""
+        ms, n = _d(), _i64()
+        self.check(_lib.mh_profile_read(self.h, region.encode(), ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0))
+        return ms.value, n.value
 
     def __del__(self):
         if getattr(self, "h", None):

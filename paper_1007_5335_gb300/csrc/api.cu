@@ -35,3 +35,53 @@ extern "C" mh_status mh_destroy(mh_ctx* ctx) {
 extern "C" const char* mh_last_error(const mh_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 extern "C" int64_t mh_kernel_launches(const mh_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+mh_ctx::~mh_ctx() {
+    for (auto& kv : prof)
+        for (auto& e : kv.second.pending) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+}
+
+prof_scope::prof_scope(mh_ctx* c, const char* n) : ctx(c), name(n) {
+    if (!ctx || !ctx->profiling) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        a = b = nullptr;
+        return;
+    }
+    cudaEventRecord(a, ctx->stream);
+}
+
+prof_scope::~prof_scope() {
+    if (!a) return;
+    cudaEventRecord(b, ctx->stream);
+    ctx->prof[name].pending.emplace_back(a, b);
+}
+
+extern "C" mh_status mh_profile_enable(mh_ctx* ctx, int on) {
+    if (!ctx) return MH_ERR_INVALID_ARG;
+    ctx->profiling = on != 0;
+    return MH_OK;
+}
+
+extern "C" mh_status mh_profile_read(mh_ctx* ctx, const char* region, double* total_ms, int64_t* launches,
+                                     int reset) {
+    if (!ctx || !region) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto& kv : ctx->prof) {
+        for (auto& e : kv.second.pending) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) kv.second.total_ms += ms;
+            kv.second.launches++;
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+        kv.second.pending.clear();
+    }
+    auto it = ctx->prof.find(region);
+    if (total_ms) *total_ms = it == ctx->prof.end() ? 0.0 : it->second.total_ms;
+    if (launches) *launches = it == ctx->prof.end() ? 0 : it->second.launches;
+    if (reset) ctx->prof.clear();
+    return MH_OK;
+}

@@ -267,23 +267,197 @@ __global__ void k_gemv64(const double* __restrict__ A, const double* __restrict_
     }
 }
 
-__global__ void k_gemv32(const float* __restrict__ A, const double* __restrict__ x, double* __restrict__ y,
+// binary32 operator times a binary32 copy of x (converted once per call: conversions
+// from binary64 run on the slow FP64 pipe of this part and must stay out of the loop).
+__global__ void k_gemv32(const float* __restrict__ A, const float* __restrict__ x, double* __restrict__ y,
                          int64_t n) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < n; row += nwarps) {
         const float2* a = reinterpret_cast<const float2*>(A + row * n);
-        const double2* xv = reinterpret_cast<const double2*>(x);
-        float acc = 0.f;
+        const float2* xv = reinterpret_cast<const float2*>(x);
+        float acc0 = 0.f, acc1 = 0.f;
         for (int64_t c = lane; c < n / 2; c += 32) {
             float2 av = __ldcs(a + c);
-            double2 xx = __ldg(xv + c);
-            acc = fmaf(av.x, (float)xx.x, acc);
-            acc = fmaf(av.y, (float)xx.y, acc);
+            float2 xx = __ldg(xv + c);
+            acc0 = fmaf(av.x, xx.x, acc0);
+            acc1 = fmaf(av.y, xx.y, acc1);
         }
-        double d = warp_sum((double)acc);
-        if (lane == 0) y[row] = d;
+        float f = acc0 + acc1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        if (lane == 0) y[row] = (double)f;
     }
+}
+
+__global__ void k_to_float_vec(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+// ---------------- binary32 double layer (mixed precision) ----------------
+
+// Source data relative to tile centres: tiles of MH_TILE consecutive nodes.
+__global__ void k_prep_src32(const double* __restrict__ geo, int64_t n, float4* src, double2* tc) {
+    const int64_t tile = blockIdx.x;
+    const int64_t s0 = tile * MH_TILE;
+    const int cnt = (n - s0) < MH_TILE ? (int)(n - s0) : MH_TILE;
+    __shared__ double cx, cy;
+    if (threadIdx.x == 0) {
+        double ax = 0, ay = 0;
+        for (int i = 0; i < cnt; ++i) {
+            ax += geo[8 * (s0 + i)];
+            ay += geo[8 * (s0 + i) + 1];
+        }
+        cx = ax / cnt;
+        cy = ay / cnt;
+        tc[tile] = make_double2(cx, cy);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const double* g = geo + 8 * (s0 + i);
+        const double sp = g[6];
+        src[s0 + i] = make_float4((float)(g[0] - cx), (float)(g[1] - cy), (float)(g[3] / sp), (float)(-g[2] / sp));
+    }
+}
+
+// Fine nodes relative to chunk centres: chunks of MH_TILE fine nodes inside each curve.
+__global__ void k_prep_fine32(const double* __restrict__ fg, const int64_t* __restrict__ foff,
+                              const int64_t* __restrict__ coff, int ncurves, float4* out, double2* cc) {
+    const int64_t chunk = blockIdx.x;
+    int k = 0;
+    while (k + 1 < ncurves && chunk >= coff[k + 1]) ++k;
+    const int64_t f0 = foff[k] + (chunk - coff[k]) * MH_TILE;
+    const int cnt = (foff[k + 1] - f0) < MH_TILE ? (int)(foff[k + 1] - f0) : MH_TILE;
+    __shared__ double cx, cy;
+    if (threadIdx.x == 0) {
+        double ax = 0, ay = 0;
+        for (int i = 0; i < cnt; ++i) {
+            ax += fg[6 * (f0 + i)];
+            ay += fg[6 * (f0 + i) + 1];
+        }
+        cx = ax / cnt;
+        cy = ay / cnt;
+        cc[chunk] = make_double2(cx, cy);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const double* g = fg + 6 * (f0 + i);
+        out[f0 + i] = make_float4((float)(g[0] - cx), (float)(g[1] - cy), (float)g[2], (float)g[3]);
+    }
+}
+
+__global__ void k_weights32(const double* __restrict__ sigma, const double* __restrict__ geo,
+                            const int32_t* __restrict__ curve_of, const int32_t* __restrict__ nn, int64_t n, float* w) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s < n) w[s] = (float)(sigma[s] * geo[8 * s + 6] * (2.0 * MH_PI / nn[curve_of[s]]));
+}
+
+// (1/alpha) K1(r/alpha) (y-x).n / r in binary32 from offsets d = y - x
+__device__ __forceinline__ float dl_kernel32(float dx, float dy, float nx, float ny, float inv_alpha) {
+    const float r2 = dx * dx + dy * dy;
+    const float rinv = rsqrtf(r2);
+    const float z = r2 * rinv * inv_alpha;
+    return mh_k1f(z) * inv_alpha * (dx * nx + dy * ny) * rinv;
+}
+
+// Coarse trapezoid sum in binary32: sources staged through shared memory in tiles of
+// MH_TILE; the target offset from the tile centre is formed once per tile in binary64;
+// per-tile partial sums are added in binary64.
+__global__ void __launch_bounds__(MH_TILE) k_dlp_coarse32(const double* __restrict__ xy,
+                                                          const uint32_t* __restrict__ fine, int64_t nt,
+                                                          const float4* __restrict__ src, const float* __restrict__ w,
+                                                          const int32_t* __restrict__ curve_of,
+                                                          const double2* __restrict__ tc, int64_t ns, float inv_alpha,
+                                                          double pref, double* out) {
+    __shared__ float4 s4[MH_TILE];
+    __shared__ float sw[MH_TILE];
+    __shared__ int sk[MH_TILE];
+    const int64_t t = blockIdx.x * (int64_t)MH_TILE + threadIdx.x;
+    const bool active = t < nt;
+    const double px = active ? xy[2 * t] : 0.0, py = active ? xy[2 * t + 1] : 0.0;
+    const uint32_t mask = active ? fine[t] : 0xffffffffu;
+    double acc = 0.0;
+    const int64_t ntile = (ns + MH_TILE - 1) / MH_TILE;
+    for (int64_t tile = 0; tile < ntile; ++tile) {
+        const int64_t s = tile * MH_TILE + threadIdx.x;
+        if (s < ns) {
+            s4[threadIdx.x] = src[s];
+            sw[threadIdx.x] = w[s];
+            sk[threadIdx.x] = curve_of[s];
+        }
+        __syncthreads();
+        const int cnt = (ns - tile * MH_TILE) < MH_TILE ? (int)(ns - tile * MH_TILE) : MH_TILE;
+        if (active) {
+            const double2 c = tc[tile];
+            const float tx = (float)(px - c.x), ty = (float)(py - c.y);
+            float part = 0.f;
+            for (int i = 0; i < cnt; ++i) {
+                if ((mask >> sk[i]) & 1u) continue;
+                const float4 v = s4[i];
+                part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha) * sw[i];
+            }
+            acc += (double)part;
+        }
+        __syncthreads();
+    }
+    if (active) out[t] = pref * acc;
+}
+
+// Density on the fine grid times |y'| h_f in binary32 (coefficients given in binary32).
+__global__ void k_fine_density32(const float* __restrict__ sc, const double* __restrict__ fg,
+                                 const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
+                                 const int64_t* __restrict__ foff, int ncurves, int64_t nfine, float* wf) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= nfine) return;
+    int k = 0;
+    while (k + 1 < ncurves && g >= foff[k + 1]) ++k;
+    const int N = nn[k];
+    const int NF = UPSAMPLE * N;
+    const int f = (int)(g - foff[k]);
+    const float* c = sc + 2 * coef_base(off, k);
+    float v = c[0];
+    for (int m = 1; m < N / 2; ++m) {
+        const int r = (int)(((int64_t)m * f) % NF);
+        float sn, cs;
+        sincospif(2.0f * (float)r / (float)NF, &sn, &cs);
+        v += 2.f * (c[2 * m] * cs - c[2 * m + 1] * sn);
+    }
+    {
+        const int r = (int)(((int64_t)(N / 2) * f) % NF);
+        v += c[N] * cospif(2.0f * (float)r / (float)NF);
+    }
+    wf[g] = v * (float)(fg[6 * g + 4] * fg[6 * g + 5]);
+}
+
+// Upsampled rule in binary32, one warp per (target, curve) pair, fine nodes in chunks of
+// MH_TILE with binary64 chunk centres.
+__global__ void k_dlp_fine32(const double* __restrict__ xy, const int32_t* __restrict__ ptgt,
+                             const int32_t* __restrict__ pcurve, int64_t npairs, const float4* __restrict__ fine32,
+                             const float* __restrict__ wf, const int64_t* __restrict__ foff,
+                             const int64_t* __restrict__ coff, const double2* __restrict__ cc, float inv_alpha,
+                             double pref, double* out) {
+    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (p >= npairs) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ptgt[p];
+    const int k = pcurve[p];
+    const double px = xy[2 * t], py = xy[2 * t + 1];
+    double acc = 0.0;
+    for (int64_t ch = coff[k]; ch < coff[k + 1]; ++ch) {
+        const double2 c = cc[ch];
+        const float tx = (float)(px - c.x), ty = (float)(py - c.y);
+        const int64_t f0 = foff[k] + (ch - coff[k]) * MH_TILE;
+        const int64_t f1 = min(f0 + MH_TILE, foff[k + 1]);
+        float part = 0.f;
+        for (int64_t f = f0 + lane; f < f1; f += 32) {
+            const float4 v = fine32[f];
+            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha) * wf[f];
+        }
+        acc += (double)part;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) atomicAdd(out + t, pref * acc);
 }
 
 // ---------------- GMRES helpers (binary64 Arnoldi) ----------------
@@ -827,8 +1001,13 @@ static int gemv_blocks(int64_t n) {
 mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec) {
     if (prec == MH_PREC_MIXED) {
         MH_TRY(ensure_fp32(ctx, b));
-        k_gemv32<<<gemv_blocks(b->n), 256, 0, ctx->stream>>>(b->op.A32.p, x, y, b->n);
+        if (!b->x32.p) MH_ALLOC(ctx, b->x32, b->n);
+        k_to_float_vec<<<mh_grid(b->n, 256), 256, 0, ctx->stream>>>(x, b->x32.p, b->n);
+        MH_LAUNCHED(ctx);
+        prof_scope ps(ctx, "bie_gemv");
+        k_gemv32<<<gemv_blocks(b->n), 256, 0, ctx->stream>>>(b->op.A32.p, b->x32.p, y, b->n);
     } else {
+        prof_scope ps(ctx, "bie_gemv");
         k_gemv64<<<gemv_blocks(b->n), 256, 0, ctx->stream>>>(b->op.A64.p, x, y, b->n);
     }
     MH_LAUNCHED(ctx);
@@ -902,6 +1081,7 @@ static mh_status gmres_core(mh_ctx* ctx, mh_boundary* bd, gmres_ws& ws, const do
 
 mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, double tol, int max_iter,
                     mh_precision prec, mh_gmres_info* info) {
+    prof_scope ps_all(ctx, "gmres");
     const int64_t n = bd->n;
     if (max_iter < 1 || max_iter > 1000) return mh_fail(ctx, MH_ERR_INVALID_ARG, "max_iter must be in 1..1000");
     gmres_ws& ws = bd->ws;
@@ -1053,9 +1233,35 @@ mh_status dlp_classify(mh_ctx* ctx, mh_boundary* b, const double* xy_dev, int64_
     return MH_OK;
 }
 
+// binary32 source tables of the mixed-precision double layer (built once per boundary)
+static mh_status prep_mixed(mh_ctx* ctx, mh_boundary* b) {
+    if (b->src32.p) return MH_OK;
+    cudaStream_t st = ctx->stream;
+    b->n_tiles = (b->n + MH_TILE - 1) / MH_TILE;
+    MH_ALLOC(ctx, b->src32, b->n);
+    MH_ALLOC(ctx, b->tile_c, b->n_tiles);
+    MH_ALLOC(ctx, b->w32, b->n);
+    k_prep_src32<<<(unsigned)b->n_tiles, 128, 0, st>>>(b->geo.p, b->n, b->src32.p, b->tile_c.p);
+    MH_LAUNCHED(ctx);
+    b->fchunk_off.assign(b->n_curves + 1, 0);
+    for (int k = 0; k < b->n_curves; ++k)
+        b->fchunk_off[k + 1] = b->fchunk_off[k] + (b->fine_off[k + 1] - b->fine_off[k] + MH_TILE - 1) / MH_TILE;
+    b->n_fchunks = b->fchunk_off[b->n_curves];
+    MH_ALLOC(ctx, b->d_fchunk_off, b->n_curves + 1);
+    MH_ALLOC(ctx, b->fine32, b->n_fine);
+    MH_ALLOC(ctx, b->fchunk_c, b->n_fchunks);
+    MH_ALLOC(ctx, b->wf32, b->n_fine);
+    MH_CUDA(ctx, cudaMemcpyAsync(b->d_fchunk_off.p, b->fchunk_off.data(), (b->n_curves + 1) * 8,
+                                 cudaMemcpyHostToDevice, st));
+    k_prep_fine32<<<(unsigned)b->n_fchunks, 128, 0, st>>>(b->fine_geo.p, b->d_fine_off.p, b->d_fchunk_off.p,
+                                                          b->n_curves, b->fine32.p, b->fchunk_c.p);
+    MH_LAUNCHED(ctx);
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
+    return MH_OK;
+}
+
 mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* tg, const double* sigma,
                        double* out, mh_precision prec) {
-    (void)prec;
     cudaStream_t st = ctx->stream;
     MH_TRY(bie_assemble(ctx, b, alpha));
     const double pref = -1.0 / (2.0 * MH_PI * alpha * alpha);
@@ -1063,24 +1269,57 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
     dbuf<double>& sc = tg->sc;
     dbuf<double>& wf = tg->wf;
     dbuf<double>& asig = tg->asig;
-    if (tg->n_ext) {
-        k_dlp_coarse<128><<<mh_grid(tg->n_ext, 128), 128, 0, st>>>(tg->xy.p, tg->fine.p, tg->n_ext, b->geo.p, sigma,
-                                                                   b->d_curve_of.p, b->d_nn.p, b->n, 1.0 / alpha,
-                                                                   pref, ext.p);
+    prof_scope ps_all(ctx, "dlp_evaluate");
+    const int64_t nmodes = b->n / 2 + b->n_curves;
+    if (prec == MH_PREC_MIXED) {
+        MH_TRY(prep_mixed(ctx, b));
+        k_weights32<<<mh_grid(b->n, 256), 256, 0, st>>>(sigma, b->geo.p, b->d_curve_of.p, b->d_nn.p, b->n, b->w32.p);
         MH_LAUNCHED(ctx);
-    }
-    if (tg->n_pairs) {
-        const int64_t nmodes = b->n / 2 + b->n_curves;
-        k_fourier_scalar<<<mh_grid(nmodes, 128), 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->n_curves, nmodes,
-                                                               sc.p);
-        MH_LAUNCHED(ctx);
-        k_fine_density<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(sc.p, b->fine_geo.p, b->d_nn.p, b->d_off.p,
-                                                                 b->d_fine_off.p, b->n_curves, b->n_fine, wf.p);
-        MH_LAUNCHED(ctx);
-        k_dlp_fine<<<mh_grid(tg->n_pairs * 32, 256), 256, 0, st>>>(tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p,
-                                                                   tg->n_pairs, b->fine_geo.p, wf.p, b->d_fine_off.p,
-                                                                   1.0 / alpha, pref, ext.p);
-        MH_LAUNCHED(ctx);
+        if (tg->n_ext) {
+            prof_scope ps(ctx, "dlp_coarse");
+            k_dlp_coarse32<<<mh_grid(tg->n_ext, MH_TILE), MH_TILE, 0, st>>>(
+                tg->xy.p, tg->fine.p, tg->n_ext, b->src32.p, b->w32.p, b->d_curve_of.p, b->tile_c.p, b->n,
+                (float)(1.0 / alpha), pref, ext.p);
+            MH_LAUNCHED(ctx);
+        }
+        if (tg->n_pairs) {
+            k_fourier_scalar<<<mh_grid(nmodes, 128), 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->n_curves, nmodes,
+                                                                   sc.p);
+            MH_LAUNCHED(ctx);
+            float* sc32 = reinterpret_cast<float*>(tg->wf.p);   // 2*nmodes floats fit in the binary64 buffer
+            k_to_float_vec<<<mh_grid(2 * nmodes, 256), 256, 0, st>>>(sc.p, sc32, 2 * nmodes);
+            MH_LAUNCHED(ctx);
+            k_fine_density32<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(sc32, b->fine_geo.p, b->d_nn.p, b->d_off.p,
+                                                                      b->d_fine_off.p, b->n_curves, b->n_fine,
+                                                                      b->wf32.p);
+            MH_LAUNCHED(ctx);
+            prof_scope ps(ctx, "dlp_fine");
+            k_dlp_fine32<<<mh_grid(tg->n_pairs * 32, 256), 256, 0, st>>>(
+                tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p, tg->n_pairs, b->fine32.p, b->wf32.p, b->d_fine_off.p,
+                b->d_fchunk_off.p, b->fchunk_c.p, (float)(1.0 / alpha), pref, ext.p);
+            MH_LAUNCHED(ctx);
+        }
+    } else {
+        if (tg->n_ext) {
+            prof_scope ps(ctx, "dlp_coarse");
+            k_dlp_coarse<128><<<mh_grid(tg->n_ext, 128), 128, 0, st>>>(tg->xy.p, tg->fine.p, tg->n_ext, b->geo.p,
+                                                                       sigma, b->d_curve_of.p, b->d_nn.p, b->n,
+                                                                       1.0 / alpha, pref, ext.p);
+            MH_LAUNCHED(ctx);
+        }
+        if (tg->n_pairs) {
+            k_fourier_scalar<<<mh_grid(nmodes, 128), 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->n_curves, nmodes,
+                                                                   sc.p);
+            MH_LAUNCHED(ctx);
+            k_fine_density<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(sc.p, b->fine_geo.p, b->d_nn.p, b->d_off.p,
+                                                                     b->d_fine_off.p, b->n_curves, b->n_fine, wf.p);
+            MH_LAUNCHED(ctx);
+            prof_scope ps(ctx, "dlp_fine");
+            k_dlp_fine<<<mh_grid(tg->n_pairs * 32, 256), 256, 0, st>>>(tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p,
+                                                                       tg->n_pairs, b->fine_geo.p, wf.p,
+                                                                       b->d_fine_off.p, 1.0 / alpha, pref, ext.p);
+            MH_LAUNCHED(ctx);
+        }
     }
     if (tg->n_line) {
         MH_TRY(bie_apply(ctx, b, sigma, asig.p, MH_PREC_FP64));

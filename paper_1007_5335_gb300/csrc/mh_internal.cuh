@@ -6,6 +6,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -13,11 +14,31 @@
 
 #define MH_PI 3.14159265358979323846
 
+// Named timing region: CUDA events recorded on the context stream around each launch.
+struct prof_region {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    double total_ms = 0.0;
+    int64_t launches = 0;
+};
+
 struct mh_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     std::string err;
     int64_t launches = 0;
+    bool profiling = false;
+    std::map<std::string, prof_region> prof;
+    ~mh_ctx();
+};
+
+// RAII scope: records a start/stop event pair on ctx->stream under `name` when
+// profiling is enabled (mh_profile_enable), nothing otherwise.
+struct prof_scope {
+    mh_ctx* ctx;
+    const char* name;
+    cudaEvent_t a = nullptr, b = nullptr;
+    prof_scope(mh_ctx* c, const char* n);
+    ~prof_scope();
 };
 
 // Records a message on ctx and returns the status.
@@ -102,7 +123,17 @@ struct mh_boundary {
     dbuf<double> fine_geo;               // [n_fine][5]: x y nx ny |y'| h_f
     bie_operator op;
     gmres_ws ws;
+    // binary32 source data for the mixed-precision double layer: offsets from tile
+    // centres (tiles of MH_TILE nodes, fine chunks of MH_TILE fine nodes per curve)
+    int64_t n_tiles = 0, n_fchunks = 0;
+    std::vector<int64_t> fchunk_off;     // per curve first chunk
+    dbuf<int64_t> d_fchunk_off;
+    dbuf<float4> src32, fine32;          // (dx, dy, nx, ny)
+    dbuf<double2> tile_c, fchunk_c;
+    dbuf<float> w32, wf32, x32;          // per call: weights, fine weights, GEMV input
 };
+
+#define MH_TILE 128
 
 // Classified target set for off-surface evaluation.
 struct dlp_targets {

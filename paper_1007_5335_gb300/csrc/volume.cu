@@ -384,6 +384,7 @@ template <typename TOP>
 mh_status run_phase(mh_ctx* ctx, VolData* V, const TOP* ops, const Phase* ph) {
     if (ph->n_tasks == 0) return MH_OK;
     const int smem = (int)(ph->smem / sizeof(double) * sizeof(TOP));
+    prof_scope ps(ctx, "volume_contract");
     k_apply<TOP><<<(unsigned)ph->n_chunks, 256, smem, ctx->stream>>>(ops, V->d_op_off.p, V->d_op_C.p, ph->chunk_op.p,
                                                                      ph->chunk_t0.p, ph->task_src.p, V->vec.p, ph->R,
                                                                      V->temp.p);
@@ -797,6 +798,7 @@ mh_status volume_apply(mh_ctx* ctx, mh_tree* t, double alpha, int p, const doubl
         }
     }
     const int64_t nn = t->n_nodes;
+    prof_scope ps(ctx, "volume_apply");
     MH_CUDA(ctx, cudaMemcpyAsync(V->vec.p + V->B_off, b, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     if (prec == MH_PREC_MIXED)
         MH_TRY(volume_run<float>(ctx, t, V, V->ops32.p));
