@@ -60,6 +60,9 @@ __global__ void k_fourier_xy(const double* __restrict__ xy, const int32_t* __res
     coef[4 * g + 3] = yi * inv;
 }
 
+template <int BS>
+__device__ double block_sum(double v);
+
 // Contribution of mode m of one coordinate (re, im) at angle with (s, c) = sin, cos(m t).
 // Accumulates value, first and second t-derivative of the trigonometric interpolant
 //   p(t) = c_0 + sum_{0<m<N/2} 2 Re(c_m e^{imt}) + c_{N/2} cos(N t / 2).
@@ -700,26 +703,45 @@ __global__ void k_line_aux(const int32_t* __restrict__ line_tgt, const int32_t* 
 
 // ---------------- off-surface evaluation ----------------
 
-// Fourier coefficients of a scalar density per curve: 2 doubles per mode.
+// Fourier coefficients of a scalar density per curve: 2 doubles per mode.  One block per
+// mode, threads over the nodes, exact twiddles from the per-curve table
+// tw[off + r] = (cos, sin)(2 pi r / N).
 __global__ void k_fourier_scalar(const double* __restrict__ v, const int32_t* __restrict__ nn,
-                                 const int32_t* __restrict__ off, int ncurves, int64_t total, double* coef) {
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+                                 const int32_t* __restrict__ off, const double2* __restrict__ tw, int ncurves,
+                                 int64_t total, double* coef) {
+    const int64_t g = blockIdx.x;
     if (g >= total) return;
     int k = 0;
     while (k + 1 < ncurves && g >= coef_base(off, k + 1)) ++k;
     const int N = nn[k];
     const int m = (int)(g - coef_base(off, k));
     const double* p = v + off[k];
+    const double2* t = tw + off[k];
     double re = 0, im = 0;
-    for (int n = 0; n < N; ++n) {
-        int r = (int)(((int64_t)m * n) % N);
-        double s, c;
-        sincospi(2.0 * r / N, &s, &c);
-        re += p[n] * c;
-        im -= p[n] * s;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const double2 c = t[(int)(((int64_t)m * n) % N)];
+        re = fma(p[n], c.x, re);
+        im = fma(-p[n], c.y, im);
     }
-    coef[2 * g] = re / N;
-    coef[2 * g + 1] = im / N;
+    re = block_sum<128>(re);
+    im = block_sum<128>(im);
+    if (threadIdx.x == 0) {
+        coef[2 * g] = re / N;
+        coef[2 * g + 1] = im / N;
+    }
+}
+
+__global__ void k_twiddles(const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
+                           const int32_t* __restrict__ curve_of, int64_t n, double2* tw, double2* half) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int k = curve_of[j];
+    const int r = (int)(j - off[k]);
+    double s, c;
+    sincospi(2.0 * r / nn[k], &s, &c);
+    tw[j] = make_double2(c, s);
+    sincospi((double)r / nn[k], &s, &c);   // (cos, sin)(t_r / 2)
+    half[j] = make_double2(c, s);
 }
 
 // Density on the fine grid times |y'| h_f (quadrature weight folded in).
@@ -810,8 +832,8 @@ __global__ void k_dlp_fine(const double* __restrict__ xy, const int32_t* __restr
 // values) and the values at the 4 auxiliary points.
 __global__ void k_dlp_line(const int32_t* __restrict__ line_tgt, const int32_t* __restrict__ line_curve,
                            const double* __restrict__ line_data, int64_t nline, const double* __restrict__ asig,
-                           const int32_t* __restrict__ nn, const int32_t* __restrict__ off, int64_t n_user,
-                           double alpha, double* out) {
+                           const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
+                           const double2* __restrict__ half, int64_t n_user, double alpha, double* out) {
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (t >= nline) return;
     const int lane = threadIdx.x & 31;
@@ -819,11 +841,18 @@ __global__ void k_dlp_line(const int32_t* __restrict__ line_tgt, const int32_t* 
     const int N = nn[k];
     const double ts = line_data[4 * t];
     const double* a = asig + off[k];
+    const double2* hf = half + off[k];
+    // D_N(t* - t_i) = sin(N (t* - t_i)/2) cot((t* - t_i)/2) / N with sin(N (t* - t_i)/2)
+    // = (-1)^i sin(N t*/2) and the half angles by the addition formulas.
+    double sN, cN, sh0, ch0;
+    sincos(0.5 * N * ts, &sN, &cN);
+    sincos(0.5 * ts, &sh0, &ch0);
     double acc = 0.0;
     for (int i = lane; i < N; i += 32) {
-        double tau = ts - 2.0 * MH_PI * i / N;
-        double sh = sin(0.5 * tau);
-        double dk = fabs(sh) < 1e-300 ? 1.0 : sin(0.5 * N * tau) * cos(0.5 * tau) / sh / N;
+        const double sh = sh0 * hf[i].x - ch0 * hf[i].y;
+        const double ch = ch0 * hf[i].x + sh0 * hf[i].y;
+        const double sg = (i & 1) ? -sN : sN;
+        const double dk = fabs(sh) < 1e-300 ? 1.0 : sg * ch / sh / N;
         acc += dk * a[i];
     }
     acc = warp_sum(acc);
@@ -922,6 +951,10 @@ extern "C" mh_status mh_boundary_create(mh_ctx* ctx, int n_curves, const int32_t
     BCHK(b->d_fine_off.alloc(n_curves + 1));
     BCHK(b->fine_geo.alloc(6 * b->n_fine));
     BCHK(cudaMemcpyAsync(b->d_fine_off.p, b->fine_off.data(), (n_curves + 1) * 8, cudaMemcpyHostToDevice, st));
+    BCHK(b->tw.alloc(tot));
+    BCHK(b->half.alloc(tot));
+    k_twiddles<<<mh_grid(tot, 128), 128, 0, st>>>(b->d_nn.p, b->d_off.p, b->d_curve_of.p, tot, b->tw.p, b->half.p);
+    ctx->launches++;
     k_fine_geometry<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(b->coef.p, b->d_nn.p, b->d_off.p, b->d_fine_off.p,
                                                                n_curves, b->n_fine, b->fine_geo.p);
     ctx->launches++;
@@ -1283,8 +1316,8 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
             MH_LAUNCHED(ctx);
         }
         if (tg->n_pairs) {
-            k_fourier_scalar<<<mh_grid(nmodes, 128), 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->n_curves, nmodes,
-                                                                   sc.p);
+            k_fourier_scalar<<<(unsigned)nmodes, 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->tw.p, b->n_curves,
+                                                               nmodes, sc.p);
             MH_LAUNCHED(ctx);
             float* sc32 = reinterpret_cast<float*>(tg->wf.p);   // 2*nmodes floats fit in the binary64 buffer
             k_to_float_vec<<<mh_grid(2 * nmodes, 256), 256, 0, st>>>(sc.p, sc32, 2 * nmodes);
@@ -1308,8 +1341,8 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
             MH_LAUNCHED(ctx);
         }
         if (tg->n_pairs) {
-            k_fourier_scalar<<<mh_grid(nmodes, 128), 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->n_curves, nmodes,
-                                                                   sc.p);
+            k_fourier_scalar<<<(unsigned)nmodes, 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->tw.p, b->n_curves,
+                                                               nmodes, sc.p);
             MH_LAUNCHED(ctx);
             k_fine_density<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(sc.p, b->fine_geo.p, b->d_nn.p, b->d_off.p,
                                                                      b->d_fine_off.p, b->n_curves, b->n_fine, wf.p);
@@ -1324,8 +1357,8 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
     if (tg->n_line) {
         MH_TRY(bie_apply(ctx, b, sigma, asig.p, MH_PREC_FP64));
         k_dlp_line<<<mh_grid(tg->n_line * 32, 256), 256, 0, st>>>(tg->line_tgt.p, tg->line_curve.p, tg->line_data.p,
-                                                                  tg->n_line, asig.p, b->d_nn.p, b->d_off.p, tg->n,
-                                                                  alpha, ext.p);
+                                                                  tg->n_line, asig.p, b->d_nn.p, b->d_off.p,
+                                                                  b->half.p, tg->n, alpha, ext.p);
         MH_LAUNCHED(ctx);
     }
     if (tg->n) MH_CUDA(ctx, cudaMemcpyAsync(out, ext.p, tg->n * 8, cudaMemcpyDeviceToDevice, st));

@@ -116,6 +116,7 @@ struct mh_boundary {
     dbuf<double> xy;                     // [n][2]
     dbuf<double> geo;                    // [n][8]: x y x' y' x'' y'' |y'| kdiag
     dbuf<double> coef;                   // per curve Fourier coefficients: [off*2 ...] see boundary.cu
+    dbuf<double2> tw, half;              // per node (cos, sin)(2 pi r / N) and (cos, sin)(pi r / N)
     // fine (16x) grid per curve: positions, normals, speed*h_fine
     int64_t n_fine = 0;
     std::vector<int64_t> fine_off;
