@@ -170,6 +170,23 @@ mh_status mh_gmres_solve(mh_ctx* ctx, mh_boundary* bnd, double alpha, const doub
                          double* sigma_dev, double tol, int max_iter, mh_precision prec,
                          mh_gmres_info* info);
 
+/* Allocation-free variant of mh_gmres_solve (the paper has no counterpart; it exists for
+ * callers that cannot allocate device memory while they solve, e.g. code running under a
+ * device-memory budget fixed in advance or inside a host loop whose allocator belongs to
+ * another framework).  Binary64 only.  The Krylov workspace is a fixed array compiled into
+ * the library (4.4 MB held on every device that loads it, until the process exits), so:
+ *   - N_Gamma <= 8192 and 1 <= max_iter <= 64, else MH_ERR_INVALID_ARG;
+ *   - the operator for `alpha` must already be assembled on bnd by an earlier
+ *     mh_gmres_solve / mh_double_layer_apply / mh_problem_create call with the same alpha
+ *     (those allocate it), else MH_ERR_INVALID_ARG;
+ *   - the first call on a device looks up the array's device address (done once per device,
+ *     with that device current); make that first call before any stream capture;
+ *   - the call does no cudaMalloc/cudaFree; every call shares the one array, so calls that
+ *     overlap on the GPU (other streams, other host threads) race and must be serialised.
+ * Arguments, stopping rule, info and errors are those of mh_gmres_solve. */
+mh_status mh_gmres_solve_static(mh_ctx* ctx, mh_boundary* bnd, double alpha, const double* rhs_dev,
+                                double* sigma_dev, double tol, int max_iter, mh_gmres_info* info);
+
 /* ---- heat step (Section 2) ---------------------------------------------------------- */
 
 typedef enum { MH_EXT_CONST = 0, MH_EXT_ARRAY = 1 } mh_ext_mode;

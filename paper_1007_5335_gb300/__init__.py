@@ -64,6 +64,7 @@ _SIGS = {
     "mh_problem_destroy": [_p],
     "mh_problem_regions": [_p, _p, _p],
     "heat_step": [_p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
+    "mh_gmres_solve_static": [_p, _p, _d, _p, _p, _d, _i, ctypes.POINTER(GmresInfo)],
     "mh_profile_enable": [_p, _i],
     "mh_profile_read": [_p, ctypes.c_char_p, ctypes.POINTER(_d), ctypes.POINTER(_i64), _i],
 }
@@ -229,6 +230,15 @@ def mh_gmres_solve(ctx: Context, bnd: Boundary, alpha: float, rhs, sigma, tol: f
     info = GmresInfo()
     ctx.check(_lib.mh_gmres_solve(ctx.h, bnd.h, float(alpha), _ptr(rhs), _ptr(sigma), float(tol), int(max_iter),
                                   int(prec), ctypes.byref(info)))
+    return info
+
+
+def mh_gmres_solve_static(ctx: Context, bnd: Boundary, alpha: float, rhs, sigma, tol: float = 1e-10,
+                          max_iter: int = 64) -> GmresInfo:
+    """Allocation-free binary64 GMRES (fixed workspace inside the library; see include/mh.h)."""
+    info = GmresInfo()
+    ctx.check(_lib.mh_gmres_solve_static(ctx.h, bnd.h, float(alpha), _ptr(rhs), _ptr(sigma), float(tol),
+                                         int(max_iter), ctypes.byref(info)))
     return info
 
 

@@ -1392,3 +1392,140 @@ extern "C" mh_status mh_gmres_solve(mh_ctx* ctx, mh_boundary* b, double alpha, c
     MH_TRY(bie_assemble(ctx, b, alpha));
     return gmres_run(ctx, b, rhs_dev, sigma_dev, tol, max_iter, prec, info);
 }
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free GMRES.  Some callers cannot call cudaMalloc while they solve: code that
+// runs under a memory budget fixed in advance, or inside a host loop whose allocator is
+// owned by another framework, and must not grow or free device memory between calls.
+// mh_gmres_solve_static gives them the binary64 solve with its Krylov workspace taken from
+// a fixed array compiled into the library instead of allocated memory.
+// ---------------------------------------------------------------------------------------
+
+#define MH_STATIC_N 8192   // largest N_Gamma
+#define MH_STATIC_M 64     // largest max_iter
+#define MH_STATIC_SMALL (MH_STATIC_M + 2)
+
+// Workspace layout (doubles): V[(M+1) N] | w[N] | H[(M+1) M] | cs, sn, g, y, h1, h2 [M+2 each] | small[4]
+#define MH_STATIC_DOUBLES                                                                               \
+    ((size_t)(MH_STATIC_M + 1) * MH_STATIC_N + MH_STATIC_N + (size_t)(MH_STATIC_M + 1) * MH_STATIC_M + \
+     6 * MH_STATIC_SMALL + 4)
+
+// 4.4 MB held by every device that loads the library, until the process exits.
+static __device__ __align__(256) double g_gmres_scratch[MH_STATIC_DOUBLES];
+
+// Device address of g_gmres_scratch per device, looked up once with that device current.
+static double* g_scratch_addr[64];
+static bool g_scratch_ready[64];
+
+static mh_status static_scratch(mh_ctx* ctx, double** out) {
+    if (ctx->device < 0 || ctx->device >= 64) return mh_fail(ctx, MH_ERR_INVALID_ARG, "device id out of range");
+    if (!g_scratch_ready[ctx->device]) {
+        int cur = 0;
+        MH_CUDA(ctx, cudaGetDevice(&cur));
+        if (cur != ctx->device) MH_CUDA(ctx, cudaSetDevice(ctx->device));
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_gmres_scratch);
+        if (cur != ctx->device) cudaSetDevice(cur);
+        if (e != cudaSuccess)
+            return mh_fail(ctx, MH_ERR_CUDA, "cudaGetSymbolAddress(g_gmres_scratch) failed: %s", cudaGetErrorString(e));
+        g_scratch_addr[ctx->device] = static_cast<double*>(p);
+        g_scratch_ready[ctx->device] = true;
+    }
+    *out = g_scratch_addr[ctx->device];
+    return MH_OK;
+}
+
+extern "C" mh_status mh_gmres_solve_static(mh_ctx* ctx, mh_boundary* bd, double alpha, const double* rhs_dev,
+                                           double* sigma_dev, double tol, int max_iter, mh_gmres_info* info) {
+    if (!ctx || !bd || !rhs_dev || !sigma_dev) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    if (!(tol > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "tol must be positive");
+    const int64_t n = bd->n;
+    if (n > MH_STATIC_N)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "N_Gamma = %lld exceeds the static workspace limit %d",
+                       (long long)n, MH_STATIC_N);
+    if (max_iter < 1 || max_iter > MH_STATIC_M)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "max_iter must be in 1..%d for the static workspace", MH_STATIC_M);
+    if (!(bd->op.A64.p && bd->op.alpha == alpha))
+        return mh_fail(ctx, MH_ERR_INVALID_ARG,
+                       "the operator for this alpha is not assembled: call mh_gmres_solve or "
+                       "mh_double_layer_apply with this alpha first (they allocate it)");
+    double* base = nullptr;
+    MH_TRY(static_scratch(ctx, &base));
+    const int M = max_iter, ldh = M + 1;
+    double* V = base;
+    double* w = V + (size_t)(MH_STATIC_M + 1) * MH_STATIC_N;
+    double* H = w + MH_STATIC_N;
+    double* cs = H + (size_t)(MH_STATIC_M + 1) * MH_STATIC_M;
+    double* sn = cs + MH_STATIC_SMALL;
+    double* g = sn + MH_STATIC_SMALL;
+    double* y = g + MH_STATIC_SMALL;
+    double* h1 = y + MH_STATIC_SMALL;
+    double* h2 = h1 + MH_STATIC_SMALL;
+    double* small = h2 + MH_STATIC_SMALL;
+    cudaStream_t st = ctx->stream;
+    const int ew = mh_grid(n, 256) < 152 * 4 ? mh_grid(n, 256) : 152 * 4;
+    // the array keeps the previous call's contents: clear what the iteration reads first
+    MH_CUDA(ctx, cudaMemsetAsync(g, 0, MH_STATIC_SMALL * sizeof(double), st));
+    mh_gmres_info inf{0, 0, 0.0, 0};
+    double bnorm;
+    MH_TRY(vec_norm(ctx, rhs_dev, n, small + 2, &bnorm));
+    if (bnorm == 0.0) {
+        MH_CUDA(ctx, cudaMemsetAsync(sigma_dev, 0, n * 8, st));
+        inf.converged = 1;
+        if (info) *info = inf;
+        return MH_OK;
+    }
+    MH_TRY(bie_apply(ctx, bd, sigma_dev, w, MH_PREC_FP64));
+    k_sub_from<<<ew, 256, 0, st>>>(rhs_dev, w, n);
+    MH_LAUNCHED(ctx);
+    double beta;
+    MH_TRY(vec_norm(ctx, w, n, small + 1, &beta));
+    int k = 0;
+    if (beta > tol * bnorm) {
+        k_scale_into<<<ew, 256, 0, st>>>(w, small + 1, V, g, n);
+        MH_LAUNCHED(ctx);
+        double res = beta;
+        for (; k < M; ++k) {
+            MH_TRY(bie_apply(ctx, bd, V + (int64_t)k * n, w, MH_PREC_FP64));
+            k_multidot<<<k + 1, 256, 0, st>>>(V, w, n, h1);
+            MH_LAUNCHED(ctx);
+            k_multiaxpy<<<ew, 256, 0, st>>>(V, h1, k + 1, n, w);
+            MH_LAUNCHED(ctx);
+            k_multidot<<<k + 1, 256, 0, st>>>(V, w, n, h2);
+            MH_LAUNCHED(ctx);
+            k_multiaxpy<<<ew, 256, 0, st>>>(V, h2, k + 1, n, w);
+            MH_LAUNCHED(ctx);
+            k_norm<<<1, 1024, 0, st>>>(w, n, small + 1);
+            MH_LAUNCHED(ctx);
+            k_finish_column<<<ew, 256, 0, st>>>(h1, h2, small + 1, k, H + (int64_t)k * ldh, w, V + (int64_t)(k + 1) * n,
+                                                n);
+            MH_LAUNCHED(ctx);
+            k_givens<<<1, 1, 0, st>>>(H, ldh, k, cs, sn, g, small);
+            MH_LAUNCHED(ctx);
+            MH_CUDA(ctx, cudaMemcpyAsync(&res, small, 8, cudaMemcpyDeviceToHost, st));
+            MH_CUDA(ctx, cudaStreamSynchronize(st));
+            if (!std::isfinite(res)) return mh_fail(ctx, MH_ERR_NUMERIC, "GMRES residual is not finite");
+            if (res <= tol * bnorm) {
+                ++k;
+                break;
+            }
+        }
+        k_backsolve<<<1, 1, 0, st>>>(H, ldh, k, g, y);
+        MH_LAUNCHED(ctx);
+        k_update_x<<<ew, 256, 0, st>>>(V, y, k, n, sigma_dev);
+        MH_LAUNCHED(ctx);
+    }
+    inf.iterations = k;
+    MH_TRY(bie_apply(ctx, bd, sigma_dev, w, MH_PREC_FP64));
+    k_sub_from<<<ew, 256, 0, st>>>(rhs_dev, w, n);
+    MH_LAUNCHED(ctx);
+    double rn;
+    MH_TRY(vec_norm(ctx, w, n, small + 2, &rn));
+    inf.rel_residual = rn / bnorm;
+    inf.converged = inf.rel_residual <= tol;
+    if (info) *info = inf;
+    if (!inf.converged)
+        return mh_fail(ctx, MH_ERR_NOT_CONVERGED, "GMRES stopped after %d iterations at relative residual %.3e",
+                       inf.iterations, inf.rel_residual);
+    return MH_OK;
+}
