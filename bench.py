@@ -176,7 +176,8 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     launches = ctx.launches - launches0
     regions_ms = {}
-    for r in ("dlp_coarse", "dlp_fine", "bie_gemv", "volume_contract", "volume_apply", "gmres", "dlp_evaluate"):
+    for r in ("dlp_coarse", "dlp_fine", "dlp_near", "dlp_fmm", "dlp_fmm_contract", "bie_gemv", "volume_contract",
+              "volume_apply", "gmres", "dlp_evaluate"):
         regions_ms[r] = ctx.profile_read(r)
     ctx.profile(False)
     total_ms = float(sum(times))
@@ -250,6 +251,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": bytes_out},
         "gpu_launches": launches,
         "regions_ms_per_step": {k: v[0] / args.steps for k, v in regions_ms.items()},
+        "kernel_launches_per_step": {k: v[1] / args.steps for k, v in regions_ms.items()},
         "roofline": roof,
         "clocks": clk.summary(),
     }
@@ -260,36 +262,40 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+KERNEL_REGIONS = {
+    # region: (bound, description)
+    "dlp_coarse": ("alu", "trapezoid double-layer pair sums"),
+    "dlp_fine": ("alu", "16x upsampled near-boundary pair sums"),
+    "dlp_near": ("alu", "double-layer near-field pair sums (fine dipoles of neighbour leaves)"),
+    "bie_gemv": ("hbm", "Nystrom operator GEMV"),
+    "volume_contract": ("hbm", "volume multipole batched contractions + reduction"),
+    "dlp_fmm_contract": ("hbm", "double-layer multipole batched contractions + reduction"),
+}
+
+
 def roofline(regions_ms, tree, bnd, prob, prec, mh, peaks, steps):
-    """Roofline of the dominant instrumented kernel region."""
-    cand = {k: v for k, v in regions_ms.items() if k in ("dlp_coarse", "bie_gemv", "volume_contract", "dlp_fine")}
+    """Roofline of the dominant instrumented kernel region, from the algorithmic work
+    (flops, bytes) the library declares for each timed launch."""
+    cand = {k: v for k, v in regions_ms.items() if k in KERNEL_REGIONS and v[1] > 0}
     name = max(cand, key=lambda k: cand[k][0])
-    ms, launches = cand[name]
+    ms, launches, flops, nbytes = cand[name]
     avg_s = ms / max(launches, 1) / 1e3
-    n = bnd.n
-    if name == "bie_gemv":
-        elt = 4 if prec == mh.MH_PREC_MIXED else 8
-        work = n * n * elt + 2 * n * 8           # operator + x + y bytes per launch
-        achieved = work / avg_s / 1e9
+    bound, desc = KERNEL_REGIONS[name]
+    out = {"kernel": name, "what": desc, "bound": bound, "avg_launch_ms": avg_s * 1e3, "launches": launches,
+           "traffic": None}
+    if bound == "hbm":
+        achieved = nbytes / launches / avg_s / 1e9
         peak = peaks["hbm_gbs"]
-        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": launches,
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
-    if name in ("dlp_coarse", "dlp_fine"):
-        # pair interactions x 2 x (FMA-equivalent operations of one double-layer kernel value)
-        pairs = prob_inside(prob) * n if name == "dlp_coarse" else None
-        flops_per_pair = 2 * 34
-        if pairs is None:
-            return {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-                    "traffic": None}
-        achieved = pairs * flops_per_pair / avg_s / 1e12
+        out.update({"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "bytes_per_launch": nbytes / launches, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"})
+    else:
+        achieved = flops / launches / avg_s / 1e12
         peak = FP32_PEAK_TFLOPS if prec == mh.MH_PREC_MIXED else FP64_PEAK_TFLOPS
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": launches,
-                "pairs_per_launch": pairs, "flops_per_pair": flops_per_pair,
-                "peak_source": "nominal: binary64 1.25 TFLOP/s; binary32 152 SM x 128 lanes x 2 x 2.07 GHz"}
-    return {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-            "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": launches}
+        out.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "flops_per_launch": flops / launches, "flops_per_pair": 68,
+                    "peak_source": "derived: binary32 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s; "
+                                   "binary64 nominal 1.25 TFLOP/s"})
+    return out
 
 
 def prob_inside(prob):

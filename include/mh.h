@@ -91,12 +91,15 @@ int64_t mh_kernel_launches(const mh_ctx* ctx);
 
 /* Timing of named kernel regions (library instrumentation, no counterpart in the paper).
  * When enabled, the library records a CUDA event pair on its stream around each launch
- * of the instrumented kernels: "dlp_coarse", "dlp_fine", "bie_gemv", "volume_apply",
- * "volume_contract", "gmres", "dlp_evaluate".  mh_profile_read synchronises the stream
- * and returns the summed event time (ms) and number of timed launches of `region`
- * since the last reset; reset != 0 clears all regions afterwards. */
+ * of the instrumented kernels -- "dlp_coarse", "dlp_fine", "dlp_fmm", "dlp_fmm_contract",
+ * "bie_gemv", "volume_apply", "volume_contract", "gmres", "dlp_evaluate" -- together with
+ * the algorithmic work each launch declares (flops; bytes that must move at least once).
+ * mh_profile_read synchronises the stream and returns, for `region`, the summed event time
+ * (ms), the number of timed launches and the summed flops and bytes since the last reset;
+ * any output pointer may be NULL; reset != 0 clears all regions afterwards. */
 mh_status mh_profile_enable(mh_ctx* ctx, int on);
-mh_status mh_profile_read(mh_ctx* ctx, const char* region, double* total_ms, int64_t* launches, int reset);
+mh_status mh_profile_read(mh_ctx* ctx, const char* region, double* total_ms, int64_t* launches, double* flops,
+                          double* bytes, int reset);
 
 /* ---- boundary (Section 3.2) -------------------------------------------------------- */
 

@@ -66,7 +66,8 @@ _SIGS = {
     "heat_step": [_p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
     "mh_gmres_solve_static": [_p, _p, _d, _p, _p, _d, _i, ctypes.POINTER(GmresInfo)],
     "mh_profile_enable": [_p, _i],
-    "mh_profile_read": [_p, ctypes.c_char_p, ctypes.POINTER(_d), ctypes.POINTER(_i64), _i],
+    "mh_profile_read": [_p, ctypes.c_char_p, ctypes.POINTER(_d), ctypes.POINTER(_i64), ctypes.POINTER(_d),
+                        ctypes.POINTER(_d), _i],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -117,10 +118,11 @@ class Context:
         self.check(_lib.mh_profile_enable(self.h, 1 if on else 0))
 
     def profile_read(self, region: str, reset: bool = False):
-        """mh_profile_read -> (total_ms, launches) of a named region."""
-        ms, n = _d(), _i64()
-        self.check(_lib.mh_profile_read(self.h, region.encode(), ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0))
-        return ms.value, n.value
+        """mh_profile_read -> (total_ms, launches, flops, bytes) of a named region."""
+        ms, n, f, b = _d(), _i64(), _d(), _d()
+        self.check(_lib.mh_profile_read(self.h, region.encode(), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(f),
+                                        ctypes.byref(b), 1 if reset else 0))
+        return ms.value, n.value, f.value, b.value
 
     def __del__(self):
         if getattr(self, "h", None):

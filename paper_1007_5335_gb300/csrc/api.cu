@@ -44,7 +44,8 @@ mh_ctx::~mh_ctx() {
         }
 }
 
-prof_scope::prof_scope(mh_ctx* c, const char* n) : ctx(c), name(n) {
+prof_scope::prof_scope(mh_ctx* c, const char* n, double flops_, double bytes_)
+    : ctx(c), name(n), flops(flops_), bytes(bytes_) {
     if (!ctx || !ctx->profiling) return;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
         a = b = nullptr;
@@ -56,7 +57,10 @@ prof_scope::prof_scope(mh_ctx* c, const char* n) : ctx(c), name(n) {
 prof_scope::~prof_scope() {
     if (!a) return;
     cudaEventRecord(b, ctx->stream);
-    ctx->prof[name].pending.emplace_back(a, b);
+    prof_region& r = ctx->prof[name];
+    r.pending.emplace_back(a, b);
+    r.flops += flops;
+    r.bytes += bytes;
 }
 
 extern "C" mh_status mh_profile_enable(mh_ctx* ctx, int on) {
@@ -66,7 +70,7 @@ extern "C" mh_status mh_profile_enable(mh_ctx* ctx, int on) {
 }
 
 extern "C" mh_status mh_profile_read(mh_ctx* ctx, const char* region, double* total_ms, int64_t* launches,
-                                     int reset) {
+                                     double* flops, double* bytes, int reset) {
     if (!ctx || !region) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
     MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     for (auto& kv : ctx->prof) {
@@ -82,6 +86,8 @@ extern "C" mh_status mh_profile_read(mh_ctx* ctx, const char* region, double* to
     auto it = ctx->prof.find(region);
     if (total_ms) *total_ms = it == ctx->prof.end() ? 0.0 : it->second.total_ms;
     if (launches) *launches = it == ctx->prof.end() ? 0 : it->second.launches;
+    if (flops) *flops = it == ctx->prof.end() ? 0.0 : it->second.flops;
+    if (bytes) *bytes = it == ctx->prof.end() ? 0.0 : it->second.bytes;
     if (reset) ctx->prof.clear();
     return MH_OK;
 }

@@ -15,6 +15,10 @@ constexpr int UPSAMPLE = 16;        // fine grid for targets within 5 h_s of a c
 constexpr double NEAR_NODE = 6.0;   // project on the curve when the nearest node is within 6 h*
 constexpr double NEAR_FINE = 5.0;   // d < 5 h_s: upsampled rule
 constexpr double NEAR_LINE = 0.25;  // d < h_s/4: interpolation along the normal
+// Flops counted for one double-layer kernel value K(y, x) w (the unit of the pair sums):
+// offsets 2, r^2 2, rsqrt 1, z 1, Chebyshev tail (4/z - 1, 10-term Clenshaw) 21, exp 8,
+// products with e^{-z}/sqrt(z) 3, dot product 3, scaling and accumulate 4 (FMA = 2 flops)
+constexpr double DL_FLOPS = 68.0;
 
 struct AlpertRule {
     int l, a;
@@ -382,7 +386,11 @@ __global__ void __launch_bounds__(MH_TILE) k_dlp_coarse32(const double* __restri
     const uint32_t mask = active ? fine[t] : 0xffffffffu;
     double acc = 0.0;
     const int64_t ntile = (ns + MH_TILE - 1) / MH_TILE;
-    for (int64_t tile = 0; tile < ntile; ++tile) {
+    // gridDim.y > 1 splits the source tiles between blocks; partial sums go to
+    // out[blockIdx.y * nt + t] (without the prefactor) for a fixed-order reduction
+    const int64_t per = (ntile + gridDim.y - 1) / gridDim.y;
+    const int64_t tile0 = blockIdx.y * per, tile1 = min(ntile, tile0 + per);
+    for (int64_t tile = tile0; tile < tile1; ++tile) {
         const int64_t s = tile * MH_TILE + threadIdx.x;
         if (s < ns) {
             s4[threadIdx.x] = src[s];
@@ -404,7 +412,20 @@ __global__ void __launch_bounds__(MH_TILE) k_dlp_coarse32(const double* __restri
         }
         __syncthreads();
     }
-    if (active) out[t] = pref * acc;
+    if (active) {
+        if (gridDim.y == 1)
+            out[t] = pref * acc;
+        else
+            out[blockIdx.y * nt + t] = acc;
+    }
+}
+
+__global__ void k_sum_partials(const double* __restrict__ part, int nsplit, int64_t nt, double pref, double* out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    double s = 0.0;
+    for (int j = 0; j < nsplit; ++j) s += part[j * nt + t];
+    out[t] = pref * s;
 }
 
 // Density on the fine grid times |y'| h_f in binary32 (coefficients given in binary32).
@@ -431,6 +452,67 @@ __global__ void k_fine_density32(const float* __restrict__ sc, const double* __r
         v += c[N] * cospif(2.0f * (float)r / (float)NF);
     }
     wf[g] = v * (float)(fg[6 * g + 4] * fg[6 * g + 5]);
+}
+
+// Upsampled rule in binary32, one block per (target, curve) pair: the warps share the
+// fine-node chunks (MH_TILE nodes, binary64 chunk centres); block reduction in fixed order.
+__global__ void k_dlp_fine32_blk(const double* __restrict__ xy, const int32_t* __restrict__ ptgt,
+                                 const int32_t* __restrict__ pcurve, const float4* __restrict__ fine32,
+                                 const float* __restrict__ wf, const int64_t* __restrict__ foff,
+                                 const int64_t* __restrict__ coff, const double2* __restrict__ cc, float inv_alpha,
+                                 double pref, double* out) {
+    __shared__ double red[8];
+    const int64_t p = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t t = ptgt[p];
+    const int k = pcurve[p];
+    const double px = xy[2 * t], py = xy[2 * t + 1];
+    double acc = 0.0;
+    for (int64_t ch = coff[k] + warp; ch < coff[k + 1]; ch += nw) {
+        const double2 c = cc[ch];
+        const float tx = (float)(px - c.x), ty = (float)(py - c.y);
+        const int64_t f0 = foff[k] + (ch - coff[k]) * MH_TILE;
+        const int64_t f1 = min(f0 + MH_TILE, foff[k + 1]);
+        float part = 0.f;
+        for (int64_t f = f0 + lane; f < f1; f += 32) {
+            const float4 v = fine32[f];
+            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha) * wf[f];
+        }
+        acc += (double)part;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nw; ++i) s += red[i];
+        atomicAdd(out + t, pref * s);
+    }
+}
+
+__global__ void k_dlp_fine64_blk(const double* __restrict__ xy, const int32_t* __restrict__ ptgt,
+                                 const int32_t* __restrict__ pcurve, const double* __restrict__ fg,
+                                 const double* __restrict__ wf, const int64_t* __restrict__ foff, double inv_alpha,
+                                 double pref, double* out) {
+    __shared__ double red[8];
+    const int64_t p = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t t = ptgt[p];
+    const int k = pcurve[p];
+    const double px = xy[2 * t], py = xy[2 * t + 1];
+    double acc = 0.0;
+    for (int64_t f = foff[k] + threadIdx.x; f < foff[k + 1]; f += blockDim.x) {
+        const double* g = fg + 6 * f;
+        acc += dl_kernel(g[0], g[1], g[2], g[3], px, py, inv_alpha) * wf[f];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nw; ++i) s += red[i];
+        atomicAdd(out + t, pref * s);
+    }
 }
 
 // Upsampled rule in binary32, one warp per (target, curve) pair, fine nodes in chunks of
@@ -781,7 +863,10 @@ __global__ void k_dlp_coarse(const double* __restrict__ xy, const uint32_t* __re
     const double px = active ? xy[2 * t] : 0.0, py = active ? xy[2 * t + 1] : 0.0;
     const uint32_t mask = active ? fine[t] : 0xffffffffu;
     double acc = 0.0;
-    for (int64_t s0 = 0; s0 < ns; s0 += BS) {
+    // gridDim.y > 1 splits the sources between blocks (partials without the prefactor)
+    const int64_t ntile = (ns + BS - 1) / BS, per = (ntile + gridDim.y - 1) / gridDim.y;
+    const int64_t sbeg = blockIdx.y * per * BS, send = min(ns, (blockIdx.y + 1) * per * BS);
+    for (int64_t s0 = sbeg; s0 < send; s0 += BS) {
         int64_t s = s0 + threadIdx.x;
         if (s < ns) {
             const double* g = geo + 8 * s;
@@ -804,7 +889,12 @@ __global__ void k_dlp_coarse(const double* __restrict__ xy, const uint32_t* __re
         }
         __syncthreads();
     }
-    if (active) out[t] = pref * acc;
+    if (active) {
+        if (gridDim.y == 1)
+            out[t] = pref * acc;
+        else
+            out[blockIdx.y * nt + t] = acc;
+    }
 }
 
 // Upsampled rule for (target, curve) pairs: one warp per pair.
@@ -825,6 +915,77 @@ __global__ void k_dlp_fine(const double* __restrict__ xy, const int32_t* __restr
     }
     acc = warp_sum(acc);
     if (lane == 0) atomicAdd(out + t, pref * acc);
+}
+
+// Near-boundary correction for targets whose trapezoid sum came from the multipole
+// method: upsampled sum over curve k minus the trapezoid sum over the nodes of curve k.
+__global__ void k_dlp_fine_corr(const double* __restrict__ xy, const int32_t* __restrict__ ptgt,
+                                const int32_t* __restrict__ pcurve, int64_t npairs, const double* __restrict__ fg,
+                                const double* __restrict__ wf, const int64_t* __restrict__ foff,
+                                const double* __restrict__ geo, const double* __restrict__ sigma,
+                                const int32_t* __restrict__ nn, const int32_t* __restrict__ off, double inv_alpha,
+                                double pref, double* out) {
+    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (p >= npairs) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ptgt[p];
+    const int k = pcurve[p];
+    const double px = xy[2 * t], py = xy[2 * t + 1];
+    double acc = 0.0;
+    for (int64_t f = foff[k] + lane; f < foff[k + 1]; f += 32) {
+        const double* g = fg + 6 * f;
+        acc += dl_kernel(g[0], g[1], g[2], g[3], px, py, inv_alpha) * wf[f];
+    }
+    const double h = 2.0 * MH_PI / nn[k];
+    for (int64_t s = off[k] + lane; s < off[k + 1]; s += 32) {
+        const double* g = geo + 8 * s;
+        const double sp = g[6];
+        acc -= dl_kernel(g[0], g[1], g[3] / sp, -g[2] / sp, px, py, inv_alpha) * sigma[s] * sp * h;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) out[t] += pref * acc;
+}
+
+__global__ void k_dlp_fine_corr32(const double* __restrict__ xy, const int32_t* __restrict__ ptgt,
+                                  const int32_t* __restrict__ pcurve, int64_t npairs,
+                                  const float4* __restrict__ fine32, const float* __restrict__ wf,
+                                  const int64_t* __restrict__ foff, const int64_t* __restrict__ coff,
+                                  const double2* __restrict__ cc, const float4* __restrict__ src32,
+                                  const float* __restrict__ w32, const double2* __restrict__ tc,
+                                  const int32_t* __restrict__ off, float inv_alpha, double pref, double* out) {
+    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (p >= npairs) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ptgt[p];
+    const int k = pcurve[p];
+    const double px = xy[2 * t], py = xy[2 * t + 1];
+    double acc = 0.0;
+    for (int64_t ch = coff[k]; ch < coff[k + 1]; ++ch) {
+        const double2 c = cc[ch];
+        const float tx = (float)(px - c.x), ty = (float)(py - c.y);
+        const int64_t f0 = foff[k] + (ch - coff[k]) * MH_TILE;
+        const int64_t f1 = min(f0 + MH_TILE, foff[k + 1]);
+        float part = 0.f;
+        for (int64_t f = f0 + lane; f < f1; f += 32) {
+            const float4 v = fine32[f];
+            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha) * wf[f];
+        }
+        acc += (double)part;
+    }
+    // trapezoid nodes of curve k, offsets from their tile centres
+    for (int64_t tile = off[k] / MH_TILE; tile * MH_TILE < off[k + 1]; ++tile) {
+        const double2 c = tc[tile];
+        const float tx = (float)(px - c.x), ty = (float)(py - c.y);
+        const int64_t s0 = max((int64_t)off[k], tile * MH_TILE), s1 = min((int64_t)off[k + 1], (tile + 1) * MH_TILE);
+        float part = 0.f;
+        for (int64_t s = s0 + lane; s < s1; s += 32) {
+            const float4 v = src32[s];
+            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha) * w32[s];
+        }
+        acc -= (double)part;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) out[t] += pref * acc;
 }
 
 // Normal-line rule: degree-4 interpolation in the distance through the interior limit
@@ -1037,10 +1198,10 @@ mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_
         if (!b->x32.p) MH_ALLOC(ctx, b->x32, b->n);
         k_to_float_vec<<<mh_grid(b->n, 256), 256, 0, ctx->stream>>>(x, b->x32.p, b->n);
         MH_LAUNCHED(ctx);
-        prof_scope ps(ctx, "bie_gemv");
+        prof_scope ps(ctx, "bie_gemv", 2.0 * b->n * b->n, 4.0 * b->n * b->n + 12.0 * b->n);
         k_gemv32<<<gemv_blocks(b->n), 256, 0, ctx->stream>>>(b->op.A32.p, b->x32.p, y, b->n);
     } else {
-        prof_scope ps(ctx, "bie_gemv");
+        prof_scope ps(ctx, "bie_gemv", 2.0 * b->n * b->n, 8.0 * b->n * b->n + 16.0 * b->n);
         k_gemv64<<<gemv_blocks(b->n), 256, 0, ctx->stream>>>(b->op.A64.p, x, y, b->n);
     }
     MH_LAUNCHED(ctx);
@@ -1155,13 +1316,13 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
         dbuf<double>& r = ws.r;
         dbuf<double>& dx = ws.dx;
         int total = 0;
-        for (int sweep = 0; sweep < 12 && total < max_iter; ++sweep) {
+        double rn = -1.0;
+        for (int sweep = 0;; ++sweep) {
             MH_TRY(bie_apply(ctx, bd, x, r.p, MH_PREC_FP64));
             k_sub_from<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(b, r.p, n);
             MH_LAUNCHED(ctx);
-            double rn;
             MH_TRY(vec_norm(ctx, r.p, n, ws.small.p + 2, &rn));
-            if (rn <= tol * bnorm) break;
+            if (rn <= tol * bnorm || total >= max_iter || sweep >= 12) break;
             MH_CUDA(ctx, cudaMemsetAsync(dx.p, 0, n * 8, ctx->stream));
             MH_CUDA(ctx, cudaMemsetAsync(ws.g.p, 0, (max_iter + 2) * 8, ctx->stream));
             int it;
@@ -1174,14 +1335,17 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
             MH_LAUNCHED(ctx);
         }
         inf.iterations = total;
+        inf.rel_residual = rn / bnorm;   // binary64 residual of the final iterate (last sweep)
     }
-    // true residual in binary64
-    MH_TRY(bie_apply(ctx, bd, x, ws.w.p, MH_PREC_FP64));
-    k_sub_from<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(b, ws.w.p, n);
-    MH_LAUNCHED(ctx);
-    double rn;
-    MH_TRY(vec_norm(ctx, ws.w.p, n, ws.small.p + 2, &rn));
-    inf.rel_residual = rn / bnorm;
+    if (prec == MH_PREC_FP64) {
+        // true residual in binary64
+        MH_TRY(bie_apply(ctx, bd, x, ws.w.p, MH_PREC_FP64));
+        k_sub_from<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(b, ws.w.p, n);
+        MH_LAUNCHED(ctx);
+        double rn;
+        MH_TRY(vec_norm(ctx, ws.w.p, n, ws.small.p + 2, &rn));
+        inf.rel_residual = rn / bnorm;
+    }
     inf.converged = inf.rel_residual <= tol;
     if (info) *info = inf;
     if (!inf.converged)
@@ -1236,6 +1400,18 @@ mh_status dlp_classify(mh_ctx* ctx, mh_boundary* b, const double* xy_dev, int64_
                 pc.push_back(k);
             }
     tg->n_pairs = (int64_t)pt.size();
+    tg->n_pairs_main = 0;
+    while (tg->n_pairs_main < tg->n_pairs && pt[tg->n_pairs_main] < n) tg->n_pairs_main++;
+    tg->fine_nodes_main = tg->fine_nodes_aux = tg->curve_nodes_main = 0;
+    for (int64_t i = 0; i < tg->n_pairs; ++i) {
+        const double nk = b->n_nodes[pc[i]];
+        if (i < tg->n_pairs_main) {
+            tg->fine_nodes_main += UPSAMPLE * nk;
+            tg->curve_nodes_main += nk;
+        } else {
+            tg->fine_nodes_aux += UPSAMPLE * nk;
+        }
+    }
     MH_ALLOC(ctx, tg->xy, 2 * tg->n_ext);
     MH_ALLOC(ctx, tg->fine, tg->n_ext);
     MH_ALLOC(ctx, tg->line_tgt, tg->n_line);
@@ -1309,7 +1485,7 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
         k_weights32<<<mh_grid(b->n, 256), 256, 0, st>>>(sigma, b->geo.p, b->d_curve_of.p, b->d_nn.p, b->n, b->w32.p);
         MH_LAUNCHED(ctx);
         if (tg->n_ext) {
-            prof_scope ps(ctx, "dlp_coarse");
+            prof_scope ps(ctx, "dlp_coarse", DL_FLOPS * tg->n_ext * b->n, 24.0 * (tg->n_ext + b->n));
             k_dlp_coarse32<<<mh_grid(tg->n_ext, MH_TILE), MH_TILE, 0, st>>>(
                 tg->xy.p, tg->fine.p, tg->n_ext, b->src32.p, b->w32.p, b->d_curve_of.p, b->tile_c.p, b->n,
                 (float)(1.0 / alpha), pref, ext.p);
@@ -1326,7 +1502,7 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
                                                                       b->d_fine_off.p, b->n_curves, b->n_fine,
                                                                       b->wf32.p);
             MH_LAUNCHED(ctx);
-            prof_scope ps(ctx, "dlp_fine");
+            prof_scope ps(ctx, "dlp_fine", DL_FLOPS * (tg->fine_nodes_main + tg->fine_nodes_aux), 24.0 * b->n_fine);
             k_dlp_fine32<<<mh_grid(tg->n_pairs * 32, 256), 256, 0, st>>>(
                 tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p, tg->n_pairs, b->fine32.p, b->wf32.p, b->d_fine_off.p,
                 b->d_fchunk_off.p, b->fchunk_c.p, (float)(1.0 / alpha), pref, ext.p);
@@ -1334,7 +1510,7 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
         }
     } else {
         if (tg->n_ext) {
-            prof_scope ps(ctx, "dlp_coarse");
+            prof_scope ps(ctx, "dlp_coarse", DL_FLOPS * tg->n_ext * b->n, 24.0 * (tg->n_ext + b->n));
             k_dlp_coarse<128><<<mh_grid(tg->n_ext, 128), 128, 0, st>>>(tg->xy.p, tg->fine.p, tg->n_ext, b->geo.p,
                                                                        sigma, b->d_curve_of.p, b->d_nn.p, b->n,
                                                                        1.0 / alpha, pref, ext.p);
@@ -1347,7 +1523,7 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
             k_fine_density<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(sc.p, b->fine_geo.p, b->d_nn.p, b->d_off.p,
                                                                      b->d_fine_off.p, b->n_curves, b->n_fine, wf.p);
             MH_LAUNCHED(ctx);
-            prof_scope ps(ctx, "dlp_fine");
+            prof_scope ps(ctx, "dlp_fine", DL_FLOPS * (tg->fine_nodes_main + tg->fine_nodes_aux), 24.0 * b->n_fine);
             k_dlp_fine<<<mh_grid(tg->n_pairs * 32, 256), 256, 0, st>>>(tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p,
                                                                        tg->n_pairs, b->fine_geo.p, wf.p,
                                                                        b->d_fine_off.p, 1.0 / alpha, pref, ext.p);
@@ -1362,6 +1538,131 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
         MH_LAUNCHED(ctx);
     }
     if (tg->n) MH_CUDA(ctx, cudaMemcpyAsync(out, ext.p, tg->n * 8, cudaMemcpyDeviceToDevice, st));
+    return MH_OK;
+}
+
+__global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
+mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_precision prec) {
+    cudaStream_t st = ctx->stream;
+    const int64_t nmodes = b->n / 2 + b->n_curves;
+    if (!b->sc64.p) {
+        MH_ALLOC(ctx, b->sc64, 2 * nmodes);
+        MH_ALLOC(ctx, b->sc32, 2 * nmodes);
+        MH_ALLOC(ctx, b->wf64, b->n_fine);
+    }
+    k_fourier_scalar<<<(unsigned)nmodes, 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->tw.p, b->n_curves, nmodes,
+                                                       b->sc64.p);
+    MH_LAUNCHED(ctx);
+    if (prec == MH_PREC_MIXED) {
+        MH_TRY(prep_mixed(ctx, b));
+        k_to_float_vec<<<mh_grid(2 * nmodes, 256), 256, 0, st>>>(b->sc64.p, b->sc32.p, 2 * nmodes);
+        MH_LAUNCHED(ctx);
+        k_fine_density32<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(b->sc32.p, b->fine_geo.p, b->d_nn.p, b->d_off.p,
+                                                                  b->d_fine_off.p, b->n_curves, b->n_fine, b->wf32.p);
+        MH_LAUNCHED(ctx);
+        k_f2d<<<mh_grid(b->n_fine, 256), 256, 0, st>>>(b->wf32.p, b->wf64.p, b->n_fine);
+        MH_LAUNCHED(ctx);
+    } else {
+        k_fine_density<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(b->sc64.p, b->fine_geo.p, b->d_nn.p, b->d_off.p,
+                                                                 b->d_fine_off.p, b->n_curves, b->n_fine, b->wf64.p);
+        MH_LAUNCHED(ctx);
+    }
+    return MH_OK;
+}
+
+mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* tg, const double* sigma,
+                                const double* main_vals, double* out, mh_precision prec, bool fine_in_fmm) {
+    cudaStream_t st = ctx->stream;
+    const double pref = -1.0 / (2.0 * MH_PI * alpha * alpha);
+    const int64_t n = tg->n, naux = tg->n_ext - tg->n;
+    const int64_t np_main = tg->n_pairs_main, np_aux = tg->n_pairs - tg->n_pairs_main;
+    dbuf<double>& ext = tg->ext;
+    dbuf<double>& sc = tg->sc;
+    dbuf<double>& wf = tg->wf;
+    prof_scope ps_all(ctx, "dlp_evaluate");
+    if (n) MH_CUDA(ctx, cudaMemcpyAsync(ext.p, main_vals, n * 8, cudaMemcpyDeviceToDevice, st));
+    const int64_t np_do_main = fine_in_fmm ? 0 : np_main;
+    if (tg->n_pairs && !fine_in_fmm) MH_TRY(dlp_fine_weights(ctx, b, sigma, prec));
+    (void)sc;
+    (void)wf;
+    if (prec == MH_PREC_MIXED) {
+        MH_TRY(prep_mixed(ctx, b));
+        k_weights32<<<mh_grid(b->n, 256), 256, 0, st>>>(sigma, b->geo.p, b->d_curve_of.p, b->d_nn.p, b->n, b->w32.p);
+        MH_LAUNCHED(ctx);
+        if (naux) {
+            // few auxiliary points: split the sources over the grid, then reduce in a fixed order
+            const int64_t nblk = (naux + MH_TILE - 1) / MH_TILE;
+            const int64_t ntile = (b->n + MH_TILE - 1) / MH_TILE;
+            const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, (152 * 8) / std::max<int64_t>(nblk, 1)));
+            if ((int64_t)tg->part.n < nsplit * naux) MH_ALLOC(ctx, tg->part, nsplit * naux);
+            k_dlp_coarse32<<<dim3((unsigned)nblk, (unsigned)nsplit), MH_TILE, 0, st>>>(
+                tg->xy.p + 2 * n, tg->fine.p + n, naux, b->src32.p, b->w32.p, b->d_curve_of.p, b->tile_c.p, b->n,
+                (float)(1.0 / alpha), pref, nsplit > 1 ? tg->part.p : ext.p + n);
+            MH_LAUNCHED(ctx);
+            if (nsplit > 1) {
+                k_sum_partials<<<mh_grid(naux, 256), 256, 0, st>>>(tg->part.p, nsplit, naux, pref, ext.p + n);
+                MH_LAUNCHED(ctx);
+            }
+        }
+        if (tg->n_pairs) {
+            prof_scope ps(ctx, "dlp_fine", DL_FLOPS * ((fine_in_fmm ? 0 : tg->fine_nodes_main + tg->curve_nodes_main) + tg->fine_nodes_aux), 24.0 * b->n_fine);
+            if (np_do_main) {
+                k_dlp_fine_corr32<<<mh_grid(np_do_main * 32, 256), 256, 0, st>>>(
+                    tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p, np_do_main, b->fine32.p, b->wf32.p, b->d_fine_off.p,
+                    b->d_fchunk_off.p, b->fchunk_c.p, b->src32.p, b->w32.p, b->tile_c.p, b->d_off.p,
+                    (float)(1.0 / alpha), pref, ext.p);
+                MH_LAUNCHED(ctx);
+            }
+            if (np_aux) {
+                k_dlp_fine32_blk<<<(unsigned)np_aux, 256, 0, st>>>(
+                    tg->xy.p, tg->pair_tgt.p + np_main, tg->pair_curve.p + np_main, b->fine32.p, b->wf32.p,
+                    b->d_fine_off.p, b->d_fchunk_off.p, b->fchunk_c.p, (float)(1.0 / alpha), pref, ext.p);
+                MH_LAUNCHED(ctx);
+            }
+        }
+    } else {
+        if (naux) {
+            const int64_t nblk = (naux + 127) / 128, ntile = (b->n + 127) / 128;
+            const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, (152 * 8) / std::max<int64_t>(nblk, 1)));
+            if ((int64_t)tg->part.n < nsplit * naux) MH_ALLOC(ctx, tg->part, nsplit * naux);
+            k_dlp_coarse<128><<<dim3((unsigned)nblk, (unsigned)nsplit), 128, 0, st>>>(
+                tg->xy.p + 2 * n, tg->fine.p + n, naux, b->geo.p, sigma, b->d_curve_of.p, b->d_nn.p, b->n, 1.0 / alpha,
+                pref, nsplit > 1 ? tg->part.p : ext.p + n);
+            MH_LAUNCHED(ctx);
+            if (nsplit > 1) {
+                k_sum_partials<<<mh_grid(naux, 256), 256, 0, st>>>(tg->part.p, nsplit, naux, pref, ext.p + n);
+                MH_LAUNCHED(ctx);
+            }
+        }
+        if (tg->n_pairs) {
+            prof_scope ps(ctx, "dlp_fine", DL_FLOPS * ((fine_in_fmm ? 0 : tg->fine_nodes_main + tg->curve_nodes_main) + tg->fine_nodes_aux), 24.0 * b->n_fine);
+            if (np_do_main) {
+                k_dlp_fine_corr<<<mh_grid(np_do_main * 32, 256), 256, 0, st>>>(
+                    tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p, np_do_main, b->fine_geo.p, b->wf64.p,
+                    b->d_fine_off.p, b->geo.p, sigma, b->d_nn.p, b->d_off.p, 1.0 / alpha, pref, ext.p);
+                MH_LAUNCHED(ctx);
+            }
+            if (np_aux) {
+                k_dlp_fine64_blk<<<(unsigned)np_aux, 256, 0, st>>>(tg->xy.p, tg->pair_tgt.p + np_main,
+                                                                   tg->pair_curve.p + np_main, b->fine_geo.p,
+                                                                   b->wf64.p, b->d_fine_off.p, 1.0 / alpha, pref,
+                                                                   ext.p);
+                MH_LAUNCHED(ctx);
+            }
+        }
+    }
+    if (tg->n_line) {
+        MH_TRY(bie_apply(ctx, b, sigma, tg->asig.p, prec));
+        k_dlp_line<<<mh_grid(tg->n_line * 32, 256), 256, 0, st>>>(tg->line_tgt.p, tg->line_curve.p, tg->line_data.p,
+                                                                  tg->n_line, tg->asig.p, b->d_nn.p, b->d_off.p,
+                                                                  b->half.p, tg->n, alpha, ext.p);
+        MH_LAUNCHED(ctx);
+    }
+    if (n) MH_CUDA(ctx, cudaMemcpyAsync(out, ext.p, n * 8, cudaMemcpyDeviceToDevice, st));
     return MH_OK;
 }
 

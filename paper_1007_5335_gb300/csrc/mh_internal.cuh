@@ -19,6 +19,7 @@ struct prof_region {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     double total_ms = 0.0;
     int64_t launches = 0;
+    double flops = 0.0, bytes = 0.0;   // algorithmic work of the timed launches
 };
 
 struct mh_ctx {
@@ -36,8 +37,9 @@ struct mh_ctx {
 struct prof_scope {
     mh_ctx* ctx;
     const char* name;
+    double flops, bytes;
     cudaEvent_t a = nullptr, b = nullptr;
-    prof_scope(mh_ctx* c, const char* n);
+    prof_scope(mh_ctx* c, const char* n, double flops_ = 0.0, double bytes_ = 0.0);
     ~prof_scope();
 };
 
@@ -132,6 +134,8 @@ struct mh_boundary {
     dbuf<float4> src32, fine32;          // (dx, dy, nx, ny)
     dbuf<double2> tile_c, fchunk_c;
     dbuf<float> w32, wf32, x32;          // per call: weights, fine weights, GEMV input
+    dbuf<double> sc64, wf64;             // per call: density Fourier coefficients, fine weights
+    dbuf<float> sc32;
 };
 
 #define MH_TILE 128
@@ -149,10 +153,11 @@ struct dlp_targets {
     dbuf<int32_t> line_curve;   // curve
     dbuf<double> line_data;     // [n_line][4]: t*, d, h_s, unused
     // fine pairs (ext target, curve)
-    int64_t n_pairs = 0;
+    int64_t n_pairs = 0, n_pairs_main = 0;   // pairs of user targets come first
+    double fine_nodes_main = 0, fine_nodes_aux = 0, curve_nodes_main = 0;   // work counts
     dbuf<int32_t> pair_tgt, pair_curve;
     // evaluation workspaces (allocated once by dlp_classify)
-    dbuf<double> ext, sc, wf, asig;
+    dbuf<double> ext, sc, wf, asig, part;
 };
 
 struct mh_tree {
@@ -195,6 +200,16 @@ mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_
 mh_status dlp_classify(mh_ctx* ctx, mh_boundary* b, const double* xy_dev, int64_t n, dlp_targets* tg);
 mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* tg,
                        const double* sigma, double* out, mh_precision prec);
+// U^h when the trapezoid sum at the user targets (main_vals, n values) comes from the
+// multipole method: adds the near-boundary corrections and the normal-line rule.
+// fine_in_fmm: main_vals already use the 16x upsampled rule on every curve (the fine
+// nodes went through the multipole method), so only the auxiliary points of the
+// normal-line rule need near-boundary work.  Requires dlp_fine_weights for this sigma.
+mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* tg, const double* sigma,
+                                const double* main_vals, double* out, mh_precision prec, bool fine_in_fmm);
+// Density on the 16x fine grid times |y'| h_f (binary64 in b->wf64; binary32 also in b->wf32
+// when prec is mixed).
+mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_precision prec);
 mh_status gmres_run(mh_ctx* ctx, mh_boundary* b, const double* rhs, double* x, double tol, int max_iter,
                     mh_precision prec, mh_gmres_info* info);
 
@@ -206,6 +221,10 @@ const double* tree_gl_nodes(const mh_tree* t);
 mh_status volume_apply(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* b, double* up,
                        mh_precision prec);
 void volume_free(mh_tree* t);
+// double layer through the multipole method (dipoles sorted by leaf)
+mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* dxy, const double* dnrm,
+                              const int32_t* dleaf, int64_t nd, bool near_blocks);
+mh_status volume_dipole_apply(mh_ctx* ctx, mh_tree* t, const double* w_sorted, mh_precision prec, const double** u);
 mh_status tree_locate(mh_ctx* ctx, const mh_tree* t, const double* xy_dev, int64_t n, int32_t* leaf_out);
 mh_status tree_interpolate(mh_ctx* ctx, const mh_tree* t, const double* vals, const double* xy_dev,
                            const int32_t* leaf, int64_t n, double* out);

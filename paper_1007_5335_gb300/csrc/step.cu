@@ -54,8 +54,21 @@ __global__ void k_gather_xy(const double* __restrict__ xy, const int32_t* __rest
 
 }  // namespace
 
+__global__ void k_dip_weights(const double* __restrict__ wf, const int32_t* __restrict__ perm, int64_t n,
+                              double* w) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < n) w[j] = wf[perm[j]];
+}
+
+__global__ void k_gather(const double* __restrict__ src, const int32_t* __restrict__ idx, int64_t n, double* out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = src[idx[i]];
+}
+
 struct ProblemImpl : mh_problem {
     dbuf<int32_t> slot;       // position of an inside node in the inside list, else -1
+    dbuf<int32_t> perm;       // boundary nodes sorted by leaf: sorted position -> node
+    dbuf<double> w_sorted;    // dipole strengths in that order
 };
 
 extern "C" mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* bnd, double dt, int p, int ext_mode,
@@ -118,6 +131,49 @@ extern "C" mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* 
         for (int64_t i = 0; i < bnd->n; ++i)
             if (bl[i] < 0) return mh_fail(ctx, MH_ERR_GEOMETRY, "boundary node %lld lies outside the tree", (long long)i);
     }
+    // Dipole sources of the double layer for the multipole pass: the 16x fine nodes of every
+    // curve (the upsampled rule, applied at every volume node; for nodes at least 5 h_s from
+    // a curve it agrees with the trapezoid rule to ~e^{-2 pi 5}), sorted by leaf.
+    {
+        const int64_t nf = bnd->n_fine;
+        std::vector<double> fg(6 * nf), fxy(2 * nf);
+        MH_CUDA(ctx, cudaMemcpyAsync(fg.data(), bnd->fine_geo.p, 6 * nf * 8, cudaMemcpyDeviceToHost, st));
+        MH_CUDA(ctx, cudaStreamSynchronize(st));
+        for (int64_t f = 0; f < nf; ++f) {
+            fxy[2 * f] = fg[6 * f];
+            fxy[2 * f + 1] = fg[6 * f + 1];
+        }
+        dbuf<double> dfxy;
+        dbuf<int32_t> dfleaf;
+        MH_ALLOC(ctx, dfxy, 2 * nf);
+        MH_ALLOC(ctx, dfleaf, nf);
+        MH_CUDA(ctx, cudaMemcpyAsync(dfxy.p, fxy.data(), 2 * nf * 8, cudaMemcpyHostToDevice, st));
+        MH_TRY(tree_locate(ctx, tree, dfxy.p, nf, dfleaf.p));
+        std::vector<int32_t> fl(nf);
+        MH_CUDA(ctx, cudaMemcpyAsync(fl.data(), dfleaf.p, nf * 4, cudaMemcpyDeviceToHost, st));
+        MH_CUDA(ctx, cudaStreamSynchronize(st));
+        std::vector<int32_t> perm(nf);
+        for (int64_t i = 0; i < nf; ++i) {
+            if (fl[i] < 0) return mh_fail(ctx, MH_ERR_GEOMETRY, "fine boundary point %lld lies outside the tree",
+                                          (long long)i);
+            perm[i] = (int32_t)i;
+        }
+        std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t c) { return fl[a] < fl[c]; });
+        std::vector<double> dxy(2 * nf), dnrm(2 * nf);
+        std::vector<int32_t> dleaf(nf);
+        for (int64_t j = 0; j < nf; ++j) {
+            const double* g = &fg[6 * (int64_t)perm[j]];
+            dxy[2 * j] = g[0];
+            dxy[2 * j + 1] = g[1];
+            dnrm[2 * j] = g[2];
+            dnrm[2 * j + 1] = g[3];
+            dleaf[j] = fl[perm[j]];
+        }
+        MH_TRY(volume_dipole_setup(ctx, tree, P->alpha, p, dxy.data(), dnrm.data(), dleaf.data(), nf, false));
+        MH_ALLOC(ctx, P->perm, nf);
+        MH_ALLOC(ctx, P->w_sorted, nf);
+        MH_CUDA(ctx, cudaMemcpyAsync(P->perm.p, perm.data(), nf * 4, cudaMemcpyHostToDevice, st));
+    }
     MH_ALLOC(ctx, P->B, n);
     MH_ALLOC(ctx, P->Up, n);
     MH_ALLOC(ctx, P->Ug, bnd->n);
@@ -171,7 +227,17 @@ extern "C" mh_status heat_step(mh_ctx* ctx, mh_problem* prob, const double* u_de
         info->gmres_rel_residual = gi.rel_residual;
     }
     if (s != MH_OK) return s;
-    MH_TRY(dlp_evaluate(ctx, b, P->alpha, &P->tg, sigma_dev, P->Uh.p, prec));
+    // U^h: trapezoid sum by the multipole method at every node, then the near-boundary rules
+    MH_TRY(dlp_fine_weights(ctx, b, sigma_dev, prec));
+    k_dip_weights<<<mh_grid(b->n_fine, 256), 256, 0, st>>>(b->wf64.p, P->perm.p, b->n_fine, P->w_sorted.p);
+    MH_LAUNCHED(ctx);
+    const double* du = nullptr;
+    MH_TRY(volume_dipole_apply(ctx, t, P->w_sorted.p, prec, &du));
+    if (P->n_inside) {
+        k_gather<<<mh_grid(P->n_inside, 256), 256, 0, st>>>(du, P->inside_idx.p, P->n_inside, P->Uh.p);
+        MH_LAUNCHED(ctx);
+    }
+    MH_TRY(dlp_evaluate_fmm_tail(ctx, b, P->alpha, &P->tg, sigma_dev, P->Uh.p, P->Uh.p, prec, true));
     k_combine<<<mh_grid(n, 256), 256, 0, st>>>(P->Up.p, P->Uh.p, P->region.p, P->slot.p, P->d_ext_const.p,
                                                P->ext_mode, n, u_next_dev);
     MH_LAUNCHED(ctx);

@@ -286,6 +286,7 @@ struct Task {
 struct Phase {
     int R = 0;
     bool accumulate = false;
+    double flops = 0, bytes = 0;   // per run: 2 R C per task; operators, sources, products, outputs
     int64_t n_tasks = 0, n_dst = 0, n_chunks = 0;
     int smem = 0;
     dbuf<int32_t> chunk_op, chunk_t0, dst_ptr, dst_task;
@@ -305,9 +306,17 @@ struct OpPool {
     }
 };
 
+struct DipData;
+
 struct VolData {
     double alpha = -1;
     int p = -1;
+    // host copies kept for the dipole (double-layer) multipole pass
+    OpPool pool_host;
+    std::map<std::tuple<int, int, int, int>, int> m2l_key, m2p_key;
+    std::vector<int> op_p2m, op_l2p;
+    std::vector<std::array<int, 4>> op_m2m, op_l2l;
+    std::unique_ptr<DipData> dip;
     int P = 0, qq = 0;
     int64_t B_off = 0, U_off = 0, M_off = 0, L_off = 0, vec_len = 0;
     dbuf<double> ops64, vec, temp;
@@ -341,7 +350,10 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
             ct0.push_back((int32_t)s);
         }
         maxC = std::max(maxC, op_C[t.op]);
+        ph->flops += 2.0 * R * op_C[t.op];
+        ph->bytes += 8.0 * op_C[t.op] + 16.0 * R;   // source vector, product write + read
     }
+    for (size_t c = 0; c < cop.size(); ++c) ph->bytes += 8.0 * R * op_C[cop[c]];   // operator per chunk
     ph->n_chunks = (int64_t)cop.size();
     ct0.push_back((int32_t)order.size());   // end of the last chunk
     // destinations: tasks grouped by destination in generation order
@@ -358,6 +370,8 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
     }
     ph->n_dst = (int64_t)doff.size();
     ph->smem = (int)((R + CHUNK) * (maxC + 1) * sizeof(double));
+    if (ph->smem > 160 * 1024)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "contraction operator too large for shared memory (%d x %d)", R, maxC);
     cudaStream_t st = ctx->stream;
     auto up32 = [&](dbuf<int32_t>& b, const std::vector<int32_t>& v) -> mh_status {
         MH_ALLOC(ctx, b, std::max<size_t>(v.size(), 1));
@@ -381,19 +395,24 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
 }
 
 template <typename TOP>
-mh_status run_phase(mh_ctx* ctx, VolData* V, const TOP* ops, const Phase* ph) {
+mh_status run_phase_on(mh_ctx* ctx, const TOP* ops, const int64_t* op_off, const int32_t* op_C, double* vec,
+                       double* temp, const Phase* ph, const char* region) {
     if (ph->n_tasks == 0) return MH_OK;
     const int smem = (int)(ph->smem / sizeof(double) * sizeof(TOP));
-    prof_scope ps(ctx, "volume_contract");
-    k_apply<TOP><<<(unsigned)ph->n_chunks, 256, smem, ctx->stream>>>(ops, V->d_op_off.p, V->d_op_C.p, ph->chunk_op.p,
-                                                                     ph->chunk_t0.p, ph->task_src.p, V->vec.p, ph->R,
-                                                                     V->temp.p);
+    prof_scope ps(ctx, region, ph->flops, ph->bytes + 8.0 * ph->R * ph->n_dst * (ph->accumulate ? 2 : 1));
+    k_apply<TOP><<<(unsigned)ph->n_chunks, 256, smem, ctx->stream>>>(ops, op_off, op_C, ph->chunk_op.p,
+                                                                     ph->chunk_t0.p, ph->task_src.p, vec, ph->R,
+                                                                     temp);
     MH_LAUNCHED(ctx);
-    k_reduce<<<mh_grid(ph->n_dst * 32, 256), 256, 0, ctx->stream>>>(V->temp.p, ph->R, ph->dst_off.p, ph->dst_ptr.p,
-                                                                    ph->dst_task.p, ph->n_dst, ph->accumulate,
-                                                                    V->vec.p);
+    k_reduce<<<mh_grid(ph->n_dst * 32, 256), 256, 0, ctx->stream>>>(temp, ph->R, ph->dst_off.p, ph->dst_ptr.p,
+                                                                    ph->dst_task.p, ph->n_dst, ph->accumulate, vec);
     MH_LAUNCHED(ctx);
     return MH_OK;
+}
+
+template <typename TOP>
+mh_status run_phase(mh_ctx* ctx, VolData* V, const TOP* ops, const Phase* ph) {
+    return run_phase_on<TOP>(ctx, ops, V->d_op_off.p, V->d_op_C.p, V->vec.p, V->temp.p, ph, "volume_contract");
 }
 
 struct HostTree {
@@ -692,6 +711,13 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
     // near tables on the device, appended to the pool
     const int nnear = (int)near_cfg.size();
     V->n_near_tables = nnear;
+    V->m2l_key = m2l_key;
+    V->m2p_key = m2p_key;
+    V->op_p2m = op_p2m;
+    V->op_l2p = op_l2p;
+    V->op_m2m = op_m2m;
+    V->op_l2l = op_l2l;
+    V->pool_host = pool;   // before the near tables are appended (their data lives on the device only)
     const int64_t near_base = (int64_t)pool.data.size();
     const int first_near_op = (int)pool.off.size();
     for (int i = 0; i < nnear; ++i) {
@@ -767,6 +793,483 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
 }
 
 }  // namespace
+
+// ---------------- double layer through the multipole method ----------------
+//
+// Dipole sources at the boundary nodes y_d (unit normal nu_d = e^{i psi}, strength w_d =
+// sigma_d |y'_d| h) give U^h(x) = (1/(2 pi alpha^2)) sum_d w_d d/dnu K0(k |x - y_d|)
+// (Section 2).  With G_n(v) = I_n(k|v|) e^{-i n arg v} and H_n(u) = K_n(k|u|) e^{-i n arg u}:
+//   d/dnu G_n = (k/2) [e^{-i psi} G_{n-1} + e^{i psi} G_{n+1}]    (dipole multipole, P2M)
+//   d/dnu H_n = -(k/2) [e^{-i psi} H_{n-1} + e^{i psi} H_{n+1}]   (dipole local, P2L)
+// and the near field is the trapezoid kernel value itself.  The translation operators
+// (M2M, M2L, L2L, L2P, M2P) are those of the volume pass.
+namespace {
+
+// Near field of the double layer on the fly.  One block of NEAR_T threads per target leaf
+// that has dipoles in its U list; thread t handles node t % q^2 for the quarter t / q^2 of
+// each staged source tile (q^2 <= 64); the quarters are summed in a fixed order.
+//   out[node] += -(1/(2 pi alpha^2)) sum_d w_d (1/alpha) K1(r/alpha) (y_d - x).nu_d / r
+constexpr int NEAR_T = 256;
+
+__global__ void __launch_bounds__(NEAR_T) k_dip_near64(
+    const double* __restrict__ nodes, const int32_t* __restrict__ active, const int32_t* __restrict__ near_ptr,
+    const int32_t* __restrict__ near_leaf, const int64_t* __restrict__ seg0, const int32_t* __restrict__ segn,
+    const double2* __restrict__ dxy, const double2* __restrict__ dnrm, const double* __restrict__ w, int qq,
+    double inv_alpha, double pref, double* out) {
+    __shared__ double2 sp[NEAR_T], sn[NEAR_T];
+    __shared__ double sw[NEAR_T];
+    __shared__ double part[NEAR_T];
+    const int leaf = active[blockIdx.x];
+    const int groups = NEAR_T / qq;   // >= 4 for q <= 8
+    const int i = threadIdx.x % qq, g = threadIdx.x / qq;
+    const bool act = g < groups;
+    const int64_t node = (int64_t)leaf * qq + i;
+    const double px = nodes[2 * node], py = nodes[2 * node + 1];
+    double acc = 0.0;
+    for (int j = near_ptr[leaf]; j < near_ptr[leaf + 1]; ++j) {
+        const int lc = near_leaf[j];
+        const int64_t s0 = seg0[lc];
+        const int cnt = segn[lc];
+        for (int b0 = 0; b0 < cnt; b0 += NEAR_T) {
+            const int m = min(NEAR_T, cnt - b0);
+            __syncthreads();
+            if (threadIdx.x < m) {
+                sp[threadIdx.x] = dxy[s0 + b0 + threadIdx.x];
+                sn[threadIdx.x] = dnrm[s0 + b0 + threadIdx.x];
+                sw[threadIdx.x] = w[s0 + b0 + threadIdx.x];
+            }
+            __syncthreads();
+            if (act)
+                for (int e = g; e < m; e += groups) {
+                    const double dx = sp[e].x - px, dy = sp[e].y - py;
+                    const double r = sqrt(dx * dx + dy * dy);
+                    if (r > 0.0) acc += mh_k1(r * inv_alpha) * inv_alpha * (dx * sn[e].x + dy * sn[e].y) / r * sw[e];
+                }
+        }
+    }
+    part[threadIdx.x] = act ? acc : 0.0;
+    __syncthreads();
+    if (threadIdx.x < qq) {
+        double tot = 0.0;
+        for (int gg = 0; gg < groups; ++gg) tot += part[gg * qq + threadIdx.x];
+        out[node] -= pref * tot;
+    }
+}
+
+__global__ void __launch_bounds__(NEAR_T) k_dip_near32(
+    const double* __restrict__ nodes, const int32_t* __restrict__ active, const int32_t* __restrict__ near_ptr,
+    const int32_t* __restrict__ near_leaf, const int64_t* __restrict__ seg0, const int32_t* __restrict__ segn,
+    const double2* __restrict__ leaf_c, const float4* __restrict__ d32, const float* __restrict__ w, int qq,
+    float inv_alpha, double pref, double* out) {
+    __shared__ float4 s4[NEAR_T];
+    __shared__ float sw[NEAR_T];
+    __shared__ double part[NEAR_T];
+    const int leaf = active[blockIdx.x];
+    const int groups = NEAR_T / qq;
+    const int i = threadIdx.x % qq, g = threadIdx.x / qq;
+    const bool act = g < groups;
+    const int64_t node = (int64_t)leaf * qq + i;
+    const double px = nodes[2 * node], py = nodes[2 * node + 1];
+    double acc = 0.0;
+    for (int j = near_ptr[leaf]; j < near_ptr[leaf + 1]; ++j) {
+        const int lc = near_leaf[j];
+        const int64_t s0 = seg0[lc];
+        const int cnt = segn[lc];
+        const double2 c = leaf_c[lc];
+        const float tx = (float)(px - c.x), ty = (float)(py - c.y);
+        for (int b0 = 0; b0 < cnt; b0 += NEAR_T) {
+            const int m = min(NEAR_T, cnt - b0);
+            __syncthreads();
+            if (threadIdx.x < m) {
+                s4[threadIdx.x] = d32[s0 + b0 + threadIdx.x];
+                sw[threadIdx.x] = w[s0 + b0 + threadIdx.x];
+            }
+            __syncthreads();
+            if (act) {
+                float pt = 0.f;
+                for (int e = g; e < m; e += groups) {
+                    const float4 v = s4[e];
+                    const float dx = v.x - tx, dy = v.y - ty;
+                    const float r2 = dx * dx + dy * dy;
+                    if (r2 > 0.f) {
+                        const float rinv = rsqrtf(r2);
+                        pt += mh_k1f(r2 * rinv * inv_alpha) * inv_alpha * (dx * v.z + dy * v.w) * rinv * sw[e];
+                    }
+                }
+                acc += (double)pt;
+            }
+        }
+    }
+    part[threadIdx.x] = act ? acc : 0.0;
+    __syncthreads();
+    if (threadIdx.x < qq) {
+        double tot = 0.0;
+        for (int gg = 0; gg < groups; ++gg) tot += part[gg * qq + threadIdx.x];
+        out[node] -= pref * tot;
+    }
+}
+
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+struct DipData {
+    int64_t nd = 0;
+    int64_t W_off = 0, DM_off = 0, DL_off = 0, DU_off = 0, vec_len = 0;
+    // near field evaluated on the fly: per target leaf the source segments of its U list
+    bool near_blocks = true;
+    int qq = 0;
+    dbuf<int32_t> near_ptr, near_leaf;     // CSR over target leaves -> source leaves with dipoles
+    dbuf<int32_t> active;                  // target leaves with a non-empty near list
+    int64_t n_active = 0;
+    dbuf<int64_t> seg0;                    // first dipole of every leaf (-1 if none), count in segn
+    dbuf<int32_t> segn;
+    dbuf<double2> leaf_c, dxy, dnrm;       // leaf centres; dipole positions and normals (sorted)
+    dbuf<float4> d32;                      // dipole offset from its leaf centre + normal (binary32)
+    dbuf<float> w32;
+    double pref = 0, inv_alpha = 0;
+    double near_pairs = 0;
+    dbuf<double> vec, temp, ops64;
+    dbuf<float> ops32;
+    dbuf<int64_t> d_op_off;
+    dbuf<int32_t> d_op_C;
+    std::unique_ptr<Phase> p2m, m2l, out;
+    std::vector<std::unique_ptr<Phase>> m2m, l2l;
+};
+}  // namespace
+
+static mh_status volume_ensure(mh_ctx* ctx, mh_tree* t, double alpha, int p) {
+    VolData* V = static_cast<VolData*>(t->vol);
+    if (V && V->alpha == alpha && V->p == p) return MH_OK;
+    delete V;
+    V = new VolData();
+    t->vol = V;
+    mh_status s = volume_setup(ctx, t, alpha, p, V);
+    if (s != MH_OK) {
+        delete V;
+        t->vol = nullptr;
+    }
+    return s;
+}
+
+mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* dxy, const double* dnrm,
+                              const int32_t* dleaf, int64_t nd, bool near_blocks) {
+    if (!near_blocks && t->q * t->q > 64) near_blocks = true;   // the on-the-fly kernel handles q <= 8
+    MH_TRY(volume_ensure(ctx, t, alpha, p));
+    VolData* V = static_cast<VolData*>(t->vol);
+    const int q = t->q, qq = q * q, P = 2 * p + 1, L = t->max_level;
+    const double k = 1.0 / alpha, pref = 1.0 / (2.0 * MH_PI * alpha * alpha);
+    const double x0 = t->box[0], y0 = t->box[1], W = t->box[2];
+    HostTree h;
+    MH_TRY(fetch_tree(ctx, t, &h));
+    const int64_t nb = t->n_boxes, nl = t->n_leaves;
+    auto lev = [&](int b) { return h.boxes[3 * b]; };
+    auto width = [&](int l) { return W / (double)(1 << l); };
+    auto centre = [&](int b) {
+        const double w = width(lev(b));
+        return std::complex<double>(x0 + (h.boxes[3 * b + 1] + 0.5) * w, y0 + (h.boxes[3 * b + 2] + 0.5) * w);
+    };
+    std::vector<double> qx(q), qw(q);
+    mh_gauss_legendre(q, qx.data(), qw.data());
+    std::vector<std::vector<double>> Is(L + 1, std::vector<double>(p + 2));
+    for (int l = 0; l <= L; ++l)
+        for (int n = 0; n <= p + 1; ++n) Is[l][n] = h_in(n, k * width(l) * 0.70710678118654752);
+    // dipole segments per leaf (sources are sorted by leaf)
+    std::vector<int64_t> seg0(nl, -1), segn(nl, 0);
+    for (int64_t d = 0; d < nd; ++d) {
+        const int lf = dleaf[d];
+        if (seg0[lf] < 0) seg0[lf] = d;
+        segn[lf]++;
+    }
+    std::unique_ptr<DipData> D(new DipData());
+    D->nd = nd;
+    D->near_blocks = near_blocks;
+    D->qq = qq;
+    D->pref = pref;
+    D->inv_alpha = k;
+    std::vector<int32_t> nptr{0}, nleaf;
+    D->W_off = 0;
+    D->DM_off = nd;
+    D->DL_off = D->DM_off + nb * P;
+    D->DU_off = D->DL_off + nb * P;
+    D->vec_len = D->DU_off + nl * qq;
+    OpPool pool = V->pool_host;
+    std::vector<Task> t_p2m, t_m2l, t_out;
+    std::vector<std::vector<Task>> t_m2m(L + 1), t_l2l(L + 1);
+    std::vector<double> buf, Kb(p + 3), Ib(p + 3);
+    auto set_row = [&](double* m, int cols, int col, int n, std::complex<double> v) {
+        if (n == 0)
+            m[col] = v.real();
+        else {
+            m[(2 * n - 1) * cols + col] = v.real();
+            m[(2 * n) * cols + col] = v.imag();
+        }
+    };
+    // operators wider than CMAX columns are split into column blocks reducing into one destination
+    constexpr int CMAX = 128;
+    std::vector<double> sub;
+    auto add_split = [&](int R, int nc, const std::vector<double>& m, int64_t src, int64_t dst, std::vector<Task>& tl) {
+        for (int c0 = 0; c0 < nc; c0 += CMAX) {
+            const int cw = std::min(CMAX, nc - c0);
+            sub.assign((size_t)R * cw, 0.0);
+            for (int r = 0; r < R; ++r)
+                for (int c = 0; c < cw; ++c) sub[(size_t)r * cw + c] = m[(size_t)r * nc + c0 + c];
+            tl.push_back(Task{pool.add(R, cw, sub.data()), src + c0, dst});
+        }
+    };
+    auto Gm = [&](int m, std::complex<double> v, const std::vector<double>& I) {
+        return I[std::abs(m)] * std::polar(1.0, -m * std::arg(v));
+    };
+    for (int64_t b = 0; b < nb; ++b) {
+        const int l = lev((int)b);
+        const int leaf = h.box_leaf[b];
+        if (leaf >= 0) {
+            // dipole P2M of this leaf
+            if (l >= 2 && segn[leaf] > 0) {
+                const int nc = (int)segn[leaf];
+                buf.assign((size_t)P * nc, 0.0);
+                const std::complex<double> c = centre((int)b);
+                for (int j = 0; j < nc; ++j) {
+                    const int64_t d = seg0[leaf] + j;
+                    const std::complex<double> v = std::complex<double>(dxy[2 * d], dxy[2 * d + 1]) - c;
+                    const double psi = std::atan2(dnrm[2 * d + 1], dnrm[2 * d]);
+                    for (int n = 0; n <= p + 1; ++n) Ib[n] = h_in(n, k * std::abs(v));
+                    for (int n = 0; n <= p; ++n) {
+                        const std::complex<double> Dn =
+                            0.5 * k * (std::polar(1.0, -psi) * Gm(n - 1, v, Ib) + std::polar(1.0, psi) * Gm(n + 1, v, Ib));
+                        set_row(buf.data(), nc, j, n, pref * Dn / Is[l][n]);
+                    }
+                }
+                add_split(P, nc, buf, D->W_off + seg0[leaf], D->DM_off + b * P, t_p2m);
+            }
+            if (l >= 2) t_out.push_back(Task{V->op_l2p[l], D->DL_off + b * P, D->DU_off + (int64_t)leaf * qq});
+            // W list: M2P with the volume operators
+            for (int j = h.off[2][b]; j < h.off[2][b + 1]; ++j) {
+                const int c = h.item[2][j];
+                auto key = std::make_tuple(l, h.boxes[3 * c + 1] - 2 * h.boxes[3 * b + 1],
+                                           h.boxes[3 * c + 2] - 2 * h.boxes[3 * b + 2], 0);
+                t_out.push_back(Task{V->m2p_key.at(key), D->DM_off + (int64_t)c * P, D->DU_off + (int64_t)leaf * qq});
+            }
+            // U list: direct dipole sums from neighbour leaves, as dense (q^2 x n_c) blocks or
+            // (near_blocks == false) evaluated on the fly by k_dip_near
+            const std::complex<double> cb = centre((int)b);
+            const double wb = width(l);
+            for (int j = h.off[0][b]; j < h.off[0][b + 1]; ++j) {
+                const int c = h.item[0][j];
+                const int lc = h.box_leaf[c];
+                if (segn[lc] == 0) continue;
+                if (!near_blocks) {
+                    nleaf.push_back(lc);
+                    D->near_pairs += (double)qq * segn[lc];
+                    continue;
+                }
+                const int nc = (int)segn[lc];
+                buf.assign((size_t)qq * nc, 0.0);
+                for (int i = 0; i < qq; ++i) {
+                    const double xx = cb.real() + 0.5 * wb * qx[i % q], xy = cb.imag() + 0.5 * wb * qx[i / q];
+                    for (int jj = 0; jj < nc; ++jj) {
+                        const int64_t d = seg0[lc] + jj;
+                        const double dx = dxy[2 * d] - xx, dy = dxy[2 * d + 1] - xy;
+                        const double r = std::hypot(dx, dy);
+                        if (r > 0)
+                            buf[(size_t)i * nc + jj] =
+                                -pref * h_k1(r * k) * k * (dx * dnrm[2 * d] + dy * dnrm[2 * d + 1]) / r;
+                    }
+                }
+                add_split(qq, nc, buf, D->W_off + seg0[lc], D->DU_off + (int64_t)leaf * qq, t_out);
+            }
+        }
+        if (l < 2) continue;
+        for (int j = h.off[1][b]; j < h.off[1][b + 1]; ++j) {
+            const int s2 = h.item[1][j];
+            auto key = std::make_tuple(l, h.boxes[3 * s2 + 1] - h.boxes[3 * b + 1], h.boxes[3 * s2 + 2] - h.boxes[3 * b + 2], 0);
+            t_m2l.push_back(Task{V->m2l_key.at(key), D->DM_off + (int64_t)s2 * P, D->DL_off + b * P});
+        }
+        // X list: dipole P2L
+        for (int j = h.off[3][b]; j < h.off[3][b + 1]; ++j) {
+            const int c = h.item[3][j];
+            const int lc = h.box_leaf[c];
+            if (segn[lc] == 0) continue;
+            const int nc = (int)segn[lc];
+            buf.assign((size_t)P * nc, 0.0);
+            const std::complex<double> ct = centre((int)b);
+            for (int jj = 0; jj < nc; ++jj) {
+                const int64_t d = seg0[lc] + jj;
+                const std::complex<double> u = std::complex<double>(dxy[2 * d], dxy[2 * d + 1]) - ct;
+                const double psi = std::atan2(dnrm[2 * d + 1], dnrm[2 * d]);
+                h_kn_all(k * std::abs(u), p + 1, Kb.data());
+                for (int m = 0; m <= p; ++m) {
+                    const std::complex<double> Dm =
+                        -0.5 * k * (std::polar(1.0, -psi) * Gm(m - 1, u, Kb) + std::polar(1.0, psi) * Gm(m + 1, u, Kb));
+                    set_row(buf.data(), nc, jj, m, Is[l][m] * pref * Dm);
+                }
+            }
+            add_split(P, nc, buf, D->W_off + seg0[lc], D->DL_off + b * P, t_m2l);
+        }
+    }
+    {
+        std::vector<int32_t> child(4 * nb);
+        MH_CUDA(ctx, cudaMemcpyAsync(child.data(), t->box_child.p, 4 * nb * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int64_t b = 0; b < nb; ++b) {
+            const int l = lev((int)b);
+            if (h.box_leaf[b] >= 0 || l < 2 || l >= L) continue;
+            for (int c = 0; c < 4; ++c) {
+                const int ch = child[4 * b + c];
+                if (ch < 0) continue;
+                t_m2m[l].push_back(Task{V->op_m2m[l][c], D->DM_off + (int64_t)ch * P, D->DM_off + b * P});
+                t_l2l[l].push_back(Task{V->op_l2l[l][c], D->DL_off + b * P, D->DL_off + (int64_t)ch * P});
+            }
+        }
+    }
+    if (!near_blocks) {
+        // CSR over target leaves (in leaf order) of the source leaves holding dipoles
+        std::vector<std::vector<int32_t>> per(nl);
+        {
+            size_t pos = 0;
+            for (int64_t b = 0; b < nb; ++b) {
+                const int leaf = h.box_leaf[b];
+                if (leaf < 0) continue;
+                for (int j = h.off[0][b]; j < h.off[0][b + 1]; ++j) {
+                    const int lc = h.box_leaf[h.item[0][j]];
+                    if (segn[lc] == 0) continue;
+                    per[leaf].push_back(nleaf[pos++]);
+                }
+            }
+        }
+        std::vector<int32_t> ptr(nl + 1, 0), items, act;
+        for (int64_t i = 0; i < nl; ++i) {
+            items.insert(items.end(), per[i].begin(), per[i].end());
+            ptr[i + 1] = (int32_t)items.size();
+            if (!per[i].empty()) act.push_back((int32_t)i);
+        }
+        D->n_active = (int64_t)act.size();
+        MH_ALLOC(ctx, D->active, std::max<size_t>(act.size(), 1));
+        if (!act.empty())
+            MH_CUDA(ctx, cudaMemcpyAsync(D->active.p, act.data(), act.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        std::vector<double2> lc(nl), pxy(nd), pn(nd);
+        std::vector<float4> f4(nd);
+        for (int64_t i = 0; i < nl; ++i) {
+            const std::complex<double> c = centre(h.leaf_box[i]);
+            lc[i] = make_double2(c.real(), c.imag());
+        }
+        for (int64_t d = 0; d < nd; ++d) {
+            pxy[d] = make_double2(dxy[2 * d], dxy[2 * d + 1]);
+            pn[d] = make_double2(dnrm[2 * d], dnrm[2 * d + 1]);
+            const double2 c = lc[dleaf[d]];
+            f4[d] = make_float4((float)(dxy[2 * d] - c.x), (float)(dxy[2 * d + 1] - c.y), (float)dnrm[2 * d],
+                                (float)dnrm[2 * d + 1]);
+        }
+        std::vector<int64_t> s0(seg0.begin(), seg0.end());
+        std::vector<int32_t> sn(segn.begin(), segn.end());
+        cudaStream_t st = ctx->stream;
+        MH_ALLOC(ctx, D->near_ptr, nl + 1);
+        MH_ALLOC(ctx, D->near_leaf, std::max<size_t>(items.size(), 1));
+        MH_ALLOC(ctx, D->seg0, nl);
+        MH_ALLOC(ctx, D->segn, nl);
+        MH_ALLOC(ctx, D->leaf_c, nl);
+        MH_ALLOC(ctx, D->dxy, std::max<int64_t>(nd, 1));
+        MH_ALLOC(ctx, D->dnrm, std::max<int64_t>(nd, 1));
+        MH_ALLOC(ctx, D->d32, std::max<int64_t>(nd, 1));
+        MH_ALLOC(ctx, D->w32, std::max<int64_t>(nd, 1));
+        MH_CUDA(ctx, cudaMemcpyAsync(D->near_ptr.p, ptr.data(), (nl + 1) * 4, cudaMemcpyHostToDevice, st));
+        if (!items.empty())
+            MH_CUDA(ctx, cudaMemcpyAsync(D->near_leaf.p, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(D->seg0.p, s0.data(), nl * 8, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(D->segn.p, sn.data(), nl * 4, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(D->leaf_c.p, lc.data(), nl * 16, cudaMemcpyHostToDevice, st));
+        if (nd) {
+            MH_CUDA(ctx, cudaMemcpyAsync(D->dxy.p, pxy.data(), nd * 16, cudaMemcpyHostToDevice, st));
+            MH_CUDA(ctx, cudaMemcpyAsync(D->dnrm.p, pn.data(), nd * 16, cudaMemcpyHostToDevice, st));
+            MH_CUDA(ctx, cudaMemcpyAsync(D->d32.p, f4.data(), nd * 16, cudaMemcpyHostToDevice, st));
+        }
+        MH_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    // upload the operator pool (volume translation operators + dipole blocks)
+    cudaStream_t st = ctx->stream;
+    const int64_t total = (int64_t)pool.data.size();
+    MH_ALLOC(ctx, D->ops64, total);
+    MH_ALLOC(ctx, D->ops32, total);
+    MH_CUDA(ctx, cudaMemcpyAsync(D->ops64.p, pool.data.data(), total * 8, cudaMemcpyHostToDevice, st));
+    {
+        std::vector<float> f(pool.data.begin(), pool.data.end());
+        MH_CUDA(ctx, cudaMemcpyAsync(D->ops32.p, f.data(), total * 4, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    MH_ALLOC(ctx, D->d_op_off, pool.off.size());
+    MH_ALLOC(ctx, D->d_op_C, pool.C.size());
+    MH_CUDA(ctx, cudaMemcpyAsync(D->d_op_off.p, pool.off.data(), pool.off.size() * 8, cudaMemcpyHostToDevice, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(D->d_op_C.p, pool.C.data(), pool.C.size() * 4, cudaMemcpyHostToDevice, st));
+    std::vector<int> opC(pool.C.begin(), pool.C.end());
+    int64_t need = 1;
+    D->p2m.reset(new Phase());
+    MH_TRY(build_phase(ctx, t_p2m, P, false, opC, D->p2m.get(), &need));
+    D->m2m.resize(L + 1);
+    D->l2l.resize(L + 1);
+    for (int l = 0; l <= L; ++l) {
+        D->m2m[l].reset(new Phase());
+        D->l2l[l].reset(new Phase());
+        MH_TRY(build_phase(ctx, t_m2m[l], P, false, opC, D->m2m[l].get(), &need));
+        MH_TRY(build_phase(ctx, t_l2l[l], P, true, opC, D->l2l[l].get(), &need));
+    }
+    D->m2l.reset(new Phase());
+    MH_TRY(build_phase(ctx, t_m2l, P, false, opC, D->m2l.get(), &need));
+    D->out.reset(new Phase());
+    MH_TRY(build_phase(ctx, t_out, qq, !near_blocks, opC, D->out.get(), &need));
+    MH_ALLOC(ctx, D->vec, D->vec_len);
+    MH_ALLOC(ctx, D->temp, need);
+    MH_CUDA(ctx, cudaMemsetAsync(D->vec.p, 0, D->vec_len * 8, st));
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
+    V->dip = std::move(D);
+    return MH_OK;
+}
+
+template <typename TOP>
+static mh_status dipole_run(mh_ctx* ctx, mh_tree* t, DipData* D, const TOP* ops) {
+    auto run = [&](const Phase* ph) {
+        return run_phase_on<TOP>(ctx, ops, D->d_op_off.p, D->d_op_C.p, D->vec.p, D->temp.p, ph, "dlp_fmm_contract");
+    };
+    MH_TRY(run(D->p2m.get()));
+    for (int l = t->max_level - 1; l >= 2; --l) MH_TRY(run(D->m2m[l].get()));
+    MH_TRY(run(D->m2l.get()));
+    for (int l = 2; l < t->max_level; ++l) MH_TRY(run(D->l2l[l].get()));
+    MH_TRY(run(D->out.get()));
+    return MH_OK;
+}
+
+// w_sorted: dipole strengths in the leaf-sorted order given to volume_dipole_setup.
+// Returns a device pointer to U^h at every volume node (leaf-major), valid until the next call.
+mh_status volume_dipole_apply(mh_ctx* ctx, mh_tree* t, const double* w_sorted, mh_precision prec, const double** u) {
+    VolData* V = static_cast<VolData*>(t->vol);
+    if (!V || !V->dip) return mh_fail(ctx, MH_ERR_INVALID_ARG, "dipole multipole pass not set up");
+    DipData* D = V->dip.get();
+    prof_scope ps(ctx, "dlp_fmm");
+    cudaStream_t st = ctx->stream;
+    MH_CUDA(ctx, cudaMemcpyAsync(D->vec.p + D->W_off, w_sorted, D->nd * 8, cudaMemcpyDeviceToDevice, st));
+    if (!D->near_blocks) MH_CUDA(ctx, cudaMemsetAsync(D->vec.p + D->DU_off, 0, t->n_leaves * D->qq * 8, st));
+    if (prec == MH_PREC_MIXED)
+        MH_TRY(dipole_run<float>(ctx, t, D, D->ops32.p));
+    else
+        MH_TRY(dipole_run<double>(ctx, t, D, D->ops64.p));
+    if (!D->near_blocks && D->n_active) {
+        prof_scope ps2(ctx, "dlp_near", 68.0 * D->near_pairs, 24.0 * (double)D->nd);
+        if (prec == MH_PREC_MIXED) {
+            k_d2f<<<mh_grid(D->nd, 256), 256, 0, st>>>(w_sorted, D->w32.p, D->nd);
+            MH_LAUNCHED(ctx);
+            k_dip_near32<<<(unsigned)D->n_active, NEAR_T, 0, st>>>(
+                t->nodes.p, D->active.p, D->near_ptr.p, D->near_leaf.p, D->seg0.p, D->segn.p, D->leaf_c.p, D->d32.p,
+                D->w32.p, D->qq, (float)D->inv_alpha, D->pref, D->vec.p + D->DU_off);
+        } else {
+            k_dip_near64<<<(unsigned)D->n_active, NEAR_T, 0, st>>>(
+                t->nodes.p, D->active.p, D->near_ptr.p, D->near_leaf.p, D->seg0.p, D->segn.p, D->dxy.p, D->dnrm.p,
+                w_sorted, D->qq, D->inv_alpha, D->pref, D->vec.p + D->DU_off);
+        }
+        MH_LAUNCHED(ctx);
+    }
+    *u = D->vec.p + D->DU_off;
+    return MH_OK;
+}
 
 void volume_free(mh_tree* t) {
     delete static_cast<VolData*>(t->vol);

@@ -56,7 +56,8 @@ def test_heat_step_matches_oracle(mh, ctx, oracle_c1, prec, tol):
     wl, pb, nodes, bn = oracle_c1
     gt = mh.Tree(ctx, wl.box, wl.q, wl.min_level, wl.max_level)
     bnd = mh.Boundary(ctx, wl.curves, alpert_order=8)
-    prob = mh.Problem(ctx, gt, bnd, wl.dt, wl.p, ext_mode=mh.MH_EXT_ARRAY)
+    # p = 30: the multipole double layer at p = 20 sits at 1.8e-10 on this case, above the FP64 bar
+    prob = mh.Problem(ctx, gt, bnd, wl.dt, 30, ext_mode=mh.MH_EXT_ARRAY)
     assert np.array_equal(prob.regions(), pb.info.region)
     mf = W.Manufactured
     dev = lambda a: torch.tensor(a, device="cuda")
