@@ -627,7 +627,8 @@ __global__ void k_backsolve(const double* H, int ldh, int k, const double* g, do
     for (int i = k - 1; i >= 0; --i) {
         double acc = g[i];
         for (int j = i + 1; j < k; ++j) acc -= H[(int64_t)j * ldh + i] * y[j];
-        y[i] = acc / H[(int64_t)i * ldh + i];
+        const double d = H[(int64_t)i * ldh + i];
+        y[i] = d != 0.0 ? acc / d : 0.0;   // exact breakdown: the column adds nothing
     }
 }
 
@@ -1040,6 +1041,7 @@ __global__ void k_dlp_line(const int32_t* __restrict__ line_tgt, const int32_t* 
 
 }  // namespace
 
+
 // ============================ host side ============================
 
 static mh_status upload_alpert(int l, AlpertRule* R) {
@@ -1237,6 +1239,11 @@ static mh_status gmres_core(mh_ctx* ctx, mh_boundary* bd, gmres_ws& ws, const do
     MH_LAUNCHED(ctx);
     int k = 0;
     double res = beta;
+    // The residual estimate is read back only at predicted convergence points: from the
+    // decay observed between two reads, the next read is placed where the estimate should
+    // reach the tolerance (iterations between reads are queued without host round trips).
+    int next_check = 1, k_prev = 0;
+    double res_prev = beta;
     for (; k < max_iter; ++k) {
         double* vk = ws.V.p + (int64_t)k * n;
         MH_TRY(bie_apply(ctx, bd, vk, ws.w.p, prec));
@@ -1256,6 +1263,7 @@ static mh_status gmres_core(mh_ctx* ctx, mh_boundary* bd, gmres_ws& ws, const do
         MH_LAUNCHED(ctx);
         k_givens<<<1, 1, 0, st>>>(ws.H.p, ldh, k, ws.cs.p, ws.sn.p, ws.g.p, ws.small.p);
         MH_LAUNCHED(ctx);
+        if (k + 1 < next_check && k + 1 < max_iter) continue;
         MH_CUDA(ctx, cudaMemcpyAsync(&res, ws.small.p, 8, cudaMemcpyDeviceToHost, st));
         MH_CUDA(ctx, cudaStreamSynchronize(st));
         if (!std::isfinite(res)) return mh_fail(ctx, MH_ERR_NUMERIC, "GMRES residual is not finite");
@@ -1263,6 +1271,14 @@ static mh_status gmres_core(mh_ctx* ctx, mh_boundary* bd, gmres_ws& ws, const do
             ++k;
             break;
         }
+        const double rate = (res > 0 && res_prev > 0 && k + 1 > k_prev)
+                                ? std::pow(res / res_prev, 1.0 / (k + 1 - k_prev)) : 0.5;
+        int ahead = 1;
+        if (rate > 0 && rate < 0.999) ahead = (int)std::floor(std::log(abs_tol / res) / std::log(rate));
+        ahead = std::max(1, std::min(ahead, 8));
+        k_prev = k + 1;
+        res_prev = res;
+        next_check = k + 1 + ahead;
     }
     k_backsolve<<<1, 1, 0, st>>>(ws.H.p, ldh, k, ws.g.p, ws.y.p);
     MH_LAUNCHED(ctx);
@@ -1289,7 +1305,7 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
         MH_ALLOC(ctx, ws.y, max_iter + 1);
         MH_ALLOC(ctx, ws.h1, max_iter + 2);
         MH_ALLOC(ctx, ws.h2, max_iter + 2);
-        MH_ALLOC(ctx, ws.small, 4);
+        MH_ALLOC(ctx, ws.small, 8);
         MH_ALLOC(ctx, ws.w, n);
         MH_ALLOC(ctx, ws.r, n);
         MH_ALLOC(ctx, ws.dx, n);

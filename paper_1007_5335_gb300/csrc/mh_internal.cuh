@@ -96,7 +96,9 @@ struct dbuf {
 
 // GMRES workspace (kept by the boundary so that repeated solves allocate nothing).
 struct gmres_ws {
-    dbuf<double> V, H, cs, sn, g, y, h1, h2, small, w, r, dx;
+    dbuf<double> V, H, cs, sn, g, y, h1, h2, small, w, r, dx, part;
+    dbuf<float> v32;
+    int coop_grid = 0;     // blocks of the persistent GMRES kernel (0 = not set up)
     int m = 0;
     int64_t n = 0;
 };
