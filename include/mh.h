@@ -193,14 +193,18 @@ mh_status mh_gmres_solve_static(mh_ctx* ctx, mh_boundary* bnd, double alpha, con
 /* ---- heat step (Section 2) ---------------------------------------------------------- */
 
 typedef enum { MH_EXT_CONST = 0, MH_EXT_ARRAY = 1 } mh_ext_mode;
+typedef enum {
+    MH_SCHEME_IMEX_EULER = 0,    /* alpha^2 = dt,     B = u^N + dt F^N (Section 2) */
+    MH_SCHEME_EXTRAP_GEAR = 1    /* alpha^2 = 2dt/3,  B = 4/3 u^N - 1/3 u^{N-1} + 4/3 dt F^N - 2/3 dt F^{N-1} */
+} mh_scheme;
 
-/* Bind a tree and a boundary into a time-stepping problem with step dt (alpha^2 = dt,
- * IMEX Euler) and multipole order p.  Volume nodes are classified (inside Omega or on
+/* Bind a tree and a boundary into a time-stepping problem with step dt, time scheme
+ * `scheme` (mh_scheme; fixes alpha^2 = dt or 2dt/3, Section 2) and multipole order p.  Volume nodes are classified (inside Omega or on
  * the exterior side of curve k) and the boundary nodes located in the leaves.
  * Exterior extension of B (Section 3.1): MH_EXT_CONST uses ext_const_host[k] + dt F
  * outside curve k (the paper's constant extension); MH_EXT_ARRAY takes the exterior
  * values from heat_step's b_ext_dev. */
-mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* bnd, double dt, int p,
+mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* bnd, double dt, int scheme, int p,
                             int ext_mode, const double* ext_const_host, mh_problem** out);
 mh_status mh_problem_destroy(mh_problem* prob);
 /* Region of every volume node: -1 inside Omega, k on the exterior side of curve k. */
@@ -216,6 +220,17 @@ mh_status mh_problem_regions(mh_ctx* ctx, const mh_problem* prob, int32_t* regio
 mh_status heat_step(mh_ctx* ctx, mh_problem* prob, const double* u_dev, const double* F_dev,
                     const double* f_next_dev, const double* b_ext_dev, double* u_next_dev,
                     double* sigma_dev, double gmres_tol, mh_precision prec, mh_step_info* info);
+
+/* One extrapolated Gear step (Section 2) on a problem created with MH_SCHEME_EXTRAP_GEAR:
+ * B = 4/3 u - 1/3 u_prev + dt (4/3 F - 2/3 F_prev) inside Omega, C_k + dt (4/3 F -
+ * 2/3 F_prev) outside (MH_EXT_CONST) or b_ext_dev (MH_EXT_ARRAY); the rest as heat_step.
+ * The scheme needs two past levels: start it with one step of another method or with
+ * known data.  u_prev_dev, F_prev_dev: n_nodes doubles.  u_next_dev may alias u_dev
+ * (not u_prev_dev). */
+mh_status heat_step_gear(mh_ctx* ctx, mh_problem* prob, const double* u_dev, const double* u_prev_dev,
+                         const double* F_dev, const double* F_prev_dev, const double* f_next_dev,
+                         const double* b_ext_dev, double* u_next_dev, double* sigma_dev, double gmres_tol,
+                         mh_precision prec, mh_step_info* info);
 
 #ifdef __cplusplus
 }

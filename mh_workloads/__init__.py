@@ -163,3 +163,62 @@ def starfish_domain(n_per_curve: int = 1024, n_holes: int = 5, seed: int = 2, q:
     return Workload("starfish_domain", [outer] + holes, (-1.0, -1.0, 2.0), q, min_level,
                     max_level, refine_tol, dt, math.sqrt(dt), steps, p,
                     gaussian_forcing(forcing_seed), False, [0.0] * (n_holes + 1))
+
+
+class Example1:
+    """The annulus problem with a known solution (the paper's Example 1): Gamma_0 the circle
+    r = 0.4 (counter-clockwise), Gamma_1 the circle r = 0.1 (clockwise), forcing
+    F = 400 cos(20 r) + 20 sin(20 r) / r and
+        u(x, t) = exp(-lam^2 t) [Y0(0.1 lam) J0(lam r) - J0(0.1 lam) Y0(lam r)] + cos(20 r),
+    lam the first root of Y0(0.1 lam) J0(0.4 lam) - J0(0.1 lam) Y0(0.4 lam) (about 10.244), so
+    that u = cos(8) on Gamma_0 and cos(2) on Gamma_1.  `u_ext` continues u inside the hole
+    (r < 0.1) by a polynomial in r^2 matching u, u_r and u_rr at r = 0.1 (C^2), so that data
+    extended outside Omega stay smooth; outside r = 0.4 the formula itself is used."""
+
+    R0, R1 = 0.4, 0.1
+
+    def __init__(self):
+        from scipy import optimize, special
+        self._j0, self._y0, self._j1, self._y1 = special.j0, special.y0, special.j1, special.y1
+        f = lambda l: special.y0(0.1 * l) * special.j0(0.4 * l) - special.j0(0.1 * l) * special.y0(0.4 * l)
+        self.lam = optimize.brentq(f, 5.0, 12.0)
+
+    def radial(self, t, r):
+        lam = self.lam
+        c1, c2 = self._y0(0.1 * lam), self._j0(0.1 * lam)
+        e = math.exp(-lam * lam * t)
+        v = e * (c1 * self._j0(lam * r) - c2 * self._y0(lam * r)) + np.cos(20 * r)
+        # d/dr and d2/dr2 (J0' = -J1, J1' = J0 - J1/z; same for Y)
+        z = lam * r
+        d1 = e * lam * (-c1 * self._j1(z) + c2 * self._y1(z)) - 20 * np.sin(20 * r)
+        d2 = e * lam * lam * (-c1 * (self._j0(z) - self._j1(z) / z) + c2 * (self._y0(z) - self._y1(z) / z)) \
+            - 400 * np.cos(20 * r)
+        return v, d1, d2
+
+    def u(self, t, xy):
+        xy = np.asarray(xy, dtype=np.float64)
+        r = np.hypot(xy[:, 0], xy[:, 1])
+        out = np.empty_like(r)
+        big = r >= self.R1
+        out[big] = self.radial(t, r[big])[0]
+        if np.any(~big):
+            # u_ext = a + b s + c s^2 with s = r^2 - R1^2, matching v, v', v'' at r = R1
+            v, d1, d2 = (float(np.asarray(q).reshape(-1)[0]) for q in self.radial(t, np.array([self.R1])))
+            b = d1 / (2 * self.R1)
+            c = (d2 - 2 * b) / (8 * self.R1 ** 2)
+            s = r[~big] ** 2 - self.R1 ** 2
+            out[~big] = v + b * s + c * s * s
+        return out
+
+    def F(self, xy):
+        xy = np.asarray(xy, dtype=np.float64)
+        r = np.hypot(xy[:, 0], xy[:, 1])
+        safe = np.where(r > 1e-12, r, 1.0)
+        return 400 * np.cos(20 * r) + np.where(r > 1e-12, 20 * np.sin(20 * r) / safe, 400.0)
+
+    def boundary_data(self):
+        return [math.cos(8.0), math.cos(2.0)]
+
+    def curves(self, n_outer, n_inner):
+        return [circle_nodes((0.0, 0.0), self.R0, n_outer, clockwise=False),
+                circle_nodes((0.0, 0.0), self.R1, n_inner, clockwise=True)]

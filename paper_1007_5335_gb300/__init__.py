@@ -22,6 +22,8 @@ MH_PREC_FP64 = 0
 MH_PREC_MIXED = 1
 MH_EXT_CONST = 0
 MH_EXT_ARRAY = 1
+MH_SCHEME_IMEX_EULER = 0
+MH_SCHEME_EXTRAP_GEAR = 1
 STATUS = {0: "MH_OK", 1: "MH_ERR_INVALID_ARG", 2: "MH_ERR_GEOMETRY", 3: "MH_ERR_CUDA", 4: "MH_ERR_OOM",
           5: "MH_ERR_NOT_CONVERGED", 6: "MH_ERR_TIMEOUT", 7: "MH_ERR_NUMERIC", 8: "MH_ERR_CALLBACK"}
 LISTS = {"U": 0, "V": 1, "W": 2, "X": 3}
@@ -60,10 +62,11 @@ _SIGS = {
     "mh_volume_potential": [_p, _p, _d, _i, _p, _p, _i],
     "mh_double_layer_apply": [_p, _p, _d, _p, _p, _i64, _p, _i],
     "mh_gmres_solve": [_p, _p, _d, _p, _p, _d, _i, _i, ctypes.POINTER(GmresInfo)],
-    "mh_problem_create": [_p, _p, _p, _d, _i, _i, _p, ctypes.POINTER(_p)],
+    "mh_problem_create": [_p, _p, _p, _d, _i, _i, _i, _p, ctypes.POINTER(_p)],
     "mh_problem_destroy": [_p],
     "mh_problem_regions": [_p, _p, _p],
     "heat_step": [_p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
+    "heat_step_gear": [_p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
     "mh_gmres_solve_static": [_p, _p, _d, _p, _p, _d, _i, ctypes.POINTER(GmresInfo)],
     "mh_profile_enable": [_p, _i],
     "mh_profile_read": [_p, ctypes.c_char_p, ctypes.POINTER(_d), ctypes.POINTER(_i64), ctypes.POINTER(_d),
@@ -245,18 +248,19 @@ def mh_gmres_solve_static(ctx: Context, bnd: Boundary, alpha: float, rhs, sigma,
 
 
 class Problem:
-    """mh_problem_create: tree + boundary + dt (alpha^2 = dt) + multipole order p."""
+    """mh_problem_create: tree + boundary + dt + scheme (alpha^2 = dt or 2 dt / 3) + multipole order p."""
 
     def __init__(self, ctx: Context, tree: Tree, bnd: Boundary, dt: float, p: int, ext_mode: int = MH_EXT_CONST,
-                 ext_const=None):
+                 ext_const=None, scheme: int = MH_SCHEME_IMEX_EULER):
         self.ctx, self.tree, self.bnd = ctx, tree, bnd
         ec = np.ascontiguousarray(ext_const if ext_const is not None else np.zeros(bnd.n_curves), dtype=np.float64)
         h = _p()
-        ctx.check(_lib.mh_problem_create(ctx.h, tree.h, bnd.h, float(dt), int(p), int(ext_mode),
+        ctx.check(_lib.mh_problem_create(ctx.h, tree.h, bnd.h, float(dt), int(scheme), int(p), int(ext_mode),
                                          ec.ctypes.data_as(_p), ctypes.byref(h)))
         self.h = h
         self.dt = dt
-        self.alpha = float(np.sqrt(dt))
+        self.scheme = scheme
+        self.alpha = float(np.sqrt(dt if scheme == MH_SCHEME_IMEX_EULER else 2.0 * dt / 3.0))
 
     def regions(self) -> np.ndarray:
         out = np.zeros(self.tree.n_nodes, dtype=np.int32)
@@ -274,6 +278,15 @@ def heat_step(ctx: Context, prob: Problem, u, F, f_next, u_next, sigma, b_ext=No
     info = StepInfo()
     ctx.check(_lib.heat_step(ctx.h, prob.h, _ptr(u), _ptr(F), _ptr(f_next), _ptr(b_ext), _ptr(u_next), _ptr(sigma),
                              float(gmres_tol), int(prec), ctypes.byref(info)))
+    return info
+
+
+def heat_step_gear(ctx: Context, prob: Problem, u, u_prev, F, F_prev, f_next, u_next, sigma, b_ext=None,
+                   gmres_tol: float = 1e-10, prec: int = MH_PREC_FP64) -> StepInfo:
+    info = StepInfo()
+    ctx.check(_lib.heat_step_gear(ctx.h, prob.h, _ptr(u), _ptr(u_prev), _ptr(F), _ptr(F_prev), _ptr(f_next),
+                                  _ptr(b_ext), _ptr(u_next), _ptr(sigma), float(gmres_tol), int(prec),
+                                  ctypes.byref(info)))
     return info
 
 

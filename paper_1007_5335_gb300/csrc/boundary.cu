@@ -276,21 +276,43 @@ __global__ void k_gemv64(const double* __restrict__ A, const double* __restrict_
 
 // binary32 operator times a binary32 copy of x (converted once per call: conversions
 // from binary64 run on the slow FP64 pipe of this part and must stay out of the loop).
+// One warp per row; four independent loads in flight per lane (16-byte loads when the
+// row length is a multiple of 4, 8-byte loads otherwise).
 __global__ void k_gemv32(const float* __restrict__ A, const float* __restrict__ x, double* __restrict__ y,
                          int64_t n) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < n; row += nwarps) {
-        const float2* a = reinterpret_cast<const float2*>(A + row * n);
-        const float2* xv = reinterpret_cast<const float2*>(x);
-        float acc0 = 0.f, acc1 = 0.f;
-        for (int64_t c = lane; c < n / 2; c += 32) {
-            float2 av = __ldcs(a + c);
-            float2 xx = __ldg(xv + c);
-            acc0 = fmaf(av.x, xx.x, acc0);
-            acc1 = fmaf(av.y, xx.y, acc1);
+        const float* a = A + row * n;
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+        if ((n & 3) == 0) {
+            const float4* a4 = reinterpret_cast<const float4*>(a);
+            const float4* x4 = reinterpret_cast<const float4*>(x);
+            const int64_t n4 = n >> 2;
+            int64_t c = lane;
+            for (; c + 96 < n4; c += 128) {
+                const float4 a0 = __ldcs(a4 + c), a1 = __ldcs(a4 + c + 32), a2 = __ldcs(a4 + c + 64),
+                             a3 = __ldcs(a4 + c + 96);
+                const float4 x0 = __ldg(x4 + c), x1 = __ldg(x4 + c + 32), x2 = __ldg(x4 + c + 64),
+                             x3 = __ldg(x4 + c + 96);
+                f0 = fmaf(a0.x, x0.x, fmaf(a0.y, x0.y, fmaf(a0.z, x0.z, fmaf(a0.w, x0.w, f0))));
+                f1 = fmaf(a1.x, x1.x, fmaf(a1.y, x1.y, fmaf(a1.z, x1.z, fmaf(a1.w, x1.w, f1))));
+                f2 = fmaf(a2.x, x2.x, fmaf(a2.y, x2.y, fmaf(a2.z, x2.z, fmaf(a2.w, x2.w, f2))));
+                f3 = fmaf(a3.x, x3.x, fmaf(a3.y, x3.y, fmaf(a3.z, x3.z, fmaf(a3.w, x3.w, f3))));
+            }
+            for (; c < n4; c += 32) {
+                const float4 av = __ldcs(a4 + c), xv = __ldg(x4 + c);
+                f0 = fmaf(av.x, xv.x, fmaf(av.y, xv.y, fmaf(av.z, xv.z, fmaf(av.w, xv.w, f0))));
+            }
+        } else {
+            const float2* a2p = reinterpret_cast<const float2*>(a);
+            const float2* x2p = reinterpret_cast<const float2*>(x);
+            for (int64_t c = lane; c < n / 2; c += 32) {
+                const float2 av = __ldcs(a2p + c), xv = __ldg(x2p + c);
+                f0 = fmaf(av.x, xv.x, fmaf(av.y, xv.y, f0));
+            }
         }
-        float f = acc0 + acc1;
+        float f = (f0 + f1) + (f2 + f3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
         if (lane == 0) y[row] = (double)f;

@@ -184,6 +184,7 @@ struct mh_problem {
     mh_tree* tree = nullptr;
     mh_boundary* bnd = nullptr;
     double dt = 0, alpha = 0;
+    int scheme = 0;
     int p = 0;
     int ext_mode = 0;
     std::vector<double> ext_const;

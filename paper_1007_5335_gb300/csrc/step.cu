@@ -28,6 +28,22 @@ __global__ void k_form_B(const double* __restrict__ u, const double* __restrict_
     B[i] = v;
 }
 
+__global__ void k_form_B_gear(const double* __restrict__ u, const double* __restrict__ up, const double* __restrict__ F,
+                              const double* __restrict__ Fp, const int32_t* __restrict__ region,
+                              const double* __restrict__ ext_const, const double* __restrict__ b_ext, int ext_mode,
+                              double dt, int64_t n, double* B) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = region[i];
+    const double forcing = dt * (4.0 * F[i] - 2.0 * Fp[i]) / 3.0;
+    double v;
+    if (r < 0)
+        v = (4.0 * u[i] - up[i]) / 3.0 + forcing;
+    else
+        v = ext_mode == MH_EXT_CONST ? ext_const[r] + forcing : b_ext[i];
+    B[i] = v;
+}
+
 __global__ void k_rhs(const double* __restrict__ f, const double* __restrict__ ug, double c, int64_t n, double* rhs) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) rhs[i] = c * (f[i] - ug[i]);
@@ -71,11 +87,13 @@ struct ProblemImpl : mh_problem {
     dbuf<double> w_sorted;    // dipole strengths in that order
 };
 
-extern "C" mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* bnd, double dt, int p, int ext_mode,
-                                       const double* ext_const_host, mh_problem** out) {
+extern "C" mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* bnd, double dt, int scheme, int p,
+                                       int ext_mode, const double* ext_const_host, mh_problem** out) {
     if (!ctx || !tree || !bnd || !out) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     if (!(dt > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "dt must be positive");
+    if (scheme != MH_SCHEME_IMEX_EULER && scheme != MH_SCHEME_EXTRAP_GEAR)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "unknown scheme %d", scheme);
     if (p < 1 || p > 40) return mh_fail(ctx, MH_ERR_INVALID_ARG, "p must be in 1..40");
     if (ext_mode != MH_EXT_CONST && ext_mode != MH_EXT_ARRAY) return mh_fail(ctx, MH_ERR_INVALID_ARG, "bad ext_mode");
     if (ext_mode == MH_EXT_CONST && !ext_const_host)
@@ -85,7 +103,8 @@ extern "C" mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* 
     P->tree = tree;
     P->bnd = bnd;
     P->dt = dt;
-    P->alpha = std::sqrt(dt);
+    P->scheme = scheme;
+    P->alpha = std::sqrt(scheme == MH_SCHEME_EXTRAP_GEAR ? 2.0 * dt / 3.0 : dt);
     P->p = p;
     P->ext_mode = ext_mode;
     const int nc = bnd->n_curves;
@@ -200,25 +219,16 @@ extern "C" mh_status mh_problem_regions(mh_ctx* ctx, const mh_problem* p, int32_
     return MH_OK;
 }
 
-extern "C" mh_status heat_step(mh_ctx* ctx, mh_problem* prob, const double* u_dev, const double* F_dev,
-                               const double* f_next_dev, const double* b_ext_dev, double* u_next_dev,
-                               double* sigma_dev, double gmres_tol, mh_precision prec, mh_step_info* info) {
-    if (!ctx || !prob || !u_dev || !F_dev || !f_next_dev || !u_next_dev || !sigma_dev)
-        return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
-    ProblemImpl* P = static_cast<ProblemImpl*>(prob);
-    if (P->ext_mode == MH_EXT_ARRAY && !b_ext_dev)
-        return mh_fail(ctx, MH_ERR_INVALID_ARG, "MH_EXT_ARRAY needs b_ext_dev");
-    if (!(gmres_tol > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "gmres_tol must be positive");
+// Everything after the right-hand side B (P->B) has been formed.
+static mh_status step_solve(mh_ctx* ctx, ProblemImpl* P, const double* f_next_dev, double* u_next_dev,
+                            double* sigma_dev, double gmres_tol, mh_precision prec, mh_step_info* info) {
     cudaStream_t st = ctx->stream;
     mh_tree* t = P->tree;
     mh_boundary* b = P->bnd;
     const int64_t n = t->n_nodes, ng = b->n;
-    k_form_B<<<mh_grid(n, 256), 256, 0, st>>>(u_dev, F_dev, P->region.p, P->d_ext_const.p, b_ext_dev, P->ext_mode,
-                                              P->dt, n, P->B.p);
-    MH_LAUNCHED(ctx);
     MH_TRY(volume_apply(ctx, t, P->alpha, P->p, P->B.p, P->Up.p, prec));
     MH_TRY(tree_interpolate(ctx, t, P->Up.p, b->xy.p, P->bnd_leaf.p, ng, P->Ug.p));
-    k_rhs<<<mh_grid(ng, 256), 256, 0, st>>>(f_next_dev, P->Ug.p, -2.0 * P->dt, ng, P->rhs.p);
+    k_rhs<<<mh_grid(ng, 256), 256, 0, st>>>(f_next_dev, P->Ug.p, -2.0 * P->alpha * P->alpha, ng, P->rhs.p);
     MH_LAUNCHED(ctx);
     mh_gmres_info gi{};
     mh_status s = gmres_run(ctx, b, P->rhs.p, sigma_dev, gmres_tol, 100, prec, &gi);
@@ -242,4 +252,42 @@ extern "C" mh_status heat_step(mh_ctx* ctx, mh_problem* prob, const double* u_de
                                                P->ext_mode, n, u_next_dev);
     MH_LAUNCHED(ctx);
     return MH_OK;
+}
+
+extern "C" mh_status heat_step(mh_ctx* ctx, mh_problem* prob, const double* u_dev, const double* F_dev,
+                               const double* f_next_dev, const double* b_ext_dev, double* u_next_dev,
+                               double* sigma_dev, double gmres_tol, mh_precision prec, mh_step_info* info) {
+    if (!ctx || !prob || !u_dev || !F_dev || !f_next_dev || !u_next_dev || !sigma_dev)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    ProblemImpl* P = static_cast<ProblemImpl*>(prob);
+    if (P->scheme != MH_SCHEME_IMEX_EULER)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "heat_step needs a problem created with MH_SCHEME_IMEX_EULER");
+    if (P->ext_mode == MH_EXT_ARRAY && !b_ext_dev)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "MH_EXT_ARRAY needs b_ext_dev");
+    if (!(gmres_tol > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "gmres_tol must be positive");
+    const int64_t n = P->tree->n_nodes;
+    k_form_B<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(u_dev, F_dev, P->region.p, P->d_ext_const.p, b_ext_dev,
+                                                       P->ext_mode, P->dt, n, P->B.p);
+    MH_LAUNCHED(ctx);
+    return step_solve(ctx, P, f_next_dev, u_next_dev, sigma_dev, gmres_tol, prec, info);
+}
+
+extern "C" mh_status heat_step_gear(mh_ctx* ctx, mh_problem* prob, const double* u_dev, const double* u_prev_dev,
+                                    const double* F_dev, const double* F_prev_dev, const double* f_next_dev,
+                                    const double* b_ext_dev, double* u_next_dev, double* sigma_dev, double gmres_tol,
+                                    mh_precision prec, mh_step_info* info) {
+    if (!ctx || !prob || !u_dev || !u_prev_dev || !F_dev || !F_prev_dev || !f_next_dev || !u_next_dev || !sigma_dev)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    ProblemImpl* P = static_cast<ProblemImpl*>(prob);
+    if (P->scheme != MH_SCHEME_EXTRAP_GEAR)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "heat_step_gear needs a problem created with MH_SCHEME_EXTRAP_GEAR");
+    if (P->ext_mode == MH_EXT_ARRAY && !b_ext_dev)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "MH_EXT_ARRAY needs b_ext_dev");
+    if (!(gmres_tol > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "gmres_tol must be positive");
+    const int64_t n = P->tree->n_nodes;
+    k_form_B_gear<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(u_dev, u_prev_dev, F_dev, F_prev_dev, P->region.p,
+                                                            P->d_ext_const.p, b_ext_dev, P->ext_mode, P->dt, n,
+                                                            P->B.p);
+    MH_LAUNCHED(ctx);
+    return step_solve(ctx, P, f_next_dev, u_next_dev, sigma_dev, gmres_tol, prec, info);
 }

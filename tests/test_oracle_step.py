@@ -57,3 +57,47 @@ def test_manufactured_first_order():
     assert abs(e1 - p1) < 0.03 * p1 and abs(e2 - p2) < 0.05 * p2, (e1, p1, e2, p2)
     assert 1.7 < e1 / e2 < 2.3
     assert max(its1 + its2) < 40
+
+
+def _run_gear(dt, t_end):
+    """Extrapolated Gear (alpha^2 = 2 dt / 3) started from exact data at t = 0 and dt."""
+    wl = W.disk_with_hole(dt=dt)
+    alpha = math.sqrt(2 * dt / 3)
+    curves = G.make_curves(wl.curves)
+    tr = T.build(wl.box, wl.q, wl.min_level, wl.max_level)
+    nodes = tr.nodes()
+    info = G.classify(curves, nodes)
+    bn = np.concatenate([c.nodes for c in curves])
+    bleaf = [tr.locate(p) for p in bn]
+    M = V.uniform_operator(wl.min_level, wl.box, wl.q, alpha, order=[(b[1], b[2]) for b in tr.leaves])
+    A = bie.nystrom_matrix(curves, alpha)
+    pb = S.Problem(curves, tr, alpha, dt, info, bleaf, A, ext_mode="array", volume_op=lambda b: M @ b, use_lu=True)
+    mf = W.Manufactured
+    u_prev, u = mf.u(0.0, nodes), mf.u(dt, nodes)
+    t = dt
+    for _ in range(int(round(t_end / dt)) - 1):
+        F, Fp = mf.F(t, nodes), mf.F(t - dt, nodes)
+        b_ext = (4 * mf.u(t, nodes) - mf.u(t - dt, nodes)) / 3 + dt * (4 * F - 2 * Fp) / 3
+        un, _, _ = S.heat_step_gear(pb, u, u_prev, F, Fp, mf.u(t + dt, bn), b_ext=b_ext)
+        u_prev, u = u, un
+        t += dt
+    return float(np.max(np.abs(u[pb.inside] - mf.u(t, nodes[pb.inside]))))
+
+
+def _scalar_gear_error(dt, t_end):
+    lam = 2 * math.pi ** 2
+    a_prev, a, t = 1.0, math.exp(-dt), dt
+    for _ in range(int(round(t_end / dt)) - 1):
+        rhs = (4 * a - a_prev) / 3 + dt * (lam - 1) * (4 * math.exp(-t) - 2 * math.exp(-(t - dt))) / 3
+        a_prev, a = a, rhs / (1 + 2 * dt * lam / 3)
+        t += dt
+    return abs(a - math.exp(-t))
+
+
+def test_manufactured_gear_second_order():
+    # steps large enough that the temporal error dominates the spatial error of this small
+    # discretisation (alpha >= 2.3 boundary spacings)
+    e1, e2 = _run_gear(4e-2, 0.16), _run_gear(2e-2, 0.16)
+    p1, p2 = _scalar_gear_error(4e-2, 0.16), _scalar_gear_error(2e-2, 0.16)
+    assert abs(e1 - p1) < 0.05 * p1 and abs(e2 - p2) < 0.1 * p2, (e1, p1, e2, p2)
+    assert 3.0 < e1 / e2 < 5.0
