@@ -100,6 +100,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_over_ranks(local_ms: float, points_per_rank: int, steps: int, dist=None, device=None):
+    """Whole-job throughput of N independent replicas: the time is the maximum over ranks
+    (each rank times its own K steps), the work is the sum of every rank's points * steps.
+    Returns (value, max_ms)."""
+    import torch
+    total_ms = float(local_ms)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return points_per_rank * steps * world / (total_ms / 1e3), total_ms
+
+
 def setup_problem(mh, ctx, wl, torch, dev):
     t0 = time.time()
     tree = mh.Tree(ctx, wl.box, wl.q, wl.min_level, wl.max_level, wl.forcing, wl.refine_tol)
@@ -180,11 +195,7 @@ def run_ours(args):
               "volume_apply", "gmres", "dlp_evaluate"):
         regions_ms[r] = ctx.profile_read(r)
     ctx.profile(False)
-    total_ms = float(sum(times))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value, total_ms = aggregate_over_ranks(sum(times), n_pts, args.steps, dist, dev)
     # end to end through the API with host buffers
     pin = lambda a: torch.tensor(a).pin_memory()
     u_h = pin(u.cpu().numpy())
@@ -210,19 +221,13 @@ def run_ours(args):
         b.synchronize()
         e2e_times.append(a.elapsed_time(b))
         u_h.copy_(out_h)
-    e2e_ms = float(sum(e2e_times))
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_value, e2e_ms = aggregate_over_ranks(sum(e2e_times), n_pts, args.steps, dist, dev)
     bytes_in = (2 * tree.n_nodes + bnd.n) * 8
     bytes_out = tree.n_nodes * 8
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    value = n_pts * args.steps * world / (total_ms / 1e3)
-    e2e_value = n_pts * args.steps * world / (e2e_ms / 1e3)
     peaks = _peaks()
     roof = roofline(regions_ms, tree, bnd, prob, prec, mh, peaks, args.steps)
     line = {
