@@ -209,6 +209,10 @@ mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* bnd, double
 mh_status mh_problem_destroy(mh_problem* prob);
 /* Region of every volume node: -1 inside Omega, k on the exterior side of curve k. */
 mh_status mh_problem_regions(mh_ctx* ctx, const mh_problem* prob, int32_t* region_host);
+/* Right-hand side -2 alpha^2 (f_next - U^p|Gamma) of the boundary equation solved by the last
+ * heat_step / heat_step_gear on this problem (Section 3.2): N_Gamma doubles copied on the
+ * ctx stream into the caller's device buffer rhs_dev.  Zeros before the first step. */
+mh_status mh_problem_rhs(mh_ctx* ctx, const mh_problem* prob, double* rhs_dev);
 
 /* One IMEX Euler step u^N -> u^{N+1} (Section 2):
  *   B = u + dt F (inside), extension outside; U^p = volume potential of B;

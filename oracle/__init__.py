@@ -16,6 +16,8 @@ Modules
   volume      direct volume potential with exact integrals of the leaf interpolant
   tree        adaptive quadtree, 2:1 balance and interaction lists
   step        IMEX (backward) Euler heat step (Section 2)
+  warmstart   learned initial guess for the boundary solve (Fourier features, MLP,
+              closed-form start, Adam, minimum-residual judge)
 
 Parity pins: every function is checked in ``tests/test_oracle_*.py`` against
 closed forms, special cases and brute force (see each module's docstring).

@@ -65,6 +65,7 @@ _SIGS = {
     "mh_problem_create": [_p, _p, _p, _d, _i, _i, _i, _p, ctypes.POINTER(_p)],
     "mh_problem_destroy": [_p],
     "mh_problem_regions": [_p, _p, _p],
+    "mh_problem_rhs": [_p, _p, _p],
     "heat_step": [_p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
     "heat_step_gear": [_p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
     "mh_gmres_solve_static": [_p, _p, _d, _p, _p, _d, _i, ctypes.POINTER(GmresInfo)],
@@ -265,6 +266,11 @@ class Problem:
     def regions(self) -> np.ndarray:
         out = np.zeros(self.tree.n_nodes, dtype=np.int32)
         self.ctx.check(_lib.mh_problem_regions(self.ctx.h, self.h, out.ctypes.data_as(_p)))
+        return out
+
+    def rhs(self, out):
+        """Right-hand side of the boundary equation of the last step, into the device buffer out."""
+        self.ctx.check(_lib.mh_problem_rhs(self.ctx.h, self.h, _ptr(out)))
         return out
 
     def __del__(self):

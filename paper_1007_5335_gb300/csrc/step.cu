@@ -197,6 +197,7 @@ extern "C" mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* 
     MH_ALLOC(ctx, P->Up, n);
     MH_ALLOC(ctx, P->Ug, bnd->n);
     MH_ALLOC(ctx, P->rhs, bnd->n);
+    MH_CUDA(ctx, cudaMemsetAsync(P->rhs.p, 0, bnd->n * 8, st));
     MH_ALLOC(ctx, P->Uh, std::max<int64_t>(P->n_inside, 1));
     // operators: boundary (alpha) and volume (alpha, p) -- built once here
     MH_TRY(bie_assemble(ctx, bnd, P->alpha));
@@ -216,6 +217,12 @@ extern "C" mh_status mh_problem_regions(mh_ctx* ctx, const mh_problem* p, int32_
     if (!ctx || !p || !region_host) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
     MH_CUDA(ctx, cudaMemcpyAsync(region_host, p->region.p, p->tree->n_nodes * 4, cudaMemcpyDeviceToHost, ctx->stream));
     MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return MH_OK;
+}
+
+extern "C" mh_status mh_problem_rhs(mh_ctx* ctx, const mh_problem* p, double* rhs_dev) {
+    if (!ctx || !p || !rhs_dev) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    MH_CUDA(ctx, cudaMemcpyAsync(rhs_dev, p->rhs.p, p->bnd->n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     return MH_OK;
 }
 
