@@ -67,11 +67,14 @@ typedef struct {
     int refinements;       /* FP64 refinement sweeps (mixed precision), else 0 */
     double rel_residual;   /* final ||b - A x|| / ||b|| computed in binary64 */
     int converged;         /* 1 if rel_residual <= tol */
+    double initial_rel_residual;   /* ||b - A x0|| / ||b|| of the initial guess */
 } mh_gmres_info;
 
 typedef struct {
     int gmres_iterations;
     double gmres_rel_residual;
+    double initial_rel_residual;   /* of the GMRES start chosen by the warm-start mode */
+    double warm_c;                 /* step length of the SECANT / LEARNED start (0 otherwise) */
 } mh_step_info;
 
 /* Field callback used by mh_tree_build: evaluate the user's F at n points
@@ -235,6 +238,110 @@ mh_status heat_step_gear(mh_ctx* ctx, mh_problem* prob, const double* u_dev, con
                          const double* F_dev, const double* F_prev_dev, const double* f_next_dev,
                          const double* b_ext_dev, double* u_next_dev, double* sigma_dev, double gmres_tol,
                          mh_precision prec, mh_step_info* info);
+
+/* ------------------------------------------------------------------------------------------
+ * Learned warm start of the boundary solve.
+ *
+ * The paper solves A sigma^{N+1} = b^{N+1} by GMRES to relative residual 1e-10 at every
+ * step (Section 3.2, Section 4) and states no initial guess.  These calls choose one.
+ * With r = b - A sigma^N, the residual of the previous-step start, a network predicts the
+ * correction delta ~ A^{-1} r:
+ *   features  x = F(r) / (|r| g_x): F = the Fourier coefficients
+ *             c_k = (1/N_k) sum_j v_j exp(-2 pi i j k / N_k), k = 0 .. n_modes-1, of every
+ *             curve, curve-major as [Re c_0, Im c_0, Re c_1, Im c_1, ...]; d = n_curves *
+ *             2 n_modes features;
+ *   network   y = W4 t(W3 t(W2 t(W1 x + b1) + b2) + b3) + b4, t = tanh, width w;
+ *   output    delta = r + |r| g_y S(y), S = Fourier synthesis
+ *             v_j = Re c_0 + 2 sum_{k>=1} Re(c_k exp(2 pi i j k / N_k));
+ *   judge     w = A delta, c = <r, w> / <w, w> (0 when <w, w> = 0 or c is not finite);
+ *             x0 = sigma^N + c delta and r0 = r - c w: the minimum residual on the line
+ *             through sigma^N, never above the previous-step start (c = 0).
+ * Parameters are binary32 in one flat array: W1 [w][d], b1 [w], W2 [w][w], b2 [w],
+ * W3 [w][w], b3 [w], W4 [d][w], b4 [d] (row-major, W[out][in]).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct mh_net mh_net;
+
+typedef enum {
+    MH_NET_FP32 = 0,    /* binary32 weights */
+    MH_NET_BF16 = 1,    /* bfloat16 weights (round to nearest even) */
+    MH_NET_BF16X2 = 2   /* bfloat16 pair hi + lo, lo = bf16(w - hi) */
+} mh_net_arith;         /* inference weights; activations and sums are binary32 in all three */
+
+typedef enum {
+    MH_WARM_PREVIOUS = 0,   /* x0 = sigma^N (default) */
+    MH_WARM_ZERO = 1,       /* x0 = 0 */
+    MH_WARM_SECANT = 2,     /* judge along sigma^N - sigma^{N-1} (no network) */
+    MH_WARM_LEARNED = 3     /* judge along the network's delta */
+} mh_warm_mode;
+
+/* Network for the boundary of bnd.  n_modes: multiple of 4, at most N_k / 2 on every curve;
+ * width: multiple of 8 in 8..1024.  Parameters start at zero, g_x = g_y = 1. */
+mh_status mh_net_create(mh_ctx* ctx, const mh_boundary* bnd, int n_modes, int width, mh_net** out);
+mh_status mh_net_destroy(mh_net* net);
+mh_status mh_net_dims(const mh_net* net, int64_t* d, int64_t* width, int64_t* n_params);
+/* Copy the parameters (n_params floats) and the scales g_x, g_y out of / into the network. */
+mh_status mh_net_get_params(mh_ctx* ctx, const mh_net* net, float* params_host, double* gx_host, double* gy_host);
+mh_status mh_net_set_params(mh_ctx* ctx, mh_net* net, const float* params_host, double gx, double gy);
+
+/* One training pair from the last step solved on prob: r = rhs - A sigma_prev (binary64,
+ * the operator of the problem's boundary and alpha, rhs of mh_problem_rhs),
+ * x = F(r)/|r|, y = F(sigma_next - sigma_prev - r)/|r| into x_dev, y_dev (d floats each,
+ * not divided by g_x, g_y); r_norm_host (nullable): |r|.  |r| = 0 gives zero rows. */
+mh_status mh_net_sample(mh_ctx* ctx, mh_problem* prob, mh_net* net, const double* sigma_prev_dev,
+                        const double* sigma_next_dev, float* x_dev, float* y_dev, double* r_norm_host);
+
+/* Closed-form start of training on n >= 2 pairs (X_dev, Y_dev: n x d rows from
+ * mh_net_sample).  g_x, g_y = RMS entries of X, Y; on X/g_x, Y/g_y (binary64):
+ *   mu = mean row, Xc = X - mu; Q = orth(Xc^T omega), then power_iters times
+ *   Q = orth(Xc^T (Xc Q)), orth = the Q factor whose R has a positive diagonal;
+ *   s = RMS of the columns of Xc Q floored at 1e-8 max s; W1 = eps diag(1/s) Q^T,
+ *   b1 = -W1 mu; W2 = W3 = I, b2 = b3 = 0; [W4 | b4] = ridge least squares
+ *   (Ha^T Ha + lam I) Z = Ha^T Y on Ha = [H, 1], H the third hidden layer on X,
+ *   lam = ridge trace(Ha^T Ha)/(w + 1).
+ * omega_dev: n x w binary32 (Gaussian draws supplied by the caller).
+ * MH_ERR_NUMERIC when an orthogonalisation or the least-squares system is singular. */
+mh_status mh_net_fit(mh_ctx* ctx, mh_net* net, const float* X_dev, const float* Y_dev, int64_t n,
+                     const float* omega_dev, double eps, int power_iters, double ridge);
+
+/* Loss L = (1/(2 n d)) sum (net(X) - T)^2 on network-unit inputs X and targets T (n x d,
+ * already divided by g_x and g_y) and its gradient (n_params floats, parameter layout)
+ * by the binary32 training kernels. */
+mh_status mh_net_loss_grad(mh_ctx* ctx, mh_net* net, const float* X_dev, const float* T_dev, int64_t n,
+                           double* loss_host, float* grad_dev);
+
+/* Network outputs Y_dev (n x d) for network-unit inputs X_dev (n x d): the binary32
+ * training kernels when training_kernels != 0 (arith ignored), else the inference kernels
+ * with weights in arith. */
+mh_status mh_net_forward(mh_ctx* ctx, mh_net* net, const float* X_dev, int64_t n, float* Y_dev,
+                         mh_net_arith arith, int training_kernels);
+
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on L over `steps` minibatches;
+ * batch_idx_dev: steps x batch row indices into X_dev, Y_dev (pairs from mh_net_sample,
+ * divided by g_x, g_y inside).  Every eval_every steps and after the last, L on the
+ * validation pairs Xv_dev, Yv_dev (n_val rows) is computed; the parameters with the lowest
+ * validation loss (the starting ones included) are kept.  first_val_host, best_val_host,
+ * best_step_host (nullable): validation loss at the start, the best loss and its step. */
+mh_status mh_net_train(mh_ctx* ctx, mh_net* net, const float* X_dev, const float* Y_dev, int64_t n,
+                       const int32_t* batch_idx_dev, int steps, int batch, double lr, const float* Xv_dev,
+                       const float* Yv_dev, int64_t n_val, int eval_every, double* first_val_host,
+                       double* best_val_host, int* best_step_host);
+
+/* Initial guess for A x = rhs on bnd at screening length alpha (the operator is assembled
+ * if needed).  r = rhs - A sigma in binary64; the judge's w = A delta in precision prec.
+ * PREVIOUS: x0 = sigma; ZERO: x0 = 0; SECANT: direction sigma - sigma_prev2 (sigma_prev2_dev
+ * required); LEARNED: the network's delta with weights in arith (net required).
+ * x0_dev (may alias sigma_dev) and r0_dev (= rhs - A x0): N_Gamma doubles.
+ * c_host (nullable): the step length. */
+mh_status mh_warm_start(mh_ctx* ctx, mh_boundary* bnd, double alpha, mh_net* net, mh_warm_mode mode,
+                        mh_net_arith arith, const double* sigma_dev, const double* sigma_prev2_dev,
+                        const double* rhs_dev, double* x0_dev, double* r0_dev, mh_precision prec,
+                        double* c_host);
+
+/* Warm-start mode of heat_step / heat_step_gear on prob (default MH_WARM_PREVIOUS).  SECANT
+ * keeps a copy of the incoming density of every step; its first step uses PREVIOUS.  The
+ * network stays owned by the caller and must outlive its use. */
+mh_status mh_problem_set_warm_start(mh_ctx* ctx, mh_problem* prob, mh_warm_mode mode, mh_net* net,
+                                    mh_net_arith arith);
 
 #ifdef __cplusplus
 }

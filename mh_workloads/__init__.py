@@ -222,3 +222,32 @@ class Example1:
     def curves(self, n_outer, n_inner):
         return [circle_nodes((0.0, 0.0), self.R0, n_outer, clockwise=False),
                 circle_nodes((0.0, 0.0), self.R1, n_inner, clockwise=True)]
+
+
+# ---------------------------------------------------------------------------- learned warm start
+WARM_TRAIN_SEEDS = tuple(range(100, 200))     # forcings whose trajectories train the network
+WARM_VALID_SEEDS = tuple(range(200, 210))     # validation trajectories (early stopping)
+WARM_TEST_SEEDS = tuple(range(300, 305))      # held-out trajectories
+
+
+def warm_start_draws(n: int, width: int, steps: int, batch: int, seed: int = 7):
+    """Random numbers of the learned warm start's training, drawn here and passed in:
+    omega (n x width standard normal, binary32) for the range finder of the closed-form start
+    and the Adam minibatches (steps x batch row indices, uniform with replacement, int32)."""
+    rng = np.random.default_rng(seed)
+    omega = rng.standard_normal((n, width)).astype(np.float32)
+    idx = rng.integers(0, n, size=(steps, batch)).astype(np.int32)
+    return omega, idx
+
+
+def warm_start_toy_data(n: int, d: int, rank: int, seed: int = 11):
+    """Small synthetic pairs for parity tests of the training kernels: rows of X in a random
+    rank-`rank` subspace with a decaying spectrum plus a mean, Y = X M^T + c (binary32)."""
+    rng = np.random.default_rng(seed)
+    basis = np.linalg.qr(rng.standard_normal((d, rank)))[0]
+    mu = rng.standard_normal(d)
+    coef = rng.standard_normal((n, rank)) * np.geomspace(1.0, 1e-2, rank)
+    X = mu + coef @ basis.T
+    M = rng.standard_normal((d, d)) / math.sqrt(d)
+    c = rng.standard_normal(d)
+    return X.astype(np.float32), (X @ M.T + c).astype(np.float32)

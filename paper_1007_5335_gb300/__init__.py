@@ -24,6 +24,13 @@ MH_EXT_CONST = 0
 MH_EXT_ARRAY = 1
 MH_SCHEME_IMEX_EULER = 0
 MH_SCHEME_EXTRAP_GEAR = 1
+MH_NET_FP32 = 0
+MH_NET_BF16 = 1
+MH_NET_BF16X2 = 2
+MH_WARM_PREVIOUS = 0
+MH_WARM_ZERO = 1
+MH_WARM_SECANT = 2
+MH_WARM_LEARNED = 3
 STATUS = {0: "MH_OK", 1: "MH_ERR_INVALID_ARG", 2: "MH_ERR_GEOMETRY", 3: "MH_ERR_CUDA", 4: "MH_ERR_OOM",
           5: "MH_ERR_NOT_CONVERGED", 6: "MH_ERR_TIMEOUT", 7: "MH_ERR_NUMERIC", 8: "MH_ERR_CALLBACK"}
 LISTS = {"U": 0, "V": 1, "W": 2, "X": 3}
@@ -35,11 +42,12 @@ _d = ctypes.c_double
 
 
 class GmresInfo(ctypes.Structure):
-    _fields_ = [("iterations", _i), ("refinements", _i), ("rel_residual", _d), ("converged", _i)]
+    _fields_ = [("iterations", _i), ("refinements", _i), ("rel_residual", _d), ("converged", _i),
+                ("initial_rel_residual", _d)]
 
 
 class StepInfo(ctypes.Structure):
-    _fields_ = [("gmres_iterations", _i), ("gmres_rel_residual", _d)]
+    _fields_ = [("gmres_iterations", _i), ("gmres_rel_residual", _d), ("initial_rel_residual", _d), ("warm_c", _d)]
 
 
 FIELD_FN = ctypes.CFUNCTYPE(_i, ctypes.POINTER(_d), _i64, ctypes.POINTER(_d), _p)
@@ -69,6 +77,19 @@ _SIGS = {
     "heat_step": [_p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
     "heat_step_gear": [_p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
     "mh_gmres_solve_static": [_p, _p, _d, _p, _p, _d, _i, ctypes.POINTER(GmresInfo)],
+    "mh_net_create": [_p, _p, _i, _i, ctypes.POINTER(_p)],
+    "mh_net_destroy": [_p],
+    "mh_net_dims": [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
+    "mh_net_get_params": [_p, _p, _p, ctypes.POINTER(_d), ctypes.POINTER(_d)],
+    "mh_net_set_params": [_p, _p, _p, _d, _d],
+    "mh_net_sample": [_p, _p, _p, _p, _p, _p, _p, ctypes.POINTER(_d)],
+    "mh_net_fit": [_p, _p, _p, _p, _i64, _p, _d, _i, _d],
+    "mh_net_loss_grad": [_p, _p, _p, _p, _i64, ctypes.POINTER(_d), _p],
+    "mh_net_forward": [_p, _p, _p, _i64, _p, _i, _i],
+    "mh_net_train": [_p, _p, _p, _p, _i64, _p, _i, _i, _d, _p, _p, _i64, _i, ctypes.POINTER(_d),
+                     ctypes.POINTER(_d), ctypes.POINTER(_i)],
+    "mh_warm_start": [_p, _p, _d, _p, _i, _i, _p, _p, _p, _p, _p, _i, ctypes.POINTER(_d)],
+    "mh_problem_set_warm_start": [_p, _p, _i, _p, _i],
     "mh_profile_enable": [_p, _i],
     "mh_profile_read": [_p, ctypes.c_char_p, ctypes.POINTER(_d), ctypes.POINTER(_i64), ctypes.POINTER(_d),
                         ctypes.POINTER(_d), _i],
@@ -93,6 +114,15 @@ def _ptr(t):
         return None
     if not t.is_cuda or t.dtype.itemsize != 8 or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor of 8-byte elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ptr4(t):
+    """Device pointer of a contiguous CUDA float32 / int32 tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype.itemsize != 4 or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor of 4-byte elements")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -268,6 +298,12 @@ class Problem:
         self.ctx.check(_lib.mh_problem_regions(self.ctx.h, self.h, out.ctypes.data_as(_p)))
         return out
 
+    def set_warm_start(self, mode: int, net=None, arith: int = MH_NET_BF16X2):
+        """mh_problem_set_warm_start: GMRES start of the following steps."""
+        self.ctx.check(_lib.mh_problem_set_warm_start(self.ctx.h, self.h, int(mode), net.h if net is not None else None,
+                                                      int(arith)))
+        self._net = net          # keep the network alive while the problem uses it
+
     def rhs(self, out):
         """Right-hand side of the boundary equation of the last step, into the device buffer out."""
         self.ctx.check(_lib.mh_problem_rhs(self.ctx.h, self.h, _ptr(out)))
@@ -294,6 +330,78 @@ def heat_step_gear(ctx: Context, prob: Problem, u, u_prev, F, F_prev, f_next, u_
                                   _ptr(b_ext), _ptr(u_next), _ptr(sigma), float(gmres_tol), int(prec),
                                   ctypes.byref(info)))
     return info
+
+
+class Net:
+    """mh_net_create: the learned warm start's network for the boundary bnd (see include/mh.h)."""
+
+    def __init__(self, ctx: Context, bnd: Boundary, n_modes: int = 256, width: int = 256):
+        self.ctx, self.bnd = ctx, bnd
+        h = _p()
+        ctx.check(_lib.mh_net_create(ctx.h, bnd.h, int(n_modes), int(width), ctypes.byref(h)))
+        self.h = h
+        d, w, n = _i64(), _i64(), _i64()
+        _lib.mh_net_dims(h, ctypes.byref(d), ctypes.byref(w), ctypes.byref(n))
+        self.d, self.width, self.n_params = d.value, w.value, n.value
+        self.n_modes = n_modes
+
+    def get_params(self):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        gx, gy = _d(), _d()
+        self.ctx.check(_lib.mh_net_get_params(self.ctx.h, self.h, out.ctypes.data_as(_p), ctypes.byref(gx),
+                                              ctypes.byref(gy)))
+        return out, gx.value, gy.value
+
+    def set_params(self, params, gx: float = 1.0, gy: float = 1.0):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        if a.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        self.ctx.check(_lib.mh_net_set_params(self.ctx.h, self.h, a.ctypes.data_as(_p), float(gx), float(gy)))
+
+    def sample(self, prob: "Problem", sigma_prev, sigma_next, x_out, y_out) -> float:
+        rn = _d()
+        self.ctx.check(_lib.mh_net_sample(self.ctx.h, prob.h, self.h, _ptr(sigma_prev), _ptr(sigma_next),
+                                          _ptr4(x_out), _ptr4(y_out), ctypes.byref(rn)))
+        return rn.value
+
+    def fit(self, X, Y, omega, eps: float = 1e-3, power_iters: int = 2, ridge: float = 1e-12):
+        self.ctx.check(_lib.mh_net_fit(self.ctx.h, self.h, _ptr4(X), _ptr4(Y), int(X.shape[0]), _ptr4(omega),
+                                       float(eps), int(power_iters), float(ridge)))
+
+    def loss_grad(self, X, T, grad_out=None) -> float:
+        loss = _d()
+        self.ctx.check(_lib.mh_net_loss_grad(self.ctx.h, self.h, _ptr4(X), _ptr4(T), int(X.shape[0]),
+                                             ctypes.byref(loss), _ptr4(grad_out)))
+        return loss.value
+
+    def forward(self, X, Y_out, arith: int = MH_NET_FP32, training_kernels: bool = True):
+        self.ctx.check(_lib.mh_net_forward(self.ctx.h, self.h, _ptr4(X), int(X.shape[0]), _ptr4(Y_out), int(arith),
+                                           1 if training_kernels else 0))
+        return Y_out
+
+    def train(self, X, Y, batch_idx, lr: float, Xv, Yv, eval_every: int = 100):
+        """Adam over the minibatches batch_idx (steps x batch int32); returns (first, best, best_step)."""
+        first, best, step = _d(), _d(), _i()
+        steps, batch = int(batch_idx.shape[0]), int(batch_idx.shape[1])
+        self.ctx.check(_lib.mh_net_train(self.ctx.h, self.h, _ptr4(X), _ptr4(Y), int(X.shape[0]), _ptr4(batch_idx),
+                                         steps, batch, float(lr), _ptr4(Xv), _ptr4(Yv), int(Xv.shape[0]),
+                                         int(eval_every), ctypes.byref(first), ctypes.byref(best),
+                                         ctypes.byref(step)))
+        return first.value, best.value, step.value
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.mh_net_destroy(self.h)
+            self.h = None
+
+
+def mh_warm_start(ctx: Context, bnd: Boundary, alpha: float, mode: int, sigma, rhs, x0_out, r0_out, net=None,
+                  arith: int = MH_NET_BF16X2, sigma_prev2=None, prec: int = MH_PREC_FP64) -> float:
+    c = _d()
+    ctx.check(_lib.mh_warm_start(ctx.h, bnd.h, float(alpha), net.h if net is not None else None, int(mode), int(arith),
+                                 _ptr(sigma), _ptr(sigma_prev2), _ptr(rhs), _ptr(x0_out), _ptr(r0_out), int(prec),
+                                 ctypes.byref(c)))
+    return c.value
 
 
 def library_path() -> str:

@@ -1243,17 +1243,23 @@ static mh_status vec_norm(mh_ctx* ctx, const double* v, int64_t n, double* dev_o
 // Unrestarted GMRES on A (precision prec) for A x = b; x holds the initial guess.
 // Returns iterations used and the Givens residual estimate (absolute).
 static mh_status gmres_core(mh_ctx* ctx, mh_boundary* bd, gmres_ws& ws, const double* b, double* x, double abs_tol,
-                            int max_iter, mh_precision prec, int* iters, double* resid) {
+                            int max_iter, mh_precision prec, int* iters, double* resid, const double* r0,
+                            double* beta0) {
     const int64_t n = bd->n;
     cudaStream_t st = ctx->stream;
     const int ew = mh_grid(n, 256) < 152 * 4 ? mh_grid(n, 256) : 152 * 4;
     const int ldh = max_iter + 1;
-    // r = b - A x
-    MH_TRY(bie_apply(ctx, bd, x, ws.w.p, prec));
-    k_sub_from<<<ew, 256, 0, st>>>(b, ws.w.p, n);
-    MH_LAUNCHED(ctx);
+    // r = b - A x (or the caller's residual of x)
+    if (r0) {
+        MH_CUDA(ctx, cudaMemcpyAsync(ws.w.p, r0, n * 8, cudaMemcpyDeviceToDevice, st));
+    } else {
+        MH_TRY(bie_apply(ctx, bd, x, ws.w.p, prec));
+        k_sub_from<<<ew, 256, 0, st>>>(b, ws.w.p, n);
+        MH_LAUNCHED(ctx);
+    }
     double beta;
     MH_TRY(vec_norm(ctx, ws.w.p, n, ws.small.p + 1, &beta));
+    if (beta0) *beta0 = beta;
     *iters = 0;
     *resid = beta;
     if (beta <= abs_tol) return MH_OK;
@@ -1312,7 +1318,7 @@ static mh_status gmres_core(mh_ctx* ctx, mh_boundary* bd, gmres_ws& ws, const do
 }
 
 mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, double tol, int max_iter,
-                    mh_precision prec, mh_gmres_info* info) {
+                    mh_precision prec, mh_gmres_info* info, const double* r0) {
     prof_scope ps_all(ctx, "gmres");
     const int64_t n = bd->n;
     if (max_iter < 1 || max_iter > 1000) return mh_fail(ctx, MH_ERR_INVALID_ARG, "max_iter must be in 1..1000");
@@ -1337,7 +1343,7 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
     MH_CUDA(ctx, cudaMemsetAsync(ws.g.p, 0, (max_iter + 2) * 8, ctx->stream));
     double bnorm;
     MH_TRY(vec_norm(ctx, b, n, ws.small.p + 2, &bnorm));
-    mh_gmres_info inf{0, 0, 0.0, 0};
+    mh_gmres_info inf{0, 0, 0.0, 0, 0.0};
     if (bnorm == 0.0) {
         MH_CUDA(ctx, cudaMemsetAsync(x, 0, n * 8, ctx->stream));
         inf.converged = 1;
@@ -1347,8 +1353,10 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
     if (prec == MH_PREC_FP64) {
         int it;
         double res;
-        MH_TRY(gmres_core(ctx, bd, ws, b, x, tol * bnorm, max_iter, MH_PREC_FP64, &it, &res));
+        double beta0;
+        MH_TRY(gmres_core(ctx, bd, ws, b, x, tol * bnorm, max_iter, MH_PREC_FP64, &it, &res, r0, &beta0));
         inf.iterations = it;
+        inf.initial_rel_residual = beta0 / bnorm;
     } else {
         // binary64 iterative refinement around binary32-operator GMRES
         dbuf<double>& r = ws.r;
@@ -1356,17 +1364,32 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
         int total = 0;
         double rn = -1.0;
         for (int sweep = 0;; ++sweep) {
-            MH_TRY(bie_apply(ctx, bd, x, r.p, MH_PREC_FP64));
-            k_sub_from<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(b, r.p, n);
-            MH_LAUNCHED(ctx);
+            // binary64 residual of x; at the first sweep the caller's r0 (if given) stands in
+            // for it, but convergence is only ever accepted on a residual computed here
+            bool computed = true;
+            if (sweep == 0 && r0) {
+                MH_CUDA(ctx, cudaMemcpyAsync(r.p, r0, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+                computed = false;
+            } else {
+                MH_TRY(bie_apply(ctx, bd, x, r.p, MH_PREC_FP64));
+                k_sub_from<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(b, r.p, n);
+                MH_LAUNCHED(ctx);
+            }
             MH_TRY(vec_norm(ctx, r.p, n, ws.small.p + 2, &rn));
+            if (sweep == 0) inf.initial_rel_residual = rn / bnorm;
+            if (!computed && rn <= tol * bnorm) {
+                MH_TRY(bie_apply(ctx, bd, x, r.p, MH_PREC_FP64));
+                k_sub_from<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(b, r.p, n);
+                MH_LAUNCHED(ctx);
+                MH_TRY(vec_norm(ctx, r.p, n, ws.small.p + 2, &rn));
+            }
             if (rn <= tol * bnorm || total >= max_iter || sweep >= 12) break;
             MH_CUDA(ctx, cudaMemsetAsync(dx.p, 0, n * 8, ctx->stream));
             MH_CUDA(ctx, cudaMemsetAsync(ws.g.p, 0, (max_iter + 2) * 8, ctx->stream));
             int it;
             double res;
             MH_TRY(gmres_core(ctx, bd, ws, r.p, dx.p, std::max(tol * bnorm, 1e-5 * rn), max_iter - total,
-                              MH_PREC_MIXED, &it, &res));
+                              MH_PREC_MIXED, &it, &res, r.p, nullptr));
             total += it;
             inf.refinements++;
             k_axpy<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(1.0, dx.p, x, n);

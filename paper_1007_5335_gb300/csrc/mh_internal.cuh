@@ -96,9 +96,7 @@ struct dbuf {
 
 // GMRES workspace (kept by the boundary so that repeated solves allocate nothing).
 struct gmres_ws {
-    dbuf<double> V, H, cs, sn, g, y, h1, h2, small, w, r, dx, part;
-    dbuf<float> v32;
-    int coop_grid = 0;     // blocks of the persistent GMRES kernel (0 = not set up)
+    dbuf<double> V, H, cs, sn, g, y, h1, h2, small, w, r, dx;
     int m = 0;
     int64_t n = 0;
 };
@@ -138,6 +136,7 @@ struct mh_boundary {
     dbuf<float> w32, wf32, x32;          // per call: weights, fine weights, GEMV input
     dbuf<double> sc64, wf64;             // per call: density Fourier coefficients, fine weights
     dbuf<float> sc32;
+    dbuf<double> warm_dir, warm_w, warm_scal;   // warm-start direction, its image, scalars
 };
 
 #define MH_TILE 128
@@ -195,7 +194,25 @@ struct mh_problem {
     int64_t n_inside = 0;
     dbuf<int32_t> bnd_leaf;              // leaf of every boundary node
     dbuf<double> B, Up, Ug, rhs, Uh;     // work arrays
+    // GMRES start (mh_problem_set_warm_start)
+    int warm_mode = 0;
+    int warm_arith = 0;
+    struct mh_net* net = nullptr;
+    bool have_prev = false;              // sig_prev holds the density entering the previous step
+    dbuf<double> sig_prev, r0, c_dev;
+    double* c_host = nullptr;            // pinned
+    ~mh_problem() {
+        if (c_host) cudaFreeHost(c_host);
+    }
 };
+
+// ---- net.cu ----
+// Initial guess for A x = rhs (see mh_warm_start in mh.h); c_dev receives the step length.
+// save (nullable) receives the incoming sigma before x0 is written.
+mh_status warm_start_run(mh_ctx* ctx, mh_boundary* bnd, double alpha, struct mh_net* net, int mode, int arith,
+                         const double* sigma, const double* sigma_prev2, const double* rhs, double* x0, double* r0,
+                         mh_precision prec, double* c_dev, double* save);
+bool net_matches(const struct mh_net* net, const mh_boundary* b);
 
 // ---- boundary.cu ----
 mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha);
@@ -213,8 +230,9 @@ mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_t
 // Density on the 16x fine grid times |y'| h_f (binary64 in b->wf64; binary32 also in b->wf32
 // when prec is mixed).
 mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_precision prec);
+// r0 (nullable): the binary64 residual rhs - A x of the initial guess, computed by the caller.
 mh_status gmres_run(mh_ctx* ctx, mh_boundary* b, const double* rhs, double* x, double tol, int max_iter,
-                    mh_precision prec, mh_gmres_info* info);
+                    mh_precision prec, mh_gmres_info* info, const double* r0 = nullptr);
 
 // ---- tree.cu ----
 void mh_gauss_legendre(int n, double* x, double* w);

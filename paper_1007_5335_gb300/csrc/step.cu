@@ -220,6 +220,28 @@ extern "C" mh_status mh_problem_regions(mh_ctx* ctx, const mh_problem* p, int32_
     return MH_OK;
 }
 
+extern "C" mh_status mh_problem_set_warm_start(mh_ctx* ctx, mh_problem* p, mh_warm_mode mode, mh_net* net,
+                                               mh_net_arith arith) {
+    if (!ctx || !p) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    if (mode < MH_WARM_PREVIOUS || mode > MH_WARM_LEARNED) return mh_fail(ctx, MH_ERR_INVALID_ARG, "bad mode");
+    if (arith < MH_NET_FP32 || arith > MH_NET_BF16X2) return mh_fail(ctx, MH_ERR_INVALID_ARG, "bad arith");
+    if (mode == MH_WARM_LEARNED && !net_matches(net, p->bnd))
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "MH_WARM_LEARNED needs a network built for this boundary");
+    const int64_t ng = p->bnd->n;
+    if (!p->r0.p) {
+        MH_ALLOC(ctx, p->r0, ng);
+        MH_ALLOC(ctx, p->c_dev, 1);
+        MH_CUDA(ctx, cudaMallocHost((void**)&p->c_host, 8));
+        *p->c_host = 0.0;
+    }
+    if (mode == MH_WARM_SECANT && !p->sig_prev.p) MH_ALLOC(ctx, p->sig_prev, ng);
+    p->warm_mode = mode;
+    p->net = mode == MH_WARM_LEARNED ? net : nullptr;
+    p->warm_arith = arith;
+    p->have_prev = false;
+    return MH_OK;
+}
+
 extern "C" mh_status mh_problem_rhs(mh_ctx* ctx, const mh_problem* p, double* rhs_dev) {
     if (!ctx || !p || !rhs_dev) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
     MH_CUDA(ctx, cudaMemcpyAsync(rhs_dev, p->rhs.p, p->bnd->n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -238,10 +260,29 @@ static mh_status step_solve(mh_ctx* ctx, ProblemImpl* P, const double* f_next_de
     k_rhs<<<mh_grid(ng, 256), 256, 0, st>>>(f_next_dev, P->Ug.p, -2.0 * P->alpha * P->alpha, ng, P->rhs.p);
     MH_LAUNCHED(ctx);
     mh_gmres_info gi{};
-    mh_status s = gmres_run(ctx, b, P->rhs.p, sigma_dev, gmres_tol, 100, prec, &gi);
+    // GMRES start (mh_problem_set_warm_start); r0 = its binary64 residual when computed here
+    const double* r0 = nullptr;
+    bool have_c = false;
+    const int mode = P->warm_mode;
+    if (mode == MH_WARM_ZERO) {
+        MH_CUDA(ctx, cudaMemsetAsync(sigma_dev, 0, ng * 8, st));
+    } else if (mode == MH_WARM_SECANT && !P->have_prev) {
+        MH_CUDA(ctx, cudaMemcpyAsync(P->sig_prev.p, sigma_dev, ng * 8, cudaMemcpyDeviceToDevice, st));
+        P->have_prev = true;
+    } else if (mode == MH_WARM_SECANT || mode == MH_WARM_LEARNED) {
+        double* keep = mode == MH_WARM_SECANT ? P->sig_prev.p : nullptr;
+        MH_TRY(warm_start_run(ctx, b, P->alpha, P->net, mode, P->warm_arith, sigma_dev, keep, P->rhs.p, sigma_dev,
+                              P->r0.p, prec, P->c_dev.p, keep));
+        MH_CUDA(ctx, cudaMemcpyAsync(P->c_host, P->c_dev.p, 8, cudaMemcpyDeviceToHost, st));
+        r0 = P->r0.p;
+        have_c = true;
+    }
+    mh_status s = gmres_run(ctx, b, P->rhs.p, sigma_dev, gmres_tol, 100, prec, &gi, r0);
     if (info) {
         info->gmres_iterations = gi.iterations;
         info->gmres_rel_residual = gi.rel_residual;
+        info->initial_rel_residual = gi.initial_rel_residual;
+        info->warm_c = have_c ? *P->c_host : 0.0;   // gmres_run synchronised the stream
     }
     if (s != MH_OK) return s;
     // U^h: trapezoid sum by the multipole method at every node, then the near-boundary rules
