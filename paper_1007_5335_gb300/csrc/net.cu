@@ -176,11 +176,15 @@ __global__ void k_features(const double* __restrict__ v, const double* __restric
     const int c = gw / K, k = gw - c * K;
     const int n = nn[c], o = off[c];
     double sr = 0.0, si = 0.0;
+    // twiddle index m = j k mod n, advanced by 32 k mod n per lane step
+    const int step = (int)((32LL * k) % n);
+    int m = (int)(((int64_t)lane * k) % n);
     for (int j = lane; j < n; j += 32) {
-        const int m = (int)(((int64_t)j * k) % n);
         const double vj = v[o + j];
         sr = fma(vj, tw[2 * (o + m)], sr);
         si = fma(-vj, tw[2 * (o + m) + 1], si);
+        m += step;
+        if (m >= n) m -= n;
     }
     sr = warp_sum_d(sr);
     si = warp_sum_d(si);
@@ -191,7 +195,8 @@ __global__ void k_features(const double* __restrict__ v, const double* __restric
     }
 }
 
-// out_j = r_j + scal[0] * gy * (Re c_0 + 2 sum_{k>=1} Re(c_k e^{2 pi i j k / N})), grid (chunks, curves).
+// out_j = r_j + scal[0] * gy * (Re c_0 + 2 sum_{k>=1} Re(c_k e^{2 pi i j k / N})).  Eight threads
+// per node split the modes (k = 1 + g + 8 i); grid (chunks of 32 nodes, curves).
 __global__ void k_synth(const float* __restrict__ y, const double* __restrict__ tw, const int32_t* __restrict__ nn,
                         const int32_t* __restrict__ off, int K, const double* __restrict__ r,
                         const double* __restrict__ scal, double gy, double* __restrict__ out) {
@@ -200,18 +205,21 @@ __global__ void k_synth(const float* __restrict__ y, const double* __restrict__ 
     for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) ys[t] = y[(int64_t)c * 2 * K + t];
     __syncthreads();
     const int n = nn[c], o = off[c];
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
+    const int j = blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3), g = threadIdx.x & 7;
+    const int jj = j < n ? j : 0;
     double v = 0.0;
-    int m = 0;
-    for (int k = 1; k < K; ++k) {
-        m += j;
-        if (m >= n) m -= n;
+    int m = (int)(((int64_t)jj * (1 + g)) % n);
+    const int step = (int)((8LL * jj) % n);
+    for (int k = 1 + g; k < K; k += 8) {
         v = fma((double)ys[2 * k], tw[2 * (o + m)], v);
         v = fma(-(double)ys[2 * k + 1], tw[2 * (o + m) + 1], v);
+        m += step;
+        if (m >= n) m -= n;
     }
-    v = (double)ys[0] + 2.0 * v;
-    out[o + j] = r[o + j] + scal[0] * gy * v;
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    if (g == 0 && j < n) out[o + j] = r[o + j] + scal[0] * gy * ((double)ys[0] + 2.0 * v);
 }
 
 __device__ __forceinline__ void bf16x8(uint4 h, float* f) {
@@ -225,55 +233,64 @@ __device__ __forceinline__ void bf16x8(uint4 h, float* f) {
     f[7] = __uint_as_float(h.w & 0xffff0000u);
 }
 
-// y[row] = act(sum_k W[row][k] x[k] + b[row]) for one input vector; a warp per row, x in
-// shared memory.  in is a multiple of 8 (16-byte rows for the bfloat16 loads).
-template <int ARITH>
+// y[row] = act(sum_k W[row][k] x[k] + b[row]) for one input vector; SPLIT warps per row
+// share the row (k-slices interleaved by 32 lanes x SPLIT), x in shared memory.  in is a
+// multiple of 8 (16-byte rows for the bfloat16 loads).
+template <int ARITH, int SPLIT>
 __global__ void __launch_bounds__(256) k_gemv_layer(const float* __restrict__ W32, const uint16_t* __restrict__ Whi,
                                                     const uint16_t* __restrict__ Wlo, const float* __restrict__ bias,
                                                     const float* __restrict__ x, int in, int out, int act,
                                                     float* __restrict__ y) {
     extern __shared__ float xs[];
+    __shared__ float part[8];
     for (int k = threadIdx.x; k < in; k += blockDim.x) xs[k] = x[k];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * 8 + warp;
-    if (row >= out) return;
+    const int row = blockIdx.x * (8 / SPLIT) + warp / SPLIT, sl = warp % SPLIT;
     float acc = 0.f;
     const float4* xv = reinterpret_cast<const float4*>(xs);
-    if (ARITH == MH_NET_FP32) {
-        const float4* wr = reinterpret_cast<const float4*>(W32 + (int64_t)row * in);
-        for (int k4 = lane; k4 < in / 4; k4 += 32) {
-            const float4 a = __ldg(wr + k4), b = xv[k4];
-            acc = fmaf(a.x, b.x, acc);
-            acc = fmaf(a.y, b.y, acc);
-            acc = fmaf(a.z, b.z, acc);
-            acc = fmaf(a.w, b.w, acc);
-        }
-    } else {
-        const uint4* hr = reinterpret_cast<const uint4*>(Whi + (int64_t)row * in);
-        const uint4* lr = reinterpret_cast<const uint4*>(Wlo + (int64_t)row * in);
-        for (int k8 = lane; k8 < in / 8; k8 += 32) {
-            float wv[8];
-            bf16x8(__ldg(hr + k8), wv);
-            if (ARITH == MH_NET_BF16X2) {
-                float lv[8];
-                bf16x8(__ldg(lr + k8), lv);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) wv[e] += lv[e];
+    if (row < out) {
+        if (ARITH == MH_NET_FP32) {
+            const float4* wr = reinterpret_cast<const float4*>(W32 + (int64_t)row * in);
+            for (int k4 = lane + 32 * sl; k4 < in / 4; k4 += 32 * SPLIT) {
+                const float4 a = __ldg(wr + k4), b = xv[k4];
+                acc = fmaf(a.x, b.x, acc);
+                acc = fmaf(a.y, b.y, acc);
+                acc = fmaf(a.z, b.z, acc);
+                acc = fmaf(a.w, b.w, acc);
             }
-            const float4 b0 = xv[2 * k8], b1 = xv[2 * k8 + 1];
-            acc = fmaf(wv[0], b0.x, acc);
-            acc = fmaf(wv[1], b0.y, acc);
-            acc = fmaf(wv[2], b0.z, acc);
-            acc = fmaf(wv[3], b0.w, acc);
-            acc = fmaf(wv[4], b1.x, acc);
-            acc = fmaf(wv[5], b1.y, acc);
-            acc = fmaf(wv[6], b1.z, acc);
-            acc = fmaf(wv[7], b1.w, acc);
+        } else {
+            const uint4* hr = reinterpret_cast<const uint4*>(Whi + (int64_t)row * in);
+            const uint4* lr = reinterpret_cast<const uint4*>(Wlo + (int64_t)row * in);
+            for (int k8 = lane + 32 * sl; k8 < in / 8; k8 += 32 * SPLIT) {
+                float wv[8];
+                bf16x8(__ldg(hr + k8), wv);
+                if (ARITH == MH_NET_BF16X2) {
+                    float lv[8];
+                    bf16x8(__ldg(lr + k8), lv);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) wv[e] += lv[e];
+                }
+                const float4 b0 = xv[2 * k8], b1 = xv[2 * k8 + 1];
+                acc = fmaf(wv[0], b0.x, acc);
+                acc = fmaf(wv[1], b0.y, acc);
+                acc = fmaf(wv[2], b0.z, acc);
+                acc = fmaf(wv[3], b0.w, acc);
+                acc = fmaf(wv[4], b1.x, acc);
+                acc = fmaf(wv[5], b1.y, acc);
+                acc = fmaf(wv[6], b1.z, acc);
+                acc = fmaf(wv[7], b1.w, acc);
+            }
         }
     }
     acc = warp_sum_f(acc);
-    if (lane == 0) {
+    if (SPLIT > 1) {
+        if (lane == 0) part[warp] = acc;
+        __syncthreads();
+        if (sl != 0) return;
+        for (int q = 1; q < SPLIT; ++q) acc += part[warp + q];
+    }
+    if (lane == 0 && row < out) {
         const float z = acc + bias[row];
         y[row] = act ? tanhf(z) : z;
     }
@@ -658,6 +675,21 @@ mh_status ensure_bf16(mh_ctx* ctx, mh_net* net) {
     return MH_OK;
 }
 
+template <int ARITH>
+void launch_gemv(cudaStream_t st, const mh_net* net, int l, const float* in, float* out) {
+    const int rows = net->lout[l], cols = net->lin[l];
+    const size_t smem = (size_t)cols * sizeof(float);
+    const int act = l < 3;
+    const float* W32 = net->P.p + net->oW[l];
+    const uint16_t* hi = net->Bhi.p ? net->Bhi.p + net->oW[l] : nullptr;
+    const uint16_t* lo = net->Blo.p ? net->Blo.p + net->oW[l] : nullptr;
+    const float* b = net->P.p + net->ob[l];
+    if (cols >= 1024)   // long rows: four warps per row
+        k_gemv_layer<ARITH, 4><<<(rows + 1) / 2, 256, smem, st>>>(W32, hi, lo, b, in, cols, rows, act, out);
+    else
+        k_gemv_layer<ARITH, 1><<<(rows + 7) / 8, 256, smem, st>>>(W32, hi, lo, b, in, cols, rows, act, out);
+}
+
 // Inference of one feature vector x (d floats) into y (d floats).
 mh_status infer_one(mh_ctx* ctx, mh_net* net, int arith, const float* x, float* y) {
     if (arith != MH_NET_FP32) MH_TRY(ensure_bf16(ctx, net));
@@ -666,20 +698,12 @@ mh_status infer_one(mh_ctx* ctx, mh_net* net, int arith, const float* x, float* 
     float* bufs[2] = {net->hA.p, net->hB.p};
     for (int l = 0; l < 4; ++l) {
         float* out = l == 3 ? y : bufs[l & 1];
-        const int rows = net->lout[l], cols = net->lin[l];
-        const size_t smem = (size_t)cols * sizeof(float);
-        const int grid = (rows + 7) / 8;
-        const int act = l < 3;
-        const float* b = net->P.p + net->ob[l];
         if (arith == MH_NET_FP32)
-            k_gemv_layer<MH_NET_FP32><<<grid, 256, smem, st>>>(net->P.p + net->oW[l], nullptr, nullptr, b, in, cols,
-                                                                rows, act, out);
+            launch_gemv<MH_NET_FP32>(st, net, l, in, out);
         else if (arith == MH_NET_BF16)
-            k_gemv_layer<MH_NET_BF16><<<grid, 256, smem, st>>>(nullptr, net->Bhi.p + net->oW[l], nullptr, b, in, cols,
-                                                                rows, act, out);
+            launch_gemv<MH_NET_BF16>(st, net, l, in, out);
         else
-            k_gemv_layer<MH_NET_BF16X2><<<grid, 256, smem, st>>>(nullptr, net->Bhi.p + net->oW[l],
-                                                                  net->Blo.p + net->oW[l], b, in, cols, rows, act, out);
+            launch_gemv<MH_NET_BF16X2>(st, net, l, in, out);
         MH_LAUNCHED(ctx);
         in = out;
     }
@@ -757,10 +781,15 @@ extern "C" mh_status mh_net_create(mh_ctx* ctx, const mh_boundary* bnd, int n_mo
     MH_ALLOC(ctx, net->scal, 8);
     const int smem = (int)(std::max<int64_t>(d, w) * 4);
     if (smem > 48 * 1024) {
-        MH_CUDA(ctx, cudaFuncSetAttribute(k_gemv_layer<MH_NET_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        MH_CUDA(ctx, cudaFuncSetAttribute(k_gemv_layer<MH_NET_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        MH_CUDA(ctx,
-                cudaFuncSetAttribute(k_gemv_layer<MH_NET_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+#define MH_GEMV_ATTR(A, S)                                                                         \
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_gemv_layer<A, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))
+        MH_GEMV_ATTR(MH_NET_FP32, 1);
+        MH_GEMV_ATTR(MH_NET_FP32, 4);
+        MH_GEMV_ATTR(MH_NET_BF16, 1);
+        MH_GEMV_ATTR(MH_NET_BF16, 4);
+        MH_GEMV_ATTR(MH_NET_BF16X2, 1);
+        MH_GEMV_ATTR(MH_NET_BF16X2, 4);
+#undef MH_GEMV_ATTR
     }
     MH_CUDA(ctx, cudaStreamSynchronize(st));
     *out = net.release();
@@ -1114,7 +1143,7 @@ mh_status warm_start_run(mh_ctx* ctx, mh_boundary* b, double alpha, mh_net* net,
         MH_LAUNCHED(ctx);
         MH_TRY(features(ctx, net, r0, scal + 1, net->xin.p));
         MH_TRY(infer_one(ctx, net, arith, net->xin.p, net->yout.p));
-        k_synth<<<dim3((unsigned)mh_grid(net->max_nodes, 256), (unsigned)net->n_curves), 256, 2 * net->K * 4, st>>>(
+        k_synth<<<dim3((unsigned)mh_grid(net->max_nodes, 32), (unsigned)net->n_curves), 256, 2 * net->K * 4, st>>>(
             net->yout.p, net->tw.p, net->d_nn.p, net->d_off.p, net->K, r0, scal, net->gy, b->warm_dir.p);
         MH_LAUNCHED(ctx);
     }
