@@ -450,32 +450,6 @@ __global__ void k_sum_partials(const double* __restrict__ part, int nsplit, int6
     out[t] = pref * s;
 }
 
-// Density on the fine grid times |y'| h_f in binary32 (coefficients given in binary32).
-__global__ void k_fine_density32(const float* __restrict__ sc, const double* __restrict__ fg,
-                                 const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
-                                 const int64_t* __restrict__ foff, int ncurves, int64_t nfine, float* wf) {
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= nfine) return;
-    int k = 0;
-    while (k + 1 < ncurves && g >= foff[k + 1]) ++k;
-    const int N = nn[k];
-    const int NF = UPSAMPLE * N;
-    const int f = (int)(g - foff[k]);
-    const float* c = sc + 2 * coef_base(off, k);
-    float v = c[0];
-    for (int m = 1; m < N / 2; ++m) {
-        const int r = (int)(((int64_t)m * f) % NF);
-        float sn, cs;
-        sincospif(2.0f * (float)r / (float)NF, &sn, &cs);
-        v += 2.f * (c[2 * m] * cs - c[2 * m + 1] * sn);
-    }
-    {
-        const int r = (int)(((int64_t)(N / 2) * f) % NF);
-        v += c[N] * cospif(2.0f * (float)r / (float)NF);
-    }
-    wf[g] = v * (float)(fg[6 * g + 4] * fg[6 * g + 5]);
-}
-
 // Upsampled rule in binary32, one block per (target, curve) pair: the warps share the
 // fine-node chunks (MH_TILE nodes, binary64 chunk centres); block reduction in fixed order.
 __global__ void k_dlp_fine32_blk(const double* __restrict__ xy, const int32_t* __restrict__ ptgt,
@@ -664,6 +638,143 @@ __global__ void k_update_x(const double* __restrict__ V, const double* __restric
     }
 }
 
+// ---- fused Arnoldi step: classical Gram-Schmidt twice over row slices of ARN_ROWS rows ----
+// Every reduction runs in a fixed order (slice partials, then the slices in index order),
+// so the iteration is deterministic.
+constexpr int ARN_ROWS = 64;
+
+// P[s k1 + i] = sum over slice s of V_i[e] w[e], i < k1 (a warp per i).
+__global__ void __launch_bounds__(256) k_arn_dots(const double* __restrict__ V, const double* __restrict__ w,
+                                                  int64_t n, int k1, double* __restrict__ P) {
+    const int s = blockIdx.x;
+    const int64_t r0 = (int64_t)s * ARN_ROWS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t e0 = r0 + lane, e1 = r0 + lane + 32;
+    const double w0 = e0 < n ? w[e0] : 0.0, w1 = e1 < n ? w[e1] : 0.0;
+    for (int i = warp; i < k1; i += 8) {
+        const double* v = V + (int64_t)i * n;
+        double a = 0.0;
+        if (e0 < n) a = v[e0] * w0;
+        if (e1 < n) a = fma(v[e1], w1, a);
+        a = warp_sum(a);
+        if (lane == 0) P[(int64_t)s * k1 + i] = a;
+    }
+}
+
+// h_i = sum_s Pin[s k1 + i]; w -= sum_i h_i V_i on the slice; then the partial dots of the
+// new w (Pdots) or its partial squared norm (Pnorm).  Block 0 stores h in hout.
+__global__ void __launch_bounds__(256) k_arn_update(const double* __restrict__ V, double* __restrict__ w, int64_t n,
+                                                    int k1, const double* __restrict__ Pin, int S,
+                                                    double* __restrict__ Pdots, double* __restrict__ Pnorm,
+                                                    double* __restrict__ hout) {
+    extern __shared__ double sh[];      // h[k1], then the slice of w
+    double* h = sh;
+    double* wsl = sh + k1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < k1; i += 8) {      // a warp per coefficient, lanes over the slices
+        double a = 0.0;
+        for (int q = lane; q < S; q += 32) a += Pin[(int64_t)q * k1 + i];
+        a = warp_sum(a);
+        if (lane == 0) {
+            h[i] = a;
+            if (blockIdx.x == 0) hout[i] = a;
+        }
+    }
+    __syncthreads();
+    const int s = blockIdx.x;
+    const int64_t r0 = (int64_t)s * ARN_ROWS;
+    if (threadIdx.x < ARN_ROWS) {
+        const int64_t e = r0 + threadIdx.x;
+        double a = 0.0;
+        if (e < n) {
+            a = w[e];
+            for (int i = 0; i < k1; ++i) a = fma(-h[i], V[(int64_t)i * n + e], a);
+            w[e] = a;
+        }
+        wsl[threadIdx.x] = a;
+    }
+    __syncthreads();
+    if (Pdots) {
+        const int64_t e0 = r0 + lane, e1 = r0 + lane + 32;
+        for (int i = warp; i < k1; i += 8) {
+            const double* v = V + (int64_t)i * n;
+            double a = 0.0;
+            if (e0 < n) a = v[e0] * wsl[lane];
+            if (e1 < n) a = fma(v[e1], wsl[lane + 32], a);
+            a = warp_sum(a);
+            if (lane == 0) Pdots[(int64_t)s * k1 + i] = a;
+        }
+    } else if (warp == 0) {
+        double a = fma(wsl[lane], wsl[lane], wsl[lane + 32] * wsl[lane + 32]);
+        a = warp_sum(a);
+        if (lane == 0) Pnorm[s] = a;
+    }
+}
+
+// ||w|| from the partial norms; v_{k+1} = w / ||w|| (and its binary32 copy when vnext32 is
+// given).  Block 0 forms column k of H (h1 + h2, ||w||), applies the previous Givens
+// rotations, forms rotation k, updates g and stores |g_{k+1}| in small[0].
+__global__ void __launch_bounds__(256) k_arn_finish(const double* __restrict__ w, int64_t n,
+                                                    const double* __restrict__ Pn, int S, int k,
+                                                    const double* __restrict__ h1, const double* __restrict__ h2,
+                                                    double* H, int ldh, double* cs, double* sn, double* g,
+                                                    double* small, double* __restrict__ vnext,
+                                                    float* __restrict__ vnext32) {
+    __shared__ double nrm;
+    if (threadIdx.x < 32) {
+        double a = 0.0;
+        for (int q = threadIdx.x; q < S; q += 32) a += Pn[q];
+        a = warp_sum(a);
+        if (threadIdx.x == 0) nrm = sqrt(a);
+    }
+    __syncthreads();
+    const double s = nrm;
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    const int64_t r0 = (int64_t)blockIdx.x * ARN_ROWS;
+    if (threadIdx.x < ARN_ROWS) {
+        const int64_t e = r0 + threadIdx.x;
+        if (e < n) {
+            const double v = w[e] * inv;
+            vnext[e] = v;
+            if (vnext32) vnext32[e] = (float)v;
+        }
+    }
+    if (blockIdx.x != 0) return;
+    // column k and the previous rotations staged in shared memory, then one thread rotates
+    extern __shared__ double gsh[];      // col[k + 2], cs[k], sn[k]
+    double* col = gsh;
+    double* c_s = gsh + k + 2;
+    double* s_s = c_s + k;
+    for (int i = threadIdx.x; i <= k; i += blockDim.x) col[i] = h1[i] + h2[i];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        c_s[i] = cs[i];
+        s_s[i] = sn[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        col[k + 1] = s;
+        for (int i = 0; i < k; ++i) {
+            const double t = c_s[i] * col[i] + s_s[i] * col[i + 1];
+            col[i + 1] = -s_s[i] * col[i] + c_s[i] * col[i + 1];
+            col[i] = t;
+        }
+        const double a = col[k], b = col[k + 1];
+        const double den = hypot(a, b);
+        const double c = den > 0 ? a / den : 1.0, sv = den > 0 ? b / den : 0.0;
+        cs[k] = c;
+        sn[k] = sv;
+        col[k] = den;
+        col[k + 1] = 0.0;
+        const double gk = g[k];
+        g[k + 1] = -sv * gk;
+        g[k] = c * gk;
+        small[0] = fabs(-sv * gk);
+    }
+    __syncthreads();
+    double* hc = H + (int64_t)k * ldh;
+    for (int i = threadIdx.x; i <= k + 1; i += blockDim.x) hc[i] = col[i];
+}
+
 // r = b - r (in place on r), v0 = r / ||r|| later
 __global__ void k_sub_from(const double* __restrict__ b, double* r, int64_t n) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -823,10 +934,14 @@ __global__ void k_fourier_scalar(const double* __restrict__ v, const int32_t* __
     const double* p = v + off[k];
     const double2* t = tw + off[k];
     double re = 0, im = 0;
+    const int step = (int)(((int64_t)m * blockDim.x) % N);   // twiddle index m n mod N, advanced per stride
+    int r = (int)(((int64_t)m * threadIdx.x) % N);
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const double2 c = t[(int)(((int64_t)m * n) % N)];
+        const double2 c = t[r];
         re = fma(p[n], c.x, re);
         im = fma(-p[n], c.y, im);
+        r += step;
+        if (r >= N) r -= N;
     }
     re = block_sum<128>(re);
     im = block_sum<128>(im);
@@ -849,26 +964,70 @@ __global__ void k_twiddles(const int32_t* __restrict__ nn, const int32_t* __rest
     half[j] = make_double2(c, s);
 }
 
-// Density on the fine grid times |y'| h_f (quadrature weight folded in).
-__global__ void k_fine_density(const double* __restrict__ sc, const double* __restrict__ fg,
-                               const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
-                               const int64_t* __restrict__ foff, int ncurves, int64_t nfine, double* wf) {
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= nfine) return;
+// Fine-grid (16x) density by sub-offset: with f = 16 j + s,
+//   p(t_f) = sum_m C_m^{(s)} e^{2 pi i m j / N},  C_m^{(s)} = w_m c_m e^{2 pi i m s / (16 N)}
+// (w_0 = 1, w_m = 2 for 0 < m < N/2, the Nyquist term real with w = 1), real part.
+// k_fine_coef writes C[(base_k + m) * 16 + s] with exact binary64 phases.
+template <typename T2>
+__global__ void k_fine_coef(const double* __restrict__ sc, const int32_t* __restrict__ nn,
+                            const int32_t* __restrict__ off, int ncurves, int64_t nmodes, T2* __restrict__ cp) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nmodes * UPSAMPLE) return;
+    const int64_t g = e / UPSAMPLE;
+    const int sub = (int)(e - g * UPSAMPLE);
     int k = 0;
-    while (k + 1 < ncurves && g >= foff[k + 1]) ++k;
+    while (k + 1 < ncurves && g >= coef_base(off, k + 1)) ++k;
     const int N = nn[k];
-    const int NF = UPSAMPLE * N;
-    const int f = (int)(g - foff[k]);
-    const double* c = sc + 2 * coef_base(off, k);
-    double v = 0, d1 = 0, d2 = 0;
-    for (int m = 0; m <= N / 2; ++m) {
-        int r = (int)(((int64_t)m * f) % NF);
-        double s, co;
-        sincospi(2.0 * r / NF, &s, &co);
-        mode_acc(m, N, c[2 * m], c[2 * m + 1], s, co, v, d1, d2);
+    const int m = (int)(g - coef_base(off, k));
+    double re = sc[2 * g], im = sc[2 * g + 1];
+    if (2 * m == N) im = 0.0;
+    const double w = (m == 0 || 2 * m == N) ? 1.0 : 2.0;
+    double sn, cs;
+    sincospi(2.0 * (double)(m * sub) / (double)(UPSAMPLE * N), &sn, &cs);
+    T2 out;
+    out.x = w * (re * cs - im * sn);
+    out.y = w * (re * sn + im * cs);
+    cp[e] = out;
+}
+
+// Block = (16 coarse indices j of curve blockIdx.y) x (16 sub-offsets s); the coarse twiddles
+// e^{2 pi i r / N} sit in shared memory (a warp reads two of them per mode: broadcast), the
+// coefficients C_m^{(s)} are read as 16 consecutive complex values per mode (coalesced).
+template <typename T, typename T2>
+__global__ void __launch_bounds__(256) k_fine_density_s(const T2* __restrict__ cp, const double2* __restrict__ tw,
+                                                        const double* __restrict__ fg, const int32_t* __restrict__ nn,
+                                                        const int32_t* __restrict__ off,
+                                                        const int64_t* __restrict__ foff, T* __restrict__ wf) {
+    extern __shared__ unsigned char smem_raw[];
+    T2* tn = reinterpret_cast<T2*>(smem_raw);
+    const int k = blockIdx.y;
+    const int N = nn[k];
+    const int j0 = blockIdx.x * 16;
+    if (j0 >= N) return;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+        const double2 t = tw[off[k] + r];
+        T2 v;
+        v.x = (T)t.x;
+        v.y = (T)t.y;
+        tn[r] = v;
     }
-    wf[g] = v * fg[6 * g + 4] * fg[6 * g + 5];
+    __syncthreads();
+    const int sub = threadIdx.x & 15, j = j0 + (threadIdx.x >> 4);
+    if (j >= N) return;
+    const T2* c = cp + coef_base(off, k) * UPSAMPLE + sub;
+    T acc = 0;
+    int r = 0;
+#pragma unroll 8
+    for (int m = 0; m <= N / 2; ++m) {
+        const T2 a = __ldg(c + (int64_t)m * UPSAMPLE);
+        const T2 t = tn[r];
+        acc = fma(a.x, t.x, acc);
+        acc = fma(-a.y, t.y, acc);
+        r += j;
+        if (r >= N) r -= N;
+    }
+    const int64_t g = foff[k] + (int64_t)UPSAMPLE * j + sub;
+    wf[g] = (T)((double)acc * fg[6 * g + 4] * fg[6 * g + 5]);
 }
 
 // Coarse trapezoid sum over all curves not flagged fine for the target:
@@ -1249,6 +1408,7 @@ static mh_status gmres_core(mh_ctx* ctx, mh_boundary* bd, gmres_ws& ws, const do
     cudaStream_t st = ctx->stream;
     const int ew = mh_grid(n, 256) < 152 * 4 ? mh_grid(n, 256) : 152 * 4;
     const int ldh = max_iter + 1;
+    if (prec == MH_PREC_MIXED) MH_TRY(ensure_fp32(ctx, bd));
     // r = b - A x (or the caller's residual of x)
     if (r0) {
         MH_CUDA(ctx, cudaMemcpyAsync(ws.w.p, r0, n * 8, cudaMemcpyDeviceToDevice, st));
@@ -1272,24 +1432,34 @@ static mh_status gmres_core(mh_ctx* ctx, mh_boundary* bd, gmres_ws& ws, const do
     // reach the tolerance (iterations between reads are queued without host round trips).
     int next_check = 1, k_prev = 0;
     double res_prev = beta;
+    const bool mixed = prec == MH_PREC_MIXED;
+    const int S = (int)((n + ARN_ROWS - 1) / ARN_ROWS);
+    if (mixed) {
+        k_to_float_vec<<<mh_grid(n, 256), 256, 0, st>>>(ws.V.p, ws.v32.p, n);
+        MH_LAUNCHED(ctx);
+    }
     for (; k < max_iter; ++k) {
-        double* vk = ws.V.p + (int64_t)k * n;
-        MH_TRY(bie_apply(ctx, bd, vk, ws.w.p, prec));
-        // classical Gram-Schmidt, twice
-        k_multidot<<<k + 1, 256, 0, st>>>(ws.V.p, ws.w.p, n, ws.h1.p);
+        const int k1 = k + 1;
+        {   // w = A v_k
+            const double* vk = ws.V.p + (int64_t)k * n;
+            prof_scope ps(ctx, "bie_gemv", 2.0 * n * n, mixed ? 4.0 * n * n + 12.0 * n : 8.0 * n * n + 16.0 * n);
+            if (mixed)
+                k_gemv32<<<gemv_blocks(n), 256, 0, st>>>(bd->op.A32.p, ws.v32.p, ws.w.p, n);
+            else
+                k_gemv64<<<gemv_blocks(n), 256, 0, st>>>(bd->op.A64.p, vk, ws.w.p, n);
+            MH_LAUNCHED(ctx);
+        }
+        // classical Gram-Schmidt twice, normalisation and the Givens update (four launches)
+        const size_t shm = (size_t)(k1 + ARN_ROWS) * sizeof(double);
+        k_arn_dots<<<S, 256, 0, st>>>(ws.V.p, ws.w.p, n, k1, ws.P1.p);
         MH_LAUNCHED(ctx);
-        k_multiaxpy<<<ew, 256, 0, st>>>(ws.V.p, ws.h1.p, k + 1, n, ws.w.p);
+        k_arn_update<<<S, 256, shm, st>>>(ws.V.p, ws.w.p, n, k1, ws.P1.p, S, ws.P2.p, nullptr, ws.h1.p);
         MH_LAUNCHED(ctx);
-        k_multidot<<<k + 1, 256, 0, st>>>(ws.V.p, ws.w.p, n, ws.h2.p);
+        k_arn_update<<<S, 256, shm, st>>>(ws.V.p, ws.w.p, n, k1, ws.P2.p, S, nullptr, ws.Pn.p, ws.h2.p);
         MH_LAUNCHED(ctx);
-        k_multiaxpy<<<ew, 256, 0, st>>>(ws.V.p, ws.h2.p, k + 1, n, ws.w.p);
-        MH_LAUNCHED(ctx);
-        k_norm<<<1, 1024, 0, st>>>(ws.w.p, n, ws.small.p + 1);
-        MH_LAUNCHED(ctx);
-        k_finish_column<<<ew, 256, 0, st>>>(ws.h1.p, ws.h2.p, ws.small.p + 1, k, ws.H.p + (int64_t)k * ldh, ws.w.p,
-                                            ws.V.p + (int64_t)(k + 1) * n, n);
-        MH_LAUNCHED(ctx);
-        k_givens<<<1, 1, 0, st>>>(ws.H.p, ldh, k, ws.cs.p, ws.sn.p, ws.g.p, ws.small.p);
+        k_arn_finish<<<S, 256, (size_t)(3 * k + 2) * sizeof(double), st>>>(ws.w.p, n, ws.Pn.p, S, k, ws.h1.p,
+                                                                            ws.h2.p, ws.H.p, ldh, ws.cs.p, ws.sn.p,
+                                        ws.g.p, ws.small.p, ws.V.p + (int64_t)k1 * n, mixed ? ws.v32.p : nullptr);
         MH_LAUNCHED(ctx);
         if (k + 1 < next_check && k + 1 < max_iter) continue;
         MH_CUDA(ctx, cudaMemcpyAsync(&res, ws.small.p, 8, cudaMemcpyDeviceToHost, st));
@@ -1337,6 +1507,11 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
         MH_ALLOC(ctx, ws.w, n);
         MH_ALLOC(ctx, ws.r, n);
         MH_ALLOC(ctx, ws.dx, n);
+        const int64_t S = (n + ARN_ROWS - 1) / ARN_ROWS;
+        MH_ALLOC(ctx, ws.P1, S * (max_iter + 1));
+        MH_ALLOC(ctx, ws.P2, S * (max_iter + 1));
+        MH_ALLOC(ctx, ws.Pn, S);
+        MH_ALLOC(ctx, ws.v32, n);
         ws.m = max_iter;
         ws.n = n;
     }
@@ -1530,6 +1705,9 @@ static mh_status prep_mixed(mh_ctx* ctx, mh_boundary* b) {
     return MH_OK;
 }
 
+static mh_status fine_density(mh_ctx* ctx, mh_boundary* b, const double* sc, mh_precision prec, float* wf32,
+                              double* wf64);
+
 mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* tg, const double* sigma,
                        double* out, mh_precision prec) {
     cudaStream_t st = ctx->stream;
@@ -1556,13 +1734,7 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
             k_fourier_scalar<<<(unsigned)nmodes, 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->tw.p, b->n_curves,
                                                                nmodes, sc.p);
             MH_LAUNCHED(ctx);
-            float* sc32 = reinterpret_cast<float*>(tg->wf.p);   // 2*nmodes floats fit in the binary64 buffer
-            k_to_float_vec<<<mh_grid(2 * nmodes, 256), 256, 0, st>>>(sc.p, sc32, 2 * nmodes);
-            MH_LAUNCHED(ctx);
-            k_fine_density32<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(sc32, b->fine_geo.p, b->d_nn.p, b->d_off.p,
-                                                                      b->d_fine_off.p, b->n_curves, b->n_fine,
-                                                                      b->wf32.p);
-            MH_LAUNCHED(ctx);
+            MH_TRY(fine_density(ctx, b, sc.p, MH_PREC_MIXED, b->wf32.p, nullptr));
             prof_scope ps(ctx, "dlp_fine", DL_FLOPS * (tg->fine_nodes_main + tg->fine_nodes_aux), 24.0 * b->n_fine);
             k_dlp_fine32<<<mh_grid(tg->n_pairs * 32, 256), 256, 0, st>>>(
                 tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p, tg->n_pairs, b->fine32.p, b->wf32.p, b->d_fine_off.p,
@@ -1581,9 +1753,7 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
             k_fourier_scalar<<<(unsigned)nmodes, 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->tw.p, b->n_curves,
                                                                nmodes, sc.p);
             MH_LAUNCHED(ctx);
-            k_fine_density<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(sc.p, b->fine_geo.p, b->d_nn.p, b->d_off.p,
-                                                                     b->d_fine_off.p, b->n_curves, b->n_fine, wf.p);
-            MH_LAUNCHED(ctx);
+            MH_TRY(fine_density(ctx, b, sc.p, MH_PREC_FP64, nullptr, wf.p));
             prof_scope ps(ctx, "dlp_fine", DL_FLOPS * (tg->fine_nodes_main + tg->fine_nodes_aux), 24.0 * b->n_fine);
             k_dlp_fine<<<mh_grid(tg->n_pairs * 32, 256), 256, 0, st>>>(tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p,
                                                                        tg->n_pairs, b->fine_geo.p, wf.p,
@@ -1607,12 +1777,38 @@ __global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, int64
     if (i < n) b[i] = (double)a[i];
 }
 
+// Density times |y'| h_f on the 16x fine grid from the density's Fourier coefficients sc
+// (binary64): into wf32 (mixed) or wf64 (binary64).
+static mh_status fine_density(mh_ctx* ctx, mh_boundary* b, const double* sc, mh_precision prec, float* wf32,
+                              double* wf64) {
+    cudaStream_t st = ctx->stream;
+    const int64_t nmodes = b->n / 2 + b->n_curves;
+    const int max_n = *std::max_element(b->n_nodes.begin(), b->n_nodes.end());
+    const dim3 grid((unsigned)((max_n + 15) / 16), (unsigned)b->n_curves);
+    if (prec == MH_PREC_MIXED) {
+        if (!b->fcp32.p) MH_ALLOC(ctx, b->fcp32, nmodes * UPSAMPLE);
+        k_fine_coef<float2><<<mh_grid(nmodes * UPSAMPLE, 256), 256, 0, st>>>(sc, b->d_nn.p, b->d_off.p, b->n_curves,
+                                                                             nmodes, b->fcp32.p);
+        MH_LAUNCHED(ctx);
+        k_fine_density_s<float, float2><<<grid, 256, max_n * sizeof(float2), st>>>(
+            b->fcp32.p, b->tw.p, b->fine_geo.p, b->d_nn.p, b->d_off.p, b->d_fine_off.p, wf32);
+    } else {
+        if (!b->fcp64.p) MH_ALLOC(ctx, b->fcp64, nmodes * UPSAMPLE);
+        k_fine_coef<double2><<<mh_grid(nmodes * UPSAMPLE, 256), 256, 0, st>>>(sc, b->d_nn.p, b->d_off.p, b->n_curves,
+                                                                              nmodes, b->fcp64.p);
+        MH_LAUNCHED(ctx);
+        k_fine_density_s<double, double2><<<grid, 256, max_n * sizeof(double2), st>>>(
+            b->fcp64.p, b->tw.p, b->fine_geo.p, b->d_nn.p, b->d_off.p, b->d_fine_off.p, wf64);
+    }
+    MH_LAUNCHED(ctx);
+    return MH_OK;
+}
+
 mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_precision prec) {
     cudaStream_t st = ctx->stream;
     const int64_t nmodes = b->n / 2 + b->n_curves;
     if (!b->sc64.p) {
         MH_ALLOC(ctx, b->sc64, 2 * nmodes);
-        MH_ALLOC(ctx, b->sc32, 2 * nmodes);
         MH_ALLOC(ctx, b->wf64, b->n_fine);
     }
     k_fourier_scalar<<<(unsigned)nmodes, 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->tw.p, b->n_curves, nmodes,
@@ -1620,17 +1816,11 @@ mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_
     MH_LAUNCHED(ctx);
     if (prec == MH_PREC_MIXED) {
         MH_TRY(prep_mixed(ctx, b));
-        k_to_float_vec<<<mh_grid(2 * nmodes, 256), 256, 0, st>>>(b->sc64.p, b->sc32.p, 2 * nmodes);
-        MH_LAUNCHED(ctx);
-        k_fine_density32<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(b->sc32.p, b->fine_geo.p, b->d_nn.p, b->d_off.p,
-                                                                  b->d_fine_off.p, b->n_curves, b->n_fine, b->wf32.p);
-        MH_LAUNCHED(ctx);
+        MH_TRY(fine_density(ctx, b, b->sc64.p, MH_PREC_MIXED, b->wf32.p, nullptr));
         k_f2d<<<mh_grid(b->n_fine, 256), 256, 0, st>>>(b->wf32.p, b->wf64.p, b->n_fine);
         MH_LAUNCHED(ctx);
     } else {
-        k_fine_density<<<mh_grid(b->n_fine, 128), 128, 0, st>>>(b->sc64.p, b->fine_geo.p, b->d_nn.p, b->d_off.p,
-                                                                 b->d_fine_off.p, b->n_curves, b->n_fine, b->wf64.p);
-        MH_LAUNCHED(ctx);
+        MH_TRY(fine_density(ctx, b, b->sc64.p, MH_PREC_FP64, nullptr, b->wf64.p));
     }
     return MH_OK;
 }

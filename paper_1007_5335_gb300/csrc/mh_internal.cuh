@@ -97,6 +97,8 @@ struct dbuf {
 // GMRES workspace (kept by the boundary so that repeated solves allocate nothing).
 struct gmres_ws {
     dbuf<double> V, H, cs, sn, g, y, h1, h2, small, w, r, dx;
+    dbuf<double> P1, P2, Pn;             // per-slice partial dot products / squared norms
+    dbuf<float> v32;                     // binary32 copy of the newest Krylov vector
     int m = 0;
     int64_t n = 0;
 };
@@ -135,8 +137,9 @@ struct mh_boundary {
     dbuf<double2> tile_c, fchunk_c;
     dbuf<float> w32, wf32, x32;          // per call: weights, fine weights, GEMV input
     dbuf<double> sc64, wf64;             // per call: density Fourier coefficients, fine weights
-    dbuf<float> sc32;
     dbuf<double> warm_dir, warm_w, warm_scal;   // warm-start direction, its image, scalars
+    dbuf<float2> fcp32;                  // fine-grid coefficients by sub-offset (binary32)
+    dbuf<double2> fcp64;                 // (binary64)
 };
 
 #define MH_TILE 128

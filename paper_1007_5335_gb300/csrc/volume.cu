@@ -227,13 +227,37 @@ __global__ void k_near_tables(const NearCfg* __restrict__ cfg, int q, const doub
     if (t < qq) out[((int64_t)c * qq + i) * qq + t] = acc;
 }
 
+// Copies src[0..n) to shared memory at row-major position (e / cols, e % cols), leading
+// dimension ld, with U independent loads in flight per thread (a load-then-store loop would
+// wait on every global load in turn).
+template <typename TD, typename TS, int U = 8>
+__device__ __forceinline__ void stage_rows(TD* dst, const TS* __restrict__ src, int n, int cols, int ld) {
+    for (int e0 = threadIdx.x; e0 < n; e0 += U * blockDim.x) {
+        TS v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = e < n ? src[e] : TS(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < n) dst[(e / cols) * ld + (e % cols)] = (TD)v[u];
+        }
+    }
+}
+
 // Batched contraction: each block applies one operator (R x C, row-major) to up to CHUNK
 // source vectors gathered from `vec` and writes the products to temp[task][R].
+// With task_dst given (phases where every destination has exactly one task and sources
+// and destinations do not overlap) the product goes straight to vec[task_dst + r]
+// (added when accumulate is set).
 template <typename TOP>
 __global__ void k_apply(const TOP* __restrict__ ops, const int64_t* __restrict__ op_off,
                         const int32_t* __restrict__ op_C, const int32_t* __restrict__ chunk_op,
                         const int32_t* __restrict__ chunk_t0, const int64_t* __restrict__ task_src,
-                        const double* __restrict__ vec, int R, double* __restrict__ temp) {
+                        const double* vec, int R, double* __restrict__ temp, const int64_t* __restrict__ task_dst,
+                        int accumulate, double* vec_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TOP* sA = reinterpret_cast<TOP*>(smem_raw);
     const int ch = blockIdx.x;
@@ -244,10 +268,19 @@ __global__ void k_apply(const TOP* __restrict__ ops, const int64_t* __restrict__
     const int lda = C + 1;
     TOP* sX = sA + R * lda;
     const TOP* A = ops + op_off[op];
-    for (int e = threadIdx.x; e < R * C; e += blockDim.x) sA[(e / C) * lda + (e % C)] = A[e];
-    for (int e = threadIdx.x; e < nt * C; e += blockDim.x) {
-        const int tt = e / C, cc = e % C;
-        sX[tt * lda + cc] = (TOP)vec[task_src[t0 + tt] + cc];
+    stage_rows<TOP, TOP>(sA, A, R * C, C, lda);
+    for (int e0 = threadIdx.x; e0 < nt * C; e0 += 4 * blockDim.x) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = e < nt * C ? vec[task_src[t0 + e / C] + e % C] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < nt * C) sX[(e / C) * lda + e % C] = (TOP)v[u];
+        }
     }
     __syncthreads();
     for (int o = threadIdx.x; o < nt * R; o += blockDim.x) {
@@ -256,9 +289,149 @@ __global__ void k_apply(const TOP* __restrict__ ops, const int64_t* __restrict__
         const TOP* x = sX + tt * lda;
         TOP acc = 0;
         for (int cc = 0; cc < C; ++cc) acc += a[cc] * x[cc];
-        temp[(int64_t)(t0 + tt) * R + r] = (double)acc;
+        if (task_dst) {
+            double* y = vec_out + task_dst[t0 + tt] + r;
+            *y = accumulate ? *y + (double)acc : (double)acc;
+        } else {
+            temp[(int64_t)(t0 + tt) * R + r] = (double)acc;
+        }
     }
 }
+
+// ---- M2M / L2L of one tree level, parent-centric (no reduction pass) ----
+// A block takes LEVEL_PB parents.  G child-position operators (P x P, row-major) are resident
+// in shared memory at a time (G = 4 when they fit, else 1; leading dimension P + 1); thread
+// (g, r) owns row r of operator c0 + g for all LEVEL_PB parents (LEVEL_PB independent
+// accumulation chains).
+constexpr int LEVEL_PB = 16;
+struct Off4 {
+    int64_t v[4];   // offsets of the four child-position operators
+};
+
+// M[parent] = sum over the children c = 0..3 of T_c M[child_c]; with G = 4 the four partial
+// sums are combined in the order c = 0, 1, 2, 3.
+template <typename TOP>
+__global__ void __launch_bounds__(256) k_m2m_level(const TOP* __restrict__ ops, Off4 oo,
+                                                   const int32_t* __restrict__ par, const int32_t* __restrict__ child,
+                                                   int64_t n_par, int P, int G, int64_t base, double* vec) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lda = P + 1;
+    TOP* sA = reinterpret_cast<TOP*>(smem_raw);           // G x P x lda
+    TOP* sX = sA + G * P * lda;                            // LEVEL_PB x 4 x lda
+    TOP* red = sX + LEVEL_PB * 4 * lda;                    // G x LEVEL_PB x P (G > 1)
+    const int64_t p0 = (int64_t)blockIdx.x * LEVEL_PB;
+    const int np = (int)min((int64_t)LEVEL_PB, n_par - p0);
+    for (int e0 = threadIdx.x; e0 < LEVEL_PB * 4 * P; e0 += 4 * blockDim.x) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int pp = e / (4 * P), rem = e - pp * 4 * P, c = rem / P, cc = rem - c * P;
+            const int ch = (e < LEVEL_PB * 4 * P && pp < np) ? child[4 * (p0 + pp) + c] : -1;
+            v[u] = ch >= 0 ? vec[base + (int64_t)ch * P + cc] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= LEVEL_PB * 4 * P) break;
+            const int pp = e / (4 * P), rem = e - pp * 4 * P, c = rem / P, cc = rem - c * P;
+            sX[(pp * 4 + c) * lda + cc] = (TOP)v[u];
+        }
+    }
+    const int g = threadIdx.x / P, r = threadIdx.x - g * P;
+    TOP acc[LEVEL_PB];
+#pragma unroll
+    for (int pp = 0; pp < LEVEL_PB; ++pp) acc[pp] = 0;
+    for (int c0 = 0; c0 < 4; c0 += G) {
+        __syncthreads();
+        for (int gg = 0; gg < G; ++gg) stage_rows<TOP, TOP>(sA + gg * P * lda, ops + oo.v[c0 + gg], P * P, P, lda);
+        __syncthreads();
+        if (g < G) {
+            const int c = c0 + g;
+            const TOP* a = sA + (g * P + r) * lda;
+            for (int cc = 0; cc < P; ++cc) {
+                const TOP av = a[cc];
+#pragma unroll
+                for (int pp = 0; pp < LEVEL_PB; ++pp) acc[pp] += av * sX[(pp * 4 + c) * lda + cc];
+            }
+        }
+    }
+    if (G == 1) {
+        if (g == 0)
+#pragma unroll
+            for (int pp = 0; pp < LEVEL_PB; ++pp)
+                if (pp < np) vec[base + (int64_t)par[p0 + pp] * P + r] = (double)acc[pp];
+        return;
+    }
+    if (g < G)
+#pragma unroll
+        for (int pp = 0; pp < LEVEL_PB; ++pp) red[(g * LEVEL_PB + pp) * P + r] = acc[pp];
+    __syncthreads();
+    for (int o = threadIdx.x; o < np * P; o += blockDim.x) {
+        const int pp = o / P, rr = o - pp * P;
+        TOP t = red[pp * P + rr];
+        for (int gg = 1; gg < G; ++gg) t += red[(gg * LEVEL_PB + pp) * P + rr];
+        vec[base + (int64_t)par[p0 + pp] * P + rr] = (double)t;
+    }
+}
+
+// L[child_c] += T_c L[parent] for the children c of every parent.
+template <typename TOP>
+__global__ void __launch_bounds__(256) k_l2l_level(const TOP* __restrict__ ops, Off4 oo,
+                                                   const int32_t* __restrict__ par, const int32_t* __restrict__ child,
+                                                   int64_t n_par, int P, int G, int64_t base, double* vec) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lda = P + 1;
+    TOP* sA = reinterpret_cast<TOP*>(smem_raw);           // G x P x lda
+    TOP* sX = sA + G * P * lda;                            // LEVEL_PB x lda
+    const int64_t p0 = (int64_t)blockIdx.x * LEVEL_PB;
+    const int np = (int)min((int64_t)LEVEL_PB, n_par - p0);
+    for (int e0 = threadIdx.x; e0 < LEVEL_PB * P; e0 += 4 * blockDim.x) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int pp = e / P, cc = e - pp * P;
+            v[u] = (e < LEVEL_PB * P && pp < np) ? vec[base + (int64_t)par[p0 + pp] * P + cc] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= LEVEL_PB * P) break;
+            sX[(e / P) * lda + e % P] = (TOP)v[u];
+        }
+    }
+    const int g = threadIdx.x / P, r = threadIdx.x - g * P;
+    for (int c0 = 0; c0 < 4; c0 += G) {
+        __syncthreads();
+        for (int gg = 0; gg < G; ++gg) stage_rows<TOP, TOP>(sA + gg * P * lda, ops + oo.v[c0 + gg], P * P, P, lda);
+        __syncthreads();
+        if (g >= G) continue;
+        const int c = c0 + g;
+        TOP acc[LEVEL_PB];
+#pragma unroll
+        for (int pp = 0; pp < LEVEL_PB; ++pp) acc[pp] = 0;
+        const TOP* a = sA + (g * P + r) * lda;
+        for (int cc = 0; cc < P; ++cc) {
+            const TOP av = a[cc];
+#pragma unroll
+            for (int pp = 0; pp < LEVEL_PB; ++pp) acc[pp] += av * sX[pp * lda + cc];
+        }
+#pragma unroll
+        for (int pp = 0; pp < LEVEL_PB; ++pp) {
+            if (pp >= np) break;
+            const int ch = child[4 * (p0 + pp) + c];
+            if (ch >= 0) vec[base + (int64_t)ch * P + r] += (double)acc[pp];
+        }
+    }
+}
+
+// Shared memory of the level kernels for P and G (bytes, with TOP of size ts).
+inline size_t level_smem(int P, int G, size_t ts) {
+    return ((size_t)G * P * (P + 1) + (size_t)LEVEL_PB * 4 * (P + 1) + (G > 1 ? (size_t)G * LEVEL_PB * P : 0)) * ts;
+}
+// Operators resident at once: 4 when the threads and the shared memory allow it.
+inline int level_groups(int P, size_t ts) { return (4 * P <= 256 && level_smem(P, 4, ts) <= 200 * 1024) ? 4 : 1; }
 
 // Per destination (one warp each): vec[dst + r] = (acc ? vec : 0) + sum of its products.
 __global__ void k_reduce(const double* __restrict__ temp, int R, const int64_t* __restrict__ dst_off,
@@ -286,6 +459,8 @@ struct Task {
 struct Phase {
     int R = 0;
     bool accumulate = false;
+    bool direct = false;           // one task per destination: products written in place
+    dbuf<int64_t> task_dst;        // destination offset of every (sorted) task when direct
     double flops = 0, bytes = 0;   // per run: 2 R C per task; operators, sources, products, outputs
     int64_t n_tasks = 0, n_dst = 0, n_chunks = 0;
     int smem = 0;
@@ -304,6 +479,15 @@ struct OpPool {
         data.insert(data.end(), v, v + (size_t)r * c);
         return (int)off.size() - 1;
     }
+};
+
+// M2M / L2L of every level 2 <= l < L in parent-centric form (shared by the volume and the
+// double-layer passes: same tree, same operators at the same pool offsets).
+struct LevelChain {
+    int64_t n_par = 0;
+    int64_t m2m_off[4] = {0, 0, 0, 0}, l2l_off[4] = {0, 0, 0, 0};
+    double flops = 0, bytes = 0;
+    dbuf<int32_t> par, child;
 };
 
 struct DipData;
@@ -325,7 +509,7 @@ struct VolData {
     dbuf<int32_t> d_op_C;
     std::vector<int> op_C;
     std::unique_ptr<Phase> p2m, m2l, out;
-    std::vector<std::unique_ptr<Phase>> m2m, l2l;   // by level
+    std::vector<std::unique_ptr<LevelChain>> chain;   // by level
     int64_t temp_len = 0;
     int64_t n_near_tables = 0;
 };
@@ -369,6 +553,17 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
         dptr.push_back((int32_t)dtask.size());
     }
     ph->n_dst = (int64_t)doff.size();
+    // direct mode: a single task per destination and source / destination ranges apart
+    if (ph->n_dst == ph->n_tasks && ph->n_tasks > 0) {
+        int64_t smin = INT64_MAX, smax = 0, dmin = INT64_MAX, dmax = 0;
+        for (const Task& t : tasks) {
+            smin = std::min(smin, t.src);
+            smax = std::max(smax, t.src + op_C[t.op]);
+            dmin = std::min(dmin, t.dst);
+            dmax = std::max(dmax, t.dst + R);
+        }
+        ph->direct = smax <= dmin || dmax <= smin;
+    }
     ph->smem = (int)((R + CHUNK) * (maxC + 1) * sizeof(double));
     if (ph->smem > 160 * 1024)
         return mh_fail(ctx, MH_ERR_INVALID_ARG, "contraction operator too large for shared memory (%d x %d)", R, maxC);
@@ -389,6 +584,11 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
     MH_TRY(up32(ph->dst_task, dtask));
     MH_TRY(up64(ph->task_src, src));
     MH_TRY(up64(ph->dst_off, doff));
+    if (ph->direct) {
+        std::vector<int64_t> tdst(tasks.size());
+        for (size_t q = 0; q < order.size(); ++q) tdst[q] = tasks[order[q]].dst;
+        MH_TRY(up64(ph->task_dst, tdst));
+    }
     MH_CUDA(ctx, cudaStreamSynchronize(st));
     *temp_need = std::max<int64_t>(*temp_need, ph->n_tasks * R);
     return MH_OK;
@@ -400,13 +600,41 @@ mh_status run_phase_on(mh_ctx* ctx, const TOP* ops, const int64_t* op_off, const
     if (ph->n_tasks == 0) return MH_OK;
     const int smem = (int)(ph->smem / sizeof(double) * sizeof(TOP));
     prof_scope ps(ctx, region, ph->flops, ph->bytes + 8.0 * ph->R * ph->n_dst * (ph->accumulate ? 2 : 1));
-    k_apply<TOP><<<(unsigned)ph->n_chunks, 256, smem, ctx->stream>>>(ops, op_off, op_C, ph->chunk_op.p,
-                                                                     ph->chunk_t0.p, ph->task_src.p, vec, ph->R,
-                                                                     temp);
+    k_apply<TOP><<<(unsigned)ph->n_chunks, 256, smem, ctx->stream>>>(
+        ops, op_off, op_C, ph->chunk_op.p, ph->chunk_t0.p, ph->task_src.p, vec, ph->R, temp,
+        ph->direct ? ph->task_dst.p : nullptr, ph->accumulate ? 1 : 0, vec);
     MH_LAUNCHED(ctx);
-    k_reduce<<<mh_grid(ph->n_dst * 32, 256), 256, 0, ctx->stream>>>(temp, ph->R, ph->dst_off.p, ph->dst_ptr.p,
-                                                                    ph->dst_task.p, ph->n_dst, ph->accumulate, vec);
-    MH_LAUNCHED(ctx);
+    if (!ph->direct) {
+        k_reduce<<<mh_grid(ph->n_dst * 32, 256), 256, 0, ctx->stream>>>(temp, ph->R, ph->dst_off.p, ph->dst_ptr.p,
+                                                                        ph->dst_task.p, ph->n_dst, ph->accumulate,
+                                                                        vec);
+        MH_LAUNCHED(ctx);
+    }
+    return MH_OK;
+}
+
+inline Off4 offs4(const int64_t* o) { return Off4{{o[0], o[1], o[2], o[3]}}; }
+
+template <typename TOP>
+mh_status run_chain(mh_ctx* ctx, const std::vector<std::unique_ptr<LevelChain>>& chain, const TOP* ops, int P,
+                    int64_t m_base, int64_t l_base, double* vec, bool upward, const char* region) {
+    const int L = (int)chain.size();
+    const int G = level_groups(P, sizeof(TOP));
+    const size_t smem = level_smem(P, G, sizeof(TOP));
+    for (int step = 0; step < L; ++step) {
+        const int l = upward ? L - 1 - step : step;
+        const LevelChain* c = chain[l].get();
+        if (!c || c->n_par == 0) continue;
+        prof_scope ps(ctx, region, c->flops, c->bytes);
+        const unsigned grid = (unsigned)((c->n_par + LEVEL_PB - 1) / LEVEL_PB);
+        if (upward)
+            k_m2m_level<TOP><<<grid, 256, smem, ctx->stream>>>(ops, offs4(c->m2m_off), c->par.p,
+                                                                c->child.p, c->n_par, P, G, m_base, vec);
+        else
+            k_l2l_level<TOP><<<grid, 256, smem, ctx->stream>>>(ops, offs4(c->l2l_off), c->par.p,
+                                                                c->child.p, c->n_par, P, G, l_base, vec);
+        MH_LAUNCHED(ctx);
+    }
     return MH_OK;
 }
 
@@ -445,7 +673,7 @@ mh_status fetch_tree(mh_ctx* ctx, const mh_tree* t, HostTree* h) {
 mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V) {
     const int q = t->q, qq = q * q, P = 2 * p + 1, L = t->max_level;
     const double k = 1.0 / alpha, pref = 1.0 / (2.0 * MH_PI * alpha * alpha);
-    const double x0 = t->box[0], y0 = t->box[1], W = t->box[2];
+    const double W = t->box[2];
     V->alpha = alpha;
     V->p = p;
     V->P = P;
@@ -558,7 +786,6 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
     std::vector<NearCfg> near_cfg;
     std::vector<int> near_level;
     std::vector<Task> t_out, t_m2l, t_p2m;
-    std::vector<std::vector<Task>> t_m2m(L + 1), t_l2l(L + 1);
     // relative centre offset (source minus target) from integer coordinates
     auto rel = [&](int tb, int sb) {
         const int lt = lev(tb), ls = lev(sb), f = std::max(lt, ls);
@@ -692,21 +919,44 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
             t_m2l.push_back(Task{id, V->B_off + (int64_t)h.box_leaf[c] * qq, V->L_off + b * P});
         }
     }
-    // M2M / L2L tasks from the parent-child structure (children of internal boxes, level >= 2)
+    // M2M / L2L: the internal boxes of levels 2 <= l < L with their four children (parent-centric)
     {
         std::vector<int32_t> child(4 * nb);
         MH_CUDA(ctx, cudaMemcpyAsync(child.data(), t->box_child.p, 4 * nb * 4, cudaMemcpyDeviceToHost, ctx->stream));
         MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        std::vector<std::vector<int32_t>> par(L + 1), chl(L + 1);
+        std::vector<int64_t> nchild(L + 1, 0);
         for (int64_t b = 0; b < nb; ++b) {
             const int l = lev((int)b);
             if (h.box_leaf[b] >= 0 || l < 2 || l >= L) continue;
-            for (int c = 0; c < 4; ++c) {
-                const int ch = child[4 * b + c];
-                if (ch < 0) continue;
-                t_m2m[l].push_back(Task{op_m2m[l][c], V->M_off + (int64_t)ch * P, V->M_off + b * P});
-                t_l2l[l].push_back(Task{op_l2l[l][c], V->L_off + b * P, V->L_off + (int64_t)ch * P});
-            }
+            int cnt = 0;
+            for (int c = 0; c < 4; ++c) cnt += child[4 * b + c] >= 0;
+            if (!cnt) continue;
+            par[l].push_back((int32_t)b);
+            for (int c = 0; c < 4; ++c) chl[l].push_back(child[4 * b + c]);
+            nchild[l] += cnt;
         }
+        V->chain.clear();
+        V->chain.resize(L);
+        for (int l = 2; l < L; ++l) {
+            if (par[l].empty()) continue;
+            std::unique_ptr<LevelChain> c(new LevelChain());
+            c->n_par = (int64_t)par[l].size();
+            for (int q4 = 0; q4 < 4; ++q4) {
+                c->m2m_off[q4] = pool.off[op_m2m[l][q4]];
+                c->l2l_off[q4] = pool.off[op_l2l[l][q4]];
+            }
+            c->flops = 2.0 * P * P * nchild[l];
+            c->bytes = 8.0 * (4.0 * P * P + 2.0 * P * (nchild[l] + c->n_par));
+            MH_ALLOC(ctx, c->par, par[l].size());
+            MH_ALLOC(ctx, c->child, chl[l].size());
+            MH_CUDA(ctx, cudaMemcpyAsync(c->par.p, par[l].data(), par[l].size() * 4, cudaMemcpyHostToDevice,
+                                         ctx->stream));
+            MH_CUDA(ctx, cudaMemcpyAsync(c->child.p, chl[l].data(), chl[l].size() * 4, cudaMemcpyHostToDevice,
+                                         ctx->stream));
+            V->chain[l] = std::move(c);
+        }
+        MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     }
     // near tables on the device, appended to the pool
     const int nnear = (int)near_cfg.size();
@@ -766,16 +1016,6 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
     int64_t need = 1;
     V->p2m.reset(new Phase());
     MH_TRY(build_phase(ctx, t_p2m, P, false, V->op_C, V->p2m.get(), &need));
-    V->m2m.clear();
-    V->l2l.clear();
-    V->m2m.resize(L + 1);
-    V->l2l.resize(L + 1);
-    for (int l = 0; l <= L; ++l) {
-        V->m2m[l].reset(new Phase());
-        V->l2l[l].reset(new Phase());
-        MH_TRY(build_phase(ctx, t_m2m[l], P, false, V->op_C, V->m2m[l].get(), &need));
-        MH_TRY(build_phase(ctx, t_l2l[l], P, true, V->op_C, V->l2l[l].get(), &need));
-    }
     V->m2l.reset(new Phase());
     MH_TRY(build_phase(ctx, t_m2l, P, false, V->op_C, V->m2l.get(), &need));
     V->out.reset(new Phase());
@@ -789,6 +1029,13 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
     for (auto* ph : {V->p2m.get(), V->m2l.get(), V->out.get()}) maxs = std::max(maxs, ph->smem);
     MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
     MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    if (P > 256 || level_smem(P, 1, 8) > 200 * 1024)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "multipole order too large for the level kernels");
+    const int lsm64 = (int)level_smem(P, level_groups(P, 8), 8), lsm32 = (int)level_smem(P, level_groups(P, 4), 4);
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_m2m_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsm64));
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_m2m_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsm32));
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_l2l_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsm64));
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_l2l_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsm32));
     return MH_OK;
 }
 
@@ -935,7 +1182,6 @@ struct DipData {
     dbuf<int64_t> d_op_off;
     dbuf<int32_t> d_op_C;
     std::unique_ptr<Phase> p2m, m2l, out;
-    std::vector<std::unique_ptr<Phase>> m2m, l2l;
 };
 }  // namespace
 
@@ -996,7 +1242,6 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
     D->vec_len = D->DU_off + nl * qq;
     OpPool pool = V->pool_host;
     std::vector<Task> t_p2m, t_m2l, t_out;
-    std::vector<std::vector<Task>> t_m2m(L + 1), t_l2l(L + 1);
     std::vector<double> buf, Kb(p + 3), Ib(p + 3);
     auto set_row = [&](double* m, int cols, int col, int n, std::complex<double> v) {
         if (n == 0)
@@ -1108,21 +1353,6 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
             add_split(P, nc, buf, D->W_off + seg0[lc], D->DL_off + b * P, t_m2l);
         }
     }
-    {
-        std::vector<int32_t> child(4 * nb);
-        MH_CUDA(ctx, cudaMemcpyAsync(child.data(), t->box_child.p, 4 * nb * 4, cudaMemcpyDeviceToHost, ctx->stream));
-        MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        for (int64_t b = 0; b < nb; ++b) {
-            const int l = lev((int)b);
-            if (h.box_leaf[b] >= 0 || l < 2 || l >= L) continue;
-            for (int c = 0; c < 4; ++c) {
-                const int ch = child[4 * b + c];
-                if (ch < 0) continue;
-                t_m2m[l].push_back(Task{V->op_m2m[l][c], D->DM_off + (int64_t)ch * P, D->DM_off + b * P});
-                t_l2l[l].push_back(Task{V->op_l2l[l][c], D->DL_off + b * P, D->DL_off + (int64_t)ch * P});
-            }
-        }
-    }
     if (!near_blocks) {
         // CSR over target leaves (in leaf order) of the source leaves holding dipoles
         std::vector<std::vector<int32_t>> per(nl);
@@ -1205,14 +1435,6 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
     int64_t need = 1;
     D->p2m.reset(new Phase());
     MH_TRY(build_phase(ctx, t_p2m, P, false, opC, D->p2m.get(), &need));
-    D->m2m.resize(L + 1);
-    D->l2l.resize(L + 1);
-    for (int l = 0; l <= L; ++l) {
-        D->m2m[l].reset(new Phase());
-        D->l2l[l].reset(new Phase());
-        MH_TRY(build_phase(ctx, t_m2m[l], P, false, opC, D->m2m[l].get(), &need));
-        MH_TRY(build_phase(ctx, t_l2l[l], P, true, opC, D->l2l[l].get(), &need));
-    }
     D->m2l.reset(new Phase());
     MH_TRY(build_phase(ctx, t_m2l, P, false, opC, D->m2l.get(), &need));
     D->out.reset(new Phase());
@@ -1226,14 +1448,14 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
 }
 
 template <typename TOP>
-static mh_status dipole_run(mh_ctx* ctx, mh_tree* t, DipData* D, const TOP* ops) {
+static mh_status dipole_run(mh_ctx* ctx, VolData* V, DipData* D, const TOP* ops) {
     auto run = [&](const Phase* ph) {
         return run_phase_on<TOP>(ctx, ops, D->d_op_off.p, D->d_op_C.p, D->vec.p, D->temp.p, ph, "dlp_fmm_contract");
     };
     MH_TRY(run(D->p2m.get()));
-    for (int l = t->max_level - 1; l >= 2; --l) MH_TRY(run(D->m2m[l].get()));
+    MH_TRY(run_chain<TOP>(ctx, V->chain, ops, V->P, D->DM_off, D->DL_off, D->vec.p, true, "dlp_fmm_contract"));
     MH_TRY(run(D->m2l.get()));
-    for (int l = 2; l < t->max_level; ++l) MH_TRY(run(D->l2l[l].get()));
+    MH_TRY(run_chain<TOP>(ctx, V->chain, ops, V->P, D->DM_off, D->DL_off, D->vec.p, false, "dlp_fmm_contract"));
     MH_TRY(run(D->out.get()));
     return MH_OK;
 }
@@ -1249,9 +1471,9 @@ mh_status volume_dipole_apply(mh_ctx* ctx, mh_tree* t, const double* w_sorted, m
     MH_CUDA(ctx, cudaMemcpyAsync(D->vec.p + D->W_off, w_sorted, D->nd * 8, cudaMemcpyDeviceToDevice, st));
     if (!D->near_blocks) MH_CUDA(ctx, cudaMemsetAsync(D->vec.p + D->DU_off, 0, t->n_leaves * D->qq * 8, st));
     if (prec == MH_PREC_MIXED)
-        MH_TRY(dipole_run<float>(ctx, t, D, D->ops32.p));
+        MH_TRY(dipole_run<float>(ctx, V, D, D->ops32.p));
     else
-        MH_TRY(dipole_run<double>(ctx, t, D, D->ops64.p));
+        MH_TRY(dipole_run<double>(ctx, V, D, D->ops64.p));
     if (!D->near_blocks && D->n_active) {
         prof_scope ps2(ctx, "dlp_near", 68.0 * D->near_pairs, 24.0 * (double)D->nd);
         if (prec == MH_PREC_MIXED) {
@@ -1279,9 +1501,9 @@ void volume_free(mh_tree* t) {
 template <typename TOP>
 static mh_status volume_run(mh_ctx* ctx, mh_tree* t, VolData* V, const TOP* ops) {
     MH_TRY(run_phase(ctx, V, ops, V->p2m.get()));
-    for (int l = t->max_level - 1; l >= 2; --l) MH_TRY(run_phase(ctx, V, ops, V->m2m[l].get()));
+    MH_TRY(run_chain<TOP>(ctx, V->chain, ops, V->P, V->M_off, V->L_off, V->vec.p, true, "volume_contract"));
     MH_TRY(run_phase(ctx, V, ops, V->m2l.get()));
-    for (int l = 2; l < t->max_level; ++l) MH_TRY(run_phase(ctx, V, ops, V->l2l[l].get()));
+    MH_TRY(run_chain<TOP>(ctx, V->chain, ops, V->P, V->M_off, V->L_off, V->vec.p, false, "volume_contract"));
     MH_TRY(run_phase(ctx, V, ops, V->out.get()));
     return MH_OK;
 }
