@@ -343,6 +343,58 @@ mh_status mh_warm_start(mh_ctx* ctx, mh_boundary* bnd, double alpha, mh_net* net
 mh_status mh_problem_set_warm_start(mh_ctx* ctx, mh_problem* prob, mh_warm_mode mode, mh_net* net,
                                     mh_net_arith arith);
 
+/* ------------------------------------------------------------------------------------------
+ * Batched stepping and autotuning of independent problems.
+ *
+ * A batch holds n problems (each with its own tree, boundary and, if used, network).
+ * mh_batch_step advances all of them by one IMEX Euler step (Section 2) as one CUDA graph
+ * launch: the first call runs the step eagerly and records the graph (one branch per problem on
+ * its own stream, GMRES with a fixed schedule of device-gated kernels instead of host
+ * read-backs: mixed precision 3 binary64 refinement sweeps x 20 Arnoldi iterations, binary64 40
+ * iterations); later calls with the same arrays, tolerance and precision relaunch the graph.
+ * The step is in place: u_dev[i] is u^N on entry and u^{N+1} on return.  One host
+ * synchronisation per call reads the per-problem GMRES results into info_host[i].
+ * MH_ERR_NOT_CONVERGED if a problem did not reach gmres_tol within the schedule (its u is the
+ * last iterate's).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct mh_batch mh_batch;
+
+mh_status mh_batch_create(mh_ctx* ctx, int n, mh_problem* const* probs_host, mh_batch** out);
+mh_status mh_batch_destroy(mh_batch* batch);
+/* All pointer arrays are host arrays of n device pointers (N_D or N_Gamma doubles as in
+ * heat_step); b_ext is not supported (problems must use MH_EXT_CONST). */
+mh_status mh_batch_step(mh_ctx* ctx, mh_batch* batch, double* const* u_dev, const double* const* F_dev,
+                        const double* const* f_next_dev, double* const* sigma_dev, double gmres_tol,
+                        mh_precision prec, mh_step_info* info_host);
+/* Kernels launched by one graph launch of the batch (0 before the graph exists). */
+int64_t mh_batch_graph_kernels(const mh_batch* batch);
+
+/* Threads per block of the binary32 near-field double-layer kernel of prob's tree
+ * (128, 256 or 512; default 256): the tile of qq targets x threads/qq source groups. */
+mh_status mh_problem_set_near_tile(mh_ctx* ctx, mh_problem* prob, int threads);
+
+typedef struct {
+    int p;              /* multipole order */
+    int near_tile;      /* threads per block of the near-field kernel */
+    double rel_err;     /* relative L2 difference of u (nodes inside Omega) from the reference order */
+    double ms_per_step; /* median step time (CUDA events) */
+} mh_tune_entry;
+
+/* Autotuner of the multipole order and the near-field tile for one geometry and alpha.
+ * For every candidate p_cand[i] and the reference order p_ref = max(p_cand) + 8 it creates a
+ * problem on (tree, bnd, dt, IMEX Euler, ext_mode / ext_const_host), runs `steps` steps from
+ * u = 0 with forcing F_dev and boundary data f_dev (both fixed in time), precision prec and the
+ * previous-step GMRES start, and records the relative L2 difference of u^steps from the
+ * reference run over the nodes inside Omega and the median step time.  The chosen p is the
+ * fastest candidate with rel_err <= err_tol (else the most accurate); for it the near-field tile
+ * in {128, 256, 512} with the fastest step is chosen.  report_host (nullable) receives
+ * n_p + 3 entries: the candidates, then the chosen p with each tile.  The tree keeps the
+ * operators of the last problem built. */
+mh_status mh_autotune(mh_ctx* ctx, mh_tree* tree, mh_boundary* bnd, double dt, int ext_mode,
+                      const double* ext_const_host, const double* F_dev, const double* f_dev, int n_p,
+                      const int* p_cand, double err_tol, int steps, mh_precision prec, int* p_out,
+                      int* tile_out, mh_tune_entry* report_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -251,3 +251,62 @@ def warm_start_toy_data(n: int, d: int, rank: int, seed: int = 11):
     M = rng.standard_normal((d, d)) / math.sqrt(d)
     c = rng.standard_normal(d)
     return X.astype(np.float32), (X @ M.T + c).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------- batched problems
+def ellipse_nodes(center, a: float, b: float, angle: float, n: int, clockwise: bool) -> np.ndarray:
+    """Nodes of an ellipse with semi-axes a, b rotated by `angle`, shape (n, 2)."""
+    t = curve_params(n)
+    s = -1.0 if clockwise else 1.0
+    x, y = a * np.cos(t), s * b * np.sin(t)
+    c, sn = math.cos(angle), math.sin(angle)
+    return np.stack([center[0] + c * x - sn * y, center[1] + sn * x + c * y], axis=1)
+
+
+BATCH_SIZE = 64
+BATCH_SEED = 4
+
+
+def batch_problem(i: int, seed: int = BATCH_SEED, steps: int = 20, npc=None, refine_tol=None) -> Workload:
+    """Problem i of the batched workload: the unit disk minus 1-8 holes (starfish
+    r(t) = r0 (1 + 0.3 cos 5t) or rotated ellipses, each kind with probability 1/2), hole sizes
+    r0 ~ U[0.05, min(0.12, 0.36 / sqrt(holes))], centres by rejection sampling keeping a gap
+    >= 0.05 between the holes' bounding circles and from the outer circle; nodes per curve
+    32 * U{8..64} (256-2048); alpha^2 = dt log-uniform in [1e-4, 1e-2]; Gaussian-sum forcing
+    (seed 1000 + i); adaptive tree (8x8 nodes per leaf, levels 4-8) with the absolute
+    refinement tolerance 10^U[-10, -5] (16k to a few 100k volume nodes); f = 0, C_k = 0.
+    npc / refine_tol override the drawn values (smaller cases for tests)."""
+    rng = np.random.default_rng([seed, i])
+    n_holes = int(rng.integers(1, 9))
+    npc_drawn = 32 * int(rng.integers(8, 65))
+    refine_tol_override = refine_tol
+    npc = npc_drawn if npc is None else npc
+    alpha2 = 10.0 ** rng.uniform(-4.0, -2.0)
+    refine_tol = 10.0 ** rng.uniform(-10.0, -5.0)
+    r_hi = min(0.12, 0.36 / math.sqrt(n_holes))
+    holes, placed = [], []          # placed: (centre, bounding radius)
+    while len(holes) < n_holes:
+        kind = rng.integers(0, 2)
+        r0 = rng.uniform(0.05, r_hi)
+        if kind == 0:
+            extent = 1.3 * r0
+        else:
+            a, b = r0, r0 * rng.uniform(0.5, 1.0)
+            ang = rng.uniform(0.0, math.pi)
+            extent = a
+        lim = 1.0 - extent - 0.05
+        c = rng.uniform(-lim, lim, 2)
+        if np.hypot(c[0], c[1]) > lim:
+            continue
+        if any(np.hypot(c[0] - d[0], c[1] - d[1]) < extent + e + 0.05 for d, e in placed):
+            continue
+        placed.append((c, extent))
+        if kind == 0:
+            holes.append(starfish_nodes(c, r0, 0.3, 5, npc, clockwise=True, phase=rng.uniform(0.0, TWO_PI)))
+        else:
+            holes.append(ellipse_nodes(c, a, b, ang, npc, clockwise=True))
+    outer = circle_nodes((0.0, 0.0), 1.0, npc, clockwise=False)
+    if refine_tol_override is not None:
+        refine_tol = refine_tol_override
+    return Workload(f"batch_{i}", [outer] + holes, (-1.0, -1.0, 2.0), 8, 4, 8, refine_tol, alpha2,
+                    math.sqrt(alpha2), steps, 20, gaussian_forcing(1000 + i), False, [0.0] * (n_holes + 1))

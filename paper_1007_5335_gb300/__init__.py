@@ -50,6 +50,10 @@ class StepInfo(ctypes.Structure):
     _fields_ = [("gmres_iterations", _i), ("gmres_rel_residual", _d), ("initial_rel_residual", _d), ("warm_c", _d)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("p", _i), ("near_tile", _i), ("rel_err", _d), ("ms_per_step", _d)]
+
+
 FIELD_FN = ctypes.CFUNCTYPE(_i, ctypes.POINTER(_d), _i64, ctypes.POINTER(_d), _p)
 
 _SIGS = {
@@ -90,6 +94,13 @@ _SIGS = {
                      ctypes.POINTER(_d), ctypes.POINTER(_i)],
     "mh_warm_start": [_p, _p, _d, _p, _i, _i, _p, _p, _p, _p, _p, _i, ctypes.POINTER(_d)],
     "mh_problem_set_warm_start": [_p, _p, _i, _p, _i],
+    "mh_batch_create": [_p, _i, _p, ctypes.POINTER(_p)],
+    "mh_batch_destroy": [_p],
+    "mh_batch_step": [_p, _p, _p, _p, _p, _p, _d, _i, _p],
+    "mh_batch_graph_kernels": [_p],
+    "mh_problem_set_near_tile": [_p, _p, _i],
+    "mh_autotune": [_p, _p, _p, _d, _i, _p, _p, _p, _i, _p, _d, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                    _p],
     "mh_profile_enable": [_p, _i],
     "mh_profile_read": [_p, ctypes.c_char_p, ctypes.POINTER(_d), ctypes.POINTER(_i64), ctypes.POINTER(_d),
                         ctypes.POINTER(_d), _i],
@@ -97,7 +108,7 @@ _SIGS = {
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
-    _f.restype = ctypes.c_int64 if _name == "mh_kernel_launches" else _i
+    _f.restype = ctypes.c_int64 if _name in ("mh_kernel_launches", "mh_batch_graph_kernels") else _i
 _lib.mh_last_error.argtypes = [_p]
 _lib.mh_last_error.restype = ctypes.c_char_p
 
@@ -304,6 +315,10 @@ class Problem:
                                                       int(arith)))
         self._net = net          # keep the network alive while the problem uses it
 
+    def set_near_tile(self, threads: int):
+        """mh_problem_set_near_tile: threads per block of the near-field double-layer kernel."""
+        self.ctx.check(_lib.mh_problem_set_near_tile(self.ctx.h, self.h, int(threads)))
+
     def rhs(self, out):
         """Right-hand side of the boundary equation of the last step, into the device buffer out."""
         self.ctx.check(_lib.mh_problem_rhs(self.ctx.h, self.h, _ptr(out)))
@@ -402,6 +417,57 @@ def mh_warm_start(ctx: Context, bnd: Boundary, alpha: float, mode: int, sigma, r
                                  _ptr(sigma), _ptr(sigma_prev2), _ptr(rhs), _ptr(x0_out), _ptr(r0_out), int(prec),
                                  ctypes.byref(c)))
     return c.value
+
+
+def _ptr_array(ts):
+    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+class Batch:
+    """mh_batch_create: independent problems stepped together, one CUDA graph launch per step."""
+
+    def __init__(self, ctx: Context, problems):
+        self.ctx, self.problems = ctx, list(problems)
+        arr = (ctypes.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        h = _p()
+        ctx.check(_lib.mh_batch_create(ctx.h, len(self.problems), ctypes.cast(arr, _p), ctypes.byref(h)))
+        self.h = h
+
+    def step(self, u, F, f_next, sigma, gmres_tol: float = 1e-10, prec: int = MH_PREC_MIXED):
+        """One in-place IMEX Euler step of every problem; lists of device tensors."""
+        for group in (u, F, f_next, sigma):
+            for t in group:
+                _ptr(t)
+        n = len(self.problems)
+        infos = (StepInfo * n)()
+        self.ctx.check(_lib.mh_batch_step(self.ctx.h, self.h, ctypes.cast(_ptr_array(u), _p),
+                                          ctypes.cast(_ptr_array(F), _p), ctypes.cast(_ptr_array(f_next), _p),
+                                          ctypes.cast(_ptr_array(sigma), _p), float(gmres_tol), int(prec),
+                                          ctypes.cast(infos, _p)))
+        return list(infos)
+
+    @property
+    def graph_kernels(self) -> int:
+        return int(_lib.mh_batch_graph_kernels(self.h))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.mh_batch_destroy(self.h)
+            self.h = None
+
+
+def mh_autotune(ctx: Context, tree: Tree, bnd: Boundary, dt: float, F, f, p_cand=(10, 16, 24), err_tol: float = 1e-7,
+                steps: int = 4, prec: int = MH_PREC_MIXED, ext_const=None):
+    """Multipole order and near-field tile for one geometry and alpha (see include/mh.h).
+    Returns (p, tile, report list of TuneEntry)."""
+    pc = (ctypes.c_int * len(p_cand))(*p_cand)
+    ec = np.ascontiguousarray(ext_const if ext_const is not None else np.zeros(bnd.n_curves), dtype=np.float64)
+    rep = (TuneEntry * (len(p_cand) + 3))()
+    p_out, t_out = _i(), _i()
+    ctx.check(_lib.mh_autotune(ctx.h, tree.h, bnd.h, float(dt), MH_EXT_CONST, ec.ctypes.data_as(_p), _ptr(F), _ptr(f),
+                               len(p_cand), ctypes.cast(pc, _p), float(err_tol), int(steps), int(prec),
+                               ctypes.byref(p_out), ctypes.byref(t_out), ctypes.cast(rep, _p)))
+    return p_out.value, t_out.value, list(rep)
 
 
 def library_path() -> str:

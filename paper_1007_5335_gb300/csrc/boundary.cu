@@ -256,7 +256,8 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
 
 // y = A x, one warp per row, 16-byte loads (N_Gamma is even, so rows stay aligned).
 __global__ void k_gemv64(const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ y,
-                         int64_t n) {
+                         int64_t n, const int* __restrict__ gate = nullptr) {
+    if (gate && *gate) return;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < n; row += nwarps) {
@@ -279,7 +280,8 @@ __global__ void k_gemv64(const double* __restrict__ A, const double* __restrict_
 // One warp per row; four independent loads in flight per lane (16-byte loads when the
 // row length is a multiple of 4, 8-byte loads otherwise).
 __global__ void k_gemv32(const float* __restrict__ A, const float* __restrict__ x, double* __restrict__ y,
-                         int64_t n) {
+                         int64_t n, const int* __restrict__ gate = nullptr) {
+    if (gate && *gate) return;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < n; row += nwarps) {
@@ -645,7 +647,9 @@ constexpr int ARN_ROWS = 64;
 
 // P[s k1 + i] = sum over slice s of V_i[e] w[e], i < k1 (a warp per i).
 __global__ void __launch_bounds__(256) k_arn_dots(const double* __restrict__ V, const double* __restrict__ w,
-                                                  int64_t n, int k1, double* __restrict__ P) {
+                                                  int64_t n, int k1, double* __restrict__ P,
+                                                  const int* __restrict__ gate = nullptr) {
+    if (gate && *gate) return;
     const int s = blockIdx.x;
     const int64_t r0 = (int64_t)s * ARN_ROWS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -666,7 +670,8 @@ __global__ void __launch_bounds__(256) k_arn_dots(const double* __restrict__ V, 
 __global__ void __launch_bounds__(256) k_arn_update(const double* __restrict__ V, double* __restrict__ w, int64_t n,
                                                     int k1, const double* __restrict__ Pin, int S,
                                                     double* __restrict__ Pdots, double* __restrict__ Pnorm,
-                                                    double* __restrict__ hout) {
+                                                    double* __restrict__ hout, const int* __restrict__ gate = nullptr) {
+    if (gate && *gate) return;
     extern __shared__ double sh[];      // h[k1], then the slice of w
     double* h = sh;
     double* wsl = sh + k1;
@@ -719,7 +724,9 @@ __global__ void __launch_bounds__(256) k_arn_finish(const double* __restrict__ w
                                                     const double* __restrict__ h1, const double* __restrict__ h2,
                                                     double* H, int ldh, double* cs, double* sn, double* g,
                                                     double* small, double* __restrict__ vnext,
-                                                    float* __restrict__ vnext32) {
+                                                    float* __restrict__ vnext32, gmres_dev* gs = nullptr,
+                                                    int m_max = 0) {
+    if (gs && gs->skip) return;
     __shared__ double nrm;
     if (threadIdx.x < 32) {
         double a = 0.0;
@@ -769,6 +776,11 @@ __global__ void __launch_bounds__(256) k_arn_finish(const double* __restrict__ w
         g[k + 1] = -sv * gk;
         g[k] = c * gk;
         small[0] = fabs(-sv * gk);
+        if (gs) {   // sync-free schedule: iteration count and the end of this sweep's Arnoldi process
+            gs->k = k + 1;
+            gs->total += 1;
+            if (fabs(sv * gk) <= gs->target || k + 1 >= m_max || den == 0.0) gs->skip = 1;
+        }
     }
     __syncthreads();
     double* hc = H + (int64_t)k * ldh;
@@ -1370,6 +1382,14 @@ static mh_status ensure_fp32(mh_ctx* ctx, mh_boundary* b) {
     return MH_OK;
 }
 
+mh_status bie_prepare(mh_ctx* ctx, mh_boundary* b, mh_precision prec) {
+    if (prec == MH_PREC_MIXED) {
+        MH_TRY(ensure_fp32(ctx, b));
+        if (!b->x32.p) MH_ALLOC(ctx, b->x32, b->n);
+    }
+    return MH_OK;
+}
+
 static int gemv_blocks(int64_t n) {
     int64_t need = (n + 7) / 8;            // 8 warps per block
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, 152 * 16));
@@ -1492,29 +1512,8 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
     prof_scope ps_all(ctx, "gmres");
     const int64_t n = bd->n;
     if (max_iter < 1 || max_iter > 1000) return mh_fail(ctx, MH_ERR_INVALID_ARG, "max_iter must be in 1..1000");
+    MH_TRY(gmres_graph_ensure(ctx, bd, max_iter));
     gmres_ws& ws = bd->ws;
-    if (ws.m < max_iter || ws.n != n) {
-        const int ldh = max_iter + 1;
-        MH_ALLOC(ctx, ws.V, (int64_t)(max_iter + 1) * n);
-        MH_ALLOC(ctx, ws.H, (int64_t)ldh * max_iter);
-        MH_ALLOC(ctx, ws.cs, max_iter + 1);
-        MH_ALLOC(ctx, ws.sn, max_iter + 1);
-        MH_ALLOC(ctx, ws.g, max_iter + 2);
-        MH_ALLOC(ctx, ws.y, max_iter + 1);
-        MH_ALLOC(ctx, ws.h1, max_iter + 2);
-        MH_ALLOC(ctx, ws.h2, max_iter + 2);
-        MH_ALLOC(ctx, ws.small, 8);
-        MH_ALLOC(ctx, ws.w, n);
-        MH_ALLOC(ctx, ws.r, n);
-        MH_ALLOC(ctx, ws.dx, n);
-        const int64_t S = (n + ARN_ROWS - 1) / ARN_ROWS;
-        MH_ALLOC(ctx, ws.P1, S * (max_iter + 1));
-        MH_ALLOC(ctx, ws.P2, S * (max_iter + 1));
-        MH_ALLOC(ctx, ws.Pn, S);
-        MH_ALLOC(ctx, ws.v32, n);
-        ws.m = max_iter;
-        ws.n = n;
-    }
     MH_CUDA(ctx, cudaMemsetAsync(ws.g.p, 0, (max_iter + 2) * 8, ctx->stream));
     double bnorm;
     MH_TRY(vec_norm(ctx, b, n, ws.small.p + 2, &bnorm));
@@ -1587,6 +1586,201 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
     if (!inf.converged)
         return mh_fail(ctx, MH_ERR_NOT_CONVERGED, "GMRES stopped after %d iterations at relative residual %.3e",
                        inf.iterations, inf.rel_residual);
+    return MH_OK;
+}
+
+// ---------------- sync-free GMRES (fixed schedule, device flags) ----------------
+
+mh_status gmres_graph_ensure(mh_ctx* ctx, mh_boundary* bd, int max_iter) {
+    const int64_t n = bd->n;
+    gmres_ws& ws = bd->ws;
+    if (ws.m >= max_iter && ws.n == n) return MH_OK;
+    const int ldh = max_iter + 1;
+    MH_ALLOC(ctx, ws.V, (int64_t)(max_iter + 1) * n);
+    MH_ALLOC(ctx, ws.H, (int64_t)ldh * max_iter);
+    MH_ALLOC(ctx, ws.cs, max_iter + 1);
+    MH_ALLOC(ctx, ws.sn, max_iter + 1);
+    MH_ALLOC(ctx, ws.g, max_iter + 2);
+    MH_ALLOC(ctx, ws.y, max_iter + 1);
+    MH_ALLOC(ctx, ws.h1, max_iter + 2);
+    MH_ALLOC(ctx, ws.h2, max_iter + 2);
+    MH_ALLOC(ctx, ws.small, 8);
+    MH_ALLOC(ctx, ws.w, n);
+    MH_ALLOC(ctx, ws.r, n);
+    MH_ALLOC(ctx, ws.dx, n);
+    const int64_t S = (n + ARN_ROWS - 1) / ARN_ROWS;
+    MH_ALLOC(ctx, ws.P1, S * (max_iter + 1));
+    MH_ALLOC(ctx, ws.P2, S * (max_iter + 1));
+    MH_ALLOC(ctx, ws.Pn, S);
+    MH_ALLOC(ctx, ws.v32, n);
+    ws.m = max_iter;
+    ws.n = n;
+    return MH_OK;
+}
+
+void gmres_graph_schedule(mh_precision prec, int* sweeps, int* m_max) {
+    if (prec == MH_PREC_MIXED) {
+        *sweeps = 3;    // binary64 refinement passes around the binary32-operator Arnoldi process
+        *m_max = 20;
+    } else {
+        *sweeps = 1;
+        *m_max = 40;
+    }
+}
+
+__global__ void k_gnorm(const double* __restrict__ v, int64_t n, double* out, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    double acc = 0.0;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc = fma(v[e], v[e], acc);
+    acc = block_sum<1024>(acc);
+    if (threadIdx.x == 0) *out = sqrt(acc);
+}
+
+__global__ void k_gsub(const double* __restrict__ b, double* r, int64_t n, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        r[e] = b[e] - r[e];
+}
+
+// Start of a sweep from the residual r (norm gs->rn): accept (converged) when allowed and
+// rn <= tol ||b||, else start an Arnoldi process on r (V_0 = r / rn, g = (rn, 0, ...), inner
+// target max(tol ||b||, 1e-5 rn) in mixed precision, tol ||b|| in binary64).  final_check: the
+// last residual of the schedule, recorded only.  ||b|| = 0 gives x = 0.
+__global__ void k_sweep_begin(gmres_dev* gs, double tol, int mixed, int may_accept, int final_check, int first,
+                              const double* __restrict__ r, double* V0, float* v32, double* g, int gsz, int64_t n,
+                              double* x) {
+    if (gs->done) return;
+    const double rn = gs->rn, bn = gs->bnorm;
+    if (bn == 0.0) {
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+            x[e] = 0.0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            gs->done = gs->skip = gs->converged = 1;
+            gs->rel = 0.0;
+        }
+        return;
+    }
+    const bool accept = may_accept || final_check;
+    const bool conv = accept && rn <= tol * bn;
+    const bool start = !conv && !final_check && rn > 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (first) gs->init_rel = rn / bn;
+        if (accept) gs->rel = rn / bn;
+        if (conv) {
+            gs->done = gs->skip = gs->converged = 1;
+        } else if (start) {
+            gs->skip = 0;
+            gs->k = 0;
+            gs->sweeps += 1;
+            gs->target = mixed ? fmax(tol * bn, 1e-5 * rn) : tol * bn;
+        } else {
+            gs->skip = 1;
+        }
+    }
+    if (!start) return;
+    const double inv = 1.0 / rn;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const double v = r[e] * inv;
+        V0[e] = v;
+        if (v32) v32[e] = (float)v;
+    }
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < gsz; i += blockDim.x) g[i] = i == 0 ? rn : 0.0;
+}
+
+// R y = g with the iteration count of the sweep (device); skipped once converged.
+__global__ void k_backsolve_g(const double* H, int ldh, const double* g, double* y, const gmres_dev* gs) {
+    if (gs->done) return;
+    const int k = gs->k;
+    for (int i = k - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int j = i + 1; j < k; ++j) acc -= H[(int64_t)j * ldh + i] * y[j];
+        const double d = H[(int64_t)i * ldh + i];
+        y[i] = d != 0.0 ? acc / d : 0.0;
+    }
+}
+
+// x += sum_{i < k} y_i V_i (k of the sweep, device); skipped once converged.
+__global__ void k_update_x_g(const double* __restrict__ V, const double* __restrict__ y, const gmres_dev* gs,
+                             int64_t n, double* x) {
+    if (gs->done) return;
+    const int k = gs->k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = x[e];
+        for (int i = 0; i < k; ++i) acc = fma(y[i], V[(int64_t)i * n + e], acc);
+        x[e] = acc;
+    }
+}
+
+mh_status gmres_run_graph(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, double tol, mh_precision prec,
+                          const double* r0, gmres_dev* gs) {
+    const int64_t n = bd->n;
+    cudaStream_t st = ctx->stream;
+    int S, m;
+    gmres_graph_schedule(prec, &S, &m);
+    gmres_ws& ws = bd->ws;
+    const bool mixed = prec == MH_PREC_MIXED;
+    if (ws.m < m || ws.n != n || (mixed && !bd->op.A32.p) || !bd->op.A64.p)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "sync-free GMRES: workspace or operator not prepared");
+    const int ldh = m + 1;
+    const int ew = mh_grid(n, 256) < 152 * 4 ? mh_grid(n, 256) : 152 * 4;
+    const int SL = (int)((n + ARN_ROWS - 1) / ARN_ROWS);
+    MH_CUDA(ctx, cudaMemsetAsync(gs, 0, sizeof(gmres_dev), st));
+    k_gnorm<<<1, 1024, 0, st>>>(b, n, &gs->bnorm, nullptr);
+    MH_LAUNCHED(ctx);
+    for (int sw = 0; sw <= S; ++sw) {
+        const bool supplied = sw == 0 && r0;
+        if (supplied) {
+            MH_CUDA(ctx, cudaMemcpyAsync(ws.r.p, r0, n * 8, cudaMemcpyDeviceToDevice, st));
+        } else {
+            k_gemv64<<<gemv_blocks(n), 256, 0, st>>>(bd->op.A64.p, x, ws.r.p, n, &gs->done);
+            MH_LAUNCHED(ctx);
+            k_gsub<<<ew, 256, 0, st>>>(b, ws.r.p, n, &gs->done);
+            MH_LAUNCHED(ctx);
+        }
+        k_gnorm<<<1, 1024, 0, st>>>(ws.r.p, n, &gs->rn, &gs->done);
+        MH_LAUNCHED(ctx);
+        k_sweep_begin<<<ew, 256, 0, st>>>(gs, tol, mixed, !supplied, sw == S, sw == 0, ws.r.p, ws.V.p,
+                                          mixed ? ws.v32.p : nullptr, ws.g.p, m + 2, n, x);
+        MH_LAUNCHED(ctx);
+        if (sw == S) break;
+        for (int k = 0; k < m; ++k) {
+            const int k1 = k + 1;
+            if (mixed)
+                k_gemv32<<<gemv_blocks(n), 256, 0, st>>>(bd->op.A32.p, ws.v32.p, ws.w.p, n, &gs->skip);
+            else
+                k_gemv64<<<gemv_blocks(n), 256, 0, st>>>(bd->op.A64.p, ws.V.p + (int64_t)k * n, ws.w.p, n,
+                                                         &gs->skip);
+            MH_LAUNCHED(ctx);
+            const size_t shm = (size_t)(k1 + ARN_ROWS) * sizeof(double);
+            k_arn_dots<<<SL, 256, 0, st>>>(ws.V.p, ws.w.p, n, k1, ws.P1.p, &gs->skip);
+            MH_LAUNCHED(ctx);
+            k_arn_update<<<SL, 256, shm, st>>>(ws.V.p, ws.w.p, n, k1, ws.P1.p, SL, ws.P2.p, nullptr, ws.h1.p,
+                                               &gs->skip);
+            MH_LAUNCHED(ctx);
+            k_arn_update<<<SL, 256, shm, st>>>(ws.V.p, ws.w.p, n, k1, ws.P2.p, SL, nullptr, ws.Pn.p, ws.h2.p,
+                                               &gs->skip);
+            MH_LAUNCHED(ctx);
+            k_arn_finish<<<SL, 256, (size_t)(3 * k + 2) * sizeof(double), st>>>(
+                ws.w.p, n, ws.Pn.p, SL, k, ws.h1.p, ws.h2.p, ws.H.p, ldh, ws.cs.p, ws.sn.p, ws.g.p, ws.small.p,
+                ws.V.p + (int64_t)k1 * n, mixed ? ws.v32.p : nullptr, gs, m);
+            MH_LAUNCHED(ctx);
+        }
+        k_backsolve_g<<<1, 1, 0, st>>>(ws.H.p, ldh, ws.g.p, ws.y.p, gs);
+        MH_LAUNCHED(ctx);
+        k_update_x_g<<<ew, 256, 0, st>>>(ws.V.p, ws.y.p, gs, n, x);
+        MH_LAUNCHED(ctx);
+    }
+    return MH_OK;
+}
+
+mh_status gmres_info_from_dev(const gmres_dev& g, double tol, mh_gmres_info* info) {
+    if (!info) return MH_OK;
+    info->iterations = g.total;
+    info->refinements = g.sweeps;
+    info->rel_residual = g.rel;
+    info->converged = g.converged && g.rel <= tol;
+    info->initial_rel_residual = g.init_rel;
     return MH_OK;
 }
 

@@ -94,6 +94,18 @@ struct dbuf {
 
 #define MH_ALLOC(ctx, buf, count) MH_CUDA(ctx, (buf).alloc(count))
 
+// Device-resident state of the sync-free GMRES (gmres_run_graph): every kernel of its fixed
+// schedule reads the flags at entry and returns at once when its work is not needed.
+struct gmres_dev {
+    double bnorm, rn, target, rel, init_rel;
+    int done;        // converged on a binary64 residual computed in this solve
+    int skip;        // done, or the Arnoldi process of the current sweep has ended
+    int k;           // Arnoldi iterations of the current sweep
+    int total;       // all Arnoldi iterations
+    int sweeps;      // sweeps started (refinement passes in mixed precision)
+    int converged;
+};
+
 // GMRES workspace (kept by the boundary so that repeated solves allocate nothing).
 struct gmres_ws {
     dbuf<double> V, H, cs, sn, g, y, h1, h2, small, w, r, dx;
@@ -204,6 +216,9 @@ struct mh_problem {
     bool have_prev = false;              // sig_prev holds the density entering the previous step
     dbuf<double> sig_prev, r0, c_dev;
     double* c_host = nullptr;            // pinned
+    // batched stepping (mh_batch_step): sync-free GMRES with its state in gstat (device)
+    bool graph_mode = false;
+    gmres_dev* gstat = nullptr;
     ~mh_problem() {
         if (c_host) cudaFreeHost(c_host);
     }
@@ -216,10 +231,14 @@ mh_status warm_start_run(mh_ctx* ctx, mh_boundary* bnd, double alpha, struct mh_
                          const double* sigma, const double* sigma_prev2, const double* rhs, double* x0, double* r0,
                          mh_precision prec, double* c_dev, double* save);
 bool net_matches(const struct mh_net* net, const mh_boundary* b);
+// Workspace of the SECANT / LEARNED starts (allocated once per boundary).
+mh_status warm_start_prepare(mh_ctx* ctx, mh_boundary* b);
 
 // ---- boundary.cu ----
 mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha);
 mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec);
+// Everything a sync-free solve in precision prec needs (binary32 operator copy).
+mh_status bie_prepare(mh_ctx* ctx, mh_boundary* b, mh_precision prec);
 mh_status dlp_classify(mh_ctx* ctx, mh_boundary* b, const double* xy_dev, int64_t n, dlp_targets* tg);
 mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* tg,
                        const double* sigma, double* out, mh_precision prec);
@@ -236,6 +255,15 @@ mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_
 // r0 (nullable): the binary64 residual rhs - A x of the initial guess, computed by the caller.
 mh_status gmres_run(mh_ctx* ctx, mh_boundary* b, const double* rhs, double* x, double tol, int max_iter,
                     mh_precision prec, mh_gmres_info* info, const double* r0 = nullptr);
+// The same solve without host synchronisation, for capture in a CUDA graph: a fixed schedule of
+// sweeps x m_max Arnoldi iterations whose kernels return at once when the device flags in gs
+// say their work is not needed.  gs (device) holds the result; gmres_graph_ensure sizes the
+// workspace beforehand (no allocation happens in gmres_run_graph).
+mh_status gmres_graph_ensure(mh_ctx* ctx, mh_boundary* b, int m_max);
+mh_status gmres_run_graph(mh_ctx* ctx, mh_boundary* b, const double* rhs, double* x, double tol, mh_precision prec,
+                          const double* r0, gmres_dev* gs);
+void gmres_graph_schedule(mh_precision prec, int* sweeps, int* m_max);
+mh_status gmres_info_from_dev(const gmres_dev& g, double tol, mh_gmres_info* info);
 
 // ---- tree.cu ----
 void mh_gauss_legendre(int n, double* x, double* w);
@@ -245,6 +273,9 @@ const double* tree_gl_nodes(const mh_tree* t);
 mh_status volume_apply(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* b, double* up,
                        mh_precision prec);
 void volume_free(mh_tree* t);
+// Threads per block of the binary32 near-field double-layer kernel (128, 256 or 512).
+mh_status volume_set_near_tile(mh_ctx* ctx, mh_tree* t, int threads);
+int volume_near_tile(const mh_tree* t);
 // double layer through the multipole method (dipoles sorted by leaf)
 mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* dxy, const double* dnrm,
                               const int32_t* dleaf, int64_t nd, bool near_blocks);

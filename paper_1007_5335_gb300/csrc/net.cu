@@ -1106,6 +1106,14 @@ extern "C" mh_status mh_net_train(mh_ctx* ctx, mh_net* net, const float* X_dev, 
     return MH_OK;
 }
 
+mh_status warm_start_prepare(mh_ctx* ctx, mh_boundary* b) {
+    if (b->warm_dir.p) return MH_OK;
+    MH_ALLOC(ctx, b->warm_dir, b->n);
+    MH_ALLOC(ctx, b->warm_w, b->n);
+    MH_ALLOC(ctx, b->warm_scal, 8);
+    return MH_OK;
+}
+
 // Shared by mh_warm_start and the time step.  r0 first holds r = rhs - A sigma (binary64).
 mh_status warm_start_run(mh_ctx* ctx, mh_boundary* b, double alpha, mh_net* net, int mode, int arith,
                          const double* sigma, const double* sigma_prev2, const double* rhs, double* x0, double* r0,
@@ -1128,11 +1136,7 @@ mh_status warm_start_run(mh_ctx* ctx, mh_boundary* b, double alpha, mh_net* net,
         if (c_dev) MH_CUDA(ctx, cudaMemsetAsync(c_dev, 0, 8, st));
         return MH_OK;
     }
-    if (!b->warm_dir.p) {
-        MH_ALLOC(ctx, b->warm_dir, n);
-        MH_ALLOC(ctx, b->warm_w, n);
-        MH_ALLOC(ctx, b->warm_scal, 8);
-    }
+    MH_TRY(warm_start_prepare(ctx, b));
     double* scal = b->warm_scal.p;
     if (mode == MH_WARM_SECANT) {
         k_axmy<<<mh_grid(n, 256), 256, 0, st>>>(sigma, sigma_prev2, n, b->warm_dir.p);

@@ -235,6 +235,7 @@ extern "C" mh_status mh_problem_set_warm_start(mh_ctx* ctx, mh_problem* p, mh_wa
         *p->c_host = 0.0;
     }
     if (mode == MH_WARM_SECANT && !p->sig_prev.p) MH_ALLOC(ctx, p->sig_prev, ng);
+    if (mode == MH_WARM_SECANT || mode == MH_WARM_LEARNED) MH_TRY(warm_start_prepare(ctx, p->bnd));
     p->warm_mode = mode;
     p->net = mode == MH_WARM_LEARNED ? net : nullptr;
     p->warm_arith = arith;
@@ -277,8 +278,12 @@ static mh_status step_solve(mh_ctx* ctx, ProblemImpl* P, const double* f_next_de
         r0 = P->r0.p;
         have_c = true;
     }
-    mh_status s = gmres_run(ctx, b, P->rhs.p, sigma_dev, gmres_tol, 100, prec, &gi, r0);
-    if (info) {
+    if (P->graph_mode) {
+        // sync-free solve: the result stays in P->gstat until the caller reads it back
+        MH_TRY(gmres_run_graph(ctx, b, P->rhs.p, sigma_dev, gmres_tol, prec, r0, P->gstat));
+    }
+    mh_status s = P->graph_mode ? MH_OK : gmres_run(ctx, b, P->rhs.p, sigma_dev, gmres_tol, 100, prec, &gi, r0);
+    if (info && !P->graph_mode) {
         info->gmres_iterations = gi.iterations;
         info->gmres_rel_residual = gi.rel_residual;
         info->initial_rel_residual = gi.initial_rel_residual;

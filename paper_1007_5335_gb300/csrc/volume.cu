@@ -1103,16 +1103,19 @@ __global__ void __launch_bounds__(NEAR_T) k_dip_near64(
     }
 }
 
-__global__ void __launch_bounds__(NEAR_T) k_dip_near32(
+// NT threads per block (the tile: qq targets x NT / qq source groups, NT sources staged per
+// round); NT in {128, 256, 512} is picked per problem by mh_autotune.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_dip_near32(
     const double* __restrict__ nodes, const int32_t* __restrict__ active, const int32_t* __restrict__ near_ptr,
     const int32_t* __restrict__ near_leaf, const int64_t* __restrict__ seg0, const int32_t* __restrict__ segn,
     const double2* __restrict__ leaf_c, const float4* __restrict__ d32, const float* __restrict__ w, int qq,
     float inv_alpha, double pref, double* out) {
-    __shared__ float4 s4[NEAR_T];
-    __shared__ float sw[NEAR_T];
-    __shared__ double part[NEAR_T];
+    __shared__ float4 s4[NT];
+    __shared__ float sw[NT];
+    __shared__ double part[NT];
     const int leaf = active[blockIdx.x];
-    const int groups = NEAR_T / qq;
+    const int groups = NT / qq;
     const int i = threadIdx.x % qq, g = threadIdx.x / qq;
     const bool act = g < groups;
     const int64_t node = (int64_t)leaf * qq + i;
@@ -1124,8 +1127,8 @@ __global__ void __launch_bounds__(NEAR_T) k_dip_near32(
         const int cnt = segn[lc];
         const double2 c = leaf_c[lc];
         const float tx = (float)(px - c.x), ty = (float)(py - c.y);
-        for (int b0 = 0; b0 < cnt; b0 += NEAR_T) {
-            const int m = min(NEAR_T, cnt - b0);
+        for (int b0 = 0; b0 < cnt; b0 += NT) {
+            const int m = min(NT, cnt - b0);
             __syncthreads();
             if (threadIdx.x < m) {
                 s4[threadIdx.x] = d32[s0 + b0 + threadIdx.x];
@@ -1177,6 +1180,7 @@ struct DipData {
     dbuf<float> w32;
     double pref = 0, inv_alpha = 0;
     double near_pairs = 0;
+    int near_t = 256;                      // threads per block of the binary32 near-field kernel
     dbuf<double> vec, temp, ops64;
     dbuf<float> ops32;
     dbuf<int64_t> d_op_off;
@@ -1479,9 +1483,17 @@ mh_status volume_dipole_apply(mh_ctx* ctx, mh_tree* t, const double* w_sorted, m
         if (prec == MH_PREC_MIXED) {
             k_d2f<<<mh_grid(D->nd, 256), 256, 0, st>>>(w_sorted, D->w32.p, D->nd);
             MH_LAUNCHED(ctx);
-            k_dip_near32<<<(unsigned)D->n_active, NEAR_T, 0, st>>>(
-                t->nodes.p, D->active.p, D->near_ptr.p, D->near_leaf.p, D->seg0.p, D->segn.p, D->leaf_c.p, D->d32.p,
-                D->w32.p, D->qq, (float)D->inv_alpha, D->pref, D->vec.p + D->DU_off);
+#define MH_NEAR32(NTV)                                                                                         \
+    k_dip_near32<NTV><<<(unsigned)D->n_active, NTV, 0, st>>>(                                                 \
+        t->nodes.p, D->active.p, D->near_ptr.p, D->near_leaf.p, D->seg0.p, D->segn.p, D->leaf_c.p, D->d32.p,   \
+        D->w32.p, D->qq, (float)D->inv_alpha, D->pref, D->vec.p + D->DU_off)
+            if (D->near_t == 128)
+                MH_NEAR32(128);
+            else if (D->near_t == 512)
+                MH_NEAR32(512);
+            else
+                MH_NEAR32(256);
+#undef MH_NEAR32
         } else {
             k_dip_near64<<<(unsigned)D->n_active, NEAR_T, 0, st>>>(
                 t->nodes.p, D->active.p, D->near_ptr.p, D->near_leaf.p, D->seg0.p, D->segn.p, D->dxy.p, D->dnrm.p,
@@ -1491,6 +1503,21 @@ mh_status volume_dipole_apply(mh_ctx* ctx, mh_tree* t, const double* w_sorted, m
     }
     *u = D->vec.p + D->DU_off;
     return MH_OK;
+}
+
+mh_status volume_set_near_tile(mh_ctx* ctx, mh_tree* t, int threads) {
+    VolData* V = static_cast<VolData*>(t->vol);
+    if (!V || !V->dip) return mh_fail(ctx, MH_ERR_INVALID_ARG, "double-layer multipole pass not set up");
+    if (threads != 128 && threads != 256 && threads != 512)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "near-field tile must be 128, 256 or 512 threads");
+    if (threads < V->dip->qq) return mh_fail(ctx, MH_ERR_INVALID_ARG, "near-field tile smaller than a leaf");
+    V->dip->near_t = threads;
+    return MH_OK;
+}
+
+int volume_near_tile(const mh_tree* t) {
+    const VolData* V = static_cast<const VolData*>(t->vol);
+    return V && V->dip ? V->dip->near_t : 0;
 }
 
 void volume_free(mh_tree* t) {
