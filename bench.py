@@ -183,6 +183,17 @@ def run_ours(args):
     def set_start(mode):
         prob.set_warm_start(mode, net, mh.MH_NET_BF16X2)
 
+    # near-field tile: the fastest of the autotuner's three shapes on a few untimed steps
+    tile_ms = {}
+    for tile in (128, 256, 512):
+        prob.set_near_tile(tile)
+        ut = torch.zeros(tree.n_nodes, dtype=torch.float64, device=dev)
+        st_ = torch.zeros(bnd.n, dtype=torch.float64, device=dev)
+        _, tt, _ = run_steps(3, ut, st_, True, prec)
+        tile_ms[tile] = float(np.median(tt))
+    near_tile = min(tile_ms, key=tile_ms.get)
+    prob.set_near_tile(near_tile)
+
     # accuracy of the headline form (precision + start) against the plain FP64 path
     # (previous-step start), same steps from u = 0
     u0 = torch.zeros(tree.n_nodes, dtype=torch.float64, device=dev)
@@ -276,7 +287,7 @@ def run_ours(args):
                                "N_D=%d (adaptive tree levels 4-8, 8x8 GL nodes per leaf), dt=alpha^2=1e-3, p=20, "
                                "IMEX Euler, GMRES tol 1e-10" % tree.n_nodes,
                    "points": n_pts, "n_gamma": bnd.n, "n_d": tree.n_nodes, "precision": args.prec,
-                   "l2": "flushed between timed steps (256 MB write, untimed)",
+                   "l2": "flushed between timed steps (256 MB write, untimed)", "near_tile": near_tile,
                    "parallelism": "replicas" if world > 1 else "single"},
         "rel_l2_vs_fp64_path": err,
         "gmres_iterations": its,

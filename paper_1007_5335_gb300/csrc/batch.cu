@@ -150,6 +150,11 @@ extern "C" mh_status mh_batch_step(mh_ctx* ctx, mh_batch* B, double* const* u_de
         key.insert(key.end(), {u_dev[i], F_dev[i], f_next_dev[i], sigma_dev[i]});
     }
     GraphModeScope scope(B->probs);
+    struct CaptureFlag {
+        mh_ctx* c;
+        ~CaptureFlag() { c->capturing = false; }
+    } cflag{ctx};
+    ctx->capturing = true;   // the eager step takes the same kernels as the recorded graph
     const bool record = !B->exec || key != B->key || gmres_tol != B->key_tol || (int)prec != B->key_prec;
     if (record) {
         int S, m;

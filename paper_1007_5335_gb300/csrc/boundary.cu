@@ -321,6 +321,87 @@ __global__ void k_gemv32(const float* __restrict__ A, const float* __restrict__ 
     }
 }
 
+// Row-split GEMVs: SPLIT warps share a row (contiguous segments in 16-byte units, combined in
+// a fixed order through shared memory).  Blocks of 8 / SPLIT rows keep the hardware's dynamic
+// block scheduling fine-grained, so no SM is left with a whole extra block of rows at the end
+// of the sweep over the operator.  n must be a multiple of 4 (binary32) or 2 (binary64).
+template <int SPLIT>
+__global__ void __launch_bounds__(256) k_gemv32s(const float* __restrict__ A, const float* __restrict__ x,
+                                                 double* __restrict__ y, int64_t n, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    __shared__ float part[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (8 / SPLIT) + warp / SPLIT;
+    const int q = warp % SPLIT;
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+    if (row < n) {
+        const int64_t n4 = n >> 2;
+        const int64_t c0 = q * n4 / SPLIT, c1 = (q + 1) * n4 / SPLIT;
+        const float4* a4 = reinterpret_cast<const float4*>(A + row * n);
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        int64_t c = c0 + lane;
+        for (; c + 96 < c1; c += 128) {
+            const float4 a0 = __ldcs(a4 + c), a1 = __ldcs(a4 + c + 32), a2 = __ldcs(a4 + c + 64),
+                         a3 = __ldcs(a4 + c + 96);
+            const float4 x0 = __ldg(x4 + c), x1 = __ldg(x4 + c + 32), x2 = __ldg(x4 + c + 64), x3 = __ldg(x4 + c + 96);
+            f0 = fmaf(a0.x, x0.x, fmaf(a0.y, x0.y, fmaf(a0.z, x0.z, fmaf(a0.w, x0.w, f0))));
+            f1 = fmaf(a1.x, x1.x, fmaf(a1.y, x1.y, fmaf(a1.z, x1.z, fmaf(a1.w, x1.w, f1))));
+            f2 = fmaf(a2.x, x2.x, fmaf(a2.y, x2.y, fmaf(a2.z, x2.z, fmaf(a2.w, x2.w, f2))));
+            f3 = fmaf(a3.x, x3.x, fmaf(a3.y, x3.y, fmaf(a3.z, x3.z, fmaf(a3.w, x3.w, f3))));
+        }
+        for (; c < c1; c += 32) {
+            const float4 av = __ldcs(a4 + c), xv = __ldg(x4 + c);
+            f0 = fmaf(av.x, xv.x, fmaf(av.y, xv.y, fmaf(av.z, xv.z, fmaf(av.w, xv.w, f0))));
+        }
+    }
+    float f = (f0 + f1) + (f2 + f3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0) part[warp] = f;
+    __syncthreads();
+    if (q == 0 && lane == 0 && row < n) {
+        float t = part[warp];
+        for (int k = 1; k < SPLIT; ++k) t += part[warp + k];
+        y[row] = (double)t;
+    }
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(256) k_gemv64s(const double* __restrict__ A, const double* __restrict__ x,
+                                                 double* __restrict__ y, int64_t n, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    __shared__ double part[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (8 / SPLIT) + warp / SPLIT;
+    const int q = warp % SPLIT;
+    double a0 = 0.0, a1 = 0.0;
+    if (row < n) {
+        const int64_t n2 = n >> 1;
+        const int64_t c0 = q * n2 / SPLIT, c1 = (q + 1) * n2 / SPLIT;
+        const double2* a = reinterpret_cast<const double2*>(A + row * n);
+        const double2* xv = reinterpret_cast<const double2*>(x);
+        int64_t c = c0 + lane;
+        for (; c + 32 < c1; c += 64) {
+            const double2 u = __ldcs(a + c), v = __ldcs(a + c + 32);
+            const double2 xu = __ldg(xv + c), xw = __ldg(xv + c + 32);
+            a0 = fma(u.x, xu.x, fma(u.y, xu.y, a0));
+            a1 = fma(v.x, xw.x, fma(v.y, xw.y, a1));
+        }
+        for (; c < c1; c += 32) {
+            const double2 u = __ldcs(a + c), xu = __ldg(xv + c);
+            a0 = fma(u.x, xu.x, fma(u.y, xu.y, a0));
+        }
+    }
+    double f = warp_sum(a0 + a1);
+    if (lane == 0) part[warp] = f;
+    __syncthreads();
+    if (q == 0 && lane == 0 && row < n) {
+        double t = part[warp];
+        for (int k = 1; k < SPLIT; ++k) t += part[warp + k];
+        y[row] = t;
+    }
+}
+
 __global__ void k_to_float_vec(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
@@ -1395,6 +1476,24 @@ static int gemv_blocks(int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, 152 * 16));
 }
 
+constexpr int GEMV_SPLIT = 4;   // warps per row of the row-split GEMVs
+
+static void gemv32(cudaStream_t st, const float* A, const float* x, double* y, int64_t n, const int* gate) {
+    if ((n & 3) == 0)
+        k_gemv32s<GEMV_SPLIT><<<(unsigned)((n + 8 / GEMV_SPLIT - 1) / (8 / GEMV_SPLIT)), 256, 0, st>>>(A, x, y, n,
+                                                                                                     gate);
+    else
+        k_gemv32<<<gemv_blocks(n), 256, 0, st>>>(A, x, y, n, gate);
+}
+
+static void gemv64(cudaStream_t st, const double* A, const double* x, double* y, int64_t n, const int* gate) {
+    if ((n & 1) == 0)
+        k_gemv64s<GEMV_SPLIT><<<(unsigned)((n + 8 / GEMV_SPLIT - 1) / (8 / GEMV_SPLIT)), 256, 0, st>>>(A, x, y, n,
+                                                                                                     gate);
+    else
+        k_gemv64<<<gemv_blocks(n), 256, 0, st>>>(A, x, y, n, gate);
+}
+
 mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec) {
     if (prec == MH_PREC_MIXED) {
         MH_TRY(ensure_fp32(ctx, b));
@@ -1402,10 +1501,10 @@ mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_
         k_to_float_vec<<<mh_grid(b->n, 256), 256, 0, ctx->stream>>>(x, b->x32.p, b->n);
         MH_LAUNCHED(ctx);
         prof_scope ps(ctx, "bie_gemv", 2.0 * b->n * b->n, 4.0 * b->n * b->n + 12.0 * b->n);
-        k_gemv32<<<gemv_blocks(b->n), 256, 0, ctx->stream>>>(b->op.A32.p, b->x32.p, y, b->n);
+        gemv32(ctx->stream, b->op.A32.p, b->x32.p, y, b->n, nullptr);
     } else {
         prof_scope ps(ctx, "bie_gemv", 2.0 * b->n * b->n, 8.0 * b->n * b->n + 16.0 * b->n);
-        k_gemv64<<<gemv_blocks(b->n), 256, 0, ctx->stream>>>(b->op.A64.p, x, y, b->n);
+        gemv64(ctx->stream, b->op.A64.p, x, y, b->n, nullptr);
     }
     MH_LAUNCHED(ctx);
     return MH_OK;
@@ -1464,9 +1563,9 @@ static mh_status gmres_core(mh_ctx* ctx, mh_boundary* bd, gmres_ws& ws, const do
             const double* vk = ws.V.p + (int64_t)k * n;
             prof_scope ps(ctx, "bie_gemv", 2.0 * n * n, mixed ? 4.0 * n * n + 12.0 * n : 8.0 * n * n + 16.0 * n);
             if (mixed)
-                k_gemv32<<<gemv_blocks(n), 256, 0, st>>>(bd->op.A32.p, ws.v32.p, ws.w.p, n);
+                gemv32(st, bd->op.A32.p, ws.v32.p, ws.w.p, n, nullptr);
             else
-                k_gemv64<<<gemv_blocks(n), 256, 0, st>>>(bd->op.A64.p, vk, ws.w.p, n);
+                gemv64(st, bd->op.A64.p, vk, ws.w.p, n, nullptr);
             MH_LAUNCHED(ctx);
         }
         // classical Gram-Schmidt twice, normalisation and the Givens update (four launches)
@@ -1562,7 +1661,9 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
             MH_CUDA(ctx, cudaMemsetAsync(ws.g.p, 0, (max_iter + 2) * 8, ctx->stream));
             int it;
             double res;
-            MH_TRY(gmres_core(ctx, bd, ws, r.p, dx.p, std::max(tol * bnorm, 1e-5 * rn), max_iter - total,
+            // half the tolerance: the binary64 residual after the sweep then lands below tol
+            // instead of just above it (which would cost another sweep and binary64 GEMV)
+            MH_TRY(gmres_core(ctx, bd, ws, r.p, dx.p, std::max(0.5 * tol * bnorm, 1e-5 * rn), max_iter - total,
                               MH_PREC_MIXED, &it, &res, r.p, nullptr));
             total += it;
             inf.refinements++;
@@ -1672,7 +1773,7 @@ __global__ void k_sweep_begin(gmres_dev* gs, double tol, int mixed, int may_acce
             gs->skip = 0;
             gs->k = 0;
             gs->sweeps += 1;
-            gs->target = mixed ? fmax(tol * bn, 1e-5 * rn) : tol * bn;
+            gs->target = mixed ? fmax(0.5 * tol * bn, 1e-5 * rn) : tol * bn;
         } else {
             gs->skip = 1;
         }
@@ -1733,7 +1834,7 @@ mh_status gmres_run_graph(mh_ctx* ctx, mh_boundary* bd, const double* b, double*
         if (supplied) {
             MH_CUDA(ctx, cudaMemcpyAsync(ws.r.p, r0, n * 8, cudaMemcpyDeviceToDevice, st));
         } else {
-            k_gemv64<<<gemv_blocks(n), 256, 0, st>>>(bd->op.A64.p, x, ws.r.p, n, &gs->done);
+            gemv64(st, bd->op.A64.p, x, ws.r.p, n, &gs->done);
             MH_LAUNCHED(ctx);
             k_gsub<<<ew, 256, 0, st>>>(b, ws.r.p, n, &gs->done);
             MH_LAUNCHED(ctx);
@@ -1747,10 +1848,9 @@ mh_status gmres_run_graph(mh_ctx* ctx, mh_boundary* bd, const double* b, double*
         for (int k = 0; k < m; ++k) {
             const int k1 = k + 1;
             if (mixed)
-                k_gemv32<<<gemv_blocks(n), 256, 0, st>>>(bd->op.A32.p, ws.v32.p, ws.w.p, n, &gs->skip);
+                gemv32(st, bd->op.A32.p, ws.v32.p, ws.w.p, n, &gs->skip);
             else
-                k_gemv64<<<gemv_blocks(n), 256, 0, st>>>(bd->op.A64.p, ws.V.p + (int64_t)k * n, ws.w.p, n,
-                                                         &gs->skip);
+                gemv64(st, bd->op.A64.p, ws.V.p + (int64_t)k * n, ws.w.p, n, &gs->skip);
             MH_LAUNCHED(ctx);
             const size_t shm = (size_t)(k1 + ARN_ROWS) * sizeof(double);
             k_arn_dots<<<SL, 256, 0, st>>>(ws.V.p, ws.w.p, n, k1, ws.P1.p, &gs->skip);

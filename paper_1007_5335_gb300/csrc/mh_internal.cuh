@@ -28,6 +28,7 @@ struct mh_ctx {
     std::string err;
     int64_t launches = 0;
     bool profiling = false;
+    bool capturing = false;   // inside a batch step: no cooperative launches
     std::map<std::string, prof_region> prof;
     ~mh_ctx();
 };

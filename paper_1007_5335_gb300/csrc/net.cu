@@ -1151,7 +1151,10 @@ mh_status warm_start_run(mh_ctx* ctx, mh_boundary* b, double alpha, mh_net* net,
             net->yout.p, net->tw.p, net->d_nn.p, net->d_off.p, net->K, r0, scal, net->gy, b->warm_dir.p);
         MH_LAUNCHED(ctx);
     }
-    MH_TRY(bie_apply(ctx, b, b->warm_dir.p, b->warm_w.p, prec));
+    // binary64 image of the direction: r0 = r - c w is handed to GMRES as the residual of x0, and
+    // a binary32 operator would leave an error of ~1e-7 |A| |c delta| in it (above the tolerance)
+    (void)prec;
+    MH_TRY(bie_apply(ctx, b, b->warm_dir.p, b->warm_w.p, MH_PREC_FP64));
     k_dot2<<<1, 1024, 0, st>>>(r0, b->warm_w.p, n, scal);
     MH_LAUNCHED(ctx);
     k_line<<<mh_grid(n, 256), 256, 0, st>>>(sigma, b->warm_dir.p, r0, b->warm_w.p, scal, n, x0, r0, save, c_dev);

@@ -26,6 +26,8 @@
 #include <tuple>
 
 #include "bessel.cuh"
+#include <cooperative_groups.h>
+
 #include "mh_internal.cuh"
 
 namespace {
@@ -426,6 +428,115 @@ __global__ void __launch_bounds__(256) k_l2l_level(const TOP* __restrict__ ops, 
     }
 }
 
+// ---- the whole M2M or L2L chain of a pass in one cooperative launch (binary32) ----
+// Levels in execution order; every block stages, once, the four operators of each level on
+// which it has a chunk of LEVEL_PB parents, then the levels run in order with a grid-wide
+// barrier between them (a level reads what the previous one wrote).  Same arithmetic and
+// summation order as k_m2m_level / k_l2l_level with all four operators resident.
+struct ChainLevel {
+    int64_t par0, n_par;   // slice of the concatenated parent / child arrays
+    Off4 off;              // the level's operators
+};
+
+template <int UP>
+__global__ void __launch_bounds__(256) k_chain_coop(const float4* __restrict__ ops, const ChainLevel* __restrict__ lv,
+                                                    int n_lv, const int32_t* __restrict__ par,
+                                                    const int32_t* __restrict__ child, int P, int64_t base,
+                                                    double* vec) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lda = P + 1;
+    const int lvl_f4 = (4 * P * lda + 3) / 4;                   // one level's operators, in float4
+    float* sOps = reinterpret_cast<float*>(smem_raw);          // n_lv x (4 x P x lda, padded to 16 B)
+    float* sX = sOps + (size_t)n_lv * 4 * lvl_f4;               // LEVEL_PB x 4 x lda
+    float* red = sX + LEVEL_PB * 4 * lda;                        // 4 x LEVEL_PB x P
+    // ops holds every level's four operators already in this layout: straight 16-byte copies,
+    // eight loads in flight per thread
+    float4* s4 = reinterpret_cast<float4*>(sOps);
+    for (int li = 0; li < n_lv; ++li) {
+        const int64_t nch = (lv[li].n_par + LEVEL_PB - 1) / LEVEL_PB;
+        if (blockIdx.x >= nch) continue;
+        const float4* src = ops + (size_t)li * lvl_f4;
+        float4* dst = s4 + (size_t)li * lvl_f4;
+        for (int e0 = threadIdx.x; e0 < lvl_f4; e0 += 8 * blockDim.x) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * blockDim.x;
+                v[u] = e < lvl_f4 ? __ldg(src + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * blockDim.x;
+                if (e < lvl_f4) dst[e] = v[u];
+            }
+        }
+    }
+    __syncthreads();
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    const int g = threadIdx.x / P, r = threadIdx.x - g * P;
+    for (int li = 0; li < n_lv; ++li) {
+        if (li > 0) grid.sync();
+        const int64_t n_par = lv[li].n_par;
+        const int32_t* lp = par + lv[li].par0;
+        const int32_t* lc = child + 4 * lv[li].par0;
+        const float* A = sOps + (size_t)li * 4 * lvl_f4;
+        for (int64_t ch = blockIdx.x; ch * LEVEL_PB < n_par; ch += gridDim.x) {
+            const int64_t p0 = ch * LEVEL_PB;
+            const int np = (int)min((int64_t)LEVEL_PB, n_par - p0);
+            __syncthreads();
+            if (UP) {
+                for (int e = threadIdx.x; e < LEVEL_PB * 4 * P; e += blockDim.x) {
+                    const int pp = e / (4 * P), rem = e - pp * 4 * P, c = rem / P, cc = rem - c * P;
+                    const int chd = pp < np ? lc[4 * (p0 + pp) + c] : -1;
+                    sX[(pp * 4 + c) * lda + cc] = chd >= 0 ? (float)vec[base + (int64_t)chd * P + cc] : 0.f;
+                }
+            } else {
+                for (int e = threadIdx.x; e < LEVEL_PB * P; e += blockDim.x) {
+                    const int pp = e / P, cc = e - pp * P;
+                    sX[pp * lda + cc] = pp < np ? (float)vec[base + (int64_t)lp[p0 + pp] * P + cc] : 0.f;
+                }
+            }
+            __syncthreads();
+            float acc[LEVEL_PB];
+#pragma unroll
+            for (int pp = 0; pp < LEVEL_PB; ++pp) acc[pp] = 0.f;
+            if (g < 4) {
+                const float* a = A + (g * P + r) * lda;
+                for (int cc = 0; cc < P; ++cc) {
+                    const float av = a[cc];
+#pragma unroll
+                    for (int pp = 0; pp < LEVEL_PB; ++pp)
+                        acc[pp] += av * (UP ? sX[(pp * 4 + g) * lda + cc] : sX[pp * lda + cc]);
+                }
+            }
+            if (UP) {
+                if (g < 4)
+#pragma unroll
+                    for (int pp = 0; pp < LEVEL_PB; ++pp) red[(g * LEVEL_PB + pp) * P + r] = acc[pp];
+                __syncthreads();
+                for (int o = threadIdx.x; o < np * P; o += blockDim.x) {
+                    const int pp = o / P, rr = o - pp * P;
+                    float t = red[pp * P + rr];
+                    for (int gg = 1; gg < 4; ++gg) t += red[(gg * LEVEL_PB + pp) * P + rr];
+                    vec[base + (int64_t)lp[p0 + pp] * P + rr] = (double)t;
+                }
+            } else if (g < 4) {
+#pragma unroll
+                for (int pp = 0; pp < LEVEL_PB; ++pp) {
+                    if (pp >= np) break;
+                    const int chd = lc[4 * (p0 + pp) + g];
+                    if (chd >= 0) vec[base + (int64_t)chd * P + r] += (double)acc[pp];
+                }
+            }
+        }
+    }
+}
+
+inline size_t coop_level_floats(int P) { return (size_t)(4 * P * (P + 1) + 3) / 4 * 4; }
+inline size_t coop_smem(int P, int n_lv) {
+    return ((size_t)n_lv * coop_level_floats(P) + (size_t)LEVEL_PB * 4 * (P + 1) + 4 * (size_t)LEVEL_PB * P) * 4;
+}
+
 // Shared memory of the level kernels for P and G (bytes, with TOP of size ts).
 inline size_t level_smem(int P, int G, size_t ts) {
     return ((size_t)G * P * (P + 1) + (size_t)LEVEL_PB * 4 * (P + 1) + (G > 1 ? (size_t)G * LEVEL_PB * P : 0)) * ts;
@@ -490,6 +601,17 @@ struct LevelChain {
     dbuf<int32_t> par, child;
 };
 
+// Device description of the whole chain for the cooperative binary32 kernel.
+struct CoopChain {
+    bool ok = false;                 // fits in shared memory and the grid can be co-resident
+    int n_lv = 0, grid = 0;
+    size_t smem = 0;
+    double flops_up = 0, bytes_up = 0, flops_down = 0, bytes_down = 0;
+    dbuf<ChainLevel> up, down;       // levels in execution order
+    dbuf<int32_t> par, child;        // concatenated over levels
+    dbuf<float> ops_up, ops_down;    // binary32 operators in the kernel's shared-memory layout
+};
+
 struct DipData;
 
 struct VolData {
@@ -510,6 +632,7 @@ struct VolData {
     std::vector<int> op_C;
     std::unique_ptr<Phase> p2m, m2l, out;
     std::vector<std::unique_ptr<LevelChain>> chain;   // by level
+    std::unique_ptr<CoopChain> coop;                  // the same chain for the cooperative kernel
     int64_t temp_len = 0;
     int64_t n_near_tables = 0;
 };
@@ -615,9 +738,32 @@ mh_status run_phase_on(mh_ctx* ctx, const TOP* ops, const int64_t* op_off, const
 
 inline Off4 offs4(const int64_t* o) { return Off4{{o[0], o[1], o[2], o[3]}}; }
 
+
 template <typename TOP>
-mh_status run_chain(mh_ctx* ctx, const std::vector<std::unique_ptr<LevelChain>>& chain, const TOP* ops, int P,
-                    int64_t m_base, int64_t l_base, double* vec, bool upward, const char* region) {
+mh_status run_chain(mh_ctx* ctx, const std::vector<std::unique_ptr<LevelChain>>& chain, const CoopChain* coop,
+                    const TOP* ops, int P, int64_t m_base, int64_t l_base, double* vec, bool upward,
+                    const char* region) {
+    if (sizeof(TOP) == 4 && coop && coop->ok && !ctx->capturing) {
+        prof_scope ps(ctx, region, upward ? coop->flops_up : coop->flops_down,
+                      upward ? coop->bytes_up : coop->bytes_down);
+        (void)ops;   // the chain's own copies of the binary32 operators
+        const float4* o = reinterpret_cast<const float4*>(upward ? coop->ops_up.p : coop->ops_down.p);
+        const ChainLevel* lv = upward ? coop->up.p : coop->down.p;
+        int n_lv = coop->n_lv;
+        const int32_t* par = coop->par.p;
+        const int32_t* child = coop->child.p;
+        int64_t base = upward ? m_base : l_base;
+        void* args[] = {(void*)&o, (void*)&lv, (void*)&n_lv, (void*)&par, (void*)&child, (void*)&P, (void*)&base,
+                        (void*)&vec};
+        if (upward)
+            MH_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_chain_coop<1>, coop->grid, 256, args, coop->smem,
+                                                     ctx->stream));
+        else
+            MH_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_chain_coop<0>, coop->grid, 256, args, coop->smem,
+                                                     ctx->stream));
+        MH_LAUNCHED(ctx);
+        return MH_OK;
+    }
     const int L = (int)chain.size();
     const int G = level_groups(P, sizeof(TOP));
     const size_t smem = level_smem(P, G, sizeof(TOP));
@@ -956,6 +1102,90 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
                                          ctx->stream));
             V->chain[l] = std::move(c);
         }
+        // the same chain for the cooperative binary32 kernel (levels finest first for M2M)
+        std::unique_ptr<CoopChain> cc(new CoopChain());
+        std::vector<ChainLevel> up;
+        std::vector<int32_t> cpar, cchild;
+        int64_t max_ch = 0;
+        for (int l = L - 1; l >= 2; --l) {
+            const LevelChain* c = V->chain[l].get();
+            if (!c) continue;
+            ChainLevel e;
+            e.par0 = (int64_t)cpar.size();
+            e.n_par = c->n_par;
+            for (int q4 = 0; q4 < 4; ++q4) e.off.v[q4] = c->m2m_off[q4];
+            up.push_back(e);
+            cpar.insert(cpar.end(), par[l].begin(), par[l].end());
+            cchild.insert(cchild.end(), chl[l].begin(), chl[l].end());
+            max_ch = std::max<int64_t>(max_ch, (c->n_par + LEVEL_PB - 1) / LEVEL_PB);
+            cc->flops_up += c->flops;
+            cc->bytes_up += c->bytes;
+        }
+        std::vector<ChainLevel> down(up.rbegin(), up.rend());
+        {
+            // operators of the downward chain: the L2L set of each level
+            int idx = 0;
+            for (int l = 2; l < L; ++l) {
+                const LevelChain* c = V->chain[l].get();
+                if (!c) continue;
+                for (int q4 = 0; q4 < 4; ++q4) down[idx].off.v[q4] = c->l2l_off[q4];
+                cc->flops_down += c->flops;
+                cc->bytes_down += c->bytes;
+                ++idx;
+            }
+        }
+        cc->n_lv = (int)up.size();
+        cc->smem = coop_smem(P, cc->n_lv);
+        int dev = 0, sms = 0, nb_up = 0, nb_down = 0, coop_attr = 0;
+        MH_CUDA(ctx, cudaGetDevice(&dev));
+        MH_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        MH_CUDA(ctx, cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, dev));
+        if (cc->n_lv > 0 && coop_attr && 4 * P <= 256 && cc->smem <= 200 * 1024) {
+            MH_CUDA(ctx, cudaFuncSetAttribute(k_chain_coop<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)cc->smem));
+            MH_CUDA(ctx, cudaFuncSetAttribute(k_chain_coop<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)cc->smem));
+            MH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_up, k_chain_coop<1>, 256, cc->smem));
+            MH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_down, k_chain_coop<0>, 256, cc->smem));
+            const int64_t cap = (int64_t)std::min(nb_up, nb_down) * sms;
+            if (cap > 0) {
+                cc->grid = (int)std::max<int64_t>(1, std::min<int64_t>(max_ch, cap));
+                MH_ALLOC(ctx, cc->up, up.size());
+                MH_ALLOC(ctx, cc->down, down.size());
+                MH_ALLOC(ctx, cc->par, cpar.size());
+                MH_ALLOC(ctx, cc->child, cchild.size());
+                MH_CUDA(ctx, cudaMemcpyAsync(cc->up.p, up.data(), up.size() * sizeof(ChainLevel), cudaMemcpyHostToDevice,
+                                             ctx->stream));
+                MH_CUDA(ctx, cudaMemcpyAsync(cc->down.p, down.data(), down.size() * sizeof(ChainLevel),
+                                             cudaMemcpyHostToDevice, ctx->stream));
+                MH_CUDA(ctx, cudaMemcpyAsync(cc->par.p, cpar.data(), cpar.size() * 4, cudaMemcpyHostToDevice,
+                                             ctx->stream));
+                MH_CUDA(ctx, cudaMemcpyAsync(cc->child.p, cchild.data(), cchild.size() * 4, cudaMemcpyHostToDevice,
+                                             ctx->stream));
+                // operators in the kernel's layout: level, child position, row (leading dimension P + 1)
+                const size_t lf = coop_level_floats(P);
+                std::vector<float> hu(lf * up.size(), 0.f), hd(lf * down.size(), 0.f);
+                auto fill = [&](std::vector<float>& h, const std::vector<ChainLevel>& lvls) {
+                    for (size_t li = 0; li < lvls.size(); ++li)
+                        for (int c4 = 0; c4 < 4; ++c4)
+                            for (int r = 0; r < P; ++r)
+                                for (int cc2 = 0; cc2 < P; ++cc2)
+                                    h[li * lf + ((size_t)c4 * P + r) * (P + 1) + cc2] =
+                                        (float)pool.data[lvls[li].off.v[c4] + (size_t)r * P + cc2];
+                };
+                fill(hu, up);
+                fill(hd, down);
+                MH_ALLOC(ctx, cc->ops_up, hu.size());
+                MH_ALLOC(ctx, cc->ops_down, hd.size());
+                MH_CUDA(ctx, cudaMemcpyAsync(cc->ops_up.p, hu.data(), hu.size() * 4, cudaMemcpyHostToDevice,
+                                             ctx->stream));
+                MH_CUDA(ctx, cudaMemcpyAsync(cc->ops_down.p, hd.data(), hd.size() * 4, cudaMemcpyHostToDevice,
+                                             ctx->stream));
+                MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+                cc->ok = true;
+            }
+        }
+        V->coop = std::move(cc);
         MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     }
     // near tables on the device, appended to the pool
@@ -1457,9 +1687,11 @@ static mh_status dipole_run(mh_ctx* ctx, VolData* V, DipData* D, const TOP* ops)
         return run_phase_on<TOP>(ctx, ops, D->d_op_off.p, D->d_op_C.p, D->vec.p, D->temp.p, ph, "dlp_fmm_contract");
     };
     MH_TRY(run(D->p2m.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain, ops, V->P, D->DM_off, D->DL_off, D->vec.p, true, "dlp_fmm_contract"));
+    MH_TRY(run_chain<TOP>(ctx, V->chain, V->coop.get(), ops, V->P, D->DM_off, D->DL_off, D->vec.p, true,
+                          "dlp_fmm_contract"));
     MH_TRY(run(D->m2l.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain, ops, V->P, D->DM_off, D->DL_off, D->vec.p, false, "dlp_fmm_contract"));
+    MH_TRY(run_chain<TOP>(ctx, V->chain, V->coop.get(), ops, V->P, D->DM_off, D->DL_off, D->vec.p, false,
+                          "dlp_fmm_contract"));
     MH_TRY(run(D->out.get()));
     return MH_OK;
 }
@@ -1528,9 +1760,11 @@ void volume_free(mh_tree* t) {
 template <typename TOP>
 static mh_status volume_run(mh_ctx* ctx, mh_tree* t, VolData* V, const TOP* ops) {
     MH_TRY(run_phase(ctx, V, ops, V->p2m.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain, ops, V->P, V->M_off, V->L_off, V->vec.p, true, "volume_contract"));
+    MH_TRY(run_chain<TOP>(ctx, V->chain, V->coop.get(), ops, V->P, V->M_off, V->L_off, V->vec.p, true,
+                          "volume_contract"));
     MH_TRY(run_phase(ctx, V, ops, V->m2l.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain, ops, V->P, V->M_off, V->L_off, V->vec.p, false, "volume_contract"));
+    MH_TRY(run_chain<TOP>(ctx, V->chain, V->coop.get(), ops, V->P, V->M_off, V->L_off, V->vec.p, false,
+                          "volume_contract"));
     MH_TRY(run_phase(ctx, V, ops, V->out.get()));
     return MH_OK;
 }
