@@ -168,11 +168,19 @@ __device__ void curve_eval_warp(const double* c, int N, double t, double out[6])
 }
 
 // K(y, x) = (1/alpha) K1(|y-x|/alpha) (y-x).n_y / |y-x|  (Section 3.2)
+// Beyond r = 45 alpha (binary64) or 30 alpha (binary32) a pair contributes K1(r/alpha) / alpha
+// < e^{-r/alpha} / alpha: below 1e-19 (1e-13) of the unit-distance value, far under the
+// rounding of the sums it enters, so the pair is skipped before K1 is evaluated.
+constexpr double MH_DL_CUT64 = 45.0;
+constexpr float MH_DL_CUT32 = 30.f;
+
 __device__ __forceinline__ double dl_kernel(double yx, double yy, double nx, double ny, double xx, double xy,
                                             double inv_alpha) {
     double dx = yx - xx, dy = yy - xy;
     double r = sqrt(dx * dx + dy * dy);
-    return mh_k1(r * inv_alpha) * inv_alpha * (dx * nx + dy * ny) / r;
+    const double z = r * inv_alpha;
+    if (z > MH_DL_CUT64) return 0.0;
+    return mh_k1(z) * inv_alpha * (dx * nx + dy * ny) / r;
 }
 
 // Trapezoid part of eq. discrete_sys (all curves), the own-curve Alpert window left
@@ -470,6 +478,7 @@ __device__ __forceinline__ float dl_kernel32(float dx, float dy, float nx, float
     const float r2 = dx * dx + dy * dy;
     const float rinv = rsqrtf(r2);
     const float z = r2 * rinv * inv_alpha;
+    if (z > MH_DL_CUT32) return 0.f;
     return mh_k1f(z) * inv_alpha * (dx * nx + dy * ny) * rinv;
 }
 

@@ -285,17 +285,47 @@ __global__ void k_apply(const TOP* __restrict__ ops, const int64_t* __restrict__
         }
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < nt * R; o += blockDim.x) {
-        const int tt = o / R, r = o % R;
-        const TOP* a = sA + r * lda;
-        const TOP* x = sX + tt * lda;
-        TOP acc = 0;
-        for (int cc = 0; cc < C; ++cc) acc += a[cc] * x[cc];
-        if (task_dst) {
-            double* y = vec_out + task_dst[t0 + tt] + r;
-            *y = accumulate ? *y + (double)acc : (double)acc;
-        } else {
-            temp[(int64_t)(t0 + tt) * R + r] = (double)acc;
+    // register tiles of 4 rows x 4 tasks: rows rg + RG i, tasks tg + TG j (strided so that the
+    // operator and source loads of a warp fall in distinct banks); 8 shared loads per 16 FMAs
+    const int RG = (R + 3) / 4, TG = (nt + 3) / 4;
+    for (int tile = threadIdx.x; tile < RG * TG; tile += blockDim.x) {
+        const int rg = tile % RG, tg = tile / RG;
+        TOP acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+        const TOP* a0 = sA + (rg + 0 * RG < R ? rg + 0 * RG : 0) * lda;
+        const TOP* a1 = sA + (rg + 1 * RG < R ? rg + 1 * RG : 0) * lda;
+        const TOP* a2 = sA + (rg + 2 * RG < R ? rg + 2 * RG : 0) * lda;
+        const TOP* a3 = sA + (rg + 3 * RG < R ? rg + 3 * RG : 0) * lda;
+        const TOP* x0 = sX + (tg + 0 * TG < nt ? tg + 0 * TG : 0) * lda;
+        const TOP* x1 = sX + (tg + 1 * TG < nt ? tg + 1 * TG : 0) * lda;
+        const TOP* x2 = sX + (tg + 2 * TG < nt ? tg + 2 * TG : 0) * lda;
+        const TOP* x3 = sX + (tg + 3 * TG < nt ? tg + 3 * TG : 0) * lda;
+        for (int cc = 0; cc < C; ++cc) {
+            const TOP av[4] = {a0[cc], a1[cc], a2[cc], a3[cc]};
+            const TOP xv[4] = {x0[cc], x1[cc], x2[cc], x3[cc]};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * xv[j];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = rg + i * RG;
+            if (r >= R) break;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int tt = tg + j * TG;
+                if (tt >= nt) break;
+                if (task_dst) {
+                    double* y = vec_out + task_dst[t0 + tt] + r;
+                    *y = accumulate ? *y + (double)acc[i][j] : (double)acc[i][j];
+                } else {
+                    temp[(int64_t)(t0 + tt) * R + r] = (double)acc[i][j];
+                }
+            }
         }
     }
 }
@@ -438,6 +468,8 @@ struct ChainLevel {
     Off4 off;              // the level's operators
 };
 
+constexpr int COOP_PB = 8;   // parents per chunk in the cooperative chain (short critical path per level)
+
 template <int UP>
 __global__ void __launch_bounds__(256) k_chain_coop(const float4* __restrict__ ops, const ChainLevel* __restrict__ lv,
                                                     int n_lv, const int32_t* __restrict__ par,
@@ -447,13 +479,13 @@ __global__ void __launch_bounds__(256) k_chain_coop(const float4* __restrict__ o
     const int lda = P + 1;
     const int lvl_f4 = (4 * P * lda + 3) / 4;                   // one level's operators, in float4
     float* sOps = reinterpret_cast<float*>(smem_raw);          // n_lv x (4 x P x lda, padded to 16 B)
-    float* sX = sOps + (size_t)n_lv * 4 * lvl_f4;               // LEVEL_PB x 4 x lda
-    float* red = sX + LEVEL_PB * 4 * lda;                        // 4 x LEVEL_PB x P
+    float* sX = sOps + (size_t)n_lv * 4 * lvl_f4;               // COOP_PB x 4 x lda
+    float* red = sX + COOP_PB * 4 * lda;                        // 4 x COOP_PB x P
     // ops holds every level's four operators already in this layout: straight 16-byte copies,
     // eight loads in flight per thread
     float4* s4 = reinterpret_cast<float4*>(sOps);
     for (int li = 0; li < n_lv; ++li) {
-        const int64_t nch = (lv[li].n_par + LEVEL_PB - 1) / LEVEL_PB;
+        const int64_t nch = (lv[li].n_par + COOP_PB - 1) / COOP_PB;
         if (blockIdx.x >= nch) continue;
         const float4* src = ops + (size_t)li * lvl_f4;
         float4* dst = s4 + (size_t)li * lvl_f4;
@@ -480,49 +512,70 @@ __global__ void __launch_bounds__(256) k_chain_coop(const float4* __restrict__ o
         const int32_t* lp = par + lv[li].par0;
         const int32_t* lc = child + 4 * lv[li].par0;
         const float* A = sOps + (size_t)li * 4 * lvl_f4;
-        for (int64_t ch = blockIdx.x; ch * LEVEL_PB < n_par; ch += gridDim.x) {
-            const int64_t p0 = ch * LEVEL_PB;
-            const int np = (int)min((int64_t)LEVEL_PB, n_par - p0);
+        for (int64_t ch = blockIdx.x; ch * COOP_PB < n_par; ch += gridDim.x) {
+            const int64_t p0 = ch * COOP_PB;
+            const int np = (int)min((int64_t)COOP_PB, n_par - p0);
             __syncthreads();
-            if (UP) {
-                for (int e = threadIdx.x; e < LEVEL_PB * 4 * P; e += blockDim.x) {
-                    const int pp = e / (4 * P), rem = e - pp * 4 * P, c = rem / P, cc = rem - c * P;
-                    const int chd = pp < np ? lc[4 * (p0 + pp) + c] : -1;
-                    sX[(pp * 4 + c) * lda + cc] = chd >= 0 ? (float)vec[base + (int64_t)chd * P + cc] : 0.f;
+            // gather with eight loads in flight per thread
+            const int ng = UP ? COOP_PB * 4 * P : COOP_PB * P;
+            for (int e0 = threadIdx.x; e0 < ng; e0 += 8 * blockDim.x) {
+                double v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    int64_t src = -1;
+                    if (e < ng) {
+                        if (UP) {
+                            const int pp = e / (4 * P), rem = e - pp * 4 * P, c = rem / P, cc = rem - c * P;
+                            const int chd = pp < np ? lc[4 * (p0 + pp) + c] : -1;
+                            if (chd >= 0) src = base + (int64_t)chd * P + cc;
+                        } else {
+                            const int pp = e / P, cc = e - pp * P;
+                            if (pp < np) src = base + (int64_t)lp[p0 + pp] * P + cc;
+                        }
+                    }
+                    v[u] = src >= 0 ? vec[src] : 0.0;
                 }
-            } else {
-                for (int e = threadIdx.x; e < LEVEL_PB * P; e += blockDim.x) {
-                    const int pp = e / P, cc = e - pp * P;
-                    sX[pp * lda + cc] = pp < np ? (float)vec[base + (int64_t)lp[p0 + pp] * P + cc] : 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    if (e >= ng) break;
+                    if (UP) {
+                        const int pp = e / (4 * P), rem = e - pp * 4 * P, c = rem / P, cc = rem - c * P;
+                        sX[(pp * 4 + c) * lda + cc] = (float)v[u];
+                    } else {
+                        const int pp = e / P, cc = e - pp * P;
+                        sX[pp * lda + cc] = (float)v[u];
+                    }
                 }
             }
             __syncthreads();
-            float acc[LEVEL_PB];
+            float acc[COOP_PB];
 #pragma unroll
-            for (int pp = 0; pp < LEVEL_PB; ++pp) acc[pp] = 0.f;
+            for (int pp = 0; pp < COOP_PB; ++pp) acc[pp] = 0.f;
             if (g < 4) {
                 const float* a = A + (g * P + r) * lda;
                 for (int cc = 0; cc < P; ++cc) {
                     const float av = a[cc];
 #pragma unroll
-                    for (int pp = 0; pp < LEVEL_PB; ++pp)
+                    for (int pp = 0; pp < COOP_PB; ++pp)
                         acc[pp] += av * (UP ? sX[(pp * 4 + g) * lda + cc] : sX[pp * lda + cc]);
                 }
             }
             if (UP) {
                 if (g < 4)
 #pragma unroll
-                    for (int pp = 0; pp < LEVEL_PB; ++pp) red[(g * LEVEL_PB + pp) * P + r] = acc[pp];
+                    for (int pp = 0; pp < COOP_PB; ++pp) red[(g * COOP_PB + pp) * P + r] = acc[pp];
                 __syncthreads();
                 for (int o = threadIdx.x; o < np * P; o += blockDim.x) {
                     const int pp = o / P, rr = o - pp * P;
                     float t = red[pp * P + rr];
-                    for (int gg = 1; gg < 4; ++gg) t += red[(gg * LEVEL_PB + pp) * P + rr];
+                    for (int gg = 1; gg < 4; ++gg) t += red[(gg * COOP_PB + pp) * P + rr];
                     vec[base + (int64_t)lp[p0 + pp] * P + rr] = (double)t;
                 }
             } else if (g < 4) {
 #pragma unroll
-                for (int pp = 0; pp < LEVEL_PB; ++pp) {
+                for (int pp = 0; pp < COOP_PB; ++pp) {
                     if (pp >= np) break;
                     const int chd = lc[4 * (p0 + pp) + g];
                     if (chd >= 0) vec[base + (int64_t)chd * P + r] += (double)acc[pp];
@@ -534,7 +587,7 @@ __global__ void __launch_bounds__(256) k_chain_coop(const float4* __restrict__ o
 
 inline size_t coop_level_floats(int P) { return (size_t)(4 * P * (P + 1) + 3) / 4 * 4; }
 inline size_t coop_smem(int P, int n_lv) {
-    return ((size_t)n_lv * coop_level_floats(P) + (size_t)LEVEL_PB * 4 * (P + 1) + 4 * (size_t)LEVEL_PB * P) * 4;
+    return ((size_t)n_lv * coop_level_floats(P) + (size_t)COOP_PB * 4 * (P + 1) + 4 * (size_t)COOP_PB * P) * 4;
 }
 
 // Shared memory of the level kernels for P and G (bytes, with TOP of size ts).
@@ -1117,7 +1170,7 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
             up.push_back(e);
             cpar.insert(cpar.end(), par[l].begin(), par[l].end());
             cchild.insert(cchild.end(), chl[l].begin(), chl[l].end());
-            max_ch = std::max<int64_t>(max_ch, (c->n_par + LEVEL_PB - 1) / LEVEL_PB);
+            max_ch = std::max<int64_t>(max_ch, (c->n_par + COOP_PB - 1) / COOP_PB);
             cc->flops_up += c->flops;
             cc->bytes_up += c->bytes;
         }
@@ -1320,7 +1373,9 @@ __global__ void __launch_bounds__(NEAR_T) k_dip_near64(
                 for (int e = g; e < m; e += groups) {
                     const double dx = sp[e].x - px, dy = sp[e].y - py;
                     const double r = sqrt(dx * dx + dy * dy);
-                    if (r > 0.0) acc += mh_k1(r * inv_alpha) * inv_alpha * (dx * sn[e].x + dy * sn[e].y) / r * sw[e];
+                    // pairs beyond 45 alpha are below the binary64 rounding of the sum (e^{-45})
+                    if (r > 0.0 && r * inv_alpha <= 45.0)
+                        acc += mh_k1(r * inv_alpha) * inv_alpha * (dx * sn[e].x + dy * sn[e].y) / r * sw[e];
                 }
         }
     }
@@ -1371,10 +1426,10 @@ __global__ void __launch_bounds__(NT) k_dip_near32(
                     const float4 v = s4[e];
                     const float dx = v.x - tx, dy = v.y - ty;
                     const float r2 = dx * dx + dy * dy;
-                    if (r2 > 0.f) {
-                        const float rinv = rsqrtf(r2);
-                        pt += mh_k1f(r2 * rinv * inv_alpha) * inv_alpha * (dx * v.z + dy * v.w) * rinv * sw[e];
-                    }
+                    const float rinv = rsqrtf(r2);
+                    const float z = r2 * rinv * inv_alpha;
+                    if (r2 > 0.f && z <= 30.f)   // beyond 30 alpha: below the binary32 rounding of the sum
+                        pt += mh_k1f(z) * inv_alpha * (dx * v.z + dy * v.w) * rinv * sw[e];
                 }
                 acc += (double)pt;
             }
