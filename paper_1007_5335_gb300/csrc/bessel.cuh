@@ -76,7 +76,9 @@ __device__ __forceinline__ float mh_k0f(float z) {
     return __expf(-z) * rsqrtf(z) * mh_clenshaw_f(mh_cheb_k0_f, MH_CHEB_K0_N32, 4.f / z - 1.f);
 }
 
-__device__ __forceinline__ float mh_k1f(float z) {
+// K1 with 1/z supplied by the caller (the pair kernels have it from their rsqrt: 1/z = alpha/r),
+// so that neither branch divides.
+__device__ __forceinline__ float mh_k1f_r(float z, float zinv) {
     if (z <= 2.f) {
         const float y = 0.25f * z * z;
         float s_i = mh_ser_i1_f[MH_BESSEL_NSER_F - 1], s_p = mh_ser_k1p_f[MH_BESSEL_NSER_F - 1];
@@ -85,7 +87,9 @@ __device__ __forceinline__ float mh_k1f(float z) {
             s_i = fmaf(s_i, y, mh_ser_i1_f[k]);
             s_p = fmaf(s_p, y, mh_ser_k1p_f[k]);
         }
-        return 1.f / z + __logf(0.5f * z) * (0.5f * z) * s_i - 0.25f * z * s_p;
+        return zinv + __logf(0.5f * z) * (0.5f * z) * s_i - 0.25f * z * s_p;
     }
-    return __expf(-z) * rsqrtf(z) * mh_clenshaw_f(mh_cheb_k1_f, MH_CHEB_K1_N32, 4.f / z - 1.f);
+    return __expf(-z) * rsqrtf(z) * mh_clenshaw_f(mh_cheb_k1_f, MH_CHEB_K1_N32, fmaf(4.f, zinv, -1.f));
 }
+
+__device__ __forceinline__ float mh_k1f(float z) { return mh_k1f_r(z, __frcp_rn(z)); }

@@ -474,12 +474,13 @@ __global__ void k_weights32(const double* __restrict__ sigma, const double* __re
 }
 
 // (1/alpha) K1(r/alpha) (y-x).n / r in binary32 from offsets d = y - x
-__device__ __forceinline__ float dl_kernel32(float dx, float dy, float nx, float ny, float inv_alpha) {
+// alpha_f = 1 / inv_alpha, formed once by the caller: 1/z = alpha / r needs no division.
+__device__ __forceinline__ float dl_kernel32(float dx, float dy, float nx, float ny, float inv_alpha, float alpha_f) {
     const float r2 = dx * dx + dy * dy;
     const float rinv = rsqrtf(r2);
     const float z = r2 * rinv * inv_alpha;
     if (z > MH_DL_CUT32) return 0.f;
-    return mh_k1f(z) * inv_alpha * (dx * nx + dy * ny) * rinv;
+    return mh_k1f_r(z, alpha_f * rinv) * inv_alpha * (dx * nx + dy * ny) * rinv;
 }
 
 // Coarse trapezoid sum in binary32: sources staged through shared memory in tiles of
@@ -491,6 +492,7 @@ __global__ void __launch_bounds__(MH_TILE) k_dlp_coarse32(const double* __restri
                                                           const int32_t* __restrict__ curve_of,
                                                           const double2* __restrict__ tc, int64_t ns, float inv_alpha,
                                                           double pref, double* out) {
+    const float alpha_f = 1.f / inv_alpha;
     __shared__ float4 s4[MH_TILE];
     __shared__ float sw[MH_TILE];
     __shared__ int sk[MH_TILE];
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(MH_TILE) k_dlp_coarse32(const double* __restri
             for (int i = 0; i < cnt; ++i) {
                 if ((mask >> sk[i]) & 1u) continue;
                 const float4 v = s4[i];
-                part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha) * sw[i];
+                part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha, alpha_f) * sw[i];
             }
             acc += (double)part;
         }
@@ -549,6 +551,7 @@ __global__ void k_dlp_fine32_blk(const double* __restrict__ xy, const int32_t* _
                                  const float* __restrict__ wf, const int64_t* __restrict__ foff,
                                  const int64_t* __restrict__ coff, const double2* __restrict__ cc, float inv_alpha,
                                  double pref, double* out) {
+    const float alpha_f = 1.f / inv_alpha;
     __shared__ double red[8];
     const int64_t p = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -564,7 +567,7 @@ __global__ void k_dlp_fine32_blk(const double* __restrict__ xy, const int32_t* _
         float part = 0.f;
         for (int64_t f = f0 + lane; f < f1; f += 32) {
             const float4 v = fine32[f];
-            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha) * wf[f];
+            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha, alpha_f) * wf[f];
         }
         acc += (double)part;
     }
@@ -610,6 +613,7 @@ __global__ void k_dlp_fine32(const double* __restrict__ xy, const int32_t* __res
                              const float* __restrict__ wf, const int64_t* __restrict__ foff,
                              const int64_t* __restrict__ coff, const double2* __restrict__ cc, float inv_alpha,
                              double pref, double* out) {
+    const float alpha_f = 1.f / inv_alpha;
     const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (p >= npairs) return;
     const int lane = threadIdx.x & 31;
@@ -625,7 +629,7 @@ __global__ void k_dlp_fine32(const double* __restrict__ xy, const int32_t* __res
         float part = 0.f;
         for (int64_t f = f0 + lane; f < f1; f += 32) {
             const float4 v = fine32[f];
-            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha) * wf[f];
+            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha, alpha_f) * wf[f];
         }
         acc += (double)part;
     }
@@ -1237,6 +1241,7 @@ __global__ void k_dlp_fine_corr32(const double* __restrict__ xy, const int32_t* 
                                   const double2* __restrict__ cc, const float4* __restrict__ src32,
                                   const float* __restrict__ w32, const double2* __restrict__ tc,
                                   const int32_t* __restrict__ off, float inv_alpha, double pref, double* out) {
+    const float alpha_f = 1.f / inv_alpha;
     const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (p >= npairs) return;
     const int lane = threadIdx.x & 31;
@@ -1252,7 +1257,7 @@ __global__ void k_dlp_fine_corr32(const double* __restrict__ xy, const int32_t* 
         float part = 0.f;
         for (int64_t f = f0 + lane; f < f1; f += 32) {
             const float4 v = fine32[f];
-            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha) * wf[f];
+            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha, alpha_f) * wf[f];
         }
         acc += (double)part;
     }
@@ -1264,7 +1269,7 @@ __global__ void k_dlp_fine_corr32(const double* __restrict__ xy, const int32_t* 
         float part = 0.f;
         for (int64_t s = s0 + lane; s < s1; s += 32) {
             const float4 v = src32[s];
-            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha) * w32[s];
+            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha, alpha_f) * w32[s];
         }
         acc -= (double)part;
     }
@@ -1503,6 +1508,18 @@ static void gemv64(cudaStream_t st, const double* A, const double* x, double* y,
         k_gemv64<<<gemv_blocks(n), 256, 0, st>>>(A, x, y, n, gate);
 }
 
+mh_status bie_apply64_gated(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, const int* gate) {
+    prof_scope ps(ctx, "bie_gemv", 2.0 * b->n * b->n, 8.0 * b->n * b->n + 16.0 * b->n);
+    gemv64(ctx->stream, b->op.A64.p, x, y, b->n, gate);
+    MH_LAUNCHED(ctx);
+    return MH_OK;
+}
+
+const double* gmres_final_residual(mh_boundary* b, mh_precision prec, bool graph) {
+    return (graph || prec == MH_PREC_MIXED) ? b->ws.r.p : b->ws.w.p;
+}
+
+
 mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec) {
     if (prec == MH_PREC_MIXED) {
         MH_TRY(ensure_fp32(ctx, b));
@@ -1628,6 +1645,8 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
     mh_gmres_info inf{0, 0, 0.0, 0, 0.0};
     if (bnorm == 0.0) {
         MH_CUDA(ctx, cudaMemsetAsync(x, 0, n * 8, ctx->stream));
+        MH_CUDA(ctx, cudaMemsetAsync(ws.r.p, 0, n * 8, ctx->stream));   // residual of x = 0
+        MH_CUDA(ctx, cudaMemsetAsync(ws.w.p, 0, n * 8, ctx->stream));
         inf.converged = 1;
         if (info) *info = inf;
         return MH_OK;
@@ -1762,8 +1781,10 @@ __global__ void k_sweep_begin(gmres_dev* gs, double tol, int mixed, int may_acce
     if (gs->done) return;
     const double rn = gs->rn, bn = gs->bnorm;
     if (bn == 0.0) {
-        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
             x[e] = 0.0;
+            const_cast<double*>(r)[e] = 0.0;   // the residual of x = 0 for b = 0
+        }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             gs->done = gs->skip = gs->converged = 1;
             gs->rel = 0.0;

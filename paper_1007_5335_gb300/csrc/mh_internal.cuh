@@ -220,6 +220,11 @@ struct mh_problem {
     // batched stepping (mh_batch_step): sync-free GMRES with its state in gstat (device)
     bool graph_mode = false;
     gmres_dev* gstat = nullptr;
+    // residual recycling: the density, right-hand side and binary64 residual the last step
+    // ended with; b - A sigma for an unchanged sigma is b - rc_b + rc_r (no operator product)
+    bool rc_valid = false;
+    dbuf<double> rc_sigma, rc_b, rc_r, r_start;
+    dbuf<int> rc_same;
     ~mh_problem() {
         if (c_host) cudaFreeHost(c_host);
     }
@@ -228,9 +233,10 @@ struct mh_problem {
 // ---- net.cu ----
 // Initial guess for A x = rhs (see mh_warm_start in mh.h); c_dev receives the step length.
 // save (nullable) receives the incoming sigma before x0 is written.
+// r_ready: r0 already holds rhs - A sigma (binary64).
 mh_status warm_start_run(mh_ctx* ctx, mh_boundary* bnd, double alpha, struct mh_net* net, int mode, int arith,
                          const double* sigma, const double* sigma_prev2, const double* rhs, double* x0, double* r0,
-                         mh_precision prec, double* c_dev, double* save);
+                         mh_precision prec, double* c_dev, double* save, bool r_ready = false);
 bool net_matches(const struct mh_net* net, const mh_boundary* b);
 // Workspace of the SECANT / LEARNED starts (allocated once per boundary).
 mh_status warm_start_prepare(mh_ctx* ctx, mh_boundary* b);
@@ -238,6 +244,10 @@ mh_status warm_start_prepare(mh_ctx* ctx, mh_boundary* b);
 // ---- boundary.cu ----
 mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha);
 mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec);
+// y = A x in binary64, skipped when *gate != 0 (gate nullable).
+mh_status bie_apply64_gated(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, const int* gate);
+// Where the last solve left the binary64 residual rhs - A x of its result.
+const double* gmres_final_residual(mh_boundary* b, mh_precision prec, bool graph);
 // Everything a sync-free solve in precision prec needs (binary32 operator copy).
 mh_status bie_prepare(mh_ctx* ctx, mh_boundary* b, mh_precision prec);
 mh_status dlp_classify(mh_ctx* ctx, mh_boundary* b, const double* xy_dev, int64_t n, dlp_targets* tg);

@@ -1117,7 +1117,7 @@ mh_status warm_start_prepare(mh_ctx* ctx, mh_boundary* b) {
 // Shared by mh_warm_start and the time step.  r0 first holds r = rhs - A sigma (binary64).
 mh_status warm_start_run(mh_ctx* ctx, mh_boundary* b, double alpha, mh_net* net, int mode, int arith,
                          const double* sigma, const double* sigma_prev2, const double* rhs, double* x0, double* r0,
-                         mh_precision prec, double* c_dev, double* save) {
+                         mh_precision prec, double* c_dev, double* save, bool r_ready) {
     cudaStream_t st = ctx->stream;
     const int64_t n = b->n;
     MH_TRY(bie_assemble(ctx, b, alpha));
@@ -1128,9 +1128,11 @@ mh_status warm_start_run(mh_ctx* ctx, mh_boundary* b, double alpha, mh_net* net,
         return MH_OK;
     }
     prof_scope ps(ctx, "warm_start");
-    MH_TRY(bie_apply(ctx, b, sigma, r0, MH_PREC_FP64));
-    k_resid<<<mh_grid(n, 256), 256, 0, st>>>(rhs, r0, n);
-    MH_LAUNCHED(ctx);
+    if (!r_ready) {
+        MH_TRY(bie_apply(ctx, b, sigma, r0, MH_PREC_FP64));
+        k_resid<<<mh_grid(n, 256), 256, 0, st>>>(rhs, r0, n);
+        MH_LAUNCHED(ctx);
+    }
     if (mode == MH_WARM_PREVIOUS) {
         if (x0 != sigma) MH_CUDA(ctx, cudaMemcpyAsync(x0, sigma, n * 8, cudaMemcpyDeviceToDevice, st));
         if (c_dev) MH_CUDA(ctx, cudaMemsetAsync(c_dev, 0, 8, st));

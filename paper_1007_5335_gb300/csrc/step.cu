@@ -44,6 +44,22 @@ __global__ void k_form_B_gear(const double* __restrict__ u, const double* __rest
     B[i] = v;
 }
 
+// same[0] stays set (nonzero) only if a == b element by element.
+__global__ void k_rc_compare(const double* __restrict__ a, const double* __restrict__ b, int64_t n, int* same) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (a[i] != b[i]) *same = 0;
+}
+
+// r = rhs - rhs_prev + r_prev when the density is the one the previous step ended with
+// (rhs_prev - A sigma = r_prev), else r = rhs - Ax (Ax computed for that case).
+__global__ void k_rc_resid(const double* __restrict__ rhs, const double* __restrict__ ax,
+                           const double* __restrict__ rhs_prev, const double* __restrict__ r_prev,
+                           const int* __restrict__ same, int64_t n, double* r) {
+    const bool s = *same != 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = s ? (rhs[i] - rhs_prev[i]) + r_prev[i] : rhs[i] - ax[i];
+}
+
 __global__ void k_rhs(const double* __restrict__ f, const double* __restrict__ ug, double c, int64_t n, double* rhs) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) rhs[i] = c * (f[i] - ug[i]);
@@ -198,6 +214,13 @@ extern "C" mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* 
     MH_ALLOC(ctx, P->Ug, bnd->n);
     MH_ALLOC(ctx, P->rhs, bnd->n);
     MH_CUDA(ctx, cudaMemsetAsync(P->rhs.p, 0, bnd->n * 8, st));
+    MH_ALLOC(ctx, P->rc_sigma, bnd->n);
+    MH_ALLOC(ctx, P->rc_b, bnd->n);
+    MH_ALLOC(ctx, P->rc_r, bnd->n);
+    MH_ALLOC(ctx, P->r_start, bnd->n);
+    MH_ALLOC(ctx, P->rc_same, 1);
+    MH_CUDA(ctx, cudaMemsetAsync(P->rc_b.p, 0, bnd->n * 8, st));
+    MH_CUDA(ctx, cudaMemsetAsync(P->rc_r.p, 0, bnd->n * 8, st));
     MH_ALLOC(ctx, P->Uh, std::max<int64_t>(P->n_inside, 1));
     // operators: boundary (alpha) and volume (alpha, p) -- built once here
     MH_TRY(bie_assemble(ctx, bnd, P->alpha));
@@ -249,6 +272,30 @@ extern "C" mh_status mh_problem_rhs(mh_ctx* ctx, const mh_problem* p, double* rh
     return MH_OK;
 }
 
+// r = rhs - A sigma in binary64 for the GMRES start; the operator product is skipped (on the
+// device) when sigma is bit for bit the density the previous step ended with.
+static mh_status start_residual(mh_ctx* ctx, ProblemImpl* P, const double* sigma, double* r) {
+    cudaStream_t st = ctx->stream;
+    mh_boundary* b = P->bnd;
+    const int64_t n = b->n;
+    MH_TRY(bie_assemble(ctx, b, P->alpha));
+    const int grid = mh_grid(n, 256) < 152 * 4 ? mh_grid(n, 256) : 152 * 4;
+    if (P->rc_valid) {
+        MH_CUDA(ctx, cudaMemsetAsync(P->rc_same.p, 1, sizeof(int), st));
+        k_rc_compare<<<grid, 256, 0, st>>>(sigma, P->rc_sigma.p, n, P->rc_same.p);
+        MH_LAUNCHED(ctx);
+        MH_TRY(bie_apply64_gated(ctx, b, sigma, r, P->rc_same.p));
+        k_rc_resid<<<grid, 256, 0, st>>>(P->rhs.p, r, P->rc_b.p, P->rc_r.p, P->rc_same.p, n, r);
+        MH_LAUNCHED(ctx);
+    } else {
+        MH_TRY(bie_apply64_gated(ctx, b, sigma, r, nullptr));
+        MH_CUDA(ctx, cudaMemsetAsync(P->rc_same.p, 0, sizeof(int), st));
+        k_rc_resid<<<grid, 256, 0, st>>>(P->rhs.p, r, P->rc_b.p, P->rc_r.p, P->rc_same.p, n, r);
+        MH_LAUNCHED(ctx);
+    }
+    return MH_OK;
+}
+
 // Everything after the right-hand side B (P->B) has been formed.
 static mh_status step_solve(mh_ctx* ctx, ProblemImpl* P, const double* f_next_dev, double* u_next_dev,
                             double* sigma_dev, double gmres_tol, mh_precision prec, mh_step_info* info) {
@@ -267,22 +314,38 @@ static mh_status step_solve(mh_ctx* ctx, ProblemImpl* P, const double* f_next_de
     const int mode = P->warm_mode;
     if (mode == MH_WARM_ZERO) {
         MH_CUDA(ctx, cudaMemsetAsync(sigma_dev, 0, ng * 8, st));
-    } else if (mode == MH_WARM_SECANT && !P->have_prev) {
-        MH_CUDA(ctx, cudaMemcpyAsync(P->sig_prev.p, sigma_dev, ng * 8, cudaMemcpyDeviceToDevice, st));
-        P->have_prev = true;
     } else if (mode == MH_WARM_SECANT || mode == MH_WARM_LEARNED) {
-        double* keep = mode == MH_WARM_SECANT ? P->sig_prev.p : nullptr;
-        MH_TRY(warm_start_run(ctx, b, P->alpha, P->net, mode, P->warm_arith, sigma_dev, keep, P->rhs.p, sigma_dev,
-                              P->r0.p, prec, P->c_dev.p, keep));
-        MH_CUDA(ctx, cudaMemcpyAsync(P->c_host, P->c_dev.p, 8, cudaMemcpyDeviceToHost, st));
+        MH_TRY(start_residual(ctx, P, sigma_dev, P->r0.p));
+        if (mode == MH_WARM_SECANT && !P->have_prev) {
+            MH_CUDA(ctx, cudaMemcpyAsync(P->sig_prev.p, sigma_dev, ng * 8, cudaMemcpyDeviceToDevice, st));
+            P->have_prev = true;
+        } else {
+            double* keep = mode == MH_WARM_SECANT ? P->sig_prev.p : nullptr;
+            MH_TRY(warm_start_run(ctx, b, P->alpha, P->net, mode, P->warm_arith, sigma_dev, keep, P->rhs.p,
+                                  sigma_dev, P->r0.p, prec, P->c_dev.p, keep, true));
+            MH_CUDA(ctx, cudaMemcpyAsync(P->c_host, P->c_dev.p, 8, cudaMemcpyDeviceToHost, st));
+            have_c = true;
+        }
         r0 = P->r0.p;
-        have_c = true;
+    } else {   // previous-step start
+        MH_TRY(start_residual(ctx, P, sigma_dev, P->r_start.p));
+        r0 = P->r_start.p;
     }
     if (P->graph_mode) {
         // sync-free solve: the result stays in P->gstat until the caller reads it back
         MH_TRY(gmres_run_graph(ctx, b, P->rhs.p, sigma_dev, gmres_tol, prec, r0, P->gstat));
     }
     mh_status s = P->graph_mode ? MH_OK : gmres_run(ctx, b, P->rhs.p, sigma_dev, gmres_tol, 100, prec, &gi, r0);
+    // keep what the next step needs to skip its first binary64 operator product
+    if (s == MH_OK) {
+        MH_CUDA(ctx, cudaMemcpyAsync(P->rc_sigma.p, sigma_dev, ng * 8, cudaMemcpyDeviceToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(P->rc_b.p, P->rhs.p, ng * 8, cudaMemcpyDeviceToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(P->rc_r.p, gmres_final_residual(b, prec, P->graph_mode), ng * 8,
+                                     cudaMemcpyDeviceToDevice, st));
+        P->rc_valid = true;
+    } else {
+        P->rc_valid = false;
+    }
     if (info && !P->graph_mode) {
         info->gmres_iterations = gi.iterations;
         info->gmres_rel_residual = gi.rel_residual;

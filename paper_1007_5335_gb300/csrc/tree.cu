@@ -404,9 +404,15 @@ __global__ void k_locate(Maps M, const int32_t* __restrict__ box_leaf, double x0
     leaf[i] = res;
 }
 
-__global__ void k_interp(const int32_t* __restrict__ boxes, const int32_t* __restrict__ leaf_box, int q,
-                         double x0, double y0, double W, const double* __restrict__ xi, const double* __restrict__ vals,
-                         const double* __restrict__ xy, const int32_t* __restrict__ leaf, int64_t n, double* out) {
+// Leaf interpolant at n points: tensor Lagrange basis on the leaf's q x q Gauss-Legendre nodes
+// in barycentric form l_a(s) = bw_a prod_{m != a} (s - xi_m) (bw_a = 1 / prod_{m != a}
+// (xi_a - xi_m), precomputed), the products by prefix and suffix sweeps: no division on the
+// slow binary64 pipe.
+template <int Q>
+__global__ void k_interp(const int32_t* __restrict__ boxes, const int32_t* __restrict__ leaf_box, double x0, double y0,
+                         double W, const double* __restrict__ xi, const double* __restrict__ bw,
+                         const double* __restrict__ vals, const double* __restrict__ xy, const int32_t* __restrict__ leaf,
+                         int64_t n, double* out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int lf = leaf[i];
@@ -415,30 +421,44 @@ __global__ void k_interp(const int32_t* __restrict__ boxes, const int32_t* __res
     const double w = W / (double)(1 << l);
     const double cx = x0 + (boxes[3 * b + 1] + 0.5) * w, cy = y0 + (boxes[3 * b + 2] + 0.5) * w;
     const double sx = (xy[2 * i] - cx) * (2.0 / w), sy = (xy[2 * i + 1] - cy) * (2.0 / w);
-    double lx[16], ly[16];
-    for (int a = 0; a < q; ++a) {
-        double px = 1.0, py = 1.0;
-        for (int m = 0; m < q; ++m) {
-            if (m == a) continue;
-            px *= (sx - xi[m]) / (xi[a] - xi[m]);
-            py *= (sy - xi[m]) / (xi[a] - xi[m]);
-        }
+    double dxv[Q], dyv[Q], lx[Q], ly[Q];
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+        dxv[m] = sx - xi[m];
+        dyv[m] = sy - xi[m];
+    }
+    double px = 1.0, py = 1.0;   // prefix products
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
         lx[a] = px;
         ly[a] = py;
+        px *= dxv[a];
+        py *= dyv[a];
     }
-    const double* v = vals + (int64_t)lf * q * q;
+    px = 1.0;
+    py = 1.0;                    // suffix products
+#pragma unroll
+    for (int a = Q - 1; a >= 0; --a) {
+        lx[a] *= px * bw[a];
+        ly[a] *= py * bw[a];
+        px *= dxv[a];
+        py *= dyv[a];
+    }
+    const double* v = vals + (int64_t)lf * Q * Q;
     double acc = 0.0;
-    for (int a = 0; a < q; ++a) {
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
         double row = 0.0;
-        for (int c = 0; c < q; ++c) row += v[a * q + c] * lx[c];
-        acc += ly[a] * row;
+#pragma unroll
+        for (int c = 0; c < Q; ++c) row = fma(v[a * Q + c], lx[c], row);
+        acc = fma(ly[a], row, acc);
     }
     out[i] = acc;
 }
 
 struct TreeExtra {
     Maps maps;
-    dbuf<double> xi;
+    dbuf<double> xi, bw;   // Gauss-Legendre nodes on [-1, 1] and their barycentric weights
 };
 
 }  // namespace
@@ -581,9 +601,21 @@ extern "C" mh_status mh_tree_build(mh_ctx* ctx, const double* box3_host, int q, 
             }
         }
     MH_ALLOC(ctx, E.xi, q);
+    MH_ALLOC(ctx, E.bw, q);
     dbuf<double> dLc;
     MH_ALLOC(ctx, dLc, 2 * q * q);
     MH_CUDA(ctx, cudaMemcpyAsync(E.xi.p, xi.data(), q * 8, cudaMemcpyHostToDevice, st));
+    {
+        std::vector<double> bwh(q);
+        for (int a = 0; a < q; ++a) {
+            double d = 1.0;
+            for (int m = 0; m < q; ++m)
+                if (m != a) d *= xi[a] - xi[m];
+            bwh[a] = 1.0 / d;
+        }
+        MH_CUDA(ctx, cudaMemcpyAsync(E.bw.p, bwh.data(), q * 8, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaStreamSynchronize(st));
+    }
     MH_CUDA(ctx, cudaMemcpyAsync(dLc.p, Lc.data(), 2 * q * q * 8, cudaMemcpyHostToDevice, st));
     const int qq = q * q;
     // refinement, level by level
@@ -783,8 +815,29 @@ mh_status tree_locate(mh_ctx* ctx, const mh_tree* t, const double* xy_dev, int64
 mh_status tree_interpolate(mh_ctx* ctx, const mh_tree* t, const double* vals, const double* xy_dev,
                            const int32_t* leaf, int64_t n, double* out) {
     if (n == 0) return MH_OK;
-    k_interp<<<mh_grid(n, 128), 128, 0, ctx->stream>>>(t->boxes.p, t->leaf_box.p, t->q, t->box[0], t->box[1],
-                                                        t->box[2], extra_of(t)->xi.p, vals, xy_dev, leaf, n, out);
+    const TreeExtra* E = extra_of(t);
+#define MH_INTERP(QV)                                                                                     \
+    k_interp<QV><<<mh_grid(n, 128), 128, 0, ctx->stream>>>(t->boxes.p, t->leaf_box.p, t->box[0], t->box[1],  \
+                                                            t->box[2], E->xi.p, E->bw.p, vals, xy_dev, leaf, n, out)
+    switch (t->q) {
+        case 2: MH_INTERP(2); break;
+        case 3: MH_INTERP(3); break;
+        case 4: MH_INTERP(4); break;
+        case 5: MH_INTERP(5); break;
+        case 6: MH_INTERP(6); break;
+        case 7: MH_INTERP(7); break;
+        case 8: MH_INTERP(8); break;
+        case 9: MH_INTERP(9); break;
+        case 10: MH_INTERP(10); break;
+        case 11: MH_INTERP(11); break;
+        case 12: MH_INTERP(12); break;
+        case 13: MH_INTERP(13); break;
+        case 14: MH_INTERP(14); break;
+        case 15: MH_INTERP(15); break;
+        case 16: MH_INTERP(16); break;
+        default: return mh_fail(ctx, MH_ERR_INVALID_ARG, "interpolation order q=%d not instantiated", t->q);
+    }
+#undef MH_INTERP
     MH_LAUNCHED(ctx);
     return MH_OK;
 }

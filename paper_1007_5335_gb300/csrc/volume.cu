@@ -1401,6 +1401,7 @@ __global__ void __launch_bounds__(NT) k_dip_near32(
     __shared__ double part[NT];
     const int leaf = active[blockIdx.x];
     const int groups = NT / qq;
+    const float alpha_f = 1.f / inv_alpha;
     const int i = threadIdx.x % qq, g = threadIdx.x / qq;
     const bool act = g < groups;
     const int64_t node = (int64_t)leaf * qq + i;
@@ -1429,7 +1430,7 @@ __global__ void __launch_bounds__(NT) k_dip_near32(
                     const float rinv = rsqrtf(r2);
                     const float z = r2 * rinv * inv_alpha;
                     if (r2 > 0.f && z <= 30.f)   // beyond 30 alpha: below the binary32 rounding of the sum
-                        pt += mh_k1f(z) * inv_alpha * (dx * v.z + dy * v.w) * rinv * sw[e];
+                        pt += mh_k1f_r(z, alpha_f * rinv) * inv_alpha * (dx * v.z + dy * v.w) * rinv * sw[e];
                 }
                 acc += (double)pt;
             }
