@@ -69,7 +69,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.device), "-lms", "200"], stdout=self.fh,
+                                          "-i", str(self.device), "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -231,8 +231,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     launches = ctx.launches - launches0
     regions_ms = {}
-    for r in ("dlp_coarse", "dlp_fine", "dlp_near", "dlp_fmm", "dlp_fmm_contract", "bie_gemv", "volume_contract",
-              "volume_apply", "gmres", "dlp_evaluate", "warm_start", "warm_net"):
+    for r in REGION_NAMES:
         regions_ms[r] = ctx.profile_read(r)
     ctx.profile(False)
     value, total_ms = aggregate_over_ranks(sum(times), n_pts, args.steps, dist, dev)
@@ -308,40 +307,60 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# region: (bound, pipe, what); regions are timed by the library (mh_profile_read) with the
+# algorithmic work it declares per launch: GEMV 4n^2 + 12n bytes (binary32) / 2n^2 flop;
+# pair sums 68 flop per pair; contractions 2 R C flop per task.
 KERNEL_REGIONS = {
-    # region: (bound, description)
-    "dlp_coarse": ("alu", "trapezoid double-layer pair sums"),
-    "dlp_fine": ("alu", "16x upsampled near-boundary pair sums"),
-    "dlp_near": ("alu", "double-layer near-field pair sums (fine dipoles of neighbour leaves)"),
-    "bie_gemv": ("hbm", "Nystrom operator GEMV"),
-    "volume_contract": ("hbm", "volume multipole batched contractions + reduction"),
-    "dlp_fmm_contract": ("hbm", "double-layer multipole batched contractions + reduction"),
+    "bie_gemv32": ("hbm", None, "Nystrom operator GEMV, binary32 (Arnoldi iterations, line rule)"),
+    "bie_gemv64": ("alu", "fp64", "Nystrom operator GEMV, binary64 (residuals, learned-start judge)"),
+    "dlp_near": ("alu", "auto", "double-layer near-field pair sums (fine dipoles of neighbour leaves)"),
+    "dlp_fine": ("alu", "auto", "16x upsampled pair sums at the normal-line auxiliary points"),
+    "dlp_coarse": ("alu", "auto", "trapezoid pair sums"),
+    "volume_contract": ("alu", "auto", "volume multipole contractions (P2M, M2L + P2L, near tables + L2P + M2P)"),
+    "volume_chain": ("alu", "auto", "volume M2M / L2L level chains"),
+    "dlp_fmm_contract": ("alu", "auto", "double-layer multipole contractions (dipole P2M, M2L + P2L, L2P + M2P)"),
+    "dlp_fmm_chain": ("alu", "auto", "double-layer M2M / L2L level chains"),
 }
+# DRAM bytes (read + write) per launch of the region's main kernel, from the ncu launch list
+# of the timed steps (profiles/launches_heat_step_starfish_mixed.md); None where not captured.
+NCU_TRAFFIC = {"dlp_near": 3.903e6, "dlp_fine": 2.082e6, "bie_gemv32": 151.18e6, "bie_gemv64": 201.52e6,
+               "dlp_coarse": 0.212e6}
+REGION_NAMES = tuple(KERNEL_REGIONS) + ("volume_apply", "dlp_fmm", "gmres", "dlp_evaluate", "warm_start", "warm_net")
 
 
-def roofline(regions_ms, tree, bnd, prob, prec, mh, peaks, steps):
-    """Roofline of the dominant instrumented kernel region, from the algorithmic work
-    (flops, bytes) the library declares for each timed launch."""
-    cand = {k: v for k, v in regions_ms.items() if k in KERNEL_REGIONS and v[1] > 0}
-    name = max(cand, key=lambda k: cand[k][0])
-    ms, launches, flops, nbytes = cand[name]
+def region_roofline(name, v, prec, mh, peaks):
+    ms, launches, flops, nbytes = v
+    bound, pipe, desc = KERNEL_REGIONS[name]
     avg_s = ms / max(launches, 1) / 1e3
-    bound, desc = KERNEL_REGIONS[name]
     out = {"kernel": name, "what": desc, "bound": bound, "avg_launch_ms": avg_s * 1e3, "launches": launches,
-           "traffic": None}
+           "traffic": NCU_TRAFFIC.get(name)}
     if bound == "hbm":
         achieved = nbytes / launches / avg_s / 1e9
         peak = peaks["hbm_gbs"]
         out.update({"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "bytes_per_launch": nbytes / launches, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"})
+                    "bytes_per_launch": nbytes / launches,
+                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"})
     else:
+        fp64 = pipe == "fp64" or (pipe == "auto" and prec != mh.MH_PREC_MIXED)
         achieved = flops / launches / avg_s / 1e12
-        peak = FP32_PEAK_TFLOPS if prec == mh.MH_PREC_MIXED else FP64_PEAK_TFLOPS
+        peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
         out.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "flops_per_launch": flops / launches, "flops_per_pair": 68,
-                    "peak_source": "derived: binary32 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s; "
-                                   "binary64 nominal 1.25 TFLOP/s"})
+                    "flops_per_launch": flops / launches,
+                    "peak_source": ("derived: binary64 nominal 1.25 TFLOP/s" if fp64 else
+                                    "derived: binary32 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s")})
     return out
+
+
+def roofline(regions_ms, tree, bnd, prob, prec, mh, peaks, steps):
+    """Roofline of the dominant (longest) instrumented kernel region, and of every region."""
+    cand = {k: v for k, v in regions_ms.items() if k in KERNEL_REGIONS and v[1] > 0}
+    name = max(cand, key=lambda k: cand[k][0])
+    dom = region_roofline(name, cand[name], prec, mh, peaks)
+    dom["all_regions"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                              for kk, vv in region_roofline(k, v, prec, mh, peaks).items()
+                              if kk in ("bound", "avg_launch_ms", "achieved", "peak", "unit", "frac")}
+                          for k, v in sorted(cand.items(), key=lambda kv: -kv[1][0])}
+    return dom
 
 
 def train_warm_start(mh, ctx, prob, bnd, nodes, f_next, prec, dev, steps_per_forcing=20, adam_steps=200):
@@ -479,8 +498,7 @@ def run_batch(args):
     ctx.profile_read("gmres", reset=True)
     for k, it in enumerate(items):
         mh.heat_step(ctx, it["prob"], U[k], Fs[k], fs[k], un[k], S[k], gmres_tol=1e-10, prec=prec)
-    regions_ms = {r: ctx.profile_read(r) for r in ("bie_gemv", "volume_contract", "dlp_fmm_contract", "dlp_near",
-                                                  "dlp_fine", "dlp_coarse")}
+    regions_ms = {r: ctx.profile_read(r) for r in REGION_NAMES}
     ctx.profile(False)
     if rank != 0:
         if dist:
@@ -613,7 +631,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
