@@ -1509,7 +1509,7 @@ static void gemv64(cudaStream_t st, const double* A, const double* x, double* y,
 }
 
 mh_status bie_apply64_gated(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, const int* gate) {
-    prof_scope ps(ctx, "bie_gemv", 2.0 * b->n * b->n, 8.0 * b->n * b->n + 16.0 * b->n);
+    prof_scope ps(ctx, "bie_gemv64", 2.0 * b->n * b->n, 8.0 * b->n * b->n + 16.0 * b->n);
     gemv64(ctx->stream, b->op.A64.p, x, y, b->n, gate);
     MH_LAUNCHED(ctx);
     return MH_OK;
@@ -1526,10 +1526,10 @@ mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_
         if (!b->x32.p) MH_ALLOC(ctx, b->x32, b->n);
         k_to_float_vec<<<mh_grid(b->n, 256), 256, 0, ctx->stream>>>(x, b->x32.p, b->n);
         MH_LAUNCHED(ctx);
-        prof_scope ps(ctx, "bie_gemv", 2.0 * b->n * b->n, 4.0 * b->n * b->n + 12.0 * b->n);
+        prof_scope ps(ctx, "bie_gemv32", 2.0 * b->n * b->n, 4.0 * b->n * b->n + 12.0 * b->n);
         gemv32(ctx->stream, b->op.A32.p, b->x32.p, y, b->n, nullptr);
     } else {
-        prof_scope ps(ctx, "bie_gemv", 2.0 * b->n * b->n, 8.0 * b->n * b->n + 16.0 * b->n);
+        prof_scope ps(ctx, "bie_gemv64", 2.0 * b->n * b->n, 8.0 * b->n * b->n + 16.0 * b->n);
         gemv64(ctx->stream, b->op.A64.p, x, y, b->n, nullptr);
     }
     MH_LAUNCHED(ctx);
@@ -1587,7 +1587,8 @@ static mh_status gmres_core(mh_ctx* ctx, mh_boundary* bd, gmres_ws& ws, const do
         const int k1 = k + 1;
         {   // w = A v_k
             const double* vk = ws.V.p + (int64_t)k * n;
-            prof_scope ps(ctx, "bie_gemv", 2.0 * n * n, mixed ? 4.0 * n * n + 12.0 * n : 8.0 * n * n + 16.0 * n);
+            prof_scope ps(ctx, mixed ? "bie_gemv32" : "bie_gemv64", 2.0 * n * n,
+                          mixed ? 4.0 * n * n + 12.0 * n : 8.0 * n * n + 16.0 * n);
             if (mixed)
                 gemv32(st, bd->op.A32.p, ws.v32.p, ws.w.p, n, nullptr);
             else

@@ -796,6 +796,7 @@ template <typename TOP>
 mh_status run_chain(mh_ctx* ctx, const std::vector<std::unique_ptr<LevelChain>>& chain, const CoopChain* coop,
                     const TOP* ops, int P, int64_t m_base, int64_t l_base, double* vec, bool upward,
                     const char* region) {
+    // the level chains are timed in their own region: "<pass>_chain"
     if (sizeof(TOP) == 4 && coop && coop->ok && !ctx->capturing) {
         prof_scope ps(ctx, region, upward ? coop->flops_up : coop->flops_down,
                       upward ? coop->bytes_up : coop->bytes_down);
@@ -1744,10 +1745,10 @@ static mh_status dipole_run(mh_ctx* ctx, VolData* V, DipData* D, const TOP* ops)
     };
     MH_TRY(run(D->p2m.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain, V->coop.get(), ops, V->P, D->DM_off, D->DL_off, D->vec.p, true,
-                          "dlp_fmm_contract"));
+                          "dlp_fmm_chain"));
     MH_TRY(run(D->m2l.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain, V->coop.get(), ops, V->P, D->DM_off, D->DL_off, D->vec.p, false,
-                          "dlp_fmm_contract"));
+                          "dlp_fmm_chain"));
     MH_TRY(run(D->out.get()));
     return MH_OK;
 }
@@ -1817,10 +1818,10 @@ template <typename TOP>
 static mh_status volume_run(mh_ctx* ctx, mh_tree* t, VolData* V, const TOP* ops) {
     MH_TRY(run_phase(ctx, V, ops, V->p2m.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain, V->coop.get(), ops, V->P, V->M_off, V->L_off, V->vec.p, true,
-                          "volume_contract"));
+                          "volume_chain"));
     MH_TRY(run_phase(ctx, V, ops, V->m2l.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain, V->coop.get(), ops, V->P, V->M_off, V->L_off, V->vec.p, false,
-                          "volume_contract"));
+                          "volume_chain"));
     MH_TRY(run_phase(ctx, V, ops, V->out.get()));
     return MH_OK;
 }
