@@ -93,3 +93,60 @@ __device__ __forceinline__ float mh_k1f_r(float z, float zinv) {
 }
 
 __device__ __forceinline__ float mh_k1f(float z) { return mh_k1f_r(z, __frcp_rn(z)); }
+
+// ---- the binary32 double-layer pair term ----
+// (1/alpha) K1(r/alpha) (d.n)/r = g(z) (d.n) / alpha^2 with g(z) = K1(z)/z, z = r/alpha
+// (Section 3.2).  Written as g, the pair needs neither r nor a division: z <= 2 is decided on
+// r^2, the series runs in y = z^2/4 = r^2/(4 alpha^2) and 1/z = alpha/r comes from the
+// pair's rsqrt.  Callers fold 1/alpha^2 into their binary64 prefactor.
+//   z <= 2 : g = 1/z^2 + log2(y) A(y) - B(y)       (the K1 series of A&S 9.6.11 over z)
+//   z > 2  : g = e^{-z} z^{-3/2} M(4/z - 1)         (M: the K1 interpolant, monomial basis)
+struct mh_dl32 {
+    float ia;        // 1/alpha
+    float a;         // alpha
+    float y_r2;      // 1/(4 alpha^2)
+    float r2_small;  // (2 alpha)^2
+    float r2_cut;    // (cut alpha)^2: farther pairs are below the binary32 rounding of a sum
+};
+
+inline mh_dl32 mh_dl32_make(double alpha, double cut) {
+    mh_dl32 c;
+    c.ia = (float)(1.0 / alpha);
+    c.a = (float)alpha;
+    c.y_r2 = (float)(0.25 / (alpha * alpha));
+    c.r2_small = (float)(4.0 * alpha * alpha);
+    c.r2_cut = (float)(cut * cut * alpha * alpha);
+    return c;
+}
+
+// g(z) for z <= 2 from y = z^2/4 and 1/z
+__device__ __forceinline__ float mh_k1oz_small_f(float y, float zinv) {
+    float a = mh_k1oz_a_f[MH_K1OZ_NA_F - 1], b = mh_k1oz_b_f[MH_K1OZ_NB_F - 1];
+#pragma unroll
+    for (int k = MH_K1OZ_NB_F - 2; k >= 0; --k) {
+        b = fmaf(b, y, mh_k1oz_b_f[k]);
+        if (k < MH_K1OZ_NA_F - 1) a = fmaf(a, y, mh_k1oz_a_f[k]);
+    }
+    return fmaf(zinv, zinv, fmaf(__log2f(y), a, -b));
+}
+
+// g(z) for z > 2 from z and 1/z
+__device__ __forceinline__ float mh_k1oz_large_f(float z, float zinv) {
+    const float x = fmaf(4.f, zinv, -1.f);
+    float m = mh_k1_mono_f[MH_K1_MONO_N32 - 1];
+#pragma unroll
+    for (int k = MH_K1_MONO_N32 - 2; k >= 0; --k) m = fmaf(m, x, mh_k1_mono_f[k]);
+    return __expf(-z) * rsqrtf(z) * zinv * m;
+}
+
+// g(r/alpha) (dx nx + dy ny) for the offset (dx, dy) of a source from a target; 0 for
+// coincident points and beyond the cut.
+__device__ __forceinline__ float mh_dl32_pair(float dx, float dy, float nx, float ny, const mh_dl32& c) {
+    const float r2 = fmaf(dx, dx, dy * dy);
+    if (!(r2 > 0.f && r2 <= c.r2_cut)) return 0.f;
+    const float rinv = rsqrtf(r2);
+    const float zinv = c.a * rinv;
+    const float g = r2 <= c.r2_small ? mh_k1oz_small_f(r2 * c.y_r2, zinv)
+                                     : mh_k1oz_large_f(r2 * rinv * c.ia, zinv);
+    return g * fmaf(dx, nx, dy * ny);
+}

@@ -473,15 +473,8 @@ __global__ void k_weights32(const double* __restrict__ sigma, const double* __re
     if (s < n) w[s] = (float)(sigma[s] * geo[8 * s + 6] * (2.0 * MH_PI / nn[curve_of[s]]));
 }
 
-// (1/alpha) K1(r/alpha) (y-x).n / r in binary32 from offsets d = y - x
-// alpha_f = 1 / inv_alpha, formed once by the caller: 1/z = alpha / r needs no division.
-__device__ __forceinline__ float dl_kernel32(float dx, float dy, float nx, float ny, float inv_alpha, float alpha_f) {
-    const float r2 = dx * dx + dy * dy;
-    const float rinv = rsqrtf(r2);
-    const float z = r2 * rinv * inv_alpha;
-    if (z > MH_DL_CUT32) return 0.f;
-    return mh_k1f_r(z, alpha_f * rinv) * inv_alpha * (dx * nx + dy * ny) * rinv;
-}
+// Binary32 double-layer pairs: mh_dl32_pair (bessel.cuh) returns g(z) (d.n) with
+// g = K1(z)/z; the kernels below apply the prefactor times 1/alpha^2 (pref32) in binary64.
 
 // Coarse trapezoid sum in binary32: sources staged through shared memory in tiles of
 // MH_TILE; the target offset from the tile centre is formed once per tile in binary64;
@@ -490,9 +483,8 @@ __global__ void __launch_bounds__(MH_TILE) k_dlp_coarse32(const double* __restri
                                                           const uint32_t* __restrict__ fine, int64_t nt,
                                                           const float4* __restrict__ src, const float* __restrict__ w,
                                                           const int32_t* __restrict__ curve_of,
-                                                          const double2* __restrict__ tc, int64_t ns, float inv_alpha,
+                                                          const double2* __restrict__ tc, int64_t ns, mh_dl32 c32,
                                                           double pref, double* out) {
-    const float alpha_f = 1.f / inv_alpha;
     __shared__ float4 s4[MH_TILE];
     __shared__ float sw[MH_TILE];
     __shared__ int sk[MH_TILE];
@@ -522,7 +514,7 @@ __global__ void __launch_bounds__(MH_TILE) k_dlp_coarse32(const double* __restri
             for (int i = 0; i < cnt; ++i) {
                 if ((mask >> sk[i]) & 1u) continue;
                 const float4 v = s4[i];
-                part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha, alpha_f) * sw[i];
+                part += mh_dl32_pair(v.x - tx, v.y - ty, v.z, v.w, c32) * sw[i];
             }
             acc += (double)part;
         }
@@ -549,9 +541,8 @@ __global__ void k_sum_partials(const double* __restrict__ part, int nsplit, int6
 __global__ void k_dlp_fine32_blk(const double* __restrict__ xy, const int32_t* __restrict__ ptgt,
                                  const int32_t* __restrict__ pcurve, const float4* __restrict__ fine32,
                                  const float* __restrict__ wf, const int64_t* __restrict__ foff,
-                                 const int64_t* __restrict__ coff, const double2* __restrict__ cc, float inv_alpha,
+                                 const int64_t* __restrict__ coff, const double2* __restrict__ cc, mh_dl32 c32,
                                  double pref, double* out) {
-    const float alpha_f = 1.f / inv_alpha;
     __shared__ double red[8];
     const int64_t p = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -567,7 +558,7 @@ __global__ void k_dlp_fine32_blk(const double* __restrict__ xy, const int32_t* _
         float part = 0.f;
         for (int64_t f = f0 + lane; f < f1; f += 32) {
             const float4 v = fine32[f];
-            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha, alpha_f) * wf[f];
+            part += mh_dl32_pair(v.x - tx, v.y - ty, v.z, v.w, c32) * wf[f];
         }
         acc += (double)part;
     }
@@ -611,9 +602,8 @@ __global__ void k_dlp_fine64_blk(const double* __restrict__ xy, const int32_t* _
 __global__ void k_dlp_fine32(const double* __restrict__ xy, const int32_t* __restrict__ ptgt,
                              const int32_t* __restrict__ pcurve, int64_t npairs, const float4* __restrict__ fine32,
                              const float* __restrict__ wf, const int64_t* __restrict__ foff,
-                             const int64_t* __restrict__ coff, const double2* __restrict__ cc, float inv_alpha,
+                             const int64_t* __restrict__ coff, const double2* __restrict__ cc, mh_dl32 c32,
                              double pref, double* out) {
-    const float alpha_f = 1.f / inv_alpha;
     const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (p >= npairs) return;
     const int lane = threadIdx.x & 31;
@@ -629,7 +619,7 @@ __global__ void k_dlp_fine32(const double* __restrict__ xy, const int32_t* __res
         float part = 0.f;
         for (int64_t f = f0 + lane; f < f1; f += 32) {
             const float4 v = fine32[f];
-            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha, alpha_f) * wf[f];
+            part += mh_dl32_pair(v.x - tx, v.y - ty, v.z, v.w, c32) * wf[f];
         }
         acc += (double)part;
     }
@@ -1240,8 +1230,7 @@ __global__ void k_dlp_fine_corr32(const double* __restrict__ xy, const int32_t* 
                                   const int64_t* __restrict__ foff, const int64_t* __restrict__ coff,
                                   const double2* __restrict__ cc, const float4* __restrict__ src32,
                                   const float* __restrict__ w32, const double2* __restrict__ tc,
-                                  const int32_t* __restrict__ off, float inv_alpha, double pref, double* out) {
-    const float alpha_f = 1.f / inv_alpha;
+                                  const int32_t* __restrict__ off, mh_dl32 c32, double pref, double* out) {
     const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (p >= npairs) return;
     const int lane = threadIdx.x & 31;
@@ -1257,7 +1246,7 @@ __global__ void k_dlp_fine_corr32(const double* __restrict__ xy, const int32_t* 
         float part = 0.f;
         for (int64_t f = f0 + lane; f < f1; f += 32) {
             const float4 v = fine32[f];
-            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha, alpha_f) * wf[f];
+            part += mh_dl32_pair(v.x - tx, v.y - ty, v.z, v.w, c32) * wf[f];
         }
         acc += (double)part;
     }
@@ -1269,7 +1258,7 @@ __global__ void k_dlp_fine_corr32(const double* __restrict__ xy, const int32_t* 
         float part = 0.f;
         for (int64_t s = s0 + lane; s < s1; s += 32) {
             const float4 v = src32[s];
-            part += dl_kernel32(v.x - tx, v.y - ty, v.z, v.w, inv_alpha, alpha_f) * w32[s];
+            part += mh_dl32_pair(v.x - tx, v.y - ty, v.z, v.w, c32) * w32[s];
         }
         acc -= (double)part;
     }
@@ -2038,6 +2027,8 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
     cudaStream_t st = ctx->stream;
     MH_TRY(bie_assemble(ctx, b, alpha));
     const double pref = -1.0 / (2.0 * MH_PI * alpha * alpha);
+    const double pref32 = pref / (alpha * alpha);
+    const mh_dl32 c32 = mh_dl32_make(alpha, MH_DL_CUT32);
     dbuf<double>& ext = tg->ext;
     dbuf<double>& sc = tg->sc;
     dbuf<double>& wf = tg->wf;
@@ -2052,7 +2043,7 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
             prof_scope ps(ctx, "dlp_coarse", DL_FLOPS * tg->n_ext * b->n, 24.0 * (tg->n_ext + b->n));
             k_dlp_coarse32<<<mh_grid(tg->n_ext, MH_TILE), MH_TILE, 0, st>>>(
                 tg->xy.p, tg->fine.p, tg->n_ext, b->src32.p, b->w32.p, b->d_curve_of.p, b->tile_c.p, b->n,
-                (float)(1.0 / alpha), pref, ext.p);
+                c32, pref32, ext.p);
             MH_LAUNCHED(ctx);
         }
         if (tg->n_pairs) {
@@ -2063,7 +2054,7 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
             prof_scope ps(ctx, "dlp_fine", DL_FLOPS * (tg->fine_nodes_main + tg->fine_nodes_aux), 24.0 * b->n_fine);
             k_dlp_fine32<<<mh_grid(tg->n_pairs * 32, 256), 256, 0, st>>>(
                 tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p, tg->n_pairs, b->fine32.p, b->wf32.p, b->d_fine_off.p,
-                b->d_fchunk_off.p, b->fchunk_c.p, (float)(1.0 / alpha), pref, ext.p);
+                b->d_fchunk_off.p, b->fchunk_c.p, c32, pref32, ext.p);
             MH_LAUNCHED(ctx);
         }
     } else {
@@ -2154,6 +2145,8 @@ mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_t
                                 const double* main_vals, double* out, mh_precision prec, bool fine_in_fmm) {
     cudaStream_t st = ctx->stream;
     const double pref = -1.0 / (2.0 * MH_PI * alpha * alpha);
+    const double pref32 = pref / (alpha * alpha);
+    const mh_dl32 c32 = mh_dl32_make(alpha, MH_DL_CUT32);
     const int64_t n = tg->n, naux = tg->n_ext - tg->n;
     const int64_t np_main = tg->n_pairs_main, np_aux = tg->n_pairs - tg->n_pairs_main;
     dbuf<double>& ext = tg->ext;
@@ -2177,10 +2170,10 @@ mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_t
             if ((int64_t)tg->part.n < nsplit * naux) MH_ALLOC(ctx, tg->part, nsplit * naux);
             k_dlp_coarse32<<<dim3((unsigned)nblk, (unsigned)nsplit), MH_TILE, 0, st>>>(
                 tg->xy.p + 2 * n, tg->fine.p + n, naux, b->src32.p, b->w32.p, b->d_curve_of.p, b->tile_c.p, b->n,
-                (float)(1.0 / alpha), pref, nsplit > 1 ? tg->part.p : ext.p + n);
+                c32, pref32, nsplit > 1 ? tg->part.p : ext.p + n);
             MH_LAUNCHED(ctx);
             if (nsplit > 1) {
-                k_sum_partials<<<mh_grid(naux, 256), 256, 0, st>>>(tg->part.p, nsplit, naux, pref, ext.p + n);
+                k_sum_partials<<<mh_grid(naux, 256), 256, 0, st>>>(tg->part.p, nsplit, naux, pref32, ext.p + n);
                 MH_LAUNCHED(ctx);
             }
         }
@@ -2190,13 +2183,13 @@ mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_t
                 k_dlp_fine_corr32<<<mh_grid(np_do_main * 32, 256), 256, 0, st>>>(
                     tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p, np_do_main, b->fine32.p, b->wf32.p, b->d_fine_off.p,
                     b->d_fchunk_off.p, b->fchunk_c.p, b->src32.p, b->w32.p, b->tile_c.p, b->d_off.p,
-                    (float)(1.0 / alpha), pref, ext.p);
+                    c32, pref32, ext.p);
                 MH_LAUNCHED(ctx);
             }
             if (np_aux) {
                 k_dlp_fine32_blk<<<(unsigned)np_aux, 256, 0, st>>>(
                     tg->xy.p, tg->pair_tgt.p + np_main, tg->pair_curve.p + np_main, b->fine32.p, b->wf32.p,
-                    b->d_fine_off.p, b->d_fchunk_off.p, b->fchunk_c.p, (float)(1.0 / alpha), pref, ext.p);
+                    b->d_fine_off.p, b->d_fchunk_off.p, b->fchunk_c.p, c32, pref32, ext.p);
                 MH_LAUNCHED(ctx);
             }
         }

@@ -1336,114 +1336,129 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
 // (M2M, M2L, L2L, L2P, M2P) are those of the volume pass.
 namespace {
 
-// Near field of the double layer on the fly.  One block of NEAR_T threads per target leaf
-// that has dipoles in its U list; thread t handles node t % q^2 for the quarter t / q^2 of
-// each staged source tile (q^2 <= 64); the quarters are summed in a fixed order.
+// Near field of the double layer on the fly.  The dipoles of a target leaf's U list form
+// one flat run (their offsets from the TARGET leaf centre precomputed in binary64, then
+// rounded); the run is cut into chunks of at most NEAR_CHUNK dipoles, one block per chunk,
+// largest chunks first, so that no leaf with a long U list holds one SM while the others
+// idle.  Thread t handles node t % q^2 for the share t / q^2 of every staged tile (q^2 <= 64).
+// A leaf in one chunk writes its nodes directly; otherwise every chunk stores its partial
+// sums and the last chunk of the leaf to finish (counted per leaf, reset by that chunk)
+// adds them in chunk order: the result does not depend on the block schedule.
 //   out[node] += -(1/(2 pi alpha^2)) sum_d w_d (1/alpha) K1(r/alpha) (y_d - x).nu_d / r
 constexpr int NEAR_T = 256;
+constexpr int NEAR_CHUNK = 512;
+
+struct NearChunk {
+    int32_t leaf, k0, k1;   // target leaf, flat dipole range [k0, k1)
+    int32_t slot;           // partial-sum slot, -1 for a leaf in one chunk
+};
+
+// Finish a chunk: block-sum the per-share partials of node i, then write or hand over.
+template <int NT>
+__device__ __forceinline__ void near_finish(double acc, bool act, int qq, int i, int groups, const NearChunk& ch,
+                                            const int2* __restrict__ leaf_red, double pref, double* part,
+                                            unsigned* cnt, double* out) {
+    __shared__ double red[NT];
+    __shared__ int last;
+    red[threadIdx.x] = act ? acc : 0.0;
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x < qq)
+        for (int gg = 0; gg < groups; ++gg) tot += red[gg * qq + threadIdx.x];
+    const int64_t node = (int64_t)ch.leaf * qq + i;
+    if (ch.slot < 0) {
+        if (threadIdx.x < qq) out[node] -= pref * tot;
+        return;
+    }
+    if (threadIdx.x < qq) part[(int64_t)ch.slot * qq + i] = tot;
+    __threadfence();
+    __syncthreads();
+    const int2 lr = leaf_red[ch.leaf];   // {first slot, chunks}
+    if (threadIdx.x == 0) last = atomicAdd(cnt + ch.leaf, 1u) == (unsigned)(lr.y - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < qq) {
+        double s = 0.0;
+        for (int c = 0; c < lr.y; ++c) s += __ldcg(part + (int64_t)(lr.x + c) * qq + i);
+        out[node] -= pref * s;
+    }
+    if (threadIdx.x == 0) cnt[ch.leaf] = 0u;
+}
 
 __global__ void __launch_bounds__(NEAR_T) k_dip_near64(
-    const double* __restrict__ nodes, const int32_t* __restrict__ active, const int32_t* __restrict__ near_ptr,
-    const int32_t* __restrict__ near_leaf, const int64_t* __restrict__ seg0, const int32_t* __restrict__ segn,
-    const double2* __restrict__ dxy, const double2* __restrict__ dnrm, const double* __restrict__ w, int qq,
-    double inv_alpha, double pref, double* out) {
+    const double* __restrict__ nodes, const NearChunk* __restrict__ chunks, const int2* __restrict__ leaf_red,
+    const int32_t* __restrict__ flat_idx, const double2* __restrict__ dxy, const double2* __restrict__ dnrm,
+    const double* __restrict__ w, int qq, double inv_alpha, double pref, double* part, unsigned* cnt,
+    double* out) {
     __shared__ double2 sp[NEAR_T], sn[NEAR_T];
     __shared__ double sw[NEAR_T];
-    __shared__ double part[NEAR_T];
-    const int leaf = active[blockIdx.x];
+    const NearChunk ch = chunks[blockIdx.x];
     const int groups = NEAR_T / qq;   // >= 4 for q <= 8
     const int i = threadIdx.x % qq, g = threadIdx.x / qq;
     const bool act = g < groups;
-    const int64_t node = (int64_t)leaf * qq + i;
+    const int64_t node = (int64_t)ch.leaf * qq + i;
     const double px = nodes[2 * node], py = nodes[2 * node + 1];
     double acc = 0.0;
-    for (int j = near_ptr[leaf]; j < near_ptr[leaf + 1]; ++j) {
-        const int lc = near_leaf[j];
-        const int64_t s0 = seg0[lc];
-        const int cnt = segn[lc];
-        for (int b0 = 0; b0 < cnt; b0 += NEAR_T) {
-            const int m = min(NEAR_T, cnt - b0);
-            __syncthreads();
-            if (threadIdx.x < m) {
-                sp[threadIdx.x] = dxy[s0 + b0 + threadIdx.x];
-                sn[threadIdx.x] = dnrm[s0 + b0 + threadIdx.x];
-                sw[threadIdx.x] = w[s0 + b0 + threadIdx.x];
-            }
-            __syncthreads();
-            if (act)
-                for (int e = g; e < m; e += groups) {
-                    const double dx = sp[e].x - px, dy = sp[e].y - py;
-                    const double r = sqrt(dx * dx + dy * dy);
-                    // pairs beyond 45 alpha are below the binary64 rounding of the sum (e^{-45})
-                    if (r > 0.0 && r * inv_alpha <= 45.0)
-                        acc += mh_k1(r * inv_alpha) * inv_alpha * (dx * sn[e].x + dy * sn[e].y) / r * sw[e];
-                }
+    for (int k0 = ch.k0; k0 < ch.k1; k0 += NEAR_T) {
+        const int m = min(NEAR_T, ch.k1 - k0);
+        __syncthreads();
+        if (threadIdx.x < m) {
+            const int d = flat_idx[k0 + threadIdx.x];
+            sp[threadIdx.x] = dxy[d];
+            sn[threadIdx.x] = dnrm[d];
+            sw[threadIdx.x] = w[d];
         }
+        __syncthreads();
+        if (act)
+            for (int e = g; e < m; e += groups) {
+                const double dx = sp[e].x - px, dy = sp[e].y - py;
+                const double r = sqrt(dx * dx + dy * dy);
+                // pairs beyond 45 alpha are below the binary64 rounding of the sum (e^{-45})
+                if (r > 0.0 && r * inv_alpha <= 45.0)
+                    acc += mh_k1(r * inv_alpha) * inv_alpha * (dx * sn[e].x + dy * sn[e].y) / r * sw[e];
+            }
     }
-    part[threadIdx.x] = act ? acc : 0.0;
-    __syncthreads();
-    if (threadIdx.x < qq) {
-        double tot = 0.0;
-        for (int gg = 0; gg < groups; ++gg) tot += part[gg * qq + threadIdx.x];
-        out[node] -= pref * tot;
-    }
+    near_finish<NEAR_T>(acc, act, qq, i, groups, ch, leaf_red, pref, part, cnt, out);
 }
 
-// NT threads per block (the tile: qq targets x NT / qq source groups, NT sources staged per
-// round); NT in {128, 256, 512} is picked per problem by mh_autotune.
+// Binary32: the staged dipole carries its weight in the normal, (x, y, w nx, w ny), and the
+// pair term is g(z) (d . w n) (mh_dl32_pair); pref already holds the factor 1/alpha^2.
+// NT threads per block (the tile: qq targets x NT / qq source shares, NT dipoles staged per
+// round); NT in {128, 256, 512} is picked per problem by timing.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_dip_near32(
-    const double* __restrict__ nodes, const int32_t* __restrict__ active, const int32_t* __restrict__ near_ptr,
-    const int32_t* __restrict__ near_leaf, const int64_t* __restrict__ seg0, const int32_t* __restrict__ segn,
-    const double2* __restrict__ leaf_c, const float4* __restrict__ d32, const float* __restrict__ w, int qq,
-    float inv_alpha, double pref, double* out) {
+    const double* __restrict__ nodes, const NearChunk* __restrict__ chunks, const int2* __restrict__ leaf_red,
+    const double2* __restrict__ leaf_c, const int32_t* __restrict__ flat_idx, const float4* __restrict__ flat32,
+    const float* __restrict__ w, int qq, mh_dl32 c32, double pref, double* part, unsigned* cnt, double* out) {
     __shared__ float4 s4[NT];
-    __shared__ float sw[NT];
-    __shared__ double part[NT];
-    const int leaf = active[blockIdx.x];
+    const NearChunk ch = chunks[blockIdx.x];
     const int groups = NT / qq;
-    const float alpha_f = 1.f / inv_alpha;
     const int i = threadIdx.x % qq, g = threadIdx.x / qq;
     const bool act = g < groups;
-    const int64_t node = (int64_t)leaf * qq + i;
-    const double px = nodes[2 * node], py = nodes[2 * node + 1];
+    const int64_t node = (int64_t)ch.leaf * qq + i;
+    const double2 c = leaf_c[ch.leaf];
+    const float tx = (float)(nodes[2 * node] - c.x), ty = (float)(nodes[2 * node + 1] - c.y);
     double acc = 0.0;
-    for (int j = near_ptr[leaf]; j < near_ptr[leaf + 1]; ++j) {
-        const int lc = near_leaf[j];
-        const int64_t s0 = seg0[lc];
-        const int cnt = segn[lc];
-        const double2 c = leaf_c[lc];
-        const float tx = (float)(px - c.x), ty = (float)(py - c.y);
-        for (int b0 = 0; b0 < cnt; b0 += NT) {
-            const int m = min(NT, cnt - b0);
-            __syncthreads();
-            if (threadIdx.x < m) {
-                s4[threadIdx.x] = d32[s0 + b0 + threadIdx.x];
-                sw[threadIdx.x] = w[s0 + b0 + threadIdx.x];
+    for (int k0 = ch.k0; k0 < ch.k1; k0 += NT) {
+        const int m = min(NT, ch.k1 - k0);
+        __syncthreads();
+        if (threadIdx.x < m) {
+            const float4 v = flat32[k0 + threadIdx.x];
+            const float wd = w[flat_idx[k0 + threadIdx.x]];
+            s4[threadIdx.x] = make_float4(v.x, v.y, v.z * wd, v.w * wd);
+        }
+        __syncthreads();
+        if (act) {
+            float pt = 0.f;
+            for (int e = g; e < m; e += groups) {
+                const float4 v = s4[e];
+                pt += mh_dl32_pair(v.x - tx, v.y - ty, v.z, v.w, c32);
             }
-            __syncthreads();
-            if (act) {
-                float pt = 0.f;
-                for (int e = g; e < m; e += groups) {
-                    const float4 v = s4[e];
-                    const float dx = v.x - tx, dy = v.y - ty;
-                    const float r2 = dx * dx + dy * dy;
-                    const float rinv = rsqrtf(r2);
-                    const float z = r2 * rinv * inv_alpha;
-                    if (r2 > 0.f && z <= 30.f)   // beyond 30 alpha: below the binary32 rounding of the sum
-                        pt += mh_k1f_r(z, alpha_f * rinv) * inv_alpha * (dx * v.z + dy * v.w) * rinv * sw[e];
-                }
-                acc += (double)pt;
-            }
+            acc += (double)pt;
         }
     }
-    part[threadIdx.x] = act ? acc : 0.0;
-    __syncthreads();
-    if (threadIdx.x < qq) {
-        double tot = 0.0;
-        for (int gg = 0; gg < groups; ++gg) tot += part[gg * qq + threadIdx.x];
-        out[node] -= pref * tot;
-    }
+    near_finish<NT>(acc, act, qq, i, groups, ch, leaf_red, pref, part, cnt, out);
 }
 
 __global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
@@ -1454,16 +1469,17 @@ __global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64
 struct DipData {
     int64_t nd = 0;
     int64_t W_off = 0, DM_off = 0, DL_off = 0, DU_off = 0, vec_len = 0;
-    // near field evaluated on the fly: per target leaf the source segments of its U list
+    // near field evaluated on the fly: per target leaf the dipoles of its U list, flattened
     bool near_blocks = true;
     int qq = 0;
-    dbuf<int32_t> near_ptr, near_leaf;     // CSR over target leaves -> source leaves with dipoles
-    dbuf<int32_t> active;                  // target leaves with a non-empty near list
-    int64_t n_active = 0;
-    dbuf<int64_t> seg0;                    // first dipole of every leaf (-1 if none), count in segn
-    dbuf<int32_t> segn;
+    dbuf<NearChunk> chunks;                // largest first
+    int64_t n_chunks = 0;
+    dbuf<int2> leaf_red;                   // per leaf: first partial slot, chunk count
+    dbuf<double> part;                     // partial sums of leaves in several chunks (slot x qq)
+    dbuf<unsigned> red_cnt;                // per leaf: chunks finished in the running launch
+    dbuf<int32_t> flat_idx;                // dipole of every flat entry
+    dbuf<float4> flat32;                   // its offset from the target leaf centre + normal (binary32)
     dbuf<double2> leaf_c, dxy, dnrm;       // leaf centres; dipole positions and normals (sorted)
-    dbuf<float4> d32;                      // dipole offset from its leaf centre + normal (binary32)
     dbuf<float> w32;
     double pref = 0, inv_alpha = 0;
     double near_pairs = 0;
@@ -1659,18 +1675,7 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
                 }
             }
         }
-        std::vector<int32_t> ptr(nl + 1, 0), items, act;
-        for (int64_t i = 0; i < nl; ++i) {
-            items.insert(items.end(), per[i].begin(), per[i].end());
-            ptr[i + 1] = (int32_t)items.size();
-            if (!per[i].empty()) act.push_back((int32_t)i);
-        }
-        D->n_active = (int64_t)act.size();
-        MH_ALLOC(ctx, D->active, std::max<size_t>(act.size(), 1));
-        if (!act.empty())
-            MH_CUDA(ctx, cudaMemcpyAsync(D->active.p, act.data(), act.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
         std::vector<double2> lc(nl), pxy(nd), pn(nd);
-        std::vector<float4> f4(nd);
         for (int64_t i = 0; i < nl; ++i) {
             const std::complex<double> c = centre(h.leaf_box[i]);
             lc[i] = make_double2(c.real(), c.imag());
@@ -1678,32 +1683,67 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
         for (int64_t d = 0; d < nd; ++d) {
             pxy[d] = make_double2(dxy[2 * d], dxy[2 * d + 1]);
             pn[d] = make_double2(dnrm[2 * d], dnrm[2 * d + 1]);
-            const double2 c = lc[dleaf[d]];
-            f4[d] = make_float4((float)(dxy[2 * d] - c.x), (float)(dxy[2 * d + 1] - c.y), (float)dnrm[2 * d],
-                                (float)dnrm[2 * d + 1]);
         }
-        std::vector<int64_t> s0(seg0.begin(), seg0.end());
-        std::vector<int32_t> sn(segn.begin(), segn.end());
+        // flat runs: target leaf i owns entries [kof[i], kof[i + 1])
+        std::vector<int64_t> kof(nl + 1, 0);
+        for (int64_t i = 0; i < nl; ++i) {
+            int64_t n_i = 0;
+            for (int32_t lc_i : per[i]) n_i += segn[lc_i];
+            kof[i + 1] = kof[i] + n_i;
+        }
+        const int64_t K = kof[nl];
+        if (K >= INT32_MAX) return mh_fail(ctx, MH_ERR_INVALID_ARG, "near-field lists exceed 2^31 entries");
+        std::vector<int32_t> fidx((size_t)K);
+        std::vector<float4> f32((size_t)K);
+        for (int64_t i = 0; i < nl; ++i) {
+            int64_t k = kof[i];
+            for (int32_t lc_i : per[i])
+                for (int64_t d = seg0[lc_i]; d < seg0[lc_i] + segn[lc_i]; ++d, ++k) {
+                    fidx[k] = (int32_t)d;
+                    f32[k] = make_float4((float)(dxy[2 * d] - lc[i].x), (float)(dxy[2 * d + 1] - lc[i].y),
+                                         (float)dnrm[2 * d], (float)dnrm[2 * d + 1]);
+                }
+        }
+        // chunks of at most NEAR_CHUNK entries, equal within a leaf, largest first
+        std::vector<NearChunk> ch;
+        std::vector<int2> lred(nl, make_int2(0, 1));
+        int32_t slots = 0;
+        for (int64_t i = 0; i < nl; ++i) {
+            const int64_t n_i = kof[i + 1] - kof[i];
+            if (n_i == 0) continue;
+            const int64_t nc = (n_i + NEAR_CHUNK - 1) / NEAR_CHUNK;
+            lred[i] = make_int2(nc > 1 ? slots : 0, (int)nc);
+            for (int64_t c = 0; c < nc; ++c)
+                ch.push_back(NearChunk{(int32_t)i, (int32_t)(kof[i] + n_i * c / nc),
+                                       (int32_t)(kof[i] + n_i * (c + 1) / nc), nc > 1 ? slots + (int32_t)c : -1});
+            if (nc > 1) slots += (int32_t)nc;
+        }
+        std::stable_sort(ch.begin(), ch.end(),
+                         [](const NearChunk& x, const NearChunk& y) { return x.k1 - x.k0 > y.k1 - y.k0; });
+        D->n_chunks = (int64_t)ch.size();
         cudaStream_t st = ctx->stream;
-        MH_ALLOC(ctx, D->near_ptr, nl + 1);
-        MH_ALLOC(ctx, D->near_leaf, std::max<size_t>(items.size(), 1));
-        MH_ALLOC(ctx, D->seg0, nl);
-        MH_ALLOC(ctx, D->segn, nl);
+        MH_ALLOC(ctx, D->chunks, std::max<size_t>(ch.size(), 1));
+        MH_ALLOC(ctx, D->leaf_red, nl);
+        MH_ALLOC(ctx, D->part, std::max<int64_t>((int64_t)slots * qq, 1));
+        MH_ALLOC(ctx, D->red_cnt, nl);
+        MH_ALLOC(ctx, D->flat_idx, std::max<int64_t>(K, 1));
+        MH_ALLOC(ctx, D->flat32, std::max<int64_t>(K, 1));
         MH_ALLOC(ctx, D->leaf_c, nl);
         MH_ALLOC(ctx, D->dxy, std::max<int64_t>(nd, 1));
         MH_ALLOC(ctx, D->dnrm, std::max<int64_t>(nd, 1));
-        MH_ALLOC(ctx, D->d32, std::max<int64_t>(nd, 1));
         MH_ALLOC(ctx, D->w32, std::max<int64_t>(nd, 1));
-        MH_CUDA(ctx, cudaMemcpyAsync(D->near_ptr.p, ptr.data(), (nl + 1) * 4, cudaMemcpyHostToDevice, st));
-        if (!items.empty())
-            MH_CUDA(ctx, cudaMemcpyAsync(D->near_leaf.p, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
-        MH_CUDA(ctx, cudaMemcpyAsync(D->seg0.p, s0.data(), nl * 8, cudaMemcpyHostToDevice, st));
-        MH_CUDA(ctx, cudaMemcpyAsync(D->segn.p, sn.data(), nl * 4, cudaMemcpyHostToDevice, st));
+        if (!ch.empty())
+            MH_CUDA(ctx, cudaMemcpyAsync(D->chunks.p, ch.data(), ch.size() * sizeof(NearChunk), cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(D->leaf_red.p, lred.data(), nl * sizeof(int2), cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemsetAsync(D->red_cnt.p, 0, nl * sizeof(unsigned), st));
+        if (K) {
+            MH_CUDA(ctx, cudaMemcpyAsync(D->flat_idx.p, fidx.data(), K * 4, cudaMemcpyHostToDevice, st));
+            MH_CUDA(ctx, cudaMemcpyAsync(D->flat32.p, f32.data(), K * 16, cudaMemcpyHostToDevice, st));
+        }
         MH_CUDA(ctx, cudaMemcpyAsync(D->leaf_c.p, lc.data(), nl * 16, cudaMemcpyHostToDevice, st));
         if (nd) {
             MH_CUDA(ctx, cudaMemcpyAsync(D->dxy.p, pxy.data(), nd * 16, cudaMemcpyHostToDevice, st));
             MH_CUDA(ctx, cudaMemcpyAsync(D->dnrm.p, pn.data(), nd * 16, cudaMemcpyHostToDevice, st));
-            MH_CUDA(ctx, cudaMemcpyAsync(D->d32.p, f4.data(), nd * 16, cudaMemcpyHostToDevice, st));
         }
         MH_CUDA(ctx, cudaStreamSynchronize(st));
     }
@@ -1767,15 +1807,18 @@ mh_status volume_dipole_apply(mh_ctx* ctx, mh_tree* t, const double* w_sorted, m
         MH_TRY(dipole_run<float>(ctx, V, D, D->ops32.p));
     else
         MH_TRY(dipole_run<double>(ctx, V, D, D->ops64.p));
-    if (!D->near_blocks && D->n_active) {
+    if (!D->near_blocks && D->n_chunks) {
         prof_scope ps2(ctx, "dlp_near", 68.0 * D->near_pairs, 24.0 * (double)D->nd);
+        const unsigned nb = (unsigned)D->n_chunks;
+        double* out = D->vec.p + D->DU_off;
         if (prec == MH_PREC_MIXED) {
             k_d2f<<<mh_grid(D->nd, 256), 256, 0, st>>>(w_sorted, D->w32.p, D->nd);
             MH_LAUNCHED(ctx);
+            const mh_dl32 c32 = mh_dl32_make(1.0 / D->inv_alpha, 30.0);
+            const double pref32 = D->pref * D->inv_alpha * D->inv_alpha;
 #define MH_NEAR32(NTV)                                                                                         \
-    k_dip_near32<NTV><<<(unsigned)D->n_active, NTV, 0, st>>>(                                                 \
-        t->nodes.p, D->active.p, D->near_ptr.p, D->near_leaf.p, D->seg0.p, D->segn.p, D->leaf_c.p, D->d32.p,   \
-        D->w32.p, D->qq, (float)D->inv_alpha, D->pref, D->vec.p + D->DU_off)
+    k_dip_near32<NTV><<<nb, NTV, 0, st>>>(t->nodes.p, D->chunks.p, D->leaf_red.p, D->leaf_c.p, D->flat_idx.p,  \
+                                          D->flat32.p, D->w32.p, D->qq, c32, pref32, D->part.p, D->red_cnt.p, out)
             if (D->near_t == 128)
                 MH_NEAR32(128);
             else if (D->near_t == 512)
@@ -1784,9 +1827,9 @@ mh_status volume_dipole_apply(mh_ctx* ctx, mh_tree* t, const double* w_sorted, m
                 MH_NEAR32(256);
 #undef MH_NEAR32
         } else {
-            k_dip_near64<<<(unsigned)D->n_active, NEAR_T, 0, st>>>(
-                t->nodes.p, D->active.p, D->near_ptr.p, D->near_leaf.p, D->seg0.p, D->segn.p, D->dxy.p, D->dnrm.p,
-                w_sorted, D->qq, D->inv_alpha, D->pref, D->vec.p + D->DU_off);
+            k_dip_near64<<<nb, NEAR_T, 0, st>>>(t->nodes.p, D->chunks.p, D->leaf_red.p, D->flat_idx.p, D->dxy.p,
+                                                D->dnrm.p, w_sorted, D->qq, D->inv_alpha, D->pref, D->part.p,
+                                                D->red_cnt.p, out);
         }
         MH_LAUNCHED(ctx);
     }
