@@ -12,6 +12,7 @@
 namespace {
 
 constexpr int UPSAMPLE = 16;        // fine grid for targets within 5 h_s of a curve
+constexpr int FINE_TG = 4;          // auxiliary targets per block of the binary32 upsampled rule
 constexpr double NEAR_NODE = 6.0;   // project on the curve when the nearest node is within 6 h*
 constexpr double NEAR_FINE = 5.0;   // d < 5 h_s: upsampled rule
 constexpr double NEAR_LINE = 0.25;  // d < h_s/4: interpolation along the normal
@@ -442,8 +443,11 @@ __global__ void k_prep_src32(const double* __restrict__ geo, int64_t n, float4* 
 }
 
 // Fine nodes relative to chunk centres: chunks of MH_TILE fine nodes inside each curve.
+// Per fine chunk: offsets of its nodes from the chunk centre (binary32), the centre in
+// binary64 and as float-float pairs (x_hi, x_lo, y_hi, y_lo), and the chunk radius.
 __global__ void k_prep_fine32(const double* __restrict__ fg, const int64_t* __restrict__ foff,
-                              const int64_t* __restrict__ coff, int ncurves, float4* out, double2* cc) {
+                              const int64_t* __restrict__ coff, int ncurves, float4* out, double2* cc,
+                              float4* ccf, float* crad) {
     const int64_t chunk = blockIdx.x;
     int k = 0;
     while (k + 1 < ncurves && chunk >= coff[k + 1]) ++k;
@@ -461,9 +465,22 @@ __global__ void k_prep_fine32(const double* __restrict__ fg, const int64_t* __re
         cc[chunk] = make_double2(cx, cy);
     }
     __syncthreads();
+    float r2max = 0.f;
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         const double* g = fg + 6 * (f0 + i);
-        out[f0 + i] = make_float4((float)(g[0] - cx), (float)(g[1] - cy), (float)g[2], (float)g[3]);
+        const float4 v = make_float4((float)(g[0] - cx), (float)(g[1] - cy), (float)g[2], (float)g[3]);
+        out[f0 + i] = v;
+        r2max = fmaxf(r2max, v.x * v.x + v.y * v.y);
+    }
+    __shared__ float red[32];
+    for (int o = 16; o > 0; o >>= 1) r2max = fmaxf(r2max, __shfl_xor_sync(0xffffffffu, r2max, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r2max;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r2max = fmaxf(r2max, red[w]);
+        const float xh = (float)cx, yh = (float)cy;
+        ccf[chunk] = make_float4(xh, (float)(cx - (double)xh), yh, (float)(cy - (double)yh));
+        crad[chunk] = sqrtf(r2max) * 1.0001f;   // covers the rounding of the offsets
     }
 }
 
@@ -536,40 +553,106 @@ __global__ void k_sum_partials(const double* __restrict__ part, int nsplit, int6
     out[t] = pref * s;
 }
 
-// Upsampled rule in binary32, one block per (target, curve) pair: the warps share the
-// fine-node chunks (MH_TILE nodes, binary64 chunk centres); block reduction in fixed order.
-__global__ void k_dlp_fine32_blk(const double* __restrict__ xy, const int32_t* __restrict__ ptgt,
-                                 const int32_t* __restrict__ pcurve, const float4* __restrict__ fine32,
-                                 const float* __restrict__ wf, const int64_t* __restrict__ foff,
-                                 const int64_t* __restrict__ coff, const double2* __restrict__ cc, mh_dl32 c32,
-                                 double pref, double* out) {
-    __shared__ double red[8];
-    const int64_t p = blockIdx.x;
+// Upsampled rule in binary32 at the auxiliary points of the normal-line rule.  One block per
+// (group of TG auxiliary targets on curve k, slice of the curve's fine chunks); each warp takes
+// one chunk (MH_TILE fine nodes) at a time and every lane evaluates its nodes against all TG
+// targets, so one load of a node serves TG pairs.  The targets' offsets from the chunk centre
+// are float-float differences (no binary64 arithmetic in the loop); a chunk farther than the
+// cut plus its radius from every target is skipped; each chunk's binary32 sums go into
+// float-float accumulators (TwoSum).  The slices of a group hand their sums to the group's last
+// block to finish, which adds them in slice order and then adds pref * sum to every target.
+template <int TG>
+__global__ void __launch_bounds__(256) k_dlp_fine32_grp(
+    const double* __restrict__ xy, const int32_t* __restrict__ pair_tgt, const int32_t* __restrict__ grp_curve,
+    const int32_t* __restrict__ grp_pair, int slices, const float4* __restrict__ fine32, const float* __restrict__ wf,
+    const int64_t* __restrict__ foff, const int64_t* __restrict__ coff, const float4* __restrict__ ccf,
+    const float* __restrict__ crad, mh_dl32 c32, float cut_r, double pref, double* part, unsigned* cnt,
+    double* out) {
+    __shared__ double red[8][TG];
+    __shared__ int last;
+    const int grp = blockIdx.x / slices, sl = blockIdx.x % slices;
+    const int k = grp_curve[grp];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t t = ptgt[p];
-    const int k = pcurve[p];
-    const double px = xy[2 * t], py = xy[2 * t + 1];
-    double acc = 0.0;
-    for (int64_t ch = coff[k] + warp; ch < coff[k + 1]; ch += nw) {
-        const double2 c = cc[ch];
-        const float tx = (float)(px - c.x), ty = (float)(py - c.y);
-        const int64_t f0 = foff[k] + (ch - coff[k]) * MH_TILE;
-        const int64_t f1 = min(f0 + MH_TILE, foff[k + 1]);
-        float part = 0.f;
-        for (int64_t f = f0 + lane; f < f1; f += 32) {
-            const float4 v = fine32[f];
-            part += mh_dl32_pair(v.x - tx, v.y - ty, v.z, v.w, c32) * wf[f];
+    float txh[TG], txl[TG], tyh[TG], tyl[TG];
+#pragma unroll
+    for (int j = 0; j < TG; ++j) {
+        const int p = grp_pair[grp * TG + j];
+        // a padding entry sits far outside every cut: its pairs and chunk tests come out 0 / false
+        const double px = p >= 0 ? xy[2 * (int64_t)pair_tgt[p]] : 1e30;
+        const double py = p >= 0 ? xy[2 * (int64_t)pair_tgt[p] + 1] : 1e30;
+        txh[j] = (float)px;
+        txl[j] = (float)(px - (double)txh[j]);
+        tyh[j] = (float)py;
+        tyl[j] = (float)(py - (double)tyh[j]);
+    }
+    const int64_t nch = coff[k + 1] - coff[k];
+    const int64_t c0 = coff[k] + nch * sl / slices, c1 = coff[k] + nch * (sl + 1) / slices;
+    const int64_t fend = foff[k + 1];
+    float hi[TG], lo[TG];
+#pragma unroll
+    for (int j = 0; j < TG; ++j) hi[j] = lo[j] = 0.f;
+    for (int64_t ch = c0 + warp; ch < c1; ch += nw) {
+        const float4 c = ccf[ch];
+        const float lim = cut_r + crad[ch];
+        float dx0[TG], dy0[TG];
+        bool near = false;
+#pragma unroll
+        for (int j = 0; j < TG; ++j) {
+            dx0[j] = (txh[j] - c.x) + (txl[j] - c.y);
+            dy0[j] = (tyh[j] - c.z) + (tyl[j] - c.w);
+            near |= fmaf(dx0[j], dx0[j], dy0[j] * dy0[j]) <= lim * lim;
         }
-        acc += (double)part;
+        if (!near) continue;   // the same for the whole warp
+        const int64_t f0 = foff[k] + (ch - coff[k]) * MH_TILE;
+        const int m = (int)min((int64_t)MH_TILE, fend - f0);
+        float pt[TG];
+#pragma unroll
+        for (int j = 0; j < TG; ++j) pt[j] = 0.f;
+        for (int i = lane; i < m; i += 32) {
+            const float4 v = fine32[f0 + i];
+            const float w = wf[f0 + i];
+            const float nx = v.z * w, ny = v.w * w;
+#pragma unroll
+            for (int j = 0; j < TG; ++j) pt[j] += mh_dl32_pair(v.x - dx0[j], v.y - dy0[j], nx, ny, c32);
+        }
+#pragma unroll
+        for (int j = 0; j < TG; ++j) {   // TwoSum: hi + lo += pt exactly up to the rounding of lo
+            const float s = hi[j] + pt[j];
+            const float bb = s - hi[j];
+            lo[j] += (hi[j] - (s - bb)) + (pt[j] - bb);
+            hi[j] = s;
+        }
     }
-    acc = warp_sum(acc);
-    if (lane == 0) red[warp] = acc;
+#pragma unroll
+    for (int j = 0; j < TG; ++j) {
+        const double v = warp_sum((double)hi[j] + (double)lo[j]);
+        if (lane == 0) red[warp][j] = v;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < nw; ++i) s += red[i];
-        atomicAdd(out + t, pref * s);
+    double s = 0.0;
+    int t = -1;
+    if (threadIdx.x < TG) {
+        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+        const int p = grp_pair[grp * TG + threadIdx.x];
+        t = p >= 0 ? pair_tgt[p] : -1;
     }
+    if (slices == 1) {
+        if (t >= 0) atomicAdd(out + t, pref * s);
+        return;
+    }
+    if (threadIdx.x < TG) part[((int64_t)grp * slices + sl) * TG + threadIdx.x] = s;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(cnt + grp, 1u) == (unsigned)(slices - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < TG) {
+        double tot = 0.0;
+        for (int q = 0; q < slices; ++q) tot += __ldcg(part + ((int64_t)grp * slices + q) * TG + threadIdx.x);
+        if (t >= 0) atomicAdd(out + t, pref * tot);
+    }
+    if (threadIdx.x == 0) cnt[grp] = 0u;
 }
 
 __global__ void k_dlp_fine64_blk(const double* __restrict__ xy, const int32_t* __restrict__ ptgt,
@@ -1962,6 +2045,36 @@ mh_status dlp_classify(mh_ctx* ctx, mh_boundary* b, const double* xy_dev, int64_
             tg->fine_nodes_aux += UPSAMPLE * nk;
         }
     }
+    // groups of FINE_TG auxiliary pairs on one curve (pairs in their order within a curve)
+    std::vector<int32_t> gcur, gpair;
+    {
+        std::vector<std::vector<int32_t>> byc(b->n_curves);
+        for (int64_t i = tg->n_pairs_main; i < tg->n_pairs; ++i) byc[pc[i]].push_back((int32_t)i);
+        int64_t min_chunks = INT64_MAX;
+        for (int k = 0; k < b->n_curves; ++k) {
+            if (byc[k].empty()) continue;
+            min_chunks = std::min<int64_t>(min_chunks, (b->fine_off[k + 1] - b->fine_off[k] + MH_TILE - 1) / MH_TILE);
+            for (size_t j0 = 0; j0 < byc[k].size(); j0 += FINE_TG) {
+                gcur.push_back(k);
+                for (int j = 0; j < FINE_TG; ++j) gpair.push_back(j0 + j < byc[k].size() ? byc[k][j0 + j] : -1);
+            }
+        }
+        tg->n_groups = (int64_t)gcur.size();
+        // slices of the fine chunks: about 8 blocks per SM over the whole launch
+        tg->fine_slices = tg->n_groups
+                              ? (int)std::max<int64_t>(1, std::min<int64_t>(min_chunks,
+                                                                            (152 * 8 + tg->n_groups - 1) / tg->n_groups))
+                              : 1;
+    }
+    MH_ALLOC(ctx, tg->grp_curve, std::max<int64_t>(tg->n_groups, 1));
+    MH_ALLOC(ctx, tg->grp_pair, std::max<int64_t>(tg->n_groups * FINE_TG, 1));
+    MH_ALLOC(ctx, tg->grp_part, std::max<int64_t>(tg->fine_slices > 1 ? tg->n_groups * tg->fine_slices * FINE_TG : 0, 1));
+    MH_ALLOC(ctx, tg->grp_cnt, std::max<int64_t>(tg->n_groups, 1));
+    MH_CUDA(ctx, cudaMemsetAsync(tg->grp_cnt.p, 0, std::max<int64_t>(tg->n_groups, 1) * sizeof(unsigned), st));
+    if (tg->n_groups) {
+        MH_CUDA(ctx, cudaMemcpyAsync(tg->grp_curve.p, gcur.data(), gcur.size() * 4, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(tg->grp_pair.p, gpair.data(), gpair.size() * 4, cudaMemcpyHostToDevice, st));
+    }
     MH_ALLOC(ctx, tg->xy, 2 * tg->n_ext);
     MH_ALLOC(ctx, tg->fine, tg->n_ext);
     MH_ALLOC(ctx, tg->line_tgt, tg->n_line);
@@ -2012,8 +2125,11 @@ static mh_status prep_mixed(mh_ctx* ctx, mh_boundary* b) {
     MH_ALLOC(ctx, b->wf32, b->n_fine);
     MH_CUDA(ctx, cudaMemcpyAsync(b->d_fchunk_off.p, b->fchunk_off.data(), (b->n_curves + 1) * 8,
                                  cudaMemcpyHostToDevice, st));
+    MH_ALLOC(ctx, b->fchunk_cf, b->n_fchunks);
+    MH_ALLOC(ctx, b->fchunk_r, b->n_fchunks);
     k_prep_fine32<<<(unsigned)b->n_fchunks, 128, 0, st>>>(b->fine_geo.p, b->d_fine_off.p, b->d_fchunk_off.p,
-                                                          b->n_curves, b->fine32.p, b->fchunk_c.p);
+                                                          b->n_curves, b->fine32.p, b->fchunk_c.p,
+                                                          b->fchunk_cf.p, b->fchunk_r.p);
     MH_LAUNCHED(ctx);
     MH_CUDA(ctx, cudaStreamSynchronize(st));
     return MH_OK;
@@ -2187,9 +2303,10 @@ mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_t
                 MH_LAUNCHED(ctx);
             }
             if (np_aux) {
-                k_dlp_fine32_blk<<<(unsigned)np_aux, 256, 0, st>>>(
-                    tg->xy.p, tg->pair_tgt.p + np_main, tg->pair_curve.p + np_main, b->fine32.p, b->wf32.p,
-                    b->d_fine_off.p, b->d_fchunk_off.p, b->fchunk_c.p, c32, pref32, ext.p);
+                k_dlp_fine32_grp<FINE_TG><<<(unsigned)(tg->n_groups * tg->fine_slices), 256, 0, st>>>(
+                    tg->xy.p, tg->pair_tgt.p, tg->grp_curve.p, tg->grp_pair.p, tg->fine_slices, b->fine32.p,
+                    b->wf32.p, b->d_fine_off.p, b->d_fchunk_off.p, b->fchunk_cf.p, b->fchunk_r.p, c32,
+                    (float)(MH_DL_CUT32 * alpha), pref32, tg->grp_part.p, tg->grp_cnt.p, ext.p);
                 MH_LAUNCHED(ctx);
             }
         }

@@ -148,6 +148,8 @@ struct mh_boundary {
     dbuf<int64_t> d_fchunk_off;
     dbuf<float4> src32, fine32;          // (dx, dy, nx, ny)
     dbuf<double2> tile_c, fchunk_c;
+    dbuf<float4> fchunk_cf;              // fine chunk centres as float-float (x_hi, x_lo, y_hi, y_lo)
+    dbuf<float> fchunk_r;                // fine chunk radii
     dbuf<float> w32, wf32, x32;          // per call: weights, fine weights, GEMV input
     dbuf<double> sc64, wf64;             // per call: density Fourier coefficients, fine weights
     dbuf<double> warm_dir, warm_w, warm_scal;   // warm-start direction, its image, scalars
@@ -173,6 +175,14 @@ struct dlp_targets {
     int64_t n_pairs = 0, n_pairs_main = 0;   // pairs of user targets come first
     double fine_nodes_main = 0, fine_nodes_aux = 0, curve_nodes_main = 0;   // work counts
     dbuf<int32_t> pair_tgt, pair_curve;
+    // binary32 upsampled rule at the auxiliary points: groups of FINE_TG pairs on one curve
+    // (grp_pair, -1 padded), each group's fine chunks in fine_slices slices, one block per
+    // (group, slice); partial sums per (group, slice, pair) in grp_part
+    int64_t n_groups = 0;
+    int fine_slices = 1;
+    dbuf<int32_t> grp_curve, grp_pair;
+    dbuf<double> grp_part;
+    dbuf<unsigned> grp_cnt;
     // evaluation workspaces (allocated once by dlp_classify)
     dbuf<double> ext, sc, wf, asig, part;
 };
