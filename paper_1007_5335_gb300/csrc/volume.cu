@@ -330,272 +330,108 @@ __global__ void k_apply(const TOP* __restrict__ ops, const int64_t* __restrict__
     }
 }
 
-// ---- M2M / L2L of one tree level, parent-centric (no reduction pass) ----
-// A block takes LEVEL_PB parents.  G child-position operators (P x P, row-major) are resident
-// in shared memory at a time (G = 4 when they fit, else 1; leading dimension P + 1); thread
-// (g, r) owns row r of operator c0 + g for all LEVEL_PB parents (LEVEL_PB independent
-// accumulation chains).
-constexpr int LEVEL_PB = 16;
-struct Off4 {
-    int64_t v[4];   // offsets of the four child-position operators
-};
+// ---- M2M / L2L chains without grid-wide barriers ----
+// The level chains are latency chains (a few small matvecs per tree level).  Both kernels
+// follow the data dependences instead of the levels:
+//  * upward (M2M): one block per internal box whose children are all leaves.  A block forms
+//    its box's multipole, then counts its arrival at the box's parent; the last child to
+//    arrive carries on with the parent (arrival counters reset by that block), so the
+//    critical path is the depth of the tree, not a barrier per level.
+//    M[parent] = sum over the children c = 0..3 of T_c M[child_c]: thread (c, r) forms row r
+//    of T_c M[child_c] (products in column order), the four are added in the order c = 0..3.
+//  * downward (L2L): one block per internal box with leaf children.  The block recomputes,
+//    in shared memory, the local expansions of the box's ancestors from the top internal
+//    level down (L[child] = L_m2l[child] + T'_c L[parent], the same operations in the same
+//    order as a level-by-level sweep), then adds T'_c L[box] to each leaf child.  Only leaf
+//    expansions are written: they are the only ones read afterwards.
+// Operators are stored transposed per (level, child position): ops[((l * 4 + c) * P + col) * P
+// + row], so the threads of a warp read consecutive words.
+template <typename T>
+__device__ __forceinline__ T chain_fma(T a, T b, T c);
+template <>
+__device__ __forceinline__ float chain_fma<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <>
+__device__ __forceinline__ double chain_fma<double>(double a, double b, double c) { return fma(a, b, c); }
 
-// M[parent] = sum over the children c = 0..3 of T_c M[child_c]; with G = 4 the four partial
-// sums are combined in the order c = 0, 1, 2, 3.
 template <typename TOP>
-__global__ void __launch_bounds__(256) k_m2m_level(const TOP* __restrict__ ops, Off4 oo,
-                                                   const int32_t* __restrict__ par, const int32_t* __restrict__ child,
-                                                   int64_t n_par, int P, int G, int64_t base, double* vec) {
+__global__ void k_chain_up(const TOP* __restrict__ ops, int P, const int32_t* __restrict__ ready,
+                           const int32_t* __restrict__ box, const int4* __restrict__ child,
+                           const int32_t* __restrict__ lvl, const int32_t* __restrict__ next,
+                           const int32_t* __restrict__ need, unsigned* cnt, int64_t base, double* vec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lda = P + 1;
-    TOP* sA = reinterpret_cast<TOP*>(smem_raw);           // G x P x lda
-    TOP* sX = sA + G * P * lda;                            // LEVEL_PB x 4 x lda
-    TOP* red = sX + LEVEL_PB * 4 * lda;                    // G x LEVEL_PB x P (G > 1)
-    const int64_t p0 = (int64_t)blockIdx.x * LEVEL_PB;
-    const int np = (int)min((int64_t)LEVEL_PB, n_par - p0);
-    for (int e0 = threadIdx.x; e0 < LEVEL_PB * 4 * P; e0 += 4 * blockDim.x) {
-        double v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = e0 + u * blockDim.x;
-            const int pp = e / (4 * P), rem = e - pp * 4 * P, c = rem / P, cc = rem - c * P;
-            const int ch = (e < LEVEL_PB * 4 * P && pp < np) ? child[4 * (p0 + pp) + c] : -1;
-            v[u] = ch >= 0 ? vec[base + (int64_t)ch * P + cc] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e >= LEVEL_PB * 4 * P) break;
-            const int pp = e / (4 * P), rem = e - pp * 4 * P, c = rem / P, cc = rem - c * P;
-            sX[(pp * 4 + c) * lda + cc] = (TOP)v[u];
-        }
-    }
-    const int g = threadIdx.x / P, r = threadIdx.x - g * P;
-    TOP acc[LEVEL_PB];
-#pragma unroll
-    for (int pp = 0; pp < LEVEL_PB; ++pp) acc[pp] = 0;
-    for (int c0 = 0; c0 < 4; c0 += G) {
+    TOP* x = reinterpret_cast<TOP*>(smem_raw);   // 4 x P child expansions
+    TOP* part = x + 4 * P;                        // 4 x P products
+    __shared__ int go;
+    const int c = threadIdx.x / P, r = threadIdx.x - c * P;
+    const bool act = c < 4;
+    int t = ready[blockIdx.x];
+    for (;;) {
+        const int4 ch4 = child[t];
+        const int chc = c == 0 ? ch4.x : c == 1 ? ch4.y : c == 2 ? ch4.z : ch4.w;
+        // children may have been written by other blocks of this launch: read through L2
+        if (act) x[c * P + r] = chc >= 0 ? (TOP)__ldcg(vec + base + (int64_t)chc * P + r) : (TOP)0;
         __syncthreads();
-        for (int gg = 0; gg < G; ++gg) stage_rows<TOP, TOP>(sA + gg * P * lda, ops + oo.v[c0 + gg], P * P, P, lda);
-        __syncthreads();
-        if (g < G) {
-            const int c = c0 + g;
-            const TOP* a = sA + (g * P + r) * lda;
-            for (int cc = 0; cc < P; ++cc) {
-                const TOP av = a[cc];
-#pragma unroll
-                for (int pp = 0; pp < LEVEL_PB; ++pp) acc[pp] += av * sX[(pp * 4 + c) * lda + cc];
-            }
+        TOP acc = 0;
+        if (act && chc >= 0) {
+            const TOP* A = ops + (int64_t)(lvl[t] * 4 + c) * P * P + r;
+            const TOP* xc = x + c * P;
+            for (int cc = 0; cc < P; ++cc) acc = chain_fma<TOP>(A[(int64_t)cc * P], xc[cc], acc);
         }
-    }
-    if (G == 1) {
-        if (g == 0)
-#pragma unroll
-            for (int pp = 0; pp < LEVEL_PB; ++pp)
-                if (pp < np) vec[base + (int64_t)par[p0 + pp] * P + r] = (double)acc[pp];
-        return;
-    }
-    if (g < G)
-#pragma unroll
-        for (int pp = 0; pp < LEVEL_PB; ++pp) red[(g * LEVEL_PB + pp) * P + r] = acc[pp];
-    __syncthreads();
-    for (int o = threadIdx.x; o < np * P; o += blockDim.x) {
-        const int pp = o / P, rr = o - pp * P;
-        TOP t = red[pp * P + rr];
-        for (int gg = 1; gg < G; ++gg) t += red[(gg * LEVEL_PB + pp) * P + rr];
-        vec[base + (int64_t)par[p0 + pp] * P + rr] = (double)t;
+        if (act) part[c * P + r] = acc;
+        __syncthreads();
+        if (threadIdx.x < P) {
+            TOP s = part[r] + part[P + r];
+            s += part[2 * P + r];
+            s += part[3 * P + r];
+            vec[base + (int64_t)box[t] * P + r] = (double)s;
+            __threadfence();
+        }
+        const int q = next[t];
+        if (q < 0) return;
+        __syncthreads();
+        if (threadIdx.x == 0) go = atomicAdd(cnt + q, 1u) == (unsigned)(need[q] - 1);
+        __syncthreads();
+        if (!go) return;
+        if (threadIdx.x == 0) cnt[q] = 0u;
+        __threadfence();
+        t = q;
     }
 }
 
-// L[child_c] += T_c L[parent] for the children c of every parent.
 template <typename TOP>
-__global__ void __launch_bounds__(256) k_l2l_level(const TOP* __restrict__ ops, Off4 oo,
-                                                   const int32_t* __restrict__ par, const int32_t* __restrict__ child,
-                                                   int64_t n_par, int P, int G, int64_t base, double* vec) {
+__global__ void k_chain_down(const TOP* __restrict__ ops, int P, const int32_t* __restrict__ poff,
+                             const int32_t* __restrict__ pbox, const int32_t* __restrict__ pop,
+                             const int4* __restrict__ leaf, const int32_t* __restrict__ lop, int64_t base,
+                             double* vec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lda = P + 1;
-    TOP* sA = reinterpret_cast<TOP*>(smem_raw);           // G x P x lda
-    TOP* sX = sA + G * P * lda;                            // LEVEL_PB x lda
-    const int64_t p0 = (int64_t)blockIdx.x * LEVEL_PB;
-    const int np = (int)min((int64_t)LEVEL_PB, n_par - p0);
-    for (int e0 = threadIdx.x; e0 < LEVEL_PB * P; e0 += 4 * blockDim.x) {
-        double v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = e0 + u * blockDim.x;
-            const int pp = e / P, cc = e - pp * P;
-            v[u] = (e < LEVEL_PB * P && pp < np) ? vec[base + (int64_t)par[p0 + pp] * P + cc] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e >= LEVEL_PB * P) break;
-            sX[(e / P) * lda + e % P] = (TOP)v[u];
-        }
-    }
-    const int g = threadIdx.x / P, r = threadIdx.x - g * P;
-    for (int c0 = 0; c0 < 4; c0 += G) {
+    TOP* x = reinterpret_cast<TOP*>(smem_raw);   // the running ancestor expansion
+    const int c = threadIdx.x / P, r = threadIdx.x - c * P;
+    const int k0 = poff[blockIdx.x], k1 = poff[blockIdx.x + 1];
+    if (threadIdx.x < P) x[r] = (TOP)vec[base + (int64_t)pbox[k0] * P + r];
+    for (int k = k0 + 1; k < k1; ++k) {
         __syncthreads();
-        for (int gg = 0; gg < G; ++gg) stage_rows<TOP, TOP>(sA + gg * P * lda, ops + oo.v[c0 + gg], P * P, P, lda);
+        TOP acc = 0;
+        if (threadIdx.x < P) {
+            const TOP* A = ops + (int64_t)pop[k] * P * P + r;
+            for (int cc = 0; cc < P; ++cc) acc = chain_fma<TOP>(A[(int64_t)cc * P], x[cc], acc);
+        }
         __syncthreads();
-        if (g >= G) continue;
-        const int c = c0 + g;
-        TOP acc[LEVEL_PB];
-#pragma unroll
-        for (int pp = 0; pp < LEVEL_PB; ++pp) acc[pp] = 0;
-        const TOP* a = sA + (g * P + r) * lda;
-        for (int cc = 0; cc < P; ++cc) {
-            const TOP av = a[cc];
-#pragma unroll
-            for (int pp = 0; pp < LEVEL_PB; ++pp) acc[pp] += av * sX[pp * lda + cc];
-        }
-#pragma unroll
-        for (int pp = 0; pp < LEVEL_PB; ++pp) {
-            if (pp >= np) break;
-            const int ch = child[4 * (p0 + pp) + c];
-            if (ch >= 0) vec[base + (int64_t)ch * P + r] += (double)acc[pp];
-        }
-    }
-}
-
-// ---- the whole M2M or L2L chain of a pass in one cooperative launch (binary32) ----
-// Levels in execution order; every block stages, once, the four operators of each level on
-// which it has a chunk of LEVEL_PB parents, then the levels run in order with a grid-wide
-// barrier between them (a level reads what the previous one wrote).  Same arithmetic and
-// summation order as k_m2m_level / k_l2l_level with all four operators resident.
-struct ChainLevel {
-    int64_t par0, n_par;   // slice of the concatenated parent / child arrays
-    Off4 off;              // the level's operators
-};
-
-constexpr int COOP_PB = 8;   // parents per chunk in the cooperative chain (short critical path per level)
-
-template <int UP>
-__global__ void __launch_bounds__(256) k_chain_coop(const float4* __restrict__ ops, const ChainLevel* __restrict__ lv,
-                                                    int n_lv, const int32_t* __restrict__ par,
-                                                    const int32_t* __restrict__ child, int P, int64_t base,
-                                                    double* vec) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lda = P + 1;
-    const int lvl_f4 = (4 * P * lda + 3) / 4;                   // one level's operators, in float4
-    float* sOps = reinterpret_cast<float*>(smem_raw);          // n_lv x (4 x P x lda, padded to 16 B)
-    float* sX = sOps + (size_t)n_lv * 4 * lvl_f4;               // COOP_PB x 4 x lda
-    float* red = sX + COOP_PB * 4 * lda;                        // 4 x COOP_PB x P
-    // ops holds every level's four operators already in this layout: straight 16-byte copies,
-    // eight loads in flight per thread
-    float4* s4 = reinterpret_cast<float4*>(sOps);
-    for (int li = 0; li < n_lv; ++li) {
-        const int64_t nch = (lv[li].n_par + COOP_PB - 1) / COOP_PB;
-        if (blockIdx.x >= nch) continue;
-        const float4* src = ops + (size_t)li * lvl_f4;
-        float4* dst = s4 + (size_t)li * lvl_f4;
-        for (int e0 = threadIdx.x; e0 < lvl_f4; e0 += 8 * blockDim.x) {
-            float4 v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int e = e0 + u * blockDim.x;
-                v[u] = e < lvl_f4 ? __ldg(src + e) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int e = e0 + u * blockDim.x;
-                if (e < lvl_f4) dst[e] = v[u];
-            }
-        }
+        if (threadIdx.x < P) x[r] = (TOP)(vec[base + (int64_t)pbox[k] * P + r] + (double)acc);
     }
     __syncthreads();
-    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
-    const int g = threadIdx.x / P, r = threadIdx.x - g * P;
-    for (int li = 0; li < n_lv; ++li) {
-        if (li > 0) grid.sync();
-        const int64_t n_par = lv[li].n_par;
-        const int32_t* lp = par + lv[li].par0;
-        const int32_t* lc = child + 4 * lv[li].par0;
-        const float* A = sOps + (size_t)li * 4 * lvl_f4;
-        for (int64_t ch = blockIdx.x; ch * COOP_PB < n_par; ch += gridDim.x) {
-            const int64_t p0 = ch * COOP_PB;
-            const int np = (int)min((int64_t)COOP_PB, n_par - p0);
-            __syncthreads();
-            // gather with eight loads in flight per thread
-            const int ng = UP ? COOP_PB * 4 * P : COOP_PB * P;
-            for (int e0 = threadIdx.x; e0 < ng; e0 += 8 * blockDim.x) {
-                double v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = e0 + u * blockDim.x;
-                    int64_t src = -1;
-                    if (e < ng) {
-                        if (UP) {
-                            const int pp = e / (4 * P), rem = e - pp * 4 * P, c = rem / P, cc = rem - c * P;
-                            const int chd = pp < np ? lc[4 * (p0 + pp) + c] : -1;
-                            if (chd >= 0) src = base + (int64_t)chd * P + cc;
-                        } else {
-                            const int pp = e / P, cc = e - pp * P;
-                            if (pp < np) src = base + (int64_t)lp[p0 + pp] * P + cc;
-                        }
-                    }
-                    v[u] = src >= 0 ? vec[src] : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = e0 + u * blockDim.x;
-                    if (e >= ng) break;
-                    if (UP) {
-                        const int pp = e / (4 * P), rem = e - pp * 4 * P, c = rem / P, cc = rem - c * P;
-                        sX[(pp * 4 + c) * lda + cc] = (float)v[u];
-                    } else {
-                        const int pp = e / P, cc = e - pp * P;
-                        sX[pp * lda + cc] = (float)v[u];
-                    }
-                }
-            }
-            __syncthreads();
-            float acc[COOP_PB];
-#pragma unroll
-            for (int pp = 0; pp < COOP_PB; ++pp) acc[pp] = 0.f;
-            if (g < 4) {
-                const float* a = A + (g * P + r) * lda;
-                for (int cc = 0; cc < P; ++cc) {
-                    const float av = a[cc];
-#pragma unroll
-                    for (int pp = 0; pp < COOP_PB; ++pp)
-                        acc[pp] += av * (UP ? sX[(pp * 4 + g) * lda + cc] : sX[pp * lda + cc]);
-                }
-            }
-            if (UP) {
-                if (g < 4)
-#pragma unroll
-                    for (int pp = 0; pp < COOP_PB; ++pp) red[(g * COOP_PB + pp) * P + r] = acc[pp];
-                __syncthreads();
-                for (int o = threadIdx.x; o < np * P; o += blockDim.x) {
-                    const int pp = o / P, rr = o - pp * P;
-                    float t = red[pp * P + rr];
-                    for (int gg = 1; gg < 4; ++gg) t += red[(gg * COOP_PB + pp) * P + rr];
-                    vec[base + (int64_t)lp[p0 + pp] * P + rr] = (double)t;
-                }
-            } else if (g < 4) {
-#pragma unroll
-                for (int pp = 0; pp < COOP_PB; ++pp) {
-                    if (pp >= np) break;
-                    const int chd = lc[4 * (p0 + pp) + g];
-                    if (chd >= 0) vec[base + (int64_t)chd * P + r] += (double)acc[pp];
-                }
-            }
+    if (c < 4) {
+        const int4 l4 = leaf[blockIdx.x];
+        const int lc = c == 0 ? l4.x : c == 1 ? l4.y : c == 2 ? l4.z : l4.w;
+        if (lc >= 0) {
+            const TOP* A = ops + (int64_t)(lop[blockIdx.x] + c) * P * P + r;
+            TOP acc = 0;
+            for (int cc = 0; cc < P; ++cc) acc = chain_fma<TOP>(A[(int64_t)cc * P], x[cc], acc);
+            vec[base + (int64_t)lc * P + r] += (double)acc;
         }
     }
 }
 
-inline size_t coop_level_floats(int P) { return (size_t)(4 * P * (P + 1) + 3) / 4 * 4; }
-inline size_t coop_smem(int P, int n_lv) {
-    return ((size_t)n_lv * coop_level_floats(P) + (size_t)COOP_PB * 4 * (P + 1) + 4 * (size_t)COOP_PB * P) * 4;
-}
-
-// Shared memory of the level kernels for P and G (bytes, with TOP of size ts).
-inline size_t level_smem(int P, int G, size_t ts) {
-    return ((size_t)G * P * (P + 1) + (size_t)LEVEL_PB * 4 * (P + 1) + (G > 1 ? (size_t)G * LEVEL_PB * P : 0)) * ts;
-}
-// Operators resident at once: 4 when the threads and the shared memory allow it.
-inline int level_groups(int P, size_t ts) { return (4 * P <= 256 && level_smem(P, 4, ts) <= 200 * 1024) ? 4 : 1; }
+inline int chain_threads(int P) { return (4 * P + 31) / 32 * 32; }
 
 // Per destination (one warp each): vec[dst + r] = (acc ? vec : 0) + sum of its products.
 __global__ void k_reduce(const double* __restrict__ temp, int R, const int64_t* __restrict__ dst_off,
@@ -647,22 +483,19 @@ struct OpPool {
 
 // M2M / L2L of every level 2 <= l < L in parent-centric form (shared by the volume and the
 // double-layer passes: same tree, same operators at the same pool offsets).
-struct LevelChain {
-    int64_t n_par = 0;
-    int64_t m2m_off[4] = {0, 0, 0, 0}, l2l_off[4] = {0, 0, 0, 0};
-    double flops = 0, bytes = 0;
-    dbuf<int32_t> par, child;
-};
-
-// Device description of the whole chain for the cooperative binary32 kernel.
-struct CoopChain {
-    bool ok = false;                 // fits in shared memory and the grid can be co-resident
-    int n_lv = 0, grid = 0;
-    size_t smem = 0;
-    double flops_up = 0, bytes_up = 0, flops_down = 0, bytes_down = 0;
-    dbuf<ChainLevel> up, down;       // levels in execution order
-    dbuf<int32_t> par, child;        // concatenated over levels
-    dbuf<float> ops_up, ops_down;    // binary32 operators in the kernel's shared-memory layout
+// Device description of the M2M / L2L chains (k_chain_up / k_chain_down).
+struct DfChain {
+    int64_t n_int = 0;                   // internal boxes of levels >= 2 (upward tasks)
+    int64_t n_ready = 0;                 // of which all children are leaves
+    int64_t n_down = 0;                  // internal boxes with leaf children (downward blocks)
+    double flops = 0, bytes = 0;         // one sweep (either direction), algorithmic
+    dbuf<int32_t> up_box, up_lvl, up_next, up_need, up_ready;
+    dbuf<int4> up_child;
+    dbuf<unsigned> up_cnt;
+    dbuf<int32_t> dn_off, dn_box, dn_op, dn_lop;
+    dbuf<int4> dn_leaf;
+    dbuf<float> m2m32, l2l32;            // transposed operators, [level][position][col][row]
+    dbuf<double> m2m64, l2l64;
 };
 
 struct DipData;
@@ -684,8 +517,7 @@ struct VolData {
     dbuf<int32_t> d_op_C;
     std::vector<int> op_C;
     std::unique_ptr<Phase> p2m, m2l, out;
-    std::vector<std::unique_ptr<LevelChain>> chain;   // by level
-    std::unique_ptr<CoopChain> coop;                  // the same chain for the cooperative kernel
+    std::unique_ptr<DfChain> chain;                   // M2M / L2L chains
     int64_t temp_len = 0;
     int64_t n_near_tables = 0;
 };
@@ -789,52 +621,28 @@ mh_status run_phase_on(mh_ctx* ctx, const TOP* ops, const int64_t* op_off, const
     return MH_OK;
 }
 
-inline Off4 offs4(const int64_t* o) { return Off4{{o[0], o[1], o[2], o[3]}}; }
 
 
 template <typename TOP>
-mh_status run_chain(mh_ctx* ctx, const std::vector<std::unique_ptr<LevelChain>>& chain, const CoopChain* coop,
-                    const TOP* ops, int P, int64_t m_base, int64_t l_base, double* vec, bool upward,
-                    const char* region) {
+mh_status run_chain(mh_ctx* ctx, const DfChain* ch, int P, int64_t m_base, int64_t l_base, double* vec,
+                    bool upward, const char* region) {
     // the level chains are timed in their own region: "<pass>_chain"
-    if (sizeof(TOP) == 4 && coop && coop->ok && !ctx->capturing) {
-        prof_scope ps(ctx, region, upward ? coop->flops_up : coop->flops_down,
-                      upward ? coop->bytes_up : coop->bytes_down);
-        (void)ops;   // the chain's own copies of the binary32 operators
-        const float4* o = reinterpret_cast<const float4*>(upward ? coop->ops_up.p : coop->ops_down.p);
-        const ChainLevel* lv = upward ? coop->up.p : coop->down.p;
-        int n_lv = coop->n_lv;
-        const int32_t* par = coop->par.p;
-        const int32_t* child = coop->child.p;
-        int64_t base = upward ? m_base : l_base;
-        void* args[] = {(void*)&o, (void*)&lv, (void*)&n_lv, (void*)&par, (void*)&child, (void*)&P, (void*)&base,
-                        (void*)&vec};
-        if (upward)
-            MH_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_chain_coop<1>, coop->grid, 256, args, coop->smem,
-                                                     ctx->stream));
-        else
-            MH_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_chain_coop<0>, coop->grid, 256, args, coop->smem,
-                                                     ctx->stream));
-        MH_LAUNCHED(ctx);
-        return MH_OK;
+    if (!ch || ch->n_int == 0) return MH_OK;
+    prof_scope ps(ctx, region, ch->flops, ch->bytes);
+    const bool f32 = sizeof(TOP) == 4;
+    const TOP* ops = reinterpret_cast<const TOP*>(upward ? (f32 ? (const void*)ch->m2m32.p : (const void*)ch->m2m64.p)
+                                                         : (f32 ? (const void*)ch->l2l32.p : (const void*)ch->l2l64.p));
+    const int nt = chain_threads(P);
+    if (upward) {
+        k_chain_up<TOP><<<(unsigned)ch->n_ready, nt, 8 * P * sizeof(TOP), ctx->stream>>>(
+            ops, P, ch->up_ready.p, ch->up_box.p, ch->up_child.p, ch->up_lvl.p, ch->up_next.p, ch->up_need.p,
+            ch->up_cnt.p, m_base, vec);
+    } else {
+        if (ch->n_down == 0) return MH_OK;
+        k_chain_down<TOP><<<(unsigned)ch->n_down, nt, P * sizeof(TOP), ctx->stream>>>(
+            ops, P, ch->dn_off.p, ch->dn_box.p, ch->dn_op.p, ch->dn_leaf.p, ch->dn_lop.p, l_base, vec);
     }
-    const int L = (int)chain.size();
-    const int G = level_groups(P, sizeof(TOP));
-    const size_t smem = level_smem(P, G, sizeof(TOP));
-    for (int step = 0; step < L; ++step) {
-        const int l = upward ? L - 1 - step : step;
-        const LevelChain* c = chain[l].get();
-        if (!c || c->n_par == 0) continue;
-        prof_scope ps(ctx, region, c->flops, c->bytes);
-        const unsigned grid = (unsigned)((c->n_par + LEVEL_PB - 1) / LEVEL_PB);
-        if (upward)
-            k_m2m_level<TOP><<<grid, 256, smem, ctx->stream>>>(ops, offs4(c->m2m_off), c->par.p,
-                                                                c->child.p, c->n_par, P, G, m_base, vec);
-        else
-            k_l2l_level<TOP><<<grid, 256, smem, ctx->stream>>>(ops, offs4(c->l2l_off), c->par.p,
-                                                                c->child.p, c->n_par, P, G, l_base, vec);
-        MH_LAUNCHED(ctx);
-    }
+    MH_LAUNCHED(ctx);
     return MH_OK;
 }
 
@@ -1119,128 +927,127 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
             t_m2l.push_back(Task{id, V->B_off + (int64_t)h.box_leaf[c] * qq, V->L_off + b * P});
         }
     }
-    // M2M / L2L: the internal boxes of levels 2 <= l < L with their four children (parent-centric)
+    // M2M / L2L chains: the internal boxes of levels 2 <= l < L with their four children
     {
         std::vector<int32_t> child(4 * nb);
         MH_CUDA(ctx, cudaMemcpyAsync(child.data(), t->box_child.p, 4 * nb * 4, cudaMemcpyDeviceToHost, ctx->stream));
         MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        std::vector<std::vector<int32_t>> par(L + 1), chl(L + 1);
-        std::vector<int64_t> nchild(L + 1, 0);
+        std::unique_ptr<DfChain> ch(new DfChain());
+        std::vector<int32_t> idx(nb, -1), parent(nb, -1), quad(nb, -1);
+        for (int64_t b = 0; b < nb; ++b)
+            for (int c = 0; c < 4; ++c)
+                if (child[4 * b + c] >= 0) {
+                    parent[child[4 * b + c]] = (int32_t)b;
+                    quad[child[4 * b + c]] = c;
+                }
+        std::vector<int32_t> ubox, ulvl, unext, uneed, uready;
+        std::vector<int4> uchild;
+        std::vector<int64_t> npar(L + 1, 0), nchild(L + 1, 0);
         for (int64_t b = 0; b < nb; ++b) {
             const int l = lev((int)b);
             if (h.box_leaf[b] >= 0 || l < 2 || l >= L) continue;
             int cnt = 0;
             for (int c = 0; c < 4; ++c) cnt += child[4 * b + c] >= 0;
             if (!cnt) continue;
-            par[l].push_back((int32_t)b);
-            for (int c = 0; c < 4; ++c) chl[l].push_back(child[4 * b + c]);
+            idx[b] = (int32_t)ubox.size();
+            ubox.push_back((int32_t)b);
+            ulvl.push_back(l);
+            uchild.push_back(make_int4(child[4 * b], child[4 * b + 1], child[4 * b + 2], child[4 * b + 3]));
+            npar[l] += 1;
             nchild[l] += cnt;
         }
-        V->chain.clear();
-        V->chain.resize(L);
+        for (int l = 2; l < L; ++l)
+            if (npar[l]) {
+                ch->flops += 2.0 * P * P * nchild[l];
+                ch->bytes += 8.0 * (4.0 * P * P + 2.0 * P * (nchild[l] + npar[l]));
+            }
+        const int64_t ni = (int64_t)ubox.size();
+        ch->n_int = ni;
+        unext.assign(ni, -1);
+        uneed.assign(ni, 0);
+        // downward blocks: internal boxes with leaf children, each with its internal ancestors
+        std::vector<int32_t> doff{0}, dbox, dop, dlop;
+        std::vector<int4> dleaf;
+        for (int64_t i = 0; i < ni; ++i) {
+            const int b = ubox[i];
+            if (parent[b] >= 0 && idx[parent[b]] >= 0) unext[i] = idx[parent[b]];
+            int leaves[4] = {-1, -1, -1, -1};
+            bool any_leaf = false;
+            for (int c = 0; c < 4; ++c) {
+                const int cb = child[4 * b + c];
+                if (cb < 0) continue;
+                if (idx[cb] >= 0)
+                    uneed[i] += 1;
+                else if (h.box_leaf[cb] >= 0) {
+                    leaves[c] = cb;
+                    any_leaf = true;
+                }
+            }
+            if (uneed[i] == 0) uready.push_back((int32_t)i);
+            if (!any_leaf) continue;
+            std::vector<int32_t> path{b};
+            while (parent[path.back()] >= 0 && idx[parent[path.back()]] >= 0) path.push_back(parent[path.back()]);
+            for (size_t k = path.size(); k-- > 0;) {
+                const int e = path[k];
+                dbox.push_back(e);
+                dop.push_back(k + 1 == path.size() ? -1 : lev(parent[e]) * 4 + quad[e]);
+            }
+            doff.push_back((int32_t)dbox.size());
+            dleaf.push_back(make_int4(leaves[0], leaves[1], leaves[2], leaves[3]));
+            dlop.push_back(ulvl[i] * 4);
+        }
+        ch->n_ready = (int64_t)uready.size();
+        ch->n_down = (int64_t)dleaf.size();
+        // operators, transposed per (level, child position)
+        const size_t PP = (size_t)P * P;
+        std::vector<double> tm((size_t)L * 4 * PP, 0.0), tl((size_t)L * 4 * PP, 0.0);
         for (int l = 2; l < L; ++l) {
-            if (par[l].empty()) continue;
-            std::unique_ptr<LevelChain> c(new LevelChain());
-            c->n_par = (int64_t)par[l].size();
-            for (int q4 = 0; q4 < 4; ++q4) {
-                c->m2m_off[q4] = pool.off[op_m2m[l][q4]];
-                c->l2l_off[q4] = pool.off[op_l2l[l][q4]];
-            }
-            c->flops = 2.0 * P * P * nchild[l];
-            c->bytes = 8.0 * (4.0 * P * P + 2.0 * P * (nchild[l] + c->n_par));
-            MH_ALLOC(ctx, c->par, par[l].size());
-            MH_ALLOC(ctx, c->child, chl[l].size());
-            MH_CUDA(ctx, cudaMemcpyAsync(c->par.p, par[l].data(), par[l].size() * 4, cudaMemcpyHostToDevice,
-                                         ctx->stream));
-            MH_CUDA(ctx, cudaMemcpyAsync(c->child.p, chl[l].data(), chl[l].size() * 4, cudaMemcpyHostToDevice,
-                                         ctx->stream));
-            V->chain[l] = std::move(c);
-        }
-        // the same chain for the cooperative binary32 kernel (levels finest first for M2M)
-        std::unique_ptr<CoopChain> cc(new CoopChain());
-        std::vector<ChainLevel> up;
-        std::vector<int32_t> cpar, cchild;
-        int64_t max_ch = 0;
-        for (int l = L - 1; l >= 2; --l) {
-            const LevelChain* c = V->chain[l].get();
-            if (!c) continue;
-            ChainLevel e;
-            e.par0 = (int64_t)cpar.size();
-            e.n_par = c->n_par;
-            for (int q4 = 0; q4 < 4; ++q4) e.off.v[q4] = c->m2m_off[q4];
-            up.push_back(e);
-            cpar.insert(cpar.end(), par[l].begin(), par[l].end());
-            cchild.insert(cchild.end(), chl[l].begin(), chl[l].end());
-            max_ch = std::max<int64_t>(max_ch, (c->n_par + COOP_PB - 1) / COOP_PB);
-            cc->flops_up += c->flops;
-            cc->bytes_up += c->bytes;
-        }
-        std::vector<ChainLevel> down(up.rbegin(), up.rend());
-        {
-            // operators of the downward chain: the L2L set of each level
-            int idx = 0;
-            for (int l = 2; l < L; ++l) {
-                const LevelChain* c = V->chain[l].get();
-                if (!c) continue;
-                for (int q4 = 0; q4 < 4; ++q4) down[idx].off.v[q4] = c->l2l_off[q4];
-                cc->flops_down += c->flops;
-                cc->bytes_down += c->bytes;
-                ++idx;
+            if (!npar[l]) continue;
+            for (int c = 0; c < 4; ++c) {
+                const double* om = pool.data.data() + pool.off[op_m2m[l][c]];
+                const double* ol = pool.data.data() + pool.off[op_l2l[l][c]];
+                for (int r = 0; r < P; ++r)
+                    for (int cc = 0; cc < P; ++cc) {
+                        tm[(l * 4 + c) * PP + (size_t)cc * P + r] = om[(size_t)r * P + cc];
+                        tl[(l * 4 + c) * PP + (size_t)cc * P + r] = ol[(size_t)r * P + cc];
+                    }
             }
         }
-        cc->n_lv = (int)up.size();
-        cc->smem = coop_smem(P, cc->n_lv);
-        int dev = 0, sms = 0, nb_up = 0, nb_down = 0, coop_attr = 0;
-        MH_CUDA(ctx, cudaGetDevice(&dev));
-        MH_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        MH_CUDA(ctx, cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, dev));
-        if (cc->n_lv > 0 && coop_attr && 4 * P <= 256 && cc->smem <= 200 * 1024) {
-            MH_CUDA(ctx, cudaFuncSetAttribute(k_chain_coop<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)cc->smem));
-            MH_CUDA(ctx, cudaFuncSetAttribute(k_chain_coop<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)cc->smem));
-            MH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_up, k_chain_coop<1>, 256, cc->smem));
-            MH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_down, k_chain_coop<0>, 256, cc->smem));
-            const int64_t cap = (int64_t)std::min(nb_up, nb_down) * sms;
-            if (cap > 0) {
-                cc->grid = (int)std::max<int64_t>(1, std::min<int64_t>(max_ch, cap));
-                MH_ALLOC(ctx, cc->up, up.size());
-                MH_ALLOC(ctx, cc->down, down.size());
-                MH_ALLOC(ctx, cc->par, cpar.size());
-                MH_ALLOC(ctx, cc->child, cchild.size());
-                MH_CUDA(ctx, cudaMemcpyAsync(cc->up.p, up.data(), up.size() * sizeof(ChainLevel), cudaMemcpyHostToDevice,
-                                             ctx->stream));
-                MH_CUDA(ctx, cudaMemcpyAsync(cc->down.p, down.data(), down.size() * sizeof(ChainLevel),
-                                             cudaMemcpyHostToDevice, ctx->stream));
-                MH_CUDA(ctx, cudaMemcpyAsync(cc->par.p, cpar.data(), cpar.size() * 4, cudaMemcpyHostToDevice,
-                                             ctx->stream));
-                MH_CUDA(ctx, cudaMemcpyAsync(cc->child.p, cchild.data(), cchild.size() * 4, cudaMemcpyHostToDevice,
-                                             ctx->stream));
-                // operators in the kernel's layout: level, child position, row (leading dimension P + 1)
-                const size_t lf = coop_level_floats(P);
-                std::vector<float> hu(lf * up.size(), 0.f), hd(lf * down.size(), 0.f);
-                auto fill = [&](std::vector<float>& h, const std::vector<ChainLevel>& lvls) {
-                    for (size_t li = 0; li < lvls.size(); ++li)
-                        for (int c4 = 0; c4 < 4; ++c4)
-                            for (int r = 0; r < P; ++r)
-                                for (int cc2 = 0; cc2 < P; ++cc2)
-                                    h[li * lf + ((size_t)c4 * P + r) * (P + 1) + cc2] =
-                                        (float)pool.data[lvls[li].off.v[c4] + (size_t)r * P + cc2];
-                };
-                fill(hu, up);
-                fill(hd, down);
-                MH_ALLOC(ctx, cc->ops_up, hu.size());
-                MH_ALLOC(ctx, cc->ops_down, hd.size());
-                MH_CUDA(ctx, cudaMemcpyAsync(cc->ops_up.p, hu.data(), hu.size() * 4, cudaMemcpyHostToDevice,
-                                             ctx->stream));
-                MH_CUDA(ctx, cudaMemcpyAsync(cc->ops_down.p, hd.data(), hd.size() * 4, cudaMemcpyHostToDevice,
-                                             ctx->stream));
-                MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-                cc->ok = true;
-            }
-        }
-        V->coop = std::move(cc);
-        MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        std::vector<float> tm32(tm.begin(), tm.end()), tl32(tl.begin(), tl.end());
+        cudaStream_t cs = ctx->stream;
+        auto up_i = [&](dbuf<int32_t>& d, const std::vector<int32_t>& v) -> mh_status {
+            MH_ALLOC(ctx, d, std::max<size_t>(v.size(), 1));
+            if (!v.empty()) MH_CUDA(ctx, cudaMemcpyAsync(d.p, v.data(), v.size() * 4, cudaMemcpyHostToDevice, cs));
+            return MH_OK;
+        };
+        auto up_4 = [&](dbuf<int4>& d, const std::vector<int4>& v) -> mh_status {
+            MH_ALLOC(ctx, d, std::max<size_t>(v.size(), 1));
+            if (!v.empty()) MH_CUDA(ctx, cudaMemcpyAsync(d.p, v.data(), v.size() * 16, cudaMemcpyHostToDevice, cs));
+            return MH_OK;
+        };
+        MH_TRY(up_i(ch->up_box, ubox));
+        MH_TRY(up_i(ch->up_lvl, ulvl));
+        MH_TRY(up_i(ch->up_next, unext));
+        MH_TRY(up_i(ch->up_need, uneed));
+        MH_TRY(up_i(ch->up_ready, uready));
+        MH_TRY(up_4(ch->up_child, uchild));
+        MH_TRY(up_i(ch->dn_off, doff));
+        MH_TRY(up_i(ch->dn_box, dbox));
+        MH_TRY(up_i(ch->dn_op, dop));
+        MH_TRY(up_i(ch->dn_lop, dlop));
+        MH_TRY(up_4(ch->dn_leaf, dleaf));
+        MH_ALLOC(ctx, ch->up_cnt, std::max<int64_t>(ni, 1));
+        MH_CUDA(ctx, cudaMemsetAsync(ch->up_cnt.p, 0, std::max<int64_t>(ni, 1) * sizeof(unsigned), cs));
+        MH_ALLOC(ctx, ch->m2m32, tm32.size());
+        MH_ALLOC(ctx, ch->l2l32, tl32.size());
+        MH_ALLOC(ctx, ch->m2m64, tm.size());
+        MH_ALLOC(ctx, ch->l2l64, tl.size());
+        MH_CUDA(ctx, cudaMemcpyAsync(ch->m2m32.p, tm32.data(), tm32.size() * 4, cudaMemcpyHostToDevice, cs));
+        MH_CUDA(ctx, cudaMemcpyAsync(ch->l2l32.p, tl32.data(), tl32.size() * 4, cudaMemcpyHostToDevice, cs));
+        MH_CUDA(ctx, cudaMemcpyAsync(ch->m2m64.p, tm.data(), tm.size() * 8, cudaMemcpyHostToDevice, cs));
+        MH_CUDA(ctx, cudaMemcpyAsync(ch->l2l64.p, tl.data(), tl.size() * 8, cudaMemcpyHostToDevice, cs));
+        MH_CUDA(ctx, cudaStreamSynchronize(cs));
+        V->chain = std::move(ch);
     }
     // near tables on the device, appended to the pool
     const int nnear = (int)near_cfg.size();
@@ -1313,13 +1120,8 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
     for (auto* ph : {V->p2m.get(), V->m2l.get(), V->out.get()}) maxs = std::max(maxs, ph->smem);
     MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
     MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-    if (P > 256 || level_smem(P, 1, 8) > 200 * 1024)
-        return mh_fail(ctx, MH_ERR_INVALID_ARG, "multipole order too large for the level kernels");
-    const int lsm64 = (int)level_smem(P, level_groups(P, 8), 8), lsm32 = (int)level_smem(P, level_groups(P, 4), 4);
-    MH_CUDA(ctx, cudaFuncSetAttribute(k_m2m_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsm64));
-    MH_CUDA(ctx, cudaFuncSetAttribute(k_m2m_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsm32));
-    MH_CUDA(ctx, cudaFuncSetAttribute(k_l2l_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsm64));
-    MH_CUDA(ctx, cudaFuncSetAttribute(k_l2l_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsm32));
+    if (chain_threads(P) > 1024)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "multipole order too large for the chain kernels");
     return MH_OK;
 }
 
@@ -1784,10 +1586,10 @@ static mh_status dipole_run(mh_ctx* ctx, VolData* V, DipData* D, const TOP* ops)
         return run_phase_on<TOP>(ctx, ops, D->d_op_off.p, D->d_op_C.p, D->vec.p, D->temp.p, ph, "dlp_fmm_contract");
     };
     MH_TRY(run(D->p2m.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain, V->coop.get(), ops, V->P, D->DM_off, D->DL_off, D->vec.p, true,
+    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, D->vec.p, true,
                           "dlp_fmm_chain"));
     MH_TRY(run(D->m2l.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain, V->coop.get(), ops, V->P, D->DM_off, D->DL_off, D->vec.p, false,
+    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, D->vec.p, false,
                           "dlp_fmm_chain"));
     MH_TRY(run(D->out.get()));
     return MH_OK;
@@ -1860,10 +1662,10 @@ void volume_free(mh_tree* t) {
 template <typename TOP>
 static mh_status volume_run(mh_ctx* ctx, mh_tree* t, VolData* V, const TOP* ops) {
     MH_TRY(run_phase(ctx, V, ops, V->p2m.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain, V->coop.get(), ops, V->P, V->M_off, V->L_off, V->vec.p, true,
+    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, V->M_off, V->L_off, V->vec.p, true,
                           "volume_chain"));
     MH_TRY(run_phase(ctx, V, ops, V->m2l.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain, V->coop.get(), ops, V->P, V->M_off, V->L_off, V->vec.p, false,
+    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, V->M_off, V->L_off, V->vec.p, false,
                           "volume_chain"));
     MH_TRY(run_phase(ctx, V, ops, V->out.get()));
     return MH_OK;
