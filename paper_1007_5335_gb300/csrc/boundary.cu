@@ -1352,31 +1352,44 @@ __global__ void k_dlp_fine_corr32(const double* __restrict__ xy, const int32_t* 
 // Normal-line rule: degree-4 interpolation in the distance through the interior limit
 // v0 = -(A sigma)(t*) / (2 alpha^2) (trigonometric interpolation of the on-surface
 // values) and the values at the 4 auxiliary points.
-__global__ void k_dlp_line(const int32_t* __restrict__ line_tgt, const int32_t* __restrict__ line_curve,
-                           const double* __restrict__ line_data, int64_t nline, const double* __restrict__ asig,
-                           const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
-                           const double2* __restrict__ half, int64_t n_user, double alpha, double* out) {
+// The interpolation weights D_N(t* - t_i) depend on the target alone and are formed once
+// (k_line_weights): D_N(t* - t_i) = sin(N (t* - t_i)/2) cot((t* - t_i)/2) / N with
+// sin(N (t* - t_i)/2) = (-1)^i sin(N t*/2) and the half angles by the addition formulas.
+__global__ void k_line_weights(const int32_t* __restrict__ line_curve, const double* __restrict__ line_data,
+                               int64_t nline, const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
+                               const double2* __restrict__ half, const int64_t* __restrict__ woff, double* w) {
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (t >= nline) return;
     const int lane = threadIdx.x & 31;
     const int k = line_curve[t];
     const int N = nn[k];
     const double ts = line_data[4 * t];
-    const double* a = asig + off[k];
     const double2* hf = half + off[k];
-    // D_N(t* - t_i) = sin(N (t* - t_i)/2) cot((t* - t_i)/2) / N with sin(N (t* - t_i)/2)
-    // = (-1)^i sin(N t*/2) and the half angles by the addition formulas.
     double sN, cN, sh0, ch0;
     sincos(0.5 * N * ts, &sN, &cN);
     sincos(0.5 * ts, &sh0, &ch0);
-    double acc = 0.0;
     for (int i = lane; i < N; i += 32) {
         const double sh = sh0 * hf[i].x - ch0 * hf[i].y;
         const double ch = ch0 * hf[i].x + sh0 * hf[i].y;
         const double sg = (i & 1) ? -sN : sN;
-        const double dk = fabs(sh) < 1e-300 ? 1.0 : sg * ch / sh / N;
-        acc += dk * a[i];
+        w[woff[t] + i] = fabs(sh) < 1e-300 ? 1.0 : sg * ch / sh / N;
     }
+}
+
+__global__ void k_dlp_line(const int32_t* __restrict__ line_tgt, const int32_t* __restrict__ line_curve,
+                           const double* __restrict__ line_data, int64_t nline, const double* __restrict__ asig,
+                           const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
+                           const double* __restrict__ lw, const int64_t* __restrict__ woff, int64_t n_user,
+                           double alpha, double* out) {
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= nline) return;
+    const int lane = threadIdx.x & 31;
+    const int k = line_curve[t];
+    const int N = nn[k];
+    const double* a = asig + off[k];
+    const double* w = lw + woff[t];
+    double acc = 0.0;
+    for (int i = lane; i < N; i += 32) acc += w[i] * a[i];
     acc = warp_sum(acc);
     if (lane == 0) {
         double vals[5], dist[5];
@@ -1390,10 +1403,10 @@ __global__ void k_dlp_line(const int32_t* __restrict__ line_tgt, const int32_t* 
         double d = line_data[4 * t + 1];
         double r = 0.0;
         for (int i = 0; i < 5; ++i) {
-            double w = 1.0;
+            double wi = 1.0;
             for (int j = 0; j < 5; ++j)
-                if (j != i) w *= (d - dist[j]) / (dist[i] - dist[j]);
-            r += w * vals[i];
+                if (j != i) wi *= (d - dist[j]) / (dist[i] - dist[j]);
+            r += wi * vals[i];
         }
         out[line_tgt[t]] = r;
     }
@@ -2092,6 +2105,16 @@ mh_status dlp_classify(mh_ctx* ctx, mh_boundary* b, const double* xy_dev, int64_
                                                                   tg->n_line, b->coef.p, b->d_nn.p, b->d_off.p, n,
                                                                   tg->xy.p);
         MH_LAUNCHED(ctx);
+        // trigonometric interpolation weights of every line target (fixed with the target)
+        std::vector<int64_t> woff(tg->n_line + 1, 0);
+        for (int64_t t = 0; t < tg->n_line; ++t) woff[t + 1] = woff[t] + b->n_nodes[lcur[t]];
+        MH_ALLOC(ctx, tg->line_woff, tg->n_line + 1);
+        MH_ALLOC(ctx, tg->line_w, std::max<int64_t>(woff[tg->n_line], 1));
+        MH_CUDA(ctx, cudaMemcpyAsync(tg->line_woff.p, woff.data(), (tg->n_line + 1) * 8, cudaMemcpyHostToDevice, st));
+        k_line_weights<<<mh_grid(tg->n_line * 32, 256), 256, 0, st>>>(tg->line_curve.p, tg->line_data.p, tg->n_line,
+                                                                      b->d_nn.p, b->d_off.p, b->half.p,
+                                                                      tg->line_woff.p, tg->line_w.p);
+        MH_LAUNCHED(ctx);
     }
     if (tg->n_pairs) {
         MH_CUDA(ctx, cudaMemcpyAsync(tg->pair_tgt.p, pt.data(), tg->n_pairs * 4, cudaMemcpyHostToDevice, st));
@@ -2197,7 +2220,8 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
         MH_TRY(bie_apply(ctx, b, sigma, asig.p, MH_PREC_FP64));
         k_dlp_line<<<mh_grid(tg->n_line * 32, 256), 256, 0, st>>>(tg->line_tgt.p, tg->line_curve.p, tg->line_data.p,
                                                                   tg->n_line, asig.p, b->d_nn.p, b->d_off.p,
-                                                                  b->half.p, tg->n, alpha, ext.p);
+                                                                  tg->line_w.p, tg->line_woff.p, tg->n, alpha,
+                                                                  ext.p);
         MH_LAUNCHED(ctx);
     }
     if (tg->n) MH_CUDA(ctx, cudaMemcpyAsync(out, ext.p, tg->n * 8, cudaMemcpyDeviceToDevice, st));
@@ -2345,7 +2369,8 @@ mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_t
         MH_TRY(bie_apply(ctx, b, sigma, tg->asig.p, prec));
         k_dlp_line<<<mh_grid(tg->n_line * 32, 256), 256, 0, st>>>(tg->line_tgt.p, tg->line_curve.p, tg->line_data.p,
                                                                   tg->n_line, tg->asig.p, b->d_nn.p, b->d_off.p,
-                                                                  b->half.p, tg->n, alpha, ext.p);
+                                                                  tg->line_w.p, tg->line_woff.p, tg->n, alpha,
+                                                                  ext.p);
         MH_LAUNCHED(ctx);
     }
     if (n) MH_CUDA(ctx, cudaMemcpyAsync(out, ext.p, n * 8, cudaMemcpyDeviceToDevice, st));

@@ -171,6 +171,8 @@ struct dlp_targets {
     dbuf<int32_t> line_tgt;     // target index
     dbuf<int32_t> line_curve;   // curve
     dbuf<double> line_data;     // [n_line][4]: t*, d, h_s, unused
+    dbuf<double> line_w;        // trigonometric interpolation weights at t*, N_k per line target
+    dbuf<int64_t> line_woff;    // [n_line + 1] offsets into line_w
     // fine pairs (ext target, curve)
     int64_t n_pairs = 0, n_pairs_main = 0;   // pairs of user targets come first
     double fine_nodes_main = 0, fine_nodes_aux = 0, curve_nodes_main = 0;   // work counts
