@@ -250,16 +250,18 @@ __device__ __forceinline__ void stage_rows(TD* dst, const TS* __restrict__ src, 
 }
 
 // Batched contraction: each block applies one operator (R x C, row-major) to up to CHUNK
-// source vectors gathered from `vec` and writes the products to temp[task][R].
-// With task_dst given (phases where every destination has exactly one task and sources
-// and destinations do not overlap) the product goes straight to vec[task_dst + r]
-// (added when accumulate is set).
-template <typename TOP>
+// source vectors gathered from the pool `src` (the operators' precision: node values and
+// expansions are kept in that precision, so the gather converts nothing) and writes the
+// products to temp[task][R].  With task_dst given (phases where every destination has exactly
+// one task and sources and destinations do not overlap) the product goes straight to
+// dst[task_dst + r] (added when accumulate is set); dst is the expansion pool (TD = TOP) or the
+// binary64 potentials (TD = double).
+template <typename TOP, typename TD>
 __global__ void k_apply(const TOP* __restrict__ ops, const int64_t* __restrict__ op_off,
                         const int32_t* __restrict__ op_C, const int32_t* __restrict__ chunk_op,
                         const int32_t* __restrict__ chunk_t0, const int64_t* __restrict__ task_src,
-                        const double* vec, int R, double* __restrict__ temp, const int64_t* __restrict__ task_dst,
-                        int accumulate, double* vec_out) {
+                        const TOP* src, int R, TOP* __restrict__ temp, const int64_t* __restrict__ task_dst,
+                        int accumulate, TD* dst) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TOP* sA = reinterpret_cast<TOP*>(smem_raw);
     const int ch = blockIdx.x;
@@ -270,18 +272,42 @@ __global__ void k_apply(const TOP* __restrict__ ops, const int64_t* __restrict__
     const int lda = C + 1;
     TOP* sX = sA + R * lda;
     const TOP* A = ops + op_off[op];
+    if (nt == 1) {
+        // a single source vector (operators owned by one leaf: dipole P2M / P2L): a GEMV that
+        // reads every operator row once, coalesced, straight from global memory
+        const int64_t s0 = task_src[t0];
+        for (int e = threadIdx.x; e < C; e += blockDim.x) sA[e] = src[s0 + e];
+        __syncthreads();
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int r = warp; r < R; r += nw) {
+            const TOP* a = A + (int64_t)r * C;
+            TOP acc = 0;
+            for (int c = lane; c < C; c += 32) acc += a[c] * sA[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) {
+                if (task_dst) {
+                    TD* y = dst + task_dst[t0] + r;
+                    *y = accumulate ? *y + (TD)acc : (TD)acc;
+                } else {
+                    temp[(int64_t)t0 * R + r] = acc;
+                }
+            }
+        }
+        return;
+    }
     stage_rows<TOP, TOP>(sA, A, R * C, C, lda);
     for (int e0 = threadIdx.x; e0 < nt * C; e0 += 4 * blockDim.x) {
-        double v[4];
+        TOP v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int e = e0 + u * blockDim.x;
-            v[u] = e < nt * C ? vec[task_src[t0 + e / C] + e % C] : 0.0;
+            v[u] = e < nt * C ? src[task_src[t0 + e / C] + e % C] : TOP(0);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int e = e0 + u * blockDim.x;
-            if (e < nt * C) sX[(e / C) * lda + e % C] = (TOP)v[u];
+            if (e < nt * C) sX[(e / C) * lda + e % C] = v[u];
         }
     }
     __syncthreads();
@@ -320,10 +346,10 @@ __global__ void k_apply(const TOP* __restrict__ ops, const int64_t* __restrict__
                 const int tt = tg + j * TG;
                 if (tt >= nt) break;
                 if (task_dst) {
-                    double* y = vec_out + task_dst[t0 + tt] + r;
-                    *y = accumulate ? *y + (double)acc[i][j] : (double)acc[i][j];
+                    TD* y = dst + task_dst[t0 + tt] + r;
+                    *y = accumulate ? *y + (TD)acc[i][j] : (TD)acc[i][j];
                 } else {
-                    temp[(int64_t)(t0 + tt) * R + r] = (double)acc[i][j];
+                    temp[(int64_t)(t0 + tt) * R + r] = acc[i][j];
                 }
             }
         }
@@ -353,11 +379,20 @@ __device__ __forceinline__ float chain_fma<float>(float a, float b, float c) { r
 template <>
 __device__ __forceinline__ double chain_fma<double>(double a, double b, double c) { return fma(a, b, c); }
 
+// Row r of an operator times x: A points at row r of the transposed operator (A[cc * P] is
+// entry (r, cc)), x is in shared memory; products added in column order.
+template <typename TOP>
+__device__ __forceinline__ TOP chain_dot(const TOP* __restrict__ A, int P, const TOP* x) {
+    TOP acc = 0;
+    for (int cc = 0; cc < P; ++cc) acc = chain_fma<TOP>(A[(int64_t)cc * P], x[cc], acc);
+    return acc;
+}
+
 template <typename TOP>
 __global__ void k_chain_up(const TOP* __restrict__ ops, int P, const int32_t* __restrict__ ready,
                            const int32_t* __restrict__ box, const int4* __restrict__ child,
                            const int32_t* __restrict__ lvl, const int32_t* __restrict__ next,
-                           const int32_t* __restrict__ need, unsigned* cnt, int64_t base, double* vec) {
+                           const int32_t* __restrict__ need, unsigned* cnt, int64_t base, TOP* vec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TOP* x = reinterpret_cast<TOP*>(smem_raw);   // 4 x P child expansions
     TOP* part = x + 4 * P;                        // 4 x P products
@@ -369,21 +404,17 @@ __global__ void k_chain_up(const TOP* __restrict__ ops, int P, const int32_t* __
         const int4 ch4 = child[t];
         const int chc = c == 0 ? ch4.x : c == 1 ? ch4.y : c == 2 ? ch4.z : ch4.w;
         // children may have been written by other blocks of this launch: read through L2
-        if (act) x[c * P + r] = chc >= 0 ? (TOP)__ldcg(vec + base + (int64_t)chc * P + r) : (TOP)0;
+        if (act) x[c * P + r] = chc >= 0 ? __ldcg(vec + base + (int64_t)chc * P + r) : TOP(0);
         __syncthreads();
         TOP acc = 0;
-        if (act && chc >= 0) {
-            const TOP* A = ops + (int64_t)(lvl[t] * 4 + c) * P * P + r;
-            const TOP* xc = x + c * P;
-            for (int cc = 0; cc < P; ++cc) acc = chain_fma<TOP>(A[(int64_t)cc * P], xc[cc], acc);
-        }
+        if (act && chc >= 0) acc = chain_dot<TOP>(ops + (int64_t)(lvl[t] * 4 + c) * P * P + r, P, x + c * P);
         if (act) part[c * P + r] = acc;
         __syncthreads();
         if (threadIdx.x < P) {
             TOP s = part[r] + part[P + r];
             s += part[2 * P + r];
             s += part[3 * P + r];
-            vec[base + (int64_t)box[t] * P + r] = (double)s;
+            vec[base + (int64_t)box[t] * P + r] = s;
             __threadfence();
         }
         const int q = next[t];
@@ -402,50 +433,62 @@ template <typename TOP>
 __global__ void k_chain_down(const TOP* __restrict__ ops, int P, const int32_t* __restrict__ poff,
                              const int32_t* __restrict__ pbox, const int32_t* __restrict__ pop,
                              const int4* __restrict__ leaf, const int32_t* __restrict__ lop, int64_t base,
-                             double* vec) {
+                             TOP* vec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TOP* x = reinterpret_cast<TOP*>(smem_raw);   // the running ancestor expansion
     const int c = threadIdx.x / P, r = threadIdx.x - c * P;
     const int k0 = poff[blockIdx.x], k1 = poff[blockIdx.x + 1];
-    if (threadIdx.x < P) x[r] = (TOP)vec[base + (int64_t)pbox[k0] * P + r];
+    const int64_t PP = (int64_t)P * P;
+    if (threadIdx.x < P) x[r] = vec[base + (int64_t)pbox[k0] * P + r];
     for (int k = k0 + 1; k < k1; ++k) {
         __syncthreads();
         TOP acc = 0;
-        if (threadIdx.x < P) {
-            const TOP* A = ops + (int64_t)pop[k] * P * P + r;
-            for (int cc = 0; cc < P; ++cc) acc = chain_fma<TOP>(A[(int64_t)cc * P], x[cc], acc);
-        }
+        if (threadIdx.x < P) acc = chain_dot<TOP>(ops + (int64_t)pop[k] * PP + r, P, x);
         __syncthreads();
-        if (threadIdx.x < P) x[r] = (TOP)(vec[base + (int64_t)pbox[k] * P + r] + (double)acc);
+        if (threadIdx.x < P) x[r] = vec[base + (int64_t)pbox[k] * P + r] + acc;
     }
     __syncthreads();
     if (c < 4) {
         const int4 l4 = leaf[blockIdx.x];
         const int lc = c == 0 ? l4.x : c == 1 ? l4.y : c == 2 ? l4.z : l4.w;
-        if (lc >= 0) {
-            const TOP* A = ops + (int64_t)(lop[blockIdx.x] + c) * P * P + r;
-            TOP acc = 0;
-            for (int cc = 0; cc < P; ++cc) acc = chain_fma<TOP>(A[(int64_t)cc * P], x[cc], acc);
-            vec[base + (int64_t)lc * P + r] += (double)acc;
-        }
+        if (lc >= 0) vec[base + (int64_t)lc * P + r] += chain_dot<TOP>(ops + (lop[blockIdx.x] + c) * PP + r, P, x);
     }
 }
 
 inline int chain_threads(int P) { return (4 * P + 31) / 32 * 32; }
 
-// Per destination (one warp each): vec[dst + r] = (acc ? vec : 0) + sum of its products.
-__global__ void k_reduce(const double* __restrict__ temp, int R, const int64_t* __restrict__ dst_off,
+// Per destination (one warp each): dst[r] = (acc ? dst[r] : 0) + the sum of its tasks' products,
+// in task order.  Binary64 products are summed in binary64; binary32 products in float-float
+// (TwoSum: the sum of the products with binary64-like accuracy and no binary64 instruction per
+// product), converted once per output.
+template <typename TT, typename TD>
+__global__ void k_reduce(const TT* __restrict__ temp, int R, const int64_t* __restrict__ dst_off,
                          const int32_t* __restrict__ dst_ptr, const int32_t* __restrict__ dst_task, int64_t n_dst,
-                         int accumulate, double* vec) {
+                         int accumulate, TD* dst) {
     const int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (d >= n_dst) return;
     const int j0 = dst_ptr[d], j1 = dst_ptr[d + 1];
-    double* y = vec + dst_off[d];
+    TD* y = dst + dst_off[d];
     for (int r = lane; r < R; r += 32) {
-        double s = accumulate ? y[r] : 0.0;
-        for (int j = j0; j < j1; ++j) s += temp[(int64_t)dst_task[j] * R + r];
-        y[r] = s;
+        if (sizeof(TT) == 8) {
+            double s = accumulate ? (double)y[r] : 0.0;
+            for (int j = j0; j < j1; ++j) s += (double)temp[(int64_t)dst_task[j] * R + r];
+            y[r] = (TD)s;
+        } else {
+            float hi = 0.f, lo = 0.f;
+            for (int j = j0; j < j1; ++j) {
+                const float v = (float)temp[(int64_t)dst_task[j] * R + r];
+                const float t = hi + v;
+                const float bb = t - hi;
+                lo += (hi - (t - bb)) + (v - bb);
+                hi = t;
+            }
+            if (sizeof(TD) == 8)
+                y[r] = (TD)((accumulate ? (double)y[r] : 0.0) + ((double)hi + (double)lo));
+            else
+                y[r] = (TD)(accumulate ? (float)y[r] + (hi + lo) : hi + lo);
+        }
     }
 }
 
@@ -460,6 +503,7 @@ struct Phase {
     int R = 0;
     bool accumulate = false;
     bool direct = false;           // one task per destination: products written in place
+    bool dst_out = false;          // destinations are the binary64 potentials (else expansions)
     dbuf<int64_t> task_dst;        // destination offset of every (sorted) task when direct
     double flops = 0, bytes = 0;   // per run: 2 R C per task; operators, sources, products, outputs
     int64_t n_tasks = 0, n_dst = 0, n_chunks = 0;
@@ -512,7 +556,7 @@ struct VolData {
     int P = 0, qq = 0;
     int64_t B_off = 0, U_off = 0, M_off = 0, L_off = 0, vec_len = 0;
     dbuf<double> ops64, vec, temp;
-    dbuf<float> ops32;
+    dbuf<float> ops32, vec32;            // vec32: binary32 mirror of vec (node values, expansions)
     dbuf<int64_t> d_op_off;
     dbuf<int32_t> d_op_C;
     std::vector<int> op_C;
@@ -602,29 +646,49 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
     return MH_OK;
 }
 
+// Expansion pool of the operators' precision: binary64 uses the main pool itself, binary32 its
+// float mirror (same layout).
 template <typename TOP>
-mh_status run_phase_on(mh_ctx* ctx, const TOP* ops, const int64_t* op_off, const int32_t* op_C, double* vec,
-                       double* temp, const Phase* ph, const char* region) {
+inline TOP* typed_pool(dbuf<double>& v64, dbuf<float>& v32);
+template <>
+inline double* typed_pool<double>(dbuf<double>& v64, dbuf<float>&) { return v64.p; }
+template <>
+inline float* typed_pool<float>(dbuf<double>&, dbuf<float>& v32) { return v32.p; }
+
+template <typename TOP>
+mh_status run_phase_on(mh_ctx* ctx, const TOP* ops, const int64_t* op_off, const int32_t* op_C, TOP* pool,
+                       double* out, double* temp, const Phase* ph, const char* region) {
     if (ph->n_tasks == 0) return MH_OK;
     const int smem = (int)(ph->smem / sizeof(double) * sizeof(TOP));
     prof_scope ps(ctx, region, ph->flops, ph->bytes + 8.0 * ph->R * ph->n_dst * (ph->accumulate ? 2 : 1));
-    k_apply<TOP><<<(unsigned)ph->n_chunks, 256, smem, ctx->stream>>>(
-        ops, op_off, op_C, ph->chunk_op.p, ph->chunk_t0.p, ph->task_src.p, vec, ph->R, temp,
-        ph->direct ? ph->task_dst.p : nullptr, ph->accumulate ? 1 : 0, vec);
-    MH_LAUNCHED(ctx);
-    if (!ph->direct) {
-        k_reduce<<<mh_grid(ph->n_dst * 32, 256), 256, 0, ctx->stream>>>(temp, ph->R, ph->dst_off.p, ph->dst_ptr.p,
-                                                                        ph->dst_task.p, ph->n_dst, ph->accumulate,
-                                                                        vec);
+    TOP* tmp = reinterpret_cast<TOP*>(temp);   // sized in binary64 words: room for either type
+    const int acc = ph->accumulate ? 1 : 0;
+    const int64_t* tdst = ph->direct ? ph->task_dst.p : nullptr;
+    const unsigned rg = (unsigned)mh_grid(ph->n_dst * 32, 256);
+    if (ph->dst_out) {
+        k_apply<TOP, double><<<(unsigned)ph->n_chunks, 256, smem, ctx->stream>>>(
+            ops, op_off, op_C, ph->chunk_op.p, ph->chunk_t0.p, ph->task_src.p, pool, ph->R, tmp, tdst, acc, out);
         MH_LAUNCHED(ctx);
+        if (!ph->direct) {
+            k_reduce<TOP, double><<<rg, 256, 0, ctx->stream>>>(tmp, ph->R, ph->dst_off.p, ph->dst_ptr.p,
+                                                               ph->dst_task.p, ph->n_dst, acc, out);
+            MH_LAUNCHED(ctx);
+        }
+    } else {
+        k_apply<TOP, TOP><<<(unsigned)ph->n_chunks, 256, smem, ctx->stream>>>(
+            ops, op_off, op_C, ph->chunk_op.p, ph->chunk_t0.p, ph->task_src.p, pool, ph->R, tmp, tdst, acc, pool);
+        MH_LAUNCHED(ctx);
+        if (!ph->direct) {
+            k_reduce<TOP, TOP><<<rg, 256, 0, ctx->stream>>>(tmp, ph->R, ph->dst_off.p, ph->dst_ptr.p,
+                                                            ph->dst_task.p, ph->n_dst, acc, pool);
+            MH_LAUNCHED(ctx);
+        }
     }
     return MH_OK;
 }
 
-
-
 template <typename TOP>
-mh_status run_chain(mh_ctx* ctx, const DfChain* ch, int P, int64_t m_base, int64_t l_base, double* vec,
+mh_status run_chain(mh_ctx* ctx, const DfChain* ch, int P, int64_t m_base, int64_t l_base, TOP* vec,
                     bool upward, const char* region) {
     // the level chains are timed in their own region: "<pass>_chain"
     if (!ch || ch->n_int == 0) return MH_OK;
@@ -648,7 +712,8 @@ mh_status run_chain(mh_ctx* ctx, const DfChain* ch, int P, int64_t m_base, int64
 
 template <typename TOP>
 mh_status run_phase(mh_ctx* ctx, VolData* V, const TOP* ops, const Phase* ph) {
-    return run_phase_on<TOP>(ctx, ops, V->d_op_off.p, V->d_op_C.p, V->vec.p, V->temp.p, ph, "volume_contract");
+    return run_phase_on<TOP>(ctx, ops, V->d_op_off.p, V->d_op_C.p, typed_pool<TOP>(V->vec, V->vec32), V->vec.p,
+                             V->temp.p, ph, "volume_contract");
 }
 
 struct HostTree {
@@ -1111,15 +1176,21 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
     MH_TRY(build_phase(ctx, t_m2l, P, false, V->op_C, V->m2l.get(), &need));
     V->out.reset(new Phase());
     MH_TRY(build_phase(ctx, t_out, qq, false, V->op_C, V->out.get(), &need));
+    V->out->dst_out = true;
     MH_ALLOC(ctx, V->vec, V->vec_len);
+    MH_ALLOC(ctx, V->vec32, V->vec_len);
     MH_ALLOC(ctx, V->temp, need);
     V->temp_len = need;
     MH_CUDA(ctx, cudaMemsetAsync(V->vec.p, 0, V->vec_len * 8, st));
+    MH_CUDA(ctx, cudaMemsetAsync(V->vec32.p, 0, V->vec_len * 4, st));
     // shared-memory opt-in for the contraction kernel
     int maxs = 0;
     for (auto* ph : {V->p2m.get(), V->m2l.get(), V->out.get()}) maxs = std::max(maxs, ph->smem);
-    MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-    MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      160 * 1024));
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      160 * 1024));
     if (chain_threads(P) > 1024)
         return mh_fail(ctx, MH_ERR_INVALID_ARG, "multipole order too large for the chain kernels");
     return MH_OK;
@@ -1282,12 +1353,11 @@ struct DipData {
     dbuf<int32_t> flat_idx;                // dipole of every flat entry
     dbuf<float4> flat32;                   // its offset from the target leaf centre + normal (binary32)
     dbuf<double2> leaf_c, dxy, dnrm;       // leaf centres; dipole positions and normals (sorted)
-    dbuf<float> w32;
     double pref = 0, inv_alpha = 0;
     double near_pairs = 0;
     int near_t = 256;                      // threads per block of the binary32 near-field kernel
     dbuf<double> vec, temp, ops64;
-    dbuf<float> ops32;
+    dbuf<float> ops32, vec32;              // vec32: binary32 mirror of vec (weights, expansions)
     dbuf<int64_t> d_op_off;
     dbuf<int32_t> d_op_C;
     std::unique_ptr<Phase> p2m, m2l, out;
@@ -1533,7 +1603,6 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
         MH_ALLOC(ctx, D->leaf_c, nl);
         MH_ALLOC(ctx, D->dxy, std::max<int64_t>(nd, 1));
         MH_ALLOC(ctx, D->dnrm, std::max<int64_t>(nd, 1));
-        MH_ALLOC(ctx, D->w32, std::max<int64_t>(nd, 1));
         if (!ch.empty())
             MH_CUDA(ctx, cudaMemcpyAsync(D->chunks.p, ch.data(), ch.size() * sizeof(NearChunk), cudaMemcpyHostToDevice, st));
         MH_CUDA(ctx, cudaMemcpyAsync(D->leaf_red.p, lred.data(), nl * sizeof(int2), cudaMemcpyHostToDevice, st));
@@ -1572,9 +1641,12 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
     MH_TRY(build_phase(ctx, t_m2l, P, false, opC, D->m2l.get(), &need));
     D->out.reset(new Phase());
     MH_TRY(build_phase(ctx, t_out, qq, !near_blocks, opC, D->out.get(), &need));
+    D->out->dst_out = true;
     MH_ALLOC(ctx, D->vec, D->vec_len);
+    MH_ALLOC(ctx, D->vec32, D->vec_len);
     MH_ALLOC(ctx, D->temp, need);
     MH_CUDA(ctx, cudaMemsetAsync(D->vec.p, 0, D->vec_len * 8, st));
+    MH_CUDA(ctx, cudaMemsetAsync(D->vec32.p, 0, D->vec_len * 4, st));
     MH_CUDA(ctx, cudaStreamSynchronize(st));
     V->dip = std::move(D);
     return MH_OK;
@@ -1582,15 +1654,15 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
 
 template <typename TOP>
 static mh_status dipole_run(mh_ctx* ctx, VolData* V, DipData* D, const TOP* ops) {
+    TOP* pool = typed_pool<TOP>(D->vec, D->vec32);
     auto run = [&](const Phase* ph) {
-        return run_phase_on<TOP>(ctx, ops, D->d_op_off.p, D->d_op_C.p, D->vec.p, D->temp.p, ph, "dlp_fmm_contract");
+        return run_phase_on<TOP>(ctx, ops, D->d_op_off.p, D->d_op_C.p, pool, D->vec.p, D->temp.p, ph,
+                                 "dlp_fmm_contract");
     };
     MH_TRY(run(D->p2m.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, D->vec.p, true,
-                          "dlp_fmm_chain"));
+    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, pool, true, "dlp_fmm_chain"));
     MH_TRY(run(D->m2l.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, D->vec.p, false,
-                          "dlp_fmm_chain"));
+    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, pool, false, "dlp_fmm_chain"));
     MH_TRY(run(D->out.get()));
     return MH_OK;
 }
@@ -1603,24 +1675,27 @@ mh_status volume_dipole_apply(mh_ctx* ctx, mh_tree* t, const double* w_sorted, m
     DipData* D = V->dip.get();
     prof_scope ps(ctx, "dlp_fmm");
     cudaStream_t st = ctx->stream;
-    MH_CUDA(ctx, cudaMemcpyAsync(D->vec.p + D->W_off, w_sorted, D->nd * 8, cudaMemcpyDeviceToDevice, st));
     if (!D->near_blocks) MH_CUDA(ctx, cudaMemsetAsync(D->vec.p + D->DU_off, 0, t->n_leaves * D->qq * 8, st));
-    if (prec == MH_PREC_MIXED)
+    if (prec == MH_PREC_MIXED) {
+        // weights in binary32 once: the contractions and the near-field kernel read them
+        k_d2f<<<mh_grid(D->nd, 256), 256, 0, st>>>(w_sorted, D->vec32.p + D->W_off, D->nd);
+        MH_LAUNCHED(ctx);
         MH_TRY(dipole_run<float>(ctx, V, D, D->ops32.p));
-    else
+    } else {
+        MH_CUDA(ctx, cudaMemcpyAsync(D->vec.p + D->W_off, w_sorted, D->nd * 8, cudaMemcpyDeviceToDevice, st));
         MH_TRY(dipole_run<double>(ctx, V, D, D->ops64.p));
+    }
     if (!D->near_blocks && D->n_chunks) {
         prof_scope ps2(ctx, "dlp_near", 68.0 * D->near_pairs, 24.0 * (double)D->nd);
         const unsigned nb = (unsigned)D->n_chunks;
         double* out = D->vec.p + D->DU_off;
         if (prec == MH_PREC_MIXED) {
-            k_d2f<<<mh_grid(D->nd, 256), 256, 0, st>>>(w_sorted, D->w32.p, D->nd);
-            MH_LAUNCHED(ctx);
+            const float* w32 = D->vec32.p + D->W_off;
             const mh_dl32 c32 = mh_dl32_make(1.0 / D->inv_alpha, 30.0);
             const double pref32 = D->pref * D->inv_alpha * D->inv_alpha;
 #define MH_NEAR32(NTV)                                                                                         \
     k_dip_near32<NTV><<<nb, NTV, 0, st>>>(t->nodes.p, D->chunks.p, D->leaf_red.p, D->leaf_c.p, D->flat_idx.p,  \
-                                          D->flat32.p, D->w32.p, D->qq, c32, pref32, D->part.p, D->red_cnt.p, out)
+                                          D->flat32.p, w32, D->qq, c32, pref32, D->part.p, D->red_cnt.p, out)
             if (D->near_t == 128)
                 MH_NEAR32(128);
             else if (D->near_t == 512)
@@ -1661,12 +1736,11 @@ void volume_free(mh_tree* t) {
 
 template <typename TOP>
 static mh_status volume_run(mh_ctx* ctx, mh_tree* t, VolData* V, const TOP* ops) {
+    TOP* pool = typed_pool<TOP>(V->vec, V->vec32);
     MH_TRY(run_phase(ctx, V, ops, V->p2m.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, V->M_off, V->L_off, V->vec.p, true,
-                          "volume_chain"));
+    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, V->M_off, V->L_off, pool, true, "volume_chain"));
     MH_TRY(run_phase(ctx, V, ops, V->m2l.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, V->M_off, V->L_off, V->vec.p, false,
-                          "volume_chain"));
+    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, V->M_off, V->L_off, pool, false, "volume_chain"));
     MH_TRY(run_phase(ctx, V, ops, V->out.get()));
     return MH_OK;
 }
@@ -1687,11 +1761,15 @@ mh_status volume_apply(mh_ctx* ctx, mh_tree* t, double alpha, int p, const doubl
     }
     const int64_t nn = t->n_nodes;
     prof_scope ps(ctx, "volume_apply");
-    MH_CUDA(ctx, cudaMemcpyAsync(V->vec.p + V->B_off, b, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-    if (prec == MH_PREC_MIXED)
+    if (prec == MH_PREC_MIXED) {
+        // node values in binary32 once: every contraction then gathers binary32
+        k_d2f<<<mh_grid(nn, 256), 256, 0, ctx->stream>>>(b, V->vec32.p + V->B_off, nn);
+        MH_LAUNCHED(ctx);
         MH_TRY(volume_run<float>(ctx, t, V, V->ops32.p));
-    else
+    } else {
+        MH_CUDA(ctx, cudaMemcpyAsync(V->vec.p + V->B_off, b, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
         MH_TRY(volume_run<double>(ctx, t, V, V->ops64.p));
+    }
     MH_CUDA(ctx, cudaMemcpyAsync(up, V->vec.p + V->U_off, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     return MH_OK;
 }
