@@ -154,22 +154,39 @@ def run_ours(args):
     f_next = torch.zeros(bnd.n, dtype=torch.float64, device=dev)     # f = 0 on every curve
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def run_steps(k, u, sigma, timed, prec_):
+    # graph form (default): the step of this one problem is one CUDA graph launch through the
+    # batch API (mh_batch_step), GMRES included (device-side loops, no host round trips); the
+    # graph is recorded on fixed arrays at the first call
+    batch = mh.Batch(ctx, [prob]) if args.graph else None
+    ub = torch.zeros(tree.n_nodes, dtype=torch.float64, device=dev)
+    sb = torch.zeros(bnd.n, dtype=torch.float64, device=dev)
+
+    def run_steps(k, u, sigma, timed, prec_, graph=False):
         un = torch.empty_like(u)
         times, its = [], []
+        if graph:
+            ub.copy_(u)
+            sb.copy_(sigma)
         for _ in range(k):
             if timed:
                 flush.zero_()
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
                 a.record()
-            info = mh.heat_step(ctx, prob, u, F, f_next, un, sigma, gmres_tol=1e-10, prec=prec_)
+            if graph:
+                info = batch.step([ub], [F], [f_next], [sb], gmres_tol=1e-10, prec=prec_)[0]
+            else:
+                info = mh.heat_step(ctx, prob, u, F, f_next, un, sigma, gmres_tol=1e-10, prec=prec_)
             if timed:
                 b.record()
                 b.synchronize()
                 times.append(a.elapsed_time(b))
             its.append(info.gmres_iterations)
-            u, un = un, u
+            if not graph:
+                u, un = un, u
+        if graph:
+            u.copy_(ub)
+            sigma.copy_(sb)
         return u, times, its
 
     # learned start: trained on this geometry from solver trajectories of other forcings
@@ -204,7 +221,7 @@ def run_ours(args):
         set_start(mh.MH_WARM_PREVIOUS)
         u64, _, _ = run_steps(args.check_steps, u0.clone(), s64, False, mh.MH_PREC_FP64)
         set_start(warm_mode)
-        u32, _, _ = run_steps(args.check_steps, u0.clone(), s32, False, prec)
+        u32, _, _ = run_steps(args.check_steps, u0.clone(), s32, False, prec, args.graph)
         regions = prob.regions()
         ins = torch.tensor(regions == -1, device=dev)
         err = float(torch.linalg.norm((u32 - u64)[ins]) / torch.linalg.norm(u64[ins]))
@@ -217,24 +234,31 @@ def run_ours(args):
     set_start(warm_mode)
 
     sigma = torch.zeros(bnd.n, dtype=torch.float64, device=dev)
-    u, _, _ = run_steps(args.warmup, u0.clone(), sigma, False, prec)
-    ctx.profile(True)
-    ctx.profile_read("gmres", reset=True)
+    u, _, _ = run_steps(args.warmup, u0.clone(), sigma, False, prec, args.graph)
     launches0 = ctx.launches
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
         torch.cuda.nvtx.range_push("timed_steps")      # lets a profiler select the timed region
-        u, times, its = run_steps(args.steps, u, sigma, True, prec)
+        u, times, its = run_steps(args.steps, u, sigma, True, prec, args.graph)
         torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
     launches = ctx.launches - launches0
+    value, total_ms = aggregate_over_ranks(sum(times), n_pts, args.steps, dist, dev)
+    # the same number of steps again with the library's region timers on (a CUDA event pair on
+    # the library's stream around every region): per-kernel durations for the roofline.  Kept
+    # out of the headline region, whose steps run without the extra event records.
+    ctx.profile(True)
+    ctx.profile_read("gmres", reset=True)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk_prof:
+        u, times_prof, _ = run_steps(args.steps, u, sigma, True, prec)
+    torch.cuda.synchronize(dev)
     regions_ms = {}
     for r in REGION_NAMES:
         regions_ms[r] = ctx.profile_read(r)
     ctx.profile(False)
-    value, total_ms = aggregate_over_ranks(sum(times), n_pts, args.steps, dist, dev)
     # end to end through the API with host buffers
     pin = lambda a: torch.tensor(a).pin_memory()
     u_h = pin(u.cpu().numpy())
@@ -245,6 +269,12 @@ def run_ours(args):
     Fd = torch.empty_like(F)
     fd = torch.empty_like(f_next)
     und = torch.empty_like(u)
+    e2e_batch = None
+    if args.graph:   # the graph of the host-buffer form is recorded on these arrays (untimed)
+        del batch
+        e2e_batch = mh.Batch(ctx, [prob])
+        ud.copy_(u)
+        e2e_batch.step([ud], [Fd], [fd], [sigma], gmres_tol=1e-10, prec=prec)
     e2e_times = []
     for _ in range(args.steps):
         flush.zero_()
@@ -254,8 +284,12 @@ def run_ours(args):
         ud.copy_(u_h, non_blocking=True)
         Fd.copy_(F_h, non_blocking=True)
         fd.copy_(f_h, non_blocking=True)
-        mh.heat_step(ctx, prob, ud, Fd, fd, und, sigma, gmres_tol=1e-10, prec=prec)
-        out_h.copy_(und, non_blocking=True)
+        if args.graph:
+            e2e_batch.step([ud], [Fd], [fd], [sigma], gmres_tol=1e-10, prec=prec)
+            out_h.copy_(ud, non_blocking=True)
+        else:
+            mh.heat_step(ctx, prob, ud, Fd, fd, und, sigma, gmres_tol=1e-10, prec=prec)
+            out_h.copy_(und, non_blocking=True)
         b.record()
         b.synchronize()
         e2e_times.append(a.elapsed_time(b))
@@ -287,6 +321,8 @@ def run_ours(args):
                                "IMEX Euler, GMRES tol 1e-10" % tree.n_nodes,
                    "points": n_pts, "n_gamma": bnd.n, "n_d": tree.n_nodes, "precision": args.prec,
                    "l2": "flushed between timed steps (256 MB write, untimed)", "near_tile": near_tile,
+                   "step_form": ("one CUDA graph launch per step (mh_batch_step of this problem)" if args.graph
+                                 else "heat_step on the stream"),
                    "parallelism": "replicas" if world > 1 else "single"},
         "rel_l2_vs_fp64_path": err,
         "gmres_iterations": its,
@@ -295,6 +331,8 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "points*timesteps/s", "h2d_bytes_per_step": bytes_in,
                 "d2h_bytes_per_step": bytes_out},
         "gpu_launches": launches,
+        "profiled_ms_per_step": float(np.mean(times_prof)),
+        "profiled_clocks": clk_prof.summary(),
         "regions_ms_per_step": {k: v[0] / args.steps for k, v in regions_ms.items()},
         "kernel_launches_per_step": {k: v[1] / args.steps for k, v in regions_ms.items()},
         "roofline": roof,
@@ -645,6 +683,8 @@ def main():
                     help="batch workload: p = 16 and the default near-field tile instead of the autotuner")
     ap.add_argument("--warm", choices=["learned", "previous", "secant", "zero"], default="learned",
                     help="GMRES start of every step (learned: the trained network with the bfloat16-pair weights)")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="step through heat_step on the stream instead of one graph launch per step")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()

@@ -26,7 +26,8 @@ struct mh_batch {
     std::vector<gmres_dev> stat_h;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int64_t graph_kernels = 0;
+    int64_t graph_kernels = 0;           // kernel nodes, a loop body counted once
+    int64_t loop_nodes = 0;              // GMRES WHILE nodes (bodies of GMRES_LOOP_KERNELS kernels)
     std::vector<const void*> key;
     double key_tol = -1.0;
     int key_prec = -1;
@@ -169,7 +170,7 @@ extern "C" mh_status mh_batch_step(mh_ctx* ctx, mh_batch* B, double* const* u_de
                              gmres_tol, prec, nullptr));
         // record the graph of the following steps
         B->drop_graph();
-        const int64_t l0 = ctx->launches;
+        const int64_t l0 = ctx->launches, ln0 = ctx->loop_nodes;
         const bool prof = ctx->profiling;
         ctx->profiling = false;
         cudaStream_t main = ctx->stream;
@@ -192,6 +193,7 @@ extern "C" mh_status mh_batch_step(mh_ctx* ctx, mh_batch* B, double* const* u_de
         const cudaError_t ee = cudaStreamEndCapture(cap, &g);
         ctx->profiling = prof;
         B->graph_kernels = ctx->launches - l0;
+        B->loop_nodes = ctx->loop_nodes - ln0;
         ctx->launches = l0;
         if (st != MH_OK || ce != cudaSuccess || ee != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -205,13 +207,17 @@ extern "C" mh_status mh_batch_step(mh_ctx* ctx, mh_batch* B, double* const* u_de
         B->key = key;
         B->key_tol = gmres_tol;
         B->key_prec = (int)prec;
-    } else {
-        MH_CUDA(ctx, cudaGraphLaunch(B->exec, ctx->stream));
-        ctx->launches += B->graph_kernels;
     }
+    const bool launched = !record;
+    if (launched) MH_CUDA(ctx, cudaGraphLaunch(B->exec, ctx->stream));
     MH_CUDA(ctx, cudaMemcpyAsync(B->stat_h.data(), B->stat.p, n * sizeof(gmres_dev), cudaMemcpyDeviceToHost,
                                  ctx->stream));
     MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (launched) {   // kernels run: the recorded nodes, each loop body once per Arnoldi iteration
+        int64_t its = 0;
+        for (int i = 0; i < n; ++i) its += B->stat_h[i].total;
+        ctx->launches += B->graph_kernels + (B->loop_nodes ? GMRES_LOOP_KERNELS * (its - B->loop_nodes) : 0);
+    }
     int bad = -1;
     for (int i = 0; i < n; ++i) {
         mh_gmres_info gi{};

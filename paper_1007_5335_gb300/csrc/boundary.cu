@@ -812,11 +812,15 @@ __global__ void k_update_x(const double* __restrict__ V, const double* __restric
 // so the iteration is deterministic.
 constexpr int ARN_ROWS = 64;
 
-// P[s k1 + i] = sum over slice s of V_i[e] w[e], i < k1 (a warp per i).
+// P[s k1 + i] = sum over slice s of V_i[e] w[e], i < k1 (a warp per i).  With kdev, k1 is
+// *kdev + 1 (the iteration count of a sweep kept on the device: one kernel node serves every
+// iteration of a graph loop).
 __global__ void __launch_bounds__(256) k_arn_dots(const double* __restrict__ V, const double* __restrict__ w,
                                                   int64_t n, int k1, double* __restrict__ P,
-                                                  const int* __restrict__ gate = nullptr) {
+                                                  const int* __restrict__ gate = nullptr,
+                                                  const int* __restrict__ kdev = nullptr) {
     if (gate && *gate) return;
+    if (kdev) k1 = *kdev + 1;
     const int s = blockIdx.x;
     const int64_t r0 = (int64_t)s * ARN_ROWS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -837,8 +841,10 @@ __global__ void __launch_bounds__(256) k_arn_dots(const double* __restrict__ V, 
 __global__ void __launch_bounds__(256) k_arn_update(const double* __restrict__ V, double* __restrict__ w, int64_t n,
                                                     int k1, const double* __restrict__ Pin, int S,
                                                     double* __restrict__ Pdots, double* __restrict__ Pnorm,
-                                                    double* __restrict__ hout, const int* __restrict__ gate = nullptr) {
+                                                    double* __restrict__ hout, const int* __restrict__ gate = nullptr,
+                                                    const int* __restrict__ kdev = nullptr) {
     if (gate && *gate) return;
+    if (kdev) k1 = *kdev + 1;
     extern __shared__ double sh[];      // h[k1], then the slice of w
     double* h = sh;
     double* wsl = sh + k1;
@@ -886,14 +892,21 @@ __global__ void __launch_bounds__(256) k_arn_update(const double* __restrict__ V
 // ||w|| from the partial norms; v_{k+1} = w / ||w|| (and its binary32 copy when vnext32 is
 // given).  Block 0 forms column k of H (h1 + h2, ||w||), applies the previous Givens
 // rotations, forms rotation k, updates g and stores |g_{k+1}| in small[0].
+// Graph loops: with kdev (= &gs->k), k comes from the device and v_{k+1} goes to
+// vnext + (k + 1) n; with loop_set, block 0 sets the loop's condition to "not ended".
 __global__ void __launch_bounds__(256) k_arn_finish(const double* __restrict__ w, int64_t n,
                                                     const double* __restrict__ Pn, int S, int k,
                                                     const double* __restrict__ h1, const double* __restrict__ h2,
                                                     double* H, int ldh, double* cs, double* sn, double* g,
                                                     double* small, double* __restrict__ vnext,
                                                     float* __restrict__ vnext32, gmres_dev* gs = nullptr,
-                                                    int m_max = 0) {
+                                                    int m_max = 0, const int* kdev = nullptr,
+                                                    cudaGraphConditionalHandle loop = 0, int loop_set = 0) {
     if (gs && gs->skip) return;
+    if (kdev) {
+        k = *kdev;
+        vnext += (int64_t)(k + 1) * n;
+    }
     __shared__ double nrm;
     if (threadIdx.x < 32) {
         double a = 0.0;
@@ -947,6 +960,7 @@ __global__ void __launch_bounds__(256) k_arn_finish(const double* __restrict__ w
             gs->k = k + 1;
             gs->total += 1;
             if (fabs(sv * gk) <= gs->target || k + 1 >= m_max || den == 0.0) gs->skip = 1;
+            if (loop_set) cudaGraphSetConditional(loop, gs->skip ? 0u : 1u);
         }
     }
     __syncthreads();
@@ -1828,6 +1842,7 @@ mh_status gmres_graph_ensure(mh_ctx* ctx, mh_boundary* bd, int max_iter) {
     MH_ALLOC(ctx, ws.P2, S * (max_iter + 1));
     MH_ALLOC(ctx, ws.Pn, S);
     MH_ALLOC(ctx, ws.v32, n);
+    if (!ws.body_stream) MH_CUDA(ctx, cudaStreamCreateWithFlags(&ws.body_stream, cudaStreamNonBlocking));
     ws.m = max_iter;
     ws.n = n;
     return MH_OK;
@@ -1861,9 +1876,11 @@ __global__ void k_gsub(const double* __restrict__ b, double* r, int64_t n, const
 // rn <= tol ||b||, else start an Arnoldi process on r (V_0 = r / rn, g = (rn, 0, ...), inner
 // target max(tol ||b||, 1e-5 rn) in mixed precision, tol ||b|| in binary64).  final_check: the
 // last residual of the schedule, recorded only.  ||b|| = 0 gives x = 0.
+// With loop_set, the condition of the sweep's Arnoldi loop (a graph WHILE node, 0 by default at
+// every launch) is set to "start".
 __global__ void k_sweep_begin(gmres_dev* gs, double tol, int mixed, int may_accept, int final_check, int first,
                               const double* __restrict__ r, double* V0, float* v32, double* g, int gsz, int64_t n,
-                              double* x) {
+                              double* x, cudaGraphConditionalHandle loop = 0, int loop_set = 0) {
     if (gs->done) return;
     const double rn = gs->rn, bn = gs->bnorm;
     if (bn == 0.0) {
@@ -1893,6 +1910,7 @@ __global__ void k_sweep_begin(gmres_dev* gs, double tol, int mixed, int may_acce
         } else {
             gs->skip = 1;
         }
+        if (loop_set) cudaGraphSetConditional(loop, start ? 1u : 0u);
     }
     if (!start) return;
     const double inv = 1.0 / rn;
@@ -1929,6 +1947,54 @@ __global__ void k_update_x_g(const double* __restrict__ V, const double* __restr
     }
 }
 
+// One binary32-operator Arnoldi iteration as the body of a graph WHILE node on the capturing
+// stream ctx->stream: the node is added after the stream's current dependencies, the body is
+// captured on the boundary's helper stream, and the stream continues after the node.  The body
+// reads the iteration count from gs->k; k_arn_finish ends the loop.
+static mh_status gmres_loop_node(mh_ctx* ctx, mh_boundary* bd, gmres_dev* gs, cudaGraphConditionalHandle h, int m,
+                                 int SL) {
+    cudaStream_t st = ctx->stream;
+    gmres_ws& ws = bd->ws;
+    const int64_t n = bd->n;
+    const int ldh = m + 1;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t nd = 0;
+    MH_CUDA(ctx, cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &edata, &nd));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    MH_CUDA(ctx, cudaGraphAddNode(&node, g, deps, edata, nd, &np));
+    MH_CUDA(ctx, cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    cudaStream_t bs = ws.body_stream;
+    MH_CUDA(ctx, cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    ctx->stream = bs;
+    gemv32(bs, bd->op.A32.p, ws.v32.p, ws.w.p, n, nullptr);
+    MH_LAUNCHED(ctx);
+    const size_t shm = (size_t)(m + ARN_ROWS) * sizeof(double);
+    k_arn_dots<<<SL, 256, 0, bs>>>(ws.V.p, ws.w.p, n, 1, ws.P1.p, nullptr, &gs->k);
+    MH_LAUNCHED(ctx);
+    k_arn_update<<<SL, 256, shm, bs>>>(ws.V.p, ws.w.p, n, 1, ws.P1.p, SL, ws.P2.p, nullptr, ws.h1.p, nullptr, &gs->k);
+    MH_LAUNCHED(ctx);
+    k_arn_update<<<SL, 256, shm, bs>>>(ws.V.p, ws.w.p, n, 1, ws.P2.p, SL, nullptr, ws.Pn.p, ws.h2.p, nullptr, &gs->k);
+    MH_LAUNCHED(ctx);
+    k_arn_finish<<<SL, 256, (size_t)(3 * m + 2) * sizeof(double), bs>>>(
+        ws.w.p, n, ws.Pn.p, SL, 0, ws.h1.p, ws.h2.p, ws.H.p, ldh, ws.cs.p, ws.sn.p, ws.g.p, ws.small.p, ws.V.p,
+        ws.v32.p, gs, m, &gs->k, h, 1);
+    MH_LAUNCHED(ctx);
+    ctx->stream = st;
+    cudaGraph_t out = nullptr;
+    MH_CUDA(ctx, cudaStreamEndCapture(bs, &out));
+    ctx->loop_nodes += 1;
+    return MH_OK;
+}
+
 mh_status gmres_run_graph(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, double tol, mh_precision prec,
                           const double* r0, gmres_dev* gs) {
     const int64_t n = bd->n;
@@ -1942,6 +2008,9 @@ mh_status gmres_run_graph(mh_ctx* ctx, mh_boundary* bd, const double* b, double*
     const int ldh = m + 1;
     const int ew = mh_grid(n, 256) < 152 * 4 ? mh_grid(n, 256) : 152 * 4;
     const int SL = (int)((n + ARN_ROWS - 1) / ARN_ROWS);
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    MH_CUDA(ctx, cudaStreamIsCapturing(st, &cst));
+    const bool capturing = cst == cudaStreamCaptureStatusActive;
     MH_CUDA(ctx, cudaMemsetAsync(gs, 0, sizeof(gmres_dev), st));
     k_gnorm<<<1, 1024, 0, st>>>(b, n, &gs->bnorm, nullptr);
     MH_LAUNCHED(ctx);
@@ -1957,10 +2026,23 @@ mh_status gmres_run_graph(mh_ctx* ctx, mh_boundary* bd, const double* b, double*
         }
         k_gnorm<<<1, 1024, 0, st>>>(ws.r.p, n, &gs->rn, &gs->done);
         MH_LAUNCHED(ctx);
+        // while the stream is being captured (a batch graph), the Arnoldi process of a sweep is a
+        // graph WHILE node over one iteration: only the iterations needed run
+        const bool loop = mixed && capturing && sw < S;
+        cudaGraphConditionalHandle h = 0;
+        if (loop) {
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t g = nullptr;
+            MH_CUDA(ctx, cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+            MH_CUDA(ctx, cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+        }
         k_sweep_begin<<<ew, 256, 0, st>>>(gs, tol, mixed, !supplied, sw == S, sw == 0, ws.r.p, ws.V.p,
-                                          mixed ? ws.v32.p : nullptr, ws.g.p, m + 2, n, x);
+                                          mixed ? ws.v32.p : nullptr, ws.g.p, m + 2, n, x, h, loop ? 1 : 0);
         MH_LAUNCHED(ctx);
         if (sw == S) break;
+        if (loop) {
+            MH_TRY(gmres_loop_node(ctx, bd, gs, h, m, SL));
+        } else
         for (int k = 0; k < m; ++k) {
             const int k1 = k + 1;
             if (mixed)

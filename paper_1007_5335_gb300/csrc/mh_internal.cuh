@@ -29,6 +29,7 @@ struct mh_ctx {
     int64_t launches = 0;
     bool profiling = false;
     bool capturing = false;   // inside a batch step: no cooperative launches
+    int64_t loop_nodes = 0;   // graph WHILE nodes recorded (their body kernels: loop_kernels each)
     std::map<std::string, prof_region> prof;
     ~mh_ctx();
 };
@@ -97,6 +98,8 @@ struct dbuf {
 
 // Device-resident state of the sync-free GMRES (gmres_run_graph): every kernel of its fixed
 // schedule reads the flags at entry and returns at once when its work is not needed.
+constexpr int GMRES_LOOP_KERNELS = 5;   // kernels in the body of a graph Arnoldi loop
+
 struct gmres_dev {
     double bnorm, rn, target, rel, init_rel;
     int done;        // converged on a binary64 residual computed in this solve
@@ -112,8 +115,15 @@ struct gmres_ws {
     dbuf<double> V, H, cs, sn, g, y, h1, h2, small, w, r, dx;
     dbuf<double> P1, P2, Pn;             // per-slice partial dot products / squared norms
     dbuf<float> v32;                     // binary32 copy of the newest Krylov vector
+    cudaStream_t body_stream = nullptr;  // captures the body of a graph loop (batch graphs)
     int m = 0;
     int64_t n = 0;
+    gmres_ws() = default;
+    gmres_ws(const gmres_ws&) = delete;
+    gmres_ws& operator=(const gmres_ws&) = delete;
+    ~gmres_ws() {
+        if (body_stream) cudaStreamDestroy(body_stream);
+    }
 };
 
 // Assembled boundary operator for one alpha (eq. discrete_sys), row-major N x N.
