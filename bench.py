@@ -351,6 +351,8 @@ def run_ours(args):
 KERNEL_REGIONS = {
     "bie_gemv32": ("hbm", None, "Nystrom operator GEMV, binary32 (Arnoldi iterations, line rule)"),
     "bie_gemv64": ("alu", "fp64", "Nystrom operator GEMV, binary64 (residuals, learned-start judge)"),
+    "bie_gemvff": ("hbm", None, "Nystrom operator GEMV, float-float on A32 + A32lo (mixed-precision residuals, "
+                                "learned-start judge)"),
     "dlp_near": ("alu", "auto", "double-layer near-field pair sums (fine dipoles of neighbour leaves)"),
     "dlp_fine": ("alu", "auto", "16x upsampled pair sums at the normal-line auxiliary points"),
     "dlp_coarse": ("alu", "auto", "trapezoid pair sums"),
@@ -363,7 +365,8 @@ KERNEL_REGIONS = {
 # of the timed steps (profiles/launches_heat_step_starfish_mixed.md); None where not captured.
 NCU_TRAFFIC = {"dlp_near": 3.903e6, "dlp_fine": 2.082e6, "bie_gemv32": 151.18e6, "bie_gemv64": 201.52e6,
                "dlp_coarse": 0.212e6}
-REGION_NAMES = tuple(KERNEL_REGIONS) + ("volume_apply", "dlp_fmm", "gmres", "dlp_evaluate", "warm_start", "warm_net")
+REGION_NAMES = tuple(KERNEL_REGIONS) + ("volume_apply", "dlp_fmm", "gmres", "dlp_evaluate", "warm_start", "warm_net",
+                                        "bie_gemv64_gated")
 
 
 def region_roofline(name, v, prec, mh, peaks):

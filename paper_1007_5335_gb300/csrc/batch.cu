@@ -29,6 +29,7 @@ struct mh_batch {
     int64_t graph_kernels = 0;           // kernel nodes, a loop body counted once
     int64_t loop_nodes = 0;              // GMRES WHILE nodes (bodies of GMRES_LOOP_KERNELS kernels)
     std::vector<const void*> key;
+    std::vector<int64_t> key_gen;        // GMRES workspace generation of every problem's boundary
     double key_tol = -1.0;
     int key_prec = -1;
     void drop_graph() {
@@ -156,14 +157,19 @@ extern "C" mh_status mh_batch_step(mh_ctx* ctx, mh_batch* B, double* const* u_de
         ~CaptureFlag() { c->capturing = false; }
     } cflag{ctx};
     ctx->capturing = true;   // the eager step takes the same kernels as the recorded graph
-    const bool record = !B->exec || key != B->key || gmres_tol != B->key_tol || (int)prec != B->key_prec;
+    // a recorded graph holds the GMRES workspaces: a solve outside the batch that grew one
+    // (reallocated it) forces a new recording
+    int S, m;
+    gmres_graph_schedule(prec, &S, &m);
+    std::vector<int64_t> gen(n);
+    for (int i = 0; i < n; ++i) {
+        MH_TRY(gmres_graph_ensure(ctx, B->probs[i]->bnd, m));
+        gen[i] = B->probs[i]->bnd->ws.gen;
+    }
+    const bool record = !B->exec || key != B->key || gen != B->key_gen || gmres_tol != B->key_tol ||
+                        (int)prec != B->key_prec;
     if (record) {
-        int S, m;
-        gmres_graph_schedule(prec, &S, &m);
-        for (auto* p : B->probs) {
-            MH_TRY(gmres_graph_ensure(ctx, p->bnd, m));
-            MH_TRY(bie_prepare(ctx, p->bnd, prec));
-        }
+        for (auto* p : B->probs) MH_TRY(bie_prepare(ctx, p->bnd, prec));
         // the eager step of this call (makes every lazy allocation)
         for (int i = 0; i < n; ++i)
             MH_TRY(heat_step(ctx, B->probs[i], u_dev[i], F_dev[i], f_next_dev[i], nullptr, u_dev[i], sigma_dev[i],
@@ -205,6 +211,7 @@ extern "C" mh_status mh_batch_step(mh_ctx* ctx, mh_batch* B, double* const* u_de
         B->graph = g;
         MH_CUDA(ctx, cudaGraphInstantiate(&B->exec, B->graph, 0));
         B->key = key;
+        B->key_gen = gen;
         B->key_tol = gmres_tol;
         B->key_prec = (int)prec;
     }

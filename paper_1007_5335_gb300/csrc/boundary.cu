@@ -263,6 +263,23 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
         b[i] = (float)a[i];
 }
 
+// lo = a - hi in binary64, rounded to binary32 (hi = a rounded to binary32)
+__global__ void k_split_lo(const double* __restrict__ a, const float* __restrict__ hi, float* __restrict__ lo,
+                           int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        lo[i] = (float)(a[i] - (double)hi[i]);
+}
+
+// x = xh + xl with xh = x rounded to binary32
+__global__ void k_split_vec(const double* __restrict__ x, float* __restrict__ xh, float* __restrict__ xl, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float h = (float)x[i];
+        xh[i] = h;
+        xl[i] = (float)(x[i] - (double)h);
+    }
+}
+
 // y = A x, one warp per row, 16-byte loads (N_Gamma is even, so rows stay aligned).
 __global__ void k_gemv64(const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ y,
                          int64_t n, const int* __restrict__ gate = nullptr) {
@@ -372,6 +389,87 @@ __global__ void __launch_bounds__(256) k_gemv32s(const float* __restrict__ A, co
         float t = part[warp];
         for (int k = 1; k < SPLIT; ++k) t += part[warp + k];
         y[row] = (double)t;
+    }
+}
+
+// Float-float product with the binary64 operator A = A32 + A32lo and x = xh + xl: per entry the
+// exact product of the high parts (TwoProduct by fma) plus the two cross terms, summed in
+// float-float (TwoSum); the dropped lo * lo term and the rounding of the cross terms are
+// ~2^-48 of the entry.  The binary32 pipe does the work (the binary64 one runs at 1/64 of its
+// rate here), so the product streams its 2 x 4 n^2 bytes at memory speed.  Row split as in
+// k_gemv32s; n a multiple of 4.
+__device__ __forceinline__ void ff_acc(float& sh, float& sl, float a, float al, float xh, float xl) {
+    const float p = a * xh;
+    const float e = fmaf(a, xh, -p);
+    const float c = fmaf(a, xl, fmaf(al, xh, e));
+    const float t = sh + p;
+    const float bb = t - sh;
+    sl += ((sh - (t - bb)) + (p - bb)) + c;
+    sh = t;
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(256) k_gemvff(const float* __restrict__ A, const float* __restrict__ Al,
+                                                const float* __restrict__ xh, const float* __restrict__ xl,
+                                                double* __restrict__ y, int64_t n, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    __shared__ float part[2][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (8 / SPLIT) + warp / SPLIT;
+    const int q = warp % SPLIT;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    if (row < n) {
+        const int64_t n4 = n >> 2;
+        const int64_t c0 = q * n4 / SPLIT, c1 = (q + 1) * n4 / SPLIT;
+        const float4* a4 = reinterpret_cast<const float4*>(A + row * n);
+        const float4* b4 = reinterpret_cast<const float4*>(Al + row * n);
+        const float4* xh4 = reinterpret_cast<const float4*>(xh);
+        const float4* xl4 = reinterpret_cast<const float4*>(xl);
+        int64_t c = c0 + lane;
+        for (; c + 32 < c1; c += 64) {
+            const float4 a0 = __ldcs(a4 + c), a1 = __ldcs(a4 + c + 32);
+            const float4 b0 = __ldcs(b4 + c), b1 = __ldcs(b4 + c + 32);
+            const float4 u0 = __ldg(xh4 + c), u1 = __ldg(xh4 + c + 32);
+            const float4 v0 = __ldg(xl4 + c), v1 = __ldg(xl4 + c + 32);
+            ff_acc(h0, l0, a0.x, b0.x, u0.x, v0.x);
+            ff_acc(h1, l1, a1.x, b1.x, u1.x, v1.x);
+            ff_acc(h0, l0, a0.y, b0.y, u0.y, v0.y);
+            ff_acc(h1, l1, a1.y, b1.y, u1.y, v1.y);
+            ff_acc(h0, l0, a0.z, b0.z, u0.z, v0.z);
+            ff_acc(h1, l1, a1.z, b1.z, u1.z, v1.z);
+            ff_acc(h0, l0, a0.w, b0.w, u0.w, v0.w);
+            ff_acc(h1, l1, a1.w, b1.w, u1.w, v1.w);
+        }
+        for (; c < c1; c += 32) {
+            const float4 a0 = __ldcs(a4 + c), b0 = __ldcs(b4 + c), u0 = __ldg(xh4 + c), v0 = __ldg(xl4 + c);
+            ff_acc(h0, l0, a0.x, b0.x, u0.x, v0.x);
+            ff_acc(h0, l0, a0.y, b0.y, u0.y, v0.y);
+            ff_acc(h0, l0, a0.z, b0.z, u0.z, v0.z);
+            ff_acc(h0, l0, a0.w, b0.w, u0.w, v0.w);
+        }
+    }
+    // combine: (h0, l0) + (h1, l1), then the lanes and the SPLIT warps of the row, in float-float
+    {
+        const float t = h0 + h1, bb = t - h0;
+        l0 += ((h0 - (t - bb)) + (h1 - bb)) + l1;
+        h0 = t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h0, o), ol = __shfl_xor_sync(0xffffffffu, l0, o);
+        const float t = h0 + oh, bb = t - h0;
+        l0 += ((h0 - (t - bb)) + (oh - bb)) + ol;
+        h0 = t;
+    }
+    if (lane == 0) {
+        part[0][warp] = h0;
+        part[1][warp] = l0;
+    }
+    __syncthreads();
+    if (q == 0 && lane == 0 && row < n) {
+        double t = (double)part[0][warp] + (double)part[1][warp];
+        for (int k = 1; k < SPLIT; ++k) t += (double)part[0][warp + k] + (double)part[1][warp + k];
+        y[row] = t;
     }
 }
 
@@ -926,7 +1024,22 @@ __global__ void __launch_bounds__(256) k_arn_finish(const double* __restrict__ w
             if (vnext32) vnext32[e] = (float)v;
         }
     }
-    if (blockIdx.x != 0) return;
+    // Column k is formed by block 0 when k is a launch argument; with the device-side state
+    // (gs) by the last block to arrive: every block has read gs->k and gs->skip before it
+    // counts its arrival, so the update of both cannot reach a block that has not started.
+    if (gs) {
+        __shared__ int last;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            last = atomicAdd(&gs->arrive, 1) == (int)gridDim.x - 1;
+        }
+        __syncthreads();
+        if (!last) return;
+        if (threadIdx.x == 0) gs->arrive = 0;
+    } else if (blockIdx.x != 0) {
+        return;
+    }
     // column k and the previous rotations staged in shared memory, then one thread rotates
     extern __shared__ double gsh[];      // col[k + 2], cs[k], sn[k]
     double* col = gsh;
@@ -1144,6 +1257,66 @@ __global__ void k_fourier_scalar(const double* __restrict__ v, const int32_t* __
     }
 }
 
+// The same coefficients for the binary32 path: density and twiddles in binary32, every product
+// accumulated in float-float (TwoSum), so that the sums carry no binary64 instruction per term
+// (the binary64 pipe runs at 1/64 of the binary32 rate here) and lose nothing to the length N.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
+    const float t = hi + v;
+    const float bb = t - hi;
+    lo += (hi - (t - bb)) + (v - bb);
+    hi = t;
+}
+
+__global__ void k_fourier_scalar32(const float* __restrict__ v, const int32_t* __restrict__ nn,
+                                   const int32_t* __restrict__ off, const float2* __restrict__ tw, int ncurves,
+                                   int64_t total, double* coef) {
+    const int64_t g = blockIdx.x;
+    if (g >= total) return;
+    int k = 0;
+    while (k + 1 < ncurves && g >= coef_base(off, k + 1)) ++k;
+    const int N = nn[k];
+    const int m = (int)(g - coef_base(off, k));
+    const float* p = v + off[k];
+    const float2* t = tw + off[k];
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    const int step = (int)(((int64_t)m * blockDim.x) % N);
+    int r = (int)(((int64_t)m * threadIdx.x) % N);
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const float2 c = t[r];
+        ff_add(rh, rl, p[n] * c.x);
+        ff_add(ih, il, -p[n] * c.y);
+        r += step;
+        if (r >= N) r -= N;
+    }
+    // block reduction in float-float, lanes then warps in a fixed order
+    __shared__ float red[4][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const float a = __shfl_xor_sync(0xffffffffu, rh, o), b = __shfl_xor_sync(0xffffffffu, rl, o);
+        const float c = __shfl_xor_sync(0xffffffffu, ih, o), d = __shfl_xor_sync(0xffffffffu, il, o);
+        ff_add(rh, rl, a);
+        rl += b;
+        ff_add(ih, il, c);
+        il += d;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = rh;
+        red[1][warp] = rl;
+        red[2][warp] = ih;
+        red[3][warp] = il;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double re = 0.0, im = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            re += (double)red[0][w] + (double)red[1][w];
+            im += (double)red[2][w] + (double)red[3][w];
+        }
+        coef[2 * g] = re / N;
+        coef[2 * g + 1] = im / N;
+    }
+}
+
 __global__ void k_twiddles(const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
                            const int32_t* __restrict__ curve_of, int64_t n, double2* tw, double2* half) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1183,8 +1356,9 @@ __global__ void k_fine_coef(const double* __restrict__ sc, const int32_t* __rest
     cp[e] = out;
 }
 
-// Block = (16 coarse indices j of curve blockIdx.y) x (16 sub-offsets s); the coarse twiddles
-// e^{2 pi i r / N} sit in shared memory (a warp reads two of them per mode: broadcast), the
+// Block = (4 coarse indices j of curve blockIdx.y) x (16 sub-offsets s) x (4 mode groups g):
+// thread (j, s, g) sums the modes m = g, g + 4, ... and the four groups (adjacent lanes) are
+// added by shuffles.  The coarse twiddles e^{2 pi i r / N} sit in shared memory; the
 // coefficients C_m^{(s)} are read as 16 consecutive complex values per mode (coalesced).
 template <typename T, typename T2>
 __global__ void __launch_bounds__(256) k_fine_density_s(const T2* __restrict__ cp, const double2* __restrict__ tw,
@@ -1195,7 +1369,7 @@ __global__ void __launch_bounds__(256) k_fine_density_s(const T2* __restrict__ c
     T2* tn = reinterpret_cast<T2*>(smem_raw);
     const int k = blockIdx.y;
     const int N = nn[k];
-    const int j0 = blockIdx.x * 16;
+    const int j0 = blockIdx.x * 4;
     if (j0 >= N) return;
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
         const double2 t = tw[off[k] + r];
@@ -1205,22 +1379,26 @@ __global__ void __launch_bounds__(256) k_fine_density_s(const T2* __restrict__ c
         tn[r] = v;
     }
     __syncthreads();
-    const int sub = threadIdx.x & 15, j = j0 + (threadIdx.x >> 4);
-    if (j >= N) return;
+    const int g = threadIdx.x & 3, sub = (threadIdx.x >> 2) & 15, j = j0 + (threadIdx.x >> 6);
+    const int jj = j < N ? j : 0;
     const T2* c = cp + coef_base(off, k) * UPSAMPLE + sub;
     T acc = 0;
-    int r = 0;
-#pragma unroll 8
-    for (int m = 0; m <= N / 2; ++m) {
+    int r = (int)(((int64_t)jj * g) % N);
+    const int step = (int)((4LL * jj) % N);
+#pragma unroll 4
+    for (int m = g; m <= N / 2; m += 4) {
         const T2 a = __ldg(c + (int64_t)m * UPSAMPLE);
         const T2 t = tn[r];
         acc = fma(a.x, t.x, acc);
         acc = fma(-a.y, t.y, acc);
-        r += j;
+        r += step;
         if (r >= N) r -= N;
     }
-    const int64_t g = foff[k] + (int64_t)UPSAMPLE * j + sub;
-    wf[g] = (T)((double)acc * fg[6 * g + 4] * fg[6 * g + 5]);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (g != 0 || j >= N) return;
+    const int64_t gi = foff[k] + (int64_t)UPSAMPLE * j + sub;
+    wf[gi] = (T)((double)acc * fg[6 * gi + 4] * fg[6 * gi + 5]);
 }
 
 // Coarse trapezoid sum over all curves not flagged fine for the target:
@@ -1550,6 +1728,7 @@ mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha) {
     const int64_t n = b->n;
     MH_ALLOC(ctx, b->op.A64, n * n);
     b->op.A32.release();
+    b->op.A32lo.release();
     b->op.alpha = -1.0;
     cudaStream_t st = ctx->stream;
     dim3 grid((unsigned)mh_grid(n, 256), (unsigned)std::min<int64_t>(n, 65535));
@@ -1573,6 +1752,15 @@ static mh_status ensure_fp32(mh_ctx* ctx, mh_boundary* b) {
     MH_ALLOC(ctx, b->op.A32, nn);
     k_to_float<<<152 * 8, 256, 0, ctx->stream>>>(b->op.A64.p, b->op.A32.p, nn);
     MH_LAUNCHED(ctx);
+    if ((b->n & 3) == 0) {   // float-float residual products (mixed precision)
+        MH_ALLOC(ctx, b->op.A32lo, nn);
+        k_split_lo<<<152 * 8, 256, 0, ctx->stream>>>(b->op.A64.p, b->op.A32.p, b->op.A32lo.p, nn);
+        MH_LAUNCHED(ctx);
+        if (!b->xhi32.p) {
+            MH_ALLOC(ctx, b->xhi32, b->n);
+            MH_ALLOC(ctx, b->xlo32, b->n);
+        }
+    }
     return MH_OK;
 }
 
@@ -1607,11 +1795,40 @@ static void gemv64(cudaStream_t st, const double* A, const double* x, double* y,
         k_gemv64<<<gemv_blocks(n), 256, 0, st>>>(A, x, y, n, gate);
 }
 
-mh_status bie_apply64_gated(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, const int* gate) {
-    prof_scope ps(ctx, "bie_gemv64", 2.0 * b->n * b->n, 8.0 * b->n * b->n + 16.0 * b->n);
-    gemv64(ctx->stream, b->op.A64.p, x, y, b->n, gate);
+// Product with the binary64 operator for a residual: in mixed precision a float-float product
+// on A32 + A32lo (when prepared: N_Gamma a multiple of 4), else binary64.
+static void gemv_resid(cudaStream_t st, mh_boundary* b, const double* x, double* y, const int* gate, bool mixed) {
+    const int64_t n = b->n;
+    if (mixed && b->op.A32lo.p) {
+        k_split_vec<<<mh_grid(n, 256), 256, 0, st>>>(x, b->xhi32.p, b->xlo32.p, n);
+        k_gemvff<GEMV_SPLIT><<<(unsigned)((n + 8 / GEMV_SPLIT - 1) / (8 / GEMV_SPLIT)), 256, 0, st>>>(
+            b->op.A32.p, b->op.A32lo.p, b->xhi32.p, b->xlo32.p, y, n, gate);
+    } else {
+        gemv64(st, b->op.A64.p, x, y, n, gate);
+    }
+}
+
+static const char* resid_region(mh_boundary* b, bool mixed, const int* gate) {
+    if (gate) return "bie_gemv64_gated";   // may be skipped on the device: timed apart
+    return mixed && b->op.A32lo.p ? "bie_gemvff" : "bie_gemv64";
+}
+
+static double resid_bytes(mh_boundary* b, bool mixed) {
+    const double n = (double)b->n;
+    return mixed && b->op.A32lo.p ? 8.0 * n * n + 24.0 * n : 8.0 * n * n + 16.0 * n;
+}
+
+mh_status bie_apply64_gated(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, const int* gate,
+                            mh_precision prec) {
+    const bool mixed = prec == MH_PREC_MIXED;
+    prof_scope ps(ctx, resid_region(b, mixed, gate), 2.0 * b->n * b->n, resid_bytes(b, mixed));
+    gemv_resid(ctx->stream, b, x, y, gate, mixed);
     MH_LAUNCHED(ctx);
     return MH_OK;
+}
+
+mh_status bie_apply_resid(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec) {
+    return bie_apply64_gated(ctx, b, x, y, nullptr, prec);
 }
 
 const double* gmres_final_residual(mh_boundary* b, mh_precision prec, bool graph) {
@@ -1772,14 +1989,14 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
                 MH_CUDA(ctx, cudaMemcpyAsync(r.p, r0, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
                 computed = false;
             } else {
-                MH_TRY(bie_apply(ctx, bd, x, r.p, MH_PREC_FP64));
+                MH_TRY(bie_apply_resid(ctx, bd, x, r.p, MH_PREC_MIXED));
                 k_sub_from<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(b, r.p, n);
                 MH_LAUNCHED(ctx);
             }
             MH_TRY(vec_norm(ctx, r.p, n, ws.small.p + 2, &rn));
             if (sweep == 0) inf.initial_rel_residual = rn / bnorm;
             if (!computed && rn <= tol * bnorm) {
-                MH_TRY(bie_apply(ctx, bd, x, r.p, MH_PREC_FP64));
+                MH_TRY(bie_apply_resid(ctx, bd, x, r.p, MH_PREC_MIXED));
                 k_sub_from<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(b, r.p, n);
                 MH_LAUNCHED(ctx);
                 MH_TRY(vec_norm(ctx, r.p, n, ws.small.p + 2, &rn));
@@ -1845,6 +2062,7 @@ mh_status gmres_graph_ensure(mh_ctx* ctx, mh_boundary* bd, int max_iter) {
     if (!ws.body_stream) MH_CUDA(ctx, cudaStreamCreateWithFlags(&ws.body_stream, cudaStreamNonBlocking));
     ws.m = max_iter;
     ws.n = n;
+    ws.gen += 1;
     return MH_OK;
 }
 
@@ -2019,7 +2237,7 @@ mh_status gmres_run_graph(mh_ctx* ctx, mh_boundary* bd, const double* b, double*
         if (supplied) {
             MH_CUDA(ctx, cudaMemcpyAsync(ws.r.p, r0, n * 8, cudaMemcpyDeviceToDevice, st));
         } else {
-            gemv64(st, bd->op.A64.p, x, ws.r.p, n, &gs->done);
+            gemv_resid(st, bd, x, ws.r.p, &gs->done, mixed);
             MH_LAUNCHED(ctx);
             k_gsub<<<ew, 256, 0, st>>>(b, ws.r.p, n, &gs->done);
             MH_LAUNCHED(ctx);
@@ -2232,6 +2450,11 @@ static mh_status prep_mixed(mh_ctx* ctx, mh_boundary* b) {
                                  cudaMemcpyHostToDevice, st));
     MH_ALLOC(ctx, b->fchunk_cf, b->n_fchunks);
     MH_ALLOC(ctx, b->fchunk_r, b->n_fchunks);
+    if (!b->x32.p) MH_ALLOC(ctx, b->x32, b->n);
+    MH_ALLOC(ctx, b->tw32, b->n);
+    k_to_float_vec<<<mh_grid(2 * b->n, 256), 256, 0, st>>>(reinterpret_cast<const double*>(b->tw.p),
+                                                            reinterpret_cast<float*>(b->tw32.p), 2 * b->n);
+    MH_LAUNCHED(ctx);
     k_prep_fine32<<<(unsigned)b->n_fchunks, 128, 0, st>>>(b->fine_geo.p, b->d_fine_off.p, b->d_fchunk_off.p,
                                                           b->n_curves, b->fine32.p, b->fchunk_c.p,
                                                           b->fchunk_cf.p, b->fchunk_r.p);
@@ -2322,7 +2545,7 @@ static mh_status fine_density(mh_ctx* ctx, mh_boundary* b, const double* sc, mh_
     cudaStream_t st = ctx->stream;
     const int64_t nmodes = b->n / 2 + b->n_curves;
     const int max_n = *std::max_element(b->n_nodes.begin(), b->n_nodes.end());
-    const dim3 grid((unsigned)((max_n + 15) / 16), (unsigned)b->n_curves);
+    const dim3 grid((unsigned)((max_n + 3) / 4), (unsigned)b->n_curves);
     if (prec == MH_PREC_MIXED) {
         if (!b->fcp32.p) MH_ALLOC(ctx, b->fcp32, nmodes * UPSAMPLE);
         k_fine_coef<float2><<<mh_grid(nmodes * UPSAMPLE, 256), 256, 0, st>>>(sc, b->d_nn.p, b->d_off.p, b->n_curves,
@@ -2349,15 +2572,20 @@ mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_
         MH_ALLOC(ctx, b->sc64, 2 * nmodes);
         MH_ALLOC(ctx, b->wf64, b->n_fine);
     }
-    k_fourier_scalar<<<(unsigned)nmodes, 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->tw.p, b->n_curves, nmodes,
-                                                       b->sc64.p);
-    MH_LAUNCHED(ctx);
     if (prec == MH_PREC_MIXED) {
         MH_TRY(prep_mixed(ctx, b));
+        k_to_float_vec<<<mh_grid(b->n, 256), 256, 0, st>>>(sigma, b->x32.p, b->n);
+        MH_LAUNCHED(ctx);
+        k_fourier_scalar32<<<(unsigned)nmodes, 128, 0, st>>>(b->x32.p, b->d_nn.p, b->d_off.p, b->tw32.p, b->n_curves,
+                                                             nmodes, b->sc64.p);
+        MH_LAUNCHED(ctx);
         MH_TRY(fine_density(ctx, b, b->sc64.p, MH_PREC_MIXED, b->wf32.p, nullptr));
         k_f2d<<<mh_grid(b->n_fine, 256), 256, 0, st>>>(b->wf32.p, b->wf64.p, b->n_fine);
         MH_LAUNCHED(ctx);
     } else {
+        k_fourier_scalar<<<(unsigned)nmodes, 128, 0, st>>>(sigma, b->d_nn.p, b->d_off.p, b->tw.p, b->n_curves,
+                                                           nmodes, b->sc64.p);
+        MH_LAUNCHED(ctx);
         MH_TRY(fine_density(ctx, b, b->sc64.p, MH_PREC_FP64, nullptr, b->wf64.p));
     }
     return MH_OK;

@@ -108,6 +108,7 @@ struct gmres_dev {
     int total;       // all Arnoldi iterations
     int sweeps;      // sweeps started (refinement passes in mixed precision)
     int converged;
+    int arrive;      // blocks of the running Arnoldi normalisation that have finished (reset by the last)
 };
 
 // GMRES workspace (kept by the boundary so that repeated solves allocate nothing).
@@ -118,6 +119,7 @@ struct gmres_ws {
     cudaStream_t body_stream = nullptr;  // captures the body of a graph loop (batch graphs)
     int m = 0;
     int64_t n = 0;
+    int64_t gen = 0;                     // bumped whenever the buffers are reallocated (recorded graphs hold them)
     gmres_ws() = default;
     gmres_ws(const gmres_ws&) = delete;
     gmres_ws& operator=(const gmres_ws&) = delete;
@@ -131,6 +133,7 @@ struct bie_operator {
     double alpha = -1.0;
     dbuf<double> A64;
     dbuf<float> A32;
+    dbuf<float> A32lo;   // A64 - A32 rounded to binary32: A32 + A32lo carries A64 to ~2^-48
 };
 
 struct mh_boundary {
@@ -158,6 +161,8 @@ struct mh_boundary {
     dbuf<int64_t> d_fchunk_off;
     dbuf<float4> src32, fine32;          // (dx, dy, nx, ny)
     dbuf<double2> tile_c, fchunk_c;
+    dbuf<float2> tw32;                   // binary32 copy of the twiddles e^{2 pi i r / N_k}
+    dbuf<float> xhi32, xlo32;            // float-float split of the input of a residual product
     dbuf<float4> fchunk_cf;              // fine chunk centres as float-float (x_hi, x_lo, y_hi, y_lo)
     dbuf<float> fchunk_r;                // fine chunk radii
     dbuf<float> w32, wf32, x32;          // per call: weights, fine weights, GEMV input
@@ -267,7 +272,10 @@ mh_status warm_start_prepare(mh_ctx* ctx, mh_boundary* b);
 mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha);
 mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec);
 // y = A x in binary64, skipped when *gate != 0 (gate nullable).
-mh_status bie_apply64_gated(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, const int* gate);
+mh_status bie_apply64_gated(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, const int* gate,
+                            mh_precision prec);
+// y = A x accurate to binary64 for residuals: float-float in mixed precision, binary64 otherwise
+mh_status bie_apply_resid(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec);
 // Where the last solve left the binary64 residual rhs - A x of its result.
 const double* gmres_final_residual(mh_boundary* b, mh_precision prec, bool graph);
 // Everything a sync-free solve in precision prec needs (binary32 operator copy).

@@ -1129,7 +1129,7 @@ mh_status warm_start_run(mh_ctx* ctx, mh_boundary* b, double alpha, mh_net* net,
     }
     prof_scope ps(ctx, "warm_start");
     if (!r_ready) {
-        MH_TRY(bie_apply(ctx, b, sigma, r0, MH_PREC_FP64));
+        MH_TRY(bie_apply_resid(ctx, b, sigma, r0, prec));
         k_resid<<<mh_grid(n, 256), 256, 0, st>>>(rhs, r0, n);
         MH_LAUNCHED(ctx);
     }
@@ -1156,7 +1156,7 @@ mh_status warm_start_run(mh_ctx* ctx, mh_boundary* b, double alpha, mh_net* net,
     // binary64 image of the direction: r0 = r - c w is handed to GMRES as the residual of x0, and
     // a binary32 operator would leave an error of ~1e-7 |A| |c delta| in it (above the tolerance)
     (void)prec;
-    MH_TRY(bie_apply(ctx, b, b->warm_dir.p, b->warm_w.p, MH_PREC_FP64));
+    MH_TRY(bie_apply_resid(ctx, b, b->warm_dir.p, b->warm_w.p, prec));
     k_dot2<<<1, 1024, 0, st>>>(r0, b->warm_w.p, n, scal);
     MH_LAUNCHED(ctx);
     k_line<<<mh_grid(n, 256), 256, 0, st>>>(sigma, b->warm_dir.p, r0, b->warm_w.p, scal, n, x0, r0, save, c_dev);

@@ -274,7 +274,7 @@ extern "C" mh_status mh_problem_rhs(mh_ctx* ctx, const mh_problem* p, double* rh
 
 // r = rhs - A sigma in binary64 for the GMRES start; the operator product is skipped (on the
 // device) when sigma is bit for bit the density the previous step ended with.
-static mh_status start_residual(mh_ctx* ctx, ProblemImpl* P, const double* sigma, double* r) {
+static mh_status start_residual(mh_ctx* ctx, ProblemImpl* P, const double* sigma, double* r, mh_precision prec) {
     cudaStream_t st = ctx->stream;
     mh_boundary* b = P->bnd;
     const int64_t n = b->n;
@@ -284,11 +284,11 @@ static mh_status start_residual(mh_ctx* ctx, ProblemImpl* P, const double* sigma
         MH_CUDA(ctx, cudaMemsetAsync(P->rc_same.p, 1, sizeof(int), st));
         k_rc_compare<<<grid, 256, 0, st>>>(sigma, P->rc_sigma.p, n, P->rc_same.p);
         MH_LAUNCHED(ctx);
-        MH_TRY(bie_apply64_gated(ctx, b, sigma, r, P->rc_same.p));
+        MH_TRY(bie_apply64_gated(ctx, b, sigma, r, P->rc_same.p, prec));
         k_rc_resid<<<grid, 256, 0, st>>>(P->rhs.p, r, P->rc_b.p, P->rc_r.p, P->rc_same.p, n, r);
         MH_LAUNCHED(ctx);
     } else {
-        MH_TRY(bie_apply64_gated(ctx, b, sigma, r, nullptr));
+        MH_TRY(bie_apply64_gated(ctx, b, sigma, r, nullptr, prec));
         MH_CUDA(ctx, cudaMemsetAsync(P->rc_same.p, 0, sizeof(int), st));
         k_rc_resid<<<grid, 256, 0, st>>>(P->rhs.p, r, P->rc_b.p, P->rc_r.p, P->rc_same.p, n, r);
         MH_LAUNCHED(ctx);
@@ -315,7 +315,7 @@ static mh_status step_solve(mh_ctx* ctx, ProblemImpl* P, const double* f_next_de
     if (mode == MH_WARM_ZERO) {
         MH_CUDA(ctx, cudaMemsetAsync(sigma_dev, 0, ng * 8, st));
     } else if (mode == MH_WARM_SECANT || mode == MH_WARM_LEARNED) {
-        MH_TRY(start_residual(ctx, P, sigma_dev, P->r0.p));
+        MH_TRY(start_residual(ctx, P, sigma_dev, P->r0.p, prec));
         if (mode == MH_WARM_SECANT && !P->have_prev) {
             MH_CUDA(ctx, cudaMemcpyAsync(P->sig_prev.p, sigma_dev, ng * 8, cudaMemcpyDeviceToDevice, st));
             P->have_prev = true;
@@ -328,7 +328,7 @@ static mh_status step_solve(mh_ctx* ctx, ProblemImpl* P, const double* f_next_de
         }
         r0 = P->r0.p;
     } else {   // previous-step start
-        MH_TRY(start_residual(ctx, P, sigma_dev, P->r_start.p));
+        MH_TRY(start_residual(ctx, P, sigma_dev, P->r_start.p, prec));
         r0 = P->r_start.p;
     }
     if (P->graph_mode) {

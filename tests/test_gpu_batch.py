@@ -5,6 +5,8 @@
   with the same problems stepped one by one by heat_step (host-synchronised GMRES): the two
   GMRES variants differ only in rounding and in where they stop below the tolerance.
 * A one-problem batch in binary64 agrees with heat_step to 1e-10.
+* A solve outside the batch that grows the Krylov workspace between batch steps makes the
+  batch record its graph again (a recorded graph holds the workspace).
 * The autotuner's choice is among the candidates, its error report falls with p and the
   chosen order meets the tolerance."""
 import numpy as np
@@ -88,6 +90,34 @@ def test_one_problem_batch_fp64(mh, ctx):
         u2, un = un, u2
     ins = _inside(p2)
     assert (torch.linalg.norm((u1 - u2)[ins]) / torch.linalg.norm(u2[ins])).item() <= 1e-10
+
+
+def test_batch_after_outside_solve(mh, ctx):
+    """A solve outside the batch (heat_step, whose GMRES grows the problem's Krylov workspace)
+    between two batch steps: the batch records its graph again on the new workspace, and the
+    steps agree with heat_step throughout (mixed precision)."""
+    wl = W.batch_problem(0, npc=192, refine_tol=1e-5)
+    t1, b1, p1, F1 = _make(mh, ctx, wl)
+    t2, b2, p2, F2 = _make(mh, ctx, wl)
+    batch = mh.Batch(ctx, [p1])
+    u1 = torch.zeros(t1.n_nodes, dtype=torch.float64, device="cuda")
+    s1 = torch.zeros(b1.n, dtype=torch.float64, device="cuda")
+    f = torch.zeros(b1.n, dtype=torch.float64, device="cuda")
+    u2, un = torch.zeros_like(u1), torch.empty_like(u1)
+    s2 = torch.zeros_like(s1)
+    tmp = torch.empty_like(u1)
+    for step in range(4):
+        if step == 2:   # an outside solve on the batch's own problem: same u and density
+            mh.heat_step(ctx, p1, u1, F1, f, tmp, s1, gmres_tol=1e-10, prec=mh.MH_PREC_MIXED)
+            u1.copy_(tmp)
+            mh.heat_step(ctx, p2, u2, F2, f, un, s2, gmres_tol=1e-10, prec=mh.MH_PREC_MIXED)
+            u2, un = un, u2
+        infos = batch.step([u1], [F1], [f], [s1], gmres_tol=1e-10, prec=mh.MH_PREC_MIXED)
+        assert infos[0].gmres_rel_residual <= 1e-10
+        mh.heat_step(ctx, p2, u2, F2, f, un, s2, gmres_tol=1e-10, prec=mh.MH_PREC_MIXED)
+        u2, un = un, u2
+    ins = _inside(p2)
+    assert (torch.linalg.norm((u1 - u2)[ins]) / torch.linalg.norm(u2[ins])).item() <= 1e-7
 
 
 def test_autotuner(mh, ctx):
