@@ -722,9 +722,15 @@ __global__ void __launch_bounds__(256) k_dlp_fine32_grp(
         }
     }
 #pragma unroll
-    for (int j = 0; j < TG; ++j) {
-        const double v = warp_sum((double)hi[j] + (double)lo[j]);
-        if (lane == 0) red[warp][j] = v;
+    for (int j = 0; j < TG; ++j) {   // warp sum in float-float, one widening per warp
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi[j], o), ol = __shfl_xor_sync(0xffffffffu, lo[j], o);
+            const float t = hi[j] + oh, bb = t - hi[j];
+            lo[j] += ((hi[j] - (t - bb)) + (oh - bb)) + ol;
+            hi[j] = t;
+        }
+        if (lane == 0) red[warp][j] = (double)hi[j] + (double)lo[j];
     }
     __syncthreads();
     double s = 0.0;
@@ -1360,8 +1366,9 @@ __global__ void k_fine_coef(const double* __restrict__ sc, const int32_t* __rest
 // thread (j, s, g) sums the modes m = g, g + 4, ... and the four groups (adjacent lanes) are
 // added by shuffles.  The coarse twiddles e^{2 pi i r / N} sit in shared memory; the
 // coefficients C_m^{(s)} are read as 16 consecutive complex values per mode (coalesced).
+// tw: the twiddles in the arithmetic's own type (a plain copy into shared memory per block).
 template <typename T, typename T2>
-__global__ void __launch_bounds__(256) k_fine_density_s(const T2* __restrict__ cp, const double2* __restrict__ tw,
+__global__ void __launch_bounds__(256) k_fine_density_s(const T2* __restrict__ cp, const T2* __restrict__ tw,
                                                         const double* __restrict__ fg, const int32_t* __restrict__ nn,
                                                         const int32_t* __restrict__ off,
                                                         const int64_t* __restrict__ foff, T* __restrict__ wf) {
@@ -1371,13 +1378,7 @@ __global__ void __launch_bounds__(256) k_fine_density_s(const T2* __restrict__ c
     const int N = nn[k];
     const int j0 = blockIdx.x * 4;
     if (j0 >= N) return;
-    for (int r = threadIdx.x; r < N; r += blockDim.x) {
-        const double2 t = tw[off[k] + r];
-        T2 v;
-        v.x = (T)t.x;
-        v.y = (T)t.y;
-        tn[r] = v;
-    }
+    for (int r = threadIdx.x; r < N; r += blockDim.x) tn[r] = tw[off[k] + r];
     __syncthreads();
     const int g = threadIdx.x & 3, sub = (threadIdx.x >> 2) & 15, j = j0 + (threadIdx.x >> 6);
     const int jj = j < N ? j : 0;
@@ -2552,7 +2553,7 @@ static mh_status fine_density(mh_ctx* ctx, mh_boundary* b, const double* sc, mh_
                                                                              nmodes, b->fcp32.p);
         MH_LAUNCHED(ctx);
         k_fine_density_s<float, float2><<<grid, 256, max_n * sizeof(float2), st>>>(
-            b->fcp32.p, b->tw.p, b->fine_geo.p, b->d_nn.p, b->d_off.p, b->d_fine_off.p, wf32);
+            b->fcp32.p, b->tw32.p, b->fine_geo.p, b->d_nn.p, b->d_off.p, b->d_fine_off.p, wf32);
     } else {
         if (!b->fcp64.p) MH_ALLOC(ctx, b->fcp64, nmodes * UPSAMPLE);
         k_fine_coef<double2><<<mh_grid(nmodes * UPSAMPLE, 256), 256, 0, st>>>(sc, b->d_nn.p, b->d_off.p, b->n_curves,

@@ -1312,7 +1312,7 @@ __global__ void __launch_bounds__(NT) k_dip_near32(
     const int64_t node = (int64_t)ch.leaf * qq + i;
     const double2 c = leaf_c[ch.leaf];
     const float tx = (float)(nodes[2 * node] - c.x), ty = (float)(nodes[2 * node + 1] - c.y);
-    double acc = 0.0;
+    float ah = 0.f, al = 0.f;   // float-float sum of the tile sums (no binary64 per tile)
     for (int k0 = ch.k0; k0 < ch.k1; k0 += NT) {
         const int m = min(NT, ch.k1 - k0);
         __syncthreads();
@@ -1328,10 +1328,12 @@ __global__ void __launch_bounds__(NT) k_dip_near32(
                 const float4 v = s4[e];
                 pt += mh_dl32_pair(v.x - tx, v.y - ty, v.z, v.w, c32);
             }
-            acc += (double)pt;
+            const float t = ah + pt, bb = t - ah;
+            al += (ah - (t - bb)) + (pt - bb);
+            ah = t;
         }
     }
-    near_finish<NT>(acc, act, qq, i, groups, ch, leaf_red, pref, part, cnt, out);
+    near_finish<NT>((double)ah + (double)al, act, qq, i, groups, ch, leaf_red, pref, part, cnt, out);
 }
 
 __global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
