@@ -1362,11 +1362,9 @@ __global__ void k_fine_coef(const double* __restrict__ sc, const int32_t* __rest
     cp[e] = out;
 }
 
-// Block = (4 coarse indices j of curve blockIdx.y) x (16 sub-offsets s) x (4 mode groups g):
-// thread (j, s, g) sums the modes m = g, g + 4, ... and the four groups (adjacent lanes) are
-// added by shuffles.  The coarse twiddles e^{2 pi i r / N} sit in shared memory; the
+// Block = (16 coarse indices j of curve blockIdx.y) x (16 sub-offsets s); the coarse twiddles
+// e^{2 pi i r / N} sit in shared memory (a warp reads two of them per mode: broadcast), the
 // coefficients C_m^{(s)} are read as 16 consecutive complex values per mode (coalesced).
-// tw: the twiddles in the arithmetic's own type (a plain copy into shared memory per block).
 template <typename T, typename T2>
 __global__ void __launch_bounds__(256) k_fine_density_s(const T2* __restrict__ cp, const T2* __restrict__ tw,
                                                         const double* __restrict__ fg, const int32_t* __restrict__ nn,
@@ -1376,30 +1374,26 @@ __global__ void __launch_bounds__(256) k_fine_density_s(const T2* __restrict__ c
     T2* tn = reinterpret_cast<T2*>(smem_raw);
     const int k = blockIdx.y;
     const int N = nn[k];
-    const int j0 = blockIdx.x * 4;
+    const int j0 = blockIdx.x * 16;
     if (j0 >= N) return;
-    for (int r = threadIdx.x; r < N; r += blockDim.x) tn[r] = tw[off[k] + r];
+    for (int r = threadIdx.x; r < N; r += blockDim.x) tn[r] = tw[off[k] + r];   // twiddles in T already
     __syncthreads();
-    const int g = threadIdx.x & 3, sub = (threadIdx.x >> 2) & 15, j = j0 + (threadIdx.x >> 6);
-    const int jj = j < N ? j : 0;
+    const int sub = threadIdx.x & 15, j = j0 + (threadIdx.x >> 4);
+    if (j >= N) return;
     const T2* c = cp + coef_base(off, k) * UPSAMPLE + sub;
     T acc = 0;
-    int r = (int)(((int64_t)jj * g) % N);
-    const int step = (int)((4LL * jj) % N);
-#pragma unroll 4
-    for (int m = g; m <= N / 2; m += 4) {
+    int r = 0;
+#pragma unroll 8
+    for (int m = 0; m <= N / 2; ++m) {
         const T2 a = __ldg(c + (int64_t)m * UPSAMPLE);
         const T2 t = tn[r];
         acc = fma(a.x, t.x, acc);
         acc = fma(-a.y, t.y, acc);
-        r += step;
+        r += j;
         if (r >= N) r -= N;
     }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (g != 0 || j >= N) return;
-    const int64_t gi = foff[k] + (int64_t)UPSAMPLE * j + sub;
-    wf[gi] = (T)((double)acc * fg[6 * gi + 4] * fg[6 * gi + 5]);
+    const int64_t g = foff[k] + (int64_t)UPSAMPLE * j + sub;
+    wf[g] = (T)((double)acc * fg[6 * g + 4] * fg[6 * g + 5]);
 }
 
 // Coarse trapezoid sum over all curves not flagged fine for the target:
@@ -2546,7 +2540,7 @@ static mh_status fine_density(mh_ctx* ctx, mh_boundary* b, const double* sc, mh_
     cudaStream_t st = ctx->stream;
     const int64_t nmodes = b->n / 2 + b->n_curves;
     const int max_n = *std::max_element(b->n_nodes.begin(), b->n_nodes.end());
-    const dim3 grid((unsigned)((max_n + 3) / 4), (unsigned)b->n_curves);
+    const dim3 grid((unsigned)((max_n + 15) / 16), (unsigned)b->n_curves);
     if (prec == MH_PREC_MIXED) {
         if (!b->fcp32.p) MH_ALLOC(ctx, b->fcp32, nmodes * UPSAMPLE);
         k_fine_coef<float2><<<mh_grid(nmodes * UPSAMPLE, 256), 256, 0, st>>>(sc, b->d_nn.p, b->d_off.p, b->n_curves,

@@ -32,7 +32,7 @@
 
 namespace {
 
-constexpr int CHUNK = 32;   // tasks per block in the contraction kernel
+constexpr int CHUNK = 64;   // tasks per block in the contraction kernel (32 where 64 does not fit)
 constexpr int NGLN = 16;    // Gauss-Legendre points per panel in the near-table rule
 constexpr int NGLQ = 32;    // Gauss-Legendre points per axis for the smooth P2M/P2L integrals
 
@@ -578,14 +578,17 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
     std::vector<int64_t> src(tasks.size());
     std::vector<int32_t> cop, ct0;
     int maxC = 1;
+    for (const Task& t : tasks) maxC = std::max(maxC, op_C[t.op]);
+    // tasks per block: CHUNK (more threads busy in the 4 x 4 tiling, the operator staged for
+    // more vectors) unless the staged operator and sources would not fit
+    const int chunk = (size_t)(R + CHUNK) * (maxC + 1) * sizeof(double) <= 160 * 1024 ? CHUNK : 32;
     for (size_t s = 0; s < order.size(); ++s) {
         const Task& t = tasks[order[s]];
         src[s] = t.src;
-        if (s == 0 || tasks[order[s - 1]].op != t.op || (int64_t)(s - ct0.back()) >= CHUNK) {
+        if (s == 0 || tasks[order[s - 1]].op != t.op || (int64_t)(s - ct0.back()) >= chunk) {
             cop.push_back(t.op);
             ct0.push_back((int32_t)s);
         }
-        maxC = std::max(maxC, op_C[t.op]);
         ph->flops += 2.0 * R * op_C[t.op];
         ph->bytes += 8.0 * op_C[t.op] + 16.0 * R;   // source vector, product write + read
     }
@@ -616,7 +619,7 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
         }
         ph->direct = smax <= dmin || dmax <= smin;
     }
-    ph->smem = (int)((R + CHUNK) * (maxC + 1) * sizeof(double));
+    ph->smem = (int)((R + chunk) * (maxC + 1) * sizeof(double));
     if (ph->smem > 160 * 1024)
         return mh_fail(ctx, MH_ERR_INVALID_ARG, "contraction operator too large for shared memory (%d x %d)", R, maxC);
     cudaStream_t st = ctx->stream;
