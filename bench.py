@@ -363,7 +363,7 @@ KERNEL_REGIONS = {
 }
 # DRAM bytes (read + write) per launch of the region's main kernel, from the ncu launch list
 # of the timed steps (profiles/launches_heat_step_starfish_mixed.md); None where not captured.
-NCU_TRAFFIC = {"dlp_near": 19.98e6, "dlp_fine": 2.10e6, "bie_gemv32": 151.16e6, "bie_gemvff": 201.45e6,
+NCU_TRAFFIC = {"dlp_near": 19.98e6, "dlp_fine": 2.10e6, "bie_gemv32": 151.15e6, "bie_gemvff": 201.53e6,
                "dlp_coarse": 0.21e6}
 REGION_NAMES = tuple(KERNEL_REGIONS) + ("volume_apply", "dlp_fmm", "gmres", "dlp_evaluate", "warm_start", "warm_net",
                                         "bie_gemv64_gated")

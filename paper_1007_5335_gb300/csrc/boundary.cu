@@ -392,12 +392,11 @@ __global__ void __launch_bounds__(256) k_gemv32s(const float* __restrict__ A, co
     }
 }
 
-// Float-float product with the binary64 operator A = A32 + A32lo and x = xh + xl: per entry the
-// exact product of the high parts (TwoProduct by fma) plus the two cross terms, summed in
-// float-float (TwoSum); the dropped lo * lo term and the rounding of the cross terms are
-// ~2^-48 of the entry.  The binary32 pipe does the work (the binary64 one runs at 1/64 of its
-// rate here), so the product streams its 2 x 4 n^2 bytes at memory speed.  Row split as in
-// k_gemv32s; n a multiple of 4.
+// One entry of the float-float product with the binary64 operator A = A32 + A32lo and
+// x = xh + xl: the exact product of the high parts (TwoProduct by fma) plus the two cross terms,
+// added to the float-float sum (sh, sl) by TwoSum; the dropped lo * lo term and the rounding of
+// the cross terms are ~2^-48 of the entry.  Binary32 pipe only (the binary64 pipe runs at 1/64
+// of its rate here).
 __device__ __forceinline__ void ff_acc(float& sh, float& sl, float a, float al, float xh, float xl) {
     const float p = a * xh;
     const float e = fmaf(a, xh, -p);
@@ -408,68 +407,102 @@ __device__ __forceinline__ void ff_acc(float& sh, float& sl, float a, float al, 
     sh = t;
 }
 
-template <int SPLIT>
-__global__ void __launch_bounds__(256) k_gemvff(const float* __restrict__ A, const float* __restrict__ Al,
-                                                const float* __restrict__ xh, const float* __restrict__ xl,
-                                                double* __restrict__ y, int64_t n, const int* __restrict__ gate) {
+// Row-split operator GEMVs whose operator loads go through shared memory by cp.async (16-byte
+// asynchronous copies): every lane issues its share of a whole piece of its quarter row (up to
+// GC_PIECE float4 per matrix) before it touches any of it, so the loads in flight are not
+// limited by registers.  A lane reads back only the float4s it copied itself (no barrier).
+// M = 1: y = A32 x in binary32; M = 2: y = (A32 + A32lo)(xh + xl) in float-float (ff_acc).
+// n a multiple of 4; SPLIT warps per row, 8 / SPLIT rows per 256-thread block.
+constexpr int GC_PIECE = 12;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+template <int SPLIT, int M>
+__global__ void __launch_bounds__(256) k_gemv_cpa(const float* __restrict__ A, const float* __restrict__ Al,
+                                                  const float* __restrict__ xh, const float* __restrict__ xl,
+                                                  double* __restrict__ y, int64_t n, const int* __restrict__ gate) {
     if (gate && *gate) return;
+    extern __shared__ __align__(16) float4 gc_stage[];   // [warp][M][GC_PIECE * 32]
     __shared__ float part[2][8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* st = gc_stage + (size_t)warp * M * GC_PIECE * 32;
     const int64_t row = (int64_t)blockIdx.x * (8 / SPLIT) + warp / SPLIT;
     const int q = warp % SPLIT;
-    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    float hi = 0.f, lo = 0.f;
     if (row < n) {
         const int64_t n4 = n >> 2;
         const int64_t c0 = q * n4 / SPLIT, c1 = (q + 1) * n4 / SPLIT;
         const float4* a4 = reinterpret_cast<const float4*>(A + row * n);
-        const float4* b4 = reinterpret_cast<const float4*>(Al + row * n);
+        const float4* b4 = reinterpret_cast<const float4*>(Al + (M == 2 ? row * n : 0));
         const float4* xh4 = reinterpret_cast<const float4*>(xh);
         const float4* xl4 = reinterpret_cast<const float4*>(xl);
-        int64_t c = c0 + lane;
-        for (; c + 32 < c1; c += 64) {
-            const float4 a0 = __ldcs(a4 + c), a1 = __ldcs(a4 + c + 32);
-            const float4 b0 = __ldcs(b4 + c), b1 = __ldcs(b4 + c + 32);
-            const float4 u0 = __ldg(xh4 + c), u1 = __ldg(xh4 + c + 32);
-            const float4 v0 = __ldg(xl4 + c), v1 = __ldg(xl4 + c + 32);
-            ff_acc(h0, l0, a0.x, b0.x, u0.x, v0.x);
-            ff_acc(h1, l1, a1.x, b1.x, u1.x, v1.x);
-            ff_acc(h0, l0, a0.y, b0.y, u0.y, v0.y);
-            ff_acc(h1, l1, a1.y, b1.y, u1.y, v1.y);
-            ff_acc(h0, l0, a0.z, b0.z, u0.z, v0.z);
-            ff_acc(h1, l1, a1.z, b1.z, u1.z, v1.z);
-            ff_acc(h0, l0, a0.w, b0.w, u0.w, v0.w);
-            ff_acc(h1, l1, a1.w, b1.w, u1.w, v1.w);
+        for (int64_t p0 = c0; p0 < c1; p0 += GC_PIECE * 32) {
+#pragma unroll
+            for (int u = 0; u < GC_PIECE; ++u) {
+                const int64_t c = p0 + lane + 32 * u;
+                if (c < c1) {
+                    cp_async16(st + lane + 32 * u, a4 + c);
+                    if (M == 2) cp_async16(st + GC_PIECE * 32 + lane + 32 * u, b4 + c);
+                }
+            }
+            cp_async_wait_all();
+#pragma unroll
+            for (int u = 0; u < GC_PIECE; ++u) {
+                const int64_t c = p0 + lane + 32 * u;
+                if (c < c1) {
+                    const float4 av = st[lane + 32 * u];
+                    const float4 uv = __ldg(xh4 + c);
+                    if (M == 1) {
+                        hi = fmaf(av.x, uv.x, hi);
+                        hi = fmaf(av.y, uv.y, hi);
+                        hi = fmaf(av.z, uv.z, hi);
+                        hi = fmaf(av.w, uv.w, hi);
+                    } else {
+                        const float4 bv = st[GC_PIECE * 32 + lane + 32 * u];
+                        const float4 vv = __ldg(xl4 + c);
+                        ff_acc(hi, lo, av.x, bv.x, uv.x, vv.x);
+                        ff_acc(hi, lo, av.y, bv.y, uv.y, vv.y);
+                        ff_acc(hi, lo, av.z, bv.z, uv.z, vv.z);
+                        ff_acc(hi, lo, av.w, bv.w, uv.w, vv.w);
+                    }
+                }
+            }
+            __syncwarp();   // the next piece reuses the warp's stage
         }
-        for (; c < c1; c += 32) {
-            const float4 a0 = __ldcs(a4 + c), b0 = __ldcs(b4 + c), u0 = __ldg(xh4 + c), v0 = __ldg(xl4 + c);
-            ff_acc(h0, l0, a0.x, b0.x, u0.x, v0.x);
-            ff_acc(h0, l0, a0.y, b0.y, u0.y, v0.y);
-            ff_acc(h0, l0, a0.z, b0.z, u0.z, v0.z);
-            ff_acc(h0, l0, a0.w, b0.w, u0.w, v0.w);
-        }
-    }
-    // combine: (h0, l0) + (h1, l1), then the lanes and the SPLIT warps of the row, in float-float
-    {
-        const float t = h0 + h1, bb = t - h0;
-        l0 += ((h0 - (t - bb)) + (h1 - bb)) + l1;
-        h0 = t;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, h0, o), ol = __shfl_xor_sync(0xffffffffu, l0, o);
-        const float t = h0 + oh, bb = t - h0;
-        l0 += ((h0 - (t - bb)) + (oh - bb)) + ol;
-        h0 = t;
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        if (M == 1) {
+            hi += oh;
+        } else {
+            const float t = hi + oh, bb = t - hi;
+            lo += ((hi - (t - bb)) + (oh - bb)) + ol;
+            hi = t;
+        }
     }
     if (lane == 0) {
-        part[0][warp] = h0;
-        part[1][warp] = l0;
+        part[0][warp] = hi;
+        part[1][warp] = lo;
     }
     __syncthreads();
     if (q == 0 && lane == 0 && row < n) {
-        double t = (double)part[0][warp] + (double)part[1][warp];
-        for (int k = 1; k < SPLIT; ++k) t += (double)part[0][warp + k] + (double)part[1][warp + k];
-        y[row] = t;
+        if (M == 1) {
+            float t = part[0][warp];
+            for (int k = 1; k < SPLIT; ++k) t += part[0][warp + k];
+            y[row] = (double)t;
+        } else {
+            double t = (double)part[0][warp] + (double)part[1][warp];
+            for (int k = 1; k < SPLIT; ++k) t += (double)part[0][warp + k] + (double)part[1][warp + k];
+            y[row] = t;
+        }
     }
 }
 
@@ -1741,7 +1774,10 @@ mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha) {
     return MH_OK;
 }
 
+static mh_status gemv_cpa_prepare(mh_ctx* ctx);
+
 static mh_status ensure_fp32(mh_ctx* ctx, mh_boundary* b) {
+    MH_TRY(gemv_cpa_prepare(ctx));
     if (b->op.A32.p) return MH_OK;
     const int64_t nn = b->n * b->n;
     MH_ALLOC(ctx, b->op.A32, nn);
@@ -1774,12 +1810,27 @@ static int gemv_blocks(int64_t n) {
 
 constexpr int GEMV_SPLIT = 4;   // warps per row of the row-split GEMVs
 
+constexpr size_t GC_SMEM2 = 8 * 2 * GC_PIECE * 32 * sizeof(float4);   // 96 KB
+
+// The binary32 GEMV keeps register loads (k_gemv32s, 29 us for the starfish operator); staging its
+// loads through cp.async measured slower (35 us).  The float-float product, with twice the bytes
+// per entry, gains from the staging (81 -> 70 us).
 static void gemv32(cudaStream_t st, const float* A, const float* x, double* y, int64_t n, const int* gate) {
     if ((n & 3) == 0)
         k_gemv32s<GEMV_SPLIT><<<(unsigned)((n + 8 / GEMV_SPLIT - 1) / (8 / GEMV_SPLIT)), 256, 0, st>>>(A, x, y, n,
                                                                                                      gate);
     else
         k_gemv32<<<gemv_blocks(n), 256, 0, st>>>(A, x, y, n, gate);
+}
+
+// Shared-memory opt-in of the cp.async GEMVs (once per process, outside any graph capture).
+static mh_status gemv_cpa_prepare(mh_ctx* ctx) {
+    static bool done = false;
+    if (done) return MH_OK;
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_gemv_cpa<GEMV_SPLIT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)GC_SMEM2));
+    done = true;
+    return MH_OK;
 }
 
 static void gemv64(cudaStream_t st, const double* A, const double* x, double* y, int64_t n, const int* gate) {
@@ -1796,7 +1847,7 @@ static void gemv_resid(cudaStream_t st, mh_boundary* b, const double* x, double*
     const int64_t n = b->n;
     if (mixed && b->op.A32lo.p) {
         k_split_vec<<<mh_grid(n, 256), 256, 0, st>>>(x, b->xhi32.p, b->xlo32.p, n);
-        k_gemvff<GEMV_SPLIT><<<(unsigned)((n + 8 / GEMV_SPLIT - 1) / (8 / GEMV_SPLIT)), 256, 0, st>>>(
+        k_gemv_cpa<GEMV_SPLIT, 2><<<(unsigned)((n + 8 / GEMV_SPLIT - 1) / (8 / GEMV_SPLIT)), 256, GC_SMEM2, st>>>(
             b->op.A32.p, b->op.A32lo.p, b->xhi32.p, b->xlo32.p, y, n, gate);
     } else {
         gemv64(st, b->op.A64.p, x, y, n, gate);
