@@ -231,21 +231,31 @@ __global__ void k_near_tables(const NearCfg* __restrict__ cfg, int q, const doub
 
 // Copies src[0..n) to shared memory at row-major position (e / cols, e % cols), leading
 // dimension ld, with U independent loads in flight per thread (a load-then-store loop would
-// wait on every global load in turn).
+// wait on every global load in turn).  The position advances incrementally (one division per
+// thread, not two per element).
 template <typename TD, typename TS, int U = 8>
 __device__ __forceinline__ void stage_rows(TD* dst, const TS* __restrict__ src, int n, int cols, int ld) {
-    for (int e0 = threadIdx.x; e0 < n; e0 += U * blockDim.x) {
+    const int stride = blockDim.x;
+    const int dc = stride % cols, dov = (stride / cols) * ld + dc;   // per stride: column, shared offset
+    int c = (int)threadIdx.x % cols, o = ((int)threadIdx.x / cols) * ld + c;
+    for (int e0 = threadIdx.x; e0 < n; e0 += U * stride) {
         TS v[U];
+        int oo[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int e = e0 + u * blockDim.x;
+            const int e = e0 + u * stride;
             v[u] = e < n ? src[e] : TS(0);
+            oo[u] = o;
+            c += dc;
+            o += dov;
+            if (c >= cols) {
+                c -= cols;
+                o += ld - cols;
+            }
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < n) dst[(e / cols) * ld + (e % cols)] = (TD)v[u];
-        }
+        for (int u = 0; u < U; ++u)
+            if (e0 + u * stride < n) dst[oo[u]] = (TD)v[u];
     }
 }
 
@@ -297,17 +307,28 @@ __global__ void k_apply(const TOP* __restrict__ ops, const int64_t* __restrict__
         return;
     }
     stage_rows<TOP, TOP>(sA, A, R * C, C, lda);
-    for (int e0 = threadIdx.x; e0 < nt * C; e0 += 4 * blockDim.x) {
-        TOP v[4];
+    {   // gather the sources: element e is (task e / C, column e % C), advanced incrementally
+        const int stride = blockDim.x, ne = nt * C;
+        const int dc = stride % C, dt = stride / C;
+        int c = (int)threadIdx.x % C, tt = (int)threadIdx.x / C;
+        for (int e0 = threadIdx.x; e0 < ne; e0 += 4 * stride) {
+            TOP v[4];
+            int oo[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = e0 + u * blockDim.x;
-            v[u] = e < nt * C ? src[task_src[t0 + e / C] + e % C] : TOP(0);
-        }
+            for (int u = 0; u < 4; ++u) {
+                const bool in = e0 + u * stride < ne;
+                v[u] = in ? src[task_src[t0 + tt] + c] : TOP(0);
+                oo[u] = tt * lda + c;
+                c += dc;
+                tt += dt;
+                if (c >= C) {
+                    c -= C;
+                    ++tt;
+                }
+            }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < nt * C) sX[(e / C) * lda + e % C] = v[u];
+            for (int u = 0; u < 4; ++u)
+                if (e0 + u * stride < ne) sX[oo[u]] = v[u];
         }
     }
     __syncthreads();
