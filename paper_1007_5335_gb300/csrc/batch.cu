@@ -209,7 +209,7 @@ extern "C" mh_status mh_batch_step(mh_ctx* ctx, mh_batch* B, double* const* u_de
                            cudaGetErrorString(ce != cudaSuccess ? ce : ee));
         }
         B->graph = g;
-        MH_CUDA(ctx, cudaGraphInstantiate(&B->exec, B->graph, 0));
+        MH_CUDA(ctx, cudaGraphInstantiate(&B->exec, B->graph, cudaGraphInstantiateFlagUseNodePriority));
         B->key = key;
         B->key_gen = gen;
         B->key_tol = gmres_tol;

@@ -14,9 +14,11 @@
 //
 // Every pass is a batch of small dense contractions "y_dst += T_op x_src" with the
 // operator T_op chosen by (level, relative configuration).  Tasks are sorted by operator;
-// a block stages one operator and up to 32 source vectors in shared memory and writes
+// a block stages one operator and up to 64 source vectors in shared memory and writes
 // its products to a task-indexed buffer, and a segmented reduction sums the products of
-// each destination in a fixed order (deterministic, no atomics).
+// each destination in a fixed order (deterministic, no atomics).  The near tables form their
+// own phase, which needs only the node values: it runs beside the multipole passes on a
+// second stream and writes U first; the output phase then adds the far field.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -533,6 +535,42 @@ struct Phase {
     dbuf<int64_t> task_src, dst_off;
 };
 
+// A second stream, of the device's highest priority, with fork / join events: the multipole
+// passes (latency chains) run there while the near fields, which do not depend on them, run
+// on the context stream and fill the SMs that the chains leave idle; the priority lets the
+// passes' blocks start before queued near-field blocks.  Created at set-up, outside any
+// stream capture.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    SideStream() = default;
+    SideStream(const SideStream&) = delete;
+    SideStream& operator=(const SideStream&) = delete;
+    ~SideStream() {
+        if (join) cudaEventDestroy(join);
+        if (fork) cudaEventDestroy(fork);
+        if (s) cudaStreamDestroy(s);
+    }
+    mh_status create(mh_ctx* ctx) {
+        int least = 0, greatest = 0;
+        MH_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        MH_CUDA(ctx, cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest));
+        MH_CUDA(ctx, cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        MH_CUDA(ctx, cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        return MH_OK;
+    }
+    // the side stream waits for everything issued so far on `main`
+    mh_status begin(mh_ctx* ctx, cudaStream_t main) {
+        MH_CUDA(ctx, cudaEventRecord(fork, main));
+        MH_CUDA(ctx, cudaStreamWaitEvent(s, fork, 0));
+        return MH_OK;
+    }
+    mh_status end(mh_ctx* ctx) {
+        MH_CUDA(ctx, cudaEventRecord(join, s));
+        return MH_OK;
+    }
+};
+
 struct OpPool {
     std::vector<double> data;
     std::vector<int64_t> off;
@@ -582,6 +620,10 @@ struct VolData {
     dbuf<int32_t> d_op_C;
     std::vector<int> op_C;
     std::unique_ptr<Phase> p2m, m2l, out;
+    std::unique_ptr<Phase> near;                      // U list: near tables on the node values
+    dbuf<double> temp_near;                           // its products (it may run beside the others)
+    bool near_cover = true;                           // every leaf has a U-list task
+    SideStream side;
     std::unique_ptr<DfChain> chain;                   // M2M / L2L chains
     int64_t temp_len = 0;
     int64_t n_near_tables = 0;
@@ -882,7 +924,7 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
     std::map<std::tuple<int, int, int, int>, int> near_key, m2l_key, m2p_key, p2l_key;
     std::vector<NearCfg> near_cfg;
     std::vector<int> near_level;
-    std::vector<Task> t_out, t_m2l, t_p2m;
+    std::vector<Task> t_out, t_m2l, t_p2m, t_near;
     // relative centre offset (source minus target) from integer coordinates
     auto rel = [&](int tb, int sb) {
         const int lt = lev(tb), ls = lev(sb), f = std::max(lt, ls);
@@ -914,7 +956,7 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
                 } else {
                     id = it->second;
                 }
-                t_out.push_back(Task{-1 - id, V->B_off + (int64_t)h.box_leaf[c] * qq, V->U_off + (int64_t)leaf * qq});
+                t_near.push_back(Task{-1 - id, V->B_off + (int64_t)h.box_leaf[c] * qq, V->U_off + (int64_t)leaf * qq});
             }
             if (l >= 2) t_out.push_back(Task{op_l2p[l], V->L_off + b * P, V->U_off + (int64_t)leaf * qq});
             // W list -> M2P
@@ -1155,8 +1197,7 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
         pool.R.push_back(qq);
         pool.C.push_back(qq);
     }
-    for (auto& tk : t_out)
-        if (tk.op < 0) tk.op = first_near_op + (-1 - tk.op);
+    for (auto& tk : t_near) tk.op = first_near_op + (-1 - tk.op);
     const int64_t total = near_base + (int64_t)nnear * qq * qq;
     MH_ALLOC(ctx, V->ops64, total);
     cudaStream_t st = ctx->stream;
@@ -1198,18 +1239,30 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
     MH_TRY(build_phase(ctx, t_p2m, P, false, V->op_C, V->p2m.get(), &need));
     V->m2l.reset(new Phase());
     MH_TRY(build_phase(ctx, t_m2l, P, false, V->op_C, V->m2l.get(), &need));
+    // U^h = near (U list, written first) + far (L2P, M2P: added once the passes are done)
+    {
+        std::vector<char> has(t->n_leaves, 0);
+        for (const Task& tk : t_near) has[(tk.dst - V->U_off) / qq] = 1;
+        V->near_cover = std::find(has.begin(), has.end(), 0) == has.end();
+    }
+    int64_t need_near = 1;
+    V->near.reset(new Phase());
+    MH_TRY(build_phase(ctx, t_near, qq, false, V->op_C, V->near.get(), &need_near));
+    V->near->dst_out = true;
     V->out.reset(new Phase());
-    MH_TRY(build_phase(ctx, t_out, qq, false, V->op_C, V->out.get(), &need));
+    MH_TRY(build_phase(ctx, t_out, qq, true, V->op_C, V->out.get(), &need));
     V->out->dst_out = true;
     MH_ALLOC(ctx, V->vec, V->vec_len);
     MH_ALLOC(ctx, V->vec32, V->vec_len);
     MH_ALLOC(ctx, V->temp, need);
+    MH_ALLOC(ctx, V->temp_near, need_near);
+    MH_TRY(V->side.create(ctx));
     V->temp_len = need;
     MH_CUDA(ctx, cudaMemsetAsync(V->vec.p, 0, V->vec_len * 8, st));
     MH_CUDA(ctx, cudaMemsetAsync(V->vec32.p, 0, V->vec_len * 4, st));
     // shared-memory opt-in for the contraction kernel
     int maxs = 0;
-    for (auto* ph : {V->p2m.get(), V->m2l.get(), V->out.get()}) maxs = std::max(maxs, ph->smem);
+    for (auto* ph : {V->p2m.get(), V->m2l.get(), V->out.get(), V->near.get()}) maxs = std::max(maxs, ph->smem);
     MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       160 * 1024));
     MH_CUDA(ctx, cudaFuncSetAttribute(k_apply<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
@@ -1387,6 +1440,7 @@ struct DipData {
     dbuf<int64_t> d_op_off;
     dbuf<int32_t> d_op_C;
     std::unique_ptr<Phase> p2m, m2l, out;
+    SideStream side;                       // the near field runs there beside the passes
 };
 }  // namespace
 
@@ -1673,13 +1727,14 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
     MH_ALLOC(ctx, D->temp, need);
     MH_CUDA(ctx, cudaMemsetAsync(D->vec.p, 0, D->vec_len * 8, st));
     MH_CUDA(ctx, cudaMemsetAsync(D->vec32.p, 0, D->vec_len * 4, st));
+    MH_TRY(D->side.create(ctx));
     MH_CUDA(ctx, cudaStreamSynchronize(st));
     V->dip = std::move(D);
     return MH_OK;
 }
 
 template <typename TOP>
-static mh_status dipole_run(mh_ctx* ctx, VolData* V, DipData* D, const TOP* ops) {
+static mh_status dipole_passes(mh_ctx* ctx, VolData* V, DipData* D, const TOP* ops) {
     TOP* pool = typed_pool<TOP>(D->vec, D->vec32);
     auto run = [&](const Phase* ph) {
         return run_phase_on<TOP>(ctx, ops, D->d_op_off.p, D->d_op_C.p, pool, D->vec.p, D->temp.p, ph,
@@ -1689,8 +1744,13 @@ static mh_status dipole_run(mh_ctx* ctx, VolData* V, DipData* D, const TOP* ops)
     MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, pool, true, "dlp_fmm_chain"));
     MH_TRY(run(D->m2l.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, pool, false, "dlp_fmm_chain"));
-    MH_TRY(run(D->out.get()));
     return MH_OK;
+}
+
+template <typename TOP>
+static mh_status dipole_out(mh_ctx* ctx, DipData* D, const TOP* ops) {
+    return run_phase_on<TOP>(ctx, ops, D->d_op_off.p, D->d_op_C.p, typed_pool<TOP>(D->vec, D->vec32), D->vec.p,
+                             D->temp.p, D->out.get(), "dlp_fmm_contract");
 }
 
 // w_sorted: dipole strengths in the leaf-sorted order given to volume_dipole_setup.
@@ -1701,21 +1761,36 @@ mh_status volume_dipole_apply(mh_ctx* ctx, mh_tree* t, const double* w_sorted, m
     DipData* D = V->dip.get();
     prof_scope ps(ctx, "dlp_fmm");
     cudaStream_t st = ctx->stream;
+    const bool mixed = prec == MH_PREC_MIXED;
     if (!D->near_blocks) MH_CUDA(ctx, cudaMemsetAsync(D->vec.p + D->DU_off, 0, t->n_leaves * D->qq * 8, st));
-    if (prec == MH_PREC_MIXED) {
+    if (mixed) {
         // weights in binary32 once: the contractions and the near-field kernel read them
         k_d2f<<<mh_grid(D->nd, 256), 256, 0, st>>>(w_sorted, D->vec32.p + D->W_off, D->nd);
         MH_LAUNCHED(ctx);
-        MH_TRY(dipole_run<float>(ctx, V, D, D->ops32.p));
     } else {
         MH_CUDA(ctx, cudaMemcpyAsync(D->vec.p + D->W_off, w_sorted, D->nd * 8, cudaMemcpyDeviceToDevice, st));
-        MH_TRY(dipole_run<double>(ctx, V, D, D->ops64.p));
     }
-    if (!D->near_blocks && D->n_chunks) {
+    // The near field reads the weights and adds into U^h only; the passes read the weights and
+    // touch only the expansions until their output phase adds the far field to U^h.  Without
+    // region timers the passes run on the side stream while the near field runs on the context
+    // stream, joined before the output phase; with the timers everything runs in order on the
+    // context stream.  Both forms add near, then far.
+    const bool near = !D->near_blocks && D->n_chunks;
+    const bool fork = near && !ctx->profiling && D->side.s;
+    if (fork) {
+        MH_TRY(D->side.begin(ctx, st));
+        ctx->stream = D->side.s;
+        const mh_status s = mixed ? dipole_passes<float>(ctx, V, D, D->ops32.p)
+                                  : dipole_passes<double>(ctx, V, D, D->ops64.p);
+        ctx->stream = st;
+        MH_TRY(s);
+        MH_TRY(D->side.end(ctx));
+    }
+    if (near) {
         prof_scope ps2(ctx, "dlp_near", 68.0 * D->near_pairs, 24.0 * (double)D->nd);
         const unsigned nb = (unsigned)D->n_chunks;
         double* out = D->vec.p + D->DU_off;
-        if (prec == MH_PREC_MIXED) {
+        if (mixed) {
             const float* w32 = D->vec32.p + D->W_off;
             const mh_dl32 c32 = mh_dl32_make(1.0 / D->inv_alpha, 30.0);
             const double pref32 = D->pref * D->inv_alpha * D->inv_alpha;
@@ -1731,11 +1806,16 @@ mh_status volume_dipole_apply(mh_ctx* ctx, mh_tree* t, const double* w_sorted, m
 #undef MH_NEAR32
         } else {
             k_dip_near64<<<nb, NEAR_T, 0, st>>>(t->nodes.p, D->chunks.p, D->leaf_red.p, D->flat_idx.p, D->dxy.p,
-                                                D->dnrm.p, w_sorted, D->qq, D->inv_alpha, D->pref, D->part.p,
-                                                D->red_cnt.p, out);
+                                                D->dnrm.p, D->vec.p + D->W_off, D->qq, D->inv_alpha, D->pref,
+                                                D->part.p, D->red_cnt.p, out);
         }
         MH_LAUNCHED(ctx);
     }
+    if (fork)
+        MH_CUDA(ctx, cudaStreamWaitEvent(st, D->side.join, 0));
+    else
+        MH_TRY(mixed ? dipole_passes<float>(ctx, V, D, D->ops32.p) : dipole_passes<double>(ctx, V, D, D->ops64.p));
+    MH_TRY(mixed ? dipole_out<float>(ctx, D, D->ops32.p) : dipole_out<double>(ctx, D, D->ops64.p));
     *u = D->vec.p + D->DU_off;
     return MH_OK;
 }
@@ -1760,13 +1840,44 @@ void volume_free(mh_tree* t) {
     t->vol = nullptr;
 }
 
+// The near tables read only the node values and write U^h; the passes touch only the
+// expansions until the output phase adds L2P and M2P to U^h.  Without region timers the passes
+// run on the side stream while the near phase runs on the context stream, joined before the
+// output phase; with the timers everything runs in order on the context stream.  Both forms
+// write U^h as near, then add far.
 template <typename TOP>
-static mh_status volume_run(mh_ctx* ctx, mh_tree* t, VolData* V, const TOP* ops) {
+static mh_status volume_passes(mh_ctx* ctx, VolData* V, const TOP* ops) {
     TOP* pool = typed_pool<TOP>(V->vec, V->vec32);
     MH_TRY(run_phase(ctx, V, ops, V->p2m.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, V->M_off, V->L_off, pool, true, "volume_chain"));
     MH_TRY(run_phase(ctx, V, ops, V->m2l.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, V->M_off, V->L_off, pool, false, "volume_chain"));
+    return MH_OK;
+}
+
+template <typename TOP>
+static mh_status volume_run(mh_ctx* ctx, mh_tree* t, VolData* V, const TOP* ops) {
+    TOP* pool = typed_pool<TOP>(V->vec, V->vec32);
+    cudaStream_t main = ctx->stream;
+    if (!V->near_cover)
+        MH_CUDA(ctx, cudaMemsetAsync(V->vec.p + V->U_off, 0, t->n_leaves * V->qq * 8, main));
+    const bool near = V->near->n_tasks > 0;
+    const bool fork = near && !ctx->profiling && V->side.s;
+    if (fork) {
+        MH_TRY(V->side.begin(ctx, main));
+        ctx->stream = V->side.s;
+        const mh_status s = volume_passes<TOP>(ctx, V, ops);
+        ctx->stream = main;
+        MH_TRY(s);
+        MH_TRY(V->side.end(ctx));
+    }
+    if (near)
+        MH_TRY(run_phase_on<TOP>(ctx, ops, V->d_op_off.p, V->d_op_C.p, pool, V->vec.p, V->temp_near.p,
+                                 V->near.get(), "volume_contract"));
+    if (fork)
+        MH_CUDA(ctx, cudaStreamWaitEvent(main, V->side.join, 0));
+    else
+        MH_TRY(volume_passes<TOP>(ctx, V, ops));
     MH_TRY(run_phase(ctx, V, ops, V->out.get()));
     return MH_OK;
 }
