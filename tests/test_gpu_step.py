@@ -78,3 +78,35 @@ def test_heat_step_matches_oracle(mh, ctx, oracle_c1, prec, tol):
     e = float(np.linalg.norm(got[inside] - ref[inside]) / np.linalg.norm(ref[inside]))
     print(f"heat_step prec={prec}: rel L2 {e:.2e}, gmres its {info.gmres_iterations}")
     assert e < tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_overlapped_and_timed_steps_agree(mh, ctx, oracle_c1, prec):
+    """The near fields run beside the multipole passes (a second stream) when the region
+    timers are off and in order when they are on; both add near, then far.  Two problems
+    stepped once from the same state agree to rounding (the binary64 upsampled rule adds
+    the sums of a target near several curves with atomics, in no fixed order)."""
+    wl, pb, nodes, bn = oracle_c1
+    mf = W.Manufactured
+    dev = lambda a: torch.tensor(a, device="cuda")
+    out = []
+    for timed in (False, True):
+        gt = mh.Tree(ctx, wl.box, wl.q, wl.min_level, wl.max_level)
+        bnd = mh.Boundary(ctx, wl.curves, alpert_order=8)
+        prob = mh.Problem(ctx, gt, bnd, wl.dt, 20, ext_mode=mh.MH_EXT_ARRAY)
+        u = dev(mf.u(0.0, nodes))
+        un = torch.empty_like(u)
+        sigma = torch.zeros(bnd.n, dtype=torch.float64, device="cuda")
+        b_ext = dev(mf.u(0.0, nodes) + wl.dt * mf.F(0.0, nodes))
+        ctx.profile(timed)
+        try:
+            mh.heat_step(ctx, prob, u, dev(mf.F(0.0, nodes)), dev(mf.u(wl.dt, bn)), un, sigma, b_ext=b_ext,
+                         gmres_tol=1e-12, prec=prec)
+            if timed:
+                assert ctx.profile_read("dlp_near", reset=True)[1] == 1   # the near field ran, timed
+        finally:
+            ctx.profile(False)
+        out.append(un.cpu().numpy())
+    ins = pb.inside
+    d = float(np.linalg.norm(out[0][ins] - out[1][ins]) / np.linalg.norm(out[1][ins]))
+    assert d <= 1e-13, d

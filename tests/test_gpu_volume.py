@@ -96,3 +96,24 @@ def test_full_size_adaptive_sampled(mh, ctx):
     e = _rel(out.cpu().numpy()[sel], ref)
     print(f"full-size adaptive p=20: {e:.2e}")
     assert e < 1e-8
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_overlapped_and_timed_forms_identical(mh, ctx, prec):
+    """Without region timers the near tables run on the context stream while the multipole
+    passes run on a second stream; with the timers every phase runs in order on one stream.
+    Both write U as near, then add far, and no sum depends on timing: identical results."""
+    wl = W.starfish_domain(n_per_curve=64)
+    gt = mh.Tree(ctx, wl.box, 4, 2, 6, wl.forcing, 1e-6)
+    rng = np.random.default_rng(7)
+    b = torch.tensor(rng.standard_normal(gt.n_nodes), device="cuda")
+    fast, timed = torch.empty_like(b), torch.empty_like(b)
+    mh.mh_volume_potential(ctx, gt, 0.05, 20, b, fast, prec=prec)
+    ctx.profile(True)
+    try:
+        mh.mh_volume_potential(ctx, gt, 0.05, 20, b, timed, prec=prec)
+        _, launches, _, _ = ctx.profile_read("volume_contract", reset=True)
+    finally:
+        ctx.profile(False)
+    assert launches >= 4   # near tables, P2M, M2L + P2L, output: one timed region each
+    assert torch.equal(fast, timed)
