@@ -2834,7 +2834,7 @@ extern "C" mh_status mh_gmres_solve_static(mh_ctx* ctx, mh_boundary* bd, double 
     const int ew = mh_grid(n, 256) < 152 * 4 ? mh_grid(n, 256) : 152 * 4;
     // the array keeps the previous call's contents: clear what the iteration reads first
     MH_CUDA(ctx, cudaMemsetAsync(g, 0, MH_STATIC_SMALL * sizeof(double), st));
-    mh_gmres_info inf{0, 0, 0.0, 0};
+    mh_gmres_info inf{0, 0, 0.0, 0, 0.0};
     double bnorm;
     MH_TRY(vec_norm(ctx, rhs_dev, n, small + 2, &bnorm));
     if (bnorm == 0.0) {
