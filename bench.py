@@ -356,7 +356,7 @@ KERNEL_REGIONS = {
     "dlp_near": ("alu", "auto", "double-layer near-field pair sums (fine dipoles of neighbour leaves)"),
     "dlp_fine": ("alu", "auto", "16x upsampled pair sums at the normal-line auxiliary points"),
     "dlp_coarse": ("alu", "auto", "trapezoid pair sums"),
-    "volume_contract": ("alu", "auto", "volume multipole contractions (P2M, M2L + P2L, near tables + L2P + M2P)"),
+    "volume_contract": ("alu", "auto", "volume multipole contractions (near tables, P2M, M2L + P2L, L2P + M2P)"),
     "volume_chain": ("alu", "auto", "volume M2M / L2L level chains"),
     "dlp_fmm_contract": ("alu", "auto", "double-layer multipole contractions (dipole P2M, M2L + P2L, L2P + M2P)"),
     "dlp_fmm_chain": ("alu", "auto", "double-layer M2M / L2L level chains"),
