@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -53,13 +54,17 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "fallback": True}
 
 
+# where ClockSampler keeps its raw nvidia-smi samples (--clocks-dir); the summary goes into the JSON line
+CLOCKS_DIR = tempfile.gettempdir()
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(CLOCKS_DIR, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -689,8 +694,12 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="step through heat_step on the stream instead of one graph launch per step")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--clocks-dir", default=None, help="directory for the raw clock samples (default: temp dir)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
+    if args.clocks_dir:
+        global CLOCKS_DIR
+        CLOCKS_DIR = args.clocks_dir
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "ours" and args.workload == "batch":
