@@ -162,7 +162,8 @@ mh_status mh_volume_potential(mh_ctx* ctx, mh_tree* tree, double alpha, int p, c
  * targets_dev != NULL: out_dev[i] = U^h(x_i) = (1/(2 pi alpha^2)) int d/dnu_y K0 sigma ds
  *   at n_targets points (2 doubles each) assumed inside Omega, with the near-boundary
  *   rule: 16x upsampled density for targets within 5 h_s of a curve, interpolation
- *   along the normal within h_s/4. */
+ *   along the normal within h_s/4.  n_targets == 0 evaluates nothing (out_dev untouched);
+ *   n_targets < 0 is MH_ERR_INVALID_ARG. */
 mh_status mh_double_layer_apply(mh_ctx* ctx, mh_boundary* bnd, double alpha, const double* sigma_dev,
                                 const double* targets_dev, int64_t n_targets, double* out_dev,
                                 mh_precision prec);

@@ -128,6 +128,12 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _need(t, n, name):
+    """Reject a buffer shorter than the n entries the library will read or write through it."""
+    if t is not None and t.numel() < n:
+        raise ValueError(f"{name}: {t.numel()} entries, the call needs {n}")
+
+
 def _ptr4(t):
     """Device pointer of a contiguous CUDA float32 / int32 tensor (or None)."""
     if t is None:
@@ -260,6 +266,8 @@ class Tree:
 
 
 def mh_volume_potential(ctx: Context, tree: Tree, alpha: float, p: int, b, out, prec: int = MH_PREC_FP64):
+    _need(b, tree.n_nodes, "b")
+    _need(out, tree.n_nodes, "out")
     ctx.check(_lib.mh_volume_potential(ctx.h, tree.h, float(alpha), int(p), _ptr(b), _ptr(out), int(prec)))
     return out
 
@@ -267,6 +275,14 @@ def mh_volume_potential(ctx: Context, tree: Tree, alpha: float, p: int, b, out, 
 def mh_double_layer_apply(ctx: Context, bnd: Boundary, alpha: float, sigma, out, targets=None,
                           prec: int = MH_PREC_FP64):
     n_t = 0 if targets is None else int(targets.shape[0])
+    _need(sigma, bnd.n, "sigma")
+    if targets is None:
+        _need(out, bnd.n, "out")
+    elif n_t == 0:
+        return out   # no targets (an empty tensor's pointer may be null, which selects the on-surface operator)
+    else:
+        _need(targets, 2 * n_t, "targets")
+        _need(out, n_t, "out")
     ctx.check(_lib.mh_double_layer_apply(ctx.h, bnd.h, float(alpha), _ptr(sigma), _ptr(targets), n_t, _ptr(out),
                                          int(prec)))
     return out
@@ -274,6 +290,8 @@ def mh_double_layer_apply(ctx: Context, bnd: Boundary, alpha: float, sigma, out,
 
 def mh_gmres_solve(ctx: Context, bnd: Boundary, alpha: float, rhs, sigma, tol: float = 1e-10,
                    max_iter: int = 100, prec: int = MH_PREC_FP64) -> GmresInfo:
+    _need(rhs, bnd.n, "rhs")
+    _need(sigma, bnd.n, "sigma")
     info = GmresInfo()
     ctx.check(_lib.mh_gmres_solve(ctx.h, bnd.h, float(alpha), _ptr(rhs), _ptr(sigma), float(tol), int(max_iter),
                                   int(prec), ctypes.byref(info)))
@@ -283,6 +301,8 @@ def mh_gmres_solve(ctx: Context, bnd: Boundary, alpha: float, rhs, sigma, tol: f
 def mh_gmres_solve_static(ctx: Context, bnd: Boundary, alpha: float, rhs, sigma, tol: float = 1e-10,
                           max_iter: int = 64) -> GmresInfo:
     """Allocation-free binary64 GMRES (fixed workspace inside the library; see include/mh.h)."""
+    _need(rhs, bnd.n, "rhs")
+    _need(sigma, bnd.n, "sigma")
     info = GmresInfo()
     ctx.check(_lib.mh_gmres_solve_static(ctx.h, bnd.h, float(alpha), _ptr(rhs), _ptr(sigma), float(tol),
                                          int(max_iter), ctypes.byref(info)))
@@ -330,8 +350,16 @@ class Problem:
             self.h = None
 
 
+def _step_sizes(prob, node_bufs, bnd_bufs):
+    for t in node_bufs:
+        _need(t, prob.tree.n_nodes, "volume-node buffer")
+    for t in bnd_bufs:
+        _need(t, prob.bnd.n, "boundary buffer")
+
+
 def heat_step(ctx: Context, prob: Problem, u, F, f_next, u_next, sigma, b_ext=None, gmres_tol: float = 1e-10,
               prec: int = MH_PREC_FP64) -> StepInfo:
+    _step_sizes(prob, (u, F, u_next, b_ext), (f_next, sigma))
     info = StepInfo()
     ctx.check(_lib.heat_step(ctx.h, prob.h, _ptr(u), _ptr(F), _ptr(f_next), _ptr(b_ext), _ptr(u_next), _ptr(sigma),
                              float(gmres_tol), int(prec), ctypes.byref(info)))
@@ -340,6 +368,7 @@ def heat_step(ctx: Context, prob: Problem, u, F, f_next, u_next, sigma, b_ext=No
 
 def heat_step_gear(ctx: Context, prob: Problem, u, u_prev, F, F_prev, f_next, u_next, sigma, b_ext=None,
                    gmres_tol: float = 1e-10, prec: int = MH_PREC_FP64) -> StepInfo:
+    _step_sizes(prob, (u, u_prev, F, F_prev, u_next, b_ext), (f_next, sigma))
     info = StepInfo()
     ctx.check(_lib.heat_step_gear(ctx.h, prob.h, _ptr(u), _ptr(u_prev), _ptr(F), _ptr(F_prev), _ptr(f_next),
                                   _ptr(b_ext), _ptr(u_next), _ptr(sigma), float(gmres_tol), int(prec),

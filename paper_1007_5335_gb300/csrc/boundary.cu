@@ -2745,6 +2745,7 @@ extern "C" mh_status mh_double_layer_apply(mh_ctx* ctx, mh_boundary* b, double a
         return MH_OK;
     }
     if (n_targets < 0) return mh_fail(ctx, MH_ERR_INVALID_ARG, "n_targets < 0");
+    if (n_targets == 0) return MH_OK;   // no targets: nothing to evaluate, out_dev untouched
     dlp_targets tg;
     MH_TRY(dlp_classify(ctx, b, targets_dev, n_targets, &tg));
     MH_TRY(dlp_evaluate(ctx, b, alpha, &tg, sigma_dev, out_dev, prec));

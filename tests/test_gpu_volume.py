@@ -117,3 +117,20 @@ def test_overlapped_and_timed_forms_identical(mh, ctx, prec):
         ctx.profile(False)
     assert launches >= 4   # near tables, P2M, M2L + P2L, output: one timed region each
     assert torch.equal(fast, timed)
+
+
+def test_minimal_uniform_tree(mh, ctx):
+    """The smallest tree with a far field: uniform level 2 (16 leaves, q = 4).  Multipoles exist
+    only at the leaf level (no M2M / L2L chain), M2L couples the non-adjacent leaves and the near
+    tables the adjacent ones.  A missing or doubled interaction shows at 1e-2; the bar leaves
+    room for the truncation at p = 20."""
+    box, q, alpha = (-1.0, -1.0, 2.0), 4, 0.1
+    gt = mh.Tree(ctx, box, q, 2, 2)
+    ot = T.build(box, q, 2, 2)
+    assert gt.n_nodes == 256
+    M = V.uniform_operator(2, box, q, alpha, order=[(b[1], b[2]) for b in ot.leaves])
+    b = _smooth_plus_noise(ot.nodes(), 3)
+    out = torch.empty(gt.n_nodes, dtype=torch.float64, device="cuda")
+    for prec, tol in ((0, 1e-8), (1, 1e-6)):
+        mh.mh_volume_potential(ctx, gt, alpha, 20, torch.tensor(b, device="cuda"), out, prec=prec)
+        assert _rel(out.cpu().numpy(), M @ b) < tol, prec
