@@ -132,3 +132,27 @@ def test_autotuner(mh, ctx):
         assert errs[p] <= 1e-7
     assert [e.near_tile for e in rep[3:]] == [128, 256, 512] and all(e.p == p for e in rep[3:])
     assert all(e.ms_per_step > 0 for e in rep)
+
+
+def test_full_size_graph_step_matches_binary64(mh, ctx):
+    """The starfish workload at full size (N_Gamma = 6144, N_D = 257,728, p = 20) in the form
+    the headline is timed in: one graph launch per step through the batch API, mixed precision.
+    Three steps agree with three binary64 heat_step calls on the stream to the 1e-6 bar of the
+    metric (relative L2 over Omega)."""
+    wl = W.starfish_domain()
+    t1, b1, p1, F1 = _make(mh, ctx, wl, p=wl.p)
+    t2, b2, p2, F2 = _make(mh, ctx, wl, p=wl.p)
+    batch = mh.Batch(ctx, [p1])
+    u1 = torch.zeros(t1.n_nodes, dtype=torch.float64, device="cuda")
+    s1 = torch.zeros(b1.n, dtype=torch.float64, device="cuda")
+    f = torch.zeros(b1.n, dtype=torch.float64, device="cuda")
+    u2, un = torch.zeros_like(u1), torch.empty_like(u1)
+    s2 = torch.zeros_like(s1)
+    for _ in range(3):
+        info = batch.step([u1], [F1], [f], [s1], gmres_tol=1e-10, prec=mh.MH_PREC_MIXED)[0]
+        assert info.gmres_rel_residual <= 1e-10
+        mh.heat_step(ctx, p2, u2, F2, f, un, s2, gmres_tol=1e-10, prec=mh.MH_PREC_FP64)
+        u2, un = un, u2
+    ins = _inside(p2)
+    err = (torch.linalg.norm((u1 - u2)[ins]) / torch.linalg.norm(u2[ins])).item()
+    assert err <= 1e-6, err
