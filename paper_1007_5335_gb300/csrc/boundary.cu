@@ -1573,8 +1573,14 @@ __global__ void k_dlp_fine_corr32(const double* __restrict__ xy, const int32_t* 
 // v0 = -(A sigma)(t*) / (2 alpha^2) (trigonometric interpolation of the on-surface
 // values) and the values at the 4 auxiliary points.
 // The interpolation weights D_N(t* - t_i) depend on the target alone and are formed once
-// (k_line_weights): D_N(t* - t_i) = sin(N (t* - t_i)/2) cot((t* - t_i)/2) / N with
-// sin(N (t* - t_i)/2) = (-1)^i sin(N t*/2) and the half angles by the addition formulas.
+// (k_line_weights): D_N(t* - t_i) = sin(N (t* - t_i)/2) cot((t* - t_i)/2) / N, written about
+// the nearest node j, t* = t_j + delta (|delta| <= h/2):
+//   sin(N (t* - t_i)/2) = (-1)^(j-i) sin(N delta/2)        (a small argument),
+//   (t* - t_i)/2 = delta/2 + (j-i) h/2                      (angle addition with the exact
+//                                                            half-angle table, i != j).
+// A target whose foot point lies on (or within rounding of) a node keeps full relative accuracy
+// in its own weight, which tends to 1 there; a closed form through sin(N t*/2) of the large
+// argument and the half-angle difference of t* and t_j loses it to cancellation.
 __global__ void k_line_weights(const int32_t* __restrict__ line_curve, const double* __restrict__ line_data,
                                int64_t nline, const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
                                const double2* __restrict__ half, const int64_t* __restrict__ woff, double* w) {
@@ -1583,15 +1589,28 @@ __global__ void k_line_weights(const int32_t* __restrict__ line_curve, const dou
     const int lane = threadIdx.x & 31;
     const int k = line_curve[t];
     const int N = nn[k];
-    const double ts = line_data[4 * t];
-    const double2* hf = half + off[k];
-    double sN, cN, sh0, ch0;
-    sincos(0.5 * N * ts, &sN, &cN);
-    sincos(0.5 * ts, &sh0, &ch0);
+    const double ts = line_data[4 * t];   // in [0, 2 pi)
+    const double2* hf = half + off[k];    // (cos, sin)(t_m / 2), m = 0..N-1
+    const double h = 2.0 * MH_PI / N;
+    int j = (int)rint(ts / h);            // 0..N
+    const double delta = ts - j * h;
+    if (j >= N) j -= N;
+    const double sNd = sin(0.5 * N * delta);
+    double sd, cd;
+    sincos(0.5 * delta, &sd, &cd);
     for (int i = lane; i < N; i += 32) {
-        const double sh = sh0 * hf[i].x - ch0 * hf[i].y;
-        const double ch = ch0 * hf[i].x + sh0 * hf[i].y;
-        const double sg = (i & 1) ? -sN : sN;
+        const int m = j - i;
+        double sh, ch;   // sin, cos of (t* - t_i) / 2
+        if (m == 0) {
+            sh = sd;
+            ch = cd;
+        } else {
+            const int am = m > 0 ? m : -m;
+            const double cm = hf[am].x, sm = m > 0 ? hf[am].y : -hf[am].y;
+            sh = sd * cm + cd * sm;
+            ch = cd * cm - sd * sm;
+        }
+        const double sg = (m & 1) ? -sNd : sNd;
         w[woff[t] + i] = fabs(sh) < 1e-300 ? 1.0 : sg * ch / sh / N;
     }
 }
