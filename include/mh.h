@@ -91,6 +91,10 @@ mh_status mh_destroy(mh_ctx* ctx);
 const char* mh_last_error(const mh_ctx* ctx);
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t mh_kernel_launches(const mh_ctx* ctx);
+/* Number of device allocations plus frees (cudaMalloc / cudaFree) the library has made so far,
+ * over all contexts of the process (library instrumentation: a call that allocates nothing
+ * leaves it unchanged). */
+int64_t mh_device_alloc_calls(void);
 
 /* Timing of named kernel regions (library instrumentation, no counterpart in the paper).
  * When enabled, the library records a CUDA event pair on its stream around each launch

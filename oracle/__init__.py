@@ -16,6 +16,7 @@ Modules
   volume      direct volume potential with exact integrals of the leaf interpolant
   tree        adaptive quadtree, 2:1 balance and interaction lists
   step        IMEX (backward) Euler heat step (Section 2)
+  pool        the independent per-target / per-row loops over spawned worker processes
   warmstart   learned initial guess for the boundary solve (Fourier features, MLP,
               closed-form start, Adam, minimum-residual judge)
 

