@@ -365,6 +365,9 @@ KERNEL_REGIONS = {
     "volume_chain": ("alu", "auto", "volume M2M / L2L level chains"),
     "dlp_fmm_contract": ("alu", "auto", "double-layer multipole contractions (dipole P2M, M2L + P2L, L2P + M2P)"),
     "dlp_fmm_chain": ("alu", "auto", "double-layer M2M / L2L level chains"),
+    "volume_contract_tc": ("hbm", None, "volume contractions on the tensor cores (k_contract_tc: TF32 head/tail "
+                                        "MMAs; binary32 sources, operators and products)"),
+    "dlp_fmm_contract_tc": ("hbm", None, "double-layer contractions on the tensor cores (k_contract_tc)"),
 }
 # DRAM bytes (read + write) per launch of the region's main kernel, from the ncu launch list
 # of the timed steps (profiles/launches_heat_step_starfish_mixed.md); None where not captured.
@@ -386,6 +389,8 @@ def region_roofline(name, v, prec, mh, peaks):
         out.update({"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "bytes_per_launch": nbytes / launches,
                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"})
+        if flops:
+            out["tflops"] = flops / launches / avg_s / 1e12
     else:
         fp64 = pipe == "fp64" or (pipe == "auto" and prec != mh.MH_PREC_MIXED)
         achieved = flops / launches / avg_s / 1e12
@@ -404,7 +409,7 @@ def roofline(regions_ms, tree, bnd, prob, prec, mh, peaks, steps):
     dom = region_roofline(name, cand[name], prec, mh, peaks)
     dom["all_regions"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
                               for kk, vv in region_roofline(k, v, prec, mh, peaks).items()
-                              if kk in ("bound", "avg_launch_ms", "achieved", "peak", "unit", "frac")}
+                              if kk in ("bound", "avg_launch_ms", "achieved", "peak", "unit", "frac", "tflops")}
                           for k, v in sorted(cand.items(), key=lambda kv: -kv[1][0])}
     return dom
 

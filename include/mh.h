@@ -108,6 +108,14 @@ mh_status mh_profile_enable(mh_ctx* ctx, int on);
 mh_status mh_profile_read(mh_ctx* ctx, const char* region, double* total_ms, int64_t* launches, double* flops,
                           double* bytes, int reset);
 
+/* Engine of the binary32 batched contractions of the multipole passes (near-field tables,
+ * P2M, M2L, P2L, L2P, M2P: Section 3.1) in MH_PREC_MIXED: on != 0 (default) forms the operators
+ * with enough tasks as TF32 head/tail matrix products on the tensor cores (three MMAs per K step,
+ * binary32 accumulation); 0 keeps every contraction on the CUDA cores.  Binary64 work is not
+ * affected.  Takes effect for work issued after the call (a batch graph recorded earlier keeps
+ * the form it was recorded with). */
+mh_status mh_set_tensor_cores(mh_ctx* ctx, int on);
+
 /* ---- boundary (Section 3.2) -------------------------------------------------------- */
 
 /* Build the boundary from node coordinates xy_host[2 N_Gamma] (curves concatenated,
@@ -142,6 +150,10 @@ mh_status mh_tree_leaves(mh_ctx* ctx, const mh_tree* tree, int32_t* out_host);
 mh_status mh_tree_boxes(mh_ctx* ctx, const mh_tree* tree, int32_t* out_host);
 /* Volume node coordinates, 2 doubles per node, into device memory. */
 mh_status mh_tree_nodes(mh_ctx* ctx, const mh_tree* tree, double* out_dev);
+/* Synchronise the context stream and report whether a bounded device wait of the tree's
+ * tensor-core contractions gave up since the last check (MH_ERR_TIMEOUT; the results of that
+ * work are not valid); MH_OK otherwise.  mh_volume_potential performs this check itself. */
+mh_status mh_tree_check(mh_ctx* ctx, mh_tree* tree);
 /* Interaction list `which` (0 = U, 1 = V, 2 = W, 3 = X) in CSR form over all boxes
  * (box ids as in mh_tree_boxes): offsets_host[n_boxes + 1]; items_host may be NULL to
  * query offsets only.  Item lists are sorted by box id. */

@@ -61,6 +61,8 @@ _SIGS = {
     "mh_destroy": [_p],
     "mh_kernel_launches": [_p],
     "mh_device_alloc_calls": [],
+    "mh_set_tensor_cores": [_p, _i],
+    "mh_tree_check": [_p, _p],
     "mh_boundary_create": [_p, _i, _p, _p, _i, ctypes.POINTER(_p)],
     "mh_boundary_destroy": [_p],
     "mh_boundary_size": [_p, ctypes.POINTER(_i64)],
@@ -166,6 +168,10 @@ class Context:
     def launches(self) -> int:
         return int(_lib.mh_kernel_launches(self.h))
 
+    def tensor_cores(self, on: bool = True):
+        """mh_set_tensor_cores: binary32 contractions on the tensor cores (default) or CUDA cores."""
+        self.check(_lib.mh_set_tensor_cores(self.h, 1 if on else 0))
+
     def profile(self, on: bool = True):
         """mh_profile_enable: time the instrumented kernel regions with CUDA events."""
         self.check(_lib.mh_profile_enable(self.h, 1 if on else 0))
@@ -252,6 +258,10 @@ class Tree:
         out = torch.empty((self.n_nodes, 2), dtype=torch.float64, device=f"cuda:{self.ctx.device}")
         self.ctx.check(_lib.mh_tree_nodes(self.ctx.h, self.h, _ptr(out)))
         return out
+
+    def check(self):
+        """mh_tree_check: raise MHError if a bounded device wait of this tree's work gave up."""
+        self.ctx.check(_lib.mh_tree_check(self.ctx.h, self.h))
 
     def list(self, which: str):
         offs = np.zeros(self.n_boxes + 1, dtype=np.int32)

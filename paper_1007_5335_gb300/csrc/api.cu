@@ -38,6 +38,12 @@ extern "C" int64_t mh_kernel_launches(const mh_ctx* ctx) { return ctx ? ctx->lau
 
 std::atomic<int64_t> g_mh_alloc_calls{0};
 
+extern "C" mh_status mh_set_tensor_cores(mh_ctx* ctx, int on) {
+    if (!ctx) return MH_ERR_INVALID_ARG;
+    ctx->tensor_cores = on != 0;
+    return MH_OK;
+}
+
 extern "C" int64_t mh_device_alloc_calls(void) { return g_mh_alloc_calls.load(std::memory_order_relaxed); }
 
 mh_ctx::~mh_ctx() {

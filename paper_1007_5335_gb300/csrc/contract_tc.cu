@@ -1,0 +1,340 @@
+// Batched dense contractions of the multipole method on the tensor cores (Section 3.1: the
+// near-field tables of adjacent leaves and the translation operators M2L, P2M, P2L, L2P, M2P
+// of the volume potential, and those of the double layer's multipole pass).
+//
+// A phase is a list of tasks y_t = T_op(t) x_t, T_op of size R x C (R, C <= 64), sorted by
+// operator.  One CTA takes up to 128 tasks of one operator and forms them as one matrix product
+// on the fifth-generation tensor cores:
+//
+//     D[m][n] = sum_k X[m][k] T[n][k],   m = task in the chunk (M = 128), n = output row
+//     (N = R rounded up to 16), k = input column (K = C rounded up to 8),
+//
+// with tcgen05.mma kind::tf32 (binary32 accumulation in tensor memory).  TF32 keeps 11
+// significant bits, so every operand is split into a TF32 head and a TF32 tail (head = the
+// value rounded to TF32, tail = the remainder rounded to TF32) and the product is formed as
+//     X T ~ Xh Th + Xh Tt + Xt Th
+// (three MMAs per K step into one accumulator): the dropped term Xt Tt and the tail roundings
+// are ~2^-22 of |X||T| per product, close to binary32 arithmetic.  The operator's head and
+// tail are split once at set-up from the binary64 operator and stored in the exact shared-memory
+// image the MMA reads, so a CTA stages it with one bulk copy; the sources are gathered,
+// split and written into their image by all threads.
+//
+// Shared-memory images use the no-swizzle K-major layout of the tensor cores: core matrices of
+// 8 rows x 16 bytes (8 x 4 TF32), row r of a core matrix at byte 16 r; the core matrix of rows
+// 8g..8g+7 and columns 4c..4c+3 starts at byte c * LBO + g * 128 (SBO = 128 between row groups,
+// LBO = rows * 16 between column groups).  One MMA consumes K = 8 columns (two column groups).
+//
+// Products leave tensor memory through tcgen05.ld (warp w reads lanes 32 (w % 4) .. + 31, i.e.
+// tasks, and half w / 4 of the columns) and are written to the task-indexed product buffer
+// (later summed per destination in a fixed order) or, in phases with one task per destination,
+// straight to the destination.  Every wait on an mbarrier is bounded; a wait that gives up sets
+// the error word, skips the rest of the work, waits (bounded) for its bulk copy and frees the
+// tensor memory it holds.
+#include <cstring>
+
+#include "mh_internal.cuh"
+
+namespace {
+
+constexpr int TC_M = 128;         // tasks per CTA (rows of the MMA)
+constexpr int TC_THREADS = 256;   // 8 warps: gather and epilogue (two column halves)
+constexpr unsigned TC_SPIN = 1u << 22;   // polls of an mbarrier before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading (K direction) and stride
+// (row-group direction) byte offsets, all >> 4; descriptor version 1 at bits 46-47; no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::tf32: D binary32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
+// 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__device__ __forceinline__ uint32_t instr_desc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase `parity` of an mbarrier: true when it completed.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (unsigned i = 0; i < TC_SPIN; ++i)
+        if (mbar_try_wait(mbar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Round to TF32 (nearest, ties away from zero): the result is a binary32 value with the low 13
+// mantissa bits zero.
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Byte offset of element (row, k) in a no-swizzle K-major image with `rows` rows.
+__device__ __forceinline__ uint32_t img_off(int row, int k, int rows) {
+    return (uint32_t)((k >> 2) * (rows * 16) + (row >> 3) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+// One CTA per chunk of up to 128 tasks of one operator (see the file comment).
+//   img: operator images (head then tail, each npad x kpad binary32 in the layout above) at
+//        img_off[op] (floats); kpad[op]: the operator's K extent (C rounded up to 8);
+//   op_C[op]: its columns C; R: rows (outputs) of every operator of the phase, npad = R
+//   rounded up to 16; kmax: the largest kpad of the phase (sizes the source images);
+//   src: binary32 pool (sources at task_src[t]); temp: products [task][R] unless task_dst is
+//   given, then the products go to dst[task_dst[t] + r] (added when accumulate is set; TD =
+//   float for the expansion pool, double for the potentials).
+template <typename TD>
+__global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
+    const float* __restrict__ img, const int64_t* __restrict__ img_off_op, const int32_t* __restrict__ kpad_op,
+    const int32_t* __restrict__ op_C, const int32_t* __restrict__ chunk_op, const int32_t* __restrict__ chunk_t0,
+    const int64_t* __restrict__ task_src, const float* src, int R, int npad, int kmax, float* __restrict__ temp,
+    const int64_t* __restrict__ task_dst, int accumulate, TD* dst, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned base (the dynamic allocation is padded by 1 KB for this)
+    unsigned char* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    const int a_bytes = TC_M * kmax * 4;        // one source image (head or tail)
+    unsigned char* sAh = base;
+    unsigned char* sAt = sAh + a_bytes;
+    unsigned char* sB = sAt + a_bytes;          // head then tail, 2 * npad * kpad floats
+    __shared__ __align__(8) uint64_t bar_copy, bar_mma;
+    __shared__ uint32_t tmem_base;
+    __shared__ int ok;
+
+    const int ch = blockIdx.x;
+    const int op = chunk_op[ch];
+    const int t0 = chunk_t0[ch];
+    const int nt = chunk_t0[ch + 1] - t0;
+    const int C = op_C[op];
+    const int kp = kpad_op[op];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t ncols = npad <= 32 ? 32u : npad <= 64 ? 64u : 128u;   // power of two >= 32
+    const uint32_t mb_copy = smem_addr(&bar_copy), mb_mma = smem_addr(&bar_mma);
+    const uint32_t img_bytes = (uint32_t)(2 * npad * kp * 4);
+
+    if (threadIdx.x == 0) {
+        mbar_init(mb_copy, 1);
+        mbar_init(mb_mma, 1);
+        fence_mbar_init();
+        ok = 1;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    // the operator image: one bulk copy (16-byte aligned source and size)
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(mb_copy, img_bytes);
+        bulk_g2s(smem_addr(sB), img + img_off_op[op], img_bytes, mb_copy);
+    }
+    // the sources: thread -> (row m, column group c); 8 consecutive rows per column group fill
+    // one 128-byte line of the image, so a warp's stores touch 4 lines without bank conflicts
+    {
+        const int groups = kp >> 2;
+        for (int e = threadIdx.x; e < TC_M * groups; e += TC_THREADS) {
+            const int m = (e & 7) | ((e >> 3) / groups) << 3;
+            const int c = (e >> 3) % groups;
+            float v[4];
+            if (m < nt) {
+                const float* s = src + task_src[t0 + m];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = 4 * c + u < C ? s[4 * c + u] : 0.f;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = 0.f;
+            }
+            float4 h, t;
+            h.x = to_tf32(v[0]);
+            h.y = to_tf32(v[1]);
+            h.z = to_tf32(v[2]);
+            h.w = to_tf32(v[3]);
+            t.x = to_tf32(v[0] - h.x);
+            t.y = to_tf32(v[1] - h.y);
+            t.z = to_tf32(v[2] - h.z);
+            t.w = to_tf32(v[3] - h.w);
+            const uint32_t o = img_off(m, 4 * c, TC_M);
+            *reinterpret_cast<float4*>(sAh + o) = h;
+            *reinterpret_cast<float4*>(sAt + o) = t;
+        }
+    }
+    fence_async_smem();   // the generic-proxy stores above become visible to the tensor cores
+    __syncthreads();
+
+    if (threadIdx.x == 0) {
+        if (!mbar_wait(mb_copy, 0)) {
+            ok = 0;
+            atomicExch(err, 1);
+        } else {
+            tc_after_sync();
+            const uint32_t idesc = instr_desc_tf32(TC_M, npad);
+            const uint32_t a_lbo = TC_M * 16, b_lbo = (uint32_t)npad * 16;
+            const uint32_t ah = smem_addr(sAh), at = smem_addr(sAt);
+            const uint32_t bh = smem_addr(sB), bt = bh + (uint32_t)(npad * kp * 4);
+            for (int ks = 0; ks < kp / 8; ++ks) {
+                const uint32_t da = (uint32_t)ks * 2 * a_lbo, db = (uint32_t)ks * 2 * b_lbo;
+                mma_tf32(tmem, smem_desc(ah + da, a_lbo, 128), smem_desc(bh + db, b_lbo, 128), idesc, ks > 0);
+                mma_tf32(tmem, smem_desc(ah + da, a_lbo, 128), smem_desc(bt + db, b_lbo, 128), idesc, 1);
+                mma_tf32(tmem, smem_desc(at + da, a_lbo, 128), smem_desc(bh + db, b_lbo, 128), idesc, 1);
+            }
+            mma_commit(mb_mma);
+        }
+    }
+    __syncthreads();
+    const bool copied = ok != 0;
+    // every thread waits for the products; the CTA goes on only if all saw them (the loads
+    // below are warp-collective)
+    const bool have = __syncthreads_and(copied && mbar_wait(mb_mma, 0)) != 0;
+    if (copied && !have && threadIdx.x == 0) atomicExch(err, 2);
+    tc_after_sync();
+    if (have) {
+        // warp w: tasks 32 (w % 4) + lane, columns [h * npad / 2, (h + 1) * npad / 2), h = w / 4
+        const int m = 32 * (warp & 3) + lane;
+        const int half = npad >> 1;
+        const int c0 = (warp >> 2) * half;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+        for (int cc = 0; cc < half; cc += 8) {
+            uint32_t r[8];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                : "r"(taddr + (uint32_t)cc));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (m < nt) {
+                const int64_t t = t0 + m;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int rr = c0 + cc + u;
+                    if (rr < R) {
+                        const float v = __uint_as_float(r[u]);
+                        if (task_dst) {
+                            TD* y = dst + task_dst[t] + rr;
+                            *y = accumulate ? *y + (TD)v : (TD)v;
+                        } else {
+                            temp[t * R + rr] = v;
+                        }
+                    }
+                }
+            }
+        }
+    } else if (threadIdx.x == 0 && !copied) {
+        mbar_wait(mb_copy, 0);   // the copy may still be in flight: let it land (bounded)
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+// Host: round a binary32 value to TF32 (nearest, ties away from zero, as cvt.rna).
+float host_tf32(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return x;   // inf / nan unchanged
+    u = (u + 0x1000u) & ~0x1FFFu;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+}  // namespace
+
+int tc_pad_rows(int R) { return (R + 15) / 16 * 16; }
+int tc_pad_cols(int C) { return (C + 7) / 8 * 8; }
+
+// Head / tail image of one R x C operator (row-major, binary64) in the layout of the file
+// comment: out receives 2 * npad * kpad floats.
+void tc_operator_image(const double* op, int R, int C, int npad, int kpad, float* out) {
+    const size_t n = (size_t)npad * kpad;
+    std::memset(out, 0, 2 * n * sizeof(float));
+    for (int r = 0; r < R; ++r)
+        for (int k = 0; k < C; ++k) {
+            const double a = op[(size_t)r * C + k];
+            const float h = host_tf32((float)a);
+            const float t = host_tf32((float)(a - (double)h));
+            const size_t o = ((size_t)(k >> 2) * (npad * 16) + (r >> 3) * 128 + (r & 7) * 16 + (k & 3) * 4) / 4;
+            out[o] = h;
+            out[n + o] = t;
+        }
+}
+
+size_t tc_smem_bytes(int npad, int kmax) { return (size_t)(2 * TC_M + 2 * npad) * kmax * 4 + 1024; }
+
+mh_status tc_prepare(mh_ctx* ctx) {
+    static bool done[64] = {};
+    if (ctx->device >= 0 && ctx->device < 64 && done[ctx->device]) return MH_OK;
+    const int lim = 227 * 1024;
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_contract_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_contract_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    if (ctx->device >= 0 && ctx->device < 64) done[ctx->device] = true;
+    return MH_OK;
+}
+
+mh_status tc_contract_launch(mh_ctx* ctx, const tc_launch& a) {
+    const size_t smem = tc_smem_bytes(a.npad, a.kmax);
+    if (smem > 227 * 1024 || a.npad > 128 || a.kmax > 64)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "tensor-core contraction too large (%d x %d)", a.npad, a.kmax);
+    if (a.n_chunks == 0) return MH_OK;
+    if (a.dst_double)
+        k_contract_tc<double><<<(unsigned)a.n_chunks, TC_THREADS, smem, ctx->stream>>>(
+            a.img, a.img_off, a.kpad, a.op_C, a.chunk_op, a.chunk_t0, a.task_src, a.src, a.R, a.npad, a.kmax, a.temp,
+            a.task_dst, a.accumulate, static_cast<double*>(a.dst), a.err);
+    else
+        k_contract_tc<float><<<(unsigned)a.n_chunks, TC_THREADS, smem, ctx->stream>>>(
+            a.img, a.img_off, a.kpad, a.op_C, a.chunk_op, a.chunk_t0, a.task_src, a.src, a.R, a.npad, a.kmax, a.temp,
+            a.task_dst, a.accumulate, static_cast<float*>(a.dst), a.err);
+    MH_LAUNCHED(ctx);
+    return MH_OK;
+}

@@ -30,6 +30,7 @@ struct mh_ctx {
     int64_t launches = 0;
     bool profiling = false;
     bool capturing = false;   // inside a batch step: no cooperative launches
+    bool tensor_cores = true; // binary32 contractions on the tensor cores (mh_set_tensor_cores)
     int64_t loop_nodes = 0;   // graph WHILE nodes recorded (their body kernels: loop_kernels each)
     std::map<std::string, prof_region> prof;
     ~mh_ctx();
@@ -39,7 +40,7 @@ struct mh_ctx {
 // profiling is enabled (mh_profile_enable), nothing otherwise.
 struct prof_scope {
     mh_ctx* ctx;
-    const char* name;
+    std::string name;
     double flops, bytes;
     cudaEvent_t a = nullptr, b = nullptr;
     prof_scope(mh_ctx* c, const char* n, double flops_ = 0.0, double bytes_ = 0.0);
@@ -104,6 +105,33 @@ struct dbuf {
 };
 
 #define MH_ALLOC(ctx, buf, count) MH_CUDA(ctx, (buf).alloc(count))
+
+// Tensor-core batched contraction (contract_tc.cu): one launch over chunks of up to 128 tasks of
+// one operator each; products to temp[task][R] or, with task_dst, straight to the destinations.
+struct tc_launch {
+    const float* img = nullptr;          // operator images (head, tail) in the tensor-core layout
+    const int64_t* img_off = nullptr;    // per operator: offset of its image (floats)
+    const int32_t* kpad = nullptr;       // per operator: columns rounded up to 8
+    const int32_t* op_C = nullptr;       // per operator: columns
+    const int32_t* chunk_op = nullptr;
+    const int32_t* chunk_t0 = nullptr;   // n_chunks + 1 entries
+    int64_t n_chunks = 0;
+    const int64_t* task_src = nullptr;
+    const float* src = nullptr;
+    int R = 0, npad = 0, kmax = 0;
+    float* temp = nullptr;
+    const int64_t* task_dst = nullptr;
+    int accumulate = 0;
+    void* dst = nullptr;
+    bool dst_double = false;
+    int* err = nullptr;                  // set when a bounded wait gave up
+};
+int tc_pad_rows(int R);
+int tc_pad_cols(int C);
+void tc_operator_image(const double* op, int R, int C, int npad, int kpad, float* out);
+size_t tc_smem_bytes(int npad, int kmax);
+mh_status tc_prepare(mh_ctx* ctx);
+mh_status tc_contract_launch(mh_ctx* ctx, const tc_launch& a);
 
 // Device-resident state of the sync-free GMRES (gmres_run_graph): every kernel of its fixed
 // schedule reads the flags at entry and returns at once when its work is not needed.

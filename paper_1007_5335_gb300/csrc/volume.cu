@@ -23,6 +23,7 @@
 #include <array>
 #include <cmath>
 #include <complex>
+#include <cstring>
 #include <map>
 #include <memory>
 #include <tuple>
@@ -533,6 +534,26 @@ struct Phase {
     int smem = 0;
     dbuf<int32_t> chunk_op, chunk_t0, dst_ptr, dst_task;
     dbuf<int64_t> task_src, dst_off;
+    // binary32 form on the tensor cores: the tasks of operators with at least TC_MIN_TASKS tasks
+    // in chunks of up to 128 (k_contract_tc), the others in the CUDA-core chunks ("rest");
+    // both write the same products, the reduction is shared
+    int64_t n_tc = 0, n_rest = 0, first_rest = 0;   // rest = CUDA-core chunks first_rest.. of chunk_op
+    int tc_npad = 0, tc_kmax = 0;
+    double tc_flops = 0, tc_bytes = 0;   // algorithmic work of the tensor-core launch (binary32 data)
+    std::vector<int> tc_ops;
+    dbuf<int32_t> tc_chunk_op, tc_chunk_t0;
+};
+
+constexpr int TC_MIN_TASKS = 16;   // operators with fewer tasks stay on the CUDA cores
+constexpr int TC_TASKS = 128;      // tasks per tensor-core chunk (rows of the MMA)
+
+// Operator images of the tensor-core path for one operator pool.
+struct TcImages {
+    dbuf<float> img;
+    dbuf<int64_t> off;                 // per operator (-1: no image)
+    dbuf<int32_t> kpad;                // per operator
+    dbuf<int> err;                     // set by a tensor-core launch whose bounded wait gave up
+    bool ready = false;
 };
 
 // A second stream, of the device's highest priority, with fork / join events: the multipole
@@ -627,17 +648,28 @@ struct VolData {
     std::unique_ptr<DfChain> chain;                   // M2M / L2L chains
     int64_t temp_len = 0;
     int64_t n_near_tables = 0;
+    TcImages tc;                                      // tensor-core images (mixed precision)
 };
 
 mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumulate, const std::vector<int>& op_C,
-                      Phase* ph, int64_t* temp_need) {
+                      Phase* ph, int64_t* temp_need, bool tc_ok = true) {
     ph->R = R;
     ph->accumulate = accumulate;
     ph->n_tasks = (int64_t)tasks.size();
-    // sort by operator (stable: keeps the generation order inside an operator)
+    // operators of the tensor-core form: >= TC_MIN_TASKS tasks and at most 64 x 64
+    std::map<int, int64_t> per_op;
+    for (const Task& t : tasks) per_op[t.op] += 1;
+    std::map<int, bool> on_tc;
+    for (auto& kv : per_op) on_tc[kv.first] = tc_ok && R <= 64 && kv.second >= TC_MIN_TASKS && op_C[kv.first] <= 64;
+    // sort by (CUDA-core form, operator), stable: keeps the generation order inside an operator
+    // and puts the tensor-core operators' tasks first, so that both forms cover contiguous
+    // ranges of the sorted tasks (the binary64 form runs over all of them)
     std::vector<int64_t> order(tasks.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int64_t)i;
-    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return tasks[a].op < tasks[b].op; });
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        const bool ra = !on_tc[tasks[a].op], rb = !on_tc[tasks[b].op];
+        return ra != rb ? rb : tasks[a].op < tasks[b].op;
+    });
     std::vector<int64_t> src(tasks.size());
     std::vector<int32_t> cop, ct0;
     int maxC = 1;
@@ -658,6 +690,38 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
     for (size_t c = 0; c < cop.size(); ++c) ph->bytes += 8.0 * R * op_C[cop[c]];   // operator per chunk
     ph->n_chunks = (int64_t)cop.size();
     ct0.push_back((int32_t)order.size());   // end of the last chunk
+    // tensor-core chunks over the leading tasks: ceil(n / 128) nearly equal chunks per
+    // operator; the CUDA-core chunks after them are the tail of the chunk list above
+    std::vector<int32_t> tcop, tct0;
+    int64_t n_tc_tasks = 0;
+    {
+        size_t s = 0;
+        while (s < order.size() && on_tc[tasks[order[s]].op]) {
+            const int op = tasks[order[s]].op;
+            size_t e = s;
+            while (e < order.size() && tasks[order[e]].op == op) ++e;
+            const int64_t n = (int64_t)(e - s);
+            const int64_t nc = (n + TC_TASKS - 1) / TC_TASKS;
+            for (int64_t c = 0; c < nc; ++c) {
+                tcop.push_back(op);
+                tct0.push_back((int32_t)(s + n * c / nc));
+            }
+            // 2 R C flop per task; bytes: the binary32 operator once per chunk, every task's
+            // source vector and product
+            ph->tc_flops += 2.0 * R * op_C[op] * n;
+            ph->tc_bytes += 4.0 * R * op_C[op] * nc + 4.0 * (op_C[op] + R) * n;
+            ph->tc_kmax = std::max(ph->tc_kmax, tc_pad_cols(op_C[op]));
+            ph->tc_ops.push_back(op);
+            s = e;
+        }
+        n_tc_tasks = (int64_t)s;
+    }
+    tct0.push_back((int32_t)n_tc_tasks);
+    ph->n_tc = (int64_t)tcop.size();
+    ph->tc_npad = tc_pad_rows(R);
+    ph->first_rest = 0;
+    while (ph->first_rest < ph->n_chunks && ct0[ph->first_rest] < n_tc_tasks) ++ph->first_rest;
+    ph->n_rest = ph->n_chunks - ph->first_rest;
     // destinations: tasks grouped by destination in generation order
     std::vector<int64_t> rank(tasks.size());
     for (size_t s = 0; s < order.size(); ++s) rank[order[s]] = (int64_t)s;
@@ -698,6 +762,8 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
     };
     MH_TRY(up32(ph->chunk_op, cop));
     MH_TRY(up32(ph->chunk_t0, ct0));
+    MH_TRY(up32(ph->tc_chunk_op, tcop));
+    MH_TRY(up32(ph->tc_chunk_t0, tct0));
     MH_TRY(up32(ph->dst_ptr, dptr));
     MH_TRY(up32(ph->dst_task, dtask));
     MH_TRY(up64(ph->task_src, src));
@@ -712,6 +778,43 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
     return MH_OK;
 }
 
+// Tensor-core images (head / tail split of the binary64 operator) of every operator that one of
+// `phases` runs on the tensor cores.  ops64: the pool's operators (binary64, row-major at off).
+mh_status build_tc_images(mh_ctx* ctx, const double* ops64, const std::vector<int64_t>& off,
+                          const std::vector<int32_t>& R, const std::vector<int32_t>& C,
+                          std::initializer_list<const Phase*> phases, TcImages* T) {
+    std::vector<int64_t> ioff(off.size(), -1);
+    std::vector<int32_t> kp(off.size(), 0);
+    size_t total = 0;
+    for (const Phase* ph : phases)
+        for (int op : ph->tc_ops) {
+            if (ioff[op] >= 0) continue;
+            if (tc_pad_rows(R[op]) != ph->tc_npad)
+                return mh_fail(ctx, MH_ERR_INVALID_ARG, "tensor-core operator rows differ from its phase");
+            ioff[op] = (int64_t)total;
+            kp[op] = tc_pad_cols(C[op]);
+            total += 2 * (size_t)tc_pad_rows(R[op]) * kp[op];
+        }
+    T->ready = total > 0;
+    if (!T->ready) return MH_OK;
+    std::vector<float> img(total);
+    for (size_t op = 0; op < off.size(); ++op)
+        if (ioff[op] >= 0)
+            tc_operator_image(ops64 + off[op], R[op], C[op], tc_pad_rows(R[op]), kp[op], img.data() + ioff[op]);
+    cudaStream_t st = ctx->stream;
+    MH_ALLOC(ctx, T->img, total);
+    MH_ALLOC(ctx, T->off, off.size());
+    MH_ALLOC(ctx, T->kpad, off.size());
+    MH_ALLOC(ctx, T->err, 1);
+    MH_CUDA(ctx, cudaMemcpyAsync(T->img.p, img.data(), total * 4, cudaMemcpyHostToDevice, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(T->off.p, ioff.data(), ioff.size() * 8, cudaMemcpyHostToDevice, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(T->kpad.p, kp.data(), kp.size() * 4, cudaMemcpyHostToDevice, st));
+    MH_CUDA(ctx, cudaMemsetAsync(T->err.p, 0, sizeof(int), st));
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
+    MH_TRY(tc_prepare(ctx));
+    return MH_OK;
+}
+
 // Expansion pool of the operators' precision: binary64 uses the main pool itself, binary32 its
 // float mirror (same layout).
 template <typename TOP>
@@ -723,27 +826,63 @@ inline float* typed_pool<float>(dbuf<double>&, dbuf<float>& v32) { return v32.p;
 
 template <typename TOP>
 mh_status run_phase_on(mh_ctx* ctx, const TOP* ops, const int64_t* op_off, const int32_t* op_C, TOP* pool,
-                       double* out, double* temp, const Phase* ph, const char* region) {
+                       double* out, double* temp, const Phase* ph, const char* region,
+                       const TcImages* tc = nullptr) {
     if (ph->n_tasks == 0) return MH_OK;
     const int smem = (int)(ph->smem / sizeof(double) * sizeof(TOP));
+    // binary32 with images: the leading operators on the tensor cores, the rest on the CUDA cores
+    const bool on_tc = sizeof(TOP) == 4 && tc && tc->ready && ctx->tensor_cores && ph->n_tc > 0;
     prof_scope ps(ctx, region, ph->flops, ph->bytes + 8.0 * ph->R * ph->n_dst * (ph->accumulate ? 2 : 1));
     TOP* tmp = reinterpret_cast<TOP*>(temp);   // sized in binary64 words: room for either type
     const int acc = ph->accumulate ? 1 : 0;
     const int64_t* tdst = ph->direct ? ph->task_dst.p : nullptr;
     const unsigned rg = (unsigned)mh_grid(ph->n_dst * 32, 256);
+    const int64_t c0 = on_tc ? ph->first_rest : 0;          // first CUDA-core chunk
+    const unsigned ncc = (unsigned)(ph->n_chunks - c0);     // CUDA-core chunks
+    if (on_tc) {
+        tc_launch a;
+        a.img = tc->img.p;
+        a.img_off = tc->off.p;
+        a.kpad = tc->kpad.p;
+        a.op_C = op_C;
+        a.chunk_op = ph->tc_chunk_op.p;
+        a.chunk_t0 = ph->tc_chunk_t0.p;
+        a.n_chunks = ph->n_tc;
+        a.task_src = ph->task_src.p;
+        a.src = reinterpret_cast<const float*>(pool);
+        a.R = ph->R;
+        a.npad = ph->tc_npad;
+        a.kmax = ph->tc_kmax;
+        a.temp = reinterpret_cast<float*>(temp);
+        a.task_dst = tdst;
+        a.accumulate = acc;
+        a.dst = ph->dst_out ? static_cast<void*>(out) : static_cast<void*>(pool);
+        a.dst_double = ph->dst_out;
+        a.err = tc->err.p;
+        // the tensor-core launch alone is also timed in "<region>_tc"
+        prof_scope pt(ctx, std::strcmp(region, "volume_contract") == 0 ? "volume_contract_tc" : "dlp_fmm_contract_tc",
+                      ph->tc_flops, ph->tc_bytes);
+        MH_TRY(tc_contract_launch(ctx, a));
+    }
     if (ph->dst_out) {
-        k_apply<TOP, double><<<(unsigned)ph->n_chunks, 256, smem, ctx->stream>>>(
-            ops, op_off, op_C, ph->chunk_op.p, ph->chunk_t0.p, ph->task_src.p, pool, ph->R, tmp, tdst, acc, out);
-        MH_LAUNCHED(ctx);
+        if (ncc) {
+            k_apply<TOP, double><<<ncc, 256, smem, ctx->stream>>>(ops, op_off, op_C, ph->chunk_op.p + c0,
+                                                                  ph->chunk_t0.p + c0, ph->task_src.p, pool, ph->R,
+                                                                  tmp, tdst, acc, out);
+            MH_LAUNCHED(ctx);
+        }
         if (!ph->direct) {
             k_reduce<TOP, double><<<rg, 256, 0, ctx->stream>>>(tmp, ph->R, ph->dst_off.p, ph->dst_ptr.p,
                                                                ph->dst_task.p, ph->n_dst, acc, out);
             MH_LAUNCHED(ctx);
         }
     } else {
-        k_apply<TOP, TOP><<<(unsigned)ph->n_chunks, 256, smem, ctx->stream>>>(
-            ops, op_off, op_C, ph->chunk_op.p, ph->chunk_t0.p, ph->task_src.p, pool, ph->R, tmp, tdst, acc, pool);
-        MH_LAUNCHED(ctx);
+        if (ncc) {
+            k_apply<TOP, TOP><<<ncc, 256, smem, ctx->stream>>>(ops, op_off, op_C, ph->chunk_op.p + c0,
+                                                               ph->chunk_t0.p + c0, ph->task_src.p, pool, ph->R, tmp,
+                                                               tdst, acc, pool);
+            MH_LAUNCHED(ctx);
+        }
         if (!ph->direct) {
             k_reduce<TOP, TOP><<<rg, 256, 0, ctx->stream>>>(tmp, ph->R, ph->dst_off.p, ph->dst_ptr.p,
                                                             ph->dst_task.p, ph->n_dst, acc, pool);
@@ -779,7 +918,7 @@ mh_status run_chain(mh_ctx* ctx, const DfChain* ch, int P, int64_t m_base, int64
 template <typename TOP>
 mh_status run_phase(mh_ctx* ctx, VolData* V, const TOP* ops, const Phase* ph) {
     return run_phase_on<TOP>(ctx, ops, V->d_op_off.p, V->d_op_C.p, typed_pool<TOP>(V->vec, V->vec32), V->vec.p,
-                             V->temp.p, ph, "volume_contract");
+                             V->temp.p, ph, "volume_contract", &V->tc);
 }
 
 struct HostTree {
@@ -1219,11 +1358,13 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
         MH_CUDA(ctx, cudaStreamSynchronize(st));
     }
     MH_ALLOC(ctx, V->ops32, total);
+    // every operator in binary64 on the host (the near tables were formed on the device): source
+    // of the binary32 copy and of the tensor-core images
+    std::vector<double> all(total);
+    MH_CUDA(ctx, cudaMemcpyAsync(all.data(), V->ops64.p, total * 8, cudaMemcpyDeviceToHost, st));
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
     {
         // binary32 copy of every operator (mixed precision)
-        std::vector<double> all(total);
-        MH_CUDA(ctx, cudaMemcpyAsync(all.data(), V->ops64.p, total * 8, cudaMemcpyDeviceToHost, st));
-        MH_CUDA(ctx, cudaStreamSynchronize(st));
         std::vector<float> f(all.begin(), all.end());
         MH_CUDA(ctx, cudaMemcpyAsync(V->ops32.p, f.data(), total * 4, cudaMemcpyHostToDevice, st));
         MH_CUDA(ctx, cudaStreamSynchronize(st));
@@ -1252,6 +1393,12 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
     V->out.reset(new Phase());
     MH_TRY(build_phase(ctx, t_out, qq, true, V->op_C, V->out.get(), &need));
     V->out->dst_out = true;
+    {
+        std::vector<int64_t> off(pool.off.begin(), pool.off.end());
+        std::vector<int32_t> rr(pool.R.begin(), pool.R.end()), cc(pool.C.begin(), pool.C.end());
+        MH_TRY(build_tc_images(ctx, all.data(), off, rr, cc, {V->p2m.get(), V->m2l.get(), V->near.get(), V->out.get()},
+                               &V->tc));
+    }
     MH_ALLOC(ctx, V->vec, V->vec_len);
     MH_ALLOC(ctx, V->vec32, V->vec_len);
     MH_ALLOC(ctx, V->temp, need);
@@ -1441,6 +1588,7 @@ struct DipData {
     dbuf<int32_t> d_op_C;
     std::unique_ptr<Phase> p2m, m2l, out;
     SideStream side;                       // the near field runs there beside the passes
+    TcImages tc;                           // tensor-core images (mixed precision)
 };
 }  // namespace
 
@@ -1722,6 +1870,11 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
     D->out.reset(new Phase());
     MH_TRY(build_phase(ctx, t_out, qq, !near_blocks, opC, D->out.get(), &need));
     D->out->dst_out = true;
+    {
+        std::vector<int64_t> off(pool.off.begin(), pool.off.end());
+        std::vector<int32_t> rr(pool.R.begin(), pool.R.end()), cc(pool.C.begin(), pool.C.end());
+        MH_TRY(build_tc_images(ctx, pool.data.data(), off, rr, cc, {D->p2m.get(), D->m2l.get(), D->out.get()}, &D->tc));
+    }
     MH_ALLOC(ctx, D->vec, D->vec_len);
     MH_ALLOC(ctx, D->vec32, D->vec_len);
     MH_ALLOC(ctx, D->temp, need);
@@ -1738,7 +1891,7 @@ static mh_status dipole_passes(mh_ctx* ctx, VolData* V, DipData* D, const TOP* o
     TOP* pool = typed_pool<TOP>(D->vec, D->vec32);
     auto run = [&](const Phase* ph) {
         return run_phase_on<TOP>(ctx, ops, D->d_op_off.p, D->d_op_C.p, pool, D->vec.p, D->temp.p, ph,
-                                 "dlp_fmm_contract");
+                                 "dlp_fmm_contract", &D->tc);
     };
     MH_TRY(run(D->p2m.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, pool, true, "dlp_fmm_chain"));
@@ -1750,7 +1903,7 @@ static mh_status dipole_passes(mh_ctx* ctx, VolData* V, DipData* D, const TOP* o
 template <typename TOP>
 static mh_status dipole_out(mh_ctx* ctx, DipData* D, const TOP* ops) {
     return run_phase_on<TOP>(ctx, ops, D->d_op_off.p, D->d_op_C.p, typed_pool<TOP>(D->vec, D->vec32), D->vec.p,
-                             D->temp.p, D->out.get(), "dlp_fmm_contract");
+                             D->temp.p, D->out.get(), "dlp_fmm_contract", &D->tc);
 }
 
 // w_sorted: dipole strengths in the leaf-sorted order given to volume_dipole_setup.
@@ -1873,7 +2026,7 @@ static mh_status volume_run(mh_ctx* ctx, mh_tree* t, VolData* V, const TOP* ops)
     }
     if (near)
         MH_TRY(run_phase_on<TOP>(ctx, ops, V->d_op_off.p, V->d_op_C.p, pool, V->vec.p, V->temp_near.p,
-                                 V->near.get(), "volume_contract"));
+                                 V->near.get(), "volume_contract", &V->tc));
     if (fork)
         MH_CUDA(ctx, cudaStreamWaitEvent(main, V->side.join, 0));
     else
@@ -1911,12 +2064,32 @@ mh_status volume_apply(mh_ctx* ctx, mh_tree* t, double alpha, int p, const doubl
     return MH_OK;
 }
 
+extern "C" mh_status mh_tree_check(mh_ctx* ctx, mh_tree* t) {
+    if (!ctx || !t) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    VolData* V = static_cast<VolData*>(t->vol);
+    if (!V) return MH_OK;
+    int code = 0;
+    for (TcImages* T : {&V->tc, V->dip ? &V->dip->tc : static_cast<TcImages*>(nullptr)}) {
+        if (!T || !T->err.p) continue;
+        int e = 0;
+        MH_CUDA(ctx, cudaMemcpy(&e, T->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            code = e;
+            MH_CUDA(ctx, cudaMemset(T->err.p, 0, sizeof(int)));
+        }
+    }
+    if (code)
+        return mh_fail(ctx, MH_ERR_TIMEOUT, "a tensor-core contraction gave up waiting for its %s",
+                       code == 1 ? "operator copy" : "matrix products");
+    return MH_OK;
+}
+
 extern "C" mh_status mh_volume_potential(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* b_dev,
                                          double* up_dev, mh_precision prec) {
     if (!ctx || !t || !b_dev || !up_dev) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
     if (!(alpha > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "alpha must be positive");
     if (p < 1 || p > 40) return mh_fail(ctx, MH_ERR_INVALID_ARG, "p must be in 1..40");
     MH_TRY(volume_apply(ctx, t, alpha, p, b_dev, up_dev, prec));
-    MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return MH_OK;
+    return mh_tree_check(ctx, t);
 }
