@@ -2673,7 +2673,8 @@ mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_
 }
 
 mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* tg, const double* sigma,
-                                const double* main_vals, double* out, mh_precision prec, bool fine_in_fmm) {
+                                const double* main_vals, double* out, mh_precision prec, bool fine_in_fmm,
+                                const double* asig_given) {
     cudaStream_t st = ctx->stream;
     const double pref = -1.0 / (2.0 * MH_PI * alpha * alpha);
     const double pref32 = pref / (alpha * alpha);
@@ -2757,9 +2758,15 @@ mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_t
         }
     }
     if (tg->n_line) {
-        MH_TRY(bie_apply(ctx, b, sigma, tg->asig.p, prec));
+        // the interior limit needs A sigma; a caller that holds the residual r = rhs - A sigma
+        // of this density passes A sigma = rhs - r instead of a product with the operator
+        const double* asig = asig_given;
+        if (!asig) {
+            MH_TRY(bie_apply(ctx, b, sigma, tg->asig.p, prec));
+            asig = tg->asig.p;
+        }
         k_dlp_line<<<mh_grid(tg->n_line * 32, 256), 256, 0, st>>>(tg->line_tgt.p, tg->line_curve.p, tg->line_data.p,
-                                                                  tg->n_line, tg->asig.p, b->d_nn.p, b->d_off.p,
+                                                                  tg->n_line, asig, b->d_nn.p, b->d_off.p,
                                                                   tg->line_w.p, tg->line_woff.p, tg->n, alpha,
                                                                   ext.p);
         MH_LAUNCHED(ctx);

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
     const int32_t* __restrict__ op_C, const int32_t* __restrict__ chunk_op, const int32_t* __restrict__ chunk_t0,
     const int64_t* __restrict__ task_src, const float* src, int R, int npad, int kmax, float* __restrict__ temp,
     const int64_t* __restrict__ task_dst, int accumulate, TD* dst, int* err) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     // 1024-byte aligned base (the dynamic allocation is padded by 1 KB for this)
     unsigned char* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     const int a_bytes = TC_M * kmax * 4;        // one source image (head or tail)
@@ -312,19 +312,30 @@ void tc_operator_image(const double* op, int R, int C, int npad, int kpad, float
 
 size_t tc_smem_bytes(int npad, int kmax) { return (size_t)(2 * TC_M + 2 * npad) * kmax * 4 + 1024; }
 
+// Largest operator of the tensor-core form: 64 x 64 (R, C <= 64).
+static const size_t TC_SMEM_MAX = tc_smem_bytes(64, 64);
+
 mh_status tc_prepare(mh_ctx* ctx) {
     static bool done[64] = {};
     if (ctx->device >= 0 && ctx->device < 64 && done[ctx->device]) return MH_OK;
-    const int lim = 227 * 1024;
-    MH_CUDA(ctx, cudaFuncSetAttribute(k_contract_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    MH_CUDA(ctx, cudaFuncSetAttribute(k_contract_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    int optin = 0;
+    MH_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    cudaFuncAttributes fa{};
+    MH_CUDA(ctx, cudaFuncGetAttributes(&fa, k_contract_tc<float>));
+    if ((size_t)optin < TC_SMEM_MAX + fa.sharedSizeBytes)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "device shared memory (%d B per block) too small for the tensor-core "
+                       "contraction (%zu B)", optin, TC_SMEM_MAX + fa.sharedSizeBytes);
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_contract_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)TC_SMEM_MAX));
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_contract_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)TC_SMEM_MAX));
     if (ctx->device >= 0 && ctx->device < 64) done[ctx->device] = true;
     return MH_OK;
 }
 
 mh_status tc_contract_launch(mh_ctx* ctx, const tc_launch& a) {
     const size_t smem = tc_smem_bytes(a.npad, a.kmax);
-    if (smem > 227 * 1024 || a.npad > 128 || a.kmax > 64)
+    if (smem > TC_SMEM_MAX || a.npad > 64 || a.kmax > 64)
         return mh_fail(ctx, MH_ERR_INVALID_ARG, "tensor-core contraction too large (%d x %d)", a.npad, a.kmax);
     if (a.n_chunks == 0) return MH_OK;
     if (a.dst_double)

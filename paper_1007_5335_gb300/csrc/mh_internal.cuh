@@ -326,7 +326,8 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
 // nodes went through the multipole method), so only the auxiliary points of the
 // normal-line rule need near-boundary work.  Requires dlp_fine_weights for this sigma.
 mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* tg, const double* sigma,
-                                const double* main_vals, double* out, mh_precision prec, bool fine_in_fmm);
+                                const double* main_vals, double* out, mh_precision prec, bool fine_in_fmm,
+                                const double* asig_given = nullptr);
 // Density on the 16x fine grid times |y'| h_f (binary64 in b->wf64; binary32 also in b->wf32
 // when prec is mixed).
 mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_precision prec);

@@ -296,6 +296,12 @@ static mh_status start_residual(mh_ctx* ctx, ProblemImpl* P, const double* sigma
     return MH_OK;
 }
 
+__global__ void k_rhs_minus_r(const double* __restrict__ rhs, const double* __restrict__ r, int64_t n,
+                              double* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = rhs[i] - r[i];
+}
+
 // Everything after the right-hand side B (P->B) has been formed.
 static mh_status step_solve(mh_ctx* ctx, ProblemImpl* P, const double* f_next_dev, double* u_next_dev,
                             double* sigma_dev, double gmres_tol, mh_precision prec, mh_step_info* info) {
@@ -363,7 +369,14 @@ static mh_status step_solve(mh_ctx* ctx, ProblemImpl* P, const double* f_next_de
         k_gather<<<mh_grid(P->n_inside, 256), 256, 0, st>>>(du, P->inside_idx.p, P->n_inside, P->Uh.p);
         MH_LAUNCHED(ctx);
     }
-    MH_TRY(dlp_evaluate_fmm_tail(ctx, b, P->alpha, &P->tg, sigma_dev, P->Uh.p, P->Uh.p, prec, true));
+    // A sigma for the normal-line rule from the solver's final residual r = rhs - A sigma
+    // (binary64, or float-float on A32 + A32lo): rhs - r, no operator product
+    if (P->tg.n_line) {
+        k_rhs_minus_r<<<mh_grid(ng, 256), 256, 0, st>>>(P->rhs.p, P->rc_r.p, ng, P->tg.asig.p);
+        MH_LAUNCHED(ctx);
+    }
+    MH_TRY(dlp_evaluate_fmm_tail(ctx, b, P->alpha, &P->tg, sigma_dev, P->Uh.p, P->Uh.p, prec, true,
+                                 P->tg.n_line ? P->tg.asig.p : nullptr));
     k_combine<<<mh_grid(n, 256), 256, 0, st>>>(P->Up.p, P->Uh.p, P->region.p, P->slot.p, P->d_ext_const.p,
                                                P->ext_mode, n, u_next_dev);
     MH_LAUNCHED(ctx);
