@@ -603,53 +603,65 @@ def prob_inside(prob):
 
 
 def cpu_baseline(wl, budget_s=20.0, seed=11):
-    """The oracle as it stands, on a bounded sample of one step of the workload: the
-    volume potential and the double layer at sampled nodes, and sampled rows of the
-    Nystrom matrix; extrapolated to one full step (N_D targets, N_Gamma rows, dense solve)."""
-    from oracle import bie, geometry as G, tree as T, volume as V
+    """The oracle as it stands, on all host cores, on a bounded sample of one step of the
+    workload: the volume potential and the double layer at sampled interior nodes and sampled
+    rows of the Nystrom matrix, each spread over a pool of worker processes (one per core; the
+    per-target and per-row loops are independent), and one dense solve (BLAS threads).  The
+    wall time per target / row with every core busy, extrapolated to one full step (N_D
+    targets, N_Gamma rows, the solve), gives points * steps / s."""
+    from oracle import bie, geometry as G, pool, tree as T
     t_start = time.time()
-    curves = G.make_curves(wl.curves)
-    tr = T.build(wl.box, wl.q, wl.min_level, wl.max_level, wl.forcing, wl.refine_tol)
-    nodes = tr.nodes()
-    leaves = tr.leaf_array()
     rng = np.random.default_rng(seed)
-    B = wl.forcing(nodes) * wl.dt
-    ntot = nodes.shape[0]
-    # per-target volume potential cost
-    t0 = time.time()
-    nv = 0
-    while time.time() - t0 < 0.45 * budget_s and nv < 64:
-        i = rng.integers(ntot)
-        V.volume_potential(leaves, B.reshape(len(leaves), -1), wl.q, wl.alpha, nodes[i:i + 1])
-        nv += 1
-    t_vol = (time.time() - t0) / nv
-    # per-row Nystrom assembly cost
-    t0 = time.time()
-    rows = np.sort(rng.choice(sum(c.n for c in curves), 16, replace=False))
-    R = bie.nystrom_matrix(curves, wl.alpha, rows=rows)
-    t_row = (time.time() - t0) / len(rows)
-    # dense solve cost (LU of an N_Gamma x N_Gamma matrix)
-    n = R.shape[1]
-    M = np.eye(n) + 1e-3 * rng.standard_normal((n, n))
-    t0 = time.time()
-    np.linalg.solve(M, rng.standard_normal(n))
-    t_solve = time.time() - t0
-    # per-target double-layer cost
-    sig = rng.standard_normal(n)
-    inside = [i for i in rng.choice(ntot, 64, replace=False)]
-    info = G.classify(curves, nodes[inside])
-    ins = [k for k, i in enumerate(inside) if info.region[k] == -1][:16]
-    t0 = time.time()
-    sub = G.classify(curves, nodes[[inside[k] for k in ins]])
-    bie.dlp_eval(curves, sig, wl.alpha, nodes[[inside[k] for k in ins]], sub, None)
-    t_dlp = (time.time() - t0) / max(len(ins), 1)
+    with pool.Workers() as wk:
+        cores = wk.n
+        tr = T.build(wl.box, wl.q, wl.min_level, wl.max_level, wl.forcing, wl.refine_tol)
+        nodes = tr.nodes()
+        leaves = tr.leaf_array()
+        B = (wl.forcing(nodes) * wl.dt).reshape(len(leaves), -1)
+        ntot = nodes.shape[0]
+        n = sum(c.shape[0] for c in wl.curves)
+
+        def timed(fn, per_worker):
+            """Marginal wall time per item with every worker busy: batches of k and 3k items per
+            worker (k = per_worker); the difference removes the per-call costs (pickling, and in
+            the double layer the upsampling of the curves that every call redoes), which a full
+            step pays once per worker, not per item."""
+            t = []
+            for k in (per_worker, 3 * per_worker):
+                t0 = time.time()
+                fn(k * cores)
+                t.append(time.time() - t0)
+            n1, n3 = per_worker * cores, 3 * per_worker * cores
+            return max((t[1] - t[0]) / (n3 - n1), 0.1 * t[1] / n3), n1 + n3
+
+        scale = max(0.25, budget_s / 20.0)
+        t_vol, nv = timed(lambda k: wk.volume_potential(leaves, B, wl.q, wl.alpha,
+                                                        nodes[rng.choice(ntot, k, replace=False)]),
+                          max(1, int(2 * scale)))
+        wk.nystrom_rows(wl.curves, wl.alpha, np.arange(cores))     # workers build the curves once
+        t_row, nr = timed(lambda k: wk.nystrom_rows(wl.curves, wl.alpha, np.sort(rng.choice(n, k, replace=False))),
+                          max(1, int(8 * scale)))
+        curves = G.make_curves(wl.curves)
+        cand = nodes[rng.choice(ntot, 64 * cores, replace=False)]
+        info = G.classify(curves, cand)
+        inside = cand[[i for i in range(len(cand)) if info.region[i] == -1 and all(
+            p is None or p["d"] >= bie.NEAR_LINE * p["hs"] for p in info.proj[i])]]
+        sig = rng.standard_normal(n)
+        pos = [0]
+
+        def dl(k):
+            wk.dlp_eval(wl.curves, sig, wl.alpha, inside[pos[0]:pos[0] + k])
+            pos[0] += k
+        t_dlp, nd = timed(dl, max(1, min(int(2 * scale), len(inside) // (4 * cores))))
+        M = np.eye(n) + 1e-3 * rng.standard_normal((n, n))
+        t0 = time.time()
+        np.linalg.solve(M, rng.standard_normal(n))
+        t_solve = time.time() - t0
     t_step = ntot * (t_vol + t_dlp) + n * t_row + t_solve
-    # the oracle's per-target loops run in one thread; only the dense solve uses BLAS threads
-    blas = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": (ntot + n) / t_step, "unit": "points*timesteps/s", "cores": 1, "blas_threads": blas,
-            "kind": "oracle",
-            "sample": f"{nv} volume targets, {len(ins)} double-layer targets, {len(rows)} Nystrom rows, one "
-                      f"{n}x{n} dense solve; extrapolated to one step ({ntot} targets, {n} rows)",
+    return {"value": (ntot + n) / t_step, "unit": "points*timesteps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nv} volume targets, {nd} double-layer targets, {nr} Nystrom rows (each set spread over "
+                      f"{cores} worker processes), one {n}x{n} dense solve; marginal wall time per item with all "
+                      f"cores busy, extrapolated to one step ({ntot} targets, {n} rows)",
             "seconds_per_step_extrapolated": t_step, "wall_s": time.time() - t_start}
 
 

@@ -44,10 +44,22 @@ def _vol_pot(a):
     return volume.volume_potential(leaves, B, q, alpha, targets)
 
 
+_CURVES = {}   # per worker: curves already built from the same node arrays
+
+
+def _curves(curve_nodes):
+    from . import geometry
+    key = tuple((len(c), np.asarray(c).tobytes().__hash__()) for c in curve_nodes)
+    if key not in _CURVES:
+        _CURVES.clear()
+        _CURVES[key] = geometry.make_curves(curve_nodes)
+    return _CURVES[key]
+
+
 def _nys_rows(a):
-    from . import bie, geometry
+    from . import bie
     curve_nodes, alpha, order, rows = a
-    return bie.nystrom_matrix(geometry.make_curves(curve_nodes), alpha, order, rows=rows)
+    return bie.nystrom_matrix(_curves(curve_nodes), alpha, order, rows=rows)
 
 
 def volume_rows(leaves, q, alpha, targets, procs=None):
@@ -74,3 +86,55 @@ def nystrom_matrix(curve_nodes, alpha, alpert_order=8, rows=None, procs=None):
     parts = _run(_nys_rows, [(curve_nodes, alpha, alpert_order, rows[c])
                              for c in _chunks(len(rows), procs or cores())], procs)
     return np.vstack(parts)
+
+
+def _dlp(a):
+    from . import bie, geometry
+    curve_nodes, sigma, alpha, targets = a
+    curves = _curves(curve_nodes)
+    return bie.dlp_eval(curves, sigma, alpha, targets, geometry.classify(curves, targets), None)
+
+
+def _ready(_):
+    from . import bie, geometry, volume  # noqa: F401  (import the oracle once per worker)
+    return 0
+
+
+class Workers:
+    """A spawn pool kept for several calls (each worker imports the oracle once), for timing
+    the oracle on all cores: every method cuts its targets / rows into one chunk per worker
+    and returns the serial function's values in order."""
+
+    def __init__(self, procs=None):
+        self.n = procs or cores()
+        self.pool = mp.get_context("spawn").Pool(self.n)
+        self.pool.map(_ready, range(self.n))
+
+    def _map(self, fn, args):
+        return self.pool.map(fn, args)
+
+    def volume_potential(self, leaves, B, q, alpha, targets):
+        targets = np.asarray(targets, dtype=np.float64)
+        return np.concatenate(self._map(_vol_pot, [(leaves, B, q, alpha, targets[c])
+                                                   for c in _chunks(len(targets), self.n)]))
+
+    def nystrom_rows(self, curve_nodes, alpha, rows, alpert_order=8):
+        rows = np.asarray(rows)
+        return np.vstack(self._map(_nys_rows, [(curve_nodes, alpha, alpert_order, rows[c])
+                                               for c in _chunks(len(rows), self.n)]))
+
+    def dlp_eval(self, curve_nodes, sigma, alpha, targets):
+        """U^h at targets inside Omega (classification in the workers; no normal-line targets)."""
+        targets = np.asarray(targets, dtype=np.float64)
+        return np.concatenate(self._map(_dlp, [(curve_nodes, sigma, alpha, targets[c])
+                                               for c in _chunks(len(targets), self.n)]))
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -9,20 +9,22 @@
 //     D[m][n] = sum_k X[m][k] T[n][k],   m = task in the chunk (M = 128), n = output row
 //     (N = R rounded up to 16), k = input column (K = C rounded up to 8),
 //
-// with tcgen05.mma kind::tf32 (binary32 accumulation in tensor memory).  TF32 keeps 11
-// significant bits, so every operand is split into a TF32 head and a TF32 tail (head = the
-// value rounded to TF32, tail = the remainder rounded to TF32) and the product is formed as
-//     X T ~ Xh Th + Xh Tt + Xt Th
-// (three MMAs per K step into one accumulator): the dropped term Xt Tt and the tail roundings
-// are ~2^-22 of |X||T| per product, close to binary32 arithmetic.  The operator's head and
-// tail are split once at set-up from the binary64 operator and stored in the exact shared-memory
-// image the MMA reads, so a CTA stages it with one bulk copy; the sources are gathered,
-// split and written into their image by all threads.
+// with tcgen05.mma kind::f16 on bfloat16 operands (binary32 accumulation in tensor memory).
+// Every binary32 operand is split exactly into three bfloat16 parts, x = x1 + x2 + x3
+// (x1 = x rounded to bfloat16, x2 = the remainder rounded, x3 = what is left; 3 x 8
+// significant bits hold all 24 of binary32), and the product is formed as
+//     X T ~ X1 T1 + X1 T2 + X2 T1 + X1 T3 + X2 T2 + X3 T1
+// (six MMAs per K step into one accumulator); the dropped terms X2 T3, X3 T2, X3 T3 are at most
+// 2^-23 |X||T| per product, the size of binary32 rounding.  The operator's three parts are
+// split once at set-up from the binary64 operator and stored in the exact shared-memory image
+// the MMA reads, so a CTA stages it with one bulk copy; the sources are gathered, split and
+// written into their images by all threads.
 //
 // Shared-memory images use the no-swizzle K-major layout of the tensor cores: core matrices of
-// 8 rows x 16 bytes (8 x 4 TF32), row r of a core matrix at byte 16 r; the core matrix of rows
-// 8g..8g+7 and columns 4c..4c+3 starts at byte c * LBO + g * 128 (SBO = 128 between row groups,
-// LBO = rows * 16 between column groups).  One MMA consumes K = 8 columns (two column groups).
+// 8 rows x 16 bytes (8 x 8 bfloat16), row r of a core matrix at byte 16 r; the core matrix of
+// rows 8g..8g+7 and columns 8c..8c+7 starts at byte c * LBO + g * 128 (SBO = 128 between row
+// groups, LBO = rows * 16 between column groups).  One MMA consumes K = 16 columns (two column
+// groups).
 //
 // Products leave tensor memory through tcgen05.ld (warp w reads lanes 32 (w % 4) .. + 31, i.e.
 // tasks, and half w / 4 of the columns) and are written to the task-indexed product buffer
@@ -30,6 +32,8 @@
 // straight to the destination.  Every wait on an mbarrier is bounded; a wait that gives up sets
 // the error word, skips the rest of the work, waits (bounded) for its bulk copy and frees the
 // tensor memory it holds.
+#include <cuda_bf16.h>
+
 #include <cstring>
 
 #include "mh_internal.cuh"
@@ -51,16 +55,16 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor of kind::tf32: D binary32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
-// 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-__device__ __forceinline__ uint32_t instr_desc_tf32(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor of kind::f16: D binary32 (bits 4-5 = 1), A and B bfloat16 (bits 7-9
+// and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__device__ __forceinline__ uint32_t instr_desc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
@@ -107,40 +111,44 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Round to TF32 (nearest, ties away from zero): the result is a binary32 value with the low 13
-// mantissa bits zero.
-__device__ __forceinline__ float to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+// Exact split of a binary32 value into three bfloat16 parts (round to nearest even each time):
+// x = p0 + p1 + p2 for every finite x whose parts stay in the normal range.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
+    p0 = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(p0);
+    p1 = __float2bfloat16_rn(r1);
+    p2 = __float2bfloat16_rn(r1 - __bfloat162float(p1));
 }
 
-// Byte offset of element (row, k) in a no-swizzle K-major image with `rows` rows.
-__device__ __forceinline__ uint32_t img_off(int row, int k, int rows) {
-    return (uint32_t)((k >> 2) * (rows * 16) + (row >> 3) * 128 + (row & 7) * 16 + (k & 3) * 4);
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// Byte offset of element (row, k) in a no-swizzle K-major bfloat16 image with `rows` rows.
+__host__ __device__ __forceinline__ uint32_t img_off(int row, int k, int rows) {
+    return (uint32_t)((k >> 3) * (rows * 16) + (row >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
 // One CTA per chunk of up to 128 tasks of one operator (see the file comment).
-//   img: operator images (head then tail, each npad x kpad binary32 in the layout above) at
-//        img_off[op] (floats); kpad[op]: the operator's K extent (C rounded up to 8);
-//   op_C[op]: its columns C; R: rows (outputs) of every operator of the phase, npad = R
-//   rounded up to 16; kmax: the largest kpad of the phase (sizes the source images);
+//   img: operator images (parts 1, 2, 3, each npad x kpad bfloat16 in the layout above) at
+//        img_off_op[op] (bfloat16 elements); kpad[op]: the operator's K extent (C rounded up to
+//        16); op_C[op]: its columns C; R: rows (outputs) of every operator of the phase, npad =
+//        R rounded up to 16; kmax: the largest kpad of the phase (sizes the source images);
 //   src: binary32 pool (sources at task_src[t]); temp: products [task][R] unless task_dst is
 //   given, then the products go to dst[task_dst[t] + r] (added when accumulate is set; TD =
 //   float for the expansion pool, double for the potentials).
 template <typename TD>
 __global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
-    const float* __restrict__ img, const int64_t* __restrict__ img_off_op, const int32_t* __restrict__ kpad_op,
+    const __nv_bfloat16* __restrict__ img, const int64_t* __restrict__ img_off_op, const int32_t* __restrict__ kpad_op,
     const int32_t* __restrict__ op_C, const int32_t* __restrict__ chunk_op, const int32_t* __restrict__ chunk_t0,
     const int64_t* __restrict__ task_src, const float* src, int R, int npad, int kmax, float* __restrict__ temp,
     const int64_t* __restrict__ task_dst, int accumulate, TD* dst, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // 1024-byte aligned base (the dynamic allocation is padded by 1 KB for this)
     unsigned char* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
-    const int a_bytes = TC_M * kmax * 4;        // one source image (head or tail)
-    unsigned char* sAh = base;
-    unsigned char* sAt = sAh + a_bytes;
-    unsigned char* sB = sAt + a_bytes;          // head then tail, 2 * npad * kpad floats
+    const int a_bytes = TC_M * kmax * 2;        // one source image (one part)
+    unsigned char* sA = base;                   // parts 1, 2, 3 of the sources
+    unsigned char* sB = sA + 3 * a_bytes;       // parts 1, 2, 3 of the operator, 3 npad kpad bf16
     __shared__ __align__(8) uint64_t bar_copy, bar_mma;
     __shared__ uint32_t tmem_base;
     __shared__ int ok;
@@ -152,9 +160,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
     const int C = op_C[op];
     const int kp = kpad_op[op];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t ncols = npad <= 32 ? 32u : npad <= 64 ? 64u : 128u;   // power of two >= 32
+    const uint32_t ncols = npad <= 32 ? 32u : 64u;   // power of two >= 32 (npad <= 64)
     const uint32_t mb_copy = smem_addr(&bar_copy), mb_mma = smem_addr(&bar_mma);
-    const uint32_t img_bytes = (uint32_t)(2 * npad * kp * 4);
+    const uint32_t part_b = (uint32_t)(npad * kp * 2);   // bytes of one operator part
 
     if (threadIdx.x == 0) {
         mbar_init(mb_copy, 1);
@@ -175,37 +183,39 @@ __global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
 
     // the operator image: one bulk copy (16-byte aligned source and size)
     if (threadIdx.x == 0) {
-        mbar_expect_tx(mb_copy, img_bytes);
-        bulk_g2s(smem_addr(sB), img + img_off_op[op], img_bytes, mb_copy);
+        mbar_expect_tx(mb_copy, 3 * part_b);
+        bulk_g2s(smem_addr(sB), img + img_off_op[op], 3 * part_b, mb_copy);
     }
-    // the sources: thread -> (row m, column group c); 8 consecutive rows per column group fill
-    // one 128-byte line of the image, so a warp's stores touch 4 lines without bank conflicts
+    // the sources: thread -> (row m, column group c of 8); 8 consecutive rows per column group
+    // fill one 128-byte line of an image, so a warp's stores touch 4 lines without conflicts
     {
-        const int groups = kp >> 2;
+        const int groups = kp >> 3;
         for (int e = threadIdx.x; e < TC_M * groups; e += TC_THREADS) {
             const int m = (e & 7) | ((e >> 3) / groups) << 3;
             const int c = (e >> 3) % groups;
-            float v[4];
+            float v[8];
             if (m < nt) {
-                const float* s = src + task_src[t0 + m];
+                const float* sp = src + task_src[t0 + m] + 8 * c;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = 4 * c + u < C ? s[4 * c + u] : 0.f;
+                for (int u = 0; u < 8; ++u) v[u] = 8 * c + u < C ? sp[u] : 0.f;
             } else {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = 0.f;
+                for (int u = 0; u < 8; ++u) v[u] = 0.f;
             }
-            float4 h, t;
-            h.x = to_tf32(v[0]);
-            h.y = to_tf32(v[1]);
-            h.z = to_tf32(v[2]);
-            h.w = to_tf32(v[3]);
-            t.x = to_tf32(v[0] - h.x);
-            t.y = to_tf32(v[1] - h.y);
-            t.z = to_tf32(v[2] - h.z);
-            t.w = to_tf32(v[3] - h.w);
-            const uint32_t o = img_off(m, 4 * c, TC_M);
-            *reinterpret_cast<float4*>(sAh + o) = h;
-            *reinterpret_cast<float4*>(sAt + o) = t;
+            uint32_t w[3][4];
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+                split3(v[u], a0, a1, a2);
+                split3(v[u + 1], b0, b1, b2);
+                w[0][u >> 1] = pack2(a0, b0);
+                w[1][u >> 1] = pack2(a1, b1);
+                w[2][u >> 1] = pack2(a2, b2);
+            }
+            const uint32_t o = img_off(m, 8 * c, TC_M);
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                *reinterpret_cast<uint4*>(sA + q * a_bytes + o) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
         }
     }
     fence_async_smem();   // the generic-proxy stores above become visible to the tensor cores
@@ -217,15 +227,17 @@ __global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
             atomicExch(err, 1);
         } else {
             tc_after_sync();
-            const uint32_t idesc = instr_desc_tf32(TC_M, npad);
+            const uint32_t idesc = instr_desc_bf16(TC_M, npad);
             const uint32_t a_lbo = TC_M * 16, b_lbo = (uint32_t)npad * 16;
-            const uint32_t ah = smem_addr(sAh), at = smem_addr(sAt);
-            const uint32_t bh = smem_addr(sB), bt = bh + (uint32_t)(npad * kp * 4);
-            for (int ks = 0; ks < kp / 8; ++ks) {
+            const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+            // (source part, operator part) of the six products whose part indices sum to <= 2
+            const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+            for (int ks = 0; ks < kp / 16; ++ks) {
                 const uint32_t da = (uint32_t)ks * 2 * a_lbo, db = (uint32_t)ks * 2 * b_lbo;
-                mma_tf32(tmem, smem_desc(ah + da, a_lbo, 128), smem_desc(bh + db, b_lbo, 128), idesc, ks > 0);
-                mma_tf32(tmem, smem_desc(ah + da, a_lbo, 128), smem_desc(bt + db, b_lbo, 128), idesc, 1);
-                mma_tf32(tmem, smem_desc(at + da, a_lbo, 128), smem_desc(bh + db, b_lbo, 128), idesc, 1);
+#pragma unroll
+                for (int j = 0; j < 6; ++j)
+                    mma_bf16(tmem, smem_desc(a0 + pa[j] * a_bytes + da, a_lbo, 128),
+                             smem_desc(b0 + pb[j] * part_b + db, b_lbo, 128), idesc, (ks | j) != 0);
             }
             mma_commit(mb_mma);
         }
@@ -278,39 +290,48 @@ __global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
     }
 }
 
-// Host: round a binary32 value to TF32 (nearest, ties away from zero, as cvt.rna).
-float host_tf32(float x) {
+// Host: round a binary32 value to bfloat16 (nearest, ties to even); returns the 16-bit pattern
+// and the rounded value in *back.
+uint16_t host_bf16(float x, float* back) {
     uint32_t u;
     std::memcpy(&u, &x, 4);
-    if ((u & 0x7F800000u) == 0x7F800000u) return x;   // inf / nan unchanged
-    u = (u + 0x1000u) & ~0x1FFFu;
-    float r;
-    std::memcpy(&r, &u, 4);
-    return r;
+    uint32_t r;
+    if ((u & 0x7F800000u) == 0x7F800000u)
+        r = u >> 16;   // inf / nan
+    else
+        r = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+    const uint32_t b = r << 16;
+    std::memcpy(back, &b, 4);
+    return (uint16_t)r;
 }
 
 }  // namespace
 
 int tc_pad_rows(int R) { return (R + 15) / 16 * 16; }
-int tc_pad_cols(int C) { return (C + 7) / 8 * 8; }
+int tc_pad_cols(int C) { return (C + 15) / 16 * 16; }
 
-// Head / tail image of one R x C operator (row-major, binary64) in the layout of the file
-// comment: out receives 2 * npad * kpad floats.
-void tc_operator_image(const double* op, int R, int C, int npad, int kpad, float* out) {
+// Three-part bfloat16 image of one R x C operator (row-major, binary64) in the layout of the
+// file comment: out receives 3 * npad * kpad bfloat16 values (16-bit patterns), part p at
+// p * npad * kpad.  Part 1 = the value rounded to bfloat16 (through binary32), parts 2 and 3 =
+// the remainders, formed in binary64 and rounded.
+void tc_operator_image(const double* op, int R, int C, int npad, int kpad, uint16_t* out) {
     const size_t n = (size_t)npad * kpad;
-    std::memset(out, 0, 2 * n * sizeof(float));
+    std::memset(out, 0, 3 * n * sizeof(uint16_t));
     for (int r = 0; r < R; ++r)
         for (int k = 0; k < C; ++k) {
             const double a = op[(size_t)r * C + k];
-            const float h = host_tf32((float)a);
-            const float t = host_tf32((float)(a - (double)h));
-            const size_t o = ((size_t)(k >> 2) * (npad * 16) + (r >> 3) * 128 + (r & 7) * 16 + (k & 3) * 4) / 4;
-            out[o] = h;
-            out[n + o] = t;
+            float b0, b1, b2;
+            const uint16_t p0 = host_bf16((float)a, &b0);
+            const uint16_t p1 = host_bf16((float)(a - (double)b0), &b1);
+            const uint16_t p2 = host_bf16((float)(a - (double)b0 - (double)b1), &b2);
+            const size_t o = img_off(r, k, npad) / 2;
+            out[o] = p0;
+            out[n + o] = p1;
+            out[2 * n + o] = p2;
         }
 }
 
-size_t tc_smem_bytes(int npad, int kmax) { return (size_t)(2 * TC_M + 2 * npad) * kmax * 4 + 1024; }
+size_t tc_smem_bytes(int npad, int kmax) { return (size_t)(3 * TC_M + 3 * npad) * kmax * 2 + 1024; }
 
 // Largest operator of the tensor-core form: 64 x 64 (R, C <= 64).
 static const size_t TC_SMEM_MAX = tc_smem_bytes(64, 64);
@@ -340,11 +361,11 @@ mh_status tc_contract_launch(mh_ctx* ctx, const tc_launch& a) {
     if (a.n_chunks == 0) return MH_OK;
     if (a.dst_double)
         k_contract_tc<double><<<(unsigned)a.n_chunks, TC_THREADS, smem, ctx->stream>>>(
-            a.img, a.img_off, a.kpad, a.op_C, a.chunk_op, a.chunk_t0, a.task_src, a.src, a.R, a.npad, a.kmax, a.temp,
+            reinterpret_cast<const __nv_bfloat16*>(a.img), a.img_off, a.kpad, a.op_C, a.chunk_op, a.chunk_t0, a.task_src, a.src, a.R, a.npad, a.kmax, a.temp,
             a.task_dst, a.accumulate, static_cast<double*>(a.dst), a.err);
     else
         k_contract_tc<float><<<(unsigned)a.n_chunks, TC_THREADS, smem, ctx->stream>>>(
-            a.img, a.img_off, a.kpad, a.op_C, a.chunk_op, a.chunk_t0, a.task_src, a.src, a.R, a.npad, a.kmax, a.temp,
+            reinterpret_cast<const __nv_bfloat16*>(a.img), a.img_off, a.kpad, a.op_C, a.chunk_op, a.chunk_t0, a.task_src, a.src, a.R, a.npad, a.kmax, a.temp,
             a.task_dst, a.accumulate, static_cast<float*>(a.dst), a.err);
     MH_LAUNCHED(ctx);
     return MH_OK;

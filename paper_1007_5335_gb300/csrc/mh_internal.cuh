@@ -109,9 +109,9 @@ struct dbuf {
 // Tensor-core batched contraction (contract_tc.cu): one launch over chunks of up to 128 tasks of
 // one operator each; products to temp[task][R] or, with task_dst, straight to the destinations.
 struct tc_launch {
-    const float* img = nullptr;          // operator images (head, tail) in the tensor-core layout
-    const int64_t* img_off = nullptr;    // per operator: offset of its image (floats)
-    const int32_t* kpad = nullptr;       // per operator: columns rounded up to 8
+    const uint16_t* img = nullptr;       // operator images (three bfloat16 parts) in the tensor-core layout
+    const int64_t* img_off = nullptr;    // per operator: offset of its image (bfloat16 elements)
+    const int32_t* kpad = nullptr;       // per operator: columns rounded up to 16
     const int32_t* op_C = nullptr;       // per operator: columns
     const int32_t* chunk_op = nullptr;
     const int32_t* chunk_t0 = nullptr;   // n_chunks + 1 entries
@@ -128,7 +128,7 @@ struct tc_launch {
 };
 int tc_pad_rows(int R);
 int tc_pad_cols(int C);
-void tc_operator_image(const double* op, int R, int C, int npad, int kpad, float* out);
+void tc_operator_image(const double* op, int R, int C, int npad, int kpad, uint16_t* out);
 size_t tc_smem_bytes(int npad, int kmax);
 mh_status tc_prepare(mh_ctx* ctx);
 mh_status tc_contract_launch(mh_ctx* ctx, const tc_launch& a);

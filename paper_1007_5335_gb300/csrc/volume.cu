@@ -549,7 +549,7 @@ constexpr int TC_TASKS = 128;      // tasks per tensor-core chunk (rows of the M
 
 // Operator images of the tensor-core path for one operator pool.
 struct TcImages {
-    dbuf<float> img;
+    dbuf<uint16_t> img;                // three bfloat16 parts per operator
     dbuf<int64_t> off;                 // per operator (-1: no image)
     dbuf<int32_t> kpad;                // per operator
     dbuf<int> err;                     // set by a tensor-core launch whose bounded wait gave up
@@ -706,8 +706,8 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
                 tcop.push_back(op);
                 tct0.push_back((int32_t)(s + n * c / nc));
             }
-            // 2 R C flop per task; bytes: the binary32 operator once per chunk, every task's
-            // source vector and product
+            // 2 R C flop per task; bytes: the operator once per chunk (at binary32 size), every
+            // task's binary32 source vector and product
             ph->tc_flops += 2.0 * R * op_C[op] * n;
             ph->tc_bytes += 4.0 * R * op_C[op] * nc + 4.0 * (op_C[op] + R) * n;
             ph->tc_kmax = std::max(ph->tc_kmax, tc_pad_cols(op_C[op]));
@@ -778,7 +778,7 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
     return MH_OK;
 }
 
-// Tensor-core images (head / tail split of the binary64 operator) of every operator that one of
+// Tensor-core images (three-part bfloat16 split of the binary64 operator) of every operator that one of
 // `phases` runs on the tensor cores.  ops64: the pool's operators (binary64, row-major at off).
 mh_status build_tc_images(mh_ctx* ctx, const double* ops64, const std::vector<int64_t>& off,
                           const std::vector<int32_t>& R, const std::vector<int32_t>& C,
@@ -793,11 +793,11 @@ mh_status build_tc_images(mh_ctx* ctx, const double* ops64, const std::vector<in
                 return mh_fail(ctx, MH_ERR_INVALID_ARG, "tensor-core operator rows differ from its phase");
             ioff[op] = (int64_t)total;
             kp[op] = tc_pad_cols(C[op]);
-            total += 2 * (size_t)tc_pad_rows(R[op]) * kp[op];
+            total += 3 * (size_t)tc_pad_rows(R[op]) * kp[op];
         }
     T->ready = total > 0;
     if (!T->ready) return MH_OK;
-    std::vector<float> img(total);
+    std::vector<uint16_t> img(total);
     for (size_t op = 0; op < off.size(); ++op)
         if (ioff[op] >= 0)
             tc_operator_image(ops64 + off[op], R[op], C[op], tc_pad_rows(R[op]), kp[op], img.data() + ioff[op]);
@@ -806,7 +806,7 @@ mh_status build_tc_images(mh_ctx* ctx, const double* ops64, const std::vector<in
     MH_ALLOC(ctx, T->off, off.size());
     MH_ALLOC(ctx, T->kpad, off.size());
     MH_ALLOC(ctx, T->err, 1);
-    MH_CUDA(ctx, cudaMemcpyAsync(T->img.p, img.data(), total * 4, cudaMemcpyHostToDevice, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(T->img.p, img.data(), total * 2, cudaMemcpyHostToDevice, st));
     MH_CUDA(ctx, cudaMemcpyAsync(T->off.p, ioff.data(), ioff.size() * 8, cudaMemcpyHostToDevice, st));
     MH_CUDA(ctx, cudaMemcpyAsync(T->kpad.p, kp.data(), kp.size() * 4, cudaMemcpyHostToDevice, st));
     MH_CUDA(ctx, cudaMemsetAsync(T->err.p, 0, sizeof(int), st));
