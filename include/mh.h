@@ -177,7 +177,7 @@ mh_status mh_volume_potential(mh_ctx* ctx, mh_tree* tree, double alpha, int p, c
  *   (y-x).n_y/|y-x|), n_targets ignored, out has N_Gamma entries.
  * targets_dev != NULL: out_dev[i] = U^h(x_i) = (1/(2 pi alpha^2)) int d/dnu_y K0 sigma ds
  *   at n_targets points (2 doubles each) assumed inside Omega, with the near-boundary
- *   rule: 16x upsampled density for targets within 5 h_s of a curve, interpolation
+ *   rule: 16x upsampled density for targets within 10 h_s of a curve, interpolation
  *   along the normal within h_s/4.  n_targets == 0 evaluates nothing (out_dev untouched);
  *   n_targets < 0 is MH_ERR_INVALID_ARG. */
 mh_status mh_double_layer_apply(mh_ctx* ctx, mh_boundary* bnd, double alpha, const double* sigma_dev,

@@ -20,8 +20,8 @@ Off-surface evaluation (Section 2, the double-layer representation of U^h):
     U^h(x) = (1/(2 pi alpha^2)) int d/dnu_y K0 sigma ds
            = -(1/(2 pi alpha^2)) sum_curves sum_n K(y_n, x) sigma_n |y'_n| h,
 with the near-boundary reading (the paper is silent on targets close to Gamma):
-  * d >= 5 h_s           : trapezoid rule on curve k;
-  * 0.25 h_s <= d < 5 h_s : trapezoid rule on 16x upsampled curve k (density and
+  * d >= 10 h_s          : trapezoid rule on curve k;
+  * 0.25 h_s <= d < 10 h_s: trapezoid rule on 16x upsampled curve k (density and
                             geometry by Fourier interpolation);
   * d < 0.25 h_s          : degree-4 polynomial in the distance along the normal
                             through the interior limit v_0 = -(A sigma)(t*)/(2 alpha^2)
@@ -41,7 +41,7 @@ from .quadrature import trig_kernel
 from .special import k1
 
 UPSAMPLE = 16
-NEAR_FAR = 5.0        # d < 5 h_s: upsampled rule
+NEAR_FAR = 10.0       # d < 10 h_s: upsampled rule (the plain rule is within ~1e-14 beyond)
 NEAR_LINE = 0.25      # d < 0.25 h_s: interpolation along the normal
 
 

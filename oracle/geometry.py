@@ -13,7 +13,7 @@ Point classification and the distance to Gamma are not spelled out in the
 paper (it needs them implicitly to restrict U = U^p + U^h to Omega, Section 2);
 the reading used here:
   * nearest node n* of curve k (smallest index on ties); h* = |y'(t_n*)| h_k;
-  * if |y_n* - x| < 6 h*: Newton on phi(t) = |y(t) - x|^2 / 2 from t_n*, giving the
+  * if |y_n* - x| < 12 h*: Newton on phi(t) = |y(t) - x|^2 / 2 from t_n*, giving the
     foot t*, the distance d = |y(t*) - x| and the side sign (x - y(t*)) . n(t*)
     (negative = Omega side);
   * otherwise the side comes from the trapezoid Laplace double layer of unit
@@ -28,7 +28,7 @@ import numpy as np
 
 from .quadrature import trig_eval
 
-NEAR_NODE_FACTOR = 6.0     # Newton projection when the nearest node is within 6 h*
+NEAR_NODE_FACTOR = 12.0    # Newton projection when the nearest node is within 12 h*
 
 
 class Curve:
@@ -104,7 +104,7 @@ def winding(curve: Curve, pts: np.ndarray) -> np.ndarray:
 
 class PointInfo:
     """Per target: region (-1 = in Omega, k = exterior side of curve k) and, per curve,
-    the projection data (None when the nearest node is >= 6 h* away)."""
+    the projection data (None when the nearest node is >= 12 h* away)."""
 
     def __init__(self, n_pts, n_curves):
         self.region = np.full(n_pts, -1, dtype=np.int64)

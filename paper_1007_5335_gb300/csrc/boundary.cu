@@ -12,10 +12,10 @@
 
 namespace {
 
-constexpr int UPSAMPLE = 16;        // fine grid for targets within 5 h_s of a curve
+constexpr int UPSAMPLE = 16;        // fine grid for targets within 10 h_s of a curve
 constexpr int FINE_TG = 4;          // auxiliary targets per block of the binary32 upsampled rule
-constexpr double NEAR_NODE = 6.0;   // project on the curve when the nearest node is within 6 h*
-constexpr double NEAR_FINE = 5.0;   // d < 5 h_s: upsampled rule
+constexpr double NEAR_NODE = 12.0;  // project on the curve when the nearest node is within 12 h*
+constexpr double NEAR_FINE = 10.0;  // d < 10 h_s: upsampled rule
 constexpr double NEAR_LINE = 0.25;  // d < h_s/4: interpolation along the normal
 // Flops counted for one double-layer kernel value K(y, x) w (the unit of the pair sums):
 // offsets 2, r^2 2, rsqrt 1, z 1, Chebyshev tail (4/z - 1, 10-term Clenshaw) 21, exp 8,
@@ -1144,7 +1144,7 @@ __global__ void k_axpy(double a, const double* __restrict__ x, double* y, int64_
 // ---------------- classification of off-surface targets ----------------
 
 // One warp per target.  For every curve: nearest node (smallest index on ties); if it is
-// closer than 6 h*, Newton projection on the trigonometric interpolant giving the foot
+// closer than 12 h*, Newton projection on the trigonometric interpolant giving the foot
 // t*, distance d and side; otherwise the side from the trapezoid Laplace double layer of
 // unit density (1 inside the outer curve, -1 inside a hole).
 __global__ void k_classify(const double* __restrict__ pts, int64_t npts, const double* __restrict__ geo,

@@ -14,8 +14,9 @@
 // (x1 = x rounded to bfloat16, x2 = the remainder rounded, x3 = what is left; 3 x 8
 // significant bits hold all 24 of binary32), and the product is formed as
 //     X T ~ X1 T1 + X1 T2 + X2 T1 + X1 T3 + X2 T2 + X3 T1
-// (six MMAs per K step into one accumulator); the dropped terms X2 T3, X3 T2, X3 T3 are at most
-// 2^-23 |X||T| per product, the size of binary32 rounding.  The operator's three parts are
+// (six MMAs per K step; X1 T1 in one accumulator, the other five in a second one, added in
+// the epilogue); the dropped terms X2 T3, X3 T2, X3 T3 are at most 2^-23 |X||T| per product,
+// the size of binary32 rounding.  The operator's three parts are
 // split once at set-up from the binary64 operator and stored in the exact shared-memory image
 // the MMA reads, so a CTA stages it with one bulk copy; the sources are gathered, split and
 // written into their images by all threads.
@@ -43,6 +44,7 @@ namespace {
 constexpr int TC_M = 128;         // tasks per CTA (rows of the MMA)
 constexpr int TC_THREADS = 256;   // 8 warps: gather and epilogue (two column halves)
 constexpr unsigned TC_SPIN = 1u << 22;   // polls of an mbarrier before a wait gives up
+constexpr int GATHER_IT = 4;     // warp items whose loads are issued together in the gather
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -138,7 +140,7 @@ __host__ __device__ __forceinline__ uint32_t img_off(int row, int k, int rows) {
 //   given, then the products go to dst[task_dst[t] + r] (added when accumulate is set; TD =
 //   float for the expansion pool, double for the potentials).
 template <typename TD>
-__global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
+__global__ void __launch_bounds__(TC_THREADS, 3) k_contract_tc(
     const __nv_bfloat16* __restrict__ img, const int64_t* __restrict__ img_off_op, const int32_t* __restrict__ kpad_op,
     const int32_t* __restrict__ op_C, const int32_t* __restrict__ chunk_op, const int32_t* __restrict__ chunk_t0,
     const int64_t* __restrict__ task_src, const float* src, int R, int npad, int kmax, float* __restrict__ temp,
@@ -160,7 +162,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
     const int C = op_C[op];
     const int kp = kpad_op[op];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t ncols = npad <= 32 ? 32u : 64u;   // power of two >= 32 (npad <= 64)
+    // two accumulators of npad columns: the leading products X1 T1 at column 0, the five
+    // smaller ones at column npad (a power of two >= 32 columns in all, npad <= 64)
+    const uint32_t ncols = 2 * npad <= 32 ? 32u : 2 * npad <= 64 ? 64u : 128u;
     const uint32_t mb_copy = smem_addr(&bar_copy), mb_mma = smem_addr(&bar_mma);
     const uint32_t part_b = (uint32_t)(npad * kp * 2);   // bytes of one operator part
 
@@ -186,36 +190,58 @@ __global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
         mbar_expect_tx(mb_copy, 3 * part_b);
         bulk_g2s(smem_addr(sB), img + img_off_op[op], 3 * part_b, mb_copy);
     }
-    // the sources: thread -> (row m, column group c of 8); 8 consecutive rows per column group
-    // fill one 128-byte line of an image, so a warp's stores touch 4 lines without conflicts
+    // the sources: a warp item is 8 rows x 16 columns (lane -> row 8 g + (lane & 7), columns
+    // 4 (lane >> 3) .. + 3 of the block): each row's 64 bytes are read as aligned 16-byte
+    // windows (the pool has slack after its end), and the three parts of a row group's 16
+    // columns fill two 128-byte lines of each image, so the stores are free of bank conflicts.
+    // A warp has at most 2 GATHER_IT items (K <= 64), taken GATHER_IT at a time: all loads of
+    // a batch are issued before any of its stores, so a batch costs two memory latencies
+    // (task offsets, then sources), not two per item.
     {
-        const int groups = kp >> 3;
-        for (int e = threadIdx.x; e < TC_M * groups; e += TC_THREADS) {
-            const int m = (e & 7) | ((e >> 3) / groups) << 3;
-            const int c = (e >> 3) % groups;
-            float v[8];
-            if (m < nt) {
-                const float* sp = src + task_src[t0 + m] + 8 * c;
+        const int nqb = kp >> 4;                       // column blocks of 16
+        const int items = (TC_M / 8) * nqb;            // warp items of the chunk
+        for (int i0 = warp; i0 < items; i0 += GATHER_IT * (TC_THREADS / 32)) {
+            int64_t s0v[GATHER_IT];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = 8 * c + u < C ? sp[u] : 0.f;
-            } else {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = 0.f;
+            for (int it = 0; it < GATHER_IT; ++it) {
+                const int wi = i0 + it * (TC_THREADS / 32);
+                const int rg = wi / nqb, qb = wi - rg * nqb;
+                const int m = rg * 8 + (lane & 7);
+                const int k0 = qb * 16 + (lane >> 3) * 4;
+                s0v[it] = (wi < items && m < nt && k0 < C) ? task_src[t0 + m] + k0 : -1;
             }
-            uint32_t w[3][4];
+            float4 wa[GATHER_IT], wb[GATHER_IT];
 #pragma unroll
-            for (int u = 0; u < 8; u += 2) {
-                __nv_bfloat16 a0, a1, a2, b0, b1, b2;
-                split3(v[u], a0, a1, a2);
-                split3(v[u + 1], b0, b1, b2);
-                w[0][u >> 1] = pack2(a0, b0);
-                w[1][u >> 1] = pack2(a1, b1);
-                w[2][u >> 1] = pack2(a2, b2);
+            for (int it = 0; it < GATHER_IT; ++it) {
+                wa[it] = wb[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (s0v[it] >= 0) {
+                    const int sh = (int)(s0v[it] & 3);
+                    const float4* wp = reinterpret_cast<const float4*>(src + (s0v[it] - sh));
+                    wa[it] = wp[0];
+                    if (sh) wb[it] = wp[1];
+                }
             }
-            const uint32_t o = img_off(m, 8 * c, TC_M);
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
-                *reinterpret_cast<uint4*>(sA + q * a_bytes + o) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+            for (int it = 0; it < GATHER_IT; ++it) {
+                const int wi = i0 + it * (TC_THREADS / 32);
+                if (wi >= items) break;
+                const int rg = wi / nqb, qb = wi - rg * nqb;
+                const int m = rg * 8 + (lane & 7);
+                const int k0 = qb * 16 + (lane >> 3) * 4;
+                const int sh = s0v[it] >= 0 ? (int)(s0v[it] & 3) : 0;
+                const float f[8] = {wa[it].x, wa[it].y, wa[it].z, wa[it].w, wb[it].x, wb[it].y, wb[it].z, wb[it].w};
+                __nv_bfloat16 p0[4], p1[4], p2[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float x = sh == 0 ? f[u] : sh == 1 ? f[u + 1] : sh == 2 ? f[u + 2] : f[u + 3];
+                    split3(s0v[it] >= 0 && k0 + u < C ? x : 0.f, p0[u], p1[u], p2[u]);
+                }
+                const uint32_t o = img_off(m, k0, TC_M);
+                *reinterpret_cast<uint2*>(sA + o) = make_uint2(pack2(p0[0], p0[1]), pack2(p0[2], p0[3]));
+                *reinterpret_cast<uint2*>(sA + a_bytes + o) = make_uint2(pack2(p1[0], p1[1]), pack2(p1[2], p1[3]));
+                *reinterpret_cast<uint2*>(sA + 2 * a_bytes + o) =
+                    make_uint2(pack2(p2[0], p2[1]), pack2(p2[2], p2[3]));
+            }
         }
     }
     fence_async_smem();   // the generic-proxy stores above become visible to the tensor cores
@@ -230,14 +256,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
             const uint32_t idesc = instr_desc_bf16(TC_M, npad);
             const uint32_t a_lbo = TC_M * 16, b_lbo = (uint32_t)npad * 16;
             const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
-            // (source part, operator part) of the six products whose part indices sum to <= 2
+            // (source part, operator part) of the six products whose part indices sum to <= 2;
+            // the first goes to the leading accumulator, the other five to the second.  The tensor
+            // cores truncate when they add into an accumulator, so each accumulation costs up to
+            // one unit in the last place of its running sum: the leading sum takes only K / 16 of
+            // them, the second sum is ~2^-8 as large
             const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
             for (int ks = 0; ks < kp / 16; ++ks) {
                 const uint32_t da = (uint32_t)ks * 2 * a_lbo, db = (uint32_t)ks * 2 * b_lbo;
 #pragma unroll
                 for (int j = 0; j < 6; ++j)
-                    mma_bf16(tmem, smem_desc(a0 + pa[j] * a_bytes + da, a_lbo, 128),
-                             smem_desc(b0 + pb[j] * part_b + db, b_lbo, 128), idesc, (ks | j) != 0);
+                    mma_bf16(j == 0 ? tmem : tmem + (uint32_t)npad, smem_desc(a0 + pa[j] * a_bytes + da, a_lbo, 128),
+                             smem_desc(b0 + pb[j] * part_b + db, b_lbo, 128), idesc,
+                             j == 0 ? ks != 0 : (ks != 0 || j != 1));
             }
             mma_commit(mb_mma);
         }
@@ -249,6 +280,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
     const bool have = __syncthreads_and(copied && mbar_wait(mb_mma, 0)) != 0;
     if (copied && !have && threadIdx.x == 0) atomicExch(err, 2);
     tc_after_sync();
+    // products: TMEM -> shared staging rows (stride npad + 1: the lanes of a warp hold different
+    // rows) -> global, written as whole rows
+    float* stage = reinterpret_cast<float*>(sA);   // the source images are no longer read
+    const int ld = npad + 1;
     if (have) {
         // warp w: tasks 32 (w % 4) + lane, columns [h * npad / 2, (h + 1) * npad / 2), h = w / 4
         const int m = 32 * (warp & 3) + lane;
@@ -256,26 +291,42 @@ __global__ void __launch_bounds__(TC_THREADS) k_contract_tc(
         const int c0 = (warp >> 2) * half;
         const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
         for (int cc = 0; cc < half; cc += 8) {
-            uint32_t r[8];
+            uint32_t r[8], q[8];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                 : "r"(taddr + (uint32_t)cc));
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7])
+                : "r"(taddr + (uint32_t)(npad + cc)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (m < nt) {
-                const int64_t t = t0 + m;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int rr = c0 + cc + u;
-                    if (rr < R) {
-                        const float v = __uint_as_float(r[u]);
-                        if (task_dst) {
-                            TD* y = dst + task_dst[t] + rr;
-                            *y = accumulate ? *y + (TD)v : (TD)v;
-                        } else {
-                            temp[t * R + rr] = v;
-                        }
-                    }
+            for (int u = 0; u < 8; ++u) stage[m * ld + c0 + cc + u] = __uint_as_float(r[u]) + __uint_as_float(q[u]);
+        }
+    }
+    __syncthreads();
+    if (have) {
+        if (!task_dst) {
+            // the chunk's products are one contiguous block temp[t0 R .. (t0 + nt) R)
+            float* out = temp + (int64_t)t0 * R;
+            const int ne = nt * R, dr = TC_THREADS % R, dm = TC_THREADS / R;
+            int mm = threadIdx.x / R, rr = threadIdx.x - mm * R;
+            for (int e = threadIdx.x; e < ne; e += TC_THREADS) {
+                out[e] = stage[mm * ld + rr];
+                rr += dr;
+                mm += dm;
+                if (rr >= R) {
+                    rr -= R;
+                    ++mm;
+                }
+            }
+        } else {
+            for (int mm = warp; mm < nt; mm += TC_THREADS / 32) {
+                TD* y = dst + task_dst[t0 + mm];
+                for (int rr = lane; rr < R; rr += 32) {
+                    const float v = stage[mm * ld + rr];
+                    y[rr] = accumulate ? y[rr] + (TD)v : (TD)v;
                 }
             }
         }
@@ -331,7 +382,13 @@ void tc_operator_image(const double* op, int R, int C, int npad, int kpad, uint1
         }
 }
 
-size_t tc_smem_bytes(int npad, int kmax) { return (size_t)(3 * TC_M + 3 * npad) * kmax * 2 + 1024; }
+// Dynamic shared memory of a launch: the source and operator images, or, if larger, the product
+// staging rows that reuse them (128 x (npad + 1) binary32), plus 1 KB for the alignment.
+size_t tc_smem_bytes(int npad, int kmax) {
+    const size_t images = (size_t)(3 * TC_M + 3 * npad) * kmax * 2;
+    const size_t stage = (size_t)TC_M * (npad + 1) * 4;
+    return (images > stage ? images : stage) + 1024;
+}
 
 // Largest operator of the tensor-core form: 64 x 64 (R, C <= 64).
 static const size_t TC_SMEM_MAX = tc_smem_bytes(64, 64);

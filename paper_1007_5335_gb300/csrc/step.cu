@@ -167,8 +167,8 @@ extern "C" mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* 
             if (bl[i] < 0) return mh_fail(ctx, MH_ERR_GEOMETRY, "boundary node %lld lies outside the tree", (long long)i);
     }
     // Dipole sources of the double layer for the multipole pass: the 16x fine nodes of every
-    // curve (the upsampled rule, applied at every volume node; for nodes at least 5 h_s from
-    // a curve it agrees with the trapezoid rule to ~e^{-2 pi 5}), sorted by leaf.
+    // curve (the upsampled rule, applied at every volume node; for nodes at least 10 h_s from
+    // a curve it agrees with the trapezoid rule to ~1e-14 for smooth densities), sorted by leaf.
     {
         const int64_t nf = bnd->n_fine;
         std::vector<double> fg(6 * nf), fxy(2 * nf);

@@ -545,6 +545,7 @@ struct Phase {
 };
 
 constexpr int TC_MIN_TASKS = 16;   // operators with fewer tasks stay on the CUDA cores
+constexpr int TC_POOL_PAD = 16;    // slack floats after the binary32 pool (aligned-window gathers)
 constexpr int TC_TASKS = 128;      // tasks per tensor-core chunk (rows of the MMA)
 
 // Operator images of the tensor-core path for one operator pool.
@@ -1400,13 +1401,15 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
                                &V->tc));
     }
     MH_ALLOC(ctx, V->vec, V->vec_len);
-    MH_ALLOC(ctx, V->vec32, V->vec_len);
+    // binary32 mirror with TC_POOL_PAD floats of slack at the end: the tensor-core gather
+    // reads sources in aligned 16-byte windows that may reach past a vector's last entry
+    MH_ALLOC(ctx, V->vec32, V->vec_len + TC_POOL_PAD);
     MH_ALLOC(ctx, V->temp, need);
     MH_ALLOC(ctx, V->temp_near, need_near);
     MH_TRY(V->side.create(ctx));
     V->temp_len = need;
     MH_CUDA(ctx, cudaMemsetAsync(V->vec.p, 0, V->vec_len * 8, st));
-    MH_CUDA(ctx, cudaMemsetAsync(V->vec32.p, 0, V->vec_len * 4, st));
+    MH_CUDA(ctx, cudaMemsetAsync(V->vec32.p, 0, (V->vec_len + TC_POOL_PAD) * 4, st));
     // shared-memory opt-in for the contraction kernel
     int maxs = 0;
     for (auto* ph : {V->p2m.get(), V->m2l.get(), V->out.get(), V->near.get()}) maxs = std::max(maxs, ph->smem);
@@ -1876,10 +1879,12 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
         MH_TRY(build_tc_images(ctx, pool.data.data(), off, rr, cc, {D->p2m.get(), D->m2l.get(), D->out.get()}, &D->tc));
     }
     MH_ALLOC(ctx, D->vec, D->vec_len);
-    MH_ALLOC(ctx, D->vec32, D->vec_len);
+    // binary32 mirror with TC_POOL_PAD floats of slack at the end: the tensor-core gather
+    // reads sources in aligned 16-byte windows that may reach past a vector's last entry
+    MH_ALLOC(ctx, D->vec32, D->vec_len + TC_POOL_PAD);
     MH_ALLOC(ctx, D->temp, need);
     MH_CUDA(ctx, cudaMemsetAsync(D->vec.p, 0, D->vec_len * 8, st));
-    MH_CUDA(ctx, cudaMemsetAsync(D->vec32.p, 0, D->vec_len * 4, st));
+    MH_CUDA(ctx, cudaMemsetAsync(D->vec32.p, 0, (D->vec_len + TC_POOL_PAD) * 4, st));
     MH_TRY(D->side.create(ctx));
     MH_CUDA(ctx, cudaStreamSynchronize(st));
     V->dip = std::move(D);
