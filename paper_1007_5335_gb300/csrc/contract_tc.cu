@@ -108,6 +108,11 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 fills the 16 bytes with zeros.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -143,8 +148,8 @@ template <typename TD>
 __global__ void __launch_bounds__(TC_THREADS, 3) k_contract_tc(
     const __nv_bfloat16* __restrict__ img, const int64_t* __restrict__ img_off_op, const int32_t* __restrict__ kpad_op,
     const int32_t* __restrict__ op_C, const int32_t* __restrict__ chunk_op, const int32_t* __restrict__ chunk_t0,
-    const int64_t* __restrict__ task_src, const float* src, int R, int npad, int kmax, float* __restrict__ temp,
-    const int64_t* __restrict__ task_dst, int accumulate, TD* dst, int* err) {
+    const uint16_t* __restrict__ spl, int64_t plane, const int64_t* __restrict__ tc_src, int R, int npad, int kmax,
+    float* __restrict__ temp, const int64_t* __restrict__ task_dst, int accumulate, TD* dst, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // 1024-byte aligned base (the dynamic allocation is padded by 1 KB for this)
     unsigned char* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
@@ -190,59 +195,30 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_contract_tc(
         mbar_expect_tx(mb_copy, 3 * part_b);
         bulk_g2s(smem_addr(sB), img + img_off_op[op], 3 * part_b, mb_copy);
     }
-    // the sources: a warp item is 8 rows x 16 columns (lane -> row 8 g + (lane & 7), columns
-    // 4 (lane >> 3) .. + 3 of the block): each row's 64 bytes are read as aligned 16-byte
-    // windows (the pool has slack after its end), and the three parts of a row group's 16
-    // columns fill two 128-byte lines of each image, so the stores are free of bank conflicts.
-    // A warp has at most 2 GATHER_IT items (K <= 64), taken GATHER_IT at a time: all loads of
-    // a batch are issued before any of its stores, so a batch costs two memory latencies
-    // (task offsets, then sources), not two per item.
+    // the sources: already split into three bfloat16 planes with 16-element rows (tc_split),
+    // so the gather is 16-byte asynchronous copies (8 columns of one part of one row each;
+    // rows past the chunk are zero-filled).  Consecutive threads take 8 rows of one column
+    // group, which fill one 128-byte line of the image: no bank conflicts.
     {
-        const int nqb = kp >> 4;                       // column blocks of 16
-        const int items = (TC_M / 8) * nqb;            // warp items of the chunk
-        for (int i0 = warp; i0 < items; i0 += GATHER_IT * (TC_THREADS / 32)) {
-            int64_t s0v[GATHER_IT];
-#pragma unroll
-            for (int it = 0; it < GATHER_IT; ++it) {
-                const int wi = i0 + it * (TC_THREADS / 32);
-                const int rg = wi / nqb, qb = wi - rg * nqb;
-                const int m = rg * 8 + (lane & 7);
-                const int k0 = qb * 16 + (lane >> 3) * 4;
-                s0v[it] = (wi < items && m < nt && k0 < C) ? task_src[t0 + m] + k0 : -1;
-            }
-            float4 wa[GATHER_IT], wb[GATHER_IT];
-#pragma unroll
-            for (int it = 0; it < GATHER_IT; ++it) {
-                wa[it] = wb[it] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (s0v[it] >= 0) {
-                    const int sh = (int)(s0v[it] & 3);
-                    const float4* wp = reinterpret_cast<const float4*>(src + (s0v[it] - sh));
-                    wa[it] = wp[0];
-                    if (sh) wb[it] = wp[1];
+        const int groups = kp >> 3;
+        for (int part = 0; part < 3; ++part) {
+            int q = threadIdx.x >> 3;                  // (row group, column group) pair of the thread
+            int rg = q / groups, cg = q - rg * groups;
+            const int dq = (TC_THREADS >> 3) / groups, dc = (TC_THREADS >> 3) % groups;
+            for (int e = threadIdx.x; e < TC_M * groups; e += TC_THREADS) {
+                const int m = rg * 8 + (threadIdx.x & 7);
+                const bool valid = m < nt;
+                const uint16_t* g = valid ? spl + part * plane + tc_src[t0 + m] + 8 * cg : spl;
+                cp_async16(smem_addr(sA + part * a_bytes + img_off(m, 8 * cg, TC_M)), g, valid ? 16u : 0u);
+                rg += dq;
+                cg += dc;
+                if (cg >= groups) {
+                    cg -= groups;
+                    ++rg;
                 }
-            }
-#pragma unroll
-            for (int it = 0; it < GATHER_IT; ++it) {
-                const int wi = i0 + it * (TC_THREADS / 32);
-                if (wi >= items) break;
-                const int rg = wi / nqb, qb = wi - rg * nqb;
-                const int m = rg * 8 + (lane & 7);
-                const int k0 = qb * 16 + (lane >> 3) * 4;
-                const int sh = s0v[it] >= 0 ? (int)(s0v[it] & 3) : 0;
-                const float f[8] = {wa[it].x, wa[it].y, wa[it].z, wa[it].w, wb[it].x, wb[it].y, wb[it].z, wb[it].w};
-                __nv_bfloat16 p0[4], p1[4], p2[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float x = sh == 0 ? f[u] : sh == 1 ? f[u + 1] : sh == 2 ? f[u + 2] : f[u + 3];
-                    split3(s0v[it] >= 0 && k0 + u < C ? x : 0.f, p0[u], p1[u], p2[u]);
-                }
-                const uint32_t o = img_off(m, k0, TC_M);
-                *reinterpret_cast<uint2*>(sA + o) = make_uint2(pack2(p0[0], p0[1]), pack2(p0[2], p0[3]));
-                *reinterpret_cast<uint2*>(sA + a_bytes + o) = make_uint2(pack2(p1[0], p1[1]), pack2(p1[2], p1[3]));
-                *reinterpret_cast<uint2*>(sA + 2 * a_bytes + o) =
-                    make_uint2(pack2(p2[0], p2[1]), pack2(p2[2], p2[3]));
             }
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
     }
     fence_async_smem();   // the generic-proxy stores above become visible to the tensor cores
     __syncthreads();
@@ -341,6 +317,21 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_contract_tc(
     }
 }
 
+// Split `count` consecutive binary32 vectors of length len (src) into the three bfloat16
+// planes (plane elements apart) at dst, each vector padded with zeros to S entries.
+__global__ void k_split_pool(const float* __restrict__ src, int len, int64_t count, int S,
+                             uint16_t* __restrict__ planes, int64_t plane, int64_t dst) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count * S) return;
+    const int64_t v = i / S;
+    const int e = (int)(i - v * S);
+    __nv_bfloat16 p0, p1, p2;
+    split3(e < len ? src[v * len + e] : 0.f, p0, p1, p2);
+    planes[dst + i] = __bfloat16_as_ushort(p0);
+    planes[plane + dst + i] = __bfloat16_as_ushort(p1);
+    planes[2 * plane + dst + i] = __bfloat16_as_ushort(p2);
+}
+
 // Host: round a binary32 value to bfloat16 (nearest, ties to even); returns the 16-bit pattern
 // and the rounded value in *back.
 uint16_t host_bf16(float x, float* back) {
@@ -418,12 +409,22 @@ mh_status tc_contract_launch(mh_ctx* ctx, const tc_launch& a) {
     if (a.n_chunks == 0) return MH_OK;
     if (a.dst_double)
         k_contract_tc<double><<<(unsigned)a.n_chunks, TC_THREADS, smem, ctx->stream>>>(
-            reinterpret_cast<const __nv_bfloat16*>(a.img), a.img_off, a.kpad, a.op_C, a.chunk_op, a.chunk_t0, a.task_src, a.src, a.R, a.npad, a.kmax, a.temp,
+            reinterpret_cast<const __nv_bfloat16*>(a.img), a.img_off, a.kpad, a.op_C, a.chunk_op, a.chunk_t0, a.spl,
+            a.plane, a.tc_src, a.R, a.npad, a.kmax, a.temp,
             a.task_dst, a.accumulate, static_cast<double*>(a.dst), a.err);
     else
         k_contract_tc<float><<<(unsigned)a.n_chunks, TC_THREADS, smem, ctx->stream>>>(
-            reinterpret_cast<const __nv_bfloat16*>(a.img), a.img_off, a.kpad, a.op_C, a.chunk_op, a.chunk_t0, a.task_src, a.src, a.R, a.npad, a.kmax, a.temp,
+            reinterpret_cast<const __nv_bfloat16*>(a.img), a.img_off, a.kpad, a.op_C, a.chunk_op, a.chunk_t0, a.spl,
+            a.plane, a.tc_src, a.R, a.npad, a.kmax, a.temp,
             a.task_dst, a.accumulate, static_cast<float*>(a.dst), a.err);
+    MH_LAUNCHED(ctx);
+    return MH_OK;
+}
+
+mh_status tc_split_launch(mh_ctx* ctx, const float* src, int len, int64_t count, int S, uint16_t* planes, int64_t plane,
+                          int64_t dst) {
+    if (count <= 0) return MH_OK;
+    k_split_pool<<<(unsigned)mh_grid(count * S, 256), 256, 0, ctx->stream>>>(src, len, count, S, planes, plane, dst);
     MH_LAUNCHED(ctx);
     return MH_OK;
 }

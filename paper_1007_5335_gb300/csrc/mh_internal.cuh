@@ -116,8 +116,9 @@ struct tc_launch {
     const int32_t* chunk_op = nullptr;
     const int32_t* chunk_t0 = nullptr;   // n_chunks + 1 entries
     int64_t n_chunks = 0;
-    const int64_t* task_src = nullptr;
-    const float* src = nullptr;
+    const uint16_t* spl = nullptr;       // pre-split sources: three bfloat16 planes
+    int64_t plane = 0;                   // elements per plane
+    const int64_t* tc_src = nullptr;     // per task: offset of its source row in a plane
     int R = 0, npad = 0, kmax = 0;
     float* temp = nullptr;
     const int64_t* task_dst = nullptr;
@@ -132,6 +133,10 @@ void tc_operator_image(const double* op, int R, int C, int npad, int kpad, uint1
 size_t tc_smem_bytes(int npad, int kmax);
 mh_status tc_prepare(mh_ctx* ctx);
 mh_status tc_contract_launch(mh_ctx* ctx, const tc_launch& a);
+// Split count binary32 vectors of length len at src into the three bfloat16 planes at dst
+// (rows padded with zeros to S entries).
+mh_status tc_split_launch(mh_ctx* ctx, const float* src, int len, int64_t count, int S, uint16_t* planes, int64_t plane,
+                          int64_t dst);
 
 // Device-resident state of the sync-free GMRES (gmres_run_graph): every kernel of its fixed
 // schedule reads the flags at entry and returns at once when its work is not needed.

@@ -541,6 +541,8 @@ struct Phase {
     int tc_npad = 0, tc_kmax = 0;
     double tc_flops = 0, tc_bytes = 0;   // algorithmic work of the tensor-core launch (binary32 data)
     std::vector<int> tc_ops;
+    std::vector<int64_t> tc_src_host;      // binary32 source offsets of the tensor-core tasks
+    dbuf<int64_t> tc_src;                  // their rows in the split planes
     dbuf<int32_t> tc_chunk_op, tc_chunk_t0;
 };
 
@@ -549,13 +551,42 @@ constexpr int TC_POOL_PAD = 16;    // slack floats after the binary32 pool (alig
 constexpr int TC_TASKS = 128;      // tasks per tensor-core chunk (rows of the MMA)
 
 // Operator images of the tensor-core path for one operator pool.
+// The pool's source vectors are also kept pre-split into three bfloat16 planes (rows padded to
+// a multiple of 16 entries), refreshed by tc_split after each range is final, so that the
+// tensor-core gather copies bytes instead of splitting every source once per task.
 struct TcImages {
     dbuf<uint16_t> img;                // three bfloat16 parts per operator
     dbuf<int64_t> off;                 // per operator (-1: no image)
     dbuf<int32_t> kpad;                // per operator
     dbuf<int> err;                     // set by a tensor-core launch whose bounded wait gave up
     bool ready = false;
+    struct Range {                     // count vectors of length len at src in the binary32 pool,
+        int64_t src;                   // rows of S entries at dst in every plane
+        int len;
+        int64_t count;
+        int S;
+        int64_t dst;
+    };
+    std::vector<Range> ranges;
+    int64_t plane = 0;                 // entries per plane
+    dbuf<uint16_t> planes;             // 3 * plane
+    // plane offset of the row of the vector starting at binary32 offset o (-1: none)
+    int64_t map(int64_t o, int* S) const {
+        for (const Range& r : ranges)
+            if (o >= r.src && o < r.src + r.count * r.len && (o - r.src) % r.len == 0) {
+                *S = r.S;
+                return r.dst + (o - r.src) / r.len * r.S;
+            }
+        return -1;
+    }
 };
+
+// Refresh the split planes of range k from the binary32 pool (after its values are final).
+mh_status tc_split(mh_ctx* ctx, const TcImages& T, int k, const float* pool32) {
+    if (!T.ready || !ctx->tensor_cores || k >= (int)T.ranges.size()) return MH_OK;
+    const TcImages::Range& r = T.ranges[k];
+    return tc_split_launch(ctx, pool32 + r.src, r.len, r.count, r.S, T.planes.p, T.plane, r.dst);
+}
 
 // A second stream, of the device's highest priority, with fork / join events: the multipole
 // passes (latency chains) run there while the near fields, which do not depend on them, run
@@ -718,6 +749,7 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
         n_tc_tasks = (int64_t)s;
     }
     tct0.push_back((int32_t)n_tc_tasks);
+    ph->tc_src_host.assign(src.begin(), src.begin() + n_tc_tasks);
     ph->n_tc = (int64_t)tcop.size();
     ph->tc_npad = tc_pad_rows(R);
     ph->first_rest = 0;
@@ -783,7 +815,8 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
 // `phases` runs on the tensor cores.  ops64: the pool's operators (binary64, row-major at off).
 mh_status build_tc_images(mh_ctx* ctx, const double* ops64, const std::vector<int64_t>& off,
                           const std::vector<int32_t>& R, const std::vector<int32_t>& C,
-                          std::initializer_list<const Phase*> phases, TcImages* T) {
+                          std::initializer_list<Phase*> phases, const std::vector<TcImages::Range>& ranges,
+                          TcImages* T) {
     std::vector<int64_t> ioff(off.size(), -1);
     std::vector<int32_t> kp(off.size(), 0);
     size_t total = 0;
@@ -792,12 +825,40 @@ mh_status build_tc_images(mh_ctx* ctx, const double* ops64, const std::vector<in
             if (ioff[op] >= 0) continue;
             if (tc_pad_rows(R[op]) != ph->tc_npad)
                 return mh_fail(ctx, MH_ERR_INVALID_ARG, "tensor-core operator rows differ from its phase");
+            bool len_ok = false;   // the operator's columns are the length of one split range
+            for (const TcImages::Range& r : ranges) len_ok = len_ok || r.len == C[op];
+            if (!len_ok)
+                return mh_fail(ctx, MH_ERR_INVALID_ARG, "tensor-core operator columns match no source vector length");
             ioff[op] = (int64_t)total;
             kp[op] = tc_pad_cols(C[op]);
             total += 3 * (size_t)tc_pad_rows(R[op]) * kp[op];
         }
     T->ready = total > 0;
     if (!T->ready) return MH_OK;
+    // split planes: every range's rows, padded to a multiple of 16 entries
+    T->ranges = ranges;
+    T->plane = 0;
+    for (TcImages::Range& r : T->ranges) {
+        r.S = (r.len + 15) / 16 * 16;
+        r.dst = T->plane;
+        T->plane += r.count * r.S;
+    }
+    MH_ALLOC(ctx, T->planes, std::max<int64_t>(3 * T->plane, 8));
+    MH_CUDA(ctx, cudaMemsetAsync(T->planes.p, 0, std::max<int64_t>(3 * T->plane, 8) * 2, ctx->stream));
+    for (Phase* ph : phases) {
+        std::vector<int64_t> rows(ph->tc_src_host.size());
+        for (size_t i = 0; i < rows.size(); ++i) {
+            int S = 0;
+            rows[i] = T->map(ph->tc_src_host[i], &S);
+            if (rows[i] < 0)
+                return mh_fail(ctx, MH_ERR_INVALID_ARG, "tensor-core source %lld is not a vector of the split ranges",
+                               (long long)ph->tc_src_host[i]);
+        }
+        MH_ALLOC(ctx, ph->tc_src, std::max<size_t>(rows.size(), 1));
+        if (!rows.empty())
+            MH_CUDA(ctx, cudaMemcpyAsync(ph->tc_src.p, rows.data(), rows.size() * 8, cudaMemcpyHostToDevice,
+                                         ctx->stream));
+    }
     std::vector<uint16_t> img(total);
     for (size_t op = 0; op < off.size(); ++op)
         if (ioff[op] >= 0)
@@ -849,8 +910,9 @@ mh_status run_phase_on(mh_ctx* ctx, const TOP* ops, const int64_t* op_off, const
         a.chunk_op = ph->tc_chunk_op.p;
         a.chunk_t0 = ph->tc_chunk_t0.p;
         a.n_chunks = ph->n_tc;
-        a.task_src = ph->task_src.p;
-        a.src = reinterpret_cast<const float*>(pool);
+        a.spl = tc->planes.p;
+        a.plane = tc->plane;
+        a.tc_src = ph->tc_src.p;
         a.R = ph->R;
         a.npad = ph->tc_npad;
         a.kmax = ph->tc_kmax;
@@ -1397,8 +1459,11 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
     {
         std::vector<int64_t> off(pool.off.begin(), pool.off.end());
         std::vector<int32_t> rr(pool.R.begin(), pool.R.end()), cc(pool.C.begin(), pool.C.end());
+        // split ranges: node values (B), multipoles (M), locals (L)
+        const std::vector<TcImages::Range> rg = {{V->B_off, qq, nl, 0, 0}, {V->M_off, P, nb, 0, 0},
+                                                 {V->L_off, P, nb, 0, 0}};
         MH_TRY(build_tc_images(ctx, all.data(), off, rr, cc, {V->p2m.get(), V->m2l.get(), V->near.get(), V->out.get()},
-                               &V->tc));
+                               rg, &V->tc));
     }
     MH_ALLOC(ctx, V->vec, V->vec_len);
     // binary32 mirror with TC_POOL_PAD floats of slack at the end: the tensor-core gather
@@ -1876,7 +1941,10 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
     {
         std::vector<int64_t> off(pool.off.begin(), pool.off.end());
         std::vector<int32_t> rr(pool.R.begin(), pool.R.end()), cc(pool.C.begin(), pool.C.end());
-        MH_TRY(build_tc_images(ctx, pool.data.data(), off, rr, cc, {D->p2m.get(), D->m2l.get(), D->out.get()}, &D->tc));
+        // split ranges: dipole multipoles (DM), locals (DL)
+        const std::vector<TcImages::Range> rg = {{D->DM_off, P, nb, 0, 0}, {D->DL_off, P, nb, 0, 0}};
+        MH_TRY(build_tc_images(ctx, pool.data.data(), off, rr, cc, {D->p2m.get(), D->m2l.get(), D->out.get()}, rg,
+                               &D->tc));
     }
     MH_ALLOC(ctx, D->vec, D->vec_len);
     // binary32 mirror with TC_POOL_PAD floats of slack at the end: the tensor-core gather
@@ -1900,8 +1968,10 @@ static mh_status dipole_passes(mh_ctx* ctx, VolData* V, DipData* D, const TOP* o
     };
     MH_TRY(run(D->p2m.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, pool, true, "dlp_fmm_chain"));
+    if (sizeof(TOP) == 4) MH_TRY(tc_split(ctx, D->tc, 0, D->vec32.p));   // multipoles final
     MH_TRY(run(D->m2l.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, pool, false, "dlp_fmm_chain"));
+    if (sizeof(TOP) == 4) MH_TRY(tc_split(ctx, D->tc, 1, D->vec32.p));   // locals final
     return MH_OK;
 }
 
@@ -2008,8 +2078,10 @@ static mh_status volume_passes(mh_ctx* ctx, VolData* V, const TOP* ops) {
     TOP* pool = typed_pool<TOP>(V->vec, V->vec32);
     MH_TRY(run_phase(ctx, V, ops, V->p2m.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, V->M_off, V->L_off, pool, true, "volume_chain"));
+    if (sizeof(TOP) == 4) MH_TRY(tc_split(ctx, V->tc, 1, V->vec32.p));   // multipoles final
     MH_TRY(run_phase(ctx, V, ops, V->m2l.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, V->M_off, V->L_off, pool, false, "volume_chain"));
+    if (sizeof(TOP) == 4) MH_TRY(tc_split(ctx, V->tc, 2, V->vec32.p));   // locals final
     return MH_OK;
 }
 
@@ -2060,6 +2132,7 @@ mh_status volume_apply(mh_ctx* ctx, mh_tree* t, double alpha, int p, const doubl
         // node values in binary32 once: every contraction then gathers binary32
         k_d2f<<<mh_grid(nn, 256), 256, 0, ctx->stream>>>(b, V->vec32.p + V->B_off, nn);
         MH_LAUNCHED(ctx);
+        MH_TRY(tc_split(ctx, V->tc, 0, V->vec32.p));   // node values final
         MH_TRY(volume_run<float>(ctx, t, V, V->ops32.p));
     } else {
         MH_CUDA(ctx, cudaMemcpyAsync(V->vec.p + V->B_off, b, nn * 8, cudaMemcpyDeviceToDevice, ctx->stream));
