@@ -139,6 +139,19 @@ __device__ __forceinline__ float mh_k1oz_large_f(float z, float zinv) {
     return __expf(-z) * rsqrtf(z) * zinv * m;
 }
 
+// g(r/alpha) (dx nx + dy ny) for the offset (dx, dy) of a source from a target, without the
+// tests of mh_dl32_pair: coincident points give 0 through the zero offset (r^2 is floored at
+// 1e-30, so g stays finite), and pairs far beyond the cut come out below the binary32 rounding
+// of any sum (e^{-z} underflows).  For loops whose pairs are near by construction.
+__device__ __forceinline__ float mh_dl32_pair_nt(float dx, float dy, float nx, float ny, const mh_dl32& c) {
+    const float r2 = fmaxf(fmaf(dx, dx, dy * dy), 1e-30f);
+    const float rinv = rsqrtf(r2);
+    const float zinv = c.a * rinv;
+    const float g = r2 <= c.r2_small ? mh_k1oz_small_f(r2 * c.y_r2, zinv)
+                                     : mh_k1oz_large_f(r2 * rinv * c.ia, zinv);
+    return g * fmaf(dx, nx, dy * ny);
+}
+
 // g(r/alpha) (dx nx + dy ny) for the offset (dx, dy) of a source from a target; 0 for
 // coincident points and beyond the cut.
 __device__ __forceinline__ float mh_dl32_pair(float dx, float dy, float nx, float ny, const mh_dl32& c) {

@@ -744,8 +744,9 @@ __global__ void __launch_bounds__(256) k_dlp_fine32_grp(
             const float4 v = fine32[f0 + i];
             const float w = wf[f0 + i];
             const float nx = v.z * w, ny = v.w * w;
+            // the chunk is within the cut of some target of the group: no per-pair tests
 #pragma unroll
-            for (int j = 0; j < TG; ++j) pt[j] += mh_dl32_pair(v.x - dx0[j], v.y - dy0[j], nx, ny, c32);
+            for (int j = 0; j < TG; ++j) pt[j] += mh_dl32_pair_nt(v.x - dx0[j], v.y - dy0[j], nx, ny, c32);
         }
 #pragma unroll
         for (int j = 0; j < TG; ++j) {   // TwoSum: hi + lo += pt exactly up to the rounding of lo

@@ -1615,11 +1615,20 @@ __global__ void __launch_bounds__(NT) k_dip_near32(
         }
         __syncthreads();
         if (act) {
-            float pt = 0.f;
-            for (int e = g; e < m; e += groups) {
-                const float4 v = s4[e];
-                pt += mh_dl32_pair(v.x - tx, v.y - ty, v.z, v.w, c32);
+            // two staged dipoles per iteration (the warp's threads share g: a uniform branch);
+            // the dipoles of neighbour leaves are near by construction: no per-pair tests
+            float pt = 0.f, pu = 0.f;
+            int e = g;
+            for (; e + groups < m; e += 2 * groups) {
+                const float4 v = s4[e], u = s4[e + groups];
+                pt += mh_dl32_pair_nt(v.x - tx, v.y - ty, v.z, v.w, c32);
+                pu += mh_dl32_pair_nt(u.x - tx, u.y - ty, u.z, u.w, c32);
             }
+            if (e < m) {
+                const float4 v = s4[e];
+                pt += mh_dl32_pair_nt(v.x - tx, v.y - ty, v.z, v.w, c32);
+            }
+            pt += pu;
             const float t = ah + pt, bb = t - ah;
             al += (ah - (t - bb)) + (pt - bb);
             ah = t;
