@@ -369,10 +369,14 @@ KERNEL_REGIONS = {
                                         "MMAs; binary32 sources, operators and products)"),
     "dlp_fmm_contract_tc": ("hbm", None, "double-layer contractions on the tensor cores (k_contract_tc)"),
 }
-# DRAM bytes (read + write) per launch of the region's main kernel, from the ncu launch list
-# of the timed steps (profiles/launches_heat_step_starfish_mixed.md); None where not captured.
-NCU_TRAFFIC = {"dlp_near": 19.98e6, "dlp_fine": 2.10e6, "bie_gemv32": 151.15e6, "bie_gemvff": 201.53e6,
-               "dlp_coarse": 0.21e6}
+# Regions that time a whole phase of several kernels (tensor-core launch, CUDA-core chunks of the
+# operators with few tasks, ordered reduction): reported, but not candidates for the dominant
+# kernel, which is the single-kernel region with the most time per step.
+PHASE_REGIONS = {"volume_contract", "dlp_fmm_contract"}
+# DRAM bytes (read + write) per launch of a region's kernel, from one-kernel ncu captures of the
+# current kernels at the sizes the bench runs (dram__bytes_read.sum + dram__bytes_write.sum);
+# the tensor-core figure is the mean over the four volume launches of one potential.
+NCU_TRAFFIC = {"bie_gemv32": 154.16e6, "dlp_near": 19.97e6, "volume_contract_tc": 4.19e6}
 REGION_NAMES = tuple(KERNEL_REGIONS) + ("volume_apply", "dlp_fmm", "gmres", "dlp_evaluate", "warm_start", "warm_net",
                                         "bie_gemv64_gated")
 
@@ -405,7 +409,7 @@ def region_roofline(name, v, prec, mh, peaks):
 def roofline(regions_ms, tree, bnd, prob, prec, mh, peaks, steps):
     """Roofline of the dominant (longest) instrumented kernel region, and of every region."""
     cand = {k: v for k, v in regions_ms.items() if k in KERNEL_REGIONS and v[1] > 0}
-    name = max(cand, key=lambda k: cand[k][0])
+    name = max((k for k in cand if k not in PHASE_REGIONS), key=lambda k: cand[k][0])
     dom = region_roofline(name, cand[name], prec, mh, peaks)
     dom["all_regions"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
                               for kk, vv in region_roofline(k, v, prec, mh, peaks).items()

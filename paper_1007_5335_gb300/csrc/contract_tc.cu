@@ -42,9 +42,9 @@
 namespace {
 
 constexpr int TC_M = 128;         // tasks per CTA (rows of the MMA)
-constexpr int TC_THREADS = 256;   // 8 warps: gather and epilogue (two column halves)
+constexpr int TC_THREADS = 512;   // 16 warps: gather, epilogue (4 lane quarters x 4 column groups), output
 constexpr unsigned TC_SPIN = 1u << 22;   // polls of an mbarrier before a wait gives up
-constexpr int GATHER_IT = 4;     // warp items whose loads are issued together in the gather
+constexpr int GATHER_MAX = TC_M * (64 / 8) / TC_THREADS;   // gather items per thread and part (K <= 64)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -136,6 +136,58 @@ __host__ __device__ __forceinline__ uint32_t img_off(int row, int k, int rows) {
     return (uint32_t)((k >> 3) * (rows * 16) + (row >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
+// Row stride of the product staging tile: R itself when R is odd (the lanes of a warp, which
+// hold different rows, then hit distinct banks, and the tile is laid out like the product
+// block), R + 1 otherwise.
+__host__ __device__ __forceinline__ int stage_ld(int R) { return (R & 1) ? R : R + 1; }
+
+// Products of a chunk (nt tasks from t0) from the staging tile to global memory.
+//   temp form: one contiguous block temp[t0 R .. (t0 + nt) R); with stride R the tile is the
+//   block itself and is copied with aligned 16-byte stores;
+//   task_dst form: row t to dst[task_dst[t] ..], added when accumulate is set.
+template <typename TD>
+__device__ __forceinline__ void write_products(const float* __restrict__ stage_out, int ld, int R, int t0, int nt,
+                                               float* __restrict__ temp, const int64_t* __restrict__ task_dst,
+                                               int accumulate, TD* dst) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (!task_dst) {
+        float* out = temp + (int64_t)t0 * R;
+        const int ne = nt * R;
+        if (ld == R) {
+            // head up to a 16-byte boundary, aligned body, tail
+            const int head = min(ne, (int)((4 - ((reinterpret_cast<uintptr_t>(out) >> 2) & 3)) & 3));
+            if ((int)threadIdx.x < head) out[threadIdx.x] = stage_out[threadIdx.x];
+            const int nb = (ne - head) >> 2;
+            float4* o4 = reinterpret_cast<float4*>(out + head);
+            for (int b = threadIdx.x; b < nb; b += TC_THREADS) {
+                const float* sp = stage_out + head + 4 * b;
+                o4[b] = make_float4(sp[0], sp[1], sp[2], sp[3]);
+            }
+            for (int e = head + 4 * nb + threadIdx.x; e < ne; e += TC_THREADS) out[e] = stage_out[e];
+        } else {
+            const int dr = TC_THREADS % R, dm = TC_THREADS / R;
+            int mm = threadIdx.x / R, rr = threadIdx.x - mm * R;
+            for (int e = threadIdx.x; e < ne; e += TC_THREADS) {
+                out[e] = stage_out[mm * ld + rr];
+                rr += dr;
+                mm += dm;
+                if (rr >= R) {
+                    rr -= R;
+                    ++mm;
+                }
+            }
+        }
+    } else {
+        for (int mm = warp; mm < nt; mm += TC_THREADS / 32) {
+            TD* y = dst + task_dst[t0 + mm];
+            for (int rr = lane; rr < R; rr += 32) {
+                const float v = stage_out[mm * ld + rr];
+                y[rr] = accumulate ? y[rr] + (TD)v : (TD)v;
+            }
+        }
+    }
+}
+
 // One CTA per chunk of up to 128 tasks of one operator (see the file comment).
 //   img: operator images (parts 1, 2, 3, each npad x kpad bfloat16 in the layout above) at
 //        img_off_op[op] (bfloat16 elements); kpad[op]: the operator's K extent (C rounded up to
@@ -145,7 +197,7 @@ __host__ __device__ __forceinline__ uint32_t img_off(int row, int k, int rows) {
 //   given, then the products go to dst[task_dst[t] + r] (added when accumulate is set; TD =
 //   float for the expansion pool, double for the potentials).
 template <typename TD>
-__global__ void __launch_bounds__(TC_THREADS, 3) k_contract_tc(
+__global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc(
     const __nv_bfloat16* __restrict__ img, const int64_t* __restrict__ img_off_op, const int32_t* __restrict__ kpad_op,
     const int32_t* __restrict__ op_C, const int32_t* __restrict__ chunk_op, const int32_t* __restrict__ chunk_t0,
     const uint16_t* __restrict__ spl, int64_t plane, const int64_t* __restrict__ tc_src, int R, int npad, int kmax,
@@ -198,18 +250,25 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_contract_tc(
     // the sources: already split into three bfloat16 planes with 16-element rows (tc_split),
     // so the gather is 16-byte asynchronous copies (8 columns of one part of one row each;
     // rows past the chunk are zero-filled).  Consecutive threads take 8 rows of one column
-    // group, which fill one 128-byte line of the image: no bank conflicts.
+    // group, which fill one 128-byte line of the image: no bank conflicts.  A thread handles
+    // the same (row, column group) items in every part; their row offsets are read first,
+    // together, so the copies wait for one memory latency, not one per item.
     {
         const int groups = kp >> 3;
-        for (int part = 0; part < 3; ++part) {
-            int q = threadIdx.x >> 3;                  // (row group, column group) pair of the thread
+        int64_t roff[GATHER_MAX];
+        uint32_t soff[GATHER_MAX];
+        int nit = 0;
+        {
+            const int q = threadIdx.x >> 3;
             int rg = q / groups, cg = q - rg * groups;
             const int dq = (TC_THREADS >> 3) / groups, dc = (TC_THREADS >> 3) % groups;
-            for (int e = threadIdx.x; e < TC_M * groups; e += TC_THREADS) {
+#pragma unroll
+            for (int it = 0; it < GATHER_MAX; ++it) {
+                const int e = threadIdx.x + it * TC_THREADS;
                 const int m = rg * 8 + (threadIdx.x & 7);
-                const bool valid = m < nt;
-                const uint16_t* g = valid ? spl + part * plane + tc_src[t0 + m] + 8 * cg : spl;
-                cp_async16(smem_addr(sA + part * a_bytes + img_off(m, 8 * cg, TC_M)), g, valid ? 16u : 0u);
+                roff[it] = e < TC_M * groups && m < nt ? tc_src[t0 + m] + 8 * cg : -1;
+                soff[it] = img_off(m & (TC_M - 1), 8 * cg, TC_M);
+                nit += e < TC_M * groups;
                 rg += dq;
                 cg += dc;
                 if (cg >= groups) {
@@ -218,6 +277,12 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_contract_tc(
                 }
             }
         }
+        for (int part = 0; part < 3; ++part)
+#pragma unroll
+            for (int it = 0; it < GATHER_MAX; ++it)
+                if (it < nit)
+                    cp_async16(smem_addr(sA + part * a_bytes + soff[it]),
+                               roff[it] >= 0 ? spl + part * plane + roff[it] : spl, roff[it] >= 0 ? 16u : 0u);
         asm volatile("cp.async.wait_all;" ::: "memory");
     }
     fence_async_smem();   // the generic-proxy stores above become visible to the tensor cores
@@ -249,63 +314,41 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_contract_tc(
             mma_commit(mb_mma);
         }
     }
-    __syncthreads();
+    // thread 0 waits for the products (the others wait at the barrier, without issuing); the
+    // CTA goes on only if they came (the loads below are warp-collective)
+    bool mine = true;
+    if (threadIdx.x == 0) mine = ok && mbar_wait(mb_mma, 0);
+    const bool have = __syncthreads_and(mine) != 0;
     const bool copied = ok != 0;
-    // every thread waits for the products; the CTA goes on only if all saw them (the loads
-    // below are warp-collective)
-    const bool have = __syncthreads_and(copied && mbar_wait(mb_mma, 0)) != 0;
     if (copied && !have && threadIdx.x == 0) atomicExch(err, 2);
     tc_after_sync();
-    // products: TMEM -> shared staging rows (stride npad + 1: the lanes of a warp hold different
-    // rows) -> global, written as whole rows
+    // products: TMEM -> shared staging rows (stride stage_ld(R)) -> global, as whole rows
     float* stage = reinterpret_cast<float*>(sA);   // the source images are no longer read
-    const int ld = npad + 1;
+    const int ld = stage_ld(R);
     if (have) {
-        // warp w: tasks 32 (w % 4) + lane, columns [h * npad / 2, (h + 1) * npad / 2), h = w / 4
+        // warp w: tasks 32 (w % 4) + lane, column octets h, h + CG, ... (h = w / 4, CG =
+        // TC_THREADS / 128 column groups)
         const int m = 32 * (warp & 3) + lane;
-        const int half = npad >> 1;
-        const int c0 = (warp >> 2) * half;
-        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
-        for (int cc = 0; cc < half; cc += 8) {
+        const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        for (int cc = 8 * (warp >> 2); cc < npad; cc += 8 * (TC_THREADS / 128)) {
             uint32_t r[8], q[8];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                : "r"(taddr + (uint32_t)cc));
+                : "r"(trow + (uint32_t)cc));
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
                 : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7])
-                : "r"(taddr + (uint32_t)(npad + cc)));
+                : "r"(trow + (uint32_t)(npad + cc)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int u = 0; u < 8; ++u) stage[m * ld + c0 + cc + u] = __uint_as_float(r[u]) + __uint_as_float(q[u]);
+            for (int u = 0; u < 8; ++u)
+                if (cc + u < R) stage[m * ld + cc + u] = __uint_as_float(r[u]) + __uint_as_float(q[u]);
         }
     }
     __syncthreads();
     if (have) {
-        if (!task_dst) {
-            // the chunk's products are one contiguous block temp[t0 R .. (t0 + nt) R)
-            float* out = temp + (int64_t)t0 * R;
-            const int ne = nt * R, dr = TC_THREADS % R, dm = TC_THREADS / R;
-            int mm = threadIdx.x / R, rr = threadIdx.x - mm * R;
-            for (int e = threadIdx.x; e < ne; e += TC_THREADS) {
-                out[e] = stage[mm * ld + rr];
-                rr += dr;
-                mm += dm;
-                if (rr >= R) {
-                    rr -= R;
-                    ++mm;
-                }
-            }
-        } else {
-            for (int mm = warp; mm < nt; mm += TC_THREADS / 32) {
-                TD* y = dst + task_dst[t0 + mm];
-                for (int rr = lane; rr < R; rr += 32) {
-                    const float v = stage[mm * ld + rr];
-                    y[rr] = accumulate ? y[rr] + (TD)v : (TD)v;
-                }
-            }
-        }
+        write_products<TD>(stage, ld, R, t0, nt, temp, task_dst, accumulate, dst);
     } else if (threadIdx.x == 0 && !copied) {
         mbar_wait(mb_copy, 0);   // the copy may still be in flight: let it land (bounded)
     }
@@ -377,7 +420,7 @@ void tc_operator_image(const double* op, int R, int C, int npad, int kpad, uint1
 // staging rows that reuse them (128 x (npad + 1) binary32), plus 1 KB for the alignment.
 size_t tc_smem_bytes(int npad, int kmax) {
     const size_t images = (size_t)(3 * TC_M + 3 * npad) * kmax * 2;
-    const size_t stage = (size_t)TC_M * (npad + 1) * 4;
+    const size_t stage = (size_t)TC_M * stage_ld(npad) * 4;
     return (images > stage ? images : stage) + 1024;
 }
 
