@@ -546,7 +546,7 @@ struct Phase {
     dbuf<int32_t> tc_chunk_op, tc_chunk_t0;
 };
 
-constexpr int TC_MIN_TASKS = 16;   // operators with fewer tasks stay on the CUDA cores
+constexpr int TC_MIN_TASKS = 1;    // operators with fewer tasks stay on the CUDA cores
 constexpr int TC_POOL_PAD = 16;    // slack floats after the binary32 pool (aligned-window gathers)
 constexpr int TC_TASKS = 128;      // tasks per tensor-core chunk (rows of the MMA)
 
@@ -683,8 +683,10 @@ struct VolData {
     TcImages tc;                                      // tensor-core images (mixed precision)
 };
 
+// ranges: the split ranges of the pool (tensor-core sources); an operator takes the tensor-core
+// form only if every one of its tasks reads a whole vector of a range whose length is its C.
 mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumulate, const std::vector<int>& op_C,
-                      Phase* ph, int64_t* temp_need, bool tc_ok = true) {
+                      Phase* ph, int64_t* temp_need, const std::vector<TcImages::Range>* ranges = nullptr) {
     ph->R = R;
     ph->accumulate = accumulate;
     ph->n_tasks = (int64_t)tasks.size();
@@ -692,7 +694,17 @@ mh_status build_phase(mh_ctx* ctx, std::vector<Task>& tasks, int R, bool accumul
     std::map<int, int64_t> per_op;
     for (const Task& t : tasks) per_op[t.op] += 1;
     std::map<int, bool> on_tc;
-    for (auto& kv : per_op) on_tc[kv.first] = tc_ok && R <= 64 && kv.second >= TC_MIN_TASKS && op_C[kv.first] <= 64;
+    for (auto& kv : per_op)
+        on_tc[kv.first] = ranges && R <= 64 && kv.second >= TC_MIN_TASKS && op_C[kv.first] <= 64;
+    if (ranges)
+        for (const Task& t : tasks) {
+            if (!on_tc[t.op]) continue;
+            bool found = false;
+            for (const TcImages::Range& r : *ranges)
+                found = found || (r.len == op_C[t.op] && t.src >= r.src && t.src < r.src + r.count * r.len &&
+                                  (t.src - r.src) % r.len == 0);
+            if (!found) on_tc[t.op] = false;
+        }
     // sort by (CUDA-core form, operator), stable: keeps the generation order inside an operator
     // and puts the tensor-core operators' tasks first, so that both forms cover contiguous
     // ranges of the sorted tasks (the binary64 form runs over all of them)
@@ -1437,12 +1449,14 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
     MH_ALLOC(ctx, V->d_op_C, pool.C.size());
     MH_CUDA(ctx, cudaMemcpyAsync(V->d_op_off.p, pool.off.data(), pool.off.size() * 8, cudaMemcpyHostToDevice, st));
     MH_CUDA(ctx, cudaMemcpyAsync(V->d_op_C.p, pool.C.data(), pool.C.size() * 4, cudaMemcpyHostToDevice, st));
-    // phases
+    // phases; split ranges of the tensor-core sources: node values (B), multipoles (M), locals (L)
+    const std::vector<TcImages::Range> rg = {{V->B_off, qq, nl, 0, 0}, {V->M_off, P, nb, 0, 0},
+                                             {V->L_off, P, nb, 0, 0}};
     int64_t need = 1;
     V->p2m.reset(new Phase());
-    MH_TRY(build_phase(ctx, t_p2m, P, false, V->op_C, V->p2m.get(), &need));
+    MH_TRY(build_phase(ctx, t_p2m, P, false, V->op_C, V->p2m.get(), &need, &rg));
     V->m2l.reset(new Phase());
-    MH_TRY(build_phase(ctx, t_m2l, P, false, V->op_C, V->m2l.get(), &need));
+    MH_TRY(build_phase(ctx, t_m2l, P, false, V->op_C, V->m2l.get(), &need, &rg));
     // U^h = near (U list, written first) + far (L2P, M2P: added once the passes are done)
     {
         std::vector<char> has(t->n_leaves, 0);
@@ -1451,17 +1465,14 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
     }
     int64_t need_near = 1;
     V->near.reset(new Phase());
-    MH_TRY(build_phase(ctx, t_near, qq, false, V->op_C, V->near.get(), &need_near));
+    MH_TRY(build_phase(ctx, t_near, qq, false, V->op_C, V->near.get(), &need_near, &rg));
     V->near->dst_out = true;
     V->out.reset(new Phase());
-    MH_TRY(build_phase(ctx, t_out, qq, true, V->op_C, V->out.get(), &need));
+    MH_TRY(build_phase(ctx, t_out, qq, true, V->op_C, V->out.get(), &need, &rg));
     V->out->dst_out = true;
     {
         std::vector<int64_t> off(pool.off.begin(), pool.off.end());
         std::vector<int32_t> rr(pool.R.begin(), pool.R.end()), cc(pool.C.begin(), pool.C.end());
-        // split ranges: node values (B), multipoles (M), locals (L)
-        const std::vector<TcImages::Range> rg = {{V->B_off, qq, nl, 0, 0}, {V->M_off, P, nb, 0, 0},
-                                                 {V->L_off, P, nb, 0, 0}};
         MH_TRY(build_tc_images(ctx, all.data(), off, rr, cc, {V->p2m.get(), V->m2l.get(), V->near.get(), V->out.get()},
                                rg, &V->tc));
     }
@@ -1939,19 +1950,20 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
     MH_CUDA(ctx, cudaMemcpyAsync(D->d_op_off.p, pool.off.data(), pool.off.size() * 8, cudaMemcpyHostToDevice, st));
     MH_CUDA(ctx, cudaMemcpyAsync(D->d_op_C.p, pool.C.data(), pool.C.size() * 4, cudaMemcpyHostToDevice, st));
     std::vector<int> opC(pool.C.begin(), pool.C.end());
+    // split ranges of the tensor-core sources: dipole multipoles (DM), locals (DL); the dipole
+    // P2M / P2L operators (one task each, on the weights) stay on the CUDA cores
+    const std::vector<TcImages::Range> rg = {{D->DM_off, P, nb, 0, 0}, {D->DL_off, P, nb, 0, 0}};
     int64_t need = 1;
     D->p2m.reset(new Phase());
-    MH_TRY(build_phase(ctx, t_p2m, P, false, opC, D->p2m.get(), &need));
+    MH_TRY(build_phase(ctx, t_p2m, P, false, opC, D->p2m.get(), &need, &rg));
     D->m2l.reset(new Phase());
-    MH_TRY(build_phase(ctx, t_m2l, P, false, opC, D->m2l.get(), &need));
+    MH_TRY(build_phase(ctx, t_m2l, P, false, opC, D->m2l.get(), &need, &rg));
     D->out.reset(new Phase());
-    MH_TRY(build_phase(ctx, t_out, qq, !near_blocks, opC, D->out.get(), &need));
+    MH_TRY(build_phase(ctx, t_out, qq, !near_blocks, opC, D->out.get(), &need, &rg));
     D->out->dst_out = true;
     {
         std::vector<int64_t> off(pool.off.begin(), pool.off.end());
         std::vector<int32_t> rr(pool.R.begin(), pool.R.end()), cc(pool.C.begin(), pool.C.end());
-        // split ranges: dipole multipoles (DM), locals (DL)
-        const std::vector<TcImages::Range> rg = {{D->DM_off, P, nb, 0, 0}, {D->DL_off, P, nb, 0, 0}};
         MH_TRY(build_tc_images(ctx, pool.data.data(), off, rr, cc, {D->p2m.get(), D->m2l.get(), D->out.get()}, rg,
                                &D->tc));
     }
