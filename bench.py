@@ -669,6 +669,52 @@ def cpu_baseline(wl, budget_s=20.0, seed=11):
             "seconds_per_step_extrapolated": t_step, "wall_s": time.time() - t_start}
 
 
+def run_profile_case(args):
+    """One small fixed case of the starfish workload for a profiler (ncu -k ... -c ...), then
+    exit: no training, no timing, no JSON line.
+      volume   : the tree, then two mixed-precision volume potentials (tensor-core contractions,
+                 M2M / L2L chains);
+      operator : the boundary, then three binary32 operator products (k_gemv32s);
+      solve    : two mixed-precision GMRES solves (float-float residual products, k_gemv_cpa);
+      step     : three mixed-precision heat steps (near-field and upsampled-rule pair sums)."""
+    import torch
+    import paper_1007_5335_gb300 as mh
+    ctx = mh.Context(0)
+    wl = W.starfish_domain()
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(0)
+    if args.profile_case == "volume":
+        tree = mh.Tree(ctx, wl.box, wl.q, wl.min_level, wl.max_level, wl.forcing, wl.refine_tol)
+        b = torch.tensor(wl.forcing(tree.nodes().cpu().numpy()) * wl.dt, device=dev)
+        out = torch.empty_like(b)
+        for _ in range(2):
+            mh.mh_volume_potential(ctx, tree, wl.alpha, wl.p, b, out, prec=mh.MH_PREC_MIXED)
+        tree.check()
+    elif args.profile_case in ("operator", "solve"):
+        bnd = mh.Boundary(ctx, wl.curves, alpert_order=8)
+        x = torch.tensor(rng.standard_normal(bnd.n), device=dev)
+        out = torch.empty_like(x)
+        if args.profile_case == "operator":
+            for _ in range(3):
+                mh.mh_double_layer_apply(ctx, bnd, wl.alpha, x, out, prec=mh.MH_PREC_MIXED)
+        else:
+            for _ in range(2):
+                out.zero_()
+                mh.mh_gmres_solve(ctx, bnd, wl.alpha, x, out, tol=1e-10, prec=mh.MH_PREC_MIXED)
+    else:
+        tree, bnd, prob, nodes, F_np, _ = setup_problem(mh, ctx, wl, torch, dev)
+        F = torch.tensor(F_np, device=dev)
+        f = torch.zeros(bnd.n, dtype=torch.float64, device=dev)
+        u = torch.zeros(tree.n_nodes, dtype=torch.float64, device=dev)
+        un = torch.empty_like(u)
+        sig = torch.zeros(bnd.n, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            mh.heat_step(ctx, prob, u, F, f, un, sig, gmres_tol=1e-10, prec=mh.MH_PREC_MIXED)
+            u, un = un, u
+        tree.check()
+    torch.cuda.synchronize(dev)
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -717,10 +763,15 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--clocks-dir", default=None, help="directory for the raw clock samples (default: temp dir)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--profile-case", choices=["volume", "operator", "solve", "step"], default=None,
+                    help="run one small fixed case for a profiler and exit (see run_profile_case)")
     args = ap.parse_args()
     if args.clocks_dir:
         global CLOCKS_DIR
         CLOCKS_DIR = args.clocks_dir
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "ours" and args.workload == "batch":

@@ -414,7 +414,7 @@ __device__ __forceinline__ void ff_acc(float& sh, float& sl, float a, float al, 
 // limited by registers.  A lane reads back only the float4s it copied itself (no barrier).
 // M = 1: y = A32 x in binary32; M = 2: y = (A32 + A32lo)(xh + xl) in float-float (ff_acc).
 // n a multiple of 4; SPLIT warps per row, 8 / SPLIT rows per 256-thread block.
-constexpr int GC_PIECE = 12;
+constexpr int GC_PIECE = 3;   // float4 per lane and matrix per piece: 24 KB per block, up to 8 blocks per SM
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
@@ -1831,11 +1831,13 @@ static int gemv_blocks(int64_t n) {
 
 constexpr int GEMV_SPLIT = 4;   // warps per row of the row-split GEMVs
 
-constexpr size_t GC_SMEM2 = 8 * 2 * GC_PIECE * 32 * sizeof(float4);   // 96 KB
+constexpr size_t GC_SMEM2 = 8 * 2 * GC_PIECE * 32 * sizeof(float4);   // 24 KB
 
-// The binary32 GEMV keeps register loads (k_gemv32s, 29 us for the starfish operator); staging its
-// loads through cp.async measured slower (35 us).  The float-float product, with twice the bytes
-// per entry, gains from the staging (81 -> 70 us).
+// The binary32 GEMV keeps register loads (k_gemv32s, 28 us for the starfish operator); staging its
+// loads through cp.async measures the same (28.6 us).  The float-float product, with twice the
+// bytes per entry, gains from the staging (81 us with register loads; 53 us with pieces of 3
+// float4 per lane, where pieces of 12 took 64 us: a warp waits for its piece before it
+// computes, and small pieces leave room for 8 blocks per SM, so some compute while others load).
 static void gemv32(cudaStream_t st, const float* A, const float* x, double* y, int64_t n, const int* gate) {
     if ((n & 3) == 0)
         k_gemv32s<GEMV_SPLIT><<<(unsigned)((n + 8 / GEMV_SPLIT - 1) / (8 / GEMV_SPLIT)), 256, 0, st>>>(A, x, y, n,
