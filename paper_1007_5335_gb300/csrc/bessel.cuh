@@ -10,6 +10,8 @@
 // The library calls log, exp and rsqrt; it does not re-implement them.
 #pragma once
 
+#include <cmath>
+
 #include "bessel_coefs.h"
 
 __device__ __forceinline__ double mh_clenshaw(const double* c, int n, double x) {
@@ -107,6 +109,9 @@ struct mh_dl32 {
     float y_r2;      // 1/(4 alpha^2)
     float r2_small;  // (2 alpha)^2
     float r2_cut;    // (cut alpha)^2: farther pairs are below the binary32 rounding of a sum
+    float a4;        // 4 alpha
+    float ml2e_ia;   // -log2(e) / alpha
+    float a32;       // alpha^{3/2}
 };
 
 inline mh_dl32 mh_dl32_make(double alpha, double cut) {
@@ -116,8 +121,38 @@ inline mh_dl32 mh_dl32_make(double alpha, double cut) {
     c.y_r2 = (float)(0.25 / (alpha * alpha));
     c.r2_small = (float)(4.0 * alpha * alpha);
     c.r2_cut = (float)(cut * cut * alpha * alpha);
+    c.a4 = (float)(4.0 * alpha);
+    c.ml2e_ia = (float)(-1.4426950408889634 / alpha);
+    c.a32 = (float)(alpha * std::sqrt(alpha));
     return c;
 }
+
+// The hardware's approximate special-function instructions (PTX rsqrt / lg2 / ex2 .approx)
+// with subnormal inputs and results flushed to zero: the pair kernels' arguments are normal
+// (r^2 is floored at 1e-30, y = r^2/(4 alpha^2) > 0) and a flushed e^{-z} is a pair far below
+// the rounding of any sum, so the flush changes no result and saves the subnormal handling.
+// e^{-z} is 2^{-z log2(e)}.
+__device__ __forceinline__ float mh_rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float mh_lg2_ftz(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float mh_ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float mh_sqrt_ftz(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+#define MH_LOG2E_F 1.4426950408889634f   // log2(e)
 
 // g(z) for z <= 2 from y = z^2/4 and 1/z
 __device__ __forceinline__ float mh_k1oz_small_f(float y, float zinv) {
@@ -127,7 +162,7 @@ __device__ __forceinline__ float mh_k1oz_small_f(float y, float zinv) {
         b = fmaf(b, y, mh_k1oz_b_f[k]);
         if (k < MH_K1OZ_NA_F - 1) a = fmaf(a, y, mh_k1oz_a_f[k]);
     }
-    return fmaf(zinv, zinv, fmaf(__log2f(y), a, -b));
+    return fmaf(zinv, zinv, fmaf(mh_lg2_ftz(y), a, -b));
 }
 
 // g(z) for z > 2 from z and 1/z
@@ -136,7 +171,7 @@ __device__ __forceinline__ float mh_k1oz_large_f(float z, float zinv) {
     float m = mh_k1_mono_f[MH_K1_MONO_N32 - 1];
 #pragma unroll
     for (int k = MH_K1_MONO_N32 - 2; k >= 0; --k) m = fmaf(m, x, mh_k1_mono_f[k]);
-    return __expf(-z) * rsqrtf(z) * zinv * m;
+    return mh_ex2_ftz(-MH_LOG2E_F * z) * mh_rsqrt_ftz(z) * zinv * m;
 }
 
 // g(r/alpha) (dx nx + dy ny) for the offset (dx, dy) of a source from a target, without the
@@ -145,7 +180,7 @@ __device__ __forceinline__ float mh_k1oz_large_f(float z, float zinv) {
 // of any sum (e^{-z} underflows).  For loops whose pairs are near by construction.
 __device__ __forceinline__ float mh_dl32_pair_nt(float dx, float dy, float nx, float ny, const mh_dl32& c) {
     const float r2 = fmaxf(fmaf(dx, dx, dy * dy), 1e-30f);
-    const float rinv = rsqrtf(r2);
+    const float rinv = mh_rsqrt_ftz(r2);
     const float zinv = c.a * rinv;
     const float g = r2 <= c.r2_small ? mh_k1oz_small_f(r2 * c.y_r2, zinv)
                                      : mh_k1oz_large_f(r2 * rinv * c.ia, zinv);
@@ -156,10 +191,25 @@ __device__ __forceinline__ float mh_dl32_pair_nt(float dx, float dy, float nx, f
 // coincident points and beyond the cut.
 __device__ __forceinline__ float mh_dl32_pair(float dx, float dy, float nx, float ny, const mh_dl32& c) {
     const float r2 = fmaf(dx, dx, dy * dy);
-    if (!(r2 > 0.f && r2 <= c.r2_cut)) return 0.f;
-    const float rinv = rsqrtf(r2);
+    if (!(r2 >= 1e-30f && r2 <= c.r2_cut)) return 0.f;   // r < 1e-15: coincident in binary32 offsets
+    const float rinv = mh_rsqrt_ftz(r2);
     const float zinv = c.a * rinv;
     const float g = r2 <= c.r2_small ? mh_k1oz_small_f(r2 * c.y_r2, zinv)
                                      : mh_k1oz_large_f(r2 * rinv * c.ia, zinv);
     return g * fmaf(dx, nx, dy * ny);
+}
+
+// g(r/alpha) (dx nx + dy ny) / alpha^{3/2} for a pair known to have r > 2 alpha (no branch):
+// with z = r/alpha, e^{-z} z^{-3/2} = alpha^{3/2} e^{-r/alpha} r^{-3/2}, so the pair needs no
+// z and no 1/z: x = 4 alpha / r - 1, e^{-z} = 2^{-log2(e) r / alpha}, r^{-3/2} = r^{-1}
+// sqrt(1/r).  Callers multiply their sums by alpha^{3/2} (c.a32).
+__device__ __forceinline__ float mh_dl32_pair_far(float dx, float dy, float nx, float ny, const mh_dl32& c) {
+    const float r2 = fmaf(dx, dx, dy * dy);
+    const float rinv = mh_rsqrt_ftz(r2);
+    const float x = fmaf(c.a4, rinv, -1.f);
+    float m = mh_k1_mono_f[MH_K1_MONO_N32 - 1];
+#pragma unroll
+    for (int k = MH_K1_MONO_N32 - 2; k >= 0; --k) m = fmaf(m, x, mh_k1_mono_f[k]);
+    const float e = mh_ex2_ftz(r2 * rinv * c.ml2e_ia);
+    return e * mh_sqrt_ftz(rinv) * rinv * m * fmaf(dx, nx, dy * ny);
 }

@@ -685,6 +685,50 @@ __global__ void k_sum_partials(const double* __restrict__ part, int nsplit, int6
     out[t] = pref * s;
 }
 
+// One warp's pairs of a fine chunk (MH_TILE nodes from f0, m of them present) against TG targets
+// at offsets (dx0, dy0) from the chunk centre: pt[j] = sum over the lane's nodes.  FAR: every
+// pair has r > 2 alpha (mh_dl32_pair_far, the alpha^{3/2} applied to the sums).
+template <int TG, bool FAR>
+__device__ __forceinline__ void fine_chunk(const float4* __restrict__ fine32, const float* __restrict__ wf, int64_t f0,
+                                           int m, int lane, const float* dx0, const float* dy0, const mh_dl32& c32,
+                                           float* pt) {
+#pragma unroll
+    for (int j = 0; j < TG; ++j) pt[j] = 0.f;
+    auto pair = [&](float dx, float dy, float nx, float ny) {
+        return FAR ? mh_dl32_pair_far(dx, dy, nx, ny, c32) : mh_dl32_pair_nt(dx, dy, nx, ny, c32);
+    };
+    if (m == MH_TILE) {
+        // a whole chunk: every lane's MH_TILE / 32 nodes are loaded before the first pair, so the
+        // loads are in flight together
+        constexpr int U = MH_TILE / 32;
+        float4 v[U];
+        float w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            v[u] = fine32[f0 + lane + 32 * u];
+            w[u] = wf[f0 + lane + 32 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float nx = v[u].z * w[u], ny = v[u].w * w[u];
+#pragma unroll
+            for (int j = 0; j < TG; ++j) pt[j] += pair(v[u].x - dx0[j], v[u].y - dy0[j], nx, ny);
+        }
+    } else {
+        for (int i = lane; i < m; i += 32) {
+            const float4 v = fine32[f0 + i];
+            const float w = wf[f0 + i];
+            const float nx = v.z * w, ny = v.w * w;
+#pragma unroll
+            for (int j = 0; j < TG; ++j) pt[j] += pair(v.x - dx0[j], v.y - dy0[j], nx, ny);
+        }
+    }
+    if (FAR) {
+#pragma unroll
+        for (int j = 0; j < TG; ++j) pt[j] *= c32.a32;
+    }
+}
+
 // Upsampled rule in binary32 at the auxiliary points of the normal-line rule.  One block per
 // (group of TG auxiliary targets on curve k, slice of the curve's fine chunks); each warp takes
 // one chunk (MH_TILE fine nodes) at a time and every lane evaluates its nodes against all TG
@@ -701,6 +745,7 @@ __global__ void __launch_bounds__(256) k_dlp_fine32_grp(
     const float* __restrict__ crad, mh_dl32 c32, float cut_r, double pref, double* part, unsigned* cnt,
     double* out) {
     __shared__ double red[8][TG];
+    const float two_a = 2.0001f * c32.a;   // beyond: z > 2 with a margin for the rounding of d2
     __shared__ int last;
     const int grp = blockIdx.x / slices, sl = blockIdx.x % slices;
     const int k = grp_curve[grp];
@@ -726,28 +771,27 @@ __global__ void __launch_bounds__(256) k_dlp_fine32_grp(
     for (int64_t ch = c0 + warp; ch < c1; ch += nw) {
         const float4 c = ccf[ch];
         const float lim = cut_r + crad[ch];
+        const float flim = two_a + crad[ch];
         float dx0[TG], dy0[TG];
-        bool near = false;
+        bool near = false, far = true;
 #pragma unroll
         for (int j = 0; j < TG; ++j) {
             dx0[j] = (txh[j] - c.x) + (txl[j] - c.y);
             dy0[j] = (tyh[j] - c.z) + (tyl[j] - c.w);
-            near |= fmaf(dx0[j], dx0[j], dy0[j] * dy0[j]) <= lim * lim;
+            const float d2 = fmaf(dx0[j], dx0[j], dy0[j] * dy0[j]);
+            near |= d2 <= lim * lim;
+            far &= d2 > flim * flim;
         }
         if (!near) continue;   // the same for the whole warp
         const int64_t f0 = foff[k] + (ch - coff[k]) * MH_TILE;
         const int m = (int)min((int64_t)MH_TILE, fend - f0);
         float pt[TG];
-#pragma unroll
-        for (int j = 0; j < TG; ++j) pt[j] = 0.f;
-        for (int i = lane; i < m; i += 32) {
-            const float4 v = fine32[f0 + i];
-            const float w = wf[f0 + i];
-            const float nx = v.z * w, ny = v.w * w;
-            // the chunk is within the cut of some target of the group: no per-pair tests
-#pragma unroll
-            for (int j = 0; j < TG; ++j) pt[j] += mh_dl32_pair_nt(v.x - dx0[j], v.y - dy0[j], nx, ny, c32);
-        }
+        // the chunk is within the cut of some target of the group: no per-pair tests; if it is
+        // beyond 2 alpha of every target, every pair takes the z > 2 form without a branch
+        if (far)
+            fine_chunk<TG, true>(fine32, wf, f0, m, lane, dx0, dy0, c32, pt);
+        else
+            fine_chunk<TG, false>(fine32, wf, f0, m, lane, dx0, dy0, c32, pt);
 #pragma unroll
         for (int j = 0; j < TG; ++j) {   // TwoSum: hi + lo += pt exactly up to the rounding of lo
             const float s = hi[j] + pt[j];
