@@ -130,7 +130,6 @@ struct tc_launch {
 int tc_pad_rows(int R);
 int tc_pad_cols(int C);
 void tc_operator_image(const double* op, int R, int C, int npad, int kpad, uint16_t* out);
-size_t tc_smem_bytes(int npad, int kmax);
 mh_status tc_prepare(mh_ctx* ctx);
 mh_status tc_contract_launch(mh_ctx* ctx, const tc_launch& a);
 // Split count binary32 vectors of length len at src into the three bfloat16 planes at dst
