@@ -376,8 +376,8 @@ PHASE_REGIONS = {"volume_contract", "dlp_fmm_contract"}
 # DRAM bytes (read + write) per launch of a region's kernel, from one-kernel ncu captures of the
 # current kernels at the sizes the bench runs (dram__bytes_read.sum + dram__bytes_write.sum);
 # the tensor-core figure is the mean over the four volume launches of one potential.
-NCU_TRAFFIC = {"bie_gemv32": 153.77e6, "bie_gemvff": 305.35e6, "dlp_near": 19.98e6, "dlp_fine": 2.10e6,
-               "volume_contract_tc": 4.70e6}
+NCU_TRAFFIC = {"bie_gemv32": 153.77e6, "bie_gemvff": 305.35e6, "dlp_near": 19.97e6, "dlp_fine": 2.12e6,
+               "volume_contract_tc": 4.71e6}
 REGION_NAMES = tuple(KERNEL_REGIONS) + ("volume_apply", "dlp_fmm", "gmres", "dlp_evaluate", "warm_start", "warm_net",
                                         "bie_gemv64_gated")
 
