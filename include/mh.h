@@ -245,6 +245,18 @@ mh_status heat_step(mh_ctx* ctx, mh_problem* prob, const double* u_dev, const do
                     const double* f_next_dev, const double* b_ext_dev, double* u_next_dev,
                     double* sigma_dev, double gmres_tol, mh_precision prec, mh_step_info* info);
 
+/* One IMEX Euler step of the Allen-Cahn equation u_t - eps Lap u = u (1 - u^2) (Section 4,
+ * Example 3), the reaction term explicit:
+ *   u^{N+1} - eps dt Lap u^{N+1} = B = u^N + dt u^N (1 - (u^N)^2)   in Omega,
+ * u^{N+1} = f_next on Gamma.  With time rescaled by eps this is heat_step with step eps dt and
+ * forcing u (1 - u^2) / eps, so prob must be created with dt = eps * dt (MH_SCHEME_IMEX_EULER:
+ * alpha^2 = eps dt); eps > 0 is passed here.  Outside Omega B is C_k + dt C_k (1 - C_k^2)
+ * (MH_EXT_CONST, u = C_k there) or b_ext_dev (MH_EXT_ARRAY); the rest of the step, the
+ * arguments and the error behaviour are those of heat_step.  u_dev and u_next_dev may alias. */
+mh_status allen_cahn_step(mh_ctx* ctx, mh_problem* prob, double eps, const double* u_dev,
+                          const double* f_next_dev, const double* b_ext_dev, double* u_next_dev,
+                          double* sigma_dev, double gmres_tol, mh_precision prec, mh_step_info* info);
+
 /* One extrapolated Gear step (Section 2) on a problem created with MH_SCHEME_EXTRAP_GEAR:
  * B = 4/3 u - 1/3 u_prev + dt (4/3 F - 2/3 F_prev) inside Omega, C_k + dt (4/3 F -
  * 2/3 F_prev) outside (MH_EXT_CONST) or b_ext_dev (MH_EXT_ARRAY); the rest as heat_step.

@@ -14,6 +14,13 @@ solved as U = U^p + U^h (Section 2):
 The volume operator is passed in as a callable so that uniform trees can use
 the dense cached operator and adaptive trees the direct sum.
 
+The Allen-Cahn equation of Section 4, Example 3, u_t - eps Lap u = u (1 - u^2), with the
+reaction term explicit is ``allen_cahn_step``: alpha^2 = eps dt and
+    B = u^N + dt u^N (1 - (u^N)^2),
+outside Omega C_k + dt C_k (1 - C_k^2) (u = C_k there); the rest of the step is the same.
+Pin: far from Gamma (d >> alpha) the step is the free-space resolvent of B,
+u^{N+1} = B + alpha^2 Lap B + O(alpha^4), on a smooth u^N.
+
 The extrapolated Gear step (Section 2, the display after eq. mod_helm_forced) is
 ``heat_step_gear``: alpha^2 = 2 dt / 3 and
     B = 4/3 u^N - 1/3 u^{N-1} + 4/3 dt F^N - 2/3 dt F^{N-1},
@@ -66,6 +73,20 @@ def heat_step_gear(pb: Problem, u, u_prev, F, F_prev, f_next, b_ext=None, sigma0
     out = ~pb.inside
     if pb.ext_mode == "const":
         B[out] = np.asarray(pb.ext_const)[region[out]] + forcing[out]
+    else:
+        B[out] = b_ext[out]
+    return _solve(pb, B, f_next, sigma0)
+
+
+def allen_cahn_step(pb: Problem, u, f_next, b_ext=None, sigma0=None):
+    """IMEX Euler for u_t - eps Lap u = u (1 - u^2) (pb.alpha^2 must be eps pb.dt): returns
+    (u_next, sigma, iterations)."""
+    region = pb.info.region
+    B = u + pb.dt * u * (1.0 - u * u)
+    out = ~pb.inside
+    if pb.ext_mode == "const":
+        c = np.asarray(pb.ext_const, dtype=float)[region[out]]
+        B[out] = c + pb.dt * c * (1.0 - c * c)
     else:
         B[out] = b_ext[out]
     return _solve(pb, B, f_next, sigma0)

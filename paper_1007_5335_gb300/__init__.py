@@ -82,6 +82,7 @@ _SIGS = {
     "mh_problem_regions": [_p, _p, _p],
     "mh_problem_rhs": [_p, _p, _p],
     "heat_step": [_p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
+    "allen_cahn_step": [_p, _p, _d, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
     "heat_step_gear": [_p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
     "mh_gmres_solve_static": [_p, _p, _d, _p, _p, _d, _i, ctypes.POINTER(GmresInfo)],
     "mh_net_create": [_p, _p, _i, _i, ctypes.POINTER(_p)],
@@ -385,6 +386,16 @@ def heat_step_gear(ctx: Context, prob: Problem, u, u_prev, F, F_prev, f_next, u_
     ctx.check(_lib.heat_step_gear(ctx.h, prob.h, _ptr(u), _ptr(u_prev), _ptr(F), _ptr(F_prev), _ptr(f_next),
                                   _ptr(b_ext), _ptr(u_next), _ptr(sigma), float(gmres_tol), int(prec),
                                   ctypes.byref(info)))
+    return info
+
+
+def allen_cahn_step(ctx: Context, prob: Problem, eps: float, u, f_next, u_next, sigma, b_ext=None,
+                    gmres_tol: float = 1e-10, prec: int = MH_PREC_FP64) -> StepInfo:
+    """One IMEX Euler step of u_t - eps Lap u = u (1 - u^2); prob created with dt = eps * dt."""
+    _step_sizes(prob, (u, u_next, b_ext), (f_next, sigma))
+    info = StepInfo()
+    ctx.check(_lib.allen_cahn_step(ctx.h, prob.h, float(eps), _ptr(u), _ptr(f_next), _ptr(b_ext), _ptr(u_next),
+                                   _ptr(sigma), float(gmres_tol), int(prec), ctypes.byref(info)))
     return info
 
 

@@ -28,6 +28,27 @@ __global__ void k_form_B(const double* __restrict__ u, const double* __restrict_
     B[i] = v;
 }
 
+// Allen-Cahn right-hand side (Section 4, Example 3): B = u + dt u (1 - u^2) inside Omega; outside
+// the constant extension C_k + dt C_k (1 - C_k^2) (u = C_k there) or caller-supplied values.
+__global__ void k_form_B_allen_cahn(const double* __restrict__ u, const int32_t* __restrict__ region,
+                                    const double* __restrict__ ext_const, const double* __restrict__ b_ext,
+                                    int ext_mode, double dt, int64_t n, double* B) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = region[i];
+    double v;
+    if (r < 0) {
+        const double a = u[i];
+        v = a + dt * a * (1.0 - a * a);
+    } else if (ext_mode == MH_EXT_CONST) {
+        const double c = ext_const[r];
+        v = c + dt * c * (1.0 - c * c);
+    } else {
+        v = b_ext[i];
+    }
+    B[i] = v;
+}
+
 __global__ void k_form_B_gear(const double* __restrict__ u, const double* __restrict__ up, const double* __restrict__ F,
                               const double* __restrict__ Fp, const int32_t* __restrict__ region,
                               const double* __restrict__ ext_const, const double* __restrict__ b_ext, int ext_mode,
@@ -417,6 +438,26 @@ extern "C" mh_status heat_step_gear(mh_ctx* ctx, mh_problem* prob, const double*
     k_form_B_gear<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(u_dev, u_prev_dev, F_dev, F_prev_dev, P->region.p,
                                                             P->d_ext_const.p, b_ext_dev, P->ext_mode, P->dt, n,
                                                             P->B.p);
+    MH_LAUNCHED(ctx);
+    return step_solve(ctx, P, f_next_dev, u_next_dev, sigma_dev, gmres_tol, prec, info);
+}
+
+extern "C" mh_status allen_cahn_step(mh_ctx* ctx, mh_problem* prob, double eps, const double* u_dev,
+                                     const double* f_next_dev, const double* b_ext_dev, double* u_next_dev,
+                                     double* sigma_dev, double gmres_tol, mh_precision prec, mh_step_info* info) {
+    if (!ctx || !prob || !u_dev || !f_next_dev || !u_next_dev || !sigma_dev)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    ProblemImpl* P = static_cast<ProblemImpl*>(prob);
+    if (P->scheme != MH_SCHEME_IMEX_EULER)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "allen_cahn_step needs a problem created with MH_SCHEME_IMEX_EULER");
+    if (!(eps > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "eps must be positive");
+    if (P->ext_mode == MH_EXT_ARRAY && !b_ext_dev)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "MH_EXT_ARRAY needs b_ext_dev");
+    if (!(gmres_tol > 0)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "gmres_tol must be positive");
+    const int64_t n = P->tree->n_nodes;
+    // the problem's dt is eps * dt (alpha^2 = eps dt): the time step itself is dt / eps
+    k_form_B_allen_cahn<<<mh_grid(n, 256), 256, 0, ctx->stream>>>(u_dev, P->region.p, P->d_ext_const.p, b_ext_dev,
+                                                                  P->ext_mode, P->dt / eps, n, P->B.p);
     MH_LAUNCHED(ctx);
     return step_solve(ctx, P, f_next_dev, u_next_dev, sigma_dev, gmres_tol, prec, info);
 }
