@@ -354,10 +354,10 @@ def run_ours(args):
 # algorithmic work it declares per launch: GEMV 4n^2 + 12n bytes (binary32) / 2n^2 flop;
 # pair sums 68 flop per pair; contractions 2 R C flop per task.
 KERNEL_REGIONS = {
-    "bie_gemv32": ("hbm", None, "Nystrom operator GEMV, binary32 (Arnoldi iterations, line rule)"),
+    "bie_gemv32": ("hbm", None, "Nystrom operator GEMV, binary32 (Arnoldi iterations)"),
     "bie_gemv64": ("alu", "fp64", "Nystrom operator GEMV, binary64 (residuals, learned-start judge)"),
-    "bie_gemvff": ("hbm", None, "Nystrom operator GEMV, float-float on A32 + A32lo (mixed-precision residuals, "
-                                "learned-start judge)"),
+    "bie_gemvff": ("hbm", None, "Nystrom operator GEMV, float-float on A32 + a binary16 low part (mixed-precision "
+                                "residuals, learned-start judge)"),
     "dlp_near": ("alu", "auto", "double-layer near-field pair sums (fine dipoles of neighbour leaves)"),
     "dlp_fine": ("alu", "auto", "16x upsampled pair sums at the normal-line auxiliary points"),
     "dlp_coarse": ("alu", "auto", "trapezoid pair sums"),
@@ -376,7 +376,7 @@ PHASE_REGIONS = {"volume_contract", "dlp_fmm_contract"}
 # DRAM bytes (read + write) per launch of a region's kernel, from one-kernel ncu captures of the
 # current kernels at the sizes the bench runs (dram__bytes_read.sum + dram__bytes_write.sum);
 # the tensor-core figure is the mean over the four volume launches of one potential.
-NCU_TRAFFIC = {"bie_gemv32": 153.77e6, "bie_gemvff": 305.35e6, "dlp_near": 19.97e6, "dlp_fine": 2.12e6,
+NCU_TRAFFIC = {"bie_gemv32": 153.77e6, "bie_gemvff": 230.31e6, "dlp_near": 19.97e6, "dlp_fine": 2.12e6,
                "volume_contract_tc": 4.71e6}
 REGION_NAMES = tuple(KERNEL_REGIONS) + ("volume_apply", "dlp_fmm", "gmres", "dlp_evaluate", "warm_start", "warm_net",
                                         "bie_gemv64_gated")

@@ -6,6 +6,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <cuda_fp16.h>
+
 #include "alpert_rule.h"
 #include "bessel.cuh"
 #include "mh_internal.cuh"
@@ -271,6 +273,15 @@ __global__ void k_split_lo(const double* __restrict__ a, const float* __restrict
         lo[i] = (float)(a[i] - (double)hi[i]);
 }
 
+// Low part of the binary64 operator in binary16: lo16 = (a - hi) 2^24 rounded to nearest
+// (the difference is exact in binary64, the scaling by a power of two too, so the only
+// rounding is the final one to binary16).
+__global__ void k_split_lo16(const double* __restrict__ a, const float* __restrict__ hi, uint16_t* __restrict__ lo,
+                             int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        lo[i] = __half_as_ushort(__double2half((a[i] - (double)hi[i]) * 16777216.0));
+}
+
 // x = xh + xl with xh = x rounded to binary32
 __global__ void k_split_vec(const double* __restrict__ x, float* __restrict__ xh, float* __restrict__ xl, int64_t n) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -504,6 +515,86 @@ __global__ void __launch_bounds__(256) k_gemv_cpa(const float* __restrict__ A, c
             for (int k = 1; k < SPLIT; ++k) t += (double)part[0][warp + k] + (double)part[1][warp + k];
             y[row] = t;
         }
+    }
+}
+
+// The float-float product with the low part in binary16: y = (A32 + 2^-24 A16)(xh + xl), 6
+// bytes per entry instead of 8.  Each piece of a warp's quarter row is copied by cp.async
+// as contiguous 512-byte runs (binary32 part: 2 GH_PIECE float4 per lane; binary16 part:
+// GH_PIECE 16-byte groups of 8 entries per lane); lane l then takes binary32 float4 j = l +
+// 32 v and the four binary16 entries of the same columns (8 bytes at j * 8 of the binary16
+// run, copied by another lane: the warp waits for all its copies first).  n a multiple of 8.
+constexpr int GH_PIECE = 2;   // 16-byte groups of binary16 per lane per piece: 24 KB per block
+
+template <int SPLIT>
+__global__ void __launch_bounds__(256) k_gemv_cph(const float* __restrict__ A, const uint16_t* __restrict__ Ah,
+                                                  const float* __restrict__ xh, const float* __restrict__ xl,
+                                                  double* __restrict__ y, int64_t n, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    extern __shared__ __align__(16) float4 gc_stage[];   // [warp][3 GH_PIECE * 32]
+    __shared__ float part[2][8];
+    constexpr float SCALE = 5.9604644775390625e-08f;   // 2^-24
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* stA = gc_stage + (size_t)warp * 3 * GH_PIECE * 32;   // 2 GH_PIECE * 32 float4
+    float4* stH = stA + 2 * GH_PIECE * 32;                       // GH_PIECE * 32 groups of 8 binary16
+    const uint2* stH2 = reinterpret_cast<const uint2*>(stH);
+    const int64_t row = (int64_t)blockIdx.x * (8 / SPLIT) + warp / SPLIT;
+    const int q = warp % SPLIT;
+    float hi = 0.f, lo = 0.f;
+    if (row < n) {
+        const int64_t n8 = n >> 3;
+        const int64_t c0 = q * n8 / SPLIT, c1 = (q + 1) * n8 / SPLIT;   // column octets of the quarter
+        const float4* a4 = reinterpret_cast<const float4*>(A + row * n);
+        const float4* h8 = reinterpret_cast<const float4*>(Ah + row * n);
+        const float4* xh4 = reinterpret_cast<const float4*>(xh);
+        const float4* xl4 = reinterpret_cast<const float4*>(xl);
+        for (int64_t p0 = c0; p0 < c1; p0 += GH_PIECE * 32) {
+#pragma unroll
+            for (int v = 0; v < 2 * GH_PIECE; ++v) {
+                const int j = lane + 32 * v;
+                if (2 * p0 + j < 2 * c1) cp_async16(stA + j, a4 + 2 * p0 + j);
+            }
+#pragma unroll
+            for (int u = 0; u < GH_PIECE; ++u) {
+                const int o = lane + 32 * u;
+                if (p0 + o < c1) cp_async16(stH + o, h8 + p0 + o);
+            }
+            cp_async_wait_all();
+            __syncwarp();   // the binary16 groups were copied by other lanes
+#pragma unroll
+            for (int v = 0; v < 2 * GH_PIECE; ++v) {
+                const int j = lane + 32 * v;
+                if (2 * p0 + j < 2 * c1) {
+                    const float4 av = stA[j];
+                    const uint2 hv = stH2[j];
+                    const float2 l01 = __half22float2(*reinterpret_cast<const __half2*>(&hv.x));
+                    const float2 l23 = __half22float2(*reinterpret_cast<const __half2*>(&hv.y));
+                    const float4 uv = __ldg(xh4 + 2 * p0 + j), vv = __ldg(xl4 + 2 * p0 + j);
+                    ff_acc(hi, lo, av.x, l01.x * SCALE, uv.x, vv.x);
+                    ff_acc(hi, lo, av.y, l01.y * SCALE, uv.y, vv.y);
+                    ff_acc(hi, lo, av.z, l23.x * SCALE, uv.z, vv.z);
+                    ff_acc(hi, lo, av.w, l23.y * SCALE, uv.w, vv.w);
+                }
+            }
+            __syncwarp();   // the next piece reuses the warp's stage
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float t = hi + oh, bb = t - hi;
+        lo += ((hi - (t - bb)) + (oh - bb)) + ol;
+        hi = t;
+    }
+    if (lane == 0) {
+        part[0][warp] = hi;
+        part[1][warp] = lo;
+    }
+    __syncthreads();
+    if (q == 0 && lane == 0 && row < n) {
+        double t = (double)part[0][warp] + (double)part[1][warp];
+        for (int k = 1; k < SPLIT; ++k) t += (double)part[0][warp + k] + (double)part[1][warp + k];
+        y[row] = t;
     }
 }
 
@@ -1822,6 +1913,7 @@ mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha) {
     MH_ALLOC(ctx, b->op.A64, n * n);
     b->op.A32.release();
     b->op.A32lo.release();
+    b->op.A16lo.release();
     b->op.alpha = -1.0;
     cudaStream_t st = ctx->stream;
     dim3 grid((unsigned)mh_grid(n, 256), (unsigned)std::min<int64_t>(n, 65535));
@@ -1848,10 +1940,16 @@ static mh_status ensure_fp32(mh_ctx* ctx, mh_boundary* b) {
     MH_ALLOC(ctx, b->op.A32, nn);
     k_to_float<<<152 * 8, 256, 0, ctx->stream>>>(b->op.A64.p, b->op.A32.p, nn);
     MH_LAUNCHED(ctx);
-    if ((b->n & 3) == 0) {   // float-float residual products (mixed precision)
+    if ((b->n & 7) == 0) {   // float-float residual products (mixed precision), binary16 low part
+        MH_ALLOC(ctx, b->op.A16lo, nn);
+        k_split_lo16<<<152 * 8, 256, 0, ctx->stream>>>(b->op.A64.p, b->op.A32.p, b->op.A16lo.p, nn);
+        MH_LAUNCHED(ctx);
+    } else if ((b->n & 3) == 0) {   // float-float residual products, binary32 low part
         MH_ALLOC(ctx, b->op.A32lo, nn);
         k_split_lo<<<152 * 8, 256, 0, ctx->stream>>>(b->op.A64.p, b->op.A32.p, b->op.A32lo.p, nn);
         MH_LAUNCHED(ctx);
+    }
+    if (b->op.A16lo.p || b->op.A32lo.p) {
         if (!b->xhi32.p) {
             MH_ALLOC(ctx, b->xhi32, b->n);
             MH_ALLOC(ctx, b->xlo32, b->n);
@@ -1876,7 +1974,11 @@ static int gemv_blocks(int64_t n) {
 constexpr int GEMV_SPLIT = 4;   // warps per row of the row-split GEMVs
 
 constexpr size_t GC_SMEM2 = 8 * 2 * GC_PIECE * 32 * sizeof(float4);   // 24 KB
+constexpr size_t GH_SMEM = 8 * 3 * GH_PIECE * 32 * sizeof(float4);    // 24 KB
 
+// The float-float product with the binary16 low part (k_gemv_cph): 47.6 us for the starfish
+// operator in ncu (226 MB), against 55.5 us for the binary32 low part (302 MB); capping it at 6
+// blocks per SM (40 registers) took 62.5 us.
 // The binary32 GEMV keeps register loads (k_gemv32s, 28 us for the starfish operator); staging its
 // loads through cp.async measures the same (28.6 us).  The float-float product, with twice the
 // bytes per entry, gains from the staging (81 us with register loads; 53 us with pieces of 3
@@ -1896,6 +1998,8 @@ static mh_status gemv_cpa_prepare(mh_ctx* ctx) {
     if (done) return MH_OK;
     MH_CUDA(ctx, cudaFuncSetAttribute(k_gemv_cpa<GEMV_SPLIT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)GC_SMEM2));
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_gemv_cph<GEMV_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)GH_SMEM));
     done = true;
     return MH_OK;
 }
@@ -1909,10 +2013,11 @@ static void gemv64(cudaStream_t st, const double* A, const double* x, double* y,
 }
 
 // Product with the binary64 operator for a residual: in mixed precision a float-float product
-// on A32 + A32lo (when prepared: N_Gamma a multiple of 4), else binary64.  The float-float
+// on A32 + 2^-24 A16lo (N_Gamma a multiple of 8) or A32 + A32lo (a multiple of 4), else
+// binary64.  The float-float
 // form first splits x into binary32 hi + lo (resid_split), then runs the GEMV (resid_gemv);
 // the two are separate so that a timed region can hold the GEMV alone.
-static bool resid_ff(const mh_boundary* b, bool mixed) { return mixed && b->op.A32lo.p; }
+static bool resid_ff(const mh_boundary* b, bool mixed) { return mixed && (b->op.A16lo.p || b->op.A32lo.p); }
 
 static void resid_split(cudaStream_t st, mh_boundary* b, const double* x) {
     k_split_vec<<<mh_grid(b->n, 256), 256, 0, st>>>(x, b->xhi32.p, b->xlo32.p, b->n);
@@ -1920,9 +2025,13 @@ static void resid_split(cudaStream_t st, mh_boundary* b, const double* x) {
 
 static void resid_gemv(cudaStream_t st, mh_boundary* b, const double* x, double* y, const int* gate, bool mixed) {
     const int64_t n = b->n;
-    if (resid_ff(b, mixed))
-        k_gemv_cpa<GEMV_SPLIT, 2><<<(unsigned)((n + 8 / GEMV_SPLIT - 1) / (8 / GEMV_SPLIT)), 256, GC_SMEM2, st>>>(
-            b->op.A32.p, b->op.A32lo.p, b->xhi32.p, b->xlo32.p, y, n, gate);
+    const unsigned grid = (unsigned)((n + 8 / GEMV_SPLIT - 1) / (8 / GEMV_SPLIT));
+    if (mixed && b->op.A16lo.p)
+        k_gemv_cph<GEMV_SPLIT><<<grid, 256, GH_SMEM, st>>>(b->op.A32.p, b->op.A16lo.p, b->xhi32.p, b->xlo32.p, y, n,
+                                                          gate);
+    else if (mixed && b->op.A32lo.p)
+        k_gemv_cpa<GEMV_SPLIT, 2><<<grid, 256, GC_SMEM2, st>>>(b->op.A32.p, b->op.A32lo.p, b->xhi32.p, b->xlo32.p, y,
+                                                               n, gate);
     else
         gemv64(st, b->op.A64.p, x, y, n, gate);
 }
@@ -1934,11 +2043,12 @@ static void gemv_resid(cudaStream_t st, mh_boundary* b, const double* x, double*
 
 static const char* resid_region(mh_boundary* b, bool mixed, const int* gate) {
     if (gate) return "bie_gemv64_gated";   // may be skipped on the device: timed apart
-    return mixed && b->op.A32lo.p ? "bie_gemvff" : "bie_gemv64";
+    return resid_ff(b, mixed) ? "bie_gemvff" : "bie_gemv64";
 }
 
 static double resid_bytes(mh_boundary* b, bool mixed) {
     const double n = (double)b->n;
+    if (mixed && b->op.A16lo.p) return 6.0 * n * n + 24.0 * n;
     return mixed && b->op.A32lo.p ? 8.0 * n * n + 24.0 * n : 8.0 * n * n + 16.0 * n;
 }
 

@@ -175,6 +175,9 @@ struct bie_operator {
     dbuf<double> A64;
     dbuf<float> A32;
     dbuf<float> A32lo;   // A64 - A32 rounded to binary32: A32 + A32lo carries A64 to ~2^-48
+    // (A64 - A32) 2^24 rounded to binary16 (bit patterns), used instead of A32lo when N is a
+    // multiple of 8: A32 + 2^-24 A16lo carries A64 to 2^-35 |A| + 2^-49
+    dbuf<uint16_t> A16lo;
 };
 
 struct mh_boundary {

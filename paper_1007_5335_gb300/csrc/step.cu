@@ -391,7 +391,7 @@ static mh_status step_solve(mh_ctx* ctx, ProblemImpl* P, const double* f_next_de
         MH_LAUNCHED(ctx);
     }
     // A sigma for the normal-line rule from the solver's final residual r = rhs - A sigma
-    // (binary64, or float-float on A32 + A32lo): rhs - r, no operator product
+    // (binary64, or float-float on the binary32 operator and its low part): rhs - r, no operator product
     if (P->tg.n_line) {
         k_rhs_minus_r<<<mh_grid(ng, 256), 256, 0, st>>>(P->rhs.p, P->rc_r.p, ng, P->tg.asig.p);
         MH_LAUNCHED(ctx);
