@@ -1566,6 +1566,49 @@ __global__ void __launch_bounds__(256) k_fine_density_s(const T2* __restrict__ c
     wf[g] = (T)((double)acc * fg[6 * g + 4] * fg[6 * g + 5]);
 }
 
+// The same fine-grid density by inverse FFT, for curves of N = 2^L <= FFT_MAX nodes: block
+// (s, k) forms p(t_{16 j + s}) = Re sum_{m <= N/2} C_m^{(s)} e^{2 pi i m j / N} for every j of
+// curve k by one radix-2 decimation-in-time transform of length N in shared memory (input in
+// bit-reversed order, twiddles e^{2 pi i r / N} from the curve's binary32 table staged beside
+// it), then multiplies by |y'| h_f as k_fine_density_s does.  N log2 N / 2 butterflies per
+// sub-offset instead of N (N/2 + 1) products; rounding ~log2 N units of binary32 against ~sqrt N
+// for the direct sum.
+constexpr int FFT_MAX = 2048;
+
+__global__ void __launch_bounds__(256) k_fine_density_fft(const float2* __restrict__ cp, const float2* __restrict__ tw,
+                                                          const double* __restrict__ fg, const int32_t* __restrict__ nn,
+                                                          const int32_t* __restrict__ off,
+                                                          const int64_t* __restrict__ foff, float* __restrict__ wf) {
+    extern __shared__ float2 fz[];   // [N] values, then [N] twiddles
+    const int s = blockIdx.x, k = blockIdx.y;
+    const int N = nn[k];
+    float2* z = fz;
+    float2* w = fz + N;
+    const int L = __ffs(N) - 1;   // N = 2^L
+    const float2* c = cp + coef_base(off, k) * UPSAMPLE + s;
+    for (int m = threadIdx.x; m < N; m += blockDim.x) {
+        z[__brev((unsigned)m) >> (32 - L)] = m <= N / 2 ? c[(int64_t)m * UPSAMPLE] : make_float2(0.f, 0.f);
+        w[m] = tw[off[k] + m];
+    }
+    __syncthreads();
+    for (int len = 2; len <= N; len <<= 1) {
+        const int half = len >> 1, step = N / len;
+        for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
+            const int pos = b & (half - 1), i = (b - pos) * 2 + pos;   // (group b / half) * len + pos
+            const float2 t = w[pos * step];
+            const float2 u = z[i], v = z[i + half];
+            const float2 vt = make_float2(v.x * t.x - v.y * t.y, v.x * t.y + v.y * t.x);
+            z[i] = make_float2(u.x + vt.x, u.y + vt.y);
+            z[i + half] = make_float2(u.x - vt.x, u.y - vt.y);
+        }
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const int64_t g = foff[k] + (int64_t)UPSAMPLE * j + s;
+        wf[g] = (float)((double)z[j].x * fg[6 * g + 4] * fg[6 * g + 5]);
+    }
+}
+
 // Coarse trapezoid sum over all curves not flagged fine for the target:
 //   out[t] = -(1/(2 pi alpha^2)) sum_n K(y_n, x_t) sigma_n |y'_n| h
 // Sources are staged through shared memory in tiles of the block size.
@@ -2789,8 +2832,14 @@ static mh_status fine_density(mh_ctx* ctx, mh_boundary* b, const double* sc, mh_
         k_fine_coef<float2><<<mh_grid(nmodes * UPSAMPLE, 256), 256, 0, st>>>(sc, b->d_nn.p, b->d_off.p, b->n_curves,
                                                                              nmodes, b->fcp32.p);
         MH_LAUNCHED(ctx);
-        k_fine_density_s<float, float2><<<grid, 256, max_n * sizeof(float2), st>>>(
-            b->fcp32.p, b->tw32.p, b->fine_geo.p, b->d_nn.p, b->d_off.p, b->d_fine_off.p, wf32);
+        bool pow2 = max_n <= FFT_MAX;
+        for (int nk : b->n_nodes) pow2 = pow2 && nk >= 2 && (nk & (nk - 1)) == 0;
+        if (pow2)
+            k_fine_density_fft<<<dim3(UPSAMPLE, (unsigned)b->n_curves), 256, 2 * max_n * sizeof(float2), st>>>(
+                b->fcp32.p, b->tw32.p, b->fine_geo.p, b->d_nn.p, b->d_off.p, b->d_fine_off.p, wf32);
+        else
+            k_fine_density_s<float, float2><<<grid, 256, max_n * sizeof(float2), st>>>(
+                b->fcp32.p, b->tw32.p, b->fine_geo.p, b->d_nn.p, b->d_off.p, b->d_fine_off.p, wf32);
     } else {
         if (!b->fcp64.p) MH_ALLOC(ctx, b->fcp64, nmodes * UPSAMPLE);
         k_fine_coef<double2><<<mh_grid(nmodes * UPSAMPLE, 256), 256, 0, st>>>(sc, b->d_nn.p, b->d_off.p, b->n_curves,
