@@ -5,8 +5,8 @@
 // residual step along delta picks the start (formulas in include/mh.h).
 //
 // Kernels:
-//   k_features      truncated DFT of every curve (warp per coefficient, binary64 sums)
-//   k_synth         Fourier synthesis plus r at every node (binary64 sums)
+//   k_features      truncated DFT of every curve (warp per coefficient, float-float sums)
+//   k_synth         Fourier synthesis plus r at every node (float-float sums)
 //   k_gemv_layer    one network layer for one input vector, weights binary32 / bfloat16 /
 //                   bfloat16 pair, binary32 accumulation: HBM/L2-bound matrix-vector work,
 //                   so the tensor pipe is not used
@@ -31,6 +31,8 @@ struct mh_net {
     std::vector<int32_t> nn, off;
     dbuf<int32_t> d_nn, d_off;
     dbuf<double> tw;                 // [n_bnd][2] cos, sin of 2 pi m / N_k (per curve, m < N_k)
+    dbuf<float2> tw32;               // the same, rounded to binary32
+    dbuf<float> v32;                 // binary32 copy of the vector being transformed
     double gx = 1.0, gy = 1.0;
     dbuf<float> P;                   // parameters (layout in mh.h)
     dbuf<uint16_t> Bhi, Blo;         // bfloat16 copies of P (only the weight blocks are read)
@@ -167,37 +169,72 @@ __global__ void k_twiddle(const int32_t* __restrict__ nn, const int32_t* __restr
     tw[2 * (off[c] + j) + 1] = s;
 }
 
-// x[c][2k], x[c][2k+1] = scale * (1/N_c) sum_j v_j (cos, -sin)(2 pi j k / N_c); one warp each.
-__global__ void k_features(const double* __restrict__ v, const double* __restrict__ tw, const int32_t* __restrict__ nn,
+// Float-float accumulation (TwoSum; the product's rounding error from fma folded into the low
+// part): sums of products of binary32 numbers to ~binary64 accuracy on the binary32 pipe (the
+// binary64 pipe runs at 1/64 of its rate here).
+__device__ __forceinline__ void ff_mac(float& hi, float& lo, float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float t = hi + p;
+    const float bb = t - hi;
+    lo += ((hi - (t - bb)) + (p - bb)) + e;
+    hi = t;
+}
+
+__device__ __forceinline__ void ff_warp_sum(float& hi, float& lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float t = hi + oh, bb = t - hi;
+        lo += ((hi - (t - bb)) + (oh - bb)) + ol;
+        hi = t;
+    }
+}
+
+__global__ void k_to_f32(const double* __restrict__ v, int64_t n, float* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)v[i];
+}
+
+__global__ void k_tw_f32(const double* __restrict__ tw, int64_t n, float2* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)tw[2 * i], (float)tw[2 * i + 1]);
+}
+
+// x[c][2k], x[c][2k+1] = scale * (1/N_c) sum_j v_j (cos, -sin)(2 pi j k / N_c); one warp each,
+// binary32 inputs and twiddles, float-float sums.
+__global__ void k_features(const float* __restrict__ v, const float2* __restrict__ tw, const int32_t* __restrict__ nn,
                            const int32_t* __restrict__ off, int n_curves, int K, const double* __restrict__ scale,
                            float* __restrict__ x) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (gw >= n_curves * K) return;
     const int c = gw / K, k = gw - c * K;
     const int n = nn[c], o = off[c];
-    double sr = 0.0, si = 0.0;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     // twiddle index m = j k mod n, advanced by 32 k mod n per lane step
     const int step = (int)((32LL * k) % n);
     int m = (int)(((int64_t)lane * k) % n);
     for (int j = lane; j < n; j += 32) {
-        const double vj = v[o + j];
-        sr = fma(vj, tw[2 * (o + m)], sr);
-        si = fma(-vj, tw[2 * (o + m) + 1], si);
+        const float vj = v[o + j];
+        const float2 t = tw[o + m];
+        ff_mac(rh, rl, vj, t.x);
+        ff_mac(ih, il, -vj, t.y);
         m += step;
         if (m >= n) m -= n;
     }
-    sr = warp_sum_d(sr);
-    si = warp_sum_d(si);
+    ff_warp_sum(rh, rl);
+    ff_warp_sum(ih, il);
     if (lane == 0) {
         const double s = scale[0] / n;
-        x[(int64_t)c * 2 * K + 2 * k] = (float)(sr * s);
-        x[(int64_t)c * 2 * K + 2 * k + 1] = (float)(si * s);
+        x[(int64_t)c * 2 * K + 2 * k] = (float)(((double)rh + (double)rl) * s);
+        x[(int64_t)c * 2 * K + 2 * k + 1] = (float)(((double)ih + (double)il) * s);
     }
 }
 
 // out_j = r_j + scal[0] * gy * (Re c_0 + 2 sum_{k>=1} Re(c_k e^{2 pi i j k / N})).  Eight threads
-// per node split the modes (k = 1 + g + 8 i); grid (chunks of 32 nodes, curves).
-__global__ void k_synth(const float* __restrict__ y, const double* __restrict__ tw, const int32_t* __restrict__ nn,
+// per node split the modes (k = 1 + g + 8 i); grid (chunks of 32 nodes, curves); binary32
+// twiddles, float-float sums.
+__global__ void k_synth(const float* __restrict__ y, const float2* __restrict__ tw, const int32_t* __restrict__ nn,
                         const int32_t* __restrict__ off, int K, const double* __restrict__ r,
                         const double* __restrict__ scal, double gy, double* __restrict__ out) {
     extern __shared__ float ys[];
@@ -207,19 +244,25 @@ __global__ void k_synth(const float* __restrict__ y, const double* __restrict__ 
     const int n = nn[c], o = off[c];
     const int j = blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3), g = threadIdx.x & 7;
     const int jj = j < n ? j : 0;
-    double v = 0.0;
+    float vh = 0.f, vl = 0.f;
     int m = (int)(((int64_t)jj * (1 + g)) % n);
     const int step = (int)((8LL * jj) % n);
     for (int k = 1 + g; k < K; k += 8) {
-        v = fma((double)ys[2 * k], tw[2 * (o + m)], v);
-        v = fma(-(double)ys[2 * k + 1], tw[2 * (o + m) + 1], v);
+        const float2 t = tw[o + m];
+        ff_mac(vh, vl, ys[2 * k], t.x);
+        ff_mac(vh, vl, -ys[2 * k + 1], t.y);
         m += step;
         if (m >= n) m -= n;
     }
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    if (g == 0 && j < n) out[o + j] = r[o + j] + scal[0] * gy * ((double)ys[0] + 2.0 * v);
+#pragma unroll
+    for (int msk = 1; msk < 8; msk <<= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, vh, msk), ol = __shfl_xor_sync(0xffffffffu, vl, msk);
+        const float t = vh + oh, bb = t - vh;
+        vl += ((vh - (t - bb)) + (oh - bb)) + ol;
+        vh = t;
+    }
+    if (g == 0 && j < n)
+        out[o + j] = r[o + j] + scal[0] * gy * ((double)ys[0] + 2.0 * ((double)vh + (double)vl));
 }
 
 __device__ __forceinline__ void bf16x8(uint4 h, float* f) {
@@ -712,8 +755,10 @@ mh_status infer_one(mh_ctx* ctx, mh_net* net, int arith, const float* x, float* 
 
 mh_status features(mh_ctx* ctx, mh_net* net, const double* v, const double* scale, float* x) {
     const int warps = net->n_curves * net->K;
-    k_features<<<(warps + 7) / 8, 256, 0, ctx->stream>>>(v, net->tw.p, net->d_nn.p, net->d_off.p, net->n_curves,
-                                                         net->K, scale, x);
+    k_to_f32<<<mh_grid(net->n_bnd, 256), 256, 0, ctx->stream>>>(v, net->n_bnd, net->v32.p);
+    MH_LAUNCHED(ctx);
+    k_features<<<(warps + 7) / 8, 256, 0, ctx->stream>>>(net->v32.p, net->tw32.p, net->d_nn.p, net->d_off.p,
+                                                         net->n_curves, net->K, scale, x);
     MH_LAUNCHED(ctx);
     return MH_OK;
 }
@@ -769,6 +814,10 @@ extern "C" mh_status mh_net_create(mh_ctx* ctx, const mh_boundary* bnd, int n_mo
     MH_ALLOC(ctx, net->tw, 2 * bnd->n);
     k_twiddle<<<dim3((unsigned)mh_grid(net->max_nodes, 256), (unsigned)bnd->n_curves), 256, 0, st>>>(
         net->d_nn.p, net->d_off.p, net->tw.p);
+    MH_LAUNCHED(ctx);
+    MH_ALLOC(ctx, net->tw32, bnd->n);
+    MH_ALLOC(ctx, net->v32, bnd->n);
+    k_tw_f32<<<mh_grid(bnd->n, 256), 256, 0, st>>>(net->tw.p, bnd->n, net->tw32.p);
     MH_LAUNCHED(ctx);
     MH_ALLOC(ctx, net->P, net->n_params);
     MH_CUDA(ctx, cudaMemsetAsync(net->P.p, 0, net->n_params * 4, st));
@@ -1150,7 +1199,7 @@ mh_status warm_start_run(mh_ctx* ctx, mh_boundary* b, double alpha, mh_net* net,
         MH_TRY(features(ctx, net, r0, scal + 1, net->xin.p));
         MH_TRY(infer_one(ctx, net, arith, net->xin.p, net->yout.p));
         k_synth<<<dim3((unsigned)mh_grid(net->max_nodes, 32), (unsigned)net->n_curves), 256, 2 * net->K * 4, st>>>(
-            net->yout.p, net->tw.p, net->d_nn.p, net->d_off.p, net->K, r0, scal, net->gy, b->warm_dir.p);
+            net->yout.p, net->tw32.p, net->d_nn.p, net->d_off.p, net->K, r0, scal, net->gy, b->warm_dir.p);
         MH_LAUNCHED(ctx);
     }
     // binary64 image of the direction: r0 = r - c w is handed to GMRES as the residual of x0, and
