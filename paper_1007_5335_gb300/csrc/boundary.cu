@@ -2880,7 +2880,9 @@ mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_
 
 mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* tg, const double* sigma,
                                 const double* main_vals, double* out, mh_precision prec, bool fine_in_fmm,
-                                const double* asig_given) {
+                                const double* asig_given, int part) {
+    if (part != 0 && !fine_in_fmm) return mh_fail(ctx, MH_ERR_INVALID_ARG, "a split tail needs the fine rule in the passes");
+    const bool do_aux = part != 2, do_finish = part != 1;
     cudaStream_t st = ctx->stream;
     const double pref = -1.0 / (2.0 * MH_PI * alpha * alpha);
     const double pref32 = pref / (alpha * alpha);
@@ -2891,78 +2893,84 @@ mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_t
     dbuf<double>& sc = tg->sc;
     dbuf<double>& wf = tg->wf;
     prof_scope ps_all(ctx, "dlp_evaluate");
-    if (n) MH_CUDA(ctx, cudaMemcpyAsync(ext.p, main_vals, n * 8, cudaMemcpyDeviceToDevice, st));
-    const int64_t np_do_main = fine_in_fmm ? 0 : np_main;
-    if (tg->n_pairs && !fine_in_fmm) MH_TRY(dlp_fine_weights(ctx, b, sigma, prec));
-    (void)sc;
-    (void)wf;
-    if (prec == MH_PREC_MIXED) {
-        MH_TRY(prep_mixed(ctx, b));
-        k_weights32<<<mh_grid(b->n, 256), 256, 0, st>>>(sigma, b->geo.p, b->d_curve_of.p, b->d_nn.p, b->n, b->w32.p);
-        MH_LAUNCHED(ctx);
-        if (naux) {
-            // few auxiliary points: split the sources over the grid, then reduce in a fixed order
-            const int64_t nblk = (naux + MH_TILE - 1) / MH_TILE;
-            const int64_t ntile = (b->n + MH_TILE - 1) / MH_TILE;
-            const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, (152 * 8) / std::max<int64_t>(nblk, 1)));
-            if ((int64_t)tg->part.n < nsplit * naux) MH_ALLOC(ctx, tg->part, nsplit * naux);
-            k_dlp_coarse32<<<dim3((unsigned)nblk, (unsigned)nsplit), MH_TILE, 0, st>>>(
-                tg->xy.p + 2 * n, tg->fine.p + n, naux, b->src32.p, b->w32.p, b->d_curve_of.p, b->tile_c.p, b->n,
-                c32, pref32, nsplit > 1 ? tg->part.p : ext.p + n);
+    // ext[0, n): the given values at the targets; ext[n, n_ext): the auxiliary points, written
+    // only by the auxiliary part (part 1), so that part can run beside the work that produces
+    // main_vals
+    if (do_finish && n) MH_CUDA(ctx, cudaMemcpyAsync(ext.p, main_vals, n * 8, cudaMemcpyDeviceToDevice, st));
+    if (do_aux) {
+        const int64_t np_do_main = fine_in_fmm ? 0 : np_main;
+        if (tg->n_pairs && !fine_in_fmm) MH_TRY(dlp_fine_weights(ctx, b, sigma, prec));
+        (void)sc;
+        (void)wf;
+        if (prec == MH_PREC_MIXED) {
+            MH_TRY(prep_mixed(ctx, b));
+            k_weights32<<<mh_grid(b->n, 256), 256, 0, st>>>(sigma, b->geo.p, b->d_curve_of.p, b->d_nn.p, b->n, b->w32.p);
             MH_LAUNCHED(ctx);
-            if (nsplit > 1) {
-                k_sum_partials<<<mh_grid(naux, 256), 256, 0, st>>>(tg->part.p, nsplit, naux, pref32, ext.p + n);
+            if (naux) {
+                // few auxiliary points: split the sources over the grid, then reduce in a fixed order
+                const int64_t nblk = (naux + MH_TILE - 1) / MH_TILE;
+                const int64_t ntile = (b->n + MH_TILE - 1) / MH_TILE;
+                const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, (152 * 8) / std::max<int64_t>(nblk, 1)));
+                if ((int64_t)tg->part.n < nsplit * naux) MH_ALLOC(ctx, tg->part, nsplit * naux);
+                k_dlp_coarse32<<<dim3((unsigned)nblk, (unsigned)nsplit), MH_TILE, 0, st>>>(
+                    tg->xy.p + 2 * n, tg->fine.p + n, naux, b->src32.p, b->w32.p, b->d_curve_of.p, b->tile_c.p, b->n,
+                    c32, pref32, nsplit > 1 ? tg->part.p : ext.p + n);
                 MH_LAUNCHED(ctx);
+                if (nsplit > 1) {
+                    k_sum_partials<<<mh_grid(naux, 256), 256, 0, st>>>(tg->part.p, nsplit, naux, pref32, ext.p + n);
+                    MH_LAUNCHED(ctx);
+                }
             }
-        }
-        if (tg->n_pairs) {
-            prof_scope ps(ctx, "dlp_fine", DL_FLOPS * ((fine_in_fmm ? 0 : tg->fine_nodes_main + tg->curve_nodes_main) + tg->fine_nodes_aux), 24.0 * b->n_fine);
-            if (np_do_main) {
-                k_dlp_fine_corr32<<<mh_grid(np_do_main * 32, 256), 256, 0, st>>>(
-                    tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p, np_do_main, b->fine32.p, b->wf32.p, b->d_fine_off.p,
-                    b->d_fchunk_off.p, b->fchunk_c.p, b->src32.p, b->w32.p, b->tile_c.p, b->d_off.p,
-                    c32, pref32, ext.p);
-                MH_LAUNCHED(ctx);
+            if (tg->n_pairs) {
+                prof_scope ps(ctx, "dlp_fine", DL_FLOPS * ((fine_in_fmm ? 0 : tg->fine_nodes_main + tg->curve_nodes_main) + tg->fine_nodes_aux), 24.0 * b->n_fine);
+                if (np_do_main) {
+                    k_dlp_fine_corr32<<<mh_grid(np_do_main * 32, 256), 256, 0, st>>>(
+                        tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p, np_do_main, b->fine32.p, b->wf32.p, b->d_fine_off.p,
+                        b->d_fchunk_off.p, b->fchunk_c.p, b->src32.p, b->w32.p, b->tile_c.p, b->d_off.p,
+                        c32, pref32, ext.p);
+                    MH_LAUNCHED(ctx);
+                }
+                if (np_aux) {
+                    k_dlp_fine32_grp<FINE_TG><<<(unsigned)(tg->n_groups * tg->fine_slices), 256, 0, st>>>(
+                        tg->xy.p, tg->pair_tgt.p, tg->grp_curve.p, tg->grp_pair.p, tg->fine_slices, b->fine32.p,
+                        b->wf32.p, b->d_fine_off.p, b->d_fchunk_off.p, b->fchunk_cf.p, b->fchunk_r.p, c32,
+                        (float)(MH_DL_CUT32 * alpha), pref32, tg->grp_part.p, tg->grp_cnt.p, ext.p);
+                    MH_LAUNCHED(ctx);
+                }
             }
-            if (np_aux) {
-                k_dlp_fine32_grp<FINE_TG><<<(unsigned)(tg->n_groups * tg->fine_slices), 256, 0, st>>>(
-                    tg->xy.p, tg->pair_tgt.p, tg->grp_curve.p, tg->grp_pair.p, tg->fine_slices, b->fine32.p,
-                    b->wf32.p, b->d_fine_off.p, b->d_fchunk_off.p, b->fchunk_cf.p, b->fchunk_r.p, c32,
-                    (float)(MH_DL_CUT32 * alpha), pref32, tg->grp_part.p, tg->grp_cnt.p, ext.p);
+        } else {
+            if (naux) {
+                const int64_t nblk = (naux + 127) / 128, ntile = (b->n + 127) / 128;
+                const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, (152 * 8) / std::max<int64_t>(nblk, 1)));
+                if ((int64_t)tg->part.n < nsplit * naux) MH_ALLOC(ctx, tg->part, nsplit * naux);
+                k_dlp_coarse<128><<<dim3((unsigned)nblk, (unsigned)nsplit), 128, 0, st>>>(
+                    tg->xy.p + 2 * n, tg->fine.p + n, naux, b->geo.p, sigma, b->d_curve_of.p, b->d_nn.p, b->n, 1.0 / alpha,
+                    pref, nsplit > 1 ? tg->part.p : ext.p + n);
                 MH_LAUNCHED(ctx);
+                if (nsplit > 1) {
+                    k_sum_partials<<<mh_grid(naux, 256), 256, 0, st>>>(tg->part.p, nsplit, naux, pref, ext.p + n);
+                    MH_LAUNCHED(ctx);
+                }
             }
-        }
-    } else {
-        if (naux) {
-            const int64_t nblk = (naux + 127) / 128, ntile = (b->n + 127) / 128;
-            const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, (152 * 8) / std::max<int64_t>(nblk, 1)));
-            if ((int64_t)tg->part.n < nsplit * naux) MH_ALLOC(ctx, tg->part, nsplit * naux);
-            k_dlp_coarse<128><<<dim3((unsigned)nblk, (unsigned)nsplit), 128, 0, st>>>(
-                tg->xy.p + 2 * n, tg->fine.p + n, naux, b->geo.p, sigma, b->d_curve_of.p, b->d_nn.p, b->n, 1.0 / alpha,
-                pref, nsplit > 1 ? tg->part.p : ext.p + n);
-            MH_LAUNCHED(ctx);
-            if (nsplit > 1) {
-                k_sum_partials<<<mh_grid(naux, 256), 256, 0, st>>>(tg->part.p, nsplit, naux, pref, ext.p + n);
-                MH_LAUNCHED(ctx);
-            }
-        }
-        if (tg->n_pairs) {
-            prof_scope ps(ctx, "dlp_fine", DL_FLOPS * ((fine_in_fmm ? 0 : tg->fine_nodes_main + tg->curve_nodes_main) + tg->fine_nodes_aux), 24.0 * b->n_fine);
-            if (np_do_main) {
-                k_dlp_fine_corr<<<mh_grid(np_do_main * 32, 256), 256, 0, st>>>(
-                    tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p, np_do_main, b->fine_geo.p, b->wf64.p,
-                    b->d_fine_off.p, b->geo.p, sigma, b->d_nn.p, b->d_off.p, 1.0 / alpha, pref, ext.p);
-                MH_LAUNCHED(ctx);
-            }
-            if (np_aux) {
-                k_dlp_fine64_blk<<<(unsigned)np_aux, 256, 0, st>>>(tg->xy.p, tg->pair_tgt.p + np_main,
-                                                                   tg->pair_curve.p + np_main, b->fine_geo.p,
-                                                                   b->wf64.p, b->d_fine_off.p, 1.0 / alpha, pref,
-                                                                   ext.p);
-                MH_LAUNCHED(ctx);
+            if (tg->n_pairs) {
+                prof_scope ps(ctx, "dlp_fine", DL_FLOPS * ((fine_in_fmm ? 0 : tg->fine_nodes_main + tg->curve_nodes_main) + tg->fine_nodes_aux), 24.0 * b->n_fine);
+                if (np_do_main) {
+                    k_dlp_fine_corr<<<mh_grid(np_do_main * 32, 256), 256, 0, st>>>(
+                        tg->xy.p, tg->pair_tgt.p, tg->pair_curve.p, np_do_main, b->fine_geo.p, b->wf64.p,
+                        b->d_fine_off.p, b->geo.p, sigma, b->d_nn.p, b->d_off.p, 1.0 / alpha, pref, ext.p);
+                    MH_LAUNCHED(ctx);
+                }
+                if (np_aux) {
+                    k_dlp_fine64_blk<<<(unsigned)np_aux, 256, 0, st>>>(tg->xy.p, tg->pair_tgt.p + np_main,
+                                                                       tg->pair_curve.p + np_main, b->fine_geo.p,
+                                                                       b->wf64.p, b->d_fine_off.p, 1.0 / alpha, pref,
+                                                                       ext.p);
+                    MH_LAUNCHED(ctx);
+                }
             }
         }
     }
+    if (!do_finish) return MH_OK;
     if (tg->n_line) {
         // the interior limit needs A sigma; a caller that holds the residual r = rhs - A sigma
         // of this density passes A sigma = rhs - r instead of a product with the operator

@@ -106,6 +106,42 @@ struct dbuf {
 
 #define MH_ALLOC(ctx, buf, count) MH_CUDA(ctx, (buf).alloc(count))
 
+// A second stream with fork / join events, for work that does not depend on what the context
+// stream runs meanwhile: the multipole passes (latency chains, on a stream of the device's
+// highest priority, so that their blocks start before queued near-field blocks) beside the
+// near fields; the sums at the normal-line auxiliary points beside the double layer's
+// multipole pass.  Created at set-up, outside any stream capture.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    SideStream() = default;
+    SideStream(const SideStream&) = delete;
+    SideStream& operator=(const SideStream&) = delete;
+    ~SideStream() {
+        if (join) cudaEventDestroy(join);
+        if (fork) cudaEventDestroy(fork);
+        if (s) cudaStreamDestroy(s);
+    }
+    mh_status create(mh_ctx* ctx, bool high_priority = true) {
+        int least = 0, greatest = 0;
+        MH_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        MH_CUDA(ctx, cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, high_priority ? greatest : least));
+        MH_CUDA(ctx, cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        MH_CUDA(ctx, cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        return MH_OK;
+    }
+    // the side stream waits for everything issued so far on `main`
+    mh_status begin(mh_ctx* ctx, cudaStream_t main) {
+        MH_CUDA(ctx, cudaEventRecord(fork, main));
+        MH_CUDA(ctx, cudaStreamWaitEvent(s, fork, 0));
+        return MH_OK;
+    }
+    mh_status end(mh_ctx* ctx) {
+        MH_CUDA(ctx, cudaEventRecord(join, s));
+        return MH_OK;
+    }
+};
+
 // Tensor-core batched contraction (contract_tc.cu): one launch over chunks of up to 128 tasks of
 // one operator each; products to temp[task][R] or, with task_dst, straight to the destinations.
 struct tc_launch {
@@ -281,6 +317,7 @@ struct mh_problem {
     int64_t n_inside = 0;
     dbuf<int32_t> bnd_leaf;              // leaf of every boundary node
     dbuf<double> B, Up, Ug, rhs, Uh;     // work arrays
+    SideStream aux;                      // the normal-line auxiliary sums beside the double layer's pass
     // GMRES start (mh_problem_set_warm_start)
     int warm_mode = 0;
     int warm_arith = 0;
@@ -332,9 +369,12 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
 // fine_in_fmm: main_vals already use the 16x upsampled rule on every curve (the fine
 // nodes went through the multipole method), so only the auxiliary points of the
 // normal-line rule need near-boundary work.  Requires dlp_fine_weights for this sigma.
+// part (fine_in_fmm only): 0 = everything; 1 = the sums at the auxiliary points (they need
+// sigma and its fine weights only, so they may run beside the pass that produces main_vals);
+// 2 = the rest, after part 1 (main_vals, the normal-line rule, out).
 mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* tg, const double* sigma,
                                 const double* main_vals, double* out, mh_precision prec, bool fine_in_fmm,
-                                const double* asig_given = nullptr);
+                                const double* asig_given = nullptr, int part = 0);
 // Density on the 16x fine grid times |y'| h_f (binary64 in b->wf64; binary32 also in b->wf32
 // when prec is mixed).
 mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_precision prec);

@@ -176,6 +176,7 @@ extern "C" mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* 
             MH_LAUNCHED(ctx);
         }
         MH_TRY(dlp_classify(ctx, bnd, xin.p, P->n_inside, &P->tg));
+        if (P->tg.n_ext > P->tg.n) MH_TRY(P->aux.create(ctx, false));
     }
     // leaf of every boundary node
     MH_ALLOC(ctx, P->bnd_leaf, bnd->n);
@@ -382,6 +383,18 @@ static mh_status step_solve(mh_ctx* ctx, ProblemImpl* P, const double* f_next_de
     if (s != MH_OK) return s;
     // U^h: trapezoid sum by the multipole method at every node, then the near-boundary rules
     MH_TRY(dlp_fine_weights(ctx, b, sigma_dev, prec));
+    // the sums at the auxiliary points of the normal-line rule need only sigma and the fine
+    // weights: without region timers they run on a second stream beside the multipole pass
+    const bool aux_fork = !ctx->profiling && P->aux.s && P->tg.n_ext > P->tg.n;
+    if (aux_fork) {
+        MH_TRY(P->aux.begin(ctx, st));
+        ctx->stream = P->aux.s;
+        const mh_status sa = dlp_evaluate_fmm_tail(ctx, b, P->alpha, &P->tg, sigma_dev, nullptr, nullptr, prec, true,
+                                                   nullptr, 1);
+        ctx->stream = st;
+        MH_TRY(sa);
+        MH_TRY(P->aux.end(ctx));
+    }
     k_dip_weights<<<mh_grid(b->n_fine, 256), 256, 0, st>>>(b->wf64.p, P->perm.p, b->n_fine, P->w_sorted.p);
     MH_LAUNCHED(ctx);
     const double* du = nullptr;
@@ -396,8 +409,9 @@ static mh_status step_solve(mh_ctx* ctx, ProblemImpl* P, const double* f_next_de
         k_rhs_minus_r<<<mh_grid(ng, 256), 256, 0, st>>>(P->rhs.p, P->rc_r.p, ng, P->tg.asig.p);
         MH_LAUNCHED(ctx);
     }
+    if (aux_fork) MH_CUDA(ctx, cudaStreamWaitEvent(st, P->aux.join, 0));
     MH_TRY(dlp_evaluate_fmm_tail(ctx, b, P->alpha, &P->tg, sigma_dev, P->Uh.p, P->Uh.p, prec, true,
-                                 P->tg.n_line ? P->tg.asig.p : nullptr));
+                                 P->tg.n_line ? P->tg.asig.p : nullptr, aux_fork ? 2 : 0));
     k_combine<<<mh_grid(n, 256), 256, 0, st>>>(P->Up.p, P->Uh.p, P->region.p, P->slot.p, P->d_ext_const.p,
                                                P->ext_mode, n, u_next_dev);
     MH_LAUNCHED(ctx);

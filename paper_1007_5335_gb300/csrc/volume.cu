@@ -588,42 +588,6 @@ mh_status tc_split(mh_ctx* ctx, const TcImages& T, int k, const float* pool32) {
     return tc_split_launch(ctx, pool32 + r.src, r.len, r.count, r.S, T.planes.p, T.plane, r.dst);
 }
 
-// A second stream, of the device's highest priority, with fork / join events: the multipole
-// passes (latency chains) run there while the near fields, which do not depend on them, run
-// on the context stream and fill the SMs that the chains leave idle; the priority lets the
-// passes' blocks start before queued near-field blocks.  Created at set-up, outside any
-// stream capture.
-struct SideStream {
-    cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
-    SideStream() = default;
-    SideStream(const SideStream&) = delete;
-    SideStream& operator=(const SideStream&) = delete;
-    ~SideStream() {
-        if (join) cudaEventDestroy(join);
-        if (fork) cudaEventDestroy(fork);
-        if (s) cudaStreamDestroy(s);
-    }
-    mh_status create(mh_ctx* ctx) {
-        int least = 0, greatest = 0;
-        MH_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
-        MH_CUDA(ctx, cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest));
-        MH_CUDA(ctx, cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        MH_CUDA(ctx, cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
-        return MH_OK;
-    }
-    // the side stream waits for everything issued so far on `main`
-    mh_status begin(mh_ctx* ctx, cudaStream_t main) {
-        MH_CUDA(ctx, cudaEventRecord(fork, main));
-        MH_CUDA(ctx, cudaStreamWaitEvent(s, fork, 0));
-        return MH_OK;
-    }
-    mh_status end(mh_ctx* ctx) {
-        MH_CUDA(ctx, cudaEventRecord(join, s));
-        return MH_OK;
-    }
-};
-
 struct OpPool {
     std::vector<double> data;
     std::vector<int64_t> off;
