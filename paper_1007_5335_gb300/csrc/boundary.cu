@@ -1578,7 +1578,8 @@ constexpr int FFT_MAX = 2048;
 __global__ void __launch_bounds__(256) k_fine_density_fft(const float2* __restrict__ cp, const float2* __restrict__ tw,
                                                           const double* __restrict__ fg, const int32_t* __restrict__ nn,
                                                           const int32_t* __restrict__ off,
-                                                          const int64_t* __restrict__ foff, float* __restrict__ wf) {
+                                                          const int64_t* __restrict__ foff, float* __restrict__ wf,
+                                                          double* __restrict__ wf64 = nullptr) {
     extern __shared__ float2 fz[];   // [N] values, then [N] twiddles
     const int s = blockIdx.x, k = blockIdx.y;
     const int N = nn[k];
@@ -1605,7 +1606,53 @@ __global__ void __launch_bounds__(256) k_fine_density_fft(const float2* __restri
     }
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         const int64_t g = foff[k] + (int64_t)UPSAMPLE * j + s;
-        wf[g] = (float)((double)z[j].x * fg[6 * g + 4] * fg[6 * g + 5]);
+        const float v = (float)((double)z[j].x * fg[6 * g + 4] * fg[6 * g + 5]);
+        wf[g] = v;
+        if (wf64) wf64[g] = (double)v;   // the binary64 image the dipole weights are taken from
+    }
+}
+
+// The coefficients C_m^{(s)} of k_fine_density_fft straight from the density, for curves of
+// N = 2^L <= FFT_MAX nodes: block k takes curve k's density to binary32, forms c_m = (1/N)
+// sum_j sigma_j e^{-2 pi i m j / N} by one radix-2 forward FFT in shared memory (the conjugate
+// twiddles), and writes C_m^{(s)} = w_m c_m e^{2 pi i m s / (16 N)} for m <= N/2 and every
+// sub-offset s (w_0 = 1, w_m = 2, the Nyquist term real with w = 1; the phases by sincospif).
+// Replaces the direct transform and k_fine_coef of the general path.
+__global__ void __launch_bounds__(256) k_fine_spectrum32(const double* __restrict__ sigma, const float2* __restrict__ tw,
+                                                         const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
+                                                         float2* __restrict__ cp) {
+    extern __shared__ float2 fz[];   // [N] values, then [N] twiddles
+    const int k = blockIdx.x;
+    const int N = nn[k];
+    float2* z = fz;
+    float2* w = fz + N;
+    const int L = __ffs(N) - 1;   // N = 2^L
+    for (int m = threadIdx.x; m < N; m += blockDim.x) {
+        z[__brev((unsigned)m) >> (32 - L)] = make_float2((float)sigma[off[k] + m], 0.f);
+        w[m] = tw[off[k] + m];
+    }
+    __syncthreads();
+    for (int len = 2; len <= N; len <<= 1) {
+        const int half = len >> 1, step = N / len;
+        for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
+            const int pos = b & (half - 1), i = (b - pos) * 2 + pos;
+            const float2 t = w[pos * step];   // e^{+2 pi i r / N}; the forward transform takes its conjugate
+            const float2 u = z[i], v = z[i + half];
+            const float2 vt = make_float2(v.x * t.x + v.y * t.y, v.y * t.x - v.x * t.y);
+            z[i] = make_float2(u.x + vt.x, u.y + vt.y);
+            z[i + half] = make_float2(u.x - vt.x, u.y - vt.y);
+        }
+        __syncthreads();
+    }
+    const int64_t base = coef_base(off, k);
+    const float invN = 1.f / (float)N;   // a power of two: exact
+    for (int e = threadIdx.x; e < (N / 2 + 1) * UPSAMPLE; e += blockDim.x) {
+        const int m = e / UPSAMPLE, s = e - m * UPSAMPLE;
+        const float re = z[m].x * invN, im = 2 * m == N ? 0.f : z[m].y * invN;
+        const float wm = (m == 0 || 2 * m == N) ? 1.f : 2.f;
+        float sn, cs;
+        sincospif((float)(2 * m * s) / (float)(UPSAMPLE * N), &sn, &cs);
+        cp[(base + m) * UPSAMPLE + s] = make_float2(wm * (re * cs - im * sn), wm * (re * sn + im * cs));
     }
 }
 
@@ -2859,7 +2906,20 @@ mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_
         MH_ALLOC(ctx, b->sc64, 2 * nmodes);
         MH_ALLOC(ctx, b->wf64, b->n_fine);
     }
-    if (prec == MH_PREC_MIXED) {
+    const int max_n = *std::max_element(b->n_nodes.begin(), b->n_nodes.end());
+    bool pow2 = max_n <= FFT_MAX;
+    for (int nk : b->n_nodes) pow2 = pow2 && nk >= 2 && (nk & (nk - 1)) == 0;
+    if (prec == MH_PREC_MIXED && pow2) {
+        // binary32 FFTs both ways: spectrum per sub-offset, then the fine grid
+        MH_TRY(prep_mixed(ctx, b));
+        if (!b->fcp32.p) MH_ALLOC(ctx, b->fcp32, nmodes * UPSAMPLE);
+        k_fine_spectrum32<<<(unsigned)b->n_curves, 256, 2 * max_n * sizeof(float2), st>>>(
+            sigma, b->tw32.p, b->d_nn.p, b->d_off.p, b->fcp32.p);
+        MH_LAUNCHED(ctx);
+        k_fine_density_fft<<<dim3(UPSAMPLE, (unsigned)b->n_curves), 256, 2 * max_n * sizeof(float2), st>>>(
+            b->fcp32.p, b->tw32.p, b->fine_geo.p, b->d_nn.p, b->d_off.p, b->d_fine_off.p, b->wf32.p, b->wf64.p);
+        MH_LAUNCHED(ctx);
+    } else if (prec == MH_PREC_MIXED) {
         MH_TRY(prep_mixed(ctx, b));
         k_to_float_vec<<<mh_grid(b->n, 256), 256, 0, st>>>(sigma, b->x32.p, b->n);
         MH_LAUNCHED(ctx);
