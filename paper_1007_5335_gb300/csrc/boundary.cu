@@ -642,7 +642,7 @@ __global__ void k_to_float_vec(const double* __restrict__ a, float* __restrict__
 // ---------------- binary32 double layer (mixed precision) ----------------
 
 // Source data relative to tile centres: tiles of MH_TILE consecutive nodes.
-__global__ void k_prep_src32(const double* __restrict__ geo, int64_t n, float4* src, double2* tc) {
+__global__ void k_prep_src32(const double* __restrict__ geo, int64_t n, float4* src, double2* tc, float* tr) {
     const int64_t tile = blockIdx.x;
     const int64_t s0 = tile * MH_TILE;
     const int cnt = (n - s0) < MH_TILE ? (int)(n - s0) : MH_TILE;
@@ -658,11 +658,18 @@ __global__ void k_prep_src32(const double* __restrict__ geo, int64_t n, float4* 
         tc[tile] = make_double2(cx, cy);
     }
     __syncthreads();
+    __shared__ float rmax;
+    if (threadIdx.x == 0) rmax = 0.f;
+    __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         const double* g = geo + 8 * (s0 + i);
         const double sp = g[6];
         src[s0 + i] = make_float4((float)(g[0] - cx), (float)(g[1] - cy), (float)(g[3] / sp), (float)(-g[2] / sp));
+        // the largest distance from the centre (non-negative floats order like their bit patterns)
+        atomicMax(reinterpret_cast<int*>(&rmax), __float_as_int((float)hypot(g[0] - cx, g[1] - cy)));
     }
+    __syncthreads();
+    if (threadIdx.x == 0) tr[tile] = rmax * 1.0001f;
 }
 
 // Fine nodes relative to chunk centres: chunks of MH_TILE fine nodes inside each curve.
@@ -717,17 +724,21 @@ __global__ void k_weights32(const double* __restrict__ sigma, const double* __re
 // g = K1(z)/z; the kernels below apply the prefactor times 1/alpha^2 (pref32) in binary64.
 
 // Coarse trapezoid sum in binary32: sources staged through shared memory in tiles of
-// MH_TILE; the target offset from the tile centre is formed once per tile in binary64;
-// per-tile partial sums are added in binary64.
+// MH_TILE (the weight folded into the normal as they are staged); the target offset from the
+// tile centre is formed once per tile in binary64; per-tile partial sums are added in binary64.
+// A tile whose nodes all lie on one curve is skipped at once when that curve is flagged for
+// the target; when it lies beyond 2 alpha of every target of the warp (tile centre distance
+// above 2 alpha plus the tile radius) its pairs take the z > 2 form without a branch or a
+// test (mh_dl32_pair_far; pairs beyond the cut come out below the rounding of the sum).
 __global__ void __launch_bounds__(MH_TILE) k_dlp_coarse32(const double* __restrict__ xy,
                                                           const uint32_t* __restrict__ fine, int64_t nt,
                                                           const float4* __restrict__ src, const float* __restrict__ w,
                                                           const int32_t* __restrict__ curve_of,
-                                                          const double2* __restrict__ tc, int64_t ns, mh_dl32 c32,
-                                                          double pref, double* out) {
+                                                          const double2* __restrict__ tc, const float* __restrict__ tr,
+                                                          int64_t ns, mh_dl32 c32, double pref, double* out) {
     __shared__ float4 s4[MH_TILE];
-    __shared__ float sw[MH_TILE];
     __shared__ int sk[MH_TILE];
+    const float two_a = 2.0001f * c32.a;
     const int64_t t = blockIdx.x * (int64_t)MH_TILE + threadIdx.x;
     const bool active = t < nt;
     const double px = active ? xy[2 * t] : 0.0, py = active ? xy[2 * t + 1] : 0.0;
@@ -741,20 +752,39 @@ __global__ void __launch_bounds__(MH_TILE) k_dlp_coarse32(const double* __restri
     for (int64_t tile = tile0; tile < tile1; ++tile) {
         const int64_t s = tile * MH_TILE + threadIdx.x;
         if (s < ns) {
-            s4[threadIdx.x] = src[s];
-            sw[threadIdx.x] = w[s];
+            const float4 v = src[s];
+            const float wd = w[s];
+            s4[threadIdx.x] = make_float4(v.x, v.y, v.z * wd, v.w * wd);
             sk[threadIdx.x] = curve_of[s];
         }
         __syncthreads();
         const int cnt = (ns - tile * MH_TILE) < MH_TILE ? (int)(ns - tile * MH_TILE) : MH_TILE;
+        const bool one_curve = sk[0] == sk[cnt - 1];   // consecutive nodes: one curve unless at a seam
+        float tx = 0.f, ty = 0.f;
+        bool skip = !active, far = true;
         if (active) {
             const double2 c = tc[tile];
-            const float tx = (float)(px - c.x), ty = (float)(py - c.y);
+            tx = (float)(px - c.x);
+            ty = (float)(py - c.y);
+            if (one_curve && ((mask >> sk[0]) & 1u)) skip = true;
+            const float lim = two_a + tr[tile];
+            far = fmaf(tx, tx, ty * ty) > lim * lim;
+        }
+        const bool warp_far = __all_sync(0xffffffffu, skip || far);
+        if (!skip) {
             float part = 0.f;
-            for (int i = 0; i < cnt; ++i) {
-                if ((mask >> sk[i]) & 1u) continue;
-                const float4 v = s4[i];
-                part += mh_dl32_pair(v.x - tx, v.y - ty, v.z, v.w, c32) * sw[i];
+            if (warp_far && one_curve) {
+                for (int i = 0; i < cnt; ++i) {
+                    const float4 v = s4[i];
+                    part += mh_dl32_pair_far(v.x - tx, v.y - ty, v.z, v.w, c32);
+                }
+                part *= c32.a32;
+            } else {
+                for (int i = 0; i < cnt; ++i) {
+                    if ((mask >> sk[i]) & 1u) continue;
+                    const float4 v = s4[i];
+                    part += mh_dl32_pair(v.x - tx, v.y - ty, v.z, v.w, c32);
+                }
             }
             acc += (double)part;
         }
@@ -2763,8 +2793,9 @@ static mh_status prep_mixed(mh_ctx* ctx, mh_boundary* b) {
     b->n_tiles = (b->n + MH_TILE - 1) / MH_TILE;
     MH_ALLOC(ctx, b->src32, b->n);
     MH_ALLOC(ctx, b->tile_c, b->n_tiles);
+    MH_ALLOC(ctx, b->tile_r, b->n_tiles);
     MH_ALLOC(ctx, b->w32, b->n);
-    k_prep_src32<<<(unsigned)b->n_tiles, 128, 0, st>>>(b->geo.p, b->n, b->src32.p, b->tile_c.p);
+    k_prep_src32<<<(unsigned)b->n_tiles, 128, 0, st>>>(b->geo.p, b->n, b->src32.p, b->tile_c.p, b->tile_r.p);
     MH_LAUNCHED(ctx);
     b->fchunk_off.assign(b->n_curves + 1, 0);
     for (int k = 0; k < b->n_curves; ++k)
@@ -2814,7 +2845,7 @@ mh_status dlp_evaluate(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_targets* t
         if (tg->n_ext) {
             prof_scope ps(ctx, "dlp_coarse", DL_FLOPS * tg->n_ext * b->n, 24.0 * (tg->n_ext + b->n));
             k_dlp_coarse32<<<mh_grid(tg->n_ext, MH_TILE), MH_TILE, 0, st>>>(
-                tg->xy.p, tg->fine.p, tg->n_ext, b->src32.p, b->w32.p, b->d_curve_of.p, b->tile_c.p, b->n,
+                tg->xy.p, tg->fine.p, tg->n_ext, b->src32.p, b->w32.p, b->d_curve_of.p, b->tile_c.p, b->tile_r.p, b->n,
                 c32, pref32, ext.p);
             MH_LAUNCHED(ctx);
         }
@@ -2973,7 +3004,7 @@ mh_status dlp_evaluate_fmm_tail(mh_ctx* ctx, mh_boundary* b, double alpha, dlp_t
                 const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, (152 * 8) / std::max<int64_t>(nblk, 1)));
                 if ((int64_t)tg->part.n < nsplit * naux) MH_ALLOC(ctx, tg->part, nsplit * naux);
                 k_dlp_coarse32<<<dim3((unsigned)nblk, (unsigned)nsplit), MH_TILE, 0, st>>>(
-                    tg->xy.p + 2 * n, tg->fine.p + n, naux, b->src32.p, b->w32.p, b->d_curve_of.p, b->tile_c.p, b->n,
+                    tg->xy.p + 2 * n, tg->fine.p + n, naux, b->src32.p, b->w32.p, b->d_curve_of.p, b->tile_c.p, b->tile_r.p, b->n,
                     c32, pref32, nsplit > 1 ? tg->part.p : ext.p + n);
                 MH_LAUNCHED(ctx);
                 if (nsplit > 1) {

@@ -241,6 +241,7 @@ struct mh_boundary {
     dbuf<int64_t> d_fchunk_off;
     dbuf<float4> src32, fine32;          // (dx, dy, nx, ny)
     dbuf<double2> tile_c, fchunk_c;
+    dbuf<float> tile_r;                  // per source tile: largest distance of a node from its centre
     dbuf<float2> tw32;                   // binary32 copy of the twiddles e^{2 pi i r / N_k}
     dbuf<float> xhi32, xlo32;            // float-float split of the input of a residual product
     dbuf<float4> fchunk_cf;              // fine chunk centres as float-float (x_hi, x_lo, y_hi, y_lo)
