@@ -17,7 +17,8 @@ forcing is not among them.
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the
 library's stream; between timed steps a 256 MB buffer is written (L2 flush, untimed).
-`e2e` repeats the K steps through the public API with host buffers: the step's inputs
+`e2e` repeats the K steps, from the state the timed steps started in (so with the same GMRES
+work), through the public API with host buffers: the step's inputs
 (u, F, f, packed in one pinned buffer) are copied from host memory and the result u^{N+1}
 is copied back inside the timed region.  With N > 1 (torchrun) every rank runs its own replica of the
 problem (the single-problem path does not shard), the time is the max over ranks and
@@ -241,6 +242,10 @@ def run_ours(args):
     sigma = torch.zeros(bnd.n, dtype=torch.float64, device=dev)
     u, _, _ = run_steps(args.warmup, u0.clone(), sigma, False, prec, args.graph)
     launches0 = ctx.launches
+    # the state the timed steps start from: the end-to-end steps below replay the same
+    # trajectory from it (same solution, same previous density, so the same GMRES work; the
+    # iteration count falls as the run goes on, and later steps would be cheaper)
+    u_start, sigma_start = u.clone(), sigma.clone()
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -268,7 +273,7 @@ def run_ours(args):
     # host buffer and go over in one copy (one 4.2 MB copy costs less than three)
     nn_, ng_ = tree.n_nodes, bnd.n
     in_h = torch.empty(2 * nn_ + ng_, dtype=torch.float64).pin_memory()
-    in_h[:nn_].copy_(u.cpu())
+    in_h[:nn_].copy_(u_start.cpu())
     in_h[nn_:2 * nn_].copy_(torch.from_numpy(F_np))
     in_h[2 * nn_:].zero_()
     u_h = in_h[:nn_]
@@ -282,7 +287,8 @@ def run_ours(args):
         e2e_batch = mh.Batch(ctx, [prob])
         ud.copy_(u)
         e2e_batch.step([ud], [Fd], [fd], [sigma], gmres_tol=1e-10, prec=prec)
-    e2e_times = []
+    sigma.copy_(sigma_start)
+    e2e_times, e2e_its = [], []
     for _ in range(args.steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
@@ -290,14 +296,15 @@ def run_ours(args):
         a.record()
         in_d.copy_(in_h, non_blocking=True)
         if args.graph:
-            e2e_batch.step([ud], [Fd], [fd], [sigma], gmres_tol=1e-10, prec=prec)
+            info = e2e_batch.step([ud], [Fd], [fd], [sigma], gmres_tol=1e-10, prec=prec)[0]
             out_h.copy_(ud, non_blocking=True)
         else:
-            mh.heat_step(ctx, prob, ud, Fd, fd, und, sigma, gmres_tol=1e-10, prec=prec)
+            info = mh.heat_step(ctx, prob, ud, Fd, fd, und, sigma, gmres_tol=1e-10, prec=prec)
             out_h.copy_(und, non_blocking=True)
         b.record()
         b.synchronize()
         e2e_times.append(a.elapsed_time(b))
+        e2e_its.append(info.gmres_iterations)
         u_h.copy_(out_h)
     e2e_value, e2e_ms = aggregate_over_ranks(sum(e2e_times), n_pts, args.steps, dist, dev)
     bytes_in = (2 * tree.n_nodes + bnd.n) * 8
@@ -334,7 +341,8 @@ def run_ours(args):
         "warm_start": dict(warm_info, gmres_iterations_mean=float(np.mean(its))),
         "setup_s": t_setup,
         "e2e": {"value": e2e_value, "unit": "points*timesteps/s", "h2d_bytes_per_step": bytes_in,
-                "d2h_bytes_per_step": bytes_out},
+                "d2h_bytes_per_step": bytes_out, "start": "the timed steps' starting state",
+                "gmres_iterations_mean": float(np.mean(e2e_its))},
         "gpu_launches": launches,
         "profiled_ms_per_step": float(np.mean(times_prof)),
         "profiled_clocks": clk_prof.summary(),
@@ -677,7 +685,8 @@ def run_profile_case(args):
                  M2M / L2L chains);
       operator : the boundary, then three binary32 operator products (k_gemv32s);
       solve    : two mixed-precision GMRES solves (float-float residual products, k_gemv_cpa);
-      step     : three mixed-precision heat steps (near-field and upsampled-rule pair sums)."""
+      step     : three mixed-precision heat steps (near-field and upsampled-rule pair sums);
+      mfree    : the heat-step problem with the matrix-free boundary operator, three products."""
     import torch
     import paper_1007_5335_gb300 as mh
     ctx = mh.Context(0)
@@ -702,6 +711,17 @@ def run_profile_case(args):
             for _ in range(2):
                 out.zero_()
                 mh.mh_gmres_solve(ctx, bnd, wl.alpha, x, out, tol=1e-10, prec=mh.MH_PREC_MIXED)
+    elif args.profile_case == "mfree":
+        tree, bnd, prob, _, _, _ = setup_problem(mh, ctx, wl, torch, dev)
+        prob.matrix_free(True)
+        x = torch.tensor(rng.standard_normal(bnd.n), device=dev)
+        out = torch.empty_like(x)
+        mh.mh_double_layer_apply(ctx, bnd, prob.alpha, x, out)
+        torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_push("mfree_products")      # lets a profiler select the products
+        for _ in range(3):
+            mh.mh_double_layer_apply(ctx, bnd, prob.alpha, x, out)
+        torch.cuda.nvtx.range_pop()
     else:
         tree, bnd, prob, nodes, F_np, _ = setup_problem(mh, ctx, wl, torch, dev)
         F = torch.tensor(F_np, device=dev)
@@ -714,6 +734,72 @@ def run_profile_case(args):
             u, un = un, u
         tree.check()
     torch.cuda.synchronize(dev)
+
+
+def run_bie_crossover(args):
+    """Boundary-operator products at growing N_Gamma (starfish domain, 6 curves of 512 to 4096
+    nodes, then 12 curves of 4096; tree, alpha and p of the heat-step workload): the dense binary64 product (k_gemv64s),
+    the dense binary32 Krylov product (k_gemv32s) and the matrix-free product (on-surface multipole
+    pass + chirp-transform Alpert correction, binary64), each the mean over K products timed by
+    the library's region events with a 256 MB L2 flush between products; the device memory of
+    each form; the matrix-free error against the dense binary64 product.  One JSON line."""
+    import torch
+    import paper_1007_5335_gb300 as mh
+    dev = torch.device("cuda:0")
+    ctx = mh.Context(0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    K = max(args.steps if args.steps < 100 else 20, 3)
+    rows = []
+    for npc, holes in ((512, 5), (1024, 5), (2048, 5), (4096, 5), (4096, 11)):
+        wl = W.starfish_domain(n_per_curve=npc, n_holes=holes)
+        tree, bnd, prob, _, _, t_setup = setup_problem(mh, ctx, wl, torch, dev)
+        n = bnd.n
+        rng = np.random.default_rng(npc)
+        y = np.concatenate(wl.curves)
+        x = torch.tensor(np.cos(3 * y[:, 0]) * np.sin(2 * y[:, 1]) + 0.3 * rng.standard_normal(n), device=dev)
+        out = torch.empty_like(x)
+
+        def timed(region, prec, parts=()):
+            for _ in range(3):
+                mh.mh_double_layer_apply(ctx, bnd, prob.alpha, x, out, prec=prec)
+            ctx.profile(True)
+            ctx.profile_read(region, reset=True)   # a reset clears every region
+            for _ in range(K):
+                flush.zero_()
+                mh.mh_double_layer_apply(ctx, bnd, prob.alpha, x, out, prec=prec)
+            ms, cnt, _, _ = ctx.profile_read(region)
+            split = {r: round(ctx.profile_read(r)[0] / K, 4) for r in parts}
+            ctx.profile_read(region, reset=True)
+            ctx.profile(False)
+            return ms / max(cnt, 1), out.cpu().numpy(), split
+
+        t64, y64, _ = timed("bie_gemv64", mh.MH_PREC_FP64)
+        t32, _, _ = timed("bie_gemv32", mh.MH_PREC_MIXED)
+        torch.cuda.synchronize(dev)
+        free_a = torch.cuda.mem_get_info(dev)[0]
+        t0 = time.time()
+        prob.matrix_free(True)
+        t_mf_setup = time.time() - t0
+        torch.cuda.synchronize(dev)
+        free_b = torch.cuda.mem_get_info(dev)[0]
+        dense_bytes = 8 * n * n + 4 * n * n + 2 * n * n    # binary64 + binary32 + binary16 low part
+        tmf, ymf, split = timed("bie_mfree", mh.MH_PREC_FP64, ("bie_fmm", "bie_fmm_contract", "bie_fmm_chain"))
+        e = float(np.linalg.norm(ymf - y64) / np.linalg.norm(y64))
+        rows.append({"n_gamma": n, "nodes_per_curve": npc, "dense_fp64_ms": round(t64, 4),
+                     "dense_fp32_ms": round(t32, 4), "matrix_free_ms": round(tmf, 4),
+                     "matrix_free_ms_split": dict(split, outside_multipole_pass=round(tmf - split["bie_fmm"], 4)),
+                     "dense_bytes": dense_bytes, "matrix_free_bytes": int(free_a - free_b + dense_bytes),
+                     "matrix_free_setup_s": round(t_mf_setup, 3), "problem_setup_s": round(t_setup, 3),
+                     "rel_l2_matrix_free_vs_dense": e})
+        del prob, bnd, tree
+        torch.cuda.synchronize(dev)
+    cross = next((r["n_gamma"] for r in rows if r["matrix_free_ms"] < r["dense_fp64_ms"]), None)
+    cross32 = next((r["n_gamma"] for r in rows if r["matrix_free_ms"] < r["dense_fp32_ms"]), None)
+    print(json.dumps({"bie_operator_products": rows, "products_per_point": K, "p": W.starfish_domain().p,
+                      "first_n_gamma_matrix_free_below_dense_fp64": cross,
+                      "first_n_gamma_matrix_free_below_dense_fp32": cross32,
+                      "l2": "flushed between products (256 MB write, untimed)"}))
+
 
 
 def run_reference(args):
@@ -764,7 +850,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--clocks-dir", default=None, help="directory for the raw clock samples (default: temp dir)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--profile-case", choices=["volume", "operator", "solve", "step"], default=None,
+    ap.add_argument("--bie-crossover", action="store_true",
+                    help="time dense and matrix-free boundary-operator products at growing N_Gamma and exit")
+    ap.add_argument("--profile-case", choices=["volume", "operator", "solve", "step", "mfree"], default=None,
                     help="run one small fixed case for a profiler and exit (see run_profile_case)")
     args = ap.parse_args()
     if args.clocks_dir:
@@ -772,6 +860,9 @@ def main():
         CLOCKS_DIR = args.clocks_dir
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.bie_crossover:
+        run_bie_crossover(args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -227,6 +227,22 @@ typedef enum {
 mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* bnd, double dt, int scheme, int p,
                             int ext_mode, const double* ext_const_host, mh_problem** out);
 mh_status mh_problem_destroy(mh_problem* prob);
+/* Matrix-free boundary operator (Section 3.2: the discrete system evaluated by the multipole
+ * method instead of a stored matrix).  enable = 1 switches every later product with the
+ * problem's boundary operator (GMRES, residuals, mh_double_layer_apply without targets) to
+ *     (A sigma)_j = sigma_j + (1/pi) [T_j - W_j] + C_j
+ * with T_j the trapezoid sum over all other nodes by an on-surface pass of the problem's tree
+ * (order p, binary64), W_j the own-curve terms inside the Alpert window (direct) and C_j the
+ * Alpert correction, the trigonometric interpolant of sigma at the correction nodes taken by
+ * chirp transforms per curve: O(N log N) work and O(N) memory instead of the O(N^2) matrix,
+ * which is released.  Binary64 only: MH_PREC_MIXED solves and the graph form of the step
+ * (mh_batch_step) then fail with MH_ERR_INVALID_ARG.  Needs an even node count per curve in
+ * [max(2 l, 4), 4096] (else MH_ERR_INVALID_ARG) and every boundary node inside the tree.
+ * enable = 0 returns to the dense operator (assembled again at its next use).  The pass has its
+ * own expansions and M2M/L2L chain (over the boxes that hold boundary nodes); it reads the
+ * tree's translation operators, so it stops working (MH_ERR_INVALID_ARG) once the tree's volume
+ * operators are rebuilt for another alpha or p. */
+mh_status mh_problem_matrix_free(mh_ctx* ctx, mh_problem* prob, int enable);
 /* Region of every volume node: -1 inside Omega, k on the exterior side of curve k. */
 mh_status mh_problem_regions(mh_ctx* ctx, const mh_problem* prob, int32_t* region_host);
 /* Right-hand side -2 alpha^2 (f_next - U^p|Gamma) of the boundary equation solved by the last

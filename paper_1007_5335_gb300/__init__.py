@@ -79,6 +79,7 @@ _SIGS = {
     "mh_gmres_solve": [_p, _p, _d, _p, _p, _d, _i, _i, ctypes.POINTER(GmresInfo)],
     "mh_problem_create": [_p, _p, _p, _d, _i, _i, _i, _p, ctypes.POINTER(_p)],
     "mh_problem_destroy": [_p],
+    "mh_problem_matrix_free": [_p, _p, _i],
     "mh_problem_regions": [_p, _p, _p],
     "mh_problem_rhs": [_p, _p, _p],
     "heat_step": [_p, _p, _p, _p, _p, _p, _p, _p, _d, _i, ctypes.POINTER(StepInfo)],
@@ -347,6 +348,11 @@ class Problem:
         self.ctx.check(_lib.mh_problem_set_warm_start(self.ctx.h, self.h, int(mode), net.h if net is not None else None,
                                                       int(arith)))
         self._net = net          # keep the network alive while the problem uses it
+
+    def matrix_free(self, enable: bool = True):
+        """mh_problem_matrix_free: the boundary operator by the on-surface multipole pass and
+        chirp-transform Alpert correction (binary64) instead of the dense matrix."""
+        self.ctx.check(_lib.mh_problem_matrix_free(self.ctx.h, self.h, 1 if enable else 0))
 
     def set_near_tile(self, threads: int):
         """mh_problem_set_near_tile: threads per block of the near-field double-layer kernel."""

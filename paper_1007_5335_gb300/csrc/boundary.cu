@@ -1608,8 +1608,7 @@ constexpr int FFT_MAX = 2048;
 __global__ void __launch_bounds__(256) k_fine_density_fft(const float2* __restrict__ cp, const float2* __restrict__ tw,
                                                           const double* __restrict__ fg, const int32_t* __restrict__ nn,
                                                           const int32_t* __restrict__ off,
-                                                          const int64_t* __restrict__ foff, float* __restrict__ wf,
-                                                          double* __restrict__ wf64 = nullptr) {
+                                                          const int64_t* __restrict__ foff, float* __restrict__ wf) {
     extern __shared__ float2 fz[];   // [N] values, then [N] twiddles
     const int s = blockIdx.x, k = blockIdx.y;
     const int N = nn[k];
@@ -1636,23 +1635,26 @@ __global__ void __launch_bounds__(256) k_fine_density_fft(const float2* __restri
     }
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         const int64_t g = foff[k] + (int64_t)UPSAMPLE * j + s;
-        const float v = (float)((double)z[j].x * fg[6 * g + 4] * fg[6 * g + 5]);
-        wf[g] = v;
-        if (wf64) wf64[g] = (double)v;   // the binary64 image the dipole weights are taken from
+        wf[g] = (float)((double)z[j].x * fg[6 * g + 4] * fg[6 * g + 5]);
     }
 }
 
-// The coefficients C_m^{(s)} of k_fine_density_fft straight from the density, for curves of
-// N = 2^L <= FFT_MAX nodes: block k takes curve k's density to binary32, forms c_m = (1/N)
-// sum_j sigma_j e^{-2 pi i m j / N} by one radix-2 forward FFT in shared memory (the conjugate
-// twiddles), and writes C_m^{(s)} = w_m c_m e^{2 pi i m s / (16 N)} for m <= N/2 and every
-// sub-offset s (w_0 = 1, w_m = 2, the Nyquist term real with w = 1; the phases by sincospif).
-// Replaces the direct transform and k_fine_coef of the general path.
-__global__ void __launch_bounds__(256) k_fine_spectrum32(const double* __restrict__ sigma, const float2* __restrict__ tw,
-                                                         const int32_t* __restrict__ nn, const int32_t* __restrict__ off,
-                                                         float2* __restrict__ cp) {
+// The density times |y'| h_f on the 16x grid straight from the density, for curves of
+// N = 2^L <= FFT_MAX nodes, in one launch: block (s, k) takes curve k's density to binary32,
+// forms c_m = (1/N) sum_j sigma_j e^{-2 pi i m j / N} by a radix-2 forward FFT in shared memory
+// (the conjugate twiddles; each of the UPSAMPLE blocks of a curve repeats this small transform),
+// multiplies in its own sub-offset's phases, C_m^{(s)} = w_m c_m e^{2 pi i m s / (16 N)} (m <= N/2;
+// w_0 = 1, w_m = 2, the Nyquist term real with w = 1; the phases by sincospif), and finishes as
+// k_fine_density_fft does (the inverse transform, the real part times |y'| h_f into wf and its
+// binary64 image wf64).
+__global__ void __launch_bounds__(256) k_fine_weights_fft(const double* __restrict__ sigma, const float2* __restrict__ tw,
+                                                          const double* __restrict__ fg, const int32_t* __restrict__ nn,
+                                                          const int32_t* __restrict__ off,
+                                                          const int64_t* __restrict__ foff, float* __restrict__ wf,
+                                                          double* __restrict__ wf64) {
     extern __shared__ float2 fz[];   // [N] values, then [N] twiddles
-    const int k = blockIdx.x;
+    constexpr int PER = FFT_MAX / 256;   // values per thread when the spectrum is reordered
+    const int s = blockIdx.x, k = blockIdx.y;
     const int N = nn[k];
     float2* z = fz;
     float2* w = fz + N;
@@ -1662,11 +1664,12 @@ __global__ void __launch_bounds__(256) k_fine_spectrum32(const double* __restric
         w[m] = tw[off[k] + m];
     }
     __syncthreads();
+    // forward transform (decimation in time, conjugate twiddles): z[m] = N c_m
     for (int len = 2; len <= N; len <<= 1) {
         const int half = len >> 1, step = N / len;
         for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
             const int pos = b & (half - 1), i = (b - pos) * 2 + pos;
-            const float2 t = w[pos * step];   // e^{+2 pi i r / N}; the forward transform takes its conjugate
+            const float2 t = w[pos * step];
             const float2 u = z[i], v = z[i + half];
             const float2 vt = make_float2(v.x * t.x + v.y * t.y, v.y * t.x - v.x * t.y);
             z[i] = make_float2(u.x + vt.x, u.y + vt.y);
@@ -1674,15 +1677,46 @@ __global__ void __launch_bounds__(256) k_fine_spectrum32(const double* __restric
         }
         __syncthreads();
     }
-    const int64_t base = coef_base(off, k);
+    // this sub-offset's coefficients, then back into bit-reversed order for the inverse
+    float2 cm[PER];
     const float invN = 1.f / (float)N;   // a power of two: exact
-    for (int e = threadIdx.x; e < (N / 2 + 1) * UPSAMPLE; e += blockDim.x) {
-        const int m = e / UPSAMPLE, s = e - m * UPSAMPLE;
-        const float re = z[m].x * invN, im = 2 * m == N ? 0.f : z[m].y * invN;
-        const float wm = (m == 0 || 2 * m == N) ? 1.f : 2.f;
-        float sn, cs;
-        sincospif((float)(2 * m * s) / (float)(UPSAMPLE * N), &sn, &cs);
-        cp[(base + m) * UPSAMPLE + s] = make_float2(wm * (re * cs - im * sn), wm * (re * sn + im * cs));
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int m = threadIdx.x + 256 * q;
+        cm[q] = make_float2(0.f, 0.f);
+        if (m < N && 2 * m <= N) {
+            const float re = z[m].x * invN, im = 2 * m == N ? 0.f : z[m].y * invN;
+            const float wm = (m == 0 || 2 * m == N) ? 1.f : 2.f;
+            float sn, cs;
+            sincospif((float)(2 * m * s) / (float)(UPSAMPLE * N), &sn, &cs);
+            cm[q] = make_float2(wm * (re * cs - im * sn), wm * (re * sn + im * cs));
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int m = threadIdx.x + 256 * q;
+        if (m < N) z[__brev((unsigned)m) >> (32 - L)] = cm[q];
+    }
+    __syncthreads();
+    // inverse transform: z[j] = sum_m C_m e^{2 pi i m j / N}
+    for (int len = 2; len <= N; len <<= 1) {
+        const int half = len >> 1, step = N / len;
+        for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
+            const int pos = b & (half - 1), i = (b - pos) * 2 + pos;
+            const float2 t = w[pos * step];
+            const float2 u = z[i], v = z[i + half];
+            const float2 vt = make_float2(v.x * t.x - v.y * t.y, v.x * t.y + v.y * t.x);
+            z[i] = make_float2(u.x + vt.x, u.y + vt.y);
+            z[i + half] = make_float2(u.x - vt.x, u.y - vt.y);
+        }
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const int64_t g = foff[k] + (int64_t)UPSAMPLE * j + s;
+        const float v = (float)((double)z[j].x * fg[6 * g + 4] * fg[6 * g + 5]);
+        wf[g] = v;
+        wf64[g] = (double)v;   // the binary64 image the dipole weights are taken from
     }
 }
 
@@ -1911,6 +1945,278 @@ __global__ void k_dlp_line(const int32_t* __restrict__ line_tgt, const int32_t* 
 }  // namespace
 
 
+// ---- matrix-free operator (Section 3.2 without the dense matrix) ----
+//
+// Row j of the discrete system is sigma_j + (1/pi) [T_j - W_j] + C_j with
+//   T_j = sum_{i != j} K(y_i, x_j) |y'_i| h sigma_i        (all curves: the multipole pass)
+//   W_j = the terms of T_j inside the own-curve Alpert window 0 < |i - j| < a (direct)
+//   C_j = sum_p cp[j][p] sigma~(t_j + s_p x_m h)           (Alpert nodes, p = (s, m))
+// where sigma~ is the trigonometric interpolant of the curve's density (the periodic kernel
+// D_N of the dense assembly).  sigma~ at the 2l shifted grids comes from the spectrum
+// c_m = (1/N) sum_n sigma_n e^{-2 pi i m n / N}:
+//   sigma~(t_j + d) = Re sum_{m <= N/2} w_m c_m e^{i m d} e^{2 pi i m j / N}
+// (w_0 = 1, w_m = 2, the Nyquist term with w = 1), one length-N transform per shift.  N_k is
+// any even count: a power of two takes radix-2 transforms of length M_k = N_k directly, any other
+// count Bluestein chirp transforms, b_n = e^{i pi n^2/N},
+//   X_k = sum_n x_n e^{-2 pi i n k/N} = conj(b_k) sum_n (x_n conj(b_n)) b_{k-n},
+// the cyclic convolution done at length M_k = 2^L >= 2N - 1 by two radix-2 transforms in shared
+// memory and the transform of the chirp filter computed once (so M_k == N_k marks the direct
+// form).  All binary64.
+
+// Alpert node weights of row j (the first half of k_assemble_alpert, kept per row):
+// cp[j][p] = (1/pi) h w_m |y'(t)| K(y(t), x_j) at t = t_j + s x_m h, s = +1 (p < l) or -1.
+__global__ void k_alpert_weights(const double* __restrict__ geo, const double* __restrict__ coef,
+                                 const int32_t* __restrict__ curve_of, const int32_t* __restrict__ nn,
+                                 const int32_t* __restrict__ off, double inv_alpha, AlpertRule R,
+                                 double* __restrict__ cp) {
+    const int64_t j = blockIdx.x;
+    const int k = curve_of[j];
+    const int N = nn[k];
+    const int jj = (int)(j - off[k]);
+    const double h = 2.0 * MH_PI / N;
+    const double* c = coef + 4 * coef_base(off, k);
+    const double* gj = geo + 8 * j;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int p = warp; p < 2 * R.l; p += nw) {
+        const int m = p % R.l;
+        const double s = p < R.l ? 1.0 : -1.0;
+        double v[6];
+        curve_eval_warp(c, N, (jj + s * R.x[m]) * h, v);
+        if ((threadIdx.x & 31) == 0) {
+            const double spd = sqrt(v[2] * v[2] + v[3] * v[3]);
+            const double K = dl_kernel(v[0], v[1], v[3] / spd, -v[2] / spd, gj[0], gj[1], inv_alpha);
+            cp[j * 2 * R.l + p] = (1.0 / MH_PI) * h * R.w[m] * spd * K;
+        }
+    }
+}
+
+// Own-curve node of window term t of row j: offset d = t/2 + 1 backwards (t even) or forwards.
+__device__ __forceinline__ int mf_win_node(int jj, int t, int N) {
+    const int d = t / 2 + 1;
+    int ii = (jj + ((t & 1) ? d : -d)) % N;
+    return ii < 0 ? ii + N : ii;
+}
+
+// Window weights of row j: win[j][t] = (1/pi) K(y_i, x_j) |y'_i| h for the 2(a - 1) own-curve
+// nodes i with 0 < |i - j| < a (the trapezoid entries the Alpert rule replaces).
+__global__ void k_mf_window_weights(const double* __restrict__ geo, const int32_t* __restrict__ curve_of,
+                                    const int32_t* __restrict__ nn, const int32_t* __restrict__ off, int64_t n,
+                                    double inv_alpha, int nw, double* __restrict__ win) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * nw) return;
+    const int64_t j = e / nw;
+    const int t = (int)(e - j * nw);
+    const int k = curve_of[j], N = nn[k], o = off[k];
+    const double* gj = geo + 8 * j;
+    const double* gi = geo + 8 * (int64_t)(o + mf_win_node((int)(j - o), t, N));
+    const double sp = gi[6];
+    win[e] = (1.0 / MH_PI) * dl_kernel(gi[0], gi[1], gi[3] / sp, -gi[2] / sp, gj[0], gj[1], inv_alpha) * sp *
+             (2.0 * MH_PI / N);
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// In-place radix-2 transform of length M = 2^L in shared memory, input in bit-reversed order:
+// z_k <- sum_n z_n e^{-2 pi i n k / M}; tw[r] = e^{-2 pi i r / M} (r < M/2).
+__device__ void fft64_shared(double2* z, const double2* tw, int M) {
+    for (int len = 2; len <= M; len <<= 1) {
+        const int half = len >> 1, step = M / len;
+        for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
+            const int pos = b & (half - 1), i = (b - pos) * 2 + pos;
+            const double2 vt = cmul(z[i + half], tw[pos * step]);
+            const double2 u = z[i];
+            z[i] = make_double2(u.x + vt.x, u.y + vt.y);
+            z[i + half] = make_double2(u.x - vt.x, u.y - vt.y);
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int MF_THREADS = 512;
+constexpr int MF_MMAX = 8192;                       // N_k <= 4096
+constexpr int MF_PER = MF_MMAX / MF_THREADS;        // entries per thread in a reordering pass
+
+// Bluestein transform of length N: on entry z holds a_n = x_n conj(b_n) (zeros for n >= N) in
+// bit-reversed order; on return z[k] = M X_k conj(b_k)^{-1} ... precisely: z[k] = conj(Y_k) with
+// Y = the cyclic convolution a * b times M, so that X_k = conj(b_k) conj(z[k]) / M for k < N.
+__device__ void bluestein_core(double2* z, const double2* tw, const double2* __restrict__ bh, int M, int L) {
+    fft64_shared(z, tw, M);
+    // pointwise product with the filter's transform, conjugated (the inverse transform as a
+    // forward one), back to bit-reversed order through registers
+    double2 r[MF_PER];
+#pragma unroll
+    for (int q = 0; q < MF_PER; ++q) {
+        const int i = threadIdx.x + MF_THREADS * q;
+        if (i < M) r[q] = cconj(cmul(z[i], bh[i]));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < MF_PER; ++q) {
+        const int i = threadIdx.x + MF_THREADS * q;
+        if (i < M) z[__brev((unsigned)i) >> (32 - L)] = r[q];
+    }
+    __syncthreads();
+    fft64_shared(z, tw, M);
+}
+
+// Per curve: the chirp b_n, the transform of the chirp filter (b_m at m and M - m) and the
+// twiddles of length M_k.  Grid: one block per curve.
+__global__ void __launch_bounds__(MF_THREADS) k_mf_chirp(const int32_t* __restrict__ nn, const int64_t* __restrict__ moff,
+                                                         const int32_t* __restrict__ Mk, const int32_t* __restrict__ off,
+                                                         double2* __restrict__ chirp, double2* __restrict__ bh,
+                                                         double2* __restrict__ twg) {
+    extern __shared__ double2 mfz[];
+    const int k = blockIdx.x, N = nn[k], M = Mk[k];
+    const int L = __ffs(M) - 1;
+    double2* z = mfz;
+    double2* tw = mfz + M;
+    for (int r = threadIdx.x; r < M / 2; r += blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * r / M, &s, &c);
+        tw[r] = make_double2(c, s);
+        twg[moff[k] / 2 + r] = tw[r];
+    }
+    if (M == N) return;   // a power of two: direct transforms, no chirp
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const int64_t q = ((int64_t)n * n) % (2 * (int64_t)N);   // b_n = e^{i pi (n^2 mod 2N) / N}
+        double s, c;
+        sincospi((double)q / N, &s, &c);
+        chirp[off[k] + n] = make_double2(c, s);
+    }
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        int n = -1;
+        if (m < N)
+            n = m;
+        else if (m > M - N)
+            n = M - m;
+        double2 v = make_double2(0.0, 0.0);
+        if (n >= 0) {
+            const int64_t q = ((int64_t)n * n) % (2 * (int64_t)N);
+            double s, c;
+            sincospi((double)q / N, &s, &c);
+            v = make_double2(c, s);
+        }
+        z[__brev((unsigned)m) >> (32 - L)] = v;
+    }
+    __syncthreads();
+    fft64_shared(z, tw, M);
+    for (int m = threadIdx.x; m < M; m += blockDim.x) bh[moff[k] + m] = z[m];
+}
+
+// Spectrum c_m (m <= N/2) of the density of every curve.  Grid: one block per curve.
+__global__ void __launch_bounds__(MF_THREADS) k_mf_spectrum(const double* __restrict__ sigma, const int32_t* __restrict__ nn,
+                                                            const int32_t* __restrict__ off, const int64_t* __restrict__ moff,
+                                                            const int32_t* __restrict__ Mk, const double2* __restrict__ chirp,
+                                                            const double2* __restrict__ bh, const double2* __restrict__ twg,
+                                                            double2* __restrict__ spec) {
+    extern __shared__ double2 mfz[];
+    const int k = blockIdx.x, N = nn[k], M = Mk[k];
+    const int L = __ffs(M) - 1;
+    double2* z = mfz;
+    double2* tw = mfz + M;
+    const double2* b = chirp + off[k];
+    for (int r = threadIdx.x; r < M / 2; r += blockDim.x) tw[r] = twg[moff[k] / 2 + r];
+    const bool direct = M == N;
+    for (int n = threadIdx.x; n < M; n += blockDim.x) {
+        double2 a = make_double2(0.0, 0.0);
+        if (direct)
+            a = make_double2(sigma[off[k] + n], 0.0);
+        else if (n < N)
+            a = make_double2(sigma[off[k] + n] * b[n].x, -sigma[off[k] + n] * b[n].y);
+        z[__brev((unsigned)n) >> (32 - L)] = a;
+    }
+    __syncthreads();
+    if (direct)
+        fft64_shared(z, tw, M);
+    else
+        bluestein_core(z, tw, bh + moff[k], M, L);
+    const double sc = direct ? 1.0 / N : 1.0 / ((double)M * N);
+    for (int m = threadIdx.x; 2 * m <= N; m += blockDim.x) {
+        const double2 X = direct ? z[m] : cmul(cconj(b[m]), cconj(z[m]));
+        spec[coef_base(off, k) + m] = make_double2(X.x * sc, X.y * sc);
+    }
+}
+
+// The interpolated density at the Alpert nodes of shift p = (s, m) of every node of curve k:
+// S[p][off_k + j] = Re sum_{m' <= N/2} w_m' c_m' e^{i m' d} e^{2 pi i m' j / N}, d = s x_m h,
+// as Re of the forward transform of conj(C) (C_m' = w_m' c_m' e^{i m' d}).  Grid (2l, curves).
+__global__ void __launch_bounds__(MF_THREADS) k_mf_shift(const double2* __restrict__ spec, const int32_t* __restrict__ nn,
+                                                         const int32_t* __restrict__ off, const int64_t* __restrict__ moff,
+                                                         const int32_t* __restrict__ Mk, const double2* __restrict__ chirp,
+                                                         const double2* __restrict__ bh, const double2* __restrict__ twg,
+                                                         AlpertRule R, int64_t n, double* __restrict__ S) {
+    extern __shared__ double2 mfz[];
+    const int p = blockIdx.x, k = blockIdx.y, N = nn[k], M = Mk[k];
+    const int L = __ffs(M) - 1;
+    const double sx = (p < R.l ? 1.0 : -1.0) * R.x[p % R.l];
+    const bool direct = M == N;
+    double2* z = mfz;
+    double2* tw = mfz + M;
+    const double2* b = chirp + off[k];
+    const double2* c = spec + coef_base(off, k);
+    for (int r = threadIdx.x; r < M / 2; r += blockDim.x) tw[r] = twg[moff[k] / 2 + r];
+    for (int mm = threadIdx.x; mm < M; mm += blockDim.x) {
+        double2 a = make_double2(0.0, 0.0);
+        if (2 * mm <= N) {
+            const double wm = (mm == 0 || 2 * mm == N) ? 1.0 : 2.0;
+            double sn, cs;
+            sincospi(2.0 * mm * sx / N, &sn, &cs);   // e^{i m' d}, d = 2 pi s x_m / N
+            const double2 C = cmul(c[mm], make_double2(wm * cs, wm * sn));
+            a = direct ? cconj(C) : cmul(cconj(C), cconj(b[mm]));
+        }
+        z[__brev((unsigned)mm) >> (32 - L)] = a;
+    }
+    __syncthreads();
+    if (direct)
+        fft64_shared(z, tw, M);
+    else
+        bluestein_core(z, tw, bh + moff[k], M, L);
+    const double sc = 1.0 / (double)M;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const double X = direct ? z[j].x * (double)M : cmul(cconj(b[j]), cconj(z[j])).x;
+        S[(int64_t)p * n + off[k] + j] = X * sc;   // Re y_j = Re X_j
+    }
+}
+
+// Dipole strengths w_i = sigma_i |y'_i| h_k.
+__global__ void k_mf_weights(const double* __restrict__ sigma, const double* __restrict__ geo,
+                             const int32_t* __restrict__ curve_of, const int32_t* __restrict__ nn, int64_t n,
+                             double* __restrict__ w) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) w[i] = sigma[i] * geo[8 * i + 6] * (2.0 * MH_PI / nn[curve_of[i]]);
+}
+
+// y_j = sigma_j - 2 alpha^2 u_j - (1/pi) W_j + C_j (a > 0), or with the diagonal limit
+// (1/pi) kappa-term h sigma_j in place of W_j and C_j (a = 0).  u_j is the multipole-pass output
+// -(1/(2 pi alpha^2)) sum_{i != j} w_i K(y_i, x_j), so -2 alpha^2 u_j = (1/pi) T_j; the window
+// terms come from the weights of k_mf_window_weights.  One warp per node: the lanes take the
+// 2(a - 1) window terms and the 2l Alpert terms, summed by a fixed-order warp reduction.
+__global__ void k_mf_combine(const double* __restrict__ sigma, const double* __restrict__ u,
+                             const double* __restrict__ geo, const int32_t* __restrict__ curve_of,
+                             const int32_t* __restrict__ nn, const int32_t* __restrict__ off, int64_t n,
+                             double alpha, int a, int l2, const double* __restrict__ win,
+                             const double* __restrict__ cp, const double* __restrict__ S, double* __restrict__ y) {
+    const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;   // the whole warp
+    const int k = curve_of[j], N = nn[k], o = off[k];
+    const int jj = (int)(j - o);
+    double v = 0.0;
+    if (a > 0) {
+        const int nw = 2 * (a - 1);
+        for (int t = lane; t < nw; t += 32) v -= win[j * nw + t] * sigma[o + mf_win_node(jj, t, N)];
+    } else if (lane == 0) {
+        const double* gj = geo + 8 * j;
+        v = (1.0 / MH_PI) * gj[7] * gj[6] * (2.0 * MH_PI / N) * sigma[j];
+    }
+    for (int p = lane; p < l2; p += 32) v += cp[j * l2 + p] * S[(int64_t)p * n + j];
+    v = warp_sum(v);
+    if (lane == 0) y[j] = sigma[j] - 2.0 * alpha * alpha * u[j] + v;
+}
+
 // ============================ host side ============================
 
 static mh_status upload_alpert(int l, AlpertRule* R) {
@@ -2027,7 +2333,133 @@ extern "C" mh_status mh_boundary_geometry(mh_ctx* ctx, const mh_boundary* b, dou
     return MH_OK;
 }
 
+// ---- matrix-free operator (host) ----
+
+// Everything of the matrix-free form but the multipole pass, which the caller has set up on
+// tree t for the boundary nodes (volume_bie_setup).  Releases the dense operator.
+mh_status bie_mfree_setup(mh_ctx* ctx, mh_boundary* b, mh_tree* t, double alpha) {
+    if (!t || !volume_bie_ready(t)) return mh_fail(ctx, MH_ERR_INVALID_ARG, "the on-surface multipole pass is not set up");
+    const int64_t n = b->n;
+    const int nc = b->n_curves, a = b->alpert_order;
+    std::vector<int32_t> Mk(nc);
+    std::vector<int64_t> moff(nc + 1, 0);
+    int mmax = 2;
+    for (int k = 0; k < nc; ++k) {
+        const int N = b->n_nodes[k];
+        if (N % 2 != 0 || N > MF_MMAX / 2 || N < std::max(2 * a, 4))
+            return mh_fail(ctx, MH_ERR_INVALID_ARG,
+                           "the matrix-free operator needs an even node count in [max(2 l, 4), %d] on every curve (curve %d has %d)",
+                           MF_MMAX / 2, k, N);
+        int M = 2;
+        if ((N & (N - 1)) == 0)
+            M = N;   // radix-2 transforms of length N
+        else
+            while (M < 2 * N - 1) M <<= 1;
+        Mk[k] = M;
+        moff[k + 1] = moff[k] + M;
+        mmax = std::max(mmax, M);
+    }
+    cudaStream_t st = ctx->stream;
+    b->mfree = false;
+    MH_ALLOC(ctx, b->mf_M, nc);
+    MH_ALLOC(ctx, b->mf_moff, nc + 1);
+    MH_CUDA(ctx, cudaMemcpyAsync(b->mf_M.p, Mk.data(), nc * 4, cudaMemcpyHostToDevice, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(b->mf_moff.p, moff.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, st));
+    MH_ALLOC(ctx, b->mf_chirp, n);
+    MH_ALLOC(ctx, b->mf_bh, moff[nc]);
+    MH_ALLOC(ctx, b->mf_tw, moff[nc] / 2);
+    MH_ALLOC(ctx, b->mf_spec, n / 2 + nc);   // N_k/2 + 1 modes per curve
+    MH_ALLOC(ctx, b->mf_w, n);
+    MH_ALLOC(ctx, b->mf_u, n);
+    const size_t smem = 24 * (size_t)mmax;
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_mf_chirp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_mf_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MH_CUDA(ctx, cudaFuncSetAttribute(k_mf_shift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_mf_chirp<<<(unsigned)nc, MF_THREADS, smem, st>>>(b->d_nn.p, b->mf_moff.p, b->mf_M.p, b->d_off.p, b->mf_chirp.p,
+                                                       b->mf_bh.p, b->mf_tw.p);
+    MH_LAUNCHED(ctx);
+    if (a > 0) {
+        AlpertRule R;
+        upload_alpert(a, &R);
+        MH_ALLOC(ctx, b->mf_cp, n * 2 * R.l);
+        MH_ALLOC(ctx, b->mf_S, n * 2 * R.l);
+        k_alpert_weights<<<(unsigned)n, 128, 0, st>>>(b->geo.p, b->coef.p, b->d_curve_of.p, b->d_nn.p, b->d_off.p,
+                                                      1.0 / alpha, R, b->mf_cp.p);
+        MH_LAUNCHED(ctx);
+        const int nw = 2 * (a - 1);
+        MH_ALLOC(ctx, b->mf_win, std::max<int64_t>(n * nw, 1));
+        if (nw) {
+            k_mf_window_weights<<<mh_grid(n * nw, 256), 256, 0, st>>>(b->geo.p, b->d_curve_of.p, b->d_nn.p, b->d_off.p, n,
+                                                                     1.0 / alpha, nw, b->mf_win.p);
+            MH_LAUNCHED(ctx);
+        }
+    }
+    if (!b->mf_side.s) MH_TRY(b->mf_side.create(ctx));
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
+    b->mf_tree = t;
+    b->mf_alpha = alpha;
+    b->mf_mmax = mmax;
+    b->mfree = true;
+    // the dense forms are not used any more
+    b->op.A64.release();
+    b->op.A32.release();
+    b->op.A32lo.release();
+    b->op.A16lo.release();
+    b->op.alpha = -1.0;
+    return MH_OK;
+}
+
+// y = A x through the matrix-free form (binary64).
+mh_status bie_apply_mfree(mh_ctx* ctx, mh_boundary* b, const double* x, double* y) {
+    if (!volume_bie_ready(b->mf_tree))
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "the multipole pass of the matrix-free operator is gone (the tree's "
+                                                "volume operators were rebuilt for another alpha or p)");
+    prof_scope ps(ctx, "bie_mfree");
+    cudaStream_t st = ctx->stream;
+    const int64_t n = b->n;
+    const int a = b->alpert_order;
+    int l2 = 0;
+    AlpertRule R;
+    // The Alpert transforms need only x: they run on the side stream beside the multipole pass,
+    // joined before the combination (inside the "bie_mfree" region, whose events are on the
+    // context stream, so its time is that of the overlapped product).
+    const bool fork = a > 0 && b->mf_side.s;
+    if (a > 0) {
+        upload_alpert(a, &R);
+        l2 = 2 * R.l;
+        cudaStream_t as = st;
+        if (fork) {
+            MH_TRY(b->mf_side.begin(ctx, st));
+            as = b->mf_side.s;
+        }
+        const size_t smem = 24 * (size_t)b->mf_mmax;
+        k_mf_spectrum<<<(unsigned)b->n_curves, MF_THREADS, smem, as>>>(x, b->d_nn.p, b->d_off.p, b->mf_moff.p, b->mf_M.p,
+                                                                        b->mf_chirp.p, b->mf_bh.p, b->mf_tw.p,
+                                                                        b->mf_spec.p);
+        MH_LAUNCHED(ctx);
+        k_mf_shift<<<dim3((unsigned)l2, (unsigned)b->n_curves), MF_THREADS, smem, as>>>(
+            b->mf_spec.p, b->d_nn.p, b->d_off.p, b->mf_moff.p, b->mf_M.p, b->mf_chirp.p, b->mf_bh.p, b->mf_tw.p, R, n,
+            b->mf_S.p);
+        MH_LAUNCHED(ctx);
+        if (fork) MH_TRY(b->mf_side.end(ctx));
+    }
+    k_mf_weights<<<mh_grid(n, 256), 256, 0, st>>>(x, b->geo.p, b->d_curve_of.p, b->d_nn.p, n, b->mf_w.p);
+    MH_LAUNCHED(ctx);
+    MH_TRY(volume_bie_apply(ctx, b->mf_tree, b->mf_w.p, b->mf_u.p));
+    if (fork) MH_CUDA(ctx, cudaStreamWaitEvent(st, b->mf_side.join, 0));
+    k_mf_combine<<<mh_grid(n * 32, 256), 256, 0, st>>>(x, b->mf_u.p, b->geo.p, b->d_curve_of.p, b->d_nn.p, b->d_off.p,
+                                                       n, b->mf_alpha, a, l2, b->mf_win.p, b->mf_cp.p, b->mf_S.p, y);
+    MH_LAUNCHED(ctx);
+    return MH_OK;
+}
+
 mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha) {
+    if (b->mfree) {
+        if (alpha != b->mf_alpha)
+            return mh_fail(ctx, MH_ERR_INVALID_ARG, "the matrix-free operator was set up for alpha = %.17g, not %.17g",
+                           b->mf_alpha, alpha);
+        return MH_OK;
+    }
     if (b->op.alpha == alpha && b->op.A64.p) return MH_OK;
     const int64_t n = b->n;
     MH_ALLOC(ctx, b->op.A64, n * n);
@@ -2054,6 +2486,7 @@ mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha) {
 static mh_status gemv_cpa_prepare(mh_ctx* ctx);
 
 static mh_status ensure_fp32(mh_ctx* ctx, mh_boundary* b) {
+    if (b->mfree) return mh_fail(ctx, MH_ERR_INVALID_ARG, "the matrix-free operator runs in binary64 only");
     MH_TRY(gemv_cpa_prepare(ctx));
     if (b->op.A32.p) return MH_OK;
     const int64_t nn = b->n * b->n;
@@ -2174,6 +2607,9 @@ static double resid_bytes(mh_boundary* b, bool mixed) {
 
 mh_status bie_apply64_gated(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, const int* gate,
                             mh_precision prec) {
+    // the gate only skips work whose result the caller then ignores: the matrix-free form
+    // always computes
+    if (b->mfree) return bie_apply_mfree(ctx, b, x, y);
     const bool mixed = prec == MH_PREC_MIXED;
     if (resid_ff(b, mixed)) {   // the split of x is not part of the timed GEMV region
         resid_split(ctx->stream, b, x);
@@ -2195,6 +2631,7 @@ const double* gmres_final_residual(mh_boundary* b, mh_precision prec, bool graph
 
 
 mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec) {
+    if (b->mfree) return bie_apply_mfree(ctx, b, x, y);
     if (prec == MH_PREC_MIXED) {
         MH_TRY(ensure_fp32(ctx, b));
         if (!b->x32.p) MH_ALLOC(ctx, b->x32, b->n);
@@ -2261,13 +2698,17 @@ static mh_status gmres_core(mh_ctx* ctx, mh_boundary* bd, gmres_ws& ws, const do
         const int k1 = k + 1;
         {   // w = A v_k
             const double* vk = ws.V.p + (int64_t)k * n;
-            prof_scope ps(ctx, mixed ? "bie_gemv32" : "bie_gemv64", 2.0 * n * n,
-                          mixed ? 4.0 * n * n + 12.0 * n : 8.0 * n * n + 16.0 * n);
-            if (mixed)
-                gemv32(st, bd->op.A32.p, ws.v32.p, ws.w.p, n, nullptr);
-            else
-                gemv64(st, bd->op.A64.p, vk, ws.w.p, n, nullptr);
-            MH_LAUNCHED(ctx);
+            if (bd->mfree) {
+                MH_TRY(bie_apply_mfree(ctx, bd, vk, ws.w.p));
+            } else {
+                prof_scope ps(ctx, mixed ? "bie_gemv32" : "bie_gemv64", 2.0 * n * n,
+                              mixed ? 4.0 * n * n + 12.0 * n : 8.0 * n * n + 16.0 * n);
+                if (mixed)
+                    gemv32(st, bd->op.A32.p, ws.v32.p, ws.w.p, n, nullptr);
+                else
+                    gemv64(st, bd->op.A64.p, vk, ws.w.p, n, nullptr);
+                MH_LAUNCHED(ctx);
+            }
         }
         // classical Gram-Schmidt twice, normalisation and the Givens update (four launches)
         const size_t shm = (size_t)(k1 + ARN_ROWS) * sizeof(double);
@@ -2312,6 +2753,8 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
     prof_scope ps_all(ctx, "gmres");
     const int64_t n = bd->n;
     if (max_iter < 1 || max_iter > 1000) return mh_fail(ctx, MH_ERR_INVALID_ARG, "max_iter must be in 1..1000");
+    if (bd->mfree && prec != MH_PREC_FP64)
+        return mh_fail(ctx, MH_ERR_INVALID_ARG, "the matrix-free operator runs in binary64 only");
     MH_TRY(gmres_graph_ensure(ctx, bd, max_iter));
     gmres_ws& ws = bd->ws;
     MH_CUDA(ctx, cudaMemsetAsync(ws.g.p, 0, (max_iter + 2) * 8, ctx->stream));
@@ -2573,6 +3016,7 @@ static mh_status gmres_loop_node(mh_ctx* ctx, mh_boundary* bd, gmres_dev* gs, cu
 
 mh_status gmres_run_graph(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, double tol, mh_precision prec,
                           const double* r0, gmres_dev* gs) {
+    if (bd->mfree) return mh_fail(ctx, MH_ERR_INVALID_ARG, "the graph form of GMRES needs the dense operator");
     const int64_t n = bd->n;
     cudaStream_t st = ctx->stream;
     int S, m;
@@ -2941,14 +3385,10 @@ mh_status dlp_fine_weights(mh_ctx* ctx, mh_boundary* b, const double* sigma, mh_
     bool pow2 = max_n <= FFT_MAX;
     for (int nk : b->n_nodes) pow2 = pow2 && nk >= 2 && (nk & (nk - 1)) == 0;
     if (prec == MH_PREC_MIXED && pow2) {
-        // binary32 FFTs both ways: spectrum per sub-offset, then the fine grid
+        // binary32 FFTs both ways in one launch
         MH_TRY(prep_mixed(ctx, b));
-        if (!b->fcp32.p) MH_ALLOC(ctx, b->fcp32, nmodes * UPSAMPLE);
-        k_fine_spectrum32<<<(unsigned)b->n_curves, 256, 2 * max_n * sizeof(float2), st>>>(
-            sigma, b->tw32.p, b->d_nn.p, b->d_off.p, b->fcp32.p);
-        MH_LAUNCHED(ctx);
-        k_fine_density_fft<<<dim3(UPSAMPLE, (unsigned)b->n_curves), 256, 2 * max_n * sizeof(float2), st>>>(
-            b->fcp32.p, b->tw32.p, b->fine_geo.p, b->d_nn.p, b->d_off.p, b->d_fine_off.p, b->wf32.p, b->wf64.p);
+        k_fine_weights_fft<<<dim3(UPSAMPLE, (unsigned)b->n_curves), 256, 2 * max_n * sizeof(float2), st>>>(
+            sigma, b->tw32.p, b->fine_geo.p, b->d_nn.p, b->d_off.p, b->d_fine_off.p, b->wf32.p, b->wf64.p);
         MH_LAUNCHED(ctx);
     } else if (prec == MH_PREC_MIXED) {
         MH_TRY(prep_mixed(ctx, b));

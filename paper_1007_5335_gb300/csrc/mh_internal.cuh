@@ -248,6 +248,21 @@ struct mh_boundary {
     dbuf<float> fchunk_r;                // fine chunk radii
     dbuf<float> w32, wf32, x32;          // per call: weights, fine weights, GEMV input
     dbuf<double> sc64, wf64;             // per call: density Fourier coefficients, fine weights
+    // matrix-free operator: the trapezoid sum by the on-surface multipole pass of a tree that
+    // holds every node, the Alpert correction by binary64 chirp transforms per curve
+    bool mfree = false;
+    mh_tree* mf_tree = nullptr;          // not owned (the problem's tree)
+    double mf_alpha = -1.0;
+    dbuf<double> mf_cp;                  // [n][2 l] Alpert node weights (kernel x rule weight x h / pi)
+    dbuf<double> mf_win;                 // [n][2 (a - 1)] own-curve window weights (kernel x |y'| h / pi)
+    dbuf<double2> mf_chirp, mf_bh, mf_tw;   // per curve: e^{i pi n^2/N}, transformed chirp filter, twiddles
+    dbuf<int64_t> mf_moff;               // per curve: offset of its M_k-entry blocks (twiddles at moff/2)
+    dbuf<int32_t> mf_M;                  // per curve: transform length M_k (power of two >= 2 N_k - 1)
+    int mf_mmax = 0;
+    dbuf<double2> mf_spec;               // per call: spectra c_m, m <= N_k/2
+    dbuf<double> mf_S;                   // per call: [2 l][n] interpolated density at the Alpert nodes
+    dbuf<double> mf_w, mf_u;             // per call: dipole strengths, multipole-pass output
+    SideStream mf_side;                  // the Alpert transforms run there beside the multipole pass
     dbuf<double> warm_dir, warm_w, warm_scal;   // warm-start direction, its image, scalars
     dbuf<float2> fcp32;                  // fine-grid coefficients by sub-offset (binary32)
     dbuf<double2> fcp64;                 // (binary64)
@@ -353,6 +368,10 @@ mh_status warm_start_prepare(mh_ctx* ctx, mh_boundary* b);
 // ---- boundary.cu ----
 mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha);
 mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec);
+// Matrix-free operator: set-up after volume_bie_setup on tree t (releases the dense forms; every
+// later operator product of b goes through it), and one product y = A x (binary64).
+mh_status bie_mfree_setup(mh_ctx* ctx, mh_boundary* b, mh_tree* t, double alpha);
+mh_status bie_apply_mfree(mh_ctx* ctx, mh_boundary* b, const double* x, double* y);
 // y = A x in binary64, skipped when *gate != 0 (gate nullable).
 mh_status bie_apply64_gated(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, const int* gate,
                             mh_precision prec);
@@ -407,6 +426,14 @@ int volume_near_tile(const mh_tree* t);
 mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* dxy, const double* dnrm,
                               const int32_t* dleaf, int64_t nd, bool near_blocks);
 mh_status volume_dipole_apply(mh_ctx* ctx, mh_tree* t, const double* w_sorted, mh_precision prec, const double** u);
+// On-surface double layer through the multipole method (binary64): set-up for the boundary
+// nodes (host arrays in node order: positions, unit normals, leaf of every node), then
+// u_i = -(1/(2 pi alpha^2)) sum_{d != i} w_d (1/alpha) K1(r/alpha) (y_d - x_i).nu_d / r at every
+// node for device strengths w (node order).
+mh_status volume_bie_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* xy, const double* nrm,
+                           const int32_t* leaf, int64_t nd);
+bool volume_bie_ready(const mh_tree* t);
+mh_status volume_bie_apply(mh_ctx* ctx, mh_tree* t, const double* w, double* u);
 mh_status tree_locate(mh_ctx* ctx, const mh_tree* t, const double* xy_dev, int64_t n, int32_t* leaf_out);
 mh_status tree_interpolate(mh_ctx* ctx, const mh_tree* t, const double* vals, const double* xy_dev,
                            const int32_t* leaf, int64_t n, double* out);

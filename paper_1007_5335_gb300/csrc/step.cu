@@ -258,6 +258,33 @@ extern "C" mh_status mh_problem_destroy(mh_problem* p) {
     return MH_OK;
 }
 
+extern "C" mh_status mh_problem_matrix_free(mh_ctx* ctx, mh_problem* prob, int enable) {
+    if (!ctx || !prob) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
+    ProblemImpl* P = static_cast<ProblemImpl*>(prob);
+    mh_boundary* b = P->bnd;
+    if (!enable) {
+        b->mfree = false;   // the dense operator is assembled again at the next use
+        return MH_OK;
+    }
+    if (b->mfree && b->mf_tree == P->tree && b->mf_alpha == P->alpha && volume_bie_ready(P->tree)) return MH_OK;
+    cudaStream_t st = ctx->stream;
+    const int64_t n = b->n;
+    std::vector<double> geo(8 * n), xy(2 * n), nrm(2 * n);
+    std::vector<int32_t> leaf(n);
+    MH_CUDA(ctx, cudaMemcpyAsync(geo.data(), b->geo.p, 8 * n * 8, cudaMemcpyDeviceToHost, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(leaf.data(), P->bnd_leaf.p, n * 4, cudaMemcpyDeviceToHost, st));
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < n; ++i) {
+        const double* g = &geo[8 * i];
+        xy[2 * i] = g[0];
+        xy[2 * i + 1] = g[1];
+        nrm[2 * i] = g[3] / g[6];    // unit normal (y', -x') / |y'|, as in the operator
+        nrm[2 * i + 1] = -g[2] / g[6];
+    }
+    MH_TRY(volume_bie_setup(ctx, P->tree, P->alpha, P->p, xy.data(), nrm.data(), leaf.data(), n));
+    return bie_mfree_setup(ctx, b, P->tree, P->alpha);
+}
+
 extern "C" mh_status mh_problem_regions(mh_ctx* ctx, const mh_problem* p, int32_t* region_host) {
     if (!ctx || !p || !region_host) return mh_fail(ctx, MH_ERR_INVALID_ARG, "null argument");
     MH_CUDA(ctx, cudaMemcpyAsync(region_host, p->region.p, p->tree->n_nodes * 4, cudaMemcpyDeviceToHost, ctx->stream));

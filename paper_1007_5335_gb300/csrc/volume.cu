@@ -619,6 +619,7 @@ struct DfChain {
 };
 
 struct DipData;
+struct BieData;
 
 struct VolData {
     double alpha = -1;
@@ -629,6 +630,7 @@ struct VolData {
     std::vector<int> op_p2m, op_l2p;
     std::vector<std::array<int, 4>> op_m2m, op_l2l;
     std::unique_ptr<DipData> dip;
+    std::unique_ptr<BieData> bie;        // on-surface double layer (matrix-free BIE operator)
     int P = 0, qq = 0;
     int64_t B_off = 0, U_off = 0, M_off = 0, L_off = 0, vec_len = 0;
     dbuf<double> ops64, vec, temp;
@@ -987,6 +989,143 @@ mh_status fetch_tree(mh_ctx* ctx, const mh_tree* t, HostTree* h) {
 }
 
 // Build every operator and pass of the multipole method for (tree, alpha, p).
+// M2M / L2L chains (k_chain_up / k_chain_down) of tree t: the internal boxes of levels
+// 2 <= l < L with their children.  With `active`, only active boxes take part (an inactive
+// child counts as absent).
+mh_status build_chain(mh_ctx* ctx, const mh_tree* t, const HostTree& h, int P, const OpPool& pool,
+                      const std::vector<std::array<int, 4>>& op_m2m, const std::vector<std::array<int, 4>>& op_l2l,
+                      const std::vector<char>* active, std::unique_ptr<DfChain>* out) {
+    const int64_t nb = t->n_boxes;
+    const int L = t->max_level;
+    auto lev = [&](int b) { return h.boxes[3 * b]; };
+    {
+        std::vector<int32_t> child(4 * nb);
+        MH_CUDA(ctx, cudaMemcpyAsync(child.data(), t->box_child.p, 4 * nb * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        std::unique_ptr<DfChain> ch(new DfChain());
+        std::vector<int32_t> idx(nb, -1), parent(nb, -1), quad(nb, -1);
+        if (active)   // children outside the active set are left out (zero expansions, no use)
+            for (int64_t b = 0; b < nb; ++b)
+                for (int c = 0; c < 4; ++c)
+                    if (child[4 * b + c] >= 0 && !(*active)[child[4 * b + c]]) child[4 * b + c] = -1;
+        for (int64_t b = 0; b < nb; ++b)
+            for (int c = 0; c < 4; ++c)
+                if (child[4 * b + c] >= 0) {
+                    parent[child[4 * b + c]] = (int32_t)b;
+                    quad[child[4 * b + c]] = c;
+                }
+        std::vector<int32_t> ubox, ulvl, unext, uneed, uready;
+        std::vector<int4> uchild;
+        std::vector<int64_t> npar(L + 1, 0), nchild(L + 1, 0);
+        for (int64_t b = 0; b < nb; ++b) {
+            const int l = lev((int)b);
+            if (h.box_leaf[b] >= 0 || l < 2 || l >= L || (active && !(*active)[b])) continue;
+            int cnt = 0;
+            for (int c = 0; c < 4; ++c) cnt += child[4 * b + c] >= 0;
+            if (!cnt) continue;
+            idx[b] = (int32_t)ubox.size();
+            ubox.push_back((int32_t)b);
+            ulvl.push_back(l);
+            uchild.push_back(make_int4(child[4 * b], child[4 * b + 1], child[4 * b + 2], child[4 * b + 3]));
+            npar[l] += 1;
+            nchild[l] += cnt;
+        }
+        for (int l = 2; l < L; ++l)
+            if (npar[l]) {
+                ch->flops += 2.0 * P * P * nchild[l];
+                ch->bytes += 8.0 * (4.0 * P * P + 2.0 * P * (nchild[l] + npar[l]));
+            }
+        const int64_t ni = (int64_t)ubox.size();
+        ch->n_int = ni;
+        unext.assign(ni, -1);
+        uneed.assign(ni, 0);
+        // downward blocks: internal boxes with leaf children, each with its internal ancestors
+        std::vector<int32_t> doff{0}, dbox, dop, dlop;
+        std::vector<int4> dleaf;
+        for (int64_t i = 0; i < ni; ++i) {
+            const int b = ubox[i];
+            if (parent[b] >= 0 && idx[parent[b]] >= 0) unext[i] = idx[parent[b]];
+            int leaves[4] = {-1, -1, -1, -1};
+            bool any_leaf = false;
+            for (int c = 0; c < 4; ++c) {
+                const int cb = child[4 * b + c];
+                if (cb < 0) continue;
+                if (idx[cb] >= 0)
+                    uneed[i] += 1;
+                else if (h.box_leaf[cb] >= 0) {
+                    leaves[c] = cb;
+                    any_leaf = true;
+                }
+            }
+            if (uneed[i] == 0) uready.push_back((int32_t)i);
+            if (!any_leaf) continue;
+            std::vector<int32_t> path{b};
+            while (parent[path.back()] >= 0 && idx[parent[path.back()]] >= 0) path.push_back(parent[path.back()]);
+            for (size_t k = path.size(); k-- > 0;) {
+                const int e = path[k];
+                dbox.push_back(e);
+                dop.push_back(k + 1 == path.size() ? -1 : lev(parent[e]) * 4 + quad[e]);
+            }
+            doff.push_back((int32_t)dbox.size());
+            dleaf.push_back(make_int4(leaves[0], leaves[1], leaves[2], leaves[3]));
+            dlop.push_back(ulvl[i] * 4);
+        }
+        ch->n_ready = (int64_t)uready.size();
+        ch->n_down = (int64_t)dleaf.size();
+        // operators, transposed per (level, child position)
+        const size_t PP = (size_t)P * P;
+        std::vector<double> tm((size_t)L * 4 * PP, 0.0), tl((size_t)L * 4 * PP, 0.0);
+        for (int l = 2; l < L; ++l) {
+            if (!npar[l]) continue;
+            for (int c = 0; c < 4; ++c) {
+                const double* om = pool.data.data() + pool.off[op_m2m[l][c]];
+                const double* ol = pool.data.data() + pool.off[op_l2l[l][c]];
+                for (int r = 0; r < P; ++r)
+                    for (int cc = 0; cc < P; ++cc) {
+                        tm[(l * 4 + c) * PP + (size_t)cc * P + r] = om[(size_t)r * P + cc];
+                        tl[(l * 4 + c) * PP + (size_t)cc * P + r] = ol[(size_t)r * P + cc];
+                    }
+            }
+        }
+        std::vector<float> tm32(tm.begin(), tm.end()), tl32(tl.begin(), tl.end());
+        cudaStream_t cs = ctx->stream;
+        auto up_i = [&](dbuf<int32_t>& d, const std::vector<int32_t>& v) -> mh_status {
+            MH_ALLOC(ctx, d, std::max<size_t>(v.size(), 1));
+            if (!v.empty()) MH_CUDA(ctx, cudaMemcpyAsync(d.p, v.data(), v.size() * 4, cudaMemcpyHostToDevice, cs));
+            return MH_OK;
+        };
+        auto up_4 = [&](dbuf<int4>& d, const std::vector<int4>& v) -> mh_status {
+            MH_ALLOC(ctx, d, std::max<size_t>(v.size(), 1));
+            if (!v.empty()) MH_CUDA(ctx, cudaMemcpyAsync(d.p, v.data(), v.size() * 16, cudaMemcpyHostToDevice, cs));
+            return MH_OK;
+        };
+        MH_TRY(up_i(ch->up_box, ubox));
+        MH_TRY(up_i(ch->up_lvl, ulvl));
+        MH_TRY(up_i(ch->up_next, unext));
+        MH_TRY(up_i(ch->up_need, uneed));
+        MH_TRY(up_i(ch->up_ready, uready));
+        MH_TRY(up_4(ch->up_child, uchild));
+        MH_TRY(up_i(ch->dn_off, doff));
+        MH_TRY(up_i(ch->dn_box, dbox));
+        MH_TRY(up_i(ch->dn_op, dop));
+        MH_TRY(up_i(ch->dn_lop, dlop));
+        MH_TRY(up_4(ch->dn_leaf, dleaf));
+        MH_ALLOC(ctx, ch->up_cnt, std::max<int64_t>(ni, 1));
+        MH_CUDA(ctx, cudaMemsetAsync(ch->up_cnt.p, 0, std::max<int64_t>(ni, 1) * sizeof(unsigned), cs));
+        MH_ALLOC(ctx, ch->m2m32, tm32.size());
+        MH_ALLOC(ctx, ch->l2l32, tl32.size());
+        MH_ALLOC(ctx, ch->m2m64, tm.size());
+        MH_ALLOC(ctx, ch->l2l64, tl.size());
+        MH_CUDA(ctx, cudaMemcpyAsync(ch->m2m32.p, tm32.data(), tm32.size() * 4, cudaMemcpyHostToDevice, cs));
+        MH_CUDA(ctx, cudaMemcpyAsync(ch->l2l32.p, tl32.data(), tl32.size() * 4, cudaMemcpyHostToDevice, cs));
+        MH_CUDA(ctx, cudaMemcpyAsync(ch->m2m64.p, tm.data(), tm.size() * 8, cudaMemcpyHostToDevice, cs));
+        MH_CUDA(ctx, cudaMemcpyAsync(ch->l2l64.p, tl.data(), tl.size() * 8, cudaMemcpyHostToDevice, cs));
+        MH_CUDA(ctx, cudaStreamSynchronize(cs));
+        *out = std::move(ch);
+    }
+    return MH_OK;
+}
+
 mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V) {
     const int q = t->q, qq = q * q, P = 2 * p + 1, L = t->max_level;
     const double k = 1.0 / alpha, pref = 1.0 / (2.0 * MH_PI * alpha * alpha);
@@ -1237,127 +1376,7 @@ mh_status volume_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, VolData* V)
         }
     }
     // M2M / L2L chains: the internal boxes of levels 2 <= l < L with their four children
-    {
-        std::vector<int32_t> child(4 * nb);
-        MH_CUDA(ctx, cudaMemcpyAsync(child.data(), t->box_child.p, 4 * nb * 4, cudaMemcpyDeviceToHost, ctx->stream));
-        MH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        std::unique_ptr<DfChain> ch(new DfChain());
-        std::vector<int32_t> idx(nb, -1), parent(nb, -1), quad(nb, -1);
-        for (int64_t b = 0; b < nb; ++b)
-            for (int c = 0; c < 4; ++c)
-                if (child[4 * b + c] >= 0) {
-                    parent[child[4 * b + c]] = (int32_t)b;
-                    quad[child[4 * b + c]] = c;
-                }
-        std::vector<int32_t> ubox, ulvl, unext, uneed, uready;
-        std::vector<int4> uchild;
-        std::vector<int64_t> npar(L + 1, 0), nchild(L + 1, 0);
-        for (int64_t b = 0; b < nb; ++b) {
-            const int l = lev((int)b);
-            if (h.box_leaf[b] >= 0 || l < 2 || l >= L) continue;
-            int cnt = 0;
-            for (int c = 0; c < 4; ++c) cnt += child[4 * b + c] >= 0;
-            if (!cnt) continue;
-            idx[b] = (int32_t)ubox.size();
-            ubox.push_back((int32_t)b);
-            ulvl.push_back(l);
-            uchild.push_back(make_int4(child[4 * b], child[4 * b + 1], child[4 * b + 2], child[4 * b + 3]));
-            npar[l] += 1;
-            nchild[l] += cnt;
-        }
-        for (int l = 2; l < L; ++l)
-            if (npar[l]) {
-                ch->flops += 2.0 * P * P * nchild[l];
-                ch->bytes += 8.0 * (4.0 * P * P + 2.0 * P * (nchild[l] + npar[l]));
-            }
-        const int64_t ni = (int64_t)ubox.size();
-        ch->n_int = ni;
-        unext.assign(ni, -1);
-        uneed.assign(ni, 0);
-        // downward blocks: internal boxes with leaf children, each with its internal ancestors
-        std::vector<int32_t> doff{0}, dbox, dop, dlop;
-        std::vector<int4> dleaf;
-        for (int64_t i = 0; i < ni; ++i) {
-            const int b = ubox[i];
-            if (parent[b] >= 0 && idx[parent[b]] >= 0) unext[i] = idx[parent[b]];
-            int leaves[4] = {-1, -1, -1, -1};
-            bool any_leaf = false;
-            for (int c = 0; c < 4; ++c) {
-                const int cb = child[4 * b + c];
-                if (cb < 0) continue;
-                if (idx[cb] >= 0)
-                    uneed[i] += 1;
-                else if (h.box_leaf[cb] >= 0) {
-                    leaves[c] = cb;
-                    any_leaf = true;
-                }
-            }
-            if (uneed[i] == 0) uready.push_back((int32_t)i);
-            if (!any_leaf) continue;
-            std::vector<int32_t> path{b};
-            while (parent[path.back()] >= 0 && idx[parent[path.back()]] >= 0) path.push_back(parent[path.back()]);
-            for (size_t k = path.size(); k-- > 0;) {
-                const int e = path[k];
-                dbox.push_back(e);
-                dop.push_back(k + 1 == path.size() ? -1 : lev(parent[e]) * 4 + quad[e]);
-            }
-            doff.push_back((int32_t)dbox.size());
-            dleaf.push_back(make_int4(leaves[0], leaves[1], leaves[2], leaves[3]));
-            dlop.push_back(ulvl[i] * 4);
-        }
-        ch->n_ready = (int64_t)uready.size();
-        ch->n_down = (int64_t)dleaf.size();
-        // operators, transposed per (level, child position)
-        const size_t PP = (size_t)P * P;
-        std::vector<double> tm((size_t)L * 4 * PP, 0.0), tl((size_t)L * 4 * PP, 0.0);
-        for (int l = 2; l < L; ++l) {
-            if (!npar[l]) continue;
-            for (int c = 0; c < 4; ++c) {
-                const double* om = pool.data.data() + pool.off[op_m2m[l][c]];
-                const double* ol = pool.data.data() + pool.off[op_l2l[l][c]];
-                for (int r = 0; r < P; ++r)
-                    for (int cc = 0; cc < P; ++cc) {
-                        tm[(l * 4 + c) * PP + (size_t)cc * P + r] = om[(size_t)r * P + cc];
-                        tl[(l * 4 + c) * PP + (size_t)cc * P + r] = ol[(size_t)r * P + cc];
-                    }
-            }
-        }
-        std::vector<float> tm32(tm.begin(), tm.end()), tl32(tl.begin(), tl.end());
-        cudaStream_t cs = ctx->stream;
-        auto up_i = [&](dbuf<int32_t>& d, const std::vector<int32_t>& v) -> mh_status {
-            MH_ALLOC(ctx, d, std::max<size_t>(v.size(), 1));
-            if (!v.empty()) MH_CUDA(ctx, cudaMemcpyAsync(d.p, v.data(), v.size() * 4, cudaMemcpyHostToDevice, cs));
-            return MH_OK;
-        };
-        auto up_4 = [&](dbuf<int4>& d, const std::vector<int4>& v) -> mh_status {
-            MH_ALLOC(ctx, d, std::max<size_t>(v.size(), 1));
-            if (!v.empty()) MH_CUDA(ctx, cudaMemcpyAsync(d.p, v.data(), v.size() * 16, cudaMemcpyHostToDevice, cs));
-            return MH_OK;
-        };
-        MH_TRY(up_i(ch->up_box, ubox));
-        MH_TRY(up_i(ch->up_lvl, ulvl));
-        MH_TRY(up_i(ch->up_next, unext));
-        MH_TRY(up_i(ch->up_need, uneed));
-        MH_TRY(up_i(ch->up_ready, uready));
-        MH_TRY(up_4(ch->up_child, uchild));
-        MH_TRY(up_i(ch->dn_off, doff));
-        MH_TRY(up_i(ch->dn_box, dbox));
-        MH_TRY(up_i(ch->dn_op, dop));
-        MH_TRY(up_i(ch->dn_lop, dlop));
-        MH_TRY(up_4(ch->dn_leaf, dleaf));
-        MH_ALLOC(ctx, ch->up_cnt, std::max<int64_t>(ni, 1));
-        MH_CUDA(ctx, cudaMemsetAsync(ch->up_cnt.p, 0, std::max<int64_t>(ni, 1) * sizeof(unsigned), cs));
-        MH_ALLOC(ctx, ch->m2m32, tm32.size());
-        MH_ALLOC(ctx, ch->l2l32, tl32.size());
-        MH_ALLOC(ctx, ch->m2m64, tm.size());
-        MH_ALLOC(ctx, ch->l2l64, tl.size());
-        MH_CUDA(ctx, cudaMemcpyAsync(ch->m2m32.p, tm32.data(), tm32.size() * 4, cudaMemcpyHostToDevice, cs));
-        MH_CUDA(ctx, cudaMemcpyAsync(ch->l2l32.p, tl32.data(), tl32.size() * 4, cudaMemcpyHostToDevice, cs));
-        MH_CUDA(ctx, cudaMemcpyAsync(ch->m2m64.p, tm.data(), tm.size() * 8, cudaMemcpyHostToDevice, cs));
-        MH_CUDA(ctx, cudaMemcpyAsync(ch->l2l64.p, tl.data(), tl.size() * 8, cudaMemcpyHostToDevice, cs));
-        MH_CUDA(ctx, cudaStreamSynchronize(cs));
-        V->chain = std::move(ch);
-    }
+    MH_TRY(build_chain(ctx, t, h, P, pool, op_m2m, op_l2l, nullptr, &V->chain));
     // near tables on the device, appended to the pool
     const int nnear = (int)near_cfg.size();
     V->n_near_tables = nnear;
@@ -1658,28 +1677,148 @@ static mh_status volume_ensure(mh_ctx* ctx, mh_tree* t, double alpha, int p) {
     return s;
 }
 
+namespace {
+
+// ---- dipole pass set-up helpers (shared by the volume-node and the boundary-node outputs) ----
+
+// Box geometry of the host tree and the expansion scales I_n(k s_l) (s_l = box radius of level l).
+struct DipGeo {
+    const HostTree* h = nullptr;
+    double x0 = 0, y0 = 0, W = 0;
+    std::vector<std::vector<double>> Is;
+    int lev(int b) const { return h->boxes[3 * b]; }
+    double width(int l) const { return W / (double)(1 << l); }
+    std::complex<double> centre(int b) const {
+        const double w = width(lev(b));
+        return std::complex<double>(x0 + (h->boxes[3 * b + 1] + 0.5) * w, y0 + (h->boxes[3 * b + 2] + 0.5) * w);
+    }
+};
+
+DipGeo dip_geo(const mh_tree* t, const HostTree& h, int p, double k) {
+    DipGeo G;
+    G.h = &h;
+    G.x0 = t->box[0];
+    G.y0 = t->box[1];
+    G.W = t->box[2];
+    G.Is.assign(t->max_level + 1, std::vector<double>(p + 2));
+    for (int l = 0; l <= t->max_level; ++l)
+        for (int n = 0; n <= p + 1; ++n) G.Is[l][n] = h_in(n, k * G.width(l) * 0.70710678118654752);
+    return G;
+}
+
+// Entry n of an expansion in the real form [a_0, a_1, b_1, ...] as column col of a matrix with
+// cols columns.
+void dip_set_row(double* m, int cols, int col, int n, std::complex<double> v) {
+    if (n == 0)
+        m[col] = v.real();
+    else {
+        m[(2 * n - 1) * cols + col] = v.real();
+        m[(2 * n) * cols + col] = v.imag();
+    }
+}
+
+// T[|m|] e^{-i m arg v} for a table T of I_n or K_n values at k|v|.
+std::complex<double> dip_g(int m, std::complex<double> v, const std::vector<double>& T) {
+    return T[std::abs(m)] * std::polar(1.0, -m * std::arg(v));
+}
+
+// Operators wider than DIP_CMAX columns are split into column blocks reducing into one destination.
+constexpr int DIP_CMAX = 128;
+void dip_add_split(OpPool& pool, int R, int nc, const std::vector<double>& m, int64_t src, int64_t dst,
+                   std::vector<Task>& tl) {
+    std::vector<double> sub;
+    for (int c0 = 0; c0 < nc; c0 += DIP_CMAX) {
+        const int cw = std::min(DIP_CMAX, nc - c0);
+        sub.assign((size_t)R * cw, 0.0);
+        for (int r = 0; r < R; ++r)
+            for (int c = 0; c < cw; ++c) sub[(size_t)r * cw + c] = m[(size_t)r * nc + c0 + c];
+        tl.push_back(Task{pool.add(R, cw, sub.data()), src + c0, dst});
+    }
+}
+
+// The source side of a dipole pass: per box of level >= 2, the P2M of a leaf's dipoles (weights
+// at W_off + their sorted position, multipoles at DM_off), the M2L over the V list and the dipole
+// P2L over the X list (locals at DL_off).  Dipoles are sorted by leaf: leaf i owns the run
+// [seg0[i], seg0[i] + segn[i]).  With `active` (per box: its subtree holds a dipole, and the
+// targets are the dipoles themselves), M2L and P2L tasks are made only between active boxes:
+// the other multipoles are zero and the other locals are never evaluated.
+void dipole_source_tasks(const DipGeo& G, const VolData* V, OpPool& pool, int p, double k, double pref,
+                         const double* dxy, const double* dnrm, const std::vector<int64_t>& seg0,
+                         const std::vector<int64_t>& segn, int64_t W_off, int64_t DM_off, int64_t DL_off,
+                         std::vector<Task>& t_p2m, std::vector<Task>& t_m2l,
+                         const std::vector<char>* active = nullptr) {
+    const HostTree& h = *G.h;
+    const int P = 2 * p + 1;
+    const int64_t nb = (int64_t)h.box_leaf.size();
+    std::vector<double> buf, Kb(p + 3), Ib(p + 3);
+    for (int64_t b = 0; b < nb; ++b) {
+        const int l = G.lev((int)b);
+        if (l < 2) continue;
+        const int leaf = h.box_leaf[b];
+        // dipole P2M of this leaf
+        if (leaf >= 0 && segn[leaf] > 0) {
+            const int nc = (int)segn[leaf];
+            buf.assign((size_t)P * nc, 0.0);
+            const std::complex<double> c = G.centre((int)b);
+            for (int j = 0; j < nc; ++j) {
+                const int64_t d = seg0[leaf] + j;
+                const std::complex<double> v = std::complex<double>(dxy[2 * d], dxy[2 * d + 1]) - c;
+                const double psi = std::atan2(dnrm[2 * d + 1], dnrm[2 * d]);
+                for (int n = 0; n <= p + 1; ++n) Ib[n] = h_in(n, k * std::abs(v));
+                for (int n = 0; n <= p; ++n) {
+                    const std::complex<double> Dn = 0.5 * k * (std::polar(1.0, -psi) * dip_g(n - 1, v, Ib) +
+                                                               std::polar(1.0, psi) * dip_g(n + 1, v, Ib));
+                    dip_set_row(buf.data(), nc, j, n, pref * Dn / G.Is[l][n]);
+                }
+            }
+            dip_add_split(pool, P, nc, buf, W_off + seg0[leaf], DM_off + b * P, t_p2m);
+        }
+        if (active && !(*active)[b]) continue;
+        for (int j = h.off[1][b]; j < h.off[1][b + 1]; ++j) {
+            const int s2 = h.item[1][j];
+            if (active && !(*active)[s2]) continue;
+            auto key = std::make_tuple(l, h.boxes[3 * s2 + 1] - h.boxes[3 * b + 1], h.boxes[3 * s2 + 2] - h.boxes[3 * b + 2], 0);
+            t_m2l.push_back(Task{V->m2l_key.at(key), DM_off + (int64_t)s2 * P, DL_off + b * P});
+        }
+        // X list: dipole P2L
+        for (int j = h.off[3][b]; j < h.off[3][b + 1]; ++j) {
+            const int c = h.item[3][j];
+            const int lc = h.box_leaf[c];
+            if (segn[lc] == 0) continue;
+            const int nc = (int)segn[lc];
+            buf.assign((size_t)P * nc, 0.0);
+            const std::complex<double> ct = G.centre((int)b);
+            for (int jj = 0; jj < nc; ++jj) {
+                const int64_t d = seg0[lc] + jj;
+                const std::complex<double> u = std::complex<double>(dxy[2 * d], dxy[2 * d + 1]) - ct;
+                const double psi = std::atan2(dnrm[2 * d + 1], dnrm[2 * d]);
+                h_kn_all(k * std::abs(u), p + 1, Kb.data());
+                for (int m = 0; m <= p; ++m) {
+                    const std::complex<double> Dm = -0.5 * k * (std::polar(1.0, -psi) * dip_g(m - 1, u, Kb) +
+                                                                std::polar(1.0, psi) * dip_g(m + 1, u, Kb));
+                    dip_set_row(buf.data(), nc, jj, m, G.Is[l][m] * pref * Dm);
+                }
+            }
+            dip_add_split(pool, P, nc, buf, W_off + seg0[lc], DL_off + b * P, t_m2l);
+        }
+    }
+}
+
+}  // namespace
+
 mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* dxy, const double* dnrm,
                               const int32_t* dleaf, int64_t nd, bool near_blocks) {
     if (!near_blocks && t->q * t->q > 64) near_blocks = true;   // the on-the-fly kernel handles q <= 8
     MH_TRY(volume_ensure(ctx, t, alpha, p));
     VolData* V = static_cast<VolData*>(t->vol);
-    const int q = t->q, qq = q * q, P = 2 * p + 1, L = t->max_level;
+    const int q = t->q, qq = q * q, P = 2 * p + 1;
     const double k = 1.0 / alpha, pref = 1.0 / (2.0 * MH_PI * alpha * alpha);
-    const double x0 = t->box[0], y0 = t->box[1], W = t->box[2];
     HostTree h;
     MH_TRY(fetch_tree(ctx, t, &h));
     const int64_t nb = t->n_boxes, nl = t->n_leaves;
-    auto lev = [&](int b) { return h.boxes[3 * b]; };
-    auto width = [&](int l) { return W / (double)(1 << l); };
-    auto centre = [&](int b) {
-        const double w = width(lev(b));
-        return std::complex<double>(x0 + (h.boxes[3 * b + 1] + 0.5) * w, y0 + (h.boxes[3 * b + 2] + 0.5) * w);
-    };
+    const DipGeo G = dip_geo(t, h, p, k);
     std::vector<double> qx(q), qw(q);
     mh_gauss_legendre(q, qx.data(), qw.data());
-    std::vector<std::vector<double>> Is(L + 1, std::vector<double>(p + 2));
-    for (int l = 0; l <= L; ++l)
-        for (int n = 0; n <= p + 1; ++n) Is[l][n] = h_in(n, k * width(l) * 0.70710678118654752);
     // dipole segments per leaf (sources are sorted by leaf)
     std::vector<int64_t> seg0(nl, -1), segn(nl, 0);
     for (int64_t d = 0; d < nd; ++d) {
@@ -1693,7 +1832,7 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
     D->qq = qq;
     D->pref = pref;
     D->inv_alpha = k;
-    std::vector<int32_t> nptr{0}, nleaf;
+    std::vector<int32_t> nleaf;
     D->W_off = 0;
     D->DM_off = nd;
     D->DL_off = D->DM_off + nb * P;
@@ -1701,115 +1840,47 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
     D->vec_len = D->DU_off + nl * qq;
     OpPool pool = V->pool_host;
     std::vector<Task> t_p2m, t_m2l, t_out;
-    std::vector<double> buf, Kb(p + 3), Ib(p + 3);
-    auto set_row = [&](double* m, int cols, int col, int n, std::complex<double> v) {
-        if (n == 0)
-            m[col] = v.real();
-        else {
-            m[(2 * n - 1) * cols + col] = v.real();
-            m[(2 * n) * cols + col] = v.imag();
-        }
-    };
-    // operators wider than CMAX columns are split into column blocks reducing into one destination
-    constexpr int CMAX = 128;
-    std::vector<double> sub;
-    auto add_split = [&](int R, int nc, const std::vector<double>& m, int64_t src, int64_t dst, std::vector<Task>& tl) {
-        for (int c0 = 0; c0 < nc; c0 += CMAX) {
-            const int cw = std::min(CMAX, nc - c0);
-            sub.assign((size_t)R * cw, 0.0);
-            for (int r = 0; r < R; ++r)
-                for (int c = 0; c < cw; ++c) sub[(size_t)r * cw + c] = m[(size_t)r * nc + c0 + c];
-            tl.push_back(Task{pool.add(R, cw, sub.data()), src + c0, dst});
-        }
-    };
-    auto Gm = [&](int m, std::complex<double> v, const std::vector<double>& I) {
-        return I[std::abs(m)] * std::polar(1.0, -m * std::arg(v));
-    };
+    dipole_source_tasks(G, V, pool, p, k, pref, dxy, dnrm, seg0, segn, D->W_off, D->DM_off, D->DL_off, t_p2m, t_m2l);
+    std::vector<double> buf;
     for (int64_t b = 0; b < nb; ++b) {
-        const int l = lev((int)b);
+        const int l = G.lev((int)b);
         const int leaf = h.box_leaf[b];
-        if (leaf >= 0) {
-            // dipole P2M of this leaf
-            if (l >= 2 && segn[leaf] > 0) {
-                const int nc = (int)segn[leaf];
-                buf.assign((size_t)P * nc, 0.0);
-                const std::complex<double> c = centre((int)b);
-                for (int j = 0; j < nc; ++j) {
-                    const int64_t d = seg0[leaf] + j;
-                    const std::complex<double> v = std::complex<double>(dxy[2 * d], dxy[2 * d + 1]) - c;
-                    const double psi = std::atan2(dnrm[2 * d + 1], dnrm[2 * d]);
-                    for (int n = 0; n <= p + 1; ++n) Ib[n] = h_in(n, k * std::abs(v));
-                    for (int n = 0; n <= p; ++n) {
-                        const std::complex<double> Dn =
-                            0.5 * k * (std::polar(1.0, -psi) * Gm(n - 1, v, Ib) + std::polar(1.0, psi) * Gm(n + 1, v, Ib));
-                        set_row(buf.data(), nc, j, n, pref * Dn / Is[l][n]);
-                    }
-                }
-                add_split(P, nc, buf, D->W_off + seg0[leaf], D->DM_off + b * P, t_p2m);
-            }
-            if (l >= 2) t_out.push_back(Task{V->op_l2p[l], D->DL_off + b * P, D->DU_off + (int64_t)leaf * qq});
-            // W list: M2P with the volume operators
-            for (int j = h.off[2][b]; j < h.off[2][b + 1]; ++j) {
-                const int c = h.item[2][j];
-                auto key = std::make_tuple(l, h.boxes[3 * c + 1] - 2 * h.boxes[3 * b + 1],
-                                           h.boxes[3 * c + 2] - 2 * h.boxes[3 * b + 2], 0);
-                t_out.push_back(Task{V->m2p_key.at(key), D->DM_off + (int64_t)c * P, D->DU_off + (int64_t)leaf * qq});
-            }
-            // U list: direct dipole sums from neighbour leaves, as dense (q^2 x n_c) blocks or
-            // (near_blocks == false) evaluated on the fly by k_dip_near
-            const std::complex<double> cb = centre((int)b);
-            const double wb = width(l);
-            for (int j = h.off[0][b]; j < h.off[0][b + 1]; ++j) {
-                const int c = h.item[0][j];
-                const int lc = h.box_leaf[c];
-                if (segn[lc] == 0) continue;
-                if (!near_blocks) {
-                    nleaf.push_back(lc);
-                    D->near_pairs += (double)qq * segn[lc];
-                    continue;
-                }
-                const int nc = (int)segn[lc];
-                buf.assign((size_t)qq * nc, 0.0);
-                for (int i = 0; i < qq; ++i) {
-                    const double xx = cb.real() + 0.5 * wb * qx[i % q], xy = cb.imag() + 0.5 * wb * qx[i / q];
-                    for (int jj = 0; jj < nc; ++jj) {
-                        const int64_t d = seg0[lc] + jj;
-                        const double dx = dxy[2 * d] - xx, dy = dxy[2 * d + 1] - xy;
-                        const double r = std::hypot(dx, dy);
-                        if (r > 0)
-                            buf[(size_t)i * nc + jj] =
-                                -pref * h_k1(r * k) * k * (dx * dnrm[2 * d] + dy * dnrm[2 * d + 1]) / r;
-                    }
-                }
-                add_split(qq, nc, buf, D->W_off + seg0[lc], D->DU_off + (int64_t)leaf * qq, t_out);
-            }
+        if (leaf < 0) continue;
+        if (l >= 2) t_out.push_back(Task{V->op_l2p[l], D->DL_off + b * P, D->DU_off + (int64_t)leaf * qq});
+        // W list: M2P with the volume operators
+        for (int j = h.off[2][b]; j < h.off[2][b + 1]; ++j) {
+            const int c = h.item[2][j];
+            auto key = std::make_tuple(l, h.boxes[3 * c + 1] - 2 * h.boxes[3 * b + 1],
+                                       h.boxes[3 * c + 2] - 2 * h.boxes[3 * b + 2], 0);
+            t_out.push_back(Task{V->m2p_key.at(key), D->DM_off + (int64_t)c * P, D->DU_off + (int64_t)leaf * qq});
         }
-        if (l < 2) continue;
-        for (int j = h.off[1][b]; j < h.off[1][b + 1]; ++j) {
-            const int s2 = h.item[1][j];
-            auto key = std::make_tuple(l, h.boxes[3 * s2 + 1] - h.boxes[3 * b + 1], h.boxes[3 * s2 + 2] - h.boxes[3 * b + 2], 0);
-            t_m2l.push_back(Task{V->m2l_key.at(key), D->DM_off + (int64_t)s2 * P, D->DL_off + b * P});
-        }
-        // X list: dipole P2L
-        for (int j = h.off[3][b]; j < h.off[3][b + 1]; ++j) {
-            const int c = h.item[3][j];
+        // U list: direct dipole sums from neighbour leaves, as dense (q^2 x n_c) blocks or
+        // (near_blocks == false) evaluated on the fly by k_dip_near
+        const std::complex<double> cb = G.centre((int)b);
+        const double wb = G.width(l);
+        for (int j = h.off[0][b]; j < h.off[0][b + 1]; ++j) {
+            const int c = h.item[0][j];
             const int lc = h.box_leaf[c];
             if (segn[lc] == 0) continue;
+            if (!near_blocks) {
+                nleaf.push_back(lc);
+                D->near_pairs += (double)qq * segn[lc];
+                continue;
+            }
             const int nc = (int)segn[lc];
-            buf.assign((size_t)P * nc, 0.0);
-            const std::complex<double> ct = centre((int)b);
-            for (int jj = 0; jj < nc; ++jj) {
-                const int64_t d = seg0[lc] + jj;
-                const std::complex<double> u = std::complex<double>(dxy[2 * d], dxy[2 * d + 1]) - ct;
-                const double psi = std::atan2(dnrm[2 * d + 1], dnrm[2 * d]);
-                h_kn_all(k * std::abs(u), p + 1, Kb.data());
-                for (int m = 0; m <= p; ++m) {
-                    const std::complex<double> Dm =
-                        -0.5 * k * (std::polar(1.0, -psi) * Gm(m - 1, u, Kb) + std::polar(1.0, psi) * Gm(m + 1, u, Kb));
-                    set_row(buf.data(), nc, jj, m, Is[l][m] * pref * Dm);
+            buf.assign((size_t)qq * nc, 0.0);
+            for (int i = 0; i < qq; ++i) {
+                const double xx = cb.real() + 0.5 * wb * qx[i % q], xy = cb.imag() + 0.5 * wb * qx[i / q];
+                for (int jj = 0; jj < nc; ++jj) {
+                    const int64_t d = seg0[lc] + jj;
+                    const double dx = dxy[2 * d] - xx, dy = dxy[2 * d + 1] - xy;
+                    const double r = std::hypot(dx, dy);
+                    if (r > 0)
+                        buf[(size_t)i * nc + jj] =
+                            -pref * h_k1(r * k) * k * (dx * dnrm[2 * d] + dy * dnrm[2 * d + 1]) / r;
                 }
             }
-            add_split(P, nc, buf, D->W_off + seg0[lc], D->DL_off + b * P, t_m2l);
+            dip_add_split(pool, qq, nc, buf, D->W_off + seg0[lc], D->DU_off + (int64_t)leaf * qq, t_out);
         }
     }
     if (!near_blocks) {
@@ -1829,7 +1900,7 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
         }
         std::vector<double2> lc(nl), pxy(nd), pn(nd);
         for (int64_t i = 0; i < nl; ++i) {
-            const std::complex<double> c = centre(h.leaf_box[i]);
+            const std::complex<double> c = G.centre(h.leaf_box[i]);
             lc[i] = make_double2(c.real(), c.imag());
         }
         for (int64_t d = 0; d < nd; ++d) {
@@ -2030,6 +2101,247 @@ mh_status volume_dipole_apply(mh_ctx* ctx, mh_tree* t, const double* w_sorted, m
         MH_TRY(mixed ? dipole_passes<float>(ctx, V, D, D->ops32.p) : dipole_passes<double>(ctx, V, D, D->ops64.p));
     MH_TRY(mixed ? dipole_out<float>(ctx, D, D->ops32.p) : dipole_out<double>(ctx, D, D->ops64.p));
     *u = D->vec.p + D->DU_off;
+    return MH_OK;
+}
+
+// ---------------- on-surface double layer through the multipole method ----------------
+//
+// The trapezoid part of the discrete system (Section 3.2) without the dense operator: the
+// boundary nodes are both the dipoles (strength w_d = sigma_d |y'_d| h) and the targets, and
+//   u(x_i) = -(1/(2 pi alpha^2)) sum_{d != i} w_d (1/alpha) K1(r/alpha) (y_d - x_i).nu_d / r
+// is formed by the dipole passes of the volume tree (P2M, M2M, M2L + P2L, L2L) followed by an
+// output phase for point targets: per leaf, targets in groups of at most BIE_RT, each group with
+// its L2P at the targets, M2P from its W list and direct dipole blocks from its U list (the
+// leaf itself included, the target's own node left out).  All in binary64.
+namespace {
+
+constexpr int BIE_RT = 16;   // targets per output group (rows of every output operator)
+
+struct BieData {
+    int64_t nd = 0, n_groups = 0;
+    int64_t W_off = 0, DM_off = 0, DL_off = 0, T_off = 0, vec_len = 0;
+    double flops = 0, near_pairs = 0;
+    dbuf<double> vec, temp, ops64;
+    dbuf<int64_t> d_op_off;
+    dbuf<int32_t> d_op_C;
+    dbuf<int32_t> perm;   // sorted position -> node
+    dbuf<int32_t> slot;   // node -> output slot (from T_off)
+    std::unique_ptr<Phase> p2m, m2l, out;
+    std::unique_ptr<DfChain> chain;   // M2M / L2L over the active boxes (own arrival counters)
+};
+
+// Angular part of an expansion row in the real form: v0 at n = 0, then 2 v_n cos(n th) and
+// -2 v_n sin(n th).
+void bie_row(double* row, int p, const double* v, double th) {
+    row[0] = v[0];
+    for (int n = 1; n <= p; ++n) {
+        row[2 * n - 1] = 2 * v[n] * std::cos(n * th);
+        row[2 * n] = -2 * v[n] * std::sin(n * th);
+    }
+}
+
+__global__ void k_bie_gather_w(const double* __restrict__ w, const int32_t* __restrict__ perm, int64_t n,
+                               double* __restrict__ ws) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) ws[i] = w[perm[i]];
+}
+
+__global__ void k_bie_scatter_u(const double* __restrict__ t, const int32_t* __restrict__ slot, int64_t n,
+                                double* __restrict__ u) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) u[i] = t[slot[i]];
+}
+
+}  // namespace
+
+mh_status volume_bie_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, const double* xy, const double* nrm,
+                           const int32_t* leaf, int64_t nd) {
+    MH_TRY(volume_ensure(ctx, t, alpha, p));
+    VolData* V = static_cast<VolData*>(t->vol);
+    const int P = 2 * p + 1;
+    const double k = 1.0 / alpha, pref = 1.0 / (2.0 * MH_PI * alpha * alpha);
+    HostTree h;
+    MH_TRY(fetch_tree(ctx, t, &h));
+    const int64_t nb = t->n_boxes, nl = t->n_leaves;
+    const DipGeo G = dip_geo(t, h, p, k);
+    // nodes sorted by leaf (stable: node order within a leaf)
+    std::vector<int32_t> perm(nd);
+    for (int64_t i = 0; i < nd; ++i) {
+        if (leaf[i] < 0 || leaf[i] >= nl) return mh_fail(ctx, MH_ERR_GEOMETRY, "boundary node %lld has no leaf", (long long)i);
+        perm[i] = (int32_t)i;
+    }
+    std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t c) { return leaf[a] < leaf[c]; });
+    std::vector<double> sxy(2 * nd), snrm(2 * nd);
+    std::vector<int64_t> seg0(nl, -1), segn(nl, 0);
+    for (int64_t j = 0; j < nd; ++j) {
+        const int32_t i = perm[j];
+        sxy[2 * j] = xy[2 * i];
+        sxy[2 * j + 1] = xy[2 * i + 1];
+        snrm[2 * j] = nrm[2 * i];
+        snrm[2 * j + 1] = nrm[2 * i + 1];
+        if (seg0[leaf[i]] < 0) seg0[leaf[i]] = j;
+        segn[leaf[i]]++;
+    }
+    std::unique_ptr<BieData> B(new BieData());
+    B->nd = nd;
+    for (int64_t i = 0; i < nl; ++i) B->n_groups += (segn[i] + BIE_RT - 1) / BIE_RT;
+    B->W_off = 0;
+    B->DM_off = nd;
+    B->DL_off = B->DM_off + nb * P;
+    B->T_off = B->DL_off + nb * P;
+    B->vec_len = B->T_off + B->n_groups * BIE_RT;
+    OpPool pool = V->pool_host;
+    std::vector<Task> t_p2m, t_m2l, t_out;
+    // active boxes: a leaf with boundary nodes and all its ancestors
+    std::vector<char> active(nb, 0);
+    {
+        std::map<std::tuple<int, int, int>, int> id;
+        for (int64_t b = 0; b < nb; ++b) id[std::make_tuple(h.boxes[3 * b], h.boxes[3 * b + 1], h.boxes[3 * b + 2])] = (int)b;
+        for (int64_t b = 0; b < nb; ++b) {
+            const int lf = h.box_leaf[b];
+            if (lf < 0 || segn[lf] == 0) continue;
+            int l = h.boxes[3 * b], x = h.boxes[3 * b + 1], y = h.boxes[3 * b + 2];
+            for (;;) {
+                auto it = id.find(std::make_tuple(l, x, y));
+                if (it == id.end() || active[it->second]) break;
+                active[it->second] = 1;
+                if (l == 0) break;
+                --l;
+                x >>= 1;
+                y >>= 1;
+            }
+        }
+    }
+    dipole_source_tasks(G, V, pool, p, k, pref, sxy.data(), snrm.data(), seg0, segn, B->W_off, B->DM_off, B->DL_off,
+                        t_p2m, t_m2l, &active);
+    MH_TRY(build_chain(ctx, t, h, P, V->pool_host, V->op_m2m, V->op_l2l, &active, &B->chain));
+    std::vector<int32_t> slot(nd);
+    std::vector<double> buf, v(p + 2), Kb(p + 3);
+    int64_t gi = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const int lf = h.box_leaf[b];
+        if (lf < 0 || segn[lf] == 0) continue;
+        const int l = G.lev((int)b);
+        const std::complex<double> cb = G.centre((int)b);
+        for (int64_t g0 = 0; g0 < segn[lf]; g0 += BIE_RT, ++gi) {
+            const int cnt = (int)std::min<int64_t>(BIE_RT, segn[lf] - g0);
+            const int64_t dst = B->T_off + gi * BIE_RT;
+            auto tgt = [&](int i) {
+                const int64_t j = seg0[lf] + g0 + i;
+                return std::complex<double>(sxy[2 * j], sxy[2 * j + 1]);
+            };
+            for (int i = 0; i < cnt; ++i) slot[perm[seg0[lf] + g0 + i]] = (int32_t)(gi * BIE_RT + i);
+            // L2P at the targets
+            if (l >= 2) {
+                buf.assign((size_t)BIE_RT * P, 0.0);
+                for (int i = 0; i < cnt; ++i) {
+                    const std::complex<double> z = tgt(i) - cb;
+                    for (int n = 0; n <= p; ++n) v[n] = h_in(n, k * std::abs(z)) / G.Is[l][n];
+                    bie_row(&buf[(size_t)i * P], p, v.data(), std::arg(z));
+                }
+                t_out.push_back(Task{pool.add(BIE_RT, P, buf.data()), B->DL_off + b * P, dst});
+                B->flops += 2.0 * BIE_RT * P;
+            }
+            // W list: M2P at the targets
+            for (int j = h.off[2][b]; j < h.off[2][b + 1]; ++j) {
+                const int c = h.item[2][j];
+                const std::complex<double> cc = G.centre(c);
+                const int lc = G.lev(c);
+                buf.assign((size_t)BIE_RT * P, 0.0);
+                for (int i = 0; i < cnt; ++i) {
+                    const std::complex<double> z = tgt(i) - cc;
+                    h_kn_all(k * std::abs(z), p, Kb.data());
+                    for (int n = 0; n <= p; ++n) v[n] = G.Is[lc][n] * Kb[n];
+                    bie_row(&buf[(size_t)i * P], p, v.data(), std::arg(z));
+                }
+                t_out.push_back(Task{pool.add(BIE_RT, P, buf.data()), B->DM_off + (int64_t)c * P, dst});
+                B->flops += 2.0 * BIE_RT * P;
+            }
+            // U list: direct dipole blocks (the leaf itself included; r = 0 is the target's own node)
+            for (int j = h.off[0][b]; j < h.off[0][b + 1]; ++j) {
+                const int lc = h.box_leaf[h.item[0][j]];
+                if (segn[lc] == 0) continue;
+                const int nc = (int)segn[lc];
+                buf.assign((size_t)BIE_RT * nc, 0.0);
+                for (int i = 0; i < cnt; ++i) {
+                    const std::complex<double> x = tgt(i);
+                    for (int jj = 0; jj < nc; ++jj) {
+                        const int64_t d = seg0[lc] + jj;
+                        const double dx = sxy[2 * d] - x.real(), dy = sxy[2 * d + 1] - x.imag();
+                        const double r = std::hypot(dx, dy);
+                        if (r > 0)
+                            buf[(size_t)i * nc + jj] =
+                                -pref * h_k1(r * k) * k * (dx * snrm[2 * d] + dy * snrm[2 * d + 1]) / r;
+                    }
+                }
+                dip_add_split(pool, BIE_RT, nc, buf, B->W_off + seg0[lc], dst, t_out);
+                B->near_pairs += (double)cnt * nc;
+                B->flops += 2.0 * BIE_RT * nc;
+            }
+        }
+    }
+    cudaStream_t st = ctx->stream;
+    const int64_t total = (int64_t)pool.data.size();
+    MH_ALLOC(ctx, B->ops64, total);
+    MH_CUDA(ctx, cudaMemcpyAsync(B->ops64.p, pool.data.data(), total * 8, cudaMemcpyHostToDevice, st));
+    MH_ALLOC(ctx, B->d_op_off, pool.off.size());
+    MH_ALLOC(ctx, B->d_op_C, pool.C.size());
+    MH_CUDA(ctx, cudaMemcpyAsync(B->d_op_off.p, pool.off.data(), pool.off.size() * 8, cudaMemcpyHostToDevice, st));
+    MH_CUDA(ctx, cudaMemcpyAsync(B->d_op_C.p, pool.C.data(), pool.C.size() * 4, cudaMemcpyHostToDevice, st));
+    std::vector<int> opC(pool.C.begin(), pool.C.end());
+    int64_t need = 1;
+    B->p2m.reset(new Phase());
+    MH_TRY(build_phase(ctx, t_p2m, P, false, opC, B->p2m.get(), &need));
+    B->m2l.reset(new Phase());
+    MH_TRY(build_phase(ctx, t_m2l, P, false, opC, B->m2l.get(), &need));
+    B->out.reset(new Phase());
+    MH_TRY(build_phase(ctx, t_out, BIE_RT, false, opC, B->out.get(), &need));
+    B->out->dst_out = true;
+    B->flops += B->p2m->flops + B->m2l->flops;
+    MH_ALLOC(ctx, B->vec, B->vec_len);
+    MH_ALLOC(ctx, B->temp, need);
+    MH_CUDA(ctx, cudaMemsetAsync(B->vec.p, 0, B->vec_len * 8, st));
+    MH_ALLOC(ctx, B->perm, std::max<int64_t>(nd, 1));
+    MH_ALLOC(ctx, B->slot, std::max<int64_t>(nd, 1));
+    if (nd) {
+        MH_CUDA(ctx, cudaMemcpyAsync(B->perm.p, perm.data(), nd * 4, cudaMemcpyHostToDevice, st));
+        MH_CUDA(ctx, cudaMemcpyAsync(B->slot.p, slot.data(), nd * 4, cudaMemcpyHostToDevice, st));
+    }
+    MH_CUDA(ctx, cudaStreamSynchronize(st));
+    V->bie = std::move(B);
+    return MH_OK;
+}
+
+bool volume_bie_ready(const mh_tree* t) {
+    const VolData* V = static_cast<const VolData*>(t->vol);
+    return V && V->bie;
+}
+
+// w: dipole strengths in node order (device); u: the trapezoid double layer at every node, in
+// node order (device), as defined above.  Runs on the context stream, with its own M2M / L2L
+// chain over the boxes that hold boundary nodes.
+mh_status volume_bie_apply(mh_ctx* ctx, mh_tree* t, const double* w, double* u) {
+    VolData* V = static_cast<VolData*>(t->vol);
+    if (!V || !V->bie) return mh_fail(ctx, MH_ERR_INVALID_ARG, "on-surface multipole pass not set up");
+    BieData* B = V->bie.get();
+    if (B->nd == 0) return MH_OK;
+    prof_scope ps(ctx, "bie_fmm", B->flops, 0.0);
+    cudaStream_t st = ctx->stream;
+    const unsigned g = (unsigned)mh_grid(B->nd, 256);
+    k_bie_gather_w<<<g, 256, 0, st>>>(w, B->perm.p, B->nd, B->vec.p + B->W_off);
+    MH_LAUNCHED(ctx);
+    auto run = [&](const Phase* ph) {
+        return run_phase_on<double>(ctx, B->ops64.p, B->d_op_off.p, B->d_op_C.p, B->vec.p, B->vec.p, B->temp.p, ph,
+                                    "bie_fmm_contract");
+    };
+    MH_TRY(run(B->p2m.get()));
+    MH_TRY(run_chain<double>(ctx, B->chain.get(), V->P, B->DM_off, B->DL_off, B->vec.p, true, "bie_fmm_chain"));
+    MH_CUDA(ctx, cudaMemsetAsync(B->vec.p + B->DL_off, 0, (B->T_off - B->DL_off) * 8, st));
+    MH_TRY(run(B->m2l.get()));
+    MH_TRY(run_chain<double>(ctx, B->chain.get(), V->P, B->DM_off, B->DL_off, B->vec.p, false, "bie_fmm_chain"));
+    MH_TRY(run(B->out.get()));
+    k_bie_scatter_u<<<g, 256, 0, st>>>(B->vec.p + B->T_off, B->slot.p, B->nd, u);
+    MH_LAUNCHED(ctx);
     return MH_OK;
 }
 
