@@ -1658,6 +1658,7 @@ struct DipData {
     dbuf<int64_t> d_op_off;
     dbuf<int32_t> d_op_C;
     std::unique_ptr<Phase> p2m, m2l, out;
+    std::unique_ptr<DfChain> chain_up;     // M2M over the boxes that hold dipoles
     SideStream side;                       // the near field runs there beside the passes
     TcImages tc;                           // tensor-core images (mixed precision)
 };
@@ -1736,17 +1737,41 @@ void dip_add_split(OpPool& pool, int R, int nc, const std::vector<double>& m, in
     }
 }
 
+// Boxes whose subtree holds a dipole: every leaf with segn > 0 and its ancestors.
+std::vector<char> dipole_active_boxes(const HostTree& h, const std::vector<int64_t>& segn) {
+    const int64_t nb = (int64_t)h.box_leaf.size();
+    std::vector<char> active(nb, 0);
+    std::map<std::tuple<int, int, int>, int> id;
+    for (int64_t b = 0; b < nb; ++b) id[std::make_tuple(h.boxes[3 * b], h.boxes[3 * b + 1], h.boxes[3 * b + 2])] = (int)b;
+    for (int64_t b = 0; b < nb; ++b) {
+        const int lf = h.box_leaf[b];
+        if (lf < 0 || segn[lf] == 0) continue;
+        int l = h.boxes[3 * b], x = h.boxes[3 * b + 1], y = h.boxes[3 * b + 2];
+        for (;;) {
+            auto it = id.find(std::make_tuple(l, x, y));
+            if (it == id.end() || active[it->second]) break;
+            active[it->second] = 1;
+            if (l == 0) break;
+            --l;
+            x >>= 1;
+            y >>= 1;
+        }
+    }
+    return active;
+}
+
 // The source side of a dipole pass: per box of level >= 2, the P2M of a leaf's dipoles (weights
 // at W_off + their sorted position, multipoles at DM_off), the M2L over the V list and the dipole
 // P2L over the X list (locals at DL_off).  Dipoles are sorted by leaf: leaf i owns the run
-// [seg0[i], seg0[i] + segn[i]).  With `active` (per box: its subtree holds a dipole, and the
-// targets are the dipoles themselves), M2L and P2L tasks are made only between active boxes:
-// the other multipoles are zero and the other locals are never evaluated.
+// [seg0[i], seg0[i] + segn[i]).  `active` marks the boxes whose subtree holds a dipole: M2L
+// tasks are made only from active sources (the other multipoles are zero, so leaving them out
+// changes no sum), and with `dst_active_only` (the targets are the dipoles themselves) M2L and
+// P2L tasks only into active boxes (the other locals are never evaluated).
 void dipole_source_tasks(const DipGeo& G, const VolData* V, OpPool& pool, int p, double k, double pref,
                          const double* dxy, const double* dnrm, const std::vector<int64_t>& seg0,
                          const std::vector<int64_t>& segn, int64_t W_off, int64_t DM_off, int64_t DL_off,
                          std::vector<Task>& t_p2m, std::vector<Task>& t_m2l,
-                         const std::vector<char>* active = nullptr) {
+                         const std::vector<char>* active = nullptr, bool dst_active_only = false) {
     const HostTree& h = *G.h;
     const int P = 2 * p + 1;
     const int64_t nb = (int64_t)h.box_leaf.size();
@@ -1773,7 +1798,7 @@ void dipole_source_tasks(const DipGeo& G, const VolData* V, OpPool& pool, int p,
             }
             dip_add_split(pool, P, nc, buf, W_off + seg0[leaf], DM_off + b * P, t_p2m);
         }
-        if (active && !(*active)[b]) continue;
+        if (active && dst_active_only && !(*active)[b]) continue;
         for (int j = h.off[1][b]; j < h.off[1][b + 1]; ++j) {
             const int s2 = h.item[1][j];
             if (active && !(*active)[s2]) continue;
@@ -1840,7 +1865,12 @@ mh_status volume_dipole_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, cons
     D->vec_len = D->DU_off + nl * qq;
     OpPool pool = V->pool_host;
     std::vector<Task> t_p2m, t_m2l, t_out;
-    dipole_source_tasks(G, V, pool, p, k, pref, dxy, dnrm, seg0, segn, D->W_off, D->DM_off, D->DL_off, t_p2m, t_m2l);
+    // multipoles are non-zero only in boxes that hold dipoles: M2L from those alone, and the
+    // upward chain over those alone (the downward chain serves every leaf: targets everywhere)
+    const std::vector<char> active = dipole_active_boxes(h, segn);
+    dipole_source_tasks(G, V, pool, p, k, pref, dxy, dnrm, seg0, segn, D->W_off, D->DM_off, D->DL_off, t_p2m, t_m2l,
+                        &active, false);
+    MH_TRY(build_chain(ctx, t, h, P, V->pool_host, V->op_m2m, V->op_l2l, &active, &D->chain_up));
     std::vector<double> buf;
     for (int64_t b = 0; b < nb; ++b) {
         const int l = G.lev((int)b);
@@ -2023,8 +2053,11 @@ static mh_status dipole_passes(mh_ctx* ctx, VolData* V, DipData* D, const TOP* o
                                  "dlp_fmm_contract", &D->tc);
     };
     MH_TRY(run(D->p2m.get()));
-    MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, pool, true, "dlp_fmm_chain"));
+    MH_TRY(run_chain<TOP>(ctx, D->chain_up.get(), V->P, D->DM_off, D->DL_off, pool, true, "dlp_fmm_chain"));
     if (sizeof(TOP) == 4) MH_TRY(tc_split(ctx, D->tc, 0, D->vec32.p));   // multipoles final
+    // boxes whose V and X lists hold no dipoles get no M2L / P2L task: their locals are zeroed
+    // here, since the downward chain adds into the leaves' locals
+    MH_CUDA(ctx, cudaMemsetAsync(pool + D->DL_off, 0, (D->DU_off - D->DL_off) * sizeof(TOP), ctx->stream));
     MH_TRY(run(D->m2l.get()));
     MH_TRY(run_chain<TOP>(ctx, V->chain.get(), V->P, D->DM_off, D->DL_off, pool, false, "dlp_fmm_chain"));
     if (sizeof(TOP) == 4) MH_TRY(tc_split(ctx, D->tc, 1, D->vec32.p));   // locals final
@@ -2192,28 +2225,9 @@ mh_status volume_bie_setup(mh_ctx* ctx, mh_tree* t, double alpha, int p, const d
     B->vec_len = B->T_off + B->n_groups * BIE_RT;
     OpPool pool = V->pool_host;
     std::vector<Task> t_p2m, t_m2l, t_out;
-    // active boxes: a leaf with boundary nodes and all its ancestors
-    std::vector<char> active(nb, 0);
-    {
-        std::map<std::tuple<int, int, int>, int> id;
-        for (int64_t b = 0; b < nb; ++b) id[std::make_tuple(h.boxes[3 * b], h.boxes[3 * b + 1], h.boxes[3 * b + 2])] = (int)b;
-        for (int64_t b = 0; b < nb; ++b) {
-            const int lf = h.box_leaf[b];
-            if (lf < 0 || segn[lf] == 0) continue;
-            int l = h.boxes[3 * b], x = h.boxes[3 * b + 1], y = h.boxes[3 * b + 2];
-            for (;;) {
-                auto it = id.find(std::make_tuple(l, x, y));
-                if (it == id.end() || active[it->second]) break;
-                active[it->second] = 1;
-                if (l == 0) break;
-                --l;
-                x >>= 1;
-                y >>= 1;
-            }
-        }
-    }
+    const std::vector<char> active = dipole_active_boxes(h, segn);
     dipole_source_tasks(G, V, pool, p, k, pref, sxy.data(), snrm.data(), seg0, segn, B->W_off, B->DM_off, B->DL_off,
-                        t_p2m, t_m2l, &active);
+                        t_p2m, t_m2l, &active, true);
     MH_TRY(build_chain(ctx, t, h, P, V->pool_host, V->op_m2m, V->op_l2l, &active, &B->chain));
     std::vector<int32_t> slot(nd);
     std::vector<double> buf, v(p + 2), Kb(p + 3);
