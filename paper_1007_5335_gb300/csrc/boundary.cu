@@ -559,6 +559,16 @@ __global__ void __launch_bounds__(256) k_gemv_cph(const float* __restrict__ A, c
                 const int o = lane + 32 * u;
                 if (p0 + o < c1) cp_async16(stH + o, h8 + p0 + o);
             }
+            // the piece's x values are loaded while the operator copies are in flight
+            float4 xu[2 * GH_PIECE], xv[2 * GH_PIECE];
+#pragma unroll
+            for (int v = 0; v < 2 * GH_PIECE; ++v) {
+                const int j = lane + 32 * v;
+                if (2 * p0 + j < 2 * c1) {
+                    xu[v] = __ldg(xh4 + 2 * p0 + j);
+                    xv[v] = __ldg(xl4 + 2 * p0 + j);
+                }
+            }
             cp_async_wait_all();
             __syncwarp();   // the binary16 groups were copied by other lanes
 #pragma unroll
@@ -569,7 +579,7 @@ __global__ void __launch_bounds__(256) k_gemv_cph(const float* __restrict__ A, c
                     const uint2 hv = stH2[j];
                     const float2 l01 = __half22float2(*reinterpret_cast<const __half2*>(&hv.x));
                     const float2 l23 = __half22float2(*reinterpret_cast<const __half2*>(&hv.y));
-                    const float4 uv = __ldg(xh4 + 2 * p0 + j), vv = __ldg(xl4 + 2 * p0 + j);
+                    const float4 uv = xu[v], vv = xv[v];
                     ff_acc(hi, lo, av.x, l01.x * SCALE, uv.x, vv.x);
                     ff_acc(hi, lo, av.y, l01.y * SCALE, uv.y, vv.y);
                     ff_acc(hi, lo, av.z, l23.x * SCALE, uv.z, vv.z);
