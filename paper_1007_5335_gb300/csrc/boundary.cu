@@ -2049,9 +2049,10 @@ constexpr int MF_THREADS = 512;
 constexpr int MF_MMAX = 8192;                       // N_k <= 4096
 constexpr int MF_PER = MF_MMAX / MF_THREADS;        // entries per thread in a reordering pass
 
-// Bluestein transform of length N: on entry z holds a_n = x_n conj(b_n) (zeros for n >= N) in
-// bit-reversed order; on return z[k] = M X_k conj(b_k)^{-1} ... precisely: z[k] = conj(Y_k) with
-// Y = the cyclic convolution a * b times M, so that X_k = conj(b_k) conj(z[k]) / M for k < N.
+// The cyclic convolution of Bluestein's transform of length N: on entry z holds
+// a_n = x_n conj(b_n) (zeros for n >= N) in bit-reversed order and bh the transform of the chirp
+// filter; on return z[k] = M conj((a * b)_k), so that X_k = conj(b_k) conj(z[k]) / M for k < N
+// (the inverse transform taken as the forward one of the conjugate).
 __device__ void bluestein_core(double2* z, const double2* tw, const double2* __restrict__ bh, int M, int L) {
     fft64_shared(z, tw, M);
     // pointwise product with the filter's transform, conjugated (the inverse transform as a
@@ -2185,10 +2186,8 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_shift(const double2* __restri
     else
         bluestein_core(z, tw, bh + moff[k], M, L);
     const double sc = 1.0 / (double)M;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const double X = direct ? z[j].x * (double)M : cmul(cconj(b[j]), cconj(z[j])).x;
-        S[(int64_t)p * n + off[k] + j] = X * sc;   // Re y_j = Re X_j
-    }
+    for (int j = threadIdx.x; j < N; j += blockDim.x)   // Re y_j = Re X_j
+        S[(int64_t)p * n + off[k] + j] = direct ? z[j].x : cmul(cconj(b[j]), cconj(z[j])).x * sc;
 }
 
 // Dipole strengths w_i = sigma_i |y'_i| h_k.
