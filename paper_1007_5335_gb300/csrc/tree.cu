@@ -194,20 +194,61 @@ __global__ void k_present(const int32_t* __restrict__ st, int64_t n, int32_t* f)
 }
 
 // Single-pass block scan helpers (exclusive), used with a host loop over chunks.
-__global__ void k_block_scan(const int32_t* __restrict__ in, int64_t n, int32_t* out, int32_t* bsum) {
-    __shared__ int32_t s[1024];
-    int64_t i = blockIdx.x * 1024LL + threadIdx.x;
-    int32_t v = i < n ? in[i] : 0;
-    s[threadIdx.x] = v;
+// Inclusive scan of one value per thread over a block of 1024 threads: warp shuffles inside
+// each warp, then the 32 warp sums scanned by the first warp.  wsum: 32 ints of shared memory;
+// on return wsum[31] holds the block's sum.
+__device__ __forceinline__ int32_t block_incl_scan_1024(int32_t v, int32_t* wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        int32_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
-        __syncthreads();
-        s[threadIdx.x] += t;
+    if (warp == 0) {
+        int32_t w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    return (warp ? wsum[warp - 1] : 0) + x;
+}
+
+// Exclusive scan of each 1024-entry block of `in` (out) and the block sums (bsum).
+__global__ void __launch_bounds__(1024) k_block_scan(const int32_t* __restrict__ in, int64_t n, int32_t* out,
+                                                     int32_t* bsum) {
+    __shared__ int32_t wsum[32];
+    const int64_t i = blockIdx.x * 1024LL + threadIdx.x;
+    const int32_t v = i < n ? in[i] : 0;
+    const int32_t incl = block_incl_scan_1024(v, wsum);
+    if (i < n) out[i] = incl - v;
+    if (threadIdx.x == 1023) bsum[blockIdx.x] = incl;
+}
+
+// Exclusive scan of n block counts by one block of 1024 threads (chunks of 1024 with a carry):
+// off[i] = c[0] + ... + c[i - 1], *total = the sum of all.
+__global__ void __launch_bounds__(1024) k_scan_offsets(const int32_t* __restrict__ c, int64_t n,
+                                                       int32_t* __restrict__ off, int64_t* __restrict__ total) {
+    __shared__ int32_t wsum[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const int32_t v = i < n ? c[i] : 0;
+        const int32_t incl = block_incl_scan_1024(v, wsum);
+        if (i < n) off[i] = (int32_t)(carry + incl - v);
+        __syncthreads();   // every thread has read carry and wsum
+        if (threadIdx.x == 1023) carry += incl;
         __syncthreads();
     }
-    if (i < n) out[i] = s[threadIdx.x] - v;
-    if (threadIdx.x == 1023) bsum[blockIdx.x] = s[1023];
+    if (threadIdx.x == 0) *total = carry;
 }
 
 __global__ void k_add_offsets(int32_t* out, int64_t n, const int32_t* __restrict__ boff) {
@@ -494,31 +535,26 @@ void mh_gauss_legendre(int n, double* x, double* w) {
     }
 }
 
-// exclusive scan of n int32 (device) into out; returns the total
+// exclusive scan of n int32 (device) into out, on the device; the total comes back to the host
+// (it sizes what the caller allocates next)
 static mh_status scan_i32(mh_ctx* ctx, const int32_t* in, int64_t n, int32_t* out, int64_t* total) {
     cudaStream_t st = ctx->stream;
     const int64_t nb = (n + 1023) / 1024;
-    dbuf<int32_t> bsum, boff, bsum2;
-    MH_ALLOC(ctx, bsum, nb + 1);
-    MH_ALLOC(ctx, boff, nb + 1);
-    if (n > 0) {
-        k_block_scan<<<(unsigned)nb, 1024, 0, st>>>(in, n, out, bsum.p);
-        MH_LAUNCHED(ctx);
-    }
-    std::vector<int32_t> hs(nb), ho(nb + 1);
-    if (nb) MH_CUDA(ctx, cudaMemcpyAsync(hs.data(), bsum.p, nb * 4, cudaMemcpyDeviceToHost, st));
+    *total = 0;
+    if (n == 0) return MH_OK;
+    dbuf<int32_t> bsum, boff;
+    dbuf<int64_t> dtot;
+    MH_ALLOC(ctx, bsum, nb);
+    MH_ALLOC(ctx, boff, nb);
+    MH_ALLOC(ctx, dtot, 1);
+    k_block_scan<<<(unsigned)nb, 1024, 0, st>>>(in, n, out, bsum.p);
+    MH_LAUNCHED(ctx);
+    k_scan_offsets<<<1, 1024, 0, st>>>(bsum.p, nb, boff.p, dtot.p);
+    MH_LAUNCHED(ctx);
+    k_add_offsets<<<(unsigned)nb, 1024, 0, st>>>(out, n, boff.p);
+    MH_LAUNCHED(ctx);
+    MH_CUDA(ctx, cudaMemcpyAsync(total, dtot.p, 8, cudaMemcpyDeviceToHost, st));
     MH_CUDA(ctx, cudaStreamSynchronize(st));
-    int64_t acc = 0;
-    for (int64_t i = 0; i < nb; ++i) {
-        ho[i] = (int32_t)acc;
-        acc += hs[i];
-    }
-    if (nb) {
-        MH_CUDA(ctx, cudaMemcpyAsync(boff.p, ho.data(), nb * 4, cudaMemcpyHostToDevice, st));
-        k_add_offsets<<<(unsigned)nb, 1024, 0, st>>>(out, n, boff.p);
-        MH_LAUNCHED(ctx);
-    }
-    *total = acc;
     return MH_OK;
 }
 
@@ -532,16 +568,15 @@ static mh_status gather_level(mh_ctx* ctx, const int32_t* st_level, int64_t n, i
     MH_ALLOC(ctx, bo, nb);
     k_count_status<<<(unsigned)nb, 256, 0, s>>>(st_level, n, want, bc.p);
     MH_LAUNCHED(ctx);
-    std::vector<int32_t> h(nb), o(nb);
-    MH_CUDA(ctx, cudaMemcpyAsync(h.data(), bc.p, nb * 4, cudaMemcpyDeviceToHost, s));
-    MH_CUDA(ctx, cudaStreamSynchronize(s));
+    // block offsets on the device; only the count comes back (it sizes `out`)
+    dbuf<int64_t> dtot;
+    MH_ALLOC(ctx, dtot, 1);
+    k_scan_offsets<<<1, 1024, 0, s>>>(bc.p, nb, bo.p, dtot.p);
+    MH_LAUNCHED(ctx);
     int64_t acc = 0;
-    for (int64_t i = 0; i < nb; ++i) {
-        o[i] = (int32_t)acc;
-        acc += h[i];
-    }
+    MH_CUDA(ctx, cudaMemcpyAsync(&acc, dtot.p, 8, cudaMemcpyDeviceToHost, s));
+    MH_CUDA(ctx, cudaStreamSynchronize(s));
     MH_ALLOC(ctx, out, std::max<int64_t>(acc, 1));
-    MH_CUDA(ctx, cudaMemcpyAsync(bo.p, o.data(), nb * 4, cudaMemcpyHostToDevice, s));
     k_gather_status<<<(unsigned)nb, 256, 0, s>>>(st_level, n, want, bo.p, out.p);
     MH_LAUNCHED(ctx);
     *count = acc;
