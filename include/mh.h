@@ -241,7 +241,8 @@ mh_status mh_problem_destroy(mh_problem* prob);
  * enable = 0 returns to the dense operator (assembled again at its next use).  The pass has its
  * own expansions and M2M/L2L chain (over the boxes that hold boundary nodes); it reads the
  * tree's translation operators, so it stops working (MH_ERR_INVALID_ARG) once the tree's volume
- * operators are rebuilt for another alpha or p. */
+ * operators are rebuilt for another alpha or p.  mh_problem_destroy returns the boundary to the
+ * dense operator. */
 mh_status mh_problem_matrix_free(mh_ctx* ctx, mh_problem* prob, int enable);
 /* Region of every volume node: -1 inside Omega, k on the exterior side of curve k. */
 mh_status mh_problem_regions(mh_ctx* ctx, const mh_problem* prob, int32_t* region_host);

@@ -254,7 +254,14 @@ extern "C" mh_status mh_problem_create(mh_ctx* ctx, mh_tree* tree, mh_boundary* 
 }
 
 extern "C" mh_status mh_problem_destroy(mh_problem* p) {
-    delete static_cast<ProblemImpl*>(p);
+    ProblemImpl* P = static_cast<ProblemImpl*>(p);
+    // a boundary whose matrix-free operator runs on this problem's tree goes back to the dense
+    // operator (assembled again at its next use): the tree may be destroyed after the problem
+    if (P && P->bnd && P->bnd->mf_tree == P->tree) {
+        P->bnd->mfree = false;
+        P->bnd->mf_tree = nullptr;
+    }
+    delete P;
     return MH_OK;
 }
 
