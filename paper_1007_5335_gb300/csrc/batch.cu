@@ -30,6 +30,7 @@ struct mh_batch {
     int64_t loop_nodes = 0;              // GMRES WHILE nodes (bodies of GMRES_LOOP_KERNELS kernels)
     std::vector<const void*> key;
     std::vector<int64_t> key_gen;        // GMRES workspace generation of every problem's boundary
+    std::vector<int64_t> key_opgen;      // operator generation of every boundary when recorded
     double key_tol = -1.0;
     int key_prec = -1;
     void drop_graph() {
@@ -149,6 +150,9 @@ extern "C" mh_status mh_batch_step(mh_ctx* ctx, mh_batch* B, double* const* u_de
     for (int i = 0; i < n; ++i) {
         if (!u_dev[i] || !F_dev[i] || !f_next_dev[i] || !sigma_dev[i])
             return mh_fail(ctx, MH_ERR_INVALID_ARG, "null array for problem %d", i);
+        if (B->probs[i]->bnd->mfree)
+            return mh_fail(ctx, MH_ERR_INVALID_ARG,
+                           "problem %d uses the matrix-free boundary operator: the graph form needs the dense one", i);
         key.insert(key.end(), {u_dev[i], F_dev[i], f_next_dev[i], sigma_dev[i]});
     }
     GraphModeScope scope(B->probs);
@@ -161,13 +165,16 @@ extern "C" mh_status mh_batch_step(mh_ctx* ctx, mh_batch* B, double* const* u_de
     // (reallocated it) forces a new recording
     int S, m;
     gmres_graph_schedule(prec, &S, &m);
-    std::vector<int64_t> gen(n);
+    std::vector<int64_t> gen(n), opgen(n);
     for (int i = 0; i < n; ++i) {
         MH_TRY(gmres_graph_ensure(ctx, B->probs[i]->bnd, m));
         gen[i] = B->probs[i]->bnd->ws.gen;
+        opgen[i] = B->probs[i]->bnd->op.gen;
     }
-    const bool record = !B->exec || key != B->key || gen != B->key_gen || gmres_tol != B->key_tol ||
-                        (int)prec != B->key_prec;
+    // ... and the operator's forms: one reassembled (another alpha) or released since the
+    // recording also forces a new one
+    const bool record = !B->exec || key != B->key || gen != B->key_gen || opgen != B->key_opgen ||
+                        gmres_tol != B->key_tol || (int)prec != B->key_prec;
     if (record) {
         for (auto* p : B->probs) MH_TRY(bie_prepare(ctx, p->bnd, prec));
         // the eager step of this call (makes every lazy allocation)
@@ -212,6 +219,9 @@ extern "C" mh_status mh_batch_step(mh_ctx* ctx, mh_batch* B, double* const* u_de
         MH_CUDA(ctx, cudaGraphInstantiate(&B->exec, B->graph, cudaGraphInstantiateFlagUseNodePriority));
         B->key = key;
         B->key_gen = gen;
+        // the operator forms the graph holds: taken after the eager step, which makes them
+        B->key_opgen.assign(n, 0);
+        for (int i = 0; i < n; ++i) B->key_opgen[i] = B->probs[i]->bnd->op.gen;
         B->key_tol = gmres_tol;
         B->key_prec = (int)prec;
     }

@@ -2415,6 +2415,7 @@ mh_status bie_mfree_setup(mh_ctx* ctx, mh_boundary* b, mh_tree* t, double alpha)
     b->op.A32lo.release();
     b->op.A16lo.release();
     b->op.alpha = -1.0;
+    b->op.gen += 1;
     return MH_OK;
 }
 
@@ -2475,6 +2476,7 @@ mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha) {
     b->op.A32.release();
     b->op.A32lo.release();
     b->op.A16lo.release();
+    b->op.gen += 1;
     b->op.alpha = -1.0;
     cudaStream_t st = ctx->stream;
     dim3 grid((unsigned)mh_grid(n, 256), (unsigned)std::min<int64_t>(n, 65535));
@@ -2494,11 +2496,19 @@ mh_status bie_assemble(mh_ctx* ctx, mh_boundary* b, double alpha) {
 
 static mh_status gemv_cpa_prepare(mh_ctx* ctx);
 
+// The dense forms exist only once bie_assemble has run (the matrix-free set-up releases them).
+static mh_status need_dense(mh_ctx* ctx, const mh_boundary* b) {
+    if (!b->op.A64.p) return mh_fail(ctx, MH_ERR_INVALID_ARG, "the dense boundary operator is not assembled");
+    return MH_OK;
+}
+
 static mh_status ensure_fp32(mh_ctx* ctx, mh_boundary* b) {
     if (b->mfree) return mh_fail(ctx, MH_ERR_INVALID_ARG, "the matrix-free operator runs in binary64 only");
+    MH_TRY(need_dense(ctx, b));
     MH_TRY(gemv_cpa_prepare(ctx));
     if (b->op.A32.p) return MH_OK;
     const int64_t nn = b->n * b->n;
+    b->op.gen += 1;
     MH_ALLOC(ctx, b->op.A32, nn);
     k_to_float<<<152 * 8, 256, 0, ctx->stream>>>(b->op.A64.p, b->op.A32.p, nn);
     MH_LAUNCHED(ctx);
@@ -2619,6 +2629,7 @@ mh_status bie_apply64_gated(mh_ctx* ctx, mh_boundary* b, const double* x, double
     // the gate only skips work whose result the caller then ignores: the matrix-free form
     // always computes
     if (b->mfree) return bie_apply_mfree(ctx, b, x, y);
+    MH_TRY(need_dense(ctx, b));
     const bool mixed = prec == MH_PREC_MIXED;
     if (resid_ff(b, mixed)) {   // the split of x is not part of the timed GEMV region
         resid_split(ctx->stream, b, x);
@@ -2641,6 +2652,7 @@ const double* gmres_final_residual(mh_boundary* b, mh_precision prec, bool graph
 
 mh_status bie_apply(mh_ctx* ctx, mh_boundary* b, const double* x, double* y, mh_precision prec) {
     if (b->mfree) return bie_apply_mfree(ctx, b, x, y);
+    MH_TRY(need_dense(ctx, b));
     if (prec == MH_PREC_MIXED) {
         MH_TRY(ensure_fp32(ctx, b));
         if (!b->x32.p) MH_ALLOC(ctx, b->x32, b->n);
@@ -2764,6 +2776,7 @@ mh_status gmres_run(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, do
     if (max_iter < 1 || max_iter > 1000) return mh_fail(ctx, MH_ERR_INVALID_ARG, "max_iter must be in 1..1000");
     if (bd->mfree && prec != MH_PREC_FP64)
         return mh_fail(ctx, MH_ERR_INVALID_ARG, "the matrix-free operator runs in binary64 only");
+    if (!bd->mfree) MH_TRY(need_dense(ctx, bd));
     MH_TRY(gmres_graph_ensure(ctx, bd, max_iter));
     gmres_ws& ws = bd->ws;
     MH_CUDA(ctx, cudaMemsetAsync(ws.g.p, 0, (max_iter + 2) * 8, ctx->stream));
@@ -3026,6 +3039,7 @@ static mh_status gmres_loop_node(mh_ctx* ctx, mh_boundary* bd, gmres_dev* gs, cu
 mh_status gmres_run_graph(mh_ctx* ctx, mh_boundary* bd, const double* b, double* x, double tol, mh_precision prec,
                           const double* r0, gmres_dev* gs) {
     if (bd->mfree) return mh_fail(ctx, MH_ERR_INVALID_ARG, "the graph form of GMRES needs the dense operator");
+    MH_TRY(need_dense(ctx, bd));
     const int64_t n = bd->n;
     cudaStream_t st = ctx->stream;
     int S, m;

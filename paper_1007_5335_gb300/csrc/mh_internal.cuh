@@ -208,6 +208,7 @@ struct gmres_ws {
 // Assembled boundary operator for one alpha (eq. discrete_sys), row-major N x N.
 struct bie_operator {
     double alpha = -1.0;
+    int64_t gen = 0;     // bumped whenever a form below is allocated or released (recorded graphs hold them)
     dbuf<double> A64;
     dbuf<float> A32;
     dbuf<float> A32lo;   // A64 - A32 rounded to binary32: A32 + A32lo carries A64 to ~2^-48

@@ -270,8 +270,9 @@ extern "C" mh_status mh_problem_matrix_free(mh_ctx* ctx, mh_problem* prob, int e
     ProblemImpl* P = static_cast<ProblemImpl*>(prob);
     mh_boundary* b = P->bnd;
     if (!enable) {
-        b->mfree = false;   // the dense operator is assembled again at the next use
-        return MH_OK;
+        if (!b->mfree) return MH_OK;
+        b->mfree = false;   // back to the dense operator, assembled again now
+        return bie_assemble(ctx, b, P->alpha);
     }
     if (b->mfree && b->mf_tree == P->tree && b->mf_alpha == P->alpha && volume_bie_ready(P->tree)) return MH_OK;
     cudaStream_t st = ctx->stream;
