@@ -179,7 +179,10 @@ mh_status mh_volume_potential(mh_ctx* ctx, mh_tree* tree, double alpha, int p, c
  *   at n_targets points (2 doubles each) assumed inside Omega, with the near-boundary
  *   rule: 16x upsampled density for targets within 10 h_s of a curve, interpolation
  *   along the normal within h_s/4.  n_targets == 0 evaluates nothing (out_dev untouched);
- *   n_targets < 0 is MH_ERR_INVALID_ARG. */
+ *   n_targets < 0 is MH_ERR_INVALID_ARG.
+ * A boundary switched to the matrix-free operator (mh_problem_matrix_free) forms A sigma that
+ * way, in binary64 whatever prec says; alpha must then be the problem's (else
+ * MH_ERR_INVALID_ARG). */
 mh_status mh_double_layer_apply(mh_ctx* ctx, mh_boundary* bnd, double alpha, const double* sigma_dev,
                                 const double* targets_dev, int64_t n_targets, double* out_dev,
                                 mh_precision prec);
@@ -188,7 +191,8 @@ mh_status mh_double_layer_apply(mh_ctx* ctx, mh_boundary* bnd, double alpha, con
  * when ||rhs - A sigma|| <= tol ||rhs|| (the paper uses tol = 1e-10, Section 4).
  * sigma_dev: in = initial guess, out = solution.  MH_PREC_MIXED runs binary32-operator
  * GMRES inside binary64 iterative refinement.  Returns MH_ERR_NOT_CONVERGED (with
- * sigma holding the best iterate) if max_iter iterations do not reach tol. */
+ * sigma holding the best iterate) if max_iter iterations do not reach tol.  With the
+ * matrix-free operator (mh_problem_matrix_free) only MH_PREC_FP64 is accepted. */
 mh_status mh_gmres_solve(mh_ctx* ctx, mh_boundary* bnd, double alpha, const double* rhs_dev,
                          double* sigma_dev, double tol, int max_iter, mh_precision prec,
                          mh_gmres_info* info);
@@ -199,8 +203,9 @@ mh_status mh_gmres_solve(mh_ctx* ctx, mh_boundary* bnd, double alpha, const doub
  * another framework).  Binary64 only.  The Krylov workspace is a fixed array compiled into
  * the library (4.4 MB held on every device that loads it, until the process exits), so:
  *   - N_Gamma <= 8192 and 1 <= max_iter <= 64, else MH_ERR_INVALID_ARG;
- *   - the operator for `alpha` must already be assembled on bnd by an earlier
+ *   - the dense operator for `alpha` must already be assembled on bnd by an earlier
  *     mh_gmres_solve / mh_double_layer_apply / mh_problem_create call with the same alpha
+ *     (a boundary on the matrix-free operator has none: MH_ERR_INVALID_ARG)
  *     (those allocate it), else MH_ERR_INVALID_ARG;
  *   - the first call on a device looks up the array's device address (done once per device,
  *     with that device current); make that first call before any stream capture;
@@ -238,7 +243,7 @@ mh_status mh_problem_destroy(mh_problem* prob);
  * which is released.  Binary64 only: MH_PREC_MIXED solves and the graph form of the step
  * (mh_batch_step) then fail with MH_ERR_INVALID_ARG.  Needs an even node count per curve in
  * [max(2 l, 4), 4096] (else MH_ERR_INVALID_ARG) and every boundary node inside the tree.
- * enable = 0 returns to the dense operator (assembled again at its next use).  The pass has its
+ * enable = 0 returns to the dense operator (assembled again before the call returns).  The pass has its
  * own expansions and M2M/L2L chain (over the boxes that hold boundary nodes); it reads the
  * tree's translation operators, so it stops working (MH_ERR_INVALID_ARG) once the tree's volume
  * operators are rebuilt for another alpha or p.  mh_problem_destroy returns the boundary to the
@@ -397,7 +402,10 @@ mh_status mh_problem_set_warm_start(mh_ctx* ctx, mh_problem* prob, mh_warm_mode 
  * launch: the first call runs the step eagerly and records the graph (one branch per problem on
  * its own stream, GMRES with a fixed schedule of device-gated kernels instead of host
  * read-backs: mixed precision 3 binary64 refinement sweeps x 20 Arnoldi iterations, binary64 40
- * iterations); later calls with the same arrays, tolerance and precision relaunch the graph.
+ * iterations); later calls with the same arrays, tolerance and precision relaunch the graph
+ * (a problem's GMRES workspace grown, or its boundary operator assembled again or released,
+ * since the recording makes the call record anew).  A problem on the matrix-free boundary
+ * operator (mh_problem_matrix_free) is refused with MH_ERR_INVALID_ARG.
  * The step is in place: u_dev[i] is u^N on entry and u^{N+1} on return.  One host
  * synchronisation per call reads the per-problem GMRES results into info_host[i].
  * MH_ERR_NOT_CONVERGED if a problem did not reach gmres_tol within the schedule (its u is the
